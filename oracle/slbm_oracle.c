@@ -1,0 +1,699 @@
+/*
+ * slbm_oracle.c -- plain, slow FP64 CPU oracle of the multi-scale
+ * semi-Lagrangian lattice Boltzmann step of Kallikounis, Dorschner & Karlin,
+ * "Multi-scale semi-Lagrangian lattice Boltzmann method" (arXiv:2102.12559).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the package smoke check and
+ * the CPU-baseline leg of the benchmark load this library.  It shares no code,
+ * header, table or constant with the CUDA path; it is its independent checker.
+ *
+ * It runs the method's steps in the paper's order and notation:
+ *   - Table I: 1-D Gauss-Hermite abscissae and weights, T_L = 1.
+ *   - Eq. (ci), (wi): tensor-product velocity sets D2Q9 / D2Q16 / D2Q25.
+ *   - Eq. (vi), (momf), (momfshort): the full Q x Q moment matrix M_lambda of a
+ *     frame lambda = {u, T}, with v_i = sqrt(theta) c_i + u, theta = T / T_L.
+ *   - Eq. (fll) and the transfer matrix G = M_lambda'^{-1} M_lambda, inverted by
+ *     generic Gauss-Jordan elimination (no Kronecker or Lagrange shortcut).
+ *   - Eq. (feqPond), (feqL0): co-moving equilibrium rho W_i and the lattice
+ *     equilibrium f^L = G_{u,T_L}^{0,T_L} f^eq.
+ *   - Sec. III.B / App. C: lifting f_q -> f_Q (keep the q x q moments, fill the
+ *     rest from the Q-lattice equilibrium, invert M_Q).
+ *   - Sec. III.C / App. C: projection f_Q -> f_q (first q x q moments, invert M_q).
+ *   - Eq. (reconstructionPond), (advectionPond) and the three steps of Sec. III.D:
+ *     departure point, lattice conversion of every collocation node whose
+ *     lattice differs from the target's (memoised, so each node is converted
+ *     at most once per step as the paper prescribes), Lagrange reconstruction.
+ *   - Eq. (Pond_f_equation) with omega_1 = omega_2: BGK relaxation to the
+ *     lattice equilibrium.
+ *   - The Mach refinement criterion of Sec. IV.A (threshold on |u| / c_s).
+ *
+ * Readings where the paper is silent (each also listed in the design notes):
+ *   - "third-order Lagrange polynomials": p = order + 1 collocation points per
+ *     axis; first node floor(x_dep - (p-1)/2 + 1/2), ties rounding up.
+ *   - A per-axis shift within 1e-12 of an integer snaps to it.
+ *   - dt = CFL / max|c| over both lattices of the pair (CFL = 1, Sec. IV).
+ *   - omega = 1 / tau, so nu = (tau - 1/2) T_L dt.
+ *   - The equilibrium that completes a lifted moment vector is the Q-lattice
+ *     equilibrium at the cell's own rho, u (and T = T_L for the athermal model)
+ *     expressed in the frame the populations live in.
+ *   - Boundary ghost nodes hold the boundary state in whichever lattice reads
+ *     them: DIRICHLET = equilibrium at a fixed rho, u; INLET = fixed u with rho
+ *     copied from the first interior node; OUTFLOW = copy of the nearest
+ *     interior node.  A non-periodic y side takes precedence at corners.
+ *
+ * Data layout (private to this file): populations of one cell contiguous,
+ * f[k][cell * Q_k + i], cell = x + nx * y, i = ix + n * iy with the 1-D nodes
+ * in ascending order.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAXN 5
+#define ORC_MAXQ 25
+
+typedef struct {
+    int n, Q;
+    double c[ORC_MAXN], w[ORC_MAXN];      /* 1-D nodes / weights, Table I */
+    double cx[ORC_MAXQ], cy[ORC_MAXQ];    /* 2-D velocities, eq. (ci)     */
+    double W[ORC_MAXQ];                   /* 2-D weights, eq. (wi)        */
+} olat;
+
+/* ---------------------------------------------------------------- Table I */
+
+/* 1-D Gauss-Hermite abscissae and weights with T_L = 1, Table I, nodes in
+ * ascending order.  Returns 0, or -1 for an unsupported n. */
+int orc_gh1d(int n, double *c, double *w)
+{
+    if (n == 3) {               /* D1Q3: 0, +-sqrt(3); 2/3, 1/6 */
+        double a = sqrt(3.0);
+        c[0] = -a;  c[1] = 0.0; c[2] = a;
+        w[0] = 1.0 / 6.0; w[1] = 2.0 / 3.0; w[2] = 1.0 / 6.0;
+        return 0;
+    }
+    if (n == 4) {               /* D1Q4: +-sqrt(3 -+ sqrt 6); (3 +- sqrt 6)/12 */
+        double s6 = sqrt(6.0);
+        double a = sqrt(3.0 - s6), b = sqrt(3.0 + s6);
+        c[0] = -b; c[1] = -a; c[2] = a; c[3] = b;
+        w[0] = (3.0 - s6) / 12.0; w[1] = (3.0 + s6) / 12.0;
+        w[2] = (3.0 + s6) / 12.0; w[3] = (3.0 - s6) / 12.0;
+        return 0;
+    }
+    if (n == 5) {               /* D1Q5: 0, +-sqrt(5 -+ sqrt 10); 8/15, (7 +- 2 sqrt 10)/60 */
+        double s10 = sqrt(10.0);
+        double a = sqrt(5.0 - s10), b = sqrt(5.0 + s10);
+        c[0] = -b; c[1] = -a; c[2] = 0.0; c[3] = a; c[4] = b;
+        w[0] = (7.0 - 2.0 * s10) / 60.0; w[1] = (7.0 + 2.0 * s10) / 60.0;
+        w[2] = 8.0 / 15.0;
+        w[3] = (7.0 + 2.0 * s10) / 60.0; w[4] = (7.0 - 2.0 * s10) / 60.0;
+        return 0;
+    }
+    return -1;
+}
+
+static int make_lattice(int n, olat *L)
+{
+    if (orc_gh1d(n, L->c, L->w)) return -1;
+    L->n = n;
+    L->Q = n * n;
+    for (int iy = 0; iy < n; ++iy)
+        for (int ix = 0; ix < n; ++ix) {
+            int i = ix + n * iy;
+            L->cx[i] = L->c[ix];
+            L->cy[i] = L->c[iy];
+            L->W[i] = L->w[ix] * L->w[iy];      /* eq. (wi) */
+        }
+    return 0;
+}
+
+/* 2-D tensor-product velocity set, eq. (ci)/(wi).  i = ix + n * iy. */
+int orc_lattice(int n, double *cx, double *cy, double *W)
+{
+    olat L;
+    if (make_lattice(n, &L)) return -1;
+    memcpy(cx, L.cx, sizeof(double) * L.Q);
+    memcpy(cy, L.cy, sizeof(double) * L.Q);
+    memcpy(W, L.W, sizeof(double) * L.Q);
+    return 0;
+}
+
+/* ------------------------------------------------------- linear algebra */
+
+static double ipow(double x, int m)
+{
+    double r = 1.0;
+    for (int k = 0; k < m; ++k) r *= x;
+    return r;
+}
+
+/* Generic Gauss-Jordan inversion with partial pivoting, N x N row-major.
+ * Returns 0, or -1 when a pivot vanishes. */
+int orc_invert(int N, const double *A, double *Ainv)
+{
+    double *a = (double *)malloc(sizeof(double) * N * 2 * N);
+    if (!a) return -1;
+    for (int r = 0; r < N; ++r)
+        for (int c = 0; c < 2 * N; ++c)
+            a[r * 2 * N + c] = c < N ? A[r * N + c] : (c - N == r ? 1.0 : 0.0);
+    for (int col = 0; col < N; ++col) {
+        int piv = col;
+        double best = fabs(a[col * 2 * N + col]);
+        for (int r = col + 1; r < N; ++r)
+            if (fabs(a[r * 2 * N + col]) > best) { best = fabs(a[r * 2 * N + col]); piv = r; }
+        if (best == 0.0) { free(a); return -1; }
+        if (piv != col)
+            for (int c = 0; c < 2 * N; ++c) {
+                double t = a[col * 2 * N + c];
+                a[col * 2 * N + c] = a[piv * 2 * N + c];
+                a[piv * 2 * N + c] = t;
+            }
+        double d = a[col * 2 * N + col];
+        for (int c = 0; c < 2 * N; ++c) a[col * 2 * N + c] /= d;
+        for (int r = 0; r < N; ++r) {
+            if (r == col) continue;
+            double m = a[r * 2 * N + col];
+            if (m == 0.0) continue;
+            for (int c = 0; c < 2 * N; ++c) a[r * 2 * N + c] -= m * a[col * 2 * N + c];
+        }
+    }
+    for (int r = 0; r < N; ++r)
+        for (int c = 0; c < N; ++c) Ainv[r * N + c] = a[r * 2 * N + N + c];
+    free(a);
+    return 0;
+}
+
+static void matvec(int N, const double *A, const double *x, double *y)
+{
+    for (int r = 0; r < N; ++r) {
+        double s = 0.0;
+        for (int c = 0; c < N; ++c) s += A[r * N + c] * x[c];
+        y[r] = s;
+    }
+}
+
+/* ------------------------------------------------ moments and frames */
+
+/* Moment matrix of eq. (momf): row r <-> exponents (a, b) = (r % n, r / n),
+ * column i <-> population i; entry (sqrt(theta) c_ix + u_x)^a (sqrt(theta)
+ * c_iy + u_y)^b with theta = T / T_L, T_L = 1, R = 1 (eq. theta, vi).
+ * lam = {u_x, u_y, T}. */
+static void moment_matrix(const olat *L, const double lam[3], double *M)
+{
+    double st = sqrt(lam[2]);
+    for (int r = 0; r < L->Q; ++r) {
+        int a = r % L->n, b = r / L->n;
+        for (int i = 0; i < L->Q; ++i)
+            M[r * L->Q + i] = ipow(st * L->cx[i] + lam[0], a) * ipow(st * L->cy[i] + lam[1], b);
+    }
+}
+
+int orc_moment_matrix(int n, const double lam[3], double *M)
+{
+    olat L;
+    if (make_lattice(n, &L)) return -1;
+    moment_matrix(&L, lam, M);
+    return 0;
+}
+
+/* Transfer matrix G_lambda^lambda' = M_lambda'^{-1} M_lambda, eq. (fll). */
+static int transfer(const olat *L, const double from[3], const double to[3], double *G)
+{
+    int Q = L->Q;
+    double Mf[ORC_MAXQ * ORC_MAXQ], Mt[ORC_MAXQ * ORC_MAXQ], Mti[ORC_MAXQ * ORC_MAXQ];
+    moment_matrix(L, from, Mf);
+    moment_matrix(L, to, Mt);
+    if (orc_invert(Q, Mt, Mti)) return -1;
+    for (int r = 0; r < Q; ++r)
+        for (int c = 0; c < Q; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < Q; ++k) s += Mti[r * Q + k] * Mf[k * Q + c];
+            G[r * Q + c] = s;
+        }
+    return 0;
+}
+
+int orc_transfer(int n, const double from[3], const double to[3], double *G)
+{
+    olat L;
+    if (make_lattice(n, &L)) return -1;
+    return transfer(&L, from, to, G);
+}
+
+/* Co-moving equilibrium f^eq_i = rho W_i, eq. (feqPond), carried into the
+ * frame lam by the transfer matrix: G_{u,T}^{lam} f^eq.  With lam = lattice
+ * frame {0, T_L} this is f^L of eq. (feqL); with T = T_L it is eq. (feqL0). */
+static int feq_in_frame(const olat *L, double rho, double ux, double uy, double T,
+                        const double lam[3], double *f)
+{
+    double G[ORC_MAXQ * ORC_MAXQ], feq[ORC_MAXQ];
+    double own[3] = {ux, uy, T};
+    for (int i = 0; i < L->Q; ++i) feq[i] = rho * L->W[i];
+    if (transfer(L, own, lam, G)) return -1;
+    matvec(L->Q, G, feq, f);
+    return 0;
+}
+
+/* Lattice-frame equilibrium f^L (eq. feqL / feqL0). */
+int orc_eq_lattice(int n, double rho, double ux, double uy, double T, double *f)
+{
+    olat L;
+    double lat[3] = {0.0, 0.0, 1.0};
+    if (make_lattice(n, &L)) return -1;
+    return feq_in_frame(&L, rho, ux, uy, T, lat, f);
+}
+
+/* rho, u and the kinetic temperature of a population vector living in frame
+ * lam (conservation laws of Sec. II.B; T from sum v^2/2 f = rho u^2/2 + rho T,
+ * i.e. C_v = D/2 for the single population, D = 2). */
+static void macro(const olat *L, const double lam[3], const double *f,
+                  double *rho, double *ux, double *uy, double *T)
+{
+    double st = sqrt(lam[2]);
+    double r = 0.0, jx = 0.0, jy = 0.0, e = 0.0;
+    for (int i = 0; i < L->Q; ++i) {
+        double vx = st * L->cx[i] + lam[0], vy = st * L->cy[i] + lam[1];
+        r += f[i];
+        jx += vx * f[i];
+        jy += vy * f[i];
+        e += (vx * vx + vy * vy) * f[i];
+    }
+    *rho = r;
+    *ux = jx / r;
+    *uy = jy / r;
+    *T = (e / r - (*ux) * (*ux) - (*uy) * (*uy)) / 2.0;
+}
+
+/* -------------------------------------------------- lifting / projection */
+
+/* Lifting f_q -> f_Q in frame lam (Sec. III.B, App. C):
+ *   m_q = M_q f_q;  M_{q->Q} = m_q (+) M^eq_{Q-q};  f_Q = M_Q^{-1} M_{q->Q}.
+ * The completing equilibrium is the Q-lattice equilibrium at the cell's rho,
+ * u computed from f_q, and at T = T_fix when T_fix > 0 (athermal model),
+ * else at the kinetic T of f_q; it is expressed in frame lam. */
+static int lift(const olat *Lq, const olat *LQ, const double lam[3], double T_fix,
+                const double *fq, double *fQ)
+{
+    int nq = Lq->n, nQ = LQ->n, Q = LQ->Q;
+    double Mq[ORC_MAXQ * ORC_MAXQ], MQ[ORC_MAXQ * ORC_MAXQ], MQi[ORC_MAXQ * ORC_MAXQ];
+    double mq[ORC_MAXQ], feqQ[ORC_MAXQ], Meq[ORC_MAXQ], M[ORC_MAXQ];
+    double rho, ux, uy, T;
+
+    moment_matrix(Lq, lam, Mq);
+    matvec(Lq->Q, Mq, fq, mq);                   /* m_q = M_q f_q, rows (a + nq b) */
+    macro(Lq, lam, fq, &rho, &ux, &uy, &T);
+    if (T_fix > 0.0) T = T_fix;
+    if (feq_in_frame(LQ, rho, ux, uy, T, lam, feqQ)) return -1;
+    moment_matrix(LQ, lam, MQ);
+    matvec(Q, MQ, feqQ, Meq);                    /* moments of f^{eq,Q} */
+    for (int r = 0; r < Q; ++r) {
+        int a = r % nQ, b = r / nQ;
+        M[r] = (a < nq && b < nq) ? mq[a + nq * b] : Meq[r];
+    }
+    if (orc_invert(Q, MQ, MQi)) return -1;
+    matvec(Q, MQi, M, fQ);                       /* eq. (liftingF) */
+    return 0;
+}
+
+/* Projection f_Q -> f_q in frame lam (Sec. III.C, App. C):
+ *   m_{Q->q} = the first q x q moments of f_Q;  f_q = M_q^{-1} m_{Q->q}. */
+static int project(const olat *LQ, const olat *Lq, const double lam[3],
+                   const double *fQ, double *fq)
+{
+    int nq = Lq->n, q = Lq->Q;
+    double st = sqrt(lam[2]);
+    double Mq[ORC_MAXQ * ORC_MAXQ], Mqi[ORC_MAXQ * ORC_MAXQ], m[ORC_MAXQ];
+    for (int r = 0; r < q; ++r) {
+        int a = r % nq, b = r / nq;
+        double s = 0.0;
+        for (int i = 0; i < LQ->Q; ++i)
+            s += ipow(st * LQ->cx[i] + lam[0], a) * ipow(st * LQ->cy[i] + lam[1], b) * fQ[i];
+        m[r] = s;
+    }
+    moment_matrix(Lq, lam, Mq);
+    if (orc_invert(q, Mq, Mqi)) return -1;
+    matvec(q, Mqi, m, fq);
+    return 0;
+}
+
+int orc_lift(int nq, int nQ, const double lam[3], double T_fix, const double *fq, double *fQ)
+{
+    olat Lq, LQ;
+    if (nq >= nQ || make_lattice(nq, &Lq) || make_lattice(nQ, &LQ)) return -1;
+    return lift(&Lq, &LQ, lam, T_fix, fq, fQ);
+}
+
+int orc_project(int nQ, int nq, const double lam[3], const double *fQ, double *fq)
+{
+    olat Lq, LQ;
+    if (nq >= nQ || make_lattice(nq, &Lq) || make_lattice(nQ, &LQ)) return -1;
+    return project(&LQ, &Lq, lam, fQ, fq);
+}
+
+/* --------------------------------------------------- Lagrange reconstruction */
+
+/* Lagrange interpolation functions a_s of eq. (reconstructionPond) on the p
+ * equispaced collocation points x0, x0+1, ..., x0+p-1, evaluated at xd. */
+void orc_lagrange(int p, double xd, long x0, double *a)
+{
+    for (int s = 0; s < p; ++s) {
+        double v = 1.0;
+        for (int r = 0; r < p; ++r)
+            if (r != s) v *= (xd - (double)(x0 + r)) / (double)(s - r);
+        a[s] = v;
+    }
+}
+
+/* First collocation point for p points around the departure point xd. */
+long orc_first_node(int p, double xd)
+{
+    return (long)floor(xd - 0.5 * (p - 1) + 0.5);
+}
+
+/* ------------------------------------------------------------ the solver */
+
+enum { ORC_BC_OUTFLOW = 0, ORC_BC_DIRICHLET = 1, ORC_BC_INLET = 2 };
+
+typedef struct {
+    int kind;
+    double *rho, *ux, *uy;       /* length = side length, or NULL */
+} obc;
+
+typedef struct {
+    int nx, ny, per_x, per_y;
+    olat L[2];                   /* 0 = low-order lattice q, 1 = high-order Q */
+    double tau, omega, dt;
+    int p;                       /* collocation points per axis */
+    int frame;                   /* 0 = lattice frame */
+    double *f[2];                /* f[k][cell * Q_k + i]; meaningful where flag == k */
+    uint8_t *flag;
+    int crit_kind;               /* 0 = fixed flags, 1 = Mach criterion */
+    double crit_thr;
+    obc bc[4];                   /* x-, x+, y-, y+ */
+    /* per-step memo of node vectors in either lattice, over a padded grid */
+    int H, px, py;
+    double *memo[2];
+    uint8_t *have[2];
+    double Minv_lat[2][ORC_MAXQ * ORC_MAXQ];
+    long steps;
+} orc_t;
+
+static long cidx(const orc_t *s, long x, long y) { return x + (long)s->nx * y; }
+
+void orc_destroy(orc_t *s);
+
+orc_t *orc_create(int nx, int ny, int per_x, int per_y, int n_lo, int n_hi,
+                  double tau, int order, int frame, double cfl)
+{
+    if (nx < 1 || ny < 1 || n_lo >= n_hi || tau <= 0.5 || order < 1 || order > 5 || frame != 0)
+        return NULL;
+    orc_t *s = (orc_t *)calloc(1, sizeof(orc_t));
+    if (!s) return NULL;
+    s->nx = nx; s->ny = ny; s->per_x = per_x; s->per_y = per_y;
+    if (make_lattice(n_lo, &s->L[0]) || make_lattice(n_hi, &s->L[1])) { free(s); return NULL; }
+    s->tau = tau;
+    s->omega = 1.0 / tau;
+    double cmax = 0.0;
+    for (int k = 0; k < 2; ++k)
+        for (int j = 0; j < s->L[k].n; ++j) cmax = fmax(cmax, fabs(s->L[k].c[j]));
+    s->dt = cfl / cmax;                          /* CFL = max|c| dt / dx, Sec. IV */
+    s->p = order + 1;
+    s->frame = frame;
+    long nc = (long)nx * ny;
+    for (int k = 0; k < 2; ++k) {
+        s->f[k] = (double *)calloc(nc * s->L[k].Q, sizeof(double));
+        double lat[3] = {0.0, 0.0, 1.0}, M[ORC_MAXQ * ORC_MAXQ];
+        moment_matrix(&s->L[k], lat, M);
+        orc_invert(s->L[k].Q, M, s->Minv_lat[k]);
+    }
+    s->flag = (uint8_t *)calloc(nc, 1);
+    s->H = s->p + 2;
+    s->px = nx + 2 * s->H;
+    s->py = ny + 2 * s->H;
+    for (int k = 0; k < 2; ++k) {
+        s->memo[k] = (double *)calloc((long)s->px * s->py * s->L[k].Q, sizeof(double));
+        s->have[k] = (uint8_t *)calloc((long)s->px * s->py, 1);
+    }
+    for (int b = 0; b < 4; ++b) s->bc[b].kind = ORC_BC_OUTFLOW;
+    if (!s->f[0] || !s->f[1] || !s->flag || !s->memo[0] || !s->memo[1] || !s->have[0] || !s->have[1]) {
+        orc_destroy(s);
+        return NULL;
+    }
+    return s;
+}
+
+void orc_destroy(orc_t *s)
+{
+    if (!s) return;
+    for (int k = 0; k < 2; ++k) { free(s->f[k]); free(s->memo[k]); free(s->have[k]); }
+    for (int b = 0; b < 4; ++b) { free(s->bc[b].rho); free(s->bc[b].ux); free(s->bc[b].uy); }
+    free(s->flag);
+    free(s);
+}
+
+double orc_dt(const orc_t *s) { return s->dt; }
+
+/* Lattice-frame equilibrium of lattice k in the solver's frame. */
+static void eq_lat(const orc_t *s, int k, double rho, double ux, double uy, double *f)
+{
+    double lat[3] = {0.0, 0.0, 1.0};
+    feq_in_frame(&s->L[k], rho, ux, uy, 1.0, lat, f);
+}
+
+/* Convert the vector of lattice `from` into lattice `to` (lift or project),
+ * lattice frame, athermal (T = T_L). */
+static void convert(const orc_t *s, int from, int to, const double *src, double *dst)
+{
+    double lat[3] = {0.0, 0.0, 1.0};
+    if (from == to) { memcpy(dst, src, sizeof(double) * s->L[to].Q); return; }
+    if (from == 0) lift(&s->L[0], &s->L[1], lat, 1.0, src, dst);
+    else project(&s->L[1], &s->L[0], lat, src, dst);
+}
+
+/* Every cell starts at the equilibrium of both lattices (both representations
+ * valid), flags 0. */
+int orc_init_equilibrium(orc_t *s, const double *rho, const double *ux, const double *uy)
+{
+    long nc = (long)s->nx * s->ny;
+    for (long c = 0; c < nc; ++c)
+        for (int k = 0; k < 2; ++k) eq_lat(s, k, rho[c], ux[c], uy[c], s->f[k] + c * s->L[k].Q);
+    memset(s->flag, 0, nc);
+    return 0;
+}
+
+/* New flags; a cell whose flag changes has its populations lifted or projected. */
+int orc_set_flags(orc_t *s, const uint8_t *fl)
+{
+    long nc = (long)s->nx * s->ny;
+    for (long c = 0; c < nc; ++c) {
+        int nf = fl[c] ? 1 : 0;
+        if (nf != s->flag[c]) {
+            convert(s, s->flag[c], nf, s->f[s->flag[c]] + c * s->L[s->flag[c]].Q, s->f[nf] + c * s->L[nf].Q);
+            s->flag[c] = (uint8_t)nf;
+        }
+    }
+    return 0;
+}
+
+void orc_get_flags(const orc_t *s, uint8_t *fl) { memcpy(fl, s->flag, (size_t)s->nx * s->ny); }
+
+int orc_set_criterion(orc_t *s, int kind, double thr)
+{
+    s->crit_kind = kind;
+    s->crit_thr = thr;
+    return 0;
+}
+
+/* Boundary of a non-periodic side: side 0 = x-, 1 = x+, 2 = y-, 3 = y+.
+ * Arrays run along the side (ny entries for x sides, nx for y sides). */
+int orc_set_bc(orc_t *s, int side, int kind, const double *rho, const double *ux, const double *uy)
+{
+    if (side < 0 || side > 3) return -1;
+    int len = side < 2 ? s->ny : s->nx;
+    obc *b = &s->bc[side];
+    free(b->rho); free(b->ux); free(b->uy);
+    b->rho = b->ux = b->uy = NULL;
+    b->kind = kind;
+    if (rho) { b->rho = (double *)malloc(sizeof(double) * len); memcpy(b->rho, rho, sizeof(double) * len); }
+    if (ux) { b->ux = (double *)malloc(sizeof(double) * len); memcpy(b->ux, ux, sizeof(double) * len); }
+    if (uy) { b->uy = (double *)malloc(sizeof(double) * len); memcpy(b->uy, uy, sizeof(double) * len); }
+    return 0;
+}
+
+static double cell_rho(const orc_t *s, long c)
+{
+    int k = s->flag[c];
+    double r = 0.0;
+    for (int i = 0; i < s->L[k].Q; ++i) r += s->f[k][c * s->L[k].Q + i];
+    return r;
+}
+
+/* Population vector of node (gx, gy) at the old time level, expressed in
+ * lattice k (step 2 of Sec. III.D), with periodic wrap and boundary ghosts. */
+static const double *node_vec(orc_t *s, long gx, long gy, int k)
+{
+    if (s->per_x) gx = ((gx % s->nx) + s->nx) % s->nx;
+    if (s->per_y) gy = ((gy % s->ny) + s->ny) % s->ny;
+    long mx = gx + s->H, my = gy + s->H;
+    long m = mx + (long)s->px * my;
+    int Q = s->L[k].Q;
+    double *out = s->memo[k] + m * Q;
+    if (gx >= 0 && gx < s->nx && gy >= 0 && gy < s->ny) {
+        long c = cidx(s, gx, gy);
+        if (s->flag[c] == k) return s->f[k] + c * Q;        /* native */
+        if (!s->have[k][m]) {
+            convert(s, s->flag[c], k, s->f[s->flag[c]] + c * s->L[s->flag[c]].Q, out);
+            s->have[k][m] = 1;
+        }
+        return out;
+    }
+    if (s->have[k][m]) return out;
+    if (gy < 0 || gy >= s->ny) {                   /* non-periodic y side */
+        const obc *b = &s->bc[gy < 0 ? 2 : 3];
+        long xi = gx < 0 ? 0 : (gx >= s->nx ? s->nx - 1 : gx);
+        long yi = gy < 0 ? 0 : s->ny - 1;
+        if (b->kind == ORC_BC_OUTFLOW) {
+            memcpy(out, node_vec(s, gx, yi, k), sizeof(double) * Q);
+        } else {
+            double rho = b->kind == ORC_BC_INLET ? cell_rho(s, cidx(s, xi, yi)) : b->rho[xi];
+            eq_lat(s, k, rho, b->ux[xi], b->uy[xi], out);
+        }
+    } else {                                       /* non-periodic x side */
+        const obc *b = &s->bc[gx < 0 ? 0 : 1];
+        long xi = gx < 0 ? 0 : s->nx - 1;
+        if (b->kind == ORC_BC_OUTFLOW) {
+            memcpy(out, node_vec(s, xi, gy, k), sizeof(double) * Q);
+        } else {
+            double rho = b->kind == ORC_BC_INLET ? cell_rho(s, cidx(s, xi, gy)) : b->rho[gy];
+            eq_lat(s, k, rho, b->ux[gy], b->uy[gy], out);
+        }
+    }
+    s->have[k][m] = 1;
+    return out;
+}
+
+static double snap(double v)
+{
+    double r = nearbyint(v);
+    return fabs(v - r) < 1e-12 ? r : v;
+}
+
+/* One lattice-frame update of cell (x, y): semi-Lagrangian propagation
+ * (Sec. III.D, eq. advectionPond / reconstructionPond) followed by BGK
+ * collision to the lattice equilibrium (eq. Pond_f_equation with
+ * omega_1 = omega_2, eq. feqL0).  Writes Q_k values to out. */
+static void update_cell(orc_t *s, long x, long y, double *out)
+{
+    int k = s->flag[cidx(s, x, y)];
+    const olat *L = &s->L[k];
+    int p = s->p;
+    double fbar[ORC_MAXQ], ax[8], ay[8];
+    for (int i = 0; i < L->Q; ++i) {
+        double xd = (double)x - snap(L->cx[i] * s->dt);   /* x_dep = x - v_i dt */
+        double yd = (double)y - snap(L->cy[i] * s->dt);
+        long x0 = orc_first_node(p, xd), y0 = orc_first_node(p, yd);
+        orc_lagrange(p, xd, x0, ax);
+        orc_lagrange(p, yd, y0, ay);
+        double acc = 0.0;
+        for (int t = 0; t < p; ++t)
+            for (int u = 0; u < p; ++u)
+                acc += ax[u] * ay[t] * node_vec(s, x0 + u, y0 + t, k)[i];
+        fbar[i] = acc;
+    }
+    double rho = 0.0, jx = 0.0, jy = 0.0, feq[ORC_MAXQ];
+    for (int i = 0; i < L->Q; ++i) {
+        rho += fbar[i];
+        jx += L->cx[i] * fbar[i];
+        jy += L->cy[i] * fbar[i];
+    }
+    eq_lat(s, k, rho, jx / rho, jy / rho, feq);
+    for (int i = 0; i < L->Q; ++i) out[i] = fbar[i] + s->omega * (feq[i] - fbar[i]);
+}
+
+static void reset_memo(orc_t *s)
+{
+    for (int k = 0; k < 2; ++k) memset(s->have[k], 0, (size_t)s->px * s->py);
+}
+
+/* Advance n time steps. */
+int orc_step(orc_t *s, int n)
+{
+    long nc = (long)s->nx * s->ny;
+    double *g[2];
+    for (int k = 0; k < 2; ++k) {
+        g[k] = (double *)malloc(sizeof(double) * nc * s->L[k].Q);
+        if (!g[k]) { free(g[0]); return -1; }
+    }
+    for (int it = 0; it < n; ++it) {
+        reset_memo(s);
+        for (long y = 0; y < s->ny; ++y)
+            for (long x = 0; x < s->nx; ++x) {
+                long c = cidx(s, x, y);
+                int k = s->flag[c];
+                update_cell(s, x, y, g[k] + c * s->L[k].Q);
+            }
+        for (int k = 0; k < 2; ++k) {
+            double *t = s->f[k]; s->f[k] = g[k]; g[k] = t;
+        }
+        /* refinement criterion on the new state: high-order iff Ma > thr,
+         * c_s = sqrt(T_L) = 1 for the athermal model; flips are converted */
+        if (s->crit_kind == 1) {
+            for (long c = 0; c < nc; ++c) {
+                int k = s->flag[c];
+                double rho, ux, uy, T;
+                double lat[3] = {0.0, 0.0, 1.0};
+                macro(&s->L[k], lat, s->f[k] + c * s->L[k].Q, &rho, &ux, &uy, &T);
+                int nf = sqrt(ux * ux + uy * uy) > s->crit_thr ? 1 : 0;
+                if (nf != k) {
+                    convert(s, k, nf, s->f[k] + c * s->L[k].Q, s->f[nf] + c * s->L[nf].Q);
+                    s->flag[c] = (uint8_t)nf;
+                }
+            }
+        }
+        s->steps++;
+    }
+    free(g[0]);
+    free(g[1]);
+    return 0;
+}
+
+/* One step's post-collision vectors of a few cells, without changing the
+ * state: out[j * 25 + i], i < Q of the cell's lattice (flag[c] tells which). */
+int orc_step_cells(orc_t *s, int m, const long *cells, double *out)
+{
+    reset_memo(s);
+    for (int j = 0; j < m; ++j) {
+        long c = cells[j];
+        if (c < 0 || c >= (long)s->nx * s->ny) return -1;
+        update_cell(s, c % s->nx, c / s->nx, out + (long)j * ORC_MAXQ);
+    }
+    return 0;
+}
+
+/* rho, u and kinetic T of every cell from its native populations. */
+int orc_moments(const orc_t *s, double *rho, double *ux, double *uy, double *T)
+{
+    long nc = (long)s->nx * s->ny;
+    double lat[3] = {0.0, 0.0, 1.0};
+    for (long c = 0; c < nc; ++c) {
+        int k = s->flag[c];
+        double r, a, b, t;
+        macro(&s->L[k], lat, s->f[k] + c * s->L[k].Q, &r, &a, &b, &t);
+        rho[c] = r; ux[c] = a; uy[c] = b;
+        if (T) T[c] = t;
+    }
+    return 0;
+}
+
+/* Global sums rho, rho u_x, rho u_y, rho E with E = sum v^2/2 f / rho. */
+int orc_audit(const orc_t *s, double out[4])
+{
+    long nc = (long)s->nx * s->ny;
+    double a[4] = {0, 0, 0, 0};
+    for (long c = 0; c < nc; ++c) {
+        int k = s->flag[c];
+        const olat *L = &s->L[k];
+        for (int i = 0; i < L->Q; ++i) {
+            double f = s->f[k][c * L->Q + i];
+            a[0] += f;
+            a[1] += L->cx[i] * f;
+            a[2] += L->cy[i] * f;
+            a[3] += 0.5 * (L->cx[i] * L->cx[i] + L->cy[i] * L->cy[i]) * f;
+        }
+    }
+    memcpy(out, a, sizeof(a));
+    return 0;
+}
+
+/* Populations of lattice k, cell-major: out[cell * Q_k + i]. */
+int orc_get_pops(const orc_t *s, int k, double *out)
+{
+    memcpy(out, s->f[k], sizeof(double) * (size_t)s->nx * s->ny * s->L[k].Q);
+    return 0;
+}
+
+int orc_set_pops(orc_t *s, int k, const double *in)
+{
+    memcpy(s->f[k], in, sizeof(double) * (size_t)s->nx * s->ny * s->L[k].Q);
+    return 0;
+}
