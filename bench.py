@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Throughput of the multi-scale semi-Lagrangian LBM step on GB300.
+
+Workload (default): the 2-D free jet, 1024 x 512 cells, FP32 populations,
+D2Q9 / D2Q25 pair, cubic Lagrange streaming, inlet slot 32 cells at Mach 0.5
+in a Mach 0.05 co-flow with a seeded 1 % inlet perturbation, outflow
+extrapolation, free-stream top / bottom, Re = 1000 on the slot, and the Mach
+> 0.3 refinement criterion applied after every step.  One bench step = one
+time step of the whole path (interface conversion, fused stream-collide with
+the criterion, ghost / boundary fill) through the C ABI.
+
+Timing: W untimed warm-up steps, then K steps each timed with CUDA events on
+the solver's stream, with L2 flushed (a 256 MiB memset) before every timed
+step.  Per-kernel device times come from the library's own event tracing.
+
+Launch: ``python bench.py`` (1 GPU) or under torchrun with --gpus N: every
+rank advances its own replica of the workload (the path is not sharded
+across GPUs), value = cell updates of all ranks / max-over-ranks time.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "multi-scale SL-LBM MLUPS"
+UNIT = "MLUPS"
+NX, NY, SLOT, MA_JET, MA_CO, RE, THR = 1024, 512, 32, 0.5, 0.05, 1000.0, 0.3
+WORKLOAD = ("free jet 1024x512, FP32, D2Q9/D2Q25, cubic SL streaming, Mach>0.3 criterion "
+            "every step, inlet/outflow/free-stream boundaries")
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_FILES = ["slbm_stream.cuh", "slbm_impl.cuh", "slbm_stream_f32.cu"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_FILES:
+        with open(os.path.join(ROOT, "paper_2102_12559_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def jet_tau(dt: float) -> float:
+    nu = MA_JET * SLOT / RE
+    return nu / dt + 0.5
+
+
+def setup_jet(solver, slbm, J):
+    solver.set_boundary(slbm.SLBM_SIDE_XMIN, slbm.SLBM_BC_INLET, None, J["in_ux"], J["in_uy"])
+    solver.set_boundary(slbm.SLBM_SIDE_XMAX, slbm.SLBM_BC_OUTFLOW)
+    for side in (slbm.SLBM_SIDE_YMIN, slbm.SLBM_SIDE_YMAX):
+        solver.set_boundary(side, slbm.SLBM_BC_DIRICHLET, np.full(NX, J["fs_rho"]),
+                            np.full(NX, J["fs_ux"]), np.full(NX, J["fs_uy"]))
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        for key in ("hbm_gbs", "hbm_GBps", "hbm_copy_gbs"):
+            if key in d:
+                return float(d[key]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def read_traffic(khash: str):
+    """DRAM bytes per stream-collide launch from the committed ncu summary,
+    valid only if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "stream_collide_jet1024x512.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_hash") != khash:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the GPU is loaded."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.proc = None
+        self.uuid = uuid
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(J, tau):
+    """The FP64 oracle as it stands, one full time step of the same workload."""
+    import oracle as O
+    o = O.Oracle(NX, NY, 3, 5, tau=tau, order=3, periodic=(False, False))
+    o.init_equilibrium(J["rho"], J["ux"], J["uy"])
+    o.set_bc(0, O.BC_INLET, None, J["in_ux"], J["in_uy"])
+    o.set_bc(1, O.BC_OUTFLOW)
+    for side in (2, 3):
+        o.set_bc(side, O.BC_DIRICHLET, np.full(NX, J["fs_rho"]), np.full(NX, J["fs_ux"]),
+                 np.full(NX, J["fs_uy"]))
+    o.set_criterion(1, THR)
+    t = time.perf_counter()
+    o.step(1)
+    el = time.perf_counter() - t
+    return {"value": NX * NY / el / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full time step of the {NX}x{NY} jet ({NX * NY} cell updates), FP64, "
+                      f"single thread, {el:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle, each step a bounded sample of the
+    workload (the post-collision update of a fixed random sample of cells)."""
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2102_12559_gb300 import workloads as WL
+    J = WL.free_jet(NX, NY, slot=SLOT, ma_jet=MA_JET, ma_co=MA_CO)
+    o = O.Oracle(NX, NY, 3, 5, tau=0.6, order=3, periodic=(False, False))
+    tau = jet_tau(o.dt)
+    o = O.Oracle(NX, NY, 3, 5, tau=tau, order=3, periodic=(False, False))
+    o.init_equilibrium(J["rho"], J["ux"], J["uy"])
+    o.set_bc(0, O.BC_INLET, None, J["in_ux"], J["in_uy"])
+    o.set_bc(1, O.BC_OUTFLOW)
+    for side in (2, 3):
+        o.set_bc(side, O.BC_DIRICHLET, np.full(NX, J["fs_rho"]), np.full(NX, J["fs_ux"]),
+                 np.full(NX, J["fs_uy"]))
+    o.set_criterion(1, THR)
+    sample = 8192
+    cells = np.random.default_rng(0).choice(NX * NY, sample, replace=False)
+    for _ in range(args.warmup):
+        o.step_cells(cells)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        o.step_cells(cells)
+    el = time.perf_counter() - t
+    value = sample * args.steps / el / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "nx": NX, "ny": NY},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{sample} random cells of the {NX}x{NY} jet per step "
+                                   "(one step's update of each), FP64, single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="slbm", choices=["slbm", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--spinup", type=int, default=0, help="untimed steps before warm-up")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2102_12559_gb300 import slbm, workloads as WL
+    J = WL.free_jet(NX, NY, slot=SLOT, ma_jet=MA_JET, ma_co=MA_CO)
+    stream = torch.cuda.current_stream(dev)
+    solver = slbm.Solver(NX, NY, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=0.6, interp_order=3,
+                         periodic=(False, False), precision=slbm.SLBM_FP32, stream=stream)
+    tau = jet_tau(solver.dt)
+    solver.close()
+    solver = slbm.Solver(NX, NY, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=tau, interp_order=3,
+                         periodic=(False, False), precision=slbm.SLBM_FP32, stream=stream)
+    solver.init_equilibrium(J["rho"], J["ux"], J["uy"])
+    setup_jet(solver, slbm, J)
+    solver.set_criterion(slbm.SLBM_CRIT_MACH, THR)
+    if args.spinup:
+        solver.step(args.spinup)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        solver.step(1)
+    torch.cuda.synchronize(dev)
+    flags_before = solver.get_flags()
+
+    clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    solver.profile(True)
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        solver.step(1)
+        e.record(stream)
+        evs.append((s, e))
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    total_ms = sum(s.elapsed_time(e) for s, e in evs)
+    kern_ms, kern_steps = solver.profile_read()
+    solver.profile(False)
+    flags_after = solver.get_flags()
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    pin = {k: torch.from_numpy(np.ascontiguousarray(J[k], dtype=np.float64)).pin_memory().numpy()
+           for k in ("rho", "ux", "uy")}
+    outs = [torch.empty(NX * NY, dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
+    torch.cuda.synchronize(dev)
+    e2e_steps = args.steps
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    flush_evs = []
+    ev0.record(stream)
+    solver.init_equilibrium(pin["rho"], pin["ux"], pin["uy"])
+    setup_jet(solver, slbm, J)
+    solver.set_criterion(slbm.SLBM_CRIT_MACH, THR)
+    for _ in range(e2e_steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        flush.zero_()
+        b.record(stream)
+        flush_evs.append((a, b))
+        solver.step(1)
+    slbm.slbm_moments(solver.h, NX * NY, outs[0], outs[1], outs[2], None)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    e2e_ms = ev0.elapsed_time(ev1) - sum(a.elapsed_time(b) for a, b in flush_evs)
+    h2d = NX * NY * (3 * 8) + 2 * NY * 8 + 2 * 3 * NX * 8
+    d2h = NX * NY * 3 * 8
+
+    t_local = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    total_ms, e2e_ms = float(t_local[0]), float(t_local[1])
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+
+    ncell = NX * NY
+    value = world * ncell * args.steps / (total_ms * 1e-3) / 1e6
+    e2e_value = world * ncell * e2e_steps / (e2e_ms * 1e-3) / 1e6
+    nhi = 0.5 * (int(flags_before.sum()) + int(flags_after.sum()))
+    # algorithmic bytes of one stream-collide launch (FP32): read + write Q
+    # populations per cell, read the flag, write the next flag
+    bytes_sc = ncell * (8 * 9 + 2) + nhi * 8 * (25 - 9)
+    sc_ms = kern_ms[0] / max(kern_steps, 1)
+    achieved = bytes_sc / (sc_ms * 1e-3) / 1e9
+    peak, peak_src = read_peaks()
+    khash = kernel_hash()
+    traffic = read_traffic(khash)
+    kps = solver.info.kernels_per_step
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "lattices": "D2Q9/D2Q25",
+                   "interp_order": 3, "tau": tau, "criterion": f"Mach>{THR}",
+                   "high_order_fraction": nhi / ncell,
+                   "l2": "flushed (256 MiB memset) before every timed step",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "stream_collide",
+                     "algorithmic_bytes_per_launch": bytes_sc, "launch_ms": sc_ms,
+                     "peak_source": peak_src, "kernel_source_hash": khash},
+        "kernels_ms_per_step": {n: float(kern_ms[i] / max(kern_steps, 1))
+                                for i, n in enumerate(slbm.KERNEL_NAMES)},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / e2e_steps,
+                "d2h_bytes_per_step": d2h / e2e_steps},
+        "gpu_launches": args.steps * kps,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(J, tau)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/*
+ * slbm.h -- C ABI of the GB300 (sm_103a) multi-scale semi-Lagrangian lattice
+ * Boltzmann step of Kallikounis, Dorschner & Karlin, "Multi-scale
+ * semi-Lagrangian lattice Boltzmann method" (arXiv:2102.12559).
+ *
+ * One handle = one 2-D grid of nx x ny cells (dx = 1, T_L = 1, R = 1).  Every
+ * cell carries a flag choosing the low-order lattice (flag 0) or the
+ * high-order lattice (flag 1) of a Gauss-Hermite pair (Table I, eqs. ci/wi).
+ * slbm_step() advances the grid: interface conversion of the populations
+ * that a cell of the other lattice will read (lifting Sec. III.B / projection
+ * Sec. III.C), semi-Lagrangian streaming by tensor-product Lagrange
+ * reconstruction at the departure points x - c_i dt (eqs. reconstructionPond,
+ * advectionPond; the three steps of Sec. III.D), and BGK collision to the
+ * lattice equilibrium f^L (eq. Pond_f_equation with omega_1 = omega_2, eqs.
+ * feqL / feqL0).  Optionally the flags follow the Mach refinement criterion of
+ * Sec. IV.A after every step.  dt follows CFL = max|c_i| dt / dx = 1 over the
+ * pair (Sec. IV); omega = 1 / tau, so the kinematic viscosity is
+ * nu = (tau - 1/2) T_L dt (Sec. II.B).
+ *
+ * Conventions shared by every entry point:
+ *  - Host field arrays are nx * ny doubles (or bytes for flags), row-major
+ *    with x fastest: element (x, y) at index x + nx * y.
+ *  - Population index i = ix + n * iy, with the n 1-D nodes of Table I in
+ *    ascending order; a lattice value below is that n (Q = n * n).
+ *  - Every call returns SLBM_OK or a negative status.  After a CUDA failure the
+ *    handle is sticky-failed: later calls return SLBM_ECUDA.  No call aborts,
+ *    throws or prints.  slbm_last_error() gives a message.
+ *  - Calls that take host arrays copy them; the caller keeps ownership.  The
+ *    handle owns its device memory (or borrows the caller's workspace, see
+ *    slbm_create_in) and frees it in slbm_destroy.
+ *  - slbm_step() is asynchronous on the handle's stream; calls that return
+ *    host data synchronise that stream.
+ *
+ * The library has no CPU fallback: without a usable CUDA device slbm_create
+ * fails with SLBM_ECUDA.
+ */
+#ifndef SLBM_H
+#define SLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SLBM_API __attribute__((visibility("default")))
+#else
+#define SLBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct slbm_s *slbm_t;
+
+/* Status codes. */
+#define SLBM_OK          0
+#define SLBM_EINVAL     -1   /* bad argument: sizes, lattice pair, tau, order, side ... */
+#define SLBM_ENOMEM     -2   /* device or host allocation failed / workspace too small */
+#define SLBM_ECUDA      -3   /* a CUDA call failed; the handle is now unusable */
+#define SLBM_ENONFINITE -4   /* the audit found a non-finite sum */
+#define SLBM_ENOCONV    -5   /* reserved: frame iteration did not converge */
+#define SLBM_ETIMEOUT   -6   /* reserved: a bounded device wait ran out */
+#define SLBM_ESTATE     -7   /* call not valid in the handle's current state */
+
+/* Lattices of Table I, by 1-D node count n: D2Q9 (n=3), D2Q16 (4), D2Q25 (5). */
+#define SLBM_D2Q9  3
+#define SLBM_D2Q16 4
+#define SLBM_D2Q25 5
+
+/* Reference frame of the populations (Sec. II.C): the lattice frame
+ * {u = 0, T = T_L}.  (The co-moving frame is not exposed by this version.) */
+#define SLBM_FRAME_LATTICE 0
+
+/* Storage / arithmetic precision of the populations. */
+#define SLBM_FP32 0          /* float storage, float arithmetic, FP64 conversion moments */
+#define SLBM_FP64 1          /* double storage and arithmetic */
+
+/* Boundary kinds for a non-periodic side (ghost layer contents):
+ *  OUTFLOW   zero-order extrapolation: copy of the nearest interior cell;
+ *  DIRICHLET lattice equilibrium at a prescribed rho, u ("free stream");
+ *  INLET     lattice equilibrium at a prescribed u and the rho of the first
+ *            interior cell (fixed velocity, zero pressure gradient, Sec. IV.A).
+ * A non-periodic y side takes precedence over an x side at the corners. */
+#define SLBM_BC_OUTFLOW   0
+#define SLBM_BC_DIRICHLET 1
+#define SLBM_BC_INLET     2
+
+/* Sides. */
+#define SLBM_SIDE_XMIN 0
+#define SLBM_SIDE_XMAX 1
+#define SLBM_SIDE_YMIN 2
+#define SLBM_SIDE_YMAX 3
+
+/* Refinement criteria (Sec. IV.A). */
+#define SLBM_CRIT_NONE 0     /* flags stay as set by slbm_set_flags */
+#define SLBM_CRIT_MACH 1     /* after every step: flag = (|u| / c_s > threshold), c_s = 1 */
+
+typedef struct {
+    int nx, ny;              /* cells, each >= 1 and >= the stencil width */
+    int periodic_x;          /* 1 = periodic along x, 0 = boundary sides XMIN/XMAX */
+    int periodic_y;          /* 1 = periodic along y, 0 = boundary sides YMIN/YMAX */
+} slbm_grid;
+
+typedef struct {
+    double dt;               /* time step, CFL / max|c| over the pair */
+    double omega;            /* 1 / tau */
+    int q_lo, q_hi;          /* Q of the two lattices */
+    int halo;                /* ghost-layer width in cells */
+    int pitch;               /* row pitch of a population plane, in elements */
+    int rows;                /* rows of a population plane including ghosts */
+    int precision;
+    int kernels_per_step;    /* kernel launches slbm_step issues per time step */
+    size_t workspace_bytes;
+    long long steps;         /* time steps taken so far */
+} slbm_info_t;
+
+/* Device bytes a handle needs for this configuration (the workspace of
+ * slbm_create_in).  Arguments as for slbm_create. */
+SLBM_API int slbm_workspace_bytes(const slbm_grid *g, int lat_lo, int lat_hi, int interp_order,
+                         int precision, size_t *bytes);
+
+/* Create a handle.  lat_lo < lat_hi are SLBM_D2Q* values; tau > 1/2 is the
+ * relaxation time in units of dt (omega = 1/tau, Sec. II.B); interp_order in
+ * 1..5 is the Lagrange order (order + 1 collocation points per axis; 3 =
+ * the paper's third-order polynomials, Sec. II.C); frame must be
+ * SLBM_FRAME_LATTICE; precision SLBM_FP32 or SLBM_FP64; cuda_stream is a
+ * cudaStream_t (NULL = the legacy default stream).  The handle allocates its
+ * own device workspace.  Populations start at rest (rho = 1, u = 0), flags 0,
+ * criterion none, every non-periodic side OUTFLOW. */
+SLBM_API int slbm_create(const slbm_grid *g, int lat_lo, int lat_hi, double tau, int interp_order,
+                int frame, int precision, void *cuda_stream, slbm_t *out);
+
+/* Same, but the device workspace is the caller's: `workspace` is a device
+ * pointer aligned to 256 bytes with at least slbm_workspace_bytes() bytes,
+ * which must outlive the handle.  The handle never frees it. */
+SLBM_API int slbm_create_in(const slbm_grid *g, int lat_lo, int lat_hi, double tau, int interp_order,
+                   int frame, int precision, void *cuda_stream, void *workspace,
+                   size_t workspace_bytes, slbm_t *out);
+
+/* Synchronise, release device memory the handle owns, free the handle. */
+SLBM_API int slbm_destroy(slbm_t h);
+
+SLBM_API int slbm_get_info(slbm_t h, slbm_info_t *info);
+
+/* Set every cell to the lattice equilibrium f^L(rho, u) (eq. feqL0) of BOTH
+ * lattices; flags are kept.  rho, ux, uy: host, nx*ny each; T must be NULL
+ * (athermal model, T = T_L). */
+SLBM_API int slbm_init_equilibrium(slbm_t h, const double *rho, const double *ux, const double *uy,
+                          const double *T);
+
+/* Set the flags (host, nx*ny bytes, 0 = lat_lo, nonzero = lat_hi).  Cells whose
+ * flag changes have their populations lifted or projected (Sec. III.B-C). */
+SLBM_API int slbm_set_flags(slbm_t h, const uint8_t *flags);
+SLBM_API int slbm_get_flags(slbm_t h, uint8_t *flags);
+
+/* Refinement criterion (SLBM_CRIT_*), threshold on the Mach number |u| / c_s,
+ * c_s = sqrt(T_L) = 1.  SLBM_CRIT_MACH is applied at once to the current
+ * state (flips lifted / projected, asynchronous) and after every step. */
+SLBM_API int slbm_set_criterion(slbm_t h, int kind, double threshold);
+
+/* Boundary of a non-periodic side.  Arrays run along the side (ny entries
+ * for XMIN/XMAX, nx for YMIN/YMAX), host doubles, copied: DIRICHLET needs
+ * rho, ux, uy; INLET needs ux, uy (rho NULL); OUTFLOW needs none. */
+SLBM_API int slbm_set_boundary(slbm_t h, int side, int kind, const double *rho, const double *ux,
+                      const double *uy);
+
+/* Advance n >= 0 time steps (asynchronous). */
+SLBM_API int slbm_step(slbm_t h, int n);
+
+/* Wait for the handle's stream. */
+SLBM_API int slbm_sync(slbm_t h);
+
+/* rho, u and the kinetic temperature T = (sum v^2 f / rho - u^2) / 2 of every
+ * cell from its own lattice's populations (Sec. II.B).  Host outputs of nx*ny
+ * doubles; any pointer may be NULL.  Synchronises. */
+SLBM_API int slbm_moments(slbm_t h, double *rho, double *ux, double *uy, double *T);
+
+/* Same into device arrays of nx*ny doubles (asynchronous; NULL skips). */
+SLBM_API int slbm_moments_device(slbm_t h, double *rho, double *ux, double *uy, double *T);
+
+/* FP64 global sums over all cells: out = {sum rho, sum rho u_x, sum rho u_y,
+ * sum rho E}, rho E = sum v^2/2 f.  Returns SLBM_ENONFINITE if any is not
+ * finite.  Synchronises. */
+SLBM_API int slbm_audit(slbm_t h, double out[4]);
+
+/* Populations of lattice k (0 = lat_lo, 1 = lat_hi) of every cell, host
+ * doubles, plane-major: out[i * nx * ny + x + nx * y].  Only cells whose
+ * flag is k (plus interface cells) hold meaningful values.  Synchronises. */
+SLBM_API int slbm_get_pops(slbm_t h, int k, double *out);
+
+/* Overwrite the populations of lattice k (same layout).  The caller is
+ * responsible for both representations where cells of the other lattice
+ * read them; a subsequent slbm_set_flags with the current flags refreshes
+ * the interface cells. */
+SLBM_API int slbm_set_pops(slbm_t h, int k, const double *in);
+
+/* Snapshot / restore the full state (populations of both lattices, flags,
+ * step count) in a host buffer.  Call with buf = NULL to get the size. */
+SLBM_API int slbm_get_state(slbm_t h, void *buf, size_t *bytes);
+SLBM_API int slbm_set_state(slbm_t h, const void *buf, size_t bytes);
+
+/* Per-kernel timing (tracing).  slbm_profile(h, 1) clears previous records
+ * and starts bracketing every kernel slbm_step launches with CUDA events on
+ * the handle's stream; slbm_profile(h, 0) stops.  slbm_profile_read()
+ * synchronises and returns, per kernel of the step sequence (index 0 =
+ * stream-collide, 1 = interface conversion, 2 = ghost / boundary fill), the
+ * summed device milliseconds over the recorded steps, and the number of
+ * recorded steps.  ms must hold SLBM_PROFILE_KERNELS doubles. */
+#define SLBM_PROFILE_KERNELS 3
+SLBM_API int slbm_profile(slbm_t h, int enable);
+SLBM_API int slbm_profile_read(slbm_t h, double *ms, long long *steps);
+
+/* Message of the last failure on this handle ("" if none); h may be NULL for
+ * the last creation failure of the calling thread. */
+SLBM_API const char *slbm_last_error(slbm_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLBM_H */

@@ -196,20 +196,27 @@ int orc_moment_matrix(int n, const double lam[3], double *M)
     return 0;
 }
 
-/* Transfer matrix G_lambda^lambda' = M_lambda'^{-1} M_lambda, eq. (fll). */
-static int transfer(const olat *L, const double from[3], const double to[3], double *G)
+/* G = Mti M_from, with Mti = M_to^{-1} already formed. */
+static void transfer_inv(const olat *L, const double from[3], const double *Mti, double *G)
 {
     int Q = L->Q;
-    double Mf[ORC_MAXQ * ORC_MAXQ], Mt[ORC_MAXQ * ORC_MAXQ], Mti[ORC_MAXQ * ORC_MAXQ];
+    double Mf[ORC_MAXQ * ORC_MAXQ];
     moment_matrix(L, from, Mf);
-    moment_matrix(L, to, Mt);
-    if (orc_invert(Q, Mt, Mti)) return -1;
     for (int r = 0; r < Q; ++r)
         for (int c = 0; c < Q; ++c) {
             double s = 0.0;
             for (int k = 0; k < Q; ++k) s += Mti[r * Q + k] * Mf[k * Q + c];
             G[r * Q + c] = s;
         }
+}
+
+/* Transfer matrix G_lambda^lambda' = M_lambda'^{-1} M_lambda, eq. (fll). */
+static int transfer(const olat *L, const double from[3], const double to[3], double *G)
+{
+    double Mt[ORC_MAXQ * ORC_MAXQ], Mti[ORC_MAXQ * ORC_MAXQ];
+    moment_matrix(L, to, Mt);
+    if (orc_invert(L->Q, Mt, Mti)) return -1;
+    transfer_inv(L, from, Mti, G);
     return 0;
 }
 
@@ -433,11 +440,17 @@ void orc_destroy(orc_t *s)
 
 double orc_dt(const orc_t *s) { return s->dt; }
 
-/* Lattice-frame equilibrium of lattice k in the solver's frame. */
+/* Lattice-frame equilibrium of lattice k, f^L = G_{u,T_L}^{0,T_L} rho W
+ * (eq. feqL0); the inverse of the constant lattice-frame moment matrix is
+ * formed once at creation (same arithmetic as feq_in_frame). */
 static void eq_lat(const orc_t *s, int k, double rho, double ux, double uy, double *f)
 {
-    double lat[3] = {0.0, 0.0, 1.0};
-    feq_in_frame(&s->L[k], rho, ux, uy, 1.0, lat, f);
+    const olat *L = &s->L[k];
+    double G[ORC_MAXQ * ORC_MAXQ], feq[ORC_MAXQ];
+    double own[3] = {ux, uy, 1.0};
+    for (int i = 0; i < L->Q; ++i) feq[i] = rho * L->W[i];
+    transfer_inv(L, own, s->Minv_lat[k], G);
+    matvec(L->Q, G, feq, f);
 }
 
 /* Convert the vector of lattice `from` into lattice `to` (lift or project),
@@ -477,10 +490,32 @@ int orc_set_flags(orc_t *s, const uint8_t *fl)
 
 void orc_get_flags(const orc_t *s, uint8_t *fl) { memcpy(fl, s->flag, (size_t)s->nx * s->ny); }
 
+/* Refinement criterion of Sec. IV.A on the current state: high-order iff
+ * Ma = |u| / c_s > thr with c_s = sqrt(T_L) = 1 (athermal model); a cell whose
+ * flag flips has its populations lifted or projected. */
+static void apply_criterion(orc_t *s)
+{
+    long nc = (long)s->nx * s->ny;
+    double lat[3] = {0.0, 0.0, 1.0};
+    for (long c = 0; c < nc; ++c) {
+        int k = s->flag[c];
+        double rho, ux, uy, T;
+        macro(&s->L[k], lat, s->f[k] + c * s->L[k].Q, &rho, &ux, &uy, &T);
+        int nf = sqrt(ux * ux + uy * uy) > s->crit_thr ? 1 : 0;
+        if (nf != k) {
+            convert(s, k, nf, s->f[k] + c * s->L[k].Q, s->f[nf] + c * s->L[nf].Q);
+            s->flag[c] = (uint8_t)nf;
+        }
+    }
+}
+
+/* kind 0: flags stay fixed; kind 1: Mach criterion, applied at once to the
+ * current state and after every step from then on. */
 int orc_set_criterion(orc_t *s, int kind, double thr)
 {
     s->crit_kind = kind;
     s->crit_thr = thr;
+    if (kind == 1) apply_criterion(s);
     return 0;
 }
 
@@ -615,21 +650,7 @@ int orc_step(orc_t *s, int n)
         for (int k = 0; k < 2; ++k) {
             double *t = s->f[k]; s->f[k] = g[k]; g[k] = t;
         }
-        /* refinement criterion on the new state: high-order iff Ma > thr,
-         * c_s = sqrt(T_L) = 1 for the athermal model; flips are converted */
-        if (s->crit_kind == 1) {
-            for (long c = 0; c < nc; ++c) {
-                int k = s->flag[c];
-                double rho, ux, uy, T;
-                double lat[3] = {0.0, 0.0, 1.0};
-                macro(&s->L[k], lat, s->f[k] + c * s->L[k].Q, &rho, &ux, &uy, &T);
-                int nf = sqrt(ux * ux + uy * uy) > s->crit_thr ? 1 : 0;
-                if (nf != k) {
-                    convert(s, k, nf, s->f[k] + c * s->L[k].Q, s->f[nf] + c * s->L[nf].Q);
-                    s->flag[c] = (uint8_t)nf;
-                }
-            }
-        }
+        if (s->crit_kind == 1) apply_criterion(s);   /* flags for the next step */
         s->steps++;
     }
     free(g[0]);

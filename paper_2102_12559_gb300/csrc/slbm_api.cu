@@ -1,0 +1,896 @@
+// slbm_api.cu -- the C ABI (include/slbm.h): handle, device-memory layout,
+// host-side constant tables and the per-step launch sequence.
+//
+// Host tables are computed here, independently of any other component:
+//  - Gauss-Hermite nodes as the roots of the probabilists' Hermite polynomial
+//    He_n (bisection + Newton on the three-term recurrence) and the weights
+//    w_j = (n-1)! / (n He_{n-1}(c_j)^2); these reproduce Table I.
+//  - The inverse Vandermonde matrix as the monomial coefficients of the
+//    Lagrange basis on the nodes (its row j gives l_j).
+//  - Per 1-D node, the Lagrange stencil of the departure point x - c_j dt
+//    (eqs. reconstructionPond / advectionPond), dt = CFL / max|c| with CFL = 1
+//    over the pair (Sec. IV).
+//  - The lifting and projection matrices of the interface kernel.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/slbm.h"
+#include "slbm_impl.cuh"
+
+using namespace slbm;
+
+namespace {
+
+thread_local char g_create_err[256] = "";
+
+// ------------------------------------------------------------ host tables
+
+double hermite_e(int n, double x, double* dprev = nullptr) {
+  double hm1 = 0.0, h = 1.0;  // He_{-1} := 0, He_0 = 1
+  for (int k = 0; k < n; ++k) {
+    const double hn = x * h - k * hm1;
+    hm1 = h;
+    h = hn;
+  }
+  if (dprev) *dprev = hm1;    // He_{n-1}(x)
+  return h;
+}
+
+void gauss_hermite(int n, double* c, double* w) {
+  // roots of He_n: sign changes on a fine grid over [-2 sqrt(n) - 1, ...], then
+  // bisection to convergence and one Newton polish (He_n' = n He_{n-1})
+  const double lim = 2.0 * std::sqrt((double)n) + 1.0;
+  const int M = 20000;
+  int found = 0;
+  double xa = -lim, fa = hermite_e(n, xa);
+  for (int s = 1; s <= M && found < n; ++s) {
+    const double xb = -lim + 2.0 * lim * s / M, fb = hermite_e(n, xb);
+    if (fa == 0.0 || fa * fb < 0.0) {
+      double lo = xa, hi = xb, flo = fa;
+      for (int it = 0; it < 200 && hi - lo > 0.0; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid == lo || mid == hi) break;
+        const double fm = hermite_e(n, mid);
+        if ((fm < 0.0) == (flo < 0.0)) { lo = mid; flo = fm; } else { hi = mid; }
+      }
+      double r = fa == 0.0 ? xa : 0.5 * (lo + hi);
+      double dp;
+      const double fr = hermite_e(n, r, &dp);
+      if (dp != 0.0) r -= fr / (n * dp);
+      c[found++] = r;
+    }
+    xa = xb;
+    fa = fb;
+  }
+  // exact symmetry about 0
+  for (int j = 0; j < n / 2; ++j) {
+    const double a = 0.5 * (c[n - 1 - j] - c[j]);
+    c[j] = -a;
+    c[n - 1 - j] = a;
+  }
+  if (n % 2) c[n / 2] = 0.0;
+  double fact = 1.0;
+  for (int k = 2; k < n; ++k) fact *= k;  // (n-1)!
+  for (int j = 0; j < n; ++j) {
+    double hp;
+    hermite_e(n, c[j], &hp);
+    w[j] = fact / (n * hp * hp);
+  }
+}
+
+// Monomial coefficients of the Lagrange basis polynomial l_j on nodes c[0..n).
+void lagrange_coeffs(const double* c, int n, int j, double* coef) {
+  double poly[kMaxN + 1] = {1.0};
+  int deg = 0;
+  double den = 1.0;
+  for (int r = 0; r < n; ++r) {
+    if (r == j) continue;
+    double nxt[kMaxN + 1] = {0.0};
+    for (int m = 0; m <= deg; ++m) {
+      nxt[m + 1] += poly[m];
+      nxt[m] -= c[r] * poly[m];
+    }
+    ++deg;
+    for (int m = 0; m <= deg; ++m) poly[m] = nxt[m];
+    den *= c[j] - c[r];
+  }
+  for (int m = 0; m < n; ++m) coef[m] = poly[m] / den;
+}
+
+double lagrange_eval(const double* c, int n, int j, double x) {
+  double v = 1.0;
+  for (int r = 0; r < n; ++r)
+    if (r != j) v *= (x - c[r]) / (c[j] - c[r]);
+  return v;
+}
+
+struct Lattice1D {
+  int n;
+  double c[kMaxN], w[kMaxN];
+  double vinv[kMaxN][kMaxN];
+};
+
+Lattice1D make_1d(int n) {
+  Lattice1D L{};
+  L.n = n;
+  gauss_hermite(n, L.c, L.w);
+  for (int j = 0; j < n; ++j) lagrange_coeffs(L.c, n, j, L.vinv[j]);
+  return L;
+}
+
+// Departure-point stencil of one node (shift s = c dt cells) with P points.
+void node_stencil(double s, int P, int* off, int* ntap, double* w) {
+  const double r = std::nearbyint(s);
+  if (std::fabs(s - r) < 1e-12) {  // integer shift: one exact tap
+    *off = -(int)r;
+    *ntap = 1;
+    w[0] = 1.0;
+    for (int a = 1; a < kMaxP; ++a) w[a] = 0.0;
+    return;
+  }
+  const double xd = -s;  // departure point relative to the cell
+  const int o = (int)std::floor(xd - 0.5 * (P - 1) + 0.5);
+  *off = o;
+  *ntap = P;
+  for (int a = 0; a < kMaxP; ++a) w[a] = 0.0;
+  for (int a = 0; a < P; ++a) {
+    double v = 1.0;
+    for (int q = 0; q < P; ++q)
+      if (q != a) v *= (xd - (double)(o + q)) / (double)(a - q);
+    w[a] = v;
+  }
+}
+
+template <class R>
+void fill_lat(LatTab<R>& T, const Lattice1D& L, double dt, int P) {
+  T.n = L.n;
+  for (int j = 0; j < kMaxN; ++j) {
+    T.off[j] = 0;
+    T.ntap[j] = 1;
+    T.c[j] = 0;
+    for (int a = 0; a < kMaxP; ++a) T.w[j][a] = 0;
+    for (int m = 0; m < kMaxN; ++m) T.vinv[j][m] = 0;
+  }
+  for (int j = 0; j < L.n; ++j) {
+    double w[kMaxP];
+    node_stencil(L.c[j] * dt, P, &T.off[j], &T.ntap[j], w);
+    T.c[j] = (R)L.c[j];
+    for (int a = 0; a < kMaxP; ++a) T.w[j][a] = (R)w[a];
+    for (int m = 0; m < L.n; ++m) T.vinv[j][m] = (R)L.vinv[j][m];
+  }
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int elem_size(int precision) { return precision == SLBM_FP64 ? 8 : 4; }
+
+struct Layout {
+  int G, pitch, rows;
+  long long plane;           // elements per plane, padded
+  size_t pops[2][2];         // byte offsets [buffer][lattice]
+  size_t flags[2], flag_tmp, macro[4], partials, audit_out, bc[4][3];
+  size_t total;
+};
+
+bool config_ok(const slbm_grid* g, int lo, int hi, int order, int precision, char* err) {
+  if (!g) { snprintf(err, 256, "null grid"); return false; }
+  if (lo < SLBM_D2Q9 || hi > SLBM_D2Q25 || lo >= hi) {
+    snprintf(err, 256, "lattice pair must satisfy D2Q9 <= lat_lo < lat_hi <= D2Q25");
+    return false;
+  }
+  if (order < 1 || order > 5) { snprintf(err, 256, "interp_order must be in 1..5"); return false; }
+  if (precision != SLBM_FP32 && precision != SLBM_FP64) {
+    snprintf(err, 256, "precision must be SLBM_FP32 or SLBM_FP64");
+    return false;
+  }
+  if (g->nx < 1 || g->ny < 1 || (long long)g->nx * g->ny > (1LL << 30)) {
+    snprintf(err, 256, "grid size out of range");
+    return false;
+  }
+  return true;
+}
+
+int reach_of(const Lattice1D& L, double dt, int P) {
+  int r = 0;
+  for (int j = 0; j < L.n; ++j) {
+    int off, nt;
+    double w[kMaxP];
+    node_stencil(L.c[j] * dt, P, &off, &nt, w);
+    r = std::max(r, std::max(-off, off + nt - 1));
+  }
+  return r;
+}
+
+double pair_dt(const Lattice1D& a, const Lattice1D& b) {
+  double cmax = 0.0;
+  for (int j = 0; j < a.n; ++j) cmax = std::max(cmax, std::fabs(a.c[j]));
+  for (int j = 0; j < b.n; ++j) cmax = std::max(cmax, std::fabs(b.c[j]));
+  return 1.0 / cmax;  // CFL = 1
+}
+
+Layout make_layout(const slbm_grid* g, int lo, int hi, int order, int precision) {
+  Layout Lo{};
+  const Lattice1D a = make_1d(lo), b = make_1d(hi);
+  const double dt = pair_dt(a, b);
+  const int P = order + 1;
+  Lo.G = std::max(1, std::max(reach_of(a, dt, P), reach_of(b, dt, P)));
+  Lo.pitch = (int)align_up((size_t)(kOX + g->nx + Lo.G), 32);
+  Lo.rows = g->ny + 2 * Lo.G;
+  Lo.plane = (long long)align_up((size_t)Lo.pitch * Lo.rows, 64);
+  const size_t es = elem_size(precision);
+  size_t off = 0;
+  const int Q[2] = {lo * lo, hi * hi};
+  for (int buf = 0; buf < 2; ++buf)
+    for (int k = 0; k < 2; ++k) {
+      Lo.pops[buf][k] = off;
+      off = align_up(off + (size_t)Q[k] * Lo.plane * es, 256);
+    }
+  const size_t nc = (size_t)g->nx * g->ny;
+  for (int f = 0; f < 2; ++f) { Lo.flags[f] = off; off = align_up(off + nc, 256); }
+  Lo.flag_tmp = off; off = align_up(off + nc, 256);
+  for (int m = 0; m < 4; ++m) { Lo.macro[m] = off; off = align_up(off + nc * 8, 256); }
+  Lo.partials = off; off = align_up(off + 4 * 1024 * 8, 256);
+  Lo.audit_out = off; off = align_up(off + 4 * 8, 256);
+  const size_t side = (size_t)std::max(g->nx, g->ny);
+  for (int s = 0; s < 4; ++s)
+    for (int q = 0; q < 3; ++q) { Lo.bc[s][q] = off; off = align_up(off + side * 8, 256); }
+  Lo.total = off;
+  return Lo;
+}
+
+}  // namespace
+
+struct slbm_s {
+  slbm_grid g;
+  int nlo, nhi, P, precision;
+  double tau;
+  Params<float> pf;
+  Params<double> pd;
+  Layout lay;
+  cudaStream_t st;
+  char* ws;
+  bool owns_ws;
+  int dev;                       // CUDA device of the workspace
+  int cur, fcur;                 // population buffer and flag buffer in use
+  int crit;
+  double thr;
+  int bc_kind[4];
+  long long steps;
+  int failed;
+  char err[256];
+  // tracing: events bracketing the kernels of each profiled step
+  int profiling;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used;
+
+  template <class T> T* at(size_t off) { return reinterpret_cast<T*>(ws + off); }
+  void* pops(int buf, int k) { return ws + lay.pops[buf][k]; }
+  uint8_t* flags(int f) { return at<uint8_t>(lay.flags[f]); }
+  size_t ncell() const { return (size_t)g.nx * g.ny; }
+};
+
+namespace {
+
+int fail(slbm_s* h, int code, const char* what, cudaError_t e = cudaSuccess) {
+  if (e != cudaSuccess)
+    snprintf(h->err, sizeof(h->err), "%s: %s", what, cudaGetErrorString(e));
+  else
+    snprintf(h->err, sizeof(h->err), "%s", what);
+  if (code == SLBM_ECUDA) h->failed = 1;
+  return code;
+}
+
+#define SLBM_CK(h, expr, what)                                \
+  do {                                                        \
+    cudaError_t e_ = (expr);                                  \
+    if (e_ != cudaSuccess) return fail((h), SLBM_ECUDA, (what), e_); \
+  } while (0)
+
+// Makes the handle's device current for the duration of a call and restores
+// the caller's device afterwards.
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceScope() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+#define SLBM_GUARD(h)                                                   \
+  if (!(h)) return SLBM_EINVAL;                                         \
+  if ((h)->failed) return SLBM_ECUDA;                                   \
+  DeviceScope slbm_device_scope_((h)->dev)
+
+BcDev bc_dev(slbm_s* h) {
+  BcDev b{};
+  for (int s = 0; s < 4; ++s) {
+    b.kind[s] = h->bc_kind[s];
+    b.rho[s] = h->at<double>(h->lay.bc[s][0]);
+    b.ux[s] = h->at<double>(h->lay.bc[s][1]);
+    b.uy[s] = h->at<double>(h->lay.bc[s][2]);
+  }
+  return b;
+}
+
+template <class S>
+cudaError_t ghosts_t(slbm_s* h, int buf, const uint8_t* flag) {
+  return launch_ghosts<S>(h->pd, (S*)h->pops(buf, 0), (S*)h->pops(buf, 1), flag, bc_dev(h), h->st);
+}
+
+cudaError_t ghosts(slbm_s* h, int buf, const uint8_t* flag) {
+  return h->precision == SLBM_FP64 ? ghosts_t<double>(h, buf, flag) : ghosts_t<float>(h, buf, flag);
+}
+
+template <class S>
+cudaError_t convert_t(slbm_s* h, int buf, const uint8_t* fold, const uint8_t* fnew) {
+  return launch_convert<S>(h->pd, (S*)h->pops(buf, 0), (S*)h->pops(buf, 1), fold, fnew, h->st);
+}
+
+cudaError_t convert(slbm_s* h, int buf, const uint8_t* fold, const uint8_t* fnew) {
+  return h->precision == SLBM_FP64 ? convert_t<double>(h, buf, fold, fnew)
+                                   : convert_t<float>(h, buf, fold, fnew);
+}
+
+// Next tracing event (recorded on the handle's stream), or success when off.
+cudaError_t mark(slbm_s* h) {
+  if (!h->profiling) return cudaSuccess;
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    h->ev_pool.push_back(e);
+  }
+  return cudaEventRecord(h->ev_pool[h->ev_used++], h->st);
+}
+
+// One time step: stream-collide (old flags) -> interface conversion (new
+// flags) -> ghost ring.
+int step_once(slbm_s* h) {
+  const int b = h->cur, nb = b ^ 1;
+  uint8_t* fold = h->flags(h->fcur);
+  uint8_t* fnew = h->crit ? h->flags(h->fcur ^ 1) : fold;
+  cudaError_t e;
+  SLBM_CK(h, mark(h), "trace event");
+  if (h->precision == SLBM_FP64)
+    e = launch_stream_collide<double, double>(h->pd, h->P, (const double*)h->pops(b, 0),
+                                              (const double*)h->pops(b, 1), (double*)h->pops(nb, 0),
+                                              (double*)h->pops(nb, 1), fold, fnew, h->st);
+  else
+    e = launch_stream_collide<float, float>(h->pf, h->P, (const float*)h->pops(b, 0),
+                                            (const float*)h->pops(b, 1), (float*)h->pops(nb, 0),
+                                            (float*)h->pops(nb, 1), fold, fnew, h->st);
+  SLBM_CK(h, e, "stream_collide launch");
+  SLBM_CK(h, mark(h), "trace event");
+  SLBM_CK(h, convert(h, nb, fold, fnew), "convert launch");
+  SLBM_CK(h, mark(h), "trace event");
+  SLBM_CK(h, ghosts(h, nb, fnew), "ghost launch");
+  SLBM_CK(h, mark(h), "trace event");
+  h->cur = nb;
+  if (h->crit) h->fcur ^= 1;
+  h->steps++;
+  return SLBM_OK;
+}
+
+template <class R>
+void fill_params(Params<R>& p, const slbm_s* h, const Lattice1D& a, const Lattice1D& b, double dt) {
+  std::memset(&p, 0, sizeof(p));
+  p.nx = h->g.nx;
+  p.ny = h->g.ny;
+  p.G = h->lay.G;
+  p.pitch = h->lay.pitch;
+  p.rows = h->lay.rows;
+  p.plane = h->lay.plane;
+  p.periodic_x = h->g.periodic_x ? 1 : 0;
+  p.periodic_y = h->g.periodic_y ? 1 : 0;
+  p.crit = h->crit;
+  p.thr = (R)h->thr;
+  p.omega = (R)(1.0 / h->tau);
+  p.band = h->lay.G;
+  fill_lat(p.lat[0], a, dt, h->P);
+  fill_lat(p.lat[1], b, dt, h->P);
+  ConvTab& t = p.conv;
+  t.nq = a.n;
+  t.nQ = b.n;
+  for (int j = 0; j < kMaxN; ++j) {
+    t.cq[j] = j < a.n ? a.c[j] : 0.0;
+    t.cQ[j] = j < b.n ? b.c[j] : 0.0;
+    for (int m = 0; m < kMaxN; ++m) {
+      t.vinvq[j][m] = (j < a.n && m < a.n) ? a.vinv[j][m] : 0.0;
+      t.vinvQ[j][m] = (j < b.n && m < b.n) ? b.vinv[j][m] : 0.0;
+      t.lift[j][m] = 0.0;
+      t.proj[j][m] = 0.0;
+    }
+  }
+  // L[a][j] = sum_{m < nq} VQ^-1[a][m] c_q[j]^m
+  for (int aa = 0; aa < b.n; ++aa)
+    for (int j = 0; j < a.n; ++j) {
+      double s = 0.0, pw = 1.0;
+      for (int m = 0; m < a.n; ++m) {
+        s += b.vinv[aa][m] * pw;
+        pw *= a.c[j];
+      }
+      t.lift[aa][j] = s;
+    }
+  // P[j][a] = l^q_j(c^Q_a)
+  for (int j = 0; j < a.n; ++j)
+    for (int aa = 0; aa < b.n; ++aa) t.proj[j][aa] = lagrange_eval(a.c, a.n, j, b.c[aa]);
+}
+
+void refresh_params(slbm_s* h) {
+  const Lattice1D a = make_1d(h->nlo), b = make_1d(h->nhi);
+  const double dt = pair_dt(a, b);
+  fill_params(h->pf, h, a, b, dt);
+  fill_params(h->pd, h, a, b, dt);
+}
+
+int upload(slbm_s* h, void* dst, const void* src, size_t bytes) {
+  SLBM_CK(h, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->st), "H2D copy");
+  return SLBM_OK;
+}
+
+template <class S>
+int pack_all(slbm_s* h, int k, double* host, int unpack, const double* in_host) {
+  const int n = k ? h->nhi : h->nlo, Q = n * n;
+  const size_t nc = h->ncell();
+  // the four nc-double macro slots stage up to four planes at a time
+  for (int i0 = 0; i0 < Q; i0 += 4) {
+    const int cnt = std::min(4, Q - i0);
+    if (unpack) {
+      // macro[0..3] are contiguous nc-double slots; stage cnt planes there
+      for (int q = 0; q < cnt; ++q) {
+        const int rc = upload(h, h->at<double>(h->lay.macro[q]), in_host + (size_t)(i0 + q) * nc,
+                              nc * 8);
+        if (rc) return rc;
+      }
+      for (int q = 0; q < cnt; ++q)
+        SLBM_CK(h, launch_pack<S>(h->pd, i0 + q, 1, nullptr, nullptr, 1, (S*)h->pops(h->cur, k),
+                                  h->at<double>(h->lay.macro[q]), h->st),
+                "unpack launch");
+    } else {
+      for (int q = 0; q < cnt; ++q) {
+        SLBM_CK(h, launch_pack<S>(h->pd, i0 + q, 1, (const S*)h->pops(h->cur, k),
+                                  h->at<double>(h->lay.macro[q]), 0, nullptr, nullptr, h->st),
+                "pack launch");
+        SLBM_CK(h, cudaMemcpyAsync(host + (size_t)(i0 + q) * nc, h->at<double>(h->lay.macro[q]),
+                                   nc * 8, cudaMemcpyDeviceToHost, h->st),
+                "D2H copy");
+      }
+    }
+    SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  }
+  return SLBM_OK;
+}
+
+int pack_any(slbm_s* h, int k, double* host, int unpack, const double* in) {
+  return h->precision == SLBM_FP64 ? pack_all<double>(h, k, host, unpack, in)
+                                   : pack_all<float>(h, k, host, unpack, in);
+}
+
+int init_eq_dev(slbm_s* h) {
+  cudaError_t e;
+  double* r = h->at<double>(h->lay.macro[0]);
+  double* u = h->at<double>(h->lay.macro[1]);
+  double* v = h->at<double>(h->lay.macro[2]);
+  if (h->precision == SLBM_FP64)
+    e = launch_init_eq<double>(h->pd, (double*)h->pops(h->cur, 0), (double*)h->pops(h->cur, 1), r,
+                               u, v, h->st);
+  else
+    e = launch_init_eq<float>(h->pd, (float*)h->pops(h->cur, 0), (float*)h->pops(h->cur, 1), r, u,
+                              v, h->st);
+  SLBM_CK(h, e, "init launch");
+  SLBM_CK(h, ghosts(h, h->cur, h->flags(h->fcur)), "ghost launch");
+  return SLBM_OK;
+}
+
+// Every argument check of slbm_create / slbm_create_in, before any CUDA call.
+bool create_args_ok(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int interp_order,
+                    int frame, int precision) {
+  if (!config_ok(g, lat_lo, lat_hi, interp_order, precision, g_create_err)) return false;
+  if (!(tau > 0.5) || !std::isfinite(tau)) {
+    snprintf(g_create_err, sizeof(g_create_err), "tau must be a finite value > 1/2");
+    return false;
+  }
+  if (frame != SLBM_FRAME_LATTICE) {
+    snprintf(g_create_err, sizeof(g_create_err), "only SLBM_FRAME_LATTICE is supported");
+    return false;
+  }
+  const Layout lay = make_layout(g, lat_lo, lat_hi, interp_order, precision);
+  if (g->nx < 2 * lay.G + 1 || g->ny < 2 * lay.G + 1) {
+    snprintf(g_create_err, sizeof(g_create_err), "grid must be at least %d cells per side",
+             2 * lay.G + 1);
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int slbm_workspace_bytes(const slbm_grid* g, int lat_lo, int lat_hi, int interp_order,
+                         int precision, size_t* bytes) {
+  char err[256];
+  if (!bytes || !config_ok(g, lat_lo, lat_hi, interp_order, precision, err)) return SLBM_EINVAL;
+  *bytes = make_layout(g, lat_lo, lat_hi, interp_order, precision).total;
+  return SLBM_OK;
+}
+
+int slbm_create_in(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int interp_order,
+                   int frame, int precision, void* cuda_stream, void* workspace,
+                   size_t workspace_bytes, slbm_t* out) {
+  if (!out) return SLBM_EINVAL;
+  *out = nullptr;
+  if (!create_args_ok(g, lat_lo, lat_hi, tau, interp_order, frame, precision))
+    return SLBM_EINVAL;
+  const Layout lay = make_layout(g, lat_lo, lat_hi, interp_order, precision);
+  if (!workspace || ((uintptr_t)workspace & 255) || workspace_bytes < lay.total) {
+    snprintf(g_create_err, sizeof(g_create_err),
+             "workspace must be 256-byte aligned and hold %zu bytes", lay.total);
+    return SLBM_ENOMEM;
+  }
+  // the handle lives on the device that holds its workspace
+  cudaPointerAttributes attr{};
+  cudaError_t e = cudaPointerGetAttributes(&attr, workspace);
+  if (e != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+    snprintf(g_create_err, sizeof(g_create_err), "workspace is not device memory: %s",
+             cudaGetErrorString(e));
+    cudaGetLastError();
+    return SLBM_EINVAL;
+  }
+  slbm_s* h = new (std::nothrow) slbm_s();
+  if (!h) return SLBM_ENOMEM;
+  h->dev = attr.device;
+  h->g = *g;
+  h->nlo = lat_lo;
+  h->nhi = lat_hi;
+  h->P = interp_order + 1;
+  h->precision = precision;
+  h->tau = tau;
+  h->lay = lay;
+  h->st = (cudaStream_t)cuda_stream;
+  h->ws = (char*)workspace;
+  h->owns_ws = false;
+  h->thr = 0.3;
+  for (int s = 0; s < 4; ++s) h->bc_kind[s] = SLBM_BC_OUTFLOW;
+  refresh_params(h);
+  // zero everything (finite stale values), flags 0, then rest state rho = 1, u = 0
+  if (cudaMemsetAsync(h->ws, 0, lay.total, h->st) != cudaSuccess) {
+    snprintf(g_create_err, sizeof(g_create_err), "workspace clear failed");
+    delete h;
+    return SLBM_ECUDA;
+  }
+  std::vector<double> one(h->ncell(), 1.0), zero(h->ncell(), 0.0);
+  int rc = slbm_init_equilibrium(h, one.data(), zero.data(), zero.data(), nullptr);
+  if (rc == SLBM_OK) rc = slbm_sync(h);
+  if (rc != SLBM_OK) {
+    snprintf(g_create_err, sizeof(g_create_err), "%s", h->err);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return SLBM_OK;
+}
+
+int slbm_create(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int interp_order,
+                int frame, int precision, void* cuda_stream, slbm_t* out) {
+  if (!out) return SLBM_EINVAL;
+  *out = nullptr;
+  size_t bytes = 0;
+  if (!create_args_ok(g, lat_lo, lat_hi, tau, interp_order, frame, precision))
+    return SLBM_EINVAL;
+  bytes = make_layout(g, lat_lo, lat_hi, interp_order, precision).total;
+  void* ws = nullptr;
+  cudaError_t e = cudaMalloc(&ws, bytes);
+  if (e != cudaSuccess) {
+    snprintf(g_create_err, sizeof(g_create_err), "cudaMalloc(%zu): %s", bytes,
+             cudaGetErrorString(e));
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? SLBM_ENOMEM : SLBM_ECUDA;
+  }
+  int rc = slbm_create_in(g, lat_lo, lat_hi, tau, interp_order, frame, precision, cuda_stream, ws,
+                          bytes, out);
+  if (rc != SLBM_OK) {
+    cudaFree(ws);
+    return rc;
+  }
+  (*out)->owns_ws = true;
+  return SLBM_OK;
+}
+
+int slbm_destroy(slbm_t h) {
+  if (!h) return SLBM_EINVAL;
+  int rc = SLBM_OK;
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) rc = SLBM_ECUDA;
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (h->owns_ws && cudaFree(h->ws) != cudaSuccess) rc = SLBM_ECUDA;
+  delete h;
+  return rc;
+}
+
+int slbm_get_info(slbm_t h, slbm_info_t* info) {
+  if (!h || !info) return SLBM_EINVAL;
+  const Lattice1D a = make_1d(h->nlo), b = make_1d(h->nhi);
+  info->dt = pair_dt(a, b);
+  info->omega = 1.0 / h->tau;
+  info->q_lo = h->nlo * h->nlo;
+  info->q_hi = h->nhi * h->nhi;
+  info->halo = h->lay.G;
+  info->pitch = h->lay.pitch;
+  info->rows = h->lay.rows;
+  info->precision = h->precision;
+  info->kernels_per_step = 3;
+  info->workspace_bytes = h->lay.total;
+  info->steps = h->steps;
+  return SLBM_OK;
+}
+
+int slbm_init_equilibrium(slbm_t h, const double* rho, const double* ux, const double* uy,
+                          const double* T) {
+  SLBM_GUARD(h);
+  if (!rho || !ux || !uy) return fail(h, SLBM_EINVAL, "rho, ux, uy are required");
+  if (T) return fail(h, SLBM_EINVAL, "the athermal lattice-frame model takes T = NULL");
+  const size_t b = h->ncell() * 8;
+  int rc;
+  if ((rc = upload(h, h->at<double>(h->lay.macro[0]), rho, b))) return rc;
+  if ((rc = upload(h, h->at<double>(h->lay.macro[1]), ux, b))) return rc;
+  if ((rc = upload(h, h->at<double>(h->lay.macro[2]), uy, b))) return rc;
+  if ((rc = init_eq_dev(h))) return rc;
+  // the caller may reuse its arrays on return
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  return SLBM_OK;
+}
+
+int slbm_set_flags(slbm_t h, const uint8_t* flags) {
+  SLBM_GUARD(h);
+  if (!flags) return fail(h, SLBM_EINVAL, "flags is required");
+  std::vector<uint8_t> norm(h->ncell());
+  for (size_t c = 0; c < norm.size(); ++c) norm[c] = flags[c] ? 1 : 0;
+  uint8_t* tmp = h->at<uint8_t>(h->lay.flag_tmp);
+  int rc;
+  if ((rc = upload(h, tmp, norm.data(), norm.size()))) return rc;
+  SLBM_CK(h, convert(h, h->cur, h->flags(h->fcur), tmp), "convert launch");
+  SLBM_CK(h, cudaMemcpyAsync(h->flags(h->fcur), tmp, norm.size(), cudaMemcpyDeviceToDevice, h->st),
+          "flag copy");
+  SLBM_CK(h, ghosts(h, h->cur, h->flags(h->fcur)), "ghost launch");
+  // the host vector must stay alive until the copy has consumed it
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  return SLBM_OK;
+}
+
+int slbm_get_flags(slbm_t h, uint8_t* flags) {
+  SLBM_GUARD(h);
+  if (!flags) return fail(h, SLBM_EINVAL, "flags is required");
+  SLBM_CK(h, cudaMemcpyAsync(flags, h->flags(h->fcur), h->ncell(), cudaMemcpyDeviceToHost, h->st),
+          "D2H copy");
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  return SLBM_OK;
+}
+
+int slbm_set_criterion(slbm_t h, int kind, double threshold) {
+  SLBM_GUARD(h);
+  if ((kind != SLBM_CRIT_NONE && kind != SLBM_CRIT_MACH) || !(threshold >= 0.0))
+    return fail(h, SLBM_EINVAL, "criterion kind or threshold invalid");
+  // flags live in buffer fcur either way; the other buffer is scratch
+  h->crit = kind;
+  h->thr = threshold;
+  refresh_params(h);
+  if (kind == SLBM_CRIT_MACH) {
+    // evaluate the criterion on the current state at once; flips are converted
+    uint8_t* tmp = h->at<uint8_t>(h->lay.flag_tmp);
+    cudaError_t e =
+        h->precision == SLBM_FP64
+            ? launch_criterion<double>(h->pd, (const double*)h->pops(h->cur, 0),
+                                       (const double*)h->pops(h->cur, 1), h->flags(h->fcur), tmp,
+                                       h->st)
+            : launch_criterion<float>(h->pd, (const float*)h->pops(h->cur, 0),
+                                      (const float*)h->pops(h->cur, 1), h->flags(h->fcur), tmp,
+                                      h->st);
+    SLBM_CK(h, e, "criterion launch");
+    SLBM_CK(h, convert(h, h->cur, h->flags(h->fcur), tmp), "convert launch");
+    SLBM_CK(h, cudaMemcpyAsync(h->flags(h->fcur), tmp, h->ncell(), cudaMemcpyDeviceToDevice, h->st),
+            "flag copy");
+    SLBM_CK(h, ghosts(h, h->cur, h->flags(h->fcur)), "ghost launch");
+  }
+  return SLBM_OK;
+}
+
+int slbm_set_boundary(slbm_t h, int side, int kind, const double* rho, const double* ux,
+                      const double* uy) {
+  SLBM_GUARD(h);
+  if (side < 0 || side > 3) return fail(h, SLBM_EINVAL, "side out of range");
+  if ((side < 2 && h->g.periodic_x) || (side >= 2 && h->g.periodic_y))
+    return fail(h, SLBM_EINVAL, "side is periodic");
+  if (kind == SLBM_BC_DIRICHLET && (!rho || !ux || !uy))
+    return fail(h, SLBM_EINVAL, "DIRICHLET needs rho, ux, uy");
+  if (kind == SLBM_BC_INLET && (!ux || !uy)) return fail(h, SLBM_EINVAL, "INLET needs ux, uy");
+  if (kind != SLBM_BC_OUTFLOW && kind != SLBM_BC_DIRICHLET && kind != SLBM_BC_INLET)
+    return fail(h, SLBM_EINVAL, "unknown boundary kind");
+  const size_t len = (size_t)(side < 2 ? h->g.ny : h->g.nx);
+  const double* src[3] = {rho, ux, uy};
+  for (int q = 0; q < 3; ++q)
+    if (src[q]) {
+      int rc = upload(h, h->at<double>(h->lay.bc[side][q]), src[q], len * 8);
+      if (rc) return rc;
+    }
+  h->bc_kind[side] = kind;
+  SLBM_CK(h, ghosts(h, h->cur, h->flags(h->fcur)), "ghost launch");
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  return SLBM_OK;
+}
+
+int slbm_step(slbm_t h, int n) {
+  SLBM_GUARD(h);
+  if (n < 0) return fail(h, SLBM_EINVAL, "n must be >= 0");
+  for (int s = 0; s < n; ++s) {
+    int rc = step_once(h);
+    if (rc) return rc;
+  }
+  return SLBM_OK;
+}
+
+int slbm_sync(slbm_t h) {
+  SLBM_GUARD(h);
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  return SLBM_OK;
+}
+
+int slbm_moments_device(slbm_t h, double* rho, double* ux, double* uy, double* T) {
+  SLBM_GUARD(h);
+  cudaError_t e;
+  if (h->precision == SLBM_FP64)
+    e = launch_moments<double>(h->pd, (const double*)h->pops(h->cur, 0),
+                               (const double*)h->pops(h->cur, 1), h->flags(h->fcur), rho, ux, uy, T,
+                               h->st);
+  else
+    e = launch_moments<float>(h->pd, (const float*)h->pops(h->cur, 0),
+                              (const float*)h->pops(h->cur, 1), h->flags(h->fcur), rho, ux, uy, T,
+                              h->st);
+  SLBM_CK(h, e, "moments launch");
+  return SLBM_OK;
+}
+
+int slbm_moments(slbm_t h, double* rho, double* ux, double* uy, double* T) {
+  SLBM_GUARD(h);
+  double* d[4];
+  for (int m = 0; m < 4; ++m) d[m] = h->at<double>(h->lay.macro[m]);
+  int rc = slbm_moments_device(h, rho ? d[0] : nullptr, ux ? d[1] : nullptr, uy ? d[2] : nullptr,
+                               T ? d[3] : nullptr);
+  if (rc) return rc;
+  double* out[4] = {rho, ux, uy, T};
+  for (int m = 0; m < 4; ++m)
+    if (out[m])
+      SLBM_CK(h, cudaMemcpyAsync(out[m], d[m], h->ncell() * 8, cudaMemcpyDeviceToHost, h->st),
+              "D2H copy");
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  return SLBM_OK;
+}
+
+int slbm_audit(slbm_t h, double out[4]) {
+  SLBM_GUARD(h);
+  if (!out) return fail(h, SLBM_EINVAL, "out is required");
+  const int np = audit_parts(h->pd);
+  double* part = h->at<double>(h->lay.partials);
+  double* res = h->at<double>(h->lay.audit_out);
+  cudaError_t e;
+  if (h->precision == SLBM_FP64)
+    e = launch_audit<double>(h->pd, (const double*)h->pops(h->cur, 0),
+                             (const double*)h->pops(h->cur, 1), h->flags(h->fcur), part, np, res,
+                             h->st);
+  else
+    e = launch_audit<float>(h->pd, (const float*)h->pops(h->cur, 0),
+                            (const float*)h->pops(h->cur, 1), h->flags(h->fcur), part, np, res,
+                            h->st);
+  SLBM_CK(h, e, "audit launch");
+  SLBM_CK(h, cudaMemcpyAsync(out, res, 32, cudaMemcpyDeviceToHost, h->st), "D2H copy");
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  for (int q = 0; q < 4; ++q)
+    if (!std::isfinite(out[q])) return fail(h, SLBM_ENONFINITE, "audit: non-finite sum");
+  return SLBM_OK;
+}
+
+int slbm_get_pops(slbm_t h, int k, double* out) {
+  SLBM_GUARD(h);
+  if ((k != 0 && k != 1) || !out) return fail(h, SLBM_EINVAL, "lattice index or output invalid");
+  return pack_any(h, k, out, 0, nullptr);
+}
+
+int slbm_set_pops(slbm_t h, int k, const double* in) {
+  SLBM_GUARD(h);
+  if ((k != 0 && k != 1) || !in) return fail(h, SLBM_EINVAL, "lattice index or input invalid");
+  int rc = pack_any(h, k, nullptr, 1, in);
+  if (rc) return rc;
+  SLBM_CK(h, ghosts(h, h->cur, h->flags(h->fcur)), "ghost launch");
+  return SLBM_OK;
+}
+
+namespace {
+struct StateHeader {
+  char magic[8];
+  int nx, ny, nlo, nhi, precision, pad;
+  long long steps;
+};
+}  // namespace
+
+int slbm_get_state(slbm_t h, void* buf, size_t* bytes) {
+  SLBM_GUARD(h);
+  if (!bytes) return fail(h, SLBM_EINVAL, "bytes is required");
+  const size_t nc = h->ncell();
+  const size_t need =
+      sizeof(StateHeader) + nc + nc * 8 * (size_t)(h->nlo * h->nlo + h->nhi * h->nhi);
+  if (!buf) { *bytes = need; return SLBM_OK; }
+  if (*bytes < need) return fail(h, SLBM_EINVAL, "state buffer too small");
+  StateHeader hd{};
+  std::memcpy(hd.magic, "SLBMST1", 8);
+  hd.nx = h->g.nx; hd.ny = h->g.ny; hd.nlo = h->nlo; hd.nhi = h->nhi;
+  hd.precision = h->precision; hd.steps = h->steps;
+  char* p = (char*)buf;
+  std::memcpy(p, &hd, sizeof(hd));
+  int rc = slbm_get_flags(h, (uint8_t*)(p + sizeof(hd)));
+  if (rc) return rc;
+  double* pops = (double*)(p + sizeof(hd) + nc);
+  if ((rc = slbm_get_pops(h, 0, pops))) return rc;
+  if ((rc = slbm_get_pops(h, 1, pops + nc * h->nlo * h->nlo))) return rc;
+  *bytes = need;
+  return SLBM_OK;
+}
+
+int slbm_set_state(slbm_t h, const void* buf, size_t bytes) {
+  SLBM_GUARD(h);
+  const size_t nc = h->ncell();
+  const size_t need =
+      sizeof(StateHeader) + nc + nc * 8 * (size_t)(h->nlo * h->nlo + h->nhi * h->nhi);
+  if (!buf || bytes < need) return fail(h, SLBM_EINVAL, "state buffer too small");
+  StateHeader hd;
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (std::memcmp(hd.magic, "SLBMST1", 8) || hd.nx != h->g.nx || hd.ny != h->g.ny ||
+      hd.nlo != h->nlo || hd.nhi != h->nhi || hd.precision != h->precision)
+    return fail(h, SLBM_EINVAL, "state does not match this handle");
+  const char* p = (const char*)buf;
+  int rc;
+  if ((rc = upload(h, h->flags(h->fcur), p + sizeof(hd), nc))) return rc;
+  const double* pops = (const double*)(p + sizeof(hd) + nc);
+  if ((rc = pack_any(h, 0, nullptr, 1, pops))) return rc;
+  if ((rc = pack_any(h, 1, nullptr, 1, pops + nc * h->nlo * h->nlo))) return rc;
+  SLBM_CK(h, ghosts(h, h->cur, h->flags(h->fcur)), "ghost launch");
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  h->steps = hd.steps;
+  return SLBM_OK;
+}
+
+int slbm_profile(slbm_t h, int enable) {
+  SLBM_GUARD(h);
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  h->profiling = enable ? 1 : 0;
+  h->ev_used = 0;
+  return SLBM_OK;
+}
+
+int slbm_profile_read(slbm_t h, double* ms, long long* steps) {
+  SLBM_GUARD(h);
+  if (!ms || !steps) return fail(h, SLBM_EINVAL, "outputs are required");
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  const int per = SLBM_PROFILE_KERNELS + 1;  // events per step
+  for (int k = 0; k < SLBM_PROFILE_KERNELS; ++k) ms[k] = 0.0;
+  const size_t n = h->ev_used / per;
+  for (size_t s = 0; s < n; ++s)
+    for (int k = 0; k < SLBM_PROFILE_KERNELS; ++k) {
+      float t = 0.f;
+      SLBM_CK(h, cudaEventElapsedTime(&t, h->ev_pool[s * per + k], h->ev_pool[s * per + k + 1]),
+              "event time");
+      ms[k] += t;
+    }
+  *steps = (long long)n;
+  return SLBM_OK;
+}
+
+const char* slbm_last_error(slbm_t h) { return h ? h->err : g_create_err; }
+
+}  // extern "C"

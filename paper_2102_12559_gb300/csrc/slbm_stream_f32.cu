@@ -1,0 +1,13 @@
+// Single-precision instantiation of the fused stream-collide kernel.
+#include "slbm_stream.cuh"
+
+namespace slbm {
+template <>
+cudaError_t launch_stream_collide<float, float>(const Params<float>& p, int P, const float* fin0,
+                                                const float* fin1, float* fout0, float* fout1,
+                                                const uint8_t* flag_cur, uint8_t* flag_nxt,
+                                                cudaStream_t st) {
+  return launch_stream_collide_impl<float, float>(p, P, fin0, fin1, fout0, fout1, flag_cur,
+                                                  flag_nxt, st);
+}
+}  // namespace slbm

@@ -1,0 +1,14 @@
+// Double-precision instantiation of the fused stream-collide kernel.
+#include "slbm_stream.cuh"
+
+namespace slbm {
+template <>
+cudaError_t launch_stream_collide<double, double>(const Params<double>& p, int P,
+                                                  const double* fin0, const double* fin1,
+                                                  double* fout0, double* fout1,
+                                                  const uint8_t* flag_cur, uint8_t* flag_nxt,
+                                                  cudaStream_t st) {
+  return launch_stream_collide_impl<double, double>(p, P, fin0, fin1, fout0, fout1, flag_cur,
+                                                    flag_nxt, st);
+}
+}  // namespace slbm

@@ -1,0 +1,367 @@
+"""Thin ctypes binding of ``libslbm.so`` (the C ABI in ``include/slbm.h``).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  The functions keep the C names (``slbm_create``,
+``slbm_step`` ...) and take numpy arrays for host buffers; ``Solver`` wraps a
+handle whose device workspace and stream come from PyTorch.
+
+There is no CPU fallback: loading fails loudly when the library has not been
+built or no CUDA device is present.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+# ---- constants mirrored from include/slbm.h
+SLBM_OK, SLBM_EINVAL, SLBM_ENOMEM, SLBM_ECUDA = 0, -1, -2, -3
+SLBM_ENONFINITE, SLBM_ENOCONV, SLBM_ETIMEOUT, SLBM_ESTATE = -4, -5, -6, -7
+SLBM_D2Q9, SLBM_D2Q16, SLBM_D2Q25 = 3, 4, 5
+SLBM_FRAME_LATTICE = 0
+SLBM_FP32, SLBM_FP64 = 0, 1
+SLBM_BC_OUTFLOW, SLBM_BC_DIRICHLET, SLBM_BC_INLET = 0, 1, 2
+SLBM_SIDE_XMIN, SLBM_SIDE_XMAX, SLBM_SIDE_YMIN, SLBM_SIDE_YMAX = 0, 1, 2, 3
+SLBM_CRIT_NONE, SLBM_CRIT_MACH = 0, 1
+
+EXPORTS = [
+    "slbm_workspace_bytes", "slbm_create", "slbm_create_in", "slbm_destroy", "slbm_get_info",
+    "slbm_init_equilibrium", "slbm_set_flags", "slbm_get_flags", "slbm_set_criterion",
+    "slbm_set_boundary", "slbm_step", "slbm_sync", "slbm_moments", "slbm_moments_device",
+    "slbm_audit", "slbm_get_pops", "slbm_set_pops", "slbm_get_state", "slbm_set_state",
+    "slbm_profile", "slbm_profile_read", "slbm_last_error",
+]
+SLBM_PROFILE_KERNELS = 3
+KERNEL_NAMES = ("stream_collide", "convert", "ghosts")
+
+
+class slbm_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("periodic_x", ctypes.c_int), ("periodic_y", ctypes.c_int)]
+
+
+class slbm_info_t(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("omega", ctypes.c_double),
+                ("q_lo", ctypes.c_int), ("q_hi", ctypes.c_int), ("halo", ctypes.c_int),
+                ("pitch", ctypes.c_int), ("rows", ctypes.c_int), ("precision", ctypes.c_int),
+                ("kernels_per_step", ctypes.c_int), ("workspace_bytes", ctypes.c_size_t),
+                ("steps", ctypes.c_longlong)]
+
+
+class SlbmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"slbm error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libslbm.so (building it first if allowed and missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library {_build.LIB} is missing: run __graft_entry__.build()")
+        _build.build()
+    L = ctypes.CDLL(_build.LIB)
+    p, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    P = ctypes.POINTER
+    L.slbm_workspace_bytes.argtypes = [P(slbm_grid), i, i, i, i, P(ctypes.c_size_t)]
+    L.slbm_create.argtypes = [P(slbm_grid), i, i, d, i, i, i, p, P(p)]
+    L.slbm_create_in.argtypes = [P(slbm_grid), i, i, d, i, i, i, p, p, ctypes.c_size_t, P(p)]
+    L.slbm_destroy.argtypes = [p]
+    L.slbm_get_info.argtypes = [p, P(slbm_info_t)]
+    L.slbm_init_equilibrium.argtypes = [p, p, p, p, p]
+    L.slbm_set_flags.argtypes = [p, p]
+    L.slbm_get_flags.argtypes = [p, p]
+    L.slbm_set_criterion.argtypes = [p, i, d]
+    L.slbm_set_boundary.argtypes = [p, i, i, p, p, p]
+    L.slbm_step.argtypes = [p, i]
+    L.slbm_sync.argtypes = [p]
+    L.slbm_moments.argtypes = [p, p, p, p, p]
+    L.slbm_moments_device.argtypes = [p, p, p, p, p]
+    L.slbm_audit.argtypes = [p, p]
+    L.slbm_get_pops.argtypes = [p, i, p]
+    L.slbm_set_pops.argtypes = [p, i, p]
+    L.slbm_get_state.argtypes = [p, p, P(ctypes.c_size_t)]
+    L.slbm_set_state.argtypes = [p, p, ctypes.c_size_t]
+    L.slbm_profile.argtypes = [p, i]
+    L.slbm_profile_read.argtypes = [p, p, P(ctypes.c_longlong)]
+    L.slbm_last_error.argtypes = [p]
+    L.slbm_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name != "slbm_last_error":
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return ctypes.c_void_p(a)
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc: int, h=None):
+    if rc != SLBM_OK:
+        msg = load().slbm_last_error(h)
+        raise SlbmError(rc, msg.decode() if msg else "")
+
+
+def _f64(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float64).ravel()
+    if a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+# ---------------------------------------------------------------- C names
+
+def slbm_workspace_bytes(nx, ny, periodic_x, periodic_y, lat_lo, lat_hi, interp_order, precision):
+    g = slbm_grid(nx, ny, int(periodic_x), int(periodic_y))
+    out = ctypes.c_size_t(0)
+    _check(load().slbm_workspace_bytes(ctypes.byref(g), lat_lo, lat_hi, interp_order, precision,
+                                       ctypes.byref(out)))
+    return out.value
+
+
+def slbm_create(nx, ny, periodic_x, periodic_y, lat_lo, lat_hi, tau, interp_order=3,
+                frame=SLBM_FRAME_LATTICE, precision=SLBM_FP32, stream=0):
+    g = slbm_grid(nx, ny, int(periodic_x), int(periodic_y))
+    h = ctypes.c_void_p()
+    _check(load().slbm_create(ctypes.byref(g), lat_lo, lat_hi, float(tau), interp_order, frame,
+                              precision, ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h
+
+
+def slbm_create_in(nx, ny, periodic_x, periodic_y, lat_lo, lat_hi, tau, interp_order, frame,
+                   precision, stream, workspace_ptr, workspace_bytes):
+    g = slbm_grid(nx, ny, int(periodic_x), int(periodic_y))
+    h = ctypes.c_void_p()
+    _check(load().slbm_create_in(ctypes.byref(g), lat_lo, lat_hi, float(tau), interp_order, frame,
+                                 precision, ctypes.c_void_p(stream), ctypes.c_void_p(workspace_ptr),
+                                 workspace_bytes, ctypes.byref(h)))
+    return h
+
+
+def slbm_destroy(h):
+    _check(load().slbm_destroy(h))
+
+
+def slbm_get_info(h) -> slbm_info_t:
+    info = slbm_info_t()
+    _check(load().slbm_get_info(h, ctypes.byref(info)), h)
+    return info
+
+
+def slbm_init_equilibrium(h, n, rho, ux, uy):
+    r, a, b = _f64(rho, n), _f64(ux, n), _f64(uy, n)
+    _check(load().slbm_init_equilibrium(h, _ptr(r), _ptr(a), _ptr(b), None), h)
+
+
+def slbm_set_flags(h, n, flags):
+    f = np.ascontiguousarray(flags, dtype=np.uint8).ravel()
+    assert f.size == n
+    _check(load().slbm_set_flags(h, _ptr(f)), h)
+
+
+def slbm_get_flags(h, n):
+    f = np.zeros(n, dtype=np.uint8)
+    _check(load().slbm_get_flags(h, _ptr(f)), h)
+    return f
+
+
+def slbm_set_criterion(h, kind, threshold):
+    _check(load().slbm_set_criterion(h, kind, float(threshold)), h)
+
+
+def slbm_set_boundary(h, side, kind, length, rho=None, ux=None, uy=None):
+    arrs = [None if a is None else _f64(a, length) for a in (rho, ux, uy)]
+    _check(load().slbm_set_boundary(h, side, kind, *[_ptr(a) for a in arrs]), h)
+
+
+def slbm_step(h, n=1):
+    _check(load().slbm_step(h, int(n)), h)
+
+
+def slbm_sync(h):
+    _check(load().slbm_sync(h), h)
+
+
+def slbm_moments(h, n, rho=None, ux=None, uy=None, T=None):
+    """Host moments; pass preallocated float64 arrays (e.g. pinned) or None
+    to allocate."""
+    outs = [np.zeros(n) if a is None else a for a in (rho, ux, uy, T)]
+    _check(load().slbm_moments(h, *[_ptr(a) for a in outs]), h)
+    return outs
+
+
+def slbm_moments_device(h, rho_ptr=0, ux_ptr=0, uy_ptr=0, T_ptr=0):
+    ptrs = [ctypes.c_void_p(p) if p else None for p in (rho_ptr, ux_ptr, uy_ptr, T_ptr)]
+    _check(load().slbm_moments_device(h, *ptrs), h)
+
+
+def slbm_audit(h):
+    out = np.zeros(4)
+    _check(load().slbm_audit(h, _ptr(out)), h)
+    return out
+
+
+def slbm_get_pops(h, k, Q, n):
+    out = np.zeros(Q * n)
+    _check(load().slbm_get_pops(h, k, _ptr(out)), h)
+    return out
+
+
+def slbm_set_pops(h, k, Q, n, pops):
+    a = _f64(pops, Q * n)
+    _check(load().slbm_set_pops(h, k, _ptr(a)), h)
+
+
+def slbm_get_state(h) -> bytes:
+    size = ctypes.c_size_t(0)
+    _check(load().slbm_get_state(h, None, ctypes.byref(size)), h)
+    buf = ctypes.create_string_buffer(size.value)
+    _check(load().slbm_get_state(h, buf, ctypes.byref(size)), h)
+    return buf.raw
+
+
+def slbm_set_state(h, state: bytes):
+    buf = ctypes.create_string_buffer(state, len(state))
+    _check(load().slbm_set_state(h, buf, len(state)), h)
+
+
+def slbm_profile(h, enable):
+    _check(load().slbm_profile(h, int(bool(enable))), h)
+
+
+def slbm_profile_read(h):
+    """(per-kernel summed device ms over the profiled steps, steps)."""
+    ms = np.zeros(SLBM_PROFILE_KERNELS)
+    n = ctypes.c_longlong(0)
+    _check(load().slbm_profile_read(h, _ptr(ms), ctypes.byref(n)), h)
+    return ms, n.value
+
+
+def slbm_last_error(h=None) -> str:
+    m = load().slbm_last_error(h)
+    return m.decode() if m else ""
+
+
+# ------------------------------------------------------------ convenience
+
+class Solver:
+    """One handle on the current CUDA device.  The device workspace is a torch
+    uint8 tensor (PyTorch's allocator) and kernels run on torch's current
+    stream, so the library composes with torch code.  Host arrays are
+    (ny, nx) numpy arrays, x fastest."""
+
+    def __init__(self, nx, ny, lat_lo=SLBM_D2Q9, lat_hi=SLBM_D2Q25, tau=0.6, interp_order=3,
+                 periodic=(True, True), precision=SLBM_FP32, stream=None, torch_workspace=True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("slbm.Solver needs a CUDA device (no CPU fallback)")
+        self.nx, self.ny = nx, ny
+        self.n = nx * ny
+        self.lat = (lat_lo, lat_hi)
+        self.Q = (lat_lo * lat_lo, lat_hi * lat_hi)
+        self.precision = precision
+        st = torch.cuda.current_stream() if stream is None else stream
+        self.stream = st
+        self._ws = None
+        if torch_workspace:
+            nbytes = slbm_workspace_bytes(nx, ny, periodic[0], periodic[1], lat_lo, lat_hi,
+                                          interp_order, precision)
+            self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+            ptr = (self._ws.data_ptr() + 255) // 256 * 256
+            self.h = slbm_create_in(nx, ny, periodic[0], periodic[1], lat_lo, lat_hi, tau,
+                                    interp_order, SLBM_FRAME_LATTICE, precision, st.cuda_stream,
+                                    ptr, nbytes)
+        else:
+            self.h = slbm_create(nx, ny, periodic[0], periodic[1], lat_lo, lat_hi, tau,
+                                 interp_order, SLBM_FRAME_LATTICE, precision, st.cuda_stream)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            slbm_destroy(self.h)
+            self.h = None
+            self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def info(self) -> slbm_info_t:
+        return slbm_get_info(self.h)
+
+    @property
+    def dt(self) -> float:
+        return self.info.dt
+
+    def init_equilibrium(self, rho, ux, uy):
+        slbm_init_equilibrium(self.h, self.n, rho, ux, uy)
+
+    def set_flags(self, flags):
+        slbm_set_flags(self.h, self.n, flags)
+
+    def get_flags(self):
+        return slbm_get_flags(self.h, self.n).reshape(self.ny, self.nx)
+
+    def set_criterion(self, kind, thr=0.3):
+        slbm_set_criterion(self.h, kind, thr)
+
+    def set_boundary(self, side, kind, rho=None, ux=None, uy=None):
+        length = self.ny if side < 2 else self.nx
+        slbm_set_boundary(self.h, side, kind, length, rho, ux, uy)
+
+    def step(self, n=1):
+        slbm_step(self.h, n)
+
+    def sync(self):
+        slbm_sync(self.h)
+
+    def moments(self):
+        r, u, v, T = slbm_moments(self.h, self.n)
+        s = (self.ny, self.nx)
+        return r.reshape(s), u.reshape(s), v.reshape(s), T.reshape(s)
+
+    def audit(self):
+        return slbm_audit(self.h)
+
+    def get_pops(self, k):
+        """Populations of lattice k as (ny, nx, Q_k) (the oracle's order)."""
+        Q = self.Q[k]
+        a = slbm_get_pops(self.h, k, Q, self.n).reshape(Q, self.ny, self.nx)
+        return np.moveaxis(a, 0, -1)
+
+    def set_pops(self, k, pops):
+        Q = self.Q[k]
+        a = np.moveaxis(np.asarray(pops, dtype=np.float64).reshape(self.ny, self.nx, Q), -1, 0)
+        slbm_set_pops(self.h, k, Q, self.n, np.ascontiguousarray(a))
+
+    def profile(self, enable=True):
+        slbm_profile(self.h, enable)
+
+    def profile_read(self):
+        return slbm_profile_read(self.h)
+
+    def get_state(self) -> bytes:
+        return slbm_get_state(self.h)
+
+    def set_state(self, s: bytes):
+        slbm_set_state(self.h, s)

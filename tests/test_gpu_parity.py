@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs, element by element.
+
+Tolerances.  FP64 runs: the two sides differ only in rounding order (product
+form vs Gauss-Jordan inverse of a moment matrix whose entries reach
+c_max^8 ~ 4.4e3), so after 200 steps the relative L2 gap stays below 1e-11.
+FP32 runs: 1e-5 relative L2 on rho, u and T after 200 steps of the 64^2
+convected vortex (the stated FP32 tolerance); single-step populations
+within 2e-6 absolute (a few float ulps of O(1) values over <= 36 taps).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2102_12559_gb300 import workloads as WL
+from paper_2102_12559_gb300 import slbm
+
+pytestmark = pytest.mark.gpu
+
+FP32, FP64 = slbm.SLBM_FP32, slbm.SLBM_FP64
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def pair(nx, ny, n_lo=3, n_hi=5, tau=0.6, order=3, periodic=(True, True), precision=FP64):
+    g = slbm.Solver(nx, ny, n_lo, n_hi, tau=tau, interp_order=order, periodic=periodic,
+                    precision=precision)
+    o = O.Oracle(nx, ny, n_lo, n_hi, tau=tau, order=order, periodic=periodic)
+    return g, o
+
+
+def both(g, o, fn, *a, **k):
+    getattr(g, fn)(*a, **k)
+    getattr(o, fn)(*a, **k)
+
+
+def test_solver_info():
+    g = slbm.Solver(40, 24, 3, 5, tau=0.7)
+    info = g.info
+    assert abs(info.dt - 1 / np.sqrt(5 + np.sqrt(10))) < 1e-15
+    assert info.q_lo == 9 and info.q_hi == 25 and info.halo == 2
+    assert abs(info.omega - 1 / 0.7) < 1e-15
+
+
+@pytest.mark.parametrize("precision,tol", [(FP64, 1e-13), (FP32, 2e-6)])
+def test_uniform_flow_stays_uniform(precision, tol):
+    N = 48
+    g = slbm.Solver(N, N, 3, 5, tau=0.52, precision=precision)
+    g.init_equilibrium(*WL.uniform(N, N, 1.2, 0.25, -0.15))
+    g.set_flags(WL.random_flags(N, N, seed=3))
+    g.step(20)
+    r, u, v, _ = g.moments()
+    assert abs(r - 1.2).max() < tol and abs(u - 0.25).max() < tol and abs(v + 0.15).max() < tol
+
+
+@pytest.mark.parametrize("n_lo,n_hi", [(3, 5), (3, 4), (4, 5)])
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 5])
+def test_one_step_populations_fp64(n_lo, n_hi, order):
+    """37 x 29 grid (ragged against the 32 x 8 tiles), random high-order discs:
+    every native population after one step equals the oracle's."""
+    nx, ny = 37, 29
+    g, o = pair(nx, ny, n_lo, n_hi, tau=0.57, order=order)
+    fields = WL.perturbed(nx, ny, seed=10 + order, amp_rho=0.05, amp_u=0.2)
+    fl = WL.random_flags(nx, ny, seed=order, blobs=3, rmin=3, rmax=7)
+    both(g, o, "init_equilibrium", *fields)
+    both(g, o, "set_flags", fl)
+    both(g, o, "step", 1)
+    for k in (0, 1):
+        m = fl == k
+        np.testing.assert_allclose(g.get_pops(k)[m], o.get_pops(k)[m], rtol=0, atol=1e-13)
+    both(g, o, "step", 2)
+    for a, b in zip(g.moments(), o.moments()):
+        assert rel_l2(a, b) < 1e-13
+
+
+@pytest.fixture(scope="module")
+def vortex_oracle():
+    """Convected athermal vortex, 64 x 64 periodic, Mach 0.1 advection,
+    eps = 0.05, R = L/10, a fixed D2Q25 disc of radius L/4, D2Q9 elsewhere,
+    cubic Lagrange, nu = 1e-3 (tau = nu / dt + 1/2), 200 steps."""
+    L = 64
+    rho, ux, uy, disc = WL.convected_vortex(L)
+    dt = O.Oracle(8, 8, 3, 5, tau=0.6).dt
+    tau = 1e-3 / dt + 0.5
+    o = O.Oracle(L, L, 3, 5, tau=tau, order=3)
+    o.init_equilibrium(rho, ux, uy)
+    o.set_flags(disc)
+    a0 = o.audit()
+    o.step(200)
+    return dict(fields=(rho, ux, uy), disc=disc, tau=tau, mom=o.moments(), audit=(a0, o.audit()),
+                flags=o.get_flags())
+
+
+@pytest.mark.parametrize("precision,tol", [(FP64, 1e-11), (FP32, 1e-5)])
+def test_convected_vortex_200_steps(vortex_oracle, precision, tol):
+    L = 64
+    g = slbm.Solver(L, L, 3, 5, tau=vortex_oracle["tau"], interp_order=3, precision=precision)
+    g.init_equilibrium(*vortex_oracle["fields"])
+    g.set_flags(vortex_oracle["disc"])
+    g.step(200)
+    mom = g.moments()
+    errs = [rel_l2(a, b) for a, b in zip(mom, vortex_oracle["mom"])]
+    print(f"precision={precision} rel L2 rho,ux,uy,T = {errs}")
+    assert max(errs) < tol, errs
+    np.testing.assert_array_equal(g.get_flags(), vortex_oracle["flags"])
+
+
+def test_mach_criterion_fp64():
+    """Flags follow |u| > 0.3 after every step; flips are lifted / projected."""
+    nx, ny = 48, 40
+    g, o = pair(nx, ny, tau=0.58)
+    rho, ux, uy = WL.perturbed(nx, ny, seed=5, amp_rho=0.02, amp_u=0.05)
+    y = np.arange(ny)[:, None]
+    ux = ux + 0.4 * np.exp(-((y - ny / 2) ** 2) / 20.0)
+    both(g, o, "init_equilibrium", rho, ux, uy)
+    both(g, o, "set_criterion", 1, 0.3)
+    for _ in range(4):
+        both(g, o, "step", 5)
+        np.testing.assert_array_equal(g.get_flags(), o.get_flags())
+    f = o.get_flags()
+    assert 0 < f.sum() < nx * ny
+    for a, b in zip(g.moments(), o.moments()):
+        assert rel_l2(a, b) < 1e-11
+
+
+def _setup_jet(s, J, nx, ny):
+    """Inlet on x-, outflow on x+, free stream on both y sides."""
+    if isinstance(s, O.Oracle):
+        s.set_bc(0, O.BC_INLET, None, J["in_ux"], J["in_uy"])
+        s.set_bc(1, O.BC_OUTFLOW)
+        for side in (2, 3):
+            s.set_bc(side, O.BC_DIRICHLET, np.full(nx, J["fs_rho"]), np.full(nx, J["fs_ux"]),
+                     np.full(nx, J["fs_uy"]))
+    else:
+        s.set_boundary(0, slbm.SLBM_BC_INLET, None, J["in_ux"], J["in_uy"])
+        s.set_boundary(1, slbm.SLBM_BC_OUTFLOW)
+        for side in (2, 3):
+            s.set_boundary(side, slbm.SLBM_BC_DIRICHLET, np.full(nx, J["fs_rho"]),
+                           np.full(nx, J["fs_ux"]), np.full(nx, J["fs_uy"]))
+
+
+def test_free_jet_boundaries_fp64():
+    """Small free jet: inlet slot (fixed velocity, zero-gradient density),
+    outflow extrapolation, free-stream top / bottom, Mach criterion."""
+    nx, ny = 96, 64
+    J = WL.free_jet(nx, ny, slot=10, developed=True, core=2.0)
+    g, o = pair(nx, ny, tau=0.56, periodic=(False, False))
+    for s in (g, o):
+        s.init_equilibrium(J["rho"], J["ux"], J["uy"])
+        _setup_jet(s, J, nx, ny)
+        s.set_criterion(1, 0.3)
+    for _ in range(3):
+        both(g, o, "step", 10)
+        np.testing.assert_array_equal(g.get_flags(), o.get_flags())
+    assert o.get_flags().sum() > 0
+    for a, b in zip(g.moments(), o.moments()):
+        assert rel_l2(a, b) < 1e-11
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_single_lattice_conservation_fp64(k):
+    N = 40
+    g = slbm.Solver(N, N, 3, 5, tau=0.53, precision=FP64)
+    g.init_equilibrium(*WL.perturbed(N, N, seed=7))
+    g.set_flags(np.full((N, N), k, np.uint8))
+    a0 = g.audit()
+    g.step(50)
+    a1 = g.audit()
+    np.testing.assert_allclose(a1[:3], a0[:3], rtol=0, atol=1e-12 * a0[0])
+
+
+def test_state_roundtrip_bit_identical():
+    N = 40
+    g = slbm.Solver(N, N, 3, 5, tau=0.55, precision=FP32)
+    g.init_equilibrium(*WL.perturbed(N, N, seed=8, amp_u=0.3))
+    g.set_criterion(1, 0.3)
+    g.step(5)
+    snap = g.get_state()
+    g.step(7)
+    a = [x.copy() for x in g.moments()] + [g.get_flags().copy()]
+    g.set_state(snap)
+    g.step(7)
+    b = list(g.moments()) + [g.get_flags()]
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_full_size_jet_one_step_sampled_fp32():
+    """The 1024 x 512 free-jet workload in the launch configuration the
+    benchmark times (FP32, BCs, Mach criterion every step): one step against
+    the oracle on sampled cells, including every interface cell."""
+    nx, ny = 1024, 512
+    J = WL.free_jet(nx, ny)
+    dt = O.Oracle(8, 8, 3, 5, tau=0.6).dt
+    tau = (0.5 * 32 / 1000.0) / dt + 0.5
+    g = slbm.Solver(nx, ny, 3, 5, tau=tau, periodic=(False, False), precision=FP32)
+    o = O.Oracle(nx, ny, 3, 5, tau=tau, periodic=(False, False))
+    for s in (g, o):
+        s.init_equilibrium(J["rho"], J["ux"], J["uy"])
+        _setup_jet(s, J, nx, ny)
+    # the oracle's criterion decision on the initial state is imposed on the
+    # GPU too, so both step with the same flags
+    o.set_criterion(1, 0.3)
+    flags0 = o.get_flags()
+    g.set_criterion(1, 0.3)
+    g.set_flags(flags0)
+    g.step(1)
+    rng = np.random.default_rng(0)
+    cells = rng.choice(nx * ny, 3000, replace=False)
+    fl = flags0.ravel()
+    edge = np.nonzero(fl != np.roll(fl, 1))[0]
+    cells = np.unique(np.concatenate([cells, edge, np.arange(nx), np.arange(nx * (ny - 1), nx * ny),
+                                      np.arange(0, nx * ny, nx), np.arange(nx - 1, nx * ny, nx)]))
+    ref = o.step_cells(cells)
+    got = [g.get_pops(0).reshape(-1, 9), g.get_pops(1).reshape(-1, 25)]
+    for j, c in enumerate(cells):
+        k = fl[c]
+        Q = 25 if k else 9
+        np.testing.assert_allclose(got[k][c], ref[j, :Q], rtol=0, atol=2e-6)
+    # the new flags agree wherever |u| is not within float rounding of the threshold
+    r, u, v, _ = g.moments()
+    speed = np.sqrt(u ** 2 + v ** 2)
+    new = g.get_flags()
+    clear = np.abs(speed - 0.3) > 1e-5
+    np.testing.assert_array_equal(new[clear], (speed > 0.3)[clear].astype(np.uint8))

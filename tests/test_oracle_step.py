@@ -131,27 +131,31 @@ def test_equilibrium_is_collision_fixed_point_and_cells_conserve():
 
 
 def test_mach_criterion_flips_and_converts():
-    """Sec. IV.A criterion: after a step a cell is high-order iff |u| > 0.3
-    (c_s = 1); a flipped cell's populations are lifted / projected, so its
-    rho and u are unchanged by the flip."""
+    """Sec. IV.A criterion: a cell is high-order iff |u| > 0.3 (c_s = 1),
+    decided when the criterion is switched on and again after every step; a
+    flipped cell's populations are lifted / projected, so its rho and u are
+    unchanged by the flip."""
     N = 16
     rho, ux, uy = WL.uniform(N, N, 1.0, 0.0, 0.0)
     x = np.arange(N)
     ux = ux + 0.5 * np.exp(-((x - N / 2) ** 2) / 8.0)[None, :]
     o = O.Oracle(N, N, 3, 5, tau=0.6)
     o.init_equilibrium(rho, ux, uy)
-    o2 = O.Oracle(N, N, 3, 5, tau=0.6)
-    o2.init_equilibrium(rho, ux, uy)
+    r0, u0, v0, _ = o.moments()
     o.set_criterion(1, 0.3)
-    o.step(1)
-    o2.step(1)
-    r, u, v, _ = o.moments()
-    r2, u2, v2, _ = o2.moments()
     fl = o.get_flags()
-    np.testing.assert_array_equal(fl, (np.sqrt(u2 ** 2 + v2 ** 2) > 0.3).astype(np.uint8))
-    assert fl.sum() > 0 and fl.sum() < N * N
-    np.testing.assert_allclose(r, r2, atol=1e-14)
-    np.testing.assert_allclose(u, u2, atol=1e-14)
+    np.testing.assert_array_equal(fl, (np.sqrt(ux ** 2 + uy ** 2) > 0.3).astype(np.uint8))
+    assert 0 < fl.sum() < N * N
+    r1, u1, v1, _ = o.moments()
+    np.testing.assert_allclose(r1, r0, atol=1e-14)
+    np.testing.assert_allclose(u1, u0, atol=1e-14)
+    cx, cy, _ = O.lattice(5)
+    f = o.get_pops(1)[fl == 1]
+    ref = np.array([O.eq_lattice(5, 1.0, a, 0.0) for a in ux[fl == 1]])
+    np.testing.assert_allclose(f, ref, atol=1e-14)      # lift of an equilibrium
+    o.step(1)
+    r, u, v, _ = o.moments()
+    np.testing.assert_array_equal(o.get_flags(), (np.sqrt(u ** 2 + v ** 2) > 0.3).astype(np.uint8))
 
 
 def test_boundary_ghosts_keep_uniform_flow():
