@@ -152,7 +152,9 @@ void fill_lat(LatTab<R>& T, const Lattice1D& L, double dt, int P) {
   for (int j = 0; j < kMaxN; ++j) {
     T.off[j] = 0;
     T.ntap[j] = 1;
+    T.kref[j] = 0;
     T.c[j] = 0;
+    T.w1[j] = 0;
     for (int a = 0; a < kMaxP; ++a) T.w[j][a] = 0;
     for (int m = 0; m < kMaxN; ++m) T.vinv[j][m] = 0;
   }
@@ -160,6 +162,12 @@ void fill_lat(LatTab<R>& T, const Lattice1D& L, double dt, int P) {
     double w[kMaxP];
     node_stencil(L.c[j] * dt, P, &T.off[j], &T.ntap[j], w);
     T.c[j] = (R)L.c[j];
+    T.w1[j] = (R)L.w[j];
+    int k = 0;  // differential form: zero the largest weight (see LatTab)
+    for (int a = 1; a < T.ntap[j]; ++a)
+      if (std::fabs(w[a]) > std::fabs(w[k])) k = a;
+    T.kref[j] = k;
+    if (T.ntap[j] > 1) w[k] = 0.0;
     for (int a = 0; a < kMaxP; ++a) T.w[j][a] = (R)w[a];
     for (int m = 0; m < L.n; ++m) T.vinv[j][m] = (R)L.vinv[j][m];
   }
@@ -320,23 +328,20 @@ BcDev bc_dev(slbm_s* h) {
   return b;
 }
 
-template <class S>
-cudaError_t ghosts_t(slbm_s* h, int buf, const uint8_t* flag) {
-  return launch_ghosts<S>(h->pd, (S*)h->pops(buf, 0), (S*)h->pops(buf, 1), flag, bc_dev(h), h->st);
-}
-
 cudaError_t ghosts(slbm_s* h, int buf, const uint8_t* flag) {
-  return h->precision == SLBM_FP64 ? ghosts_t<double>(h, buf, flag) : ghosts_t<float>(h, buf, flag);
-}
-
-template <class S>
-cudaError_t convert_t(slbm_s* h, int buf, const uint8_t* fold, const uint8_t* fnew) {
-  return launch_convert<S>(h->pd, (S*)h->pops(buf, 0), (S*)h->pops(buf, 1), fold, fnew, h->st);
+  if (h->precision == SLBM_FP64)
+    return launch_ghosts<double, double>(h->pd, (double*)h->pops(buf, 0), (double*)h->pops(buf, 1),
+                                         flag, bc_dev(h), h->st);
+  return launch_ghosts<float, float>(h->pf, (float*)h->pops(buf, 0), (float*)h->pops(buf, 1), flag,
+                                     bc_dev(h), h->st);
 }
 
 cudaError_t convert(slbm_s* h, int buf, const uint8_t* fold, const uint8_t* fnew) {
-  return h->precision == SLBM_FP64 ? convert_t<double>(h, buf, fold, fnew)
-                                   : convert_t<float>(h, buf, fold, fnew);
+  if (h->precision == SLBM_FP64)
+    return launch_convert<double, double>(h->pd, (double*)h->pops(buf, 0),
+                                          (double*)h->pops(buf, 1), fold, fnew, h->st);
+  return launch_convert<float, float>(h->pf, (float*)h->pops(buf, 0), (float*)h->pops(buf, 1),
+                                      fold, fnew, h->st);
 }
 
 // Next tracing event (recorded on the handle's stream), or success when off.
@@ -396,19 +401,12 @@ void fill_params(Params<R>& p, const slbm_s* h, const Lattice1D& a, const Lattic
   p.band = h->lay.G;
   fill_lat(p.lat[0], a, dt, h->P);
   fill_lat(p.lat[1], b, dt, h->P);
-  ConvTab& t = p.conv;
-  t.nq = a.n;
-  t.nQ = b.n;
-  for (int j = 0; j < kMaxN; ++j) {
-    t.cq[j] = j < a.n ? a.c[j] : 0.0;
-    t.cQ[j] = j < b.n ? b.c[j] : 0.0;
+  ConvTab<R>& t = p.conv;
+  for (int j = 0; j < kMaxN; ++j)
     for (int m = 0; m < kMaxN; ++m) {
-      t.vinvq[j][m] = (j < a.n && m < a.n) ? a.vinv[j][m] : 0.0;
-      t.vinvQ[j][m] = (j < b.n && m < b.n) ? b.vinv[j][m] : 0.0;
-      t.lift[j][m] = 0.0;
-      t.proj[j][m] = 0.0;
+      t.lift[j][m] = R(0);
+      t.proj[j][m] = R(0);
     }
-  }
   // L[a][j] = sum_{m < nq} VQ^-1[a][m] c_q[j]^m
   for (int aa = 0; aa < b.n; ++aa)
     for (int j = 0; j < a.n; ++j) {
@@ -417,11 +415,11 @@ void fill_params(Params<R>& p, const slbm_s* h, const Lattice1D& a, const Lattic
         s += b.vinv[aa][m] * pw;
         pw *= a.c[j];
       }
-      t.lift[aa][j] = s;
+      t.lift[aa][j] = (R)s;
     }
   // P[j][a] = l^q_j(c^Q_a)
   for (int j = 0; j < a.n; ++j)
-    for (int aa = 0; aa < b.n; ++aa) t.proj[j][aa] = lagrange_eval(a.c, a.n, j, b.c[aa]);
+    for (int aa = 0; aa < b.n; ++aa) t.proj[j][aa] = (R)lagrange_eval(a.c, a.n, j, b.c[aa]);
 }
 
 void refresh_params(slbm_s* h) {
@@ -436,8 +434,9 @@ int upload(slbm_s* h, void* dst, const void* src, size_t bytes) {
   return SLBM_OK;
 }
 
-template <class S>
-int pack_all(slbm_s* h, int k, double* host, int unpack, const double* in_host) {
+template <class S, class R>
+int pack_all(slbm_s* h, const Params<R>& prm, int k, double* host, int unpack,
+             const double* in_host) {
   const int n = k ? h->nhi : h->nlo, Q = n * n;
   const size_t nc = h->ncell();
   // the four nc-double macro slots stage up to four planes at a time
@@ -451,13 +450,14 @@ int pack_all(slbm_s* h, int k, double* host, int unpack, const double* in_host) 
         if (rc) return rc;
       }
       for (int q = 0; q < cnt; ++q)
-        SLBM_CK(h, launch_pack<S>(h->pd, i0 + q, 1, nullptr, nullptr, 1, (S*)h->pops(h->cur, k),
-                                  h->at<double>(h->lay.macro[q]), h->st),
+        SLBM_CK(h, (launch_pack<S, R>(prm, k, i0 + q, 1, nullptr, nullptr, 1,
+                                      (S*)h->pops(h->cur, k), h->at<double>(h->lay.macro[q]),
+                                      h->st)),
                 "unpack launch");
     } else {
       for (int q = 0; q < cnt; ++q) {
-        SLBM_CK(h, launch_pack<S>(h->pd, i0 + q, 1, (const S*)h->pops(h->cur, k),
-                                  h->at<double>(h->lay.macro[q]), 0, nullptr, nullptr, h->st),
+        SLBM_CK(h, (launch_pack<S, R>(prm, k, i0 + q, 1, (const S*)h->pops(h->cur, k),
+                                      h->at<double>(h->lay.macro[q]), 0, nullptr, nullptr, h->st)),
                 "pack launch");
         SLBM_CK(h, cudaMemcpyAsync(host + (size_t)(i0 + q) * nc, h->at<double>(h->lay.macro[q]),
                                    nc * 8, cudaMemcpyDeviceToHost, h->st),
@@ -470,8 +470,8 @@ int pack_all(slbm_s* h, int k, double* host, int unpack, const double* in_host) 
 }
 
 int pack_any(slbm_s* h, int k, double* host, int unpack, const double* in) {
-  return h->precision == SLBM_FP64 ? pack_all<double>(h, k, host, unpack, in)
-                                   : pack_all<float>(h, k, host, unpack, in);
+  return h->precision == SLBM_FP64 ? pack_all<double, double>(h, h->pd, k, host, unpack, in)
+                                   : pack_all<float, float>(h, h->pf, k, host, unpack, in);
 }
 
 int init_eq_dev(slbm_s* h) {
@@ -480,10 +480,12 @@ int init_eq_dev(slbm_s* h) {
   double* u = h->at<double>(h->lay.macro[1]);
   double* v = h->at<double>(h->lay.macro[2]);
   if (h->precision == SLBM_FP64)
-    e = launch_init_eq<double>(h->pd, (double*)h->pops(h->cur, 0), (double*)h->pops(h->cur, 1), r,
+    e = launch_init_eq<double, double>(h->pd, (double*)h->pops(h->cur, 0),
+                                       (double*)h->pops(h->cur, 1), r,
                                u, v, h->st);
   else
-    e = launch_init_eq<float>(h->pd, (float*)h->pops(h->cur, 0), (float*)h->pops(h->cur, 1), r, u,
+    e = launch_init_eq<float, float>(h->pf, (float*)h->pops(h->cur, 0), (float*)h->pops(h->cur, 1),
+                                     r, u,
                               v, h->st);
   SLBM_CK(h, e, "init launch");
   SLBM_CK(h, ghosts(h, h->cur, h->flags(h->fcur)), "ghost launch");
@@ -687,10 +689,10 @@ int slbm_set_criterion(slbm_t h, int kind, double threshold) {
     uint8_t* tmp = h->at<uint8_t>(h->lay.flag_tmp);
     cudaError_t e =
         h->precision == SLBM_FP64
-            ? launch_criterion<double>(h->pd, (const double*)h->pops(h->cur, 0),
+            ? launch_criterion<double, double>(h->pd, (const double*)h->pops(h->cur, 0),
                                        (const double*)h->pops(h->cur, 1), h->flags(h->fcur), tmp,
                                        h->st)
-            : launch_criterion<float>(h->pd, (const float*)h->pops(h->cur, 0),
+            : launch_criterion<float, float>(h->pf, (const float*)h->pops(h->cur, 0),
                                       (const float*)h->pops(h->cur, 1), h->flags(h->fcur), tmp,
                                       h->st);
     SLBM_CK(h, e, "criterion launch");
@@ -746,11 +748,11 @@ int slbm_moments_device(slbm_t h, double* rho, double* ux, double* uy, double* T
   SLBM_GUARD(h);
   cudaError_t e;
   if (h->precision == SLBM_FP64)
-    e = launch_moments<double>(h->pd, (const double*)h->pops(h->cur, 0),
+    e = launch_moments<double, double>(h->pd, (const double*)h->pops(h->cur, 0),
                                (const double*)h->pops(h->cur, 1), h->flags(h->fcur), rho, ux, uy, T,
                                h->st);
   else
-    e = launch_moments<float>(h->pd, (const float*)h->pops(h->cur, 0),
+    e = launch_moments<float, float>(h->pf, (const float*)h->pops(h->cur, 0),
                               (const float*)h->pops(h->cur, 1), h->flags(h->fcur), rho, ux, uy, T,
                               h->st);
   SLBM_CK(h, e, "moments launch");
@@ -776,16 +778,16 @@ int slbm_moments(slbm_t h, double* rho, double* ux, double* uy, double* T) {
 int slbm_audit(slbm_t h, double out[4]) {
   SLBM_GUARD(h);
   if (!out) return fail(h, SLBM_EINVAL, "out is required");
-  const int np = audit_parts(h->pd);
+  const int np = audit_parts(h->g.nx, h->g.ny);
   double* part = h->at<double>(h->lay.partials);
   double* res = h->at<double>(h->lay.audit_out);
   cudaError_t e;
   if (h->precision == SLBM_FP64)
-    e = launch_audit<double>(h->pd, (const double*)h->pops(h->cur, 0),
+    e = launch_audit<double, double>(h->pd, (const double*)h->pops(h->cur, 0),
                              (const double*)h->pops(h->cur, 1), h->flags(h->fcur), part, np, res,
                              h->st);
   else
-    e = launch_audit<float>(h->pd, (const float*)h->pops(h->cur, 0),
+    e = launch_audit<float, float>(h->pf, (const float*)h->pops(h->cur, 0),
                             (const float*)h->pops(h->cur, 1), h->flags(h->fcur), part, np, res,
                             h->st);
   SLBM_CK(h, e, "audit launch");

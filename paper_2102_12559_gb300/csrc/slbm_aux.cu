@@ -1,8 +1,10 @@
 // slbm_aux.cu -- interface conversion, ghost / boundary fill, equilibrium
-// initialisation, macroscopic moments, FP64 audit and host packing kernels.
-#include "slbm_impl.cuh"
-
+// initialisation, macroscopic moments, Mach criterion, FP64 audit and host
+// packing kernels.  S = storage type, R = arithmetic type (float for the FP32
+// path: GB300's FP64 rate is a small fraction of its FP32 rate, so doubles
+// appear only in moment sums and the audit).
 #include "../../include/slbm.h"
+#include "slbm_eq.cuh"
 
 namespace slbm {
 
@@ -10,130 +12,111 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// Raw Gaussian moments h_m(u) = E[(u + Z)^m], m < 5, T = T_L = 1.
-__device__ __forceinline__ void gauss_moments(double u, double* h) {
-  const double u2 = u * u;
-  h[0] = 1.0;
-  h[1] = u;
-  h[2] = 1.0 + u2;
-  h[3] = u * (u2 + 3.0);
-  h[4] = u2 * u2 + 6.0 * u2 + 3.0;
-}
-
-// 1-D lattice-equilibrium factors phi_j = sum_m vinv[j][m] h_m, j < n.
-__device__ __forceinline__ void factors(const double (*vinv)[kMaxN], int n, const double* h,
-                                        double* phi) {
-  for (int j = 0; j < n; ++j) {
-    double s = 0.0;
-    for (int m = 0; m < n; ++m) s += vinv[j][m] * h[m];
-    phi[j] = s;
-  }
-}
-
-template <class S>
-__device__ __forceinline__ double ld(const S* p) { return static_cast<double>(*p); }
-
-// Lattice-frame equilibrium of lattice k (eq. feqL0) written to planes at `base`.
-template <class S>
-__device__ void write_eq(const ConvTab& t, int k, S* f, long long plane, int base, double rho,
-                         double ux, double uy) {
-  const int n = k ? t.nQ : t.nq;
-  const double(*vinv)[kMaxN] = k ? t.vinvQ : t.vinvq;
-  double hx[kMaxN], hy[kMaxN], px[kMaxN], py[kMaxN];
-  gauss_moments(ux, hx);
-  gauss_moments(uy, hy);
-  factors(vinv, n, hx, px);
-  factors(vinv, n, hy, py);
-  for (int jy = 0; jy < n; ++jy)
-    for (int jx = 0; jx < n; ++jx)
-      f[(size_t)(jx + n * jy) * plane + base] = static_cast<S>(rho * py[jy] * px[jx]);
-}
-
-// Lifting f_q -> f_Q (Sec. III.B): the q x q moments are kept and the rest are
-// those of the Q-lattice equilibrium at the cell's rho, u.  In tensor form the
-// lifted vector is f^L_Q(rho, u) + L (f_q - f^L_q) L^T with the fixed nQ x nq
-// matrix L = VQ^-1[:, :nq] Vq, which carries the non-equilibrium part with its
-// moments intact and zero higher moments.  Accumulated in FP64.
-template <class S>
-__device__ void lift_cell(const ConvTab& t, const S* src, S* dst, long long plane, int base) {
-  const int nq = t.nq, nQ = t.nQ;
-  double F[kMaxN][kMaxN];
-  double rho = 0.0, mx = 0.0, my = 0.0;
-  for (int jy = 0; jy < nq; ++jy)
-    for (int jx = 0; jx < nq; ++jx) {
-      const double v = ld(src + (size_t)(jx + nq * jy) * plane + base);
-      F[jy][jx] = v;
-      rho += v;
-      mx += t.cq[jx] * v;
-      my += t.cq[jy] * v;
-    }
-  const double ux = mx / rho, uy = my / rho;
-  double hx[kMaxN], hy[kMaxN], pqx[kMaxN], pqy[kMaxN], pQx[kMaxN], pQy[kMaxN];
-  gauss_moments(ux, hx);
-  gauss_moments(uy, hy);
-  factors(t.vinvq, nq, hx, pqx);
-  factors(t.vinvq, nq, hy, pqy);
-  factors(t.vinvQ, nQ, hx, pQx);
-  factors(t.vinvQ, nQ, hy, pQy);
-  for (int jy = 0; jy < nq; ++jy)
-    for (int jx = 0; jx < nq; ++jx) F[jy][jx] -= rho * pqy[jy] * pqx[jx];
-  double A[kMaxN][kMaxN];  // A[ay][jx] = sum_jy L[ay][jy] D[jy][jx]
-  for (int ay = 0; ay < nQ; ++ay)
-    for (int jx = 0; jx < nq; ++jx) {
-      double s = 0.0;
-      for (int jy = 0; jy < nq; ++jy) s += t.lift[ay][jy] * F[jy][jx];
-      A[ay][jx] = s;
-    }
-  for (int ay = 0; ay < nQ; ++ay)
-    for (int ax = 0; ax < nQ; ++ax) {
-      double s = rho * pQy[ay] * pQx[ax];
-      for (int jx = 0; jx < nq; ++jx) s += t.lift[ax][jx] * A[ay][jx];
-      dst[(size_t)(ax + nQ * ay) * plane + base] = static_cast<S>(s);
-    }
-}
-
-// Projection f_Q -> f_q (Sec. III.C): f_q keeps the first q x q moments of f_Q;
-// per axis that is Lagrange interpolation of the Q nodes onto the q nodes,
-// f_q = P F_Q P^T with P[j][a] = l^q_j(c^Q_a).  Accumulated in FP64.
-template <class S>
-__device__ void project_cell(const ConvTab& t, const S* src, S* dst, long long plane, int base) {
-  const int nq = t.nq, nQ = t.nQ;
-  double F[kMaxN][kMaxN];
-  for (int ay = 0; ay < nQ; ++ay)
-    for (int ax = 0; ax < nQ; ++ax) F[ay][ax] = ld(src + (size_t)(ax + nQ * ay) * plane + base);
-  double A[kMaxN][kMaxN];  // A[jy][ax] = sum_ay P[jy][ay] F[ay][ax]
-  for (int jy = 0; jy < nq; ++jy)
-    for (int ax = 0; ax < nQ; ++ax) {
-      double s = 0.0;
-      for (int ay = 0; ay < nQ; ++ay) s += t.proj[jy][ay] * F[ay][ax];
-      A[jy][ax] = s;
-    }
-  for (int jy = 0; jy < nq; ++jy)
-    for (int jx = 0; jx < nq; ++jx) {
-      double s = 0.0;
-      for (int ax = 0; ax < nQ; ++ax) s += t.proj[jx][ax] * A[jy][ax];
-      dst[(size_t)(jx + nq * jy) * plane + base] = static_cast<S>(s);
-    }
-}
-
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// Interface conversion (step 2 of Sec. III.D, done once per node per step).
-// A cell needs its other-lattice representation when a cell of the other
-// lattice lies within the stencil reach (band), and a cell whose flag changed
-// needs its new lattice.  Both are "convert from the lattice the cell was
-// computed in (flag_old) to the other one".
-template <class S>
+template <class S, class R>
+__device__ __forceinline__ void load_dev(const LatTab<R>& L, const S* f, long long plane, int base,
+                                         R (*s)[kMaxN]) {
+  for (int iy = 0; iy < L.n; ++iy)
+    for (int ix = 0; ix < L.n; ++ix)
+      s[iy][ix] = static_cast<R>(f[(size_t)(ix + L.n * iy) * plane + base]);
+}
+
+template <class S, class R>
+__device__ __forceinline__ void store_dev(const LatTab<R>& L, S* f, long long plane, int base,
+                                          const R (*s)[kMaxN]) {
+  for (int iy = 0; iy < L.n; ++iy)
+    for (int ix = 0; ix < L.n; ++ix)
+      f[(size_t)(ix + L.n * iy) * plane + base] = static_cast<S>(s[iy][ix]);
+}
+
+// Density deviation and momentum of a deviation vector, accumulated in FP64.
+template <class R>
+__device__ __forceinline__ void sums64(const LatTab<R>& L, const R (*s)[kMaxN], double& dr,
+                                       double& mx, double& my) {
+  dr = mx = my = 0.0;
+  for (int iy = 0; iy < L.n; ++iy)
+    for (int ix = 0; ix < L.n; ++ix) {
+      const double v = (double)s[iy][ix];
+      dr += v;
+      mx += (double)L.c[ix] * v;
+      my += (double)L.c[iy] * v;
+    }
+}
+
+// Lifting f_q -> f_Q (Sec. III.B): keep the q x q moments, take the rest from
+// the Q-lattice equilibrium at the cell's rho, u.  Tensor form: f_Q = f^L_Q +
+// L (f_q - f^L_q) L^T, where L = VQ^-1[:, :nq] Vq carries the non-equilibrium
+// part with its q x q moments intact and zero higher moments; the W shift
+// cancels, so the same holds for deviations.  Moment sums in FP64.
+template <class R>
+__device__ void lift_vals(const Params<R>& p, const R (*sq)[kMaxN], R (*sQ)[kMaxN]) {
+  const LatTab<R>& Lq = p.lat[0];
+  const LatTab<R>& LQ = p.lat[1];
+  const int nq = Lq.n, nQ = LQ.n;
+  double dr, mx, my;
+  sums64<R>(Lq, sq, dr, mx, my);
+  const double rho = 1.0 + dr;
+  const R ux = (R)(mx / rho), uy = (R)(my / rho);
+  R eq[kMaxN][kMaxN], D[kMaxN][kMaxN], A[kMaxN][kMaxN];
+  eq_dev<R>(Lq, nq, (R)dr, ux, uy, eq);
+  for (int jy = 0; jy < nq; ++jy)
+    for (int jx = 0; jx < nq; ++jx) D[jy][jx] = sq[jy][jx] - eq[jy][jx];
+  eq_dev<R>(LQ, nQ, (R)dr, ux, uy, sQ);
+  for (int ay = 0; ay < nQ; ++ay)          // A[ay][jx] = sum_jy L[ay][jy] D[jy][jx]
+    for (int jx = 0; jx < nq; ++jx) {
+      R t = R(0);
+      for (int jy = 0; jy < nq; ++jy) t += p.conv.lift[ay][jy] * D[jy][jx];
+      A[ay][jx] = t;
+    }
+  for (int ay = 0; ay < nQ; ++ay)
+    for (int ax = 0; ax < nQ; ++ax) {
+      R t = R(0);
+      for (int jx = 0; jx < nq; ++jx) t += p.conv.lift[ax][jx] * A[ay][jx];
+      sQ[ay][ax] += t;
+    }
+}
+
+// Projection f_Q -> f_q (Sec. III.C): keep the first q x q moments; per axis
+// that is Lagrange interpolation of the Q nodes onto the q nodes, f_q = P F_Q
+// P^T with P[j][a] = l^q_j(c^Q_a).  P maps the rest populations W_Q to W_q, so
+// deviations project the same way.
+template <class R>
+__device__ void project_vals(const Params<R>& p, const R (*sQ)[kMaxN], R (*sq)[kMaxN]) {
+  const int nq = p.lat[0].n, nQ = p.lat[1].n;
+  R A[kMaxN][kMaxN];  // A[jy][ax] = sum_ay P[jy][ay] F[ay][ax]
+  for (int jy = 0; jy < nq; ++jy)
+    for (int ax = 0; ax < nQ; ++ax) {
+      R t = R(0);
+      for (int ay = 0; ay < nQ; ++ay) t += p.conv.proj[jy][ay] * sQ[ay][ax];
+      A[jy][ax] = t;
+    }
+  for (int jy = 0; jy < nq; ++jy)
+    for (int jx = 0; jx < nq; ++jx) {
+      R t = R(0);
+      for (int ax = 0; ax < nQ; ++ax) t += p.conv.proj[jx][ax] * A[jy][ax];
+      sq[jy][jx] = t;
+    }
+}
+
+// Interface conversion (step 2 of Sec. III.D, once per node per step).  Every
+// node a cell of the other lattice reads (the band: a cell of the other
+// lattice within the stencil reach) gets its other-lattice populations, and a
+// cell whose flag flipped gets its new lattice.  A flipped node in the band is
+// then read by the other lattice as the conversion of its NEW populations
+// (e.g. lift(project(f)) after a high -> low flip), as the paper's step 2 reads
+// every collocation point in the velocity set it now carries.
+template <class S, class R>
 __global__ void __launch_bounds__(kTX * kTY)
-k_convert(const Params<double> p, S* f0, S* f1, const uint8_t* __restrict__ flag_old,
+k_convert(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ flag_old,
           const uint8_t* __restrict__ flag_new) {
   const int x = blockIdx.x * kTX + threadIdx.x;
   const int y = blockIdx.y * kTY + threadIdx.y;
   if (x >= p.nx || y >= p.ny) return;
   const int c = x + p.nx * y;
   const int old = flag_old[c], nw = flag_new[c];
-  bool need = old != nw;
-  for (int dy = -p.band; dy <= p.band && !need; ++dy) {
+  bool band = false;
+  for (int dy = -p.band; dy <= p.band && !band; ++dy) {
     int yy = y + dy;
     if (yy < 0 || yy >= p.ny) {
       if (!p.periodic_y) continue;
@@ -145,34 +128,59 @@ k_convert(const Params<double> p, S* f0, S* f1, const uint8_t* __restrict__ flag
         if (!p.periodic_x) continue;
         xx = wrap(xx, p.nx);
       }
-      if (flag_new[xx + p.nx * yy] != nw) { need = true; break; }
+      if (flag_new[xx + p.nx * yy] != nw) { band = true; break; }
     }
   }
-  if (!need) return;
+  if (old == nw && !band) return;
   const int base = (y + p.G) * p.pitch + (x + kOX);
-  if (old == 0)
-    lift_cell<S>(p.conv, f0, f1, p.plane, base);
-  else
-    project_cell<S>(p.conv, f1, f0, p.plane, base);
+  R a[kMaxN][kMaxN], b[kMaxN][kMaxN];
+  if (old == 0) {
+    load_dev<S, R>(p.lat[0], f0, p.plane, base, a);
+    lift_vals<R>(p, a, b);
+    store_dev<S, R>(p.lat[1], f1, p.plane, base, b);
+    if (old != nw && band) {  // now high-order; low-order readers see its projection
+      project_vals<R>(p, b, a);
+      store_dev<S, R>(p.lat[0], f0, p.plane, base, a);
+    }
+  } else {
+    load_dev<S, R>(p.lat[1], f1, p.plane, base, b);
+    project_vals<R>(p, b, a);
+    store_dev<S, R>(p.lat[0], f0, p.plane, base, a);
+    if (old != nw && band) {  // now low-order; high-order readers see its lifting
+      lift_vals<R>(p, a, b);
+      store_dev<S, R>(p.lat[1], f1, p.plane, base, b);
+    }
+  }
 }
 
-template <class S>
-__device__ double cell_rho(const Params<double>& p, const S* f0, const S* f1,
-                           const uint8_t* flag, int x, int y) {
+// rho of an interior cell from its own lattice (FP64 sum of 1 + deviations).
+template <class S, class R>
+__device__ double cell_rho(const Params<R>& p, const S* f0, const S* f1, const uint8_t* flag,
+                           int x, int y) {
   const int k = flag[x + p.nx * y];
-  const int Q = k ? p.conv.nQ * p.conv.nQ : p.conv.nq * p.conv.nq;
+  const int n = p.lat[k].n;
   const S* f = k ? f1 : f0;
   const int base = (y + p.G) * p.pitch + (x + kOX);
-  double r = 0.0;
-  for (int i = 0; i < Q; ++i) r += ld(f + (size_t)i * p.plane + base);
+  double r = 1.0;
+  for (int i = 0; i < n * n; ++i) r += (double)f[(size_t)i * p.plane + base];
   return r;
+}
+
+template <class S, class R>
+__device__ void write_eq_both(const Params<R>& p, S* f0, S* f1, int base, double rho, double ux,
+                              double uy) {
+  R e[kMaxN][kMaxN];
+  for (int k = 0; k < 2; ++k) {
+    eq_dev<R>(p.lat[k], p.lat[k].n, (R)(rho - 1.0), (R)ux, (R)uy, e);
+    store_dev<S, R>(p.lat[k], k ? f1 : f0, p.plane, base, e);
+  }
 }
 
 // Ghost ring: periodic images, or the boundary state of a non-periodic side
 // in both lattices (OUTFLOW copies the nearest interior cell, DIRICHLET /
 // INLET write the lattice equilibrium).  A non-periodic y side wins at corners.
-template <class S>
-__global__ void k_ghosts(const Params<double> p, S* f0, S* f1, const uint8_t* __restrict__ flag,
+template <class S, class R>
+__global__ void k_ghosts(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ flag,
                          const BcDev bc) {
   const int G = p.G, W = p.nx + 2 * G;
   const long long nstrip = (long long)G * W;
@@ -206,7 +214,7 @@ __global__ void k_ghosts(const Params<double> p, S* f0, S* f1, const uint8_t* __
         sy = yi;
       } else {
         eq = true;
-        er = kind == SLBM_BC_INLET ? cell_rho<S>(p, f0, f1, flag, xi, yi) : bc.rho[side][xi];
+        er = kind == SLBM_BC_INLET ? cell_rho<S, R>(p, f0, f1, flag, xi, yi) : bc.rho[side][xi];
         eu = bc.ux[side][xi];
         ev = bc.uy[side][xi];
       }
@@ -223,7 +231,7 @@ __global__ void k_ghosts(const Params<double> p, S* f0, S* f1, const uint8_t* __
         sx = xi;
       } else {
         eq = true;
-        er = kind == SLBM_BC_INLET ? cell_rho<S>(p, f0, f1, flag, xi, sy) : bc.rho[side][sy];
+        er = kind == SLBM_BC_INLET ? cell_rho<S, R>(p, f0, f1, flag, xi, sy) : bc.rho[side][sy];
         eu = bc.ux[side][sy];
         ev = bc.uy[side][sy];
       }
@@ -231,58 +239,56 @@ __global__ void k_ghosts(const Params<double> p, S* f0, S* f1, const uint8_t* __
   }
   const int gbase = (gy + G) * p.pitch + (gx + kOX);
   if (eq) {
-    write_eq<S>(p.conv, 0, f0, p.plane, gbase, er, eu, ev);
-    write_eq<S>(p.conv, 1, f1, p.plane, gbase, er, eu, ev);
+    write_eq_both<S, R>(p, f0, f1, gbase, er, eu, ev);
   } else {
     const int sbase = (sy + G) * p.pitch + (sx + kOX);
-    const int q0 = p.conv.nq * p.conv.nq, q1 = p.conv.nQ * p.conv.nQ;
+    const int q0 = p.lat[0].n * p.lat[0].n, q1 = p.lat[1].n * p.lat[1].n;
     for (int i = 0; i < q0; ++i) f0[(size_t)i * p.plane + gbase] = f0[(size_t)i * p.plane + sbase];
     for (int i = 0; i < q1; ++i) f1[(size_t)i * p.plane + gbase] = f1[(size_t)i * p.plane + sbase];
   }
 }
 
-template <class S>
+template <class S, class R>
 __global__ void __launch_bounds__(kTX * kTY)
-k_init_eq(const Params<double> p, S* f0, S* f1, const double* __restrict__ rho,
+k_init_eq(const Params<R> p, S* f0, S* f1, const double* __restrict__ rho,
           const double* __restrict__ ux, const double* __restrict__ uy) {
   const int x = blockIdx.x * kTX + threadIdx.x;
   const int y = blockIdx.y * kTY + threadIdx.y;
   if (x >= p.nx || y >= p.ny) return;
   const int c = x + p.nx * y;
-  const int base = (y + p.G) * p.pitch + (x + kOX);
-  write_eq<S>(p.conv, 0, f0, p.plane, base, rho[c], ux[c], uy[c]);
-  write_eq<S>(p.conv, 1, f1, p.plane, base, rho[c], ux[c], uy[c]);
+  write_eq_both<S, R>(p, f0, f1, (y + p.G) * p.pitch + (x + kOX), rho[c], ux[c], uy[c]);
 }
 
-// Per-cell rho, u, kinetic T and (for the audit) momentum and energy sums.
-template <class S>
-__device__ void cell_moments(const Params<double>& p, const S* f0, const S* f1, int k, int base,
+// rho, momentum and sum v^2/2 f of a cell's own lattice, in FP64.
+template <class S, class R>
+__device__ void cell_moments(const Params<R>& p, const S* f0, const S* f1, int k, int base,
                              double& r, double& jx, double& jy, double& e) {
-  const int n = k ? p.conv.nQ : p.conv.nq;
-  const double* c = k ? p.conv.cQ : p.conv.cq;
+  const LatTab<R>& L = p.lat[k];
   const S* f = k ? f1 : f0;
-  r = jx = jy = e = 0.0;
-  for (int iy = 0; iy < n; ++iy)
-    for (int ix = 0; ix < n; ++ix) {
-      const double v = ld(f + (size_t)(ix + n * iy) * p.plane + base);
+  r = 1.0;
+  jx = jy = 0.0;
+  e = 1.0;  // sum W_i |c_i|^2 / 2 = D T_L / 2 = 1
+  for (int iy = 0; iy < L.n; ++iy)
+    for (int ix = 0; ix < L.n; ++ix) {
+      const double v = (double)f[(size_t)(ix + L.n * iy) * p.plane + base];
+      const double cx = (double)L.c[ix], cy = (double)L.c[iy];
       r += v;
-      jx += c[ix] * v;
-      jy += c[iy] * v;
-      e += 0.5 * (c[ix] * c[ix] + c[iy] * c[iy]) * v;
+      jx += cx * v;
+      jy += cy * v;
+      e += 0.5 * (cx * cx + cy * cy) * v;
     }
 }
 
-template <class S>
+template <class S, class R>
 __global__ void __launch_bounds__(kTX * kTY)
-k_moments(const Params<double> p, const S* f0, const S* f1, const uint8_t* __restrict__ flag,
+k_moments(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restrict__ flag,
           double* rho, double* ux, double* uy, double* T) {
   const int x = blockIdx.x * kTX + threadIdx.x;
   const int y = blockIdx.y * kTY + threadIdx.y;
   if (x >= p.nx || y >= p.ny) return;
   const int c = x + p.nx * y;
-  const int base = (y + p.G) * p.pitch + (x + kOX);
   double r, jx, jy, e;
-  cell_moments<S>(p, f0, f1, flag[c], base, r, jx, jy, e);
+  cell_moments<S, R>(p, f0, f1, flag[c], (y + p.G) * p.pitch + (x + kOX), r, jx, jy, e);
   const double u = jx / r, v = jy / r;
   if (rho) rho[c] = r;
   if (ux) ux[c] = u;
@@ -291,26 +297,25 @@ k_moments(const Params<double> p, const S* f0, const S* f1, const uint8_t* __res
 }
 
 // Mach criterion of Sec. IV.A on the current state (flag = |u| > thr, c_s = 1).
-template <class S>
+template <class S, class R>
 __global__ void __launch_bounds__(kTX * kTY)
-k_criterion(const Params<double> p, const S* f0, const S* f1, const uint8_t* __restrict__ flag,
+k_criterion(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restrict__ flag,
             uint8_t* __restrict__ flag_new) {
   const int x = blockIdx.x * kTX + threadIdx.x;
   const int y = blockIdx.y * kTY + threadIdx.y;
   if (x >= p.nx || y >= p.ny) return;
   const int c = x + p.nx * y;
-  const int base = (y + p.G) * p.pitch + (x + kOX);
   double r, jx, jy, e;
-  cell_moments<S>(p, f0, f1, flag[c], base, r, jx, jy, e);
-  const double u = jx / r, v = jy / r;
+  cell_moments<S, R>(p, f0, f1, flag[c], (y + p.G) * p.pitch + (x + kOX), r, jx, jy, e);
+  const R u = (R)(jx / r), v = (R)(jy / r);
   flag_new[c] = sqrt(u * u + v * v) > p.thr ? 1 : 0;
 }
 
 // FP64 conservation audit: per-block partial sums, then one block adds the
 // partials in a fixed order (deterministic result).
-template <class S>
+template <class S, class R>
 __global__ void __launch_bounds__(kThreads)
-k_audit_partial(const Params<double> p, const S* f0, const S* f1, const uint8_t* __restrict__ flag,
+k_audit_partial(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restrict__ flag,
                 double* partials) {
   __shared__ double sh[4][kThreads];
   double a[4] = {0.0, 0.0, 0.0, 0.0};
@@ -318,9 +323,8 @@ k_audit_partial(const Params<double> p, const S* f0, const S* f1, const uint8_t*
   for (long long c = (long long)blockIdx.x * kThreads + threadIdx.x; c < ncell;
        c += (long long)gridDim.x * kThreads) {
     const int x = (int)(c % p.nx), y = (int)(c / p.nx);
-    const int base = (y + p.G) * p.pitch + (x + kOX);
     double r, jx, jy, e;
-    cell_moments<S>(p, f0, f1, flag[c], base, r, jx, jy, e);
+    cell_moments<S, R>(p, f0, f1, flag[c], (y + p.G) * p.pitch + (x + kOX), r, jx, jy, e);
     a[0] += r; a[1] += jx; a[2] += jy; a[3] += e;
   }
   for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = a[q];
@@ -351,112 +355,114 @@ __global__ void __launch_bounds__(kThreads) k_audit_final(const double* partials
     for (int q = 0; q < 4; ++q) out4[q] = sh[q][0];
 }
 
-// Copy planes i0 .. i0+cnt-1 of one lattice's interior to / from a
-// plane-major double array.
-template <class S>
-__global__ void k_pack(const Params<double> p, int i0, int cnt, const S* f, double* out,
+// Planes i0 .. i0+cnt-1 of lattice k's interior to / from a plane-major array
+// of full populations f = s + W.
+template <class S, class R>
+__global__ void k_pack(const Params<R> p, int k, int i0, int cnt, const S* f, double* out,
                        int unpack, S* fw, const double* in) {
+  const LatTab<R>& L = p.lat[k];
   const long long ncell = (long long)p.nx * p.ny;
   const long long total = ncell * cnt;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const int i = i0 + (int)(t / ncell);
+    const double Wi = (double)L.w1[i % L.n] * (double)L.w1[i / L.n];
     const long long c = t % ncell;
     const int x = (int)(c % p.nx), y = (int)(c / p.nx);
     const size_t e = (size_t)i * p.plane + (y + p.G) * p.pitch + (x + kOX);
     if (unpack)
-      fw[e] = static_cast<S>(in[t]);
+      fw[e] = static_cast<S>(in[t] - Wi);
     else
-      out[t] = static_cast<double>(f[e]);
+      out[t] = static_cast<double>(f[e]) + Wi;
   }
 }
 
-dim3 tile_grid(const Params<double>& p) {
+template <class R>
+dim3 tile_grid(const Params<R>& p) {
   return dim3((p.nx + kTX - 1) / kTX, (p.ny + kTY - 1) / kTY);
 }
 
 }  // namespace
 
-int audit_parts(const Params<double>& p) {
-  const long long ncell = (long long)p.nx * p.ny;
-  long long b = (ncell + kThreads - 1) / kThreads;
+int audit_parts(int nx, int ny) {
+  const long long ncell = (long long)nx * ny;
+  const long long b = (ncell + kThreads - 1) / kThreads;
   return (int)(b < 1024 ? b : 1024);
 }
 
-template <class S>
-cudaError_t launch_convert(const Params<double>& pd, S* f0, S* f1, const uint8_t* flag_old,
+template <class S, class R>
+cudaError_t launch_convert(const Params<R>& p, S* f0, S* f1, const uint8_t* flag_old,
                            const uint8_t* flag_new, cudaStream_t st) {
-  k_convert<S><<<tile_grid(pd), dim3(kTX, kTY), 0, st>>>(pd, f0, f1, flag_old, flag_new);
+  k_convert<S, R><<<tile_grid(p), dim3(kTX, kTY), 0, st>>>(p, f0, f1, flag_old, flag_new);
   return cudaGetLastError();
 }
 
-template <class S>
-cudaError_t launch_ghosts(const Params<double>& pd, S* f0, S* f1, const uint8_t* flag,
-                          const BcDev& bc, cudaStream_t st) {
-  const long long total = 2LL * pd.G * (pd.nx + 2 * pd.G) + 2LL * pd.G * pd.ny;
+template <class S, class R>
+cudaError_t launch_ghosts(const Params<R>& p, S* f0, S* f1, const uint8_t* flag, const BcDev& bc,
+                          cudaStream_t st) {
+  const long long total = 2LL * p.G * (p.nx + 2 * p.G) + 2LL * p.G * p.ny;
   if (total == 0) return cudaSuccess;
-  k_ghosts<S><<<(unsigned)((total + kThreads - 1) / kThreads), kThreads, 0, st>>>(pd, f0, f1,
-                                                                                  flag, bc);
+  k_ghosts<S, R><<<(unsigned)((total + 127) / 128), 128, 0, st>>>(p, f0, f1, flag, bc);
   return cudaGetLastError();
 }
 
-template <class S>
-cudaError_t launch_init_eq(const Params<double>& pd, S* f0, S* f1, const double* rho,
-                           const double* ux, const double* uy, cudaStream_t st) {
-  k_init_eq<S><<<tile_grid(pd), dim3(kTX, kTY), 0, st>>>(pd, f0, f1, rho, ux, uy);
+template <class S, class R>
+cudaError_t launch_init_eq(const Params<R>& p, S* f0, S* f1, const double* rho, const double* ux,
+                           const double* uy, cudaStream_t st) {
+  k_init_eq<S, R><<<tile_grid(p), dim3(kTX, kTY), 0, st>>>(p, f0, f1, rho, ux, uy);
   return cudaGetLastError();
 }
 
-template <class S>
-cudaError_t launch_moments(const Params<double>& pd, const S* f0, const S* f1,
-                           const uint8_t* flag, double* rho, double* ux, double* uy, double* T,
-                           cudaStream_t st) {
-  k_moments<S><<<tile_grid(pd), dim3(kTX, kTY), 0, st>>>(pd, f0, f1, flag, rho, ux, uy, T);
+template <class S, class R>
+cudaError_t launch_moments(const Params<R>& p, const S* f0, const S* f1, const uint8_t* flag,
+                           double* rho, double* ux, double* uy, double* T, cudaStream_t st) {
+  k_moments<S, R><<<tile_grid(p), dim3(kTX, kTY), 0, st>>>(p, f0, f1, flag, rho, ux, uy, T);
   return cudaGetLastError();
 }
 
-template <class S>
-cudaError_t launch_criterion(const Params<double>& pd, const S* f0, const S* f1,
-                             const uint8_t* flag, uint8_t* flag_new, cudaStream_t st) {
-  k_criterion<S><<<tile_grid(pd), dim3(kTX, kTY), 0, st>>>(pd, f0, f1, flag, flag_new);
+template <class S, class R>
+cudaError_t launch_criterion(const Params<R>& p, const S* f0, const S* f1, const uint8_t* flag,
+                             uint8_t* flag_new, cudaStream_t st) {
+  k_criterion<S, R><<<tile_grid(p), dim3(kTX, kTY), 0, st>>>(p, f0, f1, flag, flag_new);
   return cudaGetLastError();
 }
 
-template <class S>
-cudaError_t launch_audit(const Params<double>& pd, const S* f0, const S* f1, const uint8_t* flag,
+template <class S, class R>
+cudaError_t launch_audit(const Params<R>& p, const S* f0, const S* f1, const uint8_t* flag,
                          double* partials, int nparts, double* out4, cudaStream_t st) {
-  k_audit_partial<S><<<nparts, kThreads, 0, st>>>(pd, f0, f1, flag, partials);
+  k_audit_partial<S, R><<<nparts, kThreads, 0, st>>>(p, f0, f1, flag, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_audit_final<<<1, kThreads, 0, st>>>(partials, nparts, out4);
   return cudaGetLastError();
 }
 
-template <class S>
-cudaError_t launch_pack(const Params<double>& pd, int i0, int cnt, const S* f, double* out,
+template <class S, class R>
+cudaError_t launch_pack(const Params<R>& p, int k, int i0, int cnt, const S* f, double* out,
                         int unpack, S* fw, const double* in, cudaStream_t st) {
-  k_pack<S><<<1024, kThreads, 0, st>>>(pd, i0, cnt, f, out, unpack, fw, in);
+  k_pack<S, R><<<1024, kThreads, 0, st>>>(p, k, i0, cnt, f, out, unpack, fw, in);
   return cudaGetLastError();
 }
 
-#define SLBM_AUX_INST(S)                                                                     \
-  template cudaError_t launch_convert<S>(const Params<double>&, S*, S*, const uint8_t*,      \
-                                         const uint8_t*, cudaStream_t);                      \
-  template cudaError_t launch_ghosts<S>(const Params<double>&, S*, S*, const uint8_t*,       \
-                                        const BcDev&, cudaStream_t);                         \
-  template cudaError_t launch_init_eq<S>(const Params<double>&, S*, S*, const double*,       \
-                                         const double*, const double*, cudaStream_t);        \
-  template cudaError_t launch_moments<S>(const Params<double>&, const S*, const S*,          \
-                                         const uint8_t*, double*, double*, double*, double*, \
-                                         cudaStream_t);                                      \
-  template cudaError_t launch_criterion<S>(const Params<double>&, const S*, const S*,       \
-                                           const uint8_t*, uint8_t*, cudaStream_t);          \
-  template cudaError_t launch_audit<S>(const Params<double>&, const S*, const S*,            \
-                                       const uint8_t*, double*, int, double*, cudaStream_t); \
-  template cudaError_t launch_pack<S>(const Params<double>&, int, int, const S*, double*, int, \
-                                      S*, const double*, cudaStream_t);
-SLBM_AUX_INST(float)
-SLBM_AUX_INST(double)
+#define SLBM_AUX_INST(S, R)                                                                  \
+  template cudaError_t launch_convert<S, R>(const Params<R>&, S*, S*, const uint8_t*,        \
+                                            const uint8_t*, cudaStream_t);                   \
+  template cudaError_t launch_ghosts<S, R>(const Params<R>&, S*, S*, const uint8_t*,         \
+                                           const BcDev&, cudaStream_t);                      \
+  template cudaError_t launch_init_eq<S, R>(const Params<R>&, S*, S*, const double*,         \
+                                            const double*, const double*, cudaStream_t);     \
+  template cudaError_t launch_moments<S, R>(const Params<R>&, const S*, const S*,            \
+                                            const uint8_t*, double*, double*, double*,       \
+                                            double*, cudaStream_t);                          \
+  template cudaError_t launch_criterion<S, R>(const Params<R>&, const S*, const S*,          \
+                                              const uint8_t*, uint8_t*, cudaStream_t);       \
+  template cudaError_t launch_audit<S, R>(const Params<R>&, const S*, const S*,              \
+                                          const uint8_t*, double*, int, double*,             \
+                                          cudaStream_t);                                     \
+  template cudaError_t launch_pack<S, R>(const Params<R>&, int, int, int, const S*, double*, \
+                                         int, S*, const double*, cudaStream_t);
+SLBM_AUX_INST(float, float)
+SLBM_AUX_INST(double, double)
 #undef SLBM_AUX_INST
 
 }  // namespace slbm

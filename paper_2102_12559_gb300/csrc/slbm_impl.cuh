@@ -2,12 +2,17 @@
 // semi-Lagrangian LBM library: parameter tables passed to every kernel by
 // value, the device-memory layout, and the kernel launchers.
 //
-// Layout in HBM (see the design notes): structure-of-arrays population planes,
-// x fastest.  Every plane of lattice k in buffer b holds (ny + 2G) rows of
-// `pitch` elements; cell (x, y), x in [-G, nx+G), y in [-G, ny+G), sits at
-// element (y + G) * pitch + (x + OX).  The G-wide ring of ghost cells is
-// refreshed after every step (periodic images or boundary states), so the
-// streaming kernel never wraps an index.
+// Layout in HBM: structure-of-arrays population planes, x fastest.  Every
+// plane of lattice k in buffer b holds (ny + 2G) rows of `pitch` elements;
+// cell (x, y), x in [-G, nx+G), y in [-G, ny+G), sits at element
+// (y + G) * pitch + (x + kOX).  The G-wide ring of ghost cells is refreshed
+// after every step (periodic images or boundary states), so the streaming
+// kernel never wraps an index.
+//
+// Stored values are deviations s_i = f_i - W_i from the rest equilibrium
+// (rho = 1, u = 0, whose lattice populations are the weights W_i).  The
+// method is affine in that shift (Lagrange weights sum to one, sum W_i = 1,
+// sum c_i W_i = 0), and small stored magnitudes keep FP32 rounding small.
 #pragma once
 
 #include <cstddef>
@@ -22,24 +27,27 @@ constexpr int kOX = 8;          // left pad of a row, elements (keeps 16-byte ro
 constexpr int kTX = 32;         // tile width  (one warp per row segment)
 constexpr int kTY = 8;          // tile height (8 warps per CTA)
 
-// One lattice of the pair, in the arithmetic type R of the streaming kernel.
+// One lattice of the pair, in the arithmetic type R.
 template <class R>
 struct LatTab {
   int n;                        // 1-D nodes, Q = n * n
   int off[kMaxN];               // first collocation point of node j, relative to the cell
   int ntap[kMaxN];              // 1 (shift snapped to an integer) or P
+  int kref[kMaxN];              // stencil point with the largest Lagrange weight
   R c[kMaxN];                   // 1-D velocities (T_L = 1, lattice frame)
-  R w[kMaxN][kMaxP];            // Lagrange weights of node j's departure point
+  R w1[kMaxN];                  // 1-D Gauss-Hermite weights (W_i = w1[ix] w1[iy])
+  // Lagrange weights of node j's departure point in differential form: the
+  // interpolant is v[kref] + sum_a w[a] (v[a] - v[kref]) with w[kref] = 0,
+  // which passes constants through exactly even with rounded weights.
+  R w[kMaxN][kMaxP];
   R vinv[kMaxN][kMaxN];         // inverse Vandermonde: phi_j(u) = sum_m vinv[j][m] h_m(u)
 };
 
-// Interface conversion tables (always FP64: moment accumulation in double).
+// Interface conversion tables.
+template <class R>
 struct ConvTab {
-  int nq, nQ;
-  double cq[kMaxN], cQ[kMaxN];
-  double vinvq[kMaxN][kMaxN], vinvQ[kMaxN][kMaxN];
-  double lift[kMaxN][kMaxN];    // nQ x nq: non-equilibrium lifting L = VQ^-1[:, :nq] Vq
-  double proj[kMaxN][kMaxN];    // nq x nQ: projection P[j][a] = l^q_j(c^Q_a)
+  R lift[kMaxN][kMaxN];         // nQ x nq: non-equilibrium lifting L = VQ^-1[:, :nq] Vq
+  R proj[kMaxN][kMaxN];         // nq x nQ: projection P[j][a] = l^q_j(c^Q_a)
 };
 
 template <class R>
@@ -53,7 +61,7 @@ struct Params {
   R omega;
   int band;                     // stencil reach in cells (band radius)
   LatTab<R> lat[2];             // 0 = low-order, 1 = high-order
-  ConvTab conv;
+  ConvTab<R> conv;
 };
 
 // Boundary description for the ghost kernel (device arrays, may be null).
@@ -64,42 +72,41 @@ struct BcDev {
   const double* uy[4];
 };
 
-// Launchers (defined in the kernel translation units).  S = storage type.
-// fin / fout: base of buffer b for lattice 0 and lattice 1.
+// Launchers (defined in the kernel translation units).  S = storage type,
+// R = arithmetic type.  f0 / f1: base of one buffer for lattice 0 / 1.
 template <class S, class R>
 cudaError_t launch_stream_collide(const Params<R>& p, int P, const S* fin0, const S* fin1,
                                   S* fout0, S* fout1, const uint8_t* flag_cur,
                                   uint8_t* flag_nxt, cudaStream_t st);
 
-template <class S>
-cudaError_t launch_convert(const Params<double>& pd, S* f0, S* f1, const uint8_t* flag_old,
+template <class S, class R>
+cudaError_t launch_convert(const Params<R>& p, S* f0, S* f1, const uint8_t* flag_old,
                            const uint8_t* flag_new, cudaStream_t st);
 
-template <class S>
-cudaError_t launch_ghosts(const Params<double>& pd, S* f0, S* f1, const uint8_t* flag,
+template <class S, class R>
+cudaError_t launch_ghosts(const Params<R>& p, S* f0, S* f1, const uint8_t* flag,
                           const BcDev& bc, cudaStream_t st);
 
-template <class S>
-cudaError_t launch_init_eq(const Params<double>& pd, S* f0, S* f1, const double* rho,
+template <class S, class R>
+cudaError_t launch_init_eq(const Params<R>& p, S* f0, S* f1, const double* rho,
                            const double* ux, const double* uy, cudaStream_t st);
 
-template <class S>
-cudaError_t launch_moments(const Params<double>& pd, const S* f0, const S* f1,
-                           const uint8_t* flag, double* rho, double* ux, double* uy, double* T,
-                           cudaStream_t st);
+template <class S, class R>
+cudaError_t launch_moments(const Params<R>& p, const S* f0, const S* f1, const uint8_t* flag,
+                           double* rho, double* ux, double* uy, double* T, cudaStream_t st);
 
-template <class S>
-cudaError_t launch_criterion(const Params<double>& pd, const S* f0, const S* f1,
-                             const uint8_t* flag, uint8_t* flag_new, cudaStream_t st);
+template <class S, class R>
+cudaError_t launch_criterion(const Params<R>& p, const S* f0, const S* f1, const uint8_t* flag,
+                             uint8_t* flag_new, cudaStream_t st);
 
-template <class S>
-cudaError_t launch_audit(const Params<double>& pd, const S* f0, const S* f1, const uint8_t* flag,
+template <class S, class R>
+cudaError_t launch_audit(const Params<R>& p, const S* f0, const S* f1, const uint8_t* flag,
                          double* partials, int nparts, double* out4, cudaStream_t st);
 
-template <class S>
-cudaError_t launch_pack(const Params<double>& pd, int i0, int cnt, const S* f, double* out,
+template <class S, class R>
+cudaError_t launch_pack(const Params<R>& p, int k, int i0, int cnt, const S* f, double* out,
                         int unpack, S* fw, const double* in, cudaStream_t st);
 
-int audit_parts(const Params<double>& pd);
+int audit_parts(int nx, int ny);
 
 }  // namespace slbm

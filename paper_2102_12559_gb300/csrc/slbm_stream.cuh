@@ -14,7 +14,8 @@
 //      f^L_i = rho phi_ix(u_x) phi_iy(u_y), phi = V^-1 h(u) with the Gaussian
 //      moments h_m(u) = E[(u + Z)^m] (eq. feqL0 restated for a tensor-product
 //      Gauss-Hermite lattice), and BGK: f <- f + omega (f^L - f)
-//      (eq. Pond_f_equation with omega_1 = omega_2).
+//      (eq. Pond_f_equation with omega_1 = omega_2), all on the stored
+//      deviations s_i = f_i - W_i.
 //   3. optionally the Mach criterion of Sec. IV.A for the next step's flag.
 //
 // A CTA owns a 32 x 8 tile, one cell per thread; a warp is one 32-cell row
@@ -24,43 +25,34 @@
 // lanes are all of one lattice skips the other pass entirely.
 #pragma once
 
-#include "slbm_impl.cuh"
+#include "slbm_eq.cuh"
 
 namespace slbm {
 
 template <class S, class R>
 __device__ __forceinline__ R ldg_as(const S* p) { return static_cast<R>(__ldg(p)); }
 
-// Interpolate along x over one row: node jx's stencil starting at `row`.
+// Interpolate along x over one row: node jx's stencil starting at `row`
+// (differential form v[k] + sum_a w[a] (v[a] - v[k]), see LatTab).
 template <int P, class S, class R>
 __device__ __forceinline__ R row_interp(const S* __restrict__ row, const LatTab<R>& L, int jx) {
   if (L.ntap[jx] == 1) return ldg_as<S, R>(row);
-  R t = R(0);
+  R v[P];
 #pragma unroll
-  for (int a = 0; a < P; ++a) t += L.w[jx][a] * ldg_as<S, R>(row + a);
+  for (int a = 0; a < P; ++a) v[a] = ldg_as<S, R>(row + a);
+  const int k = L.kref[jx];
+  R vk = v[0];
+#pragma unroll
+  for (int a = 1; a < P; ++a) vk = a == k ? v[a] : vk;
+  R t = vk;
+#pragma unroll
+  for (int a = 0; a < P; ++a) t += L.w[jx][a] * (v[a] - vk);
   return t;
 }
 
-// 1-D equilibrium factors phi_j(u), j < N: sum_m vinv[j][m] h_m(u).
-template <int N, class R>
-__device__ __forceinline__ void eq_factors(const LatTab<R>& L, R u, R* phi) {
-  R h[kMaxN];
-  const R u2 = u * u;
-  h[0] = R(1);
-  h[1] = u;
-  h[2] = R(1) + u2;
-  h[3] = u * (u2 + R(3));
-  h[4] = u2 * u2 + R(6) * u2 + R(3);
-#pragma unroll
-  for (int j = 0; j < N; ++j) {
-    R s = R(0);
-#pragma unroll
-    for (int m = 0; m < N; ++m) s += L.vinv[j][m] * h[m];
-    phi[j] = s;
-  }
-}
-
-// Stream + collide one cell of lattice L (N nodes per axis).
+// Stream + collide one cell of lattice L (N nodes per axis), on deviations
+// s_i = f_i - W_i (streaming is affine in the shift; the collision uses the
+// deviation form of the product equilibrium, see slbm_eq.cuh).
 template <int N, int P, class S, class R>
 __device__ __forceinline__ void stream_collide_cell(const Params<R>& p, const LatTab<R>& L,
                                                     const S* __restrict__ fin,
@@ -76,22 +68,28 @@ __device__ __forceinline__ void stream_collide_cell(const Params<R>& p, const La
       if (L.ntap[jy] == 1) {
         acc = row_interp<P, S, R>(pl + L.off[jy] * p.pitch, L, jx);
       } else {
-        acc = R(0);
+        R r[P];
 #pragma unroll
-        for (int b = 0; b < P; ++b)
-          acc += L.w[jy][b] * row_interp<P, S, R>(pl + (L.off[jy] + b) * p.pitch, L, jx);
+        for (int b = 0; b < P; ++b) r[b] = row_interp<P, S, R>(pl + (L.off[jy] + b) * p.pitch, L, jx);
+        const int k = L.kref[jy];
+        R rk = r[0];
+#pragma unroll
+        for (int b = 1; b < P; ++b) rk = b == k ? r[b] : rk;
+        acc = rk;
+#pragma unroll
+        for (int b = 0; b < P; ++b) acc += L.w[jy][b] * (r[b] - rk);
       }
       f[jx + N * jy] = acc;
     }
   }
-  // rho and momentum through row / column sums of the N x N population block
-  R rho = R(0), mx = R(0), my = R(0);
+  // density deviation and momentum through row / column sums of the N x N block
+  R dr = R(0), mx = R(0), my = R(0);
 #pragma unroll
   for (int jy = 0; jy < N; ++jy) {
     R rs = R(0);
 #pragma unroll
     for (int jx = 0; jx < N; ++jx) rs += f[jx + N * jy];
-    rho += rs;
+    dr += rs;
     my += L.c[jy] * rs;
   }
 #pragma unroll
@@ -101,19 +99,20 @@ __device__ __forceinline__ void stream_collide_cell(const Params<R>& p, const La
     for (int jy = 0; jy < N; ++jy) cs += f[jx + N * jy];
     mx += L.c[jx] * cs;
   }
-  const R inv = R(1) / rho;
+  const R inv = R(1) / (R(1) + dr);
   ux = mx * inv;
   uy = my * inv;
-  R px[N], py[N];
-  eq_factors<N, R>(L, ux, px);
-  eq_factors<N, R>(L, uy, py);
+  R dx[N], dy[N];
+  dphi<R>(L, N, ux, dx);
+  dphi<R>(L, N, uy, dy);
 #pragma unroll
   for (int jy = 0; jy < N; ++jy) {
-    const R ry = rho * py[jy];
+    const R py = L.w1[jy] + dy[jy];
 #pragma unroll
     for (int jx = 0; jx < N; ++jx) {
       const int i = jx + N * jy;
-      const R feq = ry * px[jx];
+      const R px = L.w1[jx] + dx[jx];
+      const R feq = dr * px * py + L.w1[jx] * dy[jy] + dx[jx] * L.w1[jy] + dx[jx] * dy[jy];
       fout[(size_t)i * p.plane + base] = static_cast<S>(f[i] + p.omega * (feq - f[i]));
     }
   }

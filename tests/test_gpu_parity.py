@@ -101,9 +101,12 @@ def test_convected_vortex_200_steps(vortex_oracle, precision, tol):
     g.set_flags(vortex_oracle["disc"])
     g.step(200)
     mom = g.moments()
-    errs = [rel_l2(a, b) for a, b in zip(mom, vortex_oracle["mom"])]
-    print(f"precision={precision} rel L2 rho,ux,uy,T = {errs}")
-    assert max(errs) < tol, errs
+    ref = vortex_oracle["mom"]
+    errs = [rel_l2(a, b) for a, b in zip(mom, ref)]
+    # u is a vector field: relative L2 of (u_x, u_y) together
+    eu = rel_l2(np.stack([mom[1], mom[2]]), np.stack([ref[1], ref[2]]))
+    print(f"precision={precision} rel L2 rho,ux,uy,T = {errs}, vector u = {eu}")
+    assert max(errs[0], eu, errs[3]) < tol, (errs, eu)
     np.testing.assert_array_equal(g.get_flags(), vortex_oracle["flags"])
 
 
@@ -215,13 +218,19 @@ def test_full_size_jet_one_step_sampled_fp32():
                                       np.arange(0, nx * ny, nx), np.arange(nx - 1, nx * ny, nx)]))
     ref = o.step_cells(cells)
     got = [g.get_pops(0).reshape(-1, 9), g.get_pops(1).reshape(-1, 25)]
+    new = g.get_flags().ravel()
     for j, c in enumerate(cells):
         k = fl[c]
         Q = 25 if k else 9
-        np.testing.assert_allclose(got[k][c], ref[j, :Q], rtol=0, atol=2e-6)
+        if new[c] == k:
+            np.testing.assert_allclose(got[k][c], ref[j, :Q], rtol=0, atol=2e-6)
+        else:
+            # flipped after the step: its new lattice holds the oracle's
+            # lifting / projection of the step's result
+            conv = O.lift(3, 5, ref[j, :9]) if k == 0 else O.project(5, 3, ref[j, :25])
+            np.testing.assert_allclose(got[new[c]][c], conv, rtol=0, atol=2e-6)
     # the new flags agree wherever |u| is not within float rounding of the threshold
     r, u, v, _ = g.moments()
-    speed = np.sqrt(u ** 2 + v ** 2)
-    new = g.get_flags()
+    speed = np.sqrt(u ** 2 + v ** 2).ravel()
     clear = np.abs(speed - 0.3) > 1e-5
     np.testing.assert_array_equal(new[clear], (speed > 0.3)[clear].astype(np.uint8))
