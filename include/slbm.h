@@ -59,7 +59,7 @@ typedef struct slbm_s *slbm_t;
 #define SLBM_ECUDA      -3   /* a CUDA call failed; the handle is now unusable */
 #define SLBM_ENONFINITE -4   /* the audit found a non-finite sum */
 #define SLBM_ENOCONV    -5   /* reserved: frame iteration did not converge */
-#define SLBM_ETIMEOUT   -6   /* reserved: a bounded device wait ran out */
+#define SLBM_ETIMEOUT   -6   /* a bounded device wait ran out; the handle is now unusable */
 #define SLBM_ESTATE     -7   /* call not valid in the handle's current state */
 
 /* Lattices of Table I, by 1-D node count n: D2Q9 (n=3), D2Q16 (4), D2Q25 (5). */
@@ -188,10 +188,9 @@ SLBM_API int slbm_audit(slbm_t h, double out[4]);
  * flag is k (plus interface cells) hold meaningful values.  Synchronises. */
 SLBM_API int slbm_get_pops(slbm_t h, int k, double *out);
 
-/* Overwrite the populations of lattice k (same layout).  The caller is
- * responsible for both representations where cells of the other lattice
- * read them; a subsequent slbm_set_flags with the current flags refreshes
- * the interface cells. */
+/* Overwrite the populations of lattice k (same layout).  Afterwards the
+ * interface cells' other-lattice populations are recomputed from each cell's
+ * own lattice (lift / project), as after a step. */
 SLBM_API int slbm_set_pops(slbm_t h, int k, const double *in);
 
 /* Snapshot / restore the full state (populations of both lattices, flags,
@@ -203,10 +202,10 @@ SLBM_API int slbm_set_state(slbm_t h, const void *buf, size_t bytes);
  * and starts bracketing every kernel slbm_step launches with CUDA events on
  * the handle's stream; slbm_profile(h, 0) stops.  slbm_profile_read()
  * synchronises and returns, per kernel of the step sequence (index 0 =
- * stream-collide, 1 = interface conversion, 2 = ghost / boundary fill), the
- * summed device milliseconds over the recorded steps, and the number of
+ * stream-collide, 1 = interface conversion with the boundary ghost images),
+ * the summed device milliseconds over the recorded steps, and the number of
  * recorded steps.  ms must hold SLBM_PROFILE_KERNELS doubles. */
-#define SLBM_PROFILE_KERNELS 3
+#define SLBM_PROFILE_KERNELS 2
 SLBM_API int slbm_profile(slbm_t h, int enable);
 SLBM_API int slbm_profile_read(slbm_t h, double *ms, long long *steps);
 

@@ -19,6 +19,9 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "../../include/slbm.h"
 #include "slbm_impl.cuh"
 
@@ -152,7 +155,6 @@ void fill_lat(LatTab<R>& T, const Lattice1D& L, double dt, int P) {
   for (int j = 0; j < kMaxN; ++j) {
     T.off[j] = 0;
     T.ntap[j] = 1;
-    T.kref[j] = 0;
     T.c[j] = 0;
     T.w1[j] = 0;
     for (int a = 0; a < kMaxP; ++a) T.w[j][a] = 0;
@@ -163,11 +165,7 @@ void fill_lat(LatTab<R>& T, const Lattice1D& L, double dt, int P) {
     node_stencil(L.c[j] * dt, P, &T.off[j], &T.ntap[j], w);
     T.c[j] = (R)L.c[j];
     T.w1[j] = (R)L.w[j];
-    int k = 0;  // differential form: zero the largest weight (see LatTab)
-    for (int a = 1; a < T.ntap[j]; ++a)
-      if (std::fabs(w[a]) > std::fabs(w[k])) k = a;
-    T.kref[j] = k;
-    if (T.ntap[j] > 1) w[k] = 0.0;
+    if (T.ntap[j] > 1) w[(P - 1) / 2] = 0.0;  // differential form (see LatTab)
     for (int a = 0; a < kMaxP; ++a) T.w[j][a] = (R)w[a];
     for (int m = 0; m < L.n; ++m) T.vinv[j][m] = (R)L.vinv[j][m];
   }
@@ -181,7 +179,7 @@ struct Layout {
   int G, pitch, rows;
   long long plane;           // elements per plane, padded
   size_t pops[2][2];         // byte offsets [buffer][lattice]
-  size_t flags[2], flag_tmp, macro[4], partials, audit_out, bc[4][3];
+  size_t flags[2], flag_tmp, tile_mask, macro[4], partials, audit_out, err, bc[4][3];
   size_t total;
 };
 
@@ -241,9 +239,12 @@ Layout make_layout(const slbm_grid* g, int lo, int hi, int order, int precision)
   const size_t nc = (size_t)g->nx * g->ny;
   for (int f = 0; f < 2; ++f) { Lo.flags[f] = off; off = align_up(off + nc, 256); }
   Lo.flag_tmp = off; off = align_up(off + nc, 256);
+  const size_t ntiles = (size_t)((g->nx + kTX - 1) / kTX) * ((g->ny + kTY - 1) / kTY);
+  Lo.tile_mask = off; off = align_up(off + ntiles, 256);
   for (int m = 0; m < 4; ++m) { Lo.macro[m] = off; off = align_up(off + nc * 8, 256); }
   Lo.partials = off; off = align_up(off + 4 * 1024 * 8, 256);
   Lo.audit_out = off; off = align_up(off + 4 * 8, 256);
+  Lo.err = off; off = align_up(off + 16, 256);
   const size_t side = (size_t)std::max(g->nx, g->ny);
   for (int s = 0; s < 4; ++s)
     for (int q = 0; q < 3; ++q) { Lo.bc[s][q] = off; off = align_up(off + side * 8, 256); }
@@ -254,6 +255,7 @@ Layout make_layout(const slbm_grid* g, int lo, int hi, int order, int precision)
 }  // namespace
 
 struct slbm_s {
+  CUtensorMap tmap[2][2];        // TMA descriptors of the planes [buffer][lattice]
   slbm_grid g;
   int nlo, nhi, P, precision;
   double tau;
@@ -328,20 +330,83 @@ BcDev bc_dev(slbm_s* h) {
   return b;
 }
 
-cudaError_t ghosts(slbm_s* h, int buf, const uint8_t* flag) {
-  if (h->precision == SLBM_FP64)
-    return launch_ghosts<double, double>(h->pd, (double*)h->pops(buf, 0), (double*)h->pops(buf, 1),
-                                         flag, bc_dev(h), h->st);
-  return launch_ghosts<float, float>(h->pf, (float*)h->pops(buf, 0), (float*)h->pops(buf, 1), flag,
-                                     bc_dev(h), h->st);
+// Full ghost fill of both buffers (setup paths).  The buffer in use gets its
+// exact ghosts; the other one gets the constant DIRICHLET states the step
+// never rewrites (its copies are refreshed by the post-step kernel).
+cudaError_t ghosts(slbm_s* h, const uint8_t* flag) {
+  for (int b = 0; b < 2; ++b) {
+    const int buf = b == 0 ? h->cur ^ 1 : h->cur;
+    cudaError_t e;
+    if (h->precision == SLBM_FP64)
+      e = launch_ghosts<double, double>(h->pd, (double*)h->pops(buf, 0), (double*)h->pops(buf, 1),
+                                        flag, bc_dev(h), h->st);
+    else
+      e = launch_ghosts<float, float>(h->pf, (float*)h->pops(buf, 0), (float*)h->pops(buf, 1), flag,
+                                      bc_dev(h), h->st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
+// Interface conversion of buffer `buf` plus the boundary cells' ghost images.
 cudaError_t convert(slbm_s* h, int buf, const uint8_t* fold, const uint8_t* fnew) {
+  uint8_t* mask = h->at<uint8_t>(h->lay.tile_mask);
   if (h->precision == SLBM_FP64)
-    return launch_convert<double, double>(h->pd, (double*)h->pops(buf, 0),
-                                          (double*)h->pops(buf, 1), fold, fnew, h->st);
-  return launch_convert<float, float>(h->pf, (float*)h->pops(buf, 0), (float*)h->pops(buf, 1),
-                                      fold, fnew, h->st);
+    return launch_post<double, double>(h->pd, (double*)h->pops(buf, 0), (double*)h->pops(buf, 1),
+                                       fold, fnew, bc_dev(h), 1, mask, h->st);
+  return launch_post<float, float>(h->pf, (float*)h->pops(buf, 0), (float*)h->pops(buf, 1), fold,
+                                   fnew, bc_dev(h), 1, mask, h->st);
+}
+
+// TMA descriptors of every population buffer: a 3-D tensor {pitch, rows, Q}
+// elements per lattice and buffer, box {kTX + 8, kTY + 2G, Q} (the tile, its
+// halo and every plane), no swizzle, zero fill out of bounds.
+int encode_tmaps(slbm_s* h) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return fail(h, SLBM_ECUDA, "cuTensorMapEncodeTiled is not available");
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const int es = elem_size(h->precision);
+  for (int b = 0; b < 2; ++b)
+    for (int k = 0; k < 2; ++k) {
+      const int n = k ? h->nhi : h->nlo;
+      unsigned box[3];
+      stream_box(h->lay.G, n * n, box);
+      const cuuint64_t dims[3] = {(cuuint64_t)h->lay.pitch, (cuuint64_t)h->lay.rows,
+                                  (cuuint64_t)(n * n)};
+      const cuuint64_t strides[2] = {(cuuint64_t)h->lay.pitch * es,
+                                     (cuuint64_t)h->lay.plane * es};
+      const cuuint32_t boxd[3] = {box[0], box[1], box[2]};
+      const cuuint32_t estr[3] = {1, 1, 1};
+      const CUresult r = encode(
+          &h->tmap[b][k],
+          es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+          h->pops(b, k), dims, strides, boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return fail(h, SLBM_ECUDA, "cuTensorMapEncodeTiled failed");
+    }
+  return SLBM_OK;
+}
+
+// The device error word: a bounded wait that ran out makes the handle fail.
+int check_device_error(slbm_s* h) {
+  int v = 0;
+  SLBM_CK(h, cudaMemcpyAsync(&v, h->at<int>(h->lay.err), sizeof(int), cudaMemcpyDeviceToHost,
+                             h->st),
+          "D2H copy");
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  if (v) {
+    h->failed = 1;
+    return fail(h, SLBM_ETIMEOUT, "a bounded device wait ran out (TMA copy did not complete)");
+  }
+  return SLBM_OK;
 }
 
 // Next tracing event (recorded on the handle's stream), or success when off.
@@ -357,26 +422,26 @@ cudaError_t mark(slbm_s* h) {
 }
 
 // One time step: stream-collide (old flags) -> interface conversion (new
-// flags) -> ghost ring.
+// flags) with the boundary cells' ghost images.
 int step_once(slbm_s* h) {
   const int b = h->cur, nb = b ^ 1;
   uint8_t* fold = h->flags(h->fcur);
   uint8_t* fnew = h->crit ? h->flags(h->fcur ^ 1) : fold;
   cudaError_t e;
   SLBM_CK(h, mark(h), "trace event");
+  int* err = h->at<int>(h->lay.err);
+  const uint8_t* mask = h->at<uint8_t>(h->lay.tile_mask);
   if (h->precision == SLBM_FP64)
-    e = launch_stream_collide<double, double>(h->pd, h->P, (const double*)h->pops(b, 0),
-                                              (const double*)h->pops(b, 1), (double*)h->pops(nb, 0),
-                                              (double*)h->pops(nb, 1), fold, fnew, h->st);
+    e = launch_stream_collide<double, double>(h->pd, h->P, &h->tmap[b][0], &h->tmap[b][1],
+                                              (double*)h->pops(nb, 0), (double*)h->pops(nb, 1),
+                                              fold, fnew, mask, err, h->st);
   else
-    e = launch_stream_collide<float, float>(h->pf, h->P, (const float*)h->pops(b, 0),
-                                            (const float*)h->pops(b, 1), (float*)h->pops(nb, 0),
-                                            (float*)h->pops(nb, 1), fold, fnew, h->st);
+    e = launch_stream_collide<float, float>(h->pf, h->P, &h->tmap[b][0], &h->tmap[b][1],
+                                            (float*)h->pops(nb, 0), (float*)h->pops(nb, 1), fold,
+                                            fnew, mask, err, h->st);
   SLBM_CK(h, e, "stream_collide launch");
   SLBM_CK(h, mark(h), "trace event");
-  SLBM_CK(h, convert(h, nb, fold, fnew), "convert launch");
-  SLBM_CK(h, mark(h), "trace event");
-  SLBM_CK(h, ghosts(h, nb, fnew), "ghost launch");
+  SLBM_CK(h, convert(h, nb, fold, fnew), "post-step launch");
   SLBM_CK(h, mark(h), "trace event");
   h->cur = nb;
   if (h->crit) h->fcur ^= 1;
@@ -488,7 +553,8 @@ int init_eq_dev(slbm_s* h) {
                                      r, u,
                               v, h->st);
   SLBM_CK(h, e, "init launch");
-  SLBM_CK(h, ghosts(h, h->cur, h->flags(h->fcur)), "ghost launch");
+  SLBM_CK(h, convert(h, h->cur, h->flags(h->fcur), h->flags(h->fcur)), "post-step launch");
+  SLBM_CK(h, ghosts(h, h->flags(h->fcur)), "ghost launch");
   return SLBM_OK;
 }
 
@@ -563,6 +629,11 @@ int slbm_create_in(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int i
   h->thr = 0.3;
   for (int s = 0; s < 4; ++s) h->bc_kind[s] = SLBM_BC_OUTFLOW;
   refresh_params(h);
+  if (encode_tmaps(h) != SLBM_OK) {
+    snprintf(g_create_err, sizeof(g_create_err), "%s", h->err);
+    delete h;
+    return SLBM_ECUDA;
+  }
   // zero everything (finite stale values), flags 0, then rest state rho = 1, u = 0
   if (cudaMemsetAsync(h->ws, 0, lay.total, h->st) != cudaSuccess) {
     snprintf(g_create_err, sizeof(g_create_err), "workspace clear failed");
@@ -628,7 +699,7 @@ int slbm_get_info(slbm_t h, slbm_info_t* info) {
   info->pitch = h->lay.pitch;
   info->rows = h->lay.rows;
   info->precision = h->precision;
-  info->kernels_per_step = 3;
+  info->kernels_per_step = 2;
   info->workspace_bytes = h->lay.total;
   info->steps = h->steps;
   return SLBM_OK;
@@ -661,7 +732,7 @@ int slbm_set_flags(slbm_t h, const uint8_t* flags) {
   SLBM_CK(h, convert(h, h->cur, h->flags(h->fcur), tmp), "convert launch");
   SLBM_CK(h, cudaMemcpyAsync(h->flags(h->fcur), tmp, norm.size(), cudaMemcpyDeviceToDevice, h->st),
           "flag copy");
-  SLBM_CK(h, ghosts(h, h->cur, h->flags(h->fcur)), "ghost launch");
+  SLBM_CK(h, ghosts(h, h->flags(h->fcur)), "ghost launch");
   // the host vector must stay alive until the copy has consumed it
   SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
   return SLBM_OK;
@@ -699,7 +770,7 @@ int slbm_set_criterion(slbm_t h, int kind, double threshold) {
     SLBM_CK(h, convert(h, h->cur, h->flags(h->fcur), tmp), "convert launch");
     SLBM_CK(h, cudaMemcpyAsync(h->flags(h->fcur), tmp, h->ncell(), cudaMemcpyDeviceToDevice, h->st),
             "flag copy");
-    SLBM_CK(h, ghosts(h, h->cur, h->flags(h->fcur)), "ghost launch");
+    SLBM_CK(h, ghosts(h, h->flags(h->fcur)), "ghost launch");
   }
   return SLBM_OK;
 }
@@ -723,7 +794,7 @@ int slbm_set_boundary(slbm_t h, int side, int kind, const double* rho, const dou
       if (rc) return rc;
     }
   h->bc_kind[side] = kind;
-  SLBM_CK(h, ghosts(h, h->cur, h->flags(h->fcur)), "ghost launch");
+  SLBM_CK(h, ghosts(h, h->flags(h->fcur)), "ghost launch");
   SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
   return SLBM_OK;
 }
@@ -741,7 +812,7 @@ int slbm_step(slbm_t h, int n) {
 int slbm_sync(slbm_t h) {
   SLBM_GUARD(h);
   SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
-  return SLBM_OK;
+  return check_device_error(h);
 }
 
 int slbm_moments_device(slbm_t h, double* rho, double* ux, double* uy, double* T) {
@@ -772,7 +843,7 @@ int slbm_moments(slbm_t h, double* rho, double* ux, double* uy, double* T) {
       SLBM_CK(h, cudaMemcpyAsync(out[m], d[m], h->ncell() * 8, cudaMemcpyDeviceToHost, h->st),
               "D2H copy");
   SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
-  return SLBM_OK;
+  return check_device_error(h);
 }
 
 int slbm_audit(slbm_t h, double out[4]) {
@@ -793,6 +864,7 @@ int slbm_audit(slbm_t h, double out[4]) {
   SLBM_CK(h, e, "audit launch");
   SLBM_CK(h, cudaMemcpyAsync(out, res, 32, cudaMemcpyDeviceToHost, h->st), "D2H copy");
   SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  if (int rc = check_device_error(h)) return rc;
   for (int q = 0; q < 4; ++q)
     if (!std::isfinite(out[q])) return fail(h, SLBM_ENONFINITE, "audit: non-finite sum");
   return SLBM_OK;
@@ -809,7 +881,8 @@ int slbm_set_pops(slbm_t h, int k, const double* in) {
   if ((k != 0 && k != 1) || !in) return fail(h, SLBM_EINVAL, "lattice index or input invalid");
   int rc = pack_any(h, k, nullptr, 1, in);
   if (rc) return rc;
-  SLBM_CK(h, ghosts(h, h->cur, h->flags(h->fcur)), "ghost launch");
+  SLBM_CK(h, convert(h, h->cur, h->flags(h->fcur), h->flags(h->fcur)), "post-step launch");
+  SLBM_CK(h, ghosts(h, h->flags(h->fcur)), "ghost launch");
   return SLBM_OK;
 }
 
@@ -861,7 +934,10 @@ int slbm_set_state(slbm_t h, const void* buf, size_t bytes) {
   const double* pops = (const double*)(p + sizeof(hd) + nc);
   if ((rc = pack_any(h, 0, nullptr, 1, pops))) return rc;
   if ((rc = pack_any(h, 1, nullptr, 1, pops + nc * h->nlo * h->nlo))) return rc;
-  SLBM_CK(h, ghosts(h, h->cur, h->flags(h->fcur)), "ghost launch");
+  // masks from the restored flags; the restored band populations are the
+  // conversions of the restored native ones, so recomputing them is exact
+  SLBM_CK(h, convert(h, h->cur, h->flags(h->fcur), h->flags(h->fcur)), "post-step launch");
+  SLBM_CK(h, ghosts(h, h->flags(h->fcur)), "ghost launch");
   SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
   h->steps = hd.steps;
   return SLBM_OK;

@@ -1,6 +1,5 @@
-// slbm_aux.cu -- interface conversion, ghost / boundary fill, equilibrium
-// initialisation, macroscopic moments, Mach criterion, FP64 audit and host
-// packing kernels.  S = storage type, R = arithmetic type (float for the FP32
+// slbm_aux.cu -- setup ghost / boundary fill, equilibrium initialisation,
+// macroscopic moments, Mach criterion, FP64 audit and host packing kernels.  S = storage type, R = arithmetic type (float for the FP32
 // path: GB300's FP64 rate is a small fraction of its FP32 rate, so doubles
 // appear only in moment sums and the audit).
 #include "../../include/slbm.h"
@@ -28,129 +27,6 @@ __device__ __forceinline__ void store_dev(const LatTab<R>& L, S* f, long long pl
   for (int iy = 0; iy < L.n; ++iy)
     for (int ix = 0; ix < L.n; ++ix)
       f[(size_t)(ix + L.n * iy) * plane + base] = static_cast<S>(s[iy][ix]);
-}
-
-// Density deviation and momentum of a deviation vector, accumulated in FP64.
-template <class R>
-__device__ __forceinline__ void sums64(const LatTab<R>& L, const R (*s)[kMaxN], double& dr,
-                                       double& mx, double& my) {
-  dr = mx = my = 0.0;
-  for (int iy = 0; iy < L.n; ++iy)
-    for (int ix = 0; ix < L.n; ++ix) {
-      const double v = (double)s[iy][ix];
-      dr += v;
-      mx += (double)L.c[ix] * v;
-      my += (double)L.c[iy] * v;
-    }
-}
-
-// Lifting f_q -> f_Q (Sec. III.B): keep the q x q moments, take the rest from
-// the Q-lattice equilibrium at the cell's rho, u.  Tensor form: f_Q = f^L_Q +
-// L (f_q - f^L_q) L^T, where L = VQ^-1[:, :nq] Vq carries the non-equilibrium
-// part with its q x q moments intact and zero higher moments; the W shift
-// cancels, so the same holds for deviations.  Moment sums in FP64.
-template <class R>
-__device__ void lift_vals(const Params<R>& p, const R (*sq)[kMaxN], R (*sQ)[kMaxN]) {
-  const LatTab<R>& Lq = p.lat[0];
-  const LatTab<R>& LQ = p.lat[1];
-  const int nq = Lq.n, nQ = LQ.n;
-  double dr, mx, my;
-  sums64<R>(Lq, sq, dr, mx, my);
-  const double rho = 1.0 + dr;
-  const R ux = (R)(mx / rho), uy = (R)(my / rho);
-  R eq[kMaxN][kMaxN], D[kMaxN][kMaxN], A[kMaxN][kMaxN];
-  eq_dev<R>(Lq, nq, (R)dr, ux, uy, eq);
-  for (int jy = 0; jy < nq; ++jy)
-    for (int jx = 0; jx < nq; ++jx) D[jy][jx] = sq[jy][jx] - eq[jy][jx];
-  eq_dev<R>(LQ, nQ, (R)dr, ux, uy, sQ);
-  for (int ay = 0; ay < nQ; ++ay)          // A[ay][jx] = sum_jy L[ay][jy] D[jy][jx]
-    for (int jx = 0; jx < nq; ++jx) {
-      R t = R(0);
-      for (int jy = 0; jy < nq; ++jy) t += p.conv.lift[ay][jy] * D[jy][jx];
-      A[ay][jx] = t;
-    }
-  for (int ay = 0; ay < nQ; ++ay)
-    for (int ax = 0; ax < nQ; ++ax) {
-      R t = R(0);
-      for (int jx = 0; jx < nq; ++jx) t += p.conv.lift[ax][jx] * A[ay][jx];
-      sQ[ay][ax] += t;
-    }
-}
-
-// Projection f_Q -> f_q (Sec. III.C): keep the first q x q moments; per axis
-// that is Lagrange interpolation of the Q nodes onto the q nodes, f_q = P F_Q
-// P^T with P[j][a] = l^q_j(c^Q_a).  P maps the rest populations W_Q to W_q, so
-// deviations project the same way.
-template <class R>
-__device__ void project_vals(const Params<R>& p, const R (*sQ)[kMaxN], R (*sq)[kMaxN]) {
-  const int nq = p.lat[0].n, nQ = p.lat[1].n;
-  R A[kMaxN][kMaxN];  // A[jy][ax] = sum_ay P[jy][ay] F[ay][ax]
-  for (int jy = 0; jy < nq; ++jy)
-    for (int ax = 0; ax < nQ; ++ax) {
-      R t = R(0);
-      for (int ay = 0; ay < nQ; ++ay) t += p.conv.proj[jy][ay] * sQ[ay][ax];
-      A[jy][ax] = t;
-    }
-  for (int jy = 0; jy < nq; ++jy)
-    for (int jx = 0; jx < nq; ++jx) {
-      R t = R(0);
-      for (int ax = 0; ax < nQ; ++ax) t += p.conv.proj[jx][ax] * A[jy][ax];
-      sq[jy][jx] = t;
-    }
-}
-
-// Interface conversion (step 2 of Sec. III.D, once per node per step).  Every
-// node a cell of the other lattice reads (the band: a cell of the other
-// lattice within the stencil reach) gets its other-lattice populations, and a
-// cell whose flag flipped gets its new lattice.  A flipped node in the band is
-// then read by the other lattice as the conversion of its NEW populations
-// (e.g. lift(project(f)) after a high -> low flip), as the paper's step 2 reads
-// every collocation point in the velocity set it now carries.
-template <class S, class R>
-__global__ void __launch_bounds__(kTX * kTY)
-k_convert(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ flag_old,
-          const uint8_t* __restrict__ flag_new) {
-  const int x = blockIdx.x * kTX + threadIdx.x;
-  const int y = blockIdx.y * kTY + threadIdx.y;
-  if (x >= p.nx || y >= p.ny) return;
-  const int c = x + p.nx * y;
-  const int old = flag_old[c], nw = flag_new[c];
-  bool band = false;
-  for (int dy = -p.band; dy <= p.band && !band; ++dy) {
-    int yy = y + dy;
-    if (yy < 0 || yy >= p.ny) {
-      if (!p.periodic_y) continue;
-      yy = wrap(yy, p.ny);
-    }
-    for (int dx = -p.band; dx <= p.band; ++dx) {
-      int xx = x + dx;
-      if (xx < 0 || xx >= p.nx) {
-        if (!p.periodic_x) continue;
-        xx = wrap(xx, p.nx);
-      }
-      if (flag_new[xx + p.nx * yy] != nw) { band = true; break; }
-    }
-  }
-  if (old == nw && !band) return;
-  const int base = (y + p.G) * p.pitch + (x + kOX);
-  R a[kMaxN][kMaxN], b[kMaxN][kMaxN];
-  if (old == 0) {
-    load_dev<S, R>(p.lat[0], f0, p.plane, base, a);
-    lift_vals<R>(p, a, b);
-    store_dev<S, R>(p.lat[1], f1, p.plane, base, b);
-    if (old != nw && band) {  // now high-order; low-order readers see its projection
-      project_vals<R>(p, b, a);
-      store_dev<S, R>(p.lat[0], f0, p.plane, base, a);
-    }
-  } else {
-    load_dev<S, R>(p.lat[1], f1, p.plane, base, b);
-    project_vals<R>(p, b, a);
-    store_dev<S, R>(p.lat[0], f0, p.plane, base, a);
-    if (old != nw && band) {  // now low-order; high-order readers see its lifting
-      lift_vals<R>(p, a, b);
-      store_dev<S, R>(p.lat[1], f1, p.plane, base, b);
-    }
-  }
 }
 
 // rho of an interior cell from its own lattice (FP64 sum of 1 + deviations).
@@ -201,40 +77,34 @@ __global__ void k_ghosts(const Params<R> p, S* f0, S* f1, const uint8_t* __restr
     gy = (int)(j / G); gx = p.nx + (int)(j % G);
   }
   int sx = gx, sy = gy;
+  if (p.periodic_x) sx = wrap(sx, p.nx);
+  if (p.periodic_y) sy = wrap(sy, p.ny);
   bool eq = false;
   double er = 1.0, eu = 0.0, ev = 0.0;
-  if (sy < 0 || sy >= p.ny) {
-    if (p.periodic_y) {
-      sy = wrap(sy, p.ny);
+  if (sy < 0 || sy >= p.ny) {  // non-periodic y side (wins at corners)
+    const int side = sy < 0 ? SLBM_SIDE_YMIN : SLBM_SIDE_YMAX;
+    const int xi = min(max(sx, 0), p.nx - 1), yi = sy < 0 ? 0 : p.ny - 1;
+    const int kind = bc.kind[side];
+    if (kind == SLBM_BC_OUTFLOW) {
+      sy = yi;
     } else {
-      const int side = sy < 0 ? SLBM_SIDE_YMIN : SLBM_SIDE_YMAX;
-      const int xi = min(max(sx, 0), p.nx - 1), yi = sy < 0 ? 0 : p.ny - 1;
-      const int kind = bc.kind[side];
-      if (kind == SLBM_BC_OUTFLOW) {
-        sy = yi;
-      } else {
-        eq = true;
-        er = kind == SLBM_BC_INLET ? cell_rho<S, R>(p, f0, f1, flag, xi, yi) : bc.rho[side][xi];
-        eu = bc.ux[side][xi];
-        ev = bc.uy[side][xi];
-      }
+      eq = true;
+      er = kind == SLBM_BC_INLET ? cell_rho<S, R>(p, f0, f1, flag, xi, yi) : bc.rho[side][xi];
+      eu = bc.ux[side][xi];
+      ev = bc.uy[side][xi];
     }
   }
-  if (!eq && (sx < 0 || sx >= p.nx)) {
-    if (p.periodic_x) {
-      sx = wrap(sx, p.nx);
+  if (!eq && (sx < 0 || sx >= p.nx)) {  // non-periodic x side
+    const int side = sx < 0 ? SLBM_SIDE_XMIN : SLBM_SIDE_XMAX;
+    const int xi = sx < 0 ? 0 : p.nx - 1;
+    const int kind = bc.kind[side];
+    if (kind == SLBM_BC_OUTFLOW) {
+      sx = xi;
     } else {
-      const int side = sx < 0 ? SLBM_SIDE_XMIN : SLBM_SIDE_XMAX;
-      const int xi = sx < 0 ? 0 : p.nx - 1;
-      const int kind = bc.kind[side];
-      if (kind == SLBM_BC_OUTFLOW) {
-        sx = xi;
-      } else {
-        eq = true;
-        er = kind == SLBM_BC_INLET ? cell_rho<S, R>(p, f0, f1, flag, xi, sy) : bc.rho[side][sy];
-        eu = bc.ux[side][sy];
-        ev = bc.uy[side][sy];
-      }
+      eq = true;
+      er = kind == SLBM_BC_INLET ? cell_rho<S, R>(p, f0, f1, flag, xi, sy) : bc.rho[side][sy];
+      eu = bc.ux[side][sy];
+      ev = bc.uy[side][sy];
     }
   }
   const int gbase = (gy + G) * p.pitch + (gx + kOX);
@@ -243,8 +113,11 @@ __global__ void k_ghosts(const Params<R> p, S* f0, S* f1, const uint8_t* __restr
   } else {
     const int sbase = (sy + G) * p.pitch + (sx + kOX);
     const int q0 = p.lat[0].n * p.lat[0].n, q1 = p.lat[1].n * p.lat[1].n;
-    for (int i = 0; i < q0; ++i) f0[(size_t)i * p.plane + gbase] = f0[(size_t)i * p.plane + sbase];
-    for (int i = 0; i < q1; ++i) f1[(size_t)i * p.plane + gbase] = f1[(size_t)i * p.plane + sbase];
+    S v[kMaxN * kMaxN];  // loads first, then stores (no serialised round trips)
+    for (int i = 0; i < q0; ++i) v[i] = f0[(size_t)i * p.plane + sbase];
+    for (int i = 0; i < q0; ++i) f0[(size_t)i * p.plane + gbase] = v[i];
+    for (int i = 0; i < q1; ++i) v[i] = f1[(size_t)i * p.plane + sbase];
+    for (int i = 0; i < q1; ++i) f1[(size_t)i * p.plane + gbase] = v[i];
   }
 }
 
@@ -391,13 +264,6 @@ int audit_parts(int nx, int ny) {
 }
 
 template <class S, class R>
-cudaError_t launch_convert(const Params<R>& p, S* f0, S* f1, const uint8_t* flag_old,
-                           const uint8_t* flag_new, cudaStream_t st) {
-  k_convert<S, R><<<tile_grid(p), dim3(kTX, kTY), 0, st>>>(p, f0, f1, flag_old, flag_new);
-  return cudaGetLastError();
-}
-
-template <class S, class R>
 cudaError_t launch_ghosts(const Params<R>& p, S* f0, S* f1, const uint8_t* flag, const BcDev& bc,
                           cudaStream_t st) {
   const long long total = 2LL * p.G * (p.nx + 2 * p.G) + 2LL * p.G * p.ny;
@@ -445,8 +311,6 @@ cudaError_t launch_pack(const Params<R>& p, int k, int i0, int cnt, const S* f, 
 }
 
 #define SLBM_AUX_INST(S, R)                                                                  \
-  template cudaError_t launch_convert<S, R>(const Params<R>&, S*, S*, const uint8_t*,        \
-                                            const uint8_t*, cudaStream_t);                   \
   template cudaError_t launch_ghosts<S, R>(const Params<R>&, S*, S*, const uint8_t*,         \
                                            const BcDev&, cudaStream_t);                      \
   template cudaError_t launch_init_eq<S, R>(const Params<R>&, S*, S*, const double*,         \

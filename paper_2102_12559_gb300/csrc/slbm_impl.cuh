@@ -33,12 +33,12 @@ struct LatTab {
   int n;                        // 1-D nodes, Q = n * n
   int off[kMaxN];               // first collocation point of node j, relative to the cell
   int ntap[kMaxN];              // 1 (shift snapped to an integer) or P
-  int kref[kMaxN];              // stencil point with the largest Lagrange weight
   R c[kMaxN];                   // 1-D velocities (T_L = 1, lattice frame)
   R w1[kMaxN];                  // 1-D Gauss-Hermite weights (W_i = w1[ix] w1[iy])
-  // Lagrange weights of node j's departure point in differential form: the
-  // interpolant is v[kref] + sum_a w[a] (v[a] - v[kref]) with w[kref] = 0,
-  // which passes constants through exactly even with rounded weights.
+  // Lagrange weights of node j's departure point in differential form: with
+  // the reference point r = (P - 1) / 2 the interpolant is
+  // v[r] + sum_{a != r} w[a] (v[a] - v[r]) (w[r] stored as 0), which passes
+  // constants through exactly even with rounded weights.
   R w[kMaxN][kMaxP];
   R vinv[kMaxN][kMaxN];         // inverse Vandermonde: phi_j(u) = sum_m vinv[j][m] h_m(u)
 };
@@ -64,7 +64,7 @@ struct Params {
   ConvTab<R> conv;
 };
 
-// Boundary description for the ghost kernel (device arrays, may be null).
+// Boundary description (device arrays of the prescribed states, may be null).
 struct BcDev {
   int kind[4];                  // per side SLBM_BC_*
   const double* rho[4];
@@ -74,15 +74,31 @@ struct BcDev {
 
 // Launchers (defined in the kernel translation units).  S = storage type,
 // R = arithmetic type.  f0 / f1: base of one buffer for lattice 0 / 1.
+// Stream-collide from the buffer described by the tensor maps tm0 / tm1
+// (TMA descriptors of lattice 0 / 1 planes: {pitch, rows, Q} elements) into
+// fout0 / fout1.  `err` receives 1 if a bounded wait ran out.
 template <class S, class R>
-cudaError_t launch_stream_collide(const Params<R>& p, int P, const S* fin0, const S* fin1,
+cudaError_t launch_stream_collide(const Params<R>& p, int P, const void* tm0, const void* tm1,
                                   S* fout0, S* fout1, const uint8_t* flag_cur,
-                                  uint8_t* flag_nxt, cudaStream_t st);
+                                  uint8_t* flag_nxt, const uint8_t* tile_mask, int* err,
+                                  cudaStream_t st);
 
+// Bytes of dynamic shared memory the stream-collide kernel stages per CTA, and
+// the TMA box it loads: {kTX + 8, kTY + 2G, Q}.
+size_t stream_stage_bytes(int elem_size, int nh, int G);
+void stream_box(int G, int Q, unsigned box[3]);
+
+// Post-step: interface conversion for band / flipped cells (flag_old = the
+// lattice each cell was computed in, flag_new = next step's flags), the
+// per-tile lattice mask of flag_new (bit 0: a low-order cell, bit 1: a
+// high-order cell) and, if `images`, the ghost images of boundary cells.
 template <class S, class R>
-cudaError_t launch_convert(const Params<R>& p, S* f0, S* f1, const uint8_t* flag_old,
-                           const uint8_t* flag_new, cudaStream_t st);
+cudaError_t launch_post(const Params<R>& p, S* f0, S* f1, const uint8_t* flag_old,
+                        const uint8_t* flag_new, const BcDev& bc, int images,
+                        uint8_t* tile_mask, cudaStream_t st);
 
+// Full ghost-ring fill of one buffer (setup paths: every ghost, including the
+// constant DIRICHLET states).
 template <class S, class R>
 cudaError_t launch_ghosts(const Params<R>& p, S* f0, S* f1, const uint8_t* flag,
                           const BcDev& bc, cudaStream_t st);

@@ -1,4 +1,4 @@
-// slbm_stream.cuh -- fused stream-collide kernel (sm_103a).
+// slbm_stream.cuh -- fused stream-collide kernel (sm_103a, TMA-staged).
 //
 // One time step of every cell, lattice frame (Sec. II.C "Lattice reference
 // frame" and Sec. III.D):
@@ -8,7 +8,7 @@
 //      c_i dt is a constant, so each population plane is a separable
 //      constant-coefficient stencil; shifts that are integers (the rest node
 //      and the CFL = 1 outer node) are single taps.  Collocation points of the
-//      other lattice were converted beforehand by the interface kernel, so
+//      other lattice were converted beforehand by the post-step kernel, so
 //      every tap reads the target lattice's own planes.
 //   2. rho, rho u (Sec. II.B), the lattice equilibrium in product form
 //      f^L_i = rho phi_ix(u_x) phi_iy(u_y), phi = V^-1 h(u) with the Gaussian
@@ -18,66 +18,121 @@
 //      deviations s_i = f_i - W_i.
 //   3. optionally the Mach criterion of Sec. IV.A for the next step's flag.
 //
-// A CTA owns a 32 x 8 tile, one cell per thread; a warp is one 32-cell row
-// segment.  A warp runs the low-order pass for its low-order lanes, then the
-// high-order pass for its high-order lanes: inside a pass all active lanes
-// execute the same Q-specific code, so no warp diverges on Q; a warp whose
-// lanes are all of one lattice skips the other pass entirely.
+// Work is split into 32 x 8 tiles, one cell per thread; a warp is one 32-cell
+// row segment.  A persistent CTA (two per SM) walks its tiles; for each
+// lattice a tile holds, one elected thread loads every plane of that lattice
+// for the tile and its halo -- a [Q][8 + 2G][40] box -- with a single 3-D TMA
+// copy (cp.async.bulk.tensor) into a shared-memory stage, completion signalled
+// on an mbarrier, while the previous stage computes.  Threads stream from
+// shared memory, where a warp's 32 consecutive taps hit 32 distinct banks.
+// Each (tile, lattice) item runs only that lattice's Q-specific code on the
+// lanes whose cells carry it, so no warp diverges on Q and a tile of one
+// lattice costs one pass.
 #pragma once
+
+#include <cuda.h>
 
 #include "slbm_eq.cuh"
 
 namespace slbm {
 
-template <class S, class R>
-__device__ __forceinline__ R ldg_as(const S* p) { return static_cast<R>(__ldg(p)); }
+constexpr int kXH = 4;                           // halo columns each side (>= G, 16-byte aligned)
+constexpr int kTXP = kTX + 2 * kXH;              // staged row length (40)
+constexpr long long kWaitCycles = 2000000000LL;  // ~1 s bound on an mbarrier wait
+
+// ------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false after ~kWaitCycles without completion.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > kWaitCycles) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, uint64_t* bar,
+                                            int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// ------------------------------------------------------------ the math
 
 // Interpolate along x over one row: node jx's stencil starting at `row`
-// (differential form v[k] + sum_a w[a] (v[a] - v[k]), see LatTab).
+// (differential form v[r] + sum_{a != r} w[a] (v[a] - v[r]), r = (P-1)/2).
 template <int P, class S, class R>
-__device__ __forceinline__ R row_interp(const S* __restrict__ row, const LatTab<R>& L, int jx) {
-  if (L.ntap[jx] == 1) return ldg_as<S, R>(row);
-  R v[P];
+__device__ __forceinline__ R row_interp(const S* row, const LatTab<R>& L, int jx) {
+  constexpr int r = (P - 1) / 2;
+  if (L.ntap[jx] == 1) return static_cast<R>(row[0]);
+  const R vr = static_cast<R>(row[r]);
+  R t = vr;
 #pragma unroll
-  for (int a = 0; a < P; ++a) v[a] = ldg_as<S, R>(row + a);
-  const int k = L.kref[jx];
-  R vk = v[0];
-#pragma unroll
-  for (int a = 1; a < P; ++a) vk = a == k ? v[a] : vk;
-  R t = vk;
-#pragma unroll
-  for (int a = 0; a < P; ++a) t += L.w[jx][a] * (v[a] - vk);
+  for (int a = 0; a < P; ++a)
+    if (a != r) t += L.w[jx][a] * (static_cast<R>(row[a]) - vr);
   return t;
 }
 
-// Stream + collide one cell of lattice L (N nodes per axis), on deviations
+// Stream + collide one cell of lattice L (N nodes per axis) from the staged
+// planes (cell at `src`, planes `pl` apart, rows `pitch` apart), on deviations
 // s_i = f_i - W_i (streaming is affine in the shift; the collision uses the
 // deviation form of the product equilibrium, see slbm_eq.cuh).
 template <int N, int P, class S, class R>
 __device__ __forceinline__ void stream_collide_cell(const Params<R>& p, const LatTab<R>& L,
-                                                    const S* __restrict__ fin,
-                                                    S* __restrict__ fout, int base, R& ux,
+                                                    const S* src, int pl, int pitch,
+                                                    S* __restrict__ fout, int obase, R& ux,
                                                     R& uy) {
   R f[N * N];
 #pragma unroll
   for (int jy = 0; jy < N; ++jy) {
 #pragma unroll
     for (int jx = 0; jx < N; ++jx) {
-      const S* pl = fin + (size_t)(jx + N * jy) * p.plane + base + L.off[jx];
+      const S* q = src + (jx + N * jy) * pl + L.off[jx];
       R acc;
       if (L.ntap[jy] == 1) {
-        acc = row_interp<P, S, R>(pl + L.off[jy] * p.pitch, L, jx);
+        acc = row_interp<P, S, R>(q + L.off[jy] * pitch, L, jx);
       } else {
+        constexpr int rr = (P - 1) / 2;
         R r[P];
 #pragma unroll
-        for (int b = 0; b < P; ++b) r[b] = row_interp<P, S, R>(pl + (L.off[jy] + b) * p.pitch, L, jx);
-        const int k = L.kref[jy];
-        R rk = r[0];
+        for (int b = 0; b < P; ++b) r[b] = row_interp<P, S, R>(q + (L.off[jy] + b) * pitch, L, jx);
+        acc = r[rr];
 #pragma unroll
-        for (int b = 1; b < P; ++b) rk = b == k ? r[b] : rk;
-        acc = rk;
-#pragma unroll
-        for (int b = 0; b < P; ++b) acc += L.w[jy][b] * (r[b] - rk);
+        for (int b = 0; b < P; ++b)
+          if (b != rr) acc += L.w[jy][b] * (r[b] - r[rr]);
       }
       f[jx + N * jy] = acc;
     }
@@ -113,41 +168,133 @@ __device__ __forceinline__ void stream_collide_cell(const Params<R>& p, const La
       const int i = jx + N * jy;
       const R px = L.w1[jx] + dx[jx];
       const R feq = dr * px * py + L.w1[jx] * dy[jy] + dx[jx] * L.w1[jy] + dx[jx] * dy[jy];
-      fout[(size_t)i * p.plane + base] = static_cast<S>(f[i] + p.omega * (feq - f[i]));
+      fout[(size_t)i * p.plane + obase] = static_cast<S>(f[i] + p.omega * (feq - f[i]));
     }
   }
 }
 
+constexpr int kStages = 2;  // staged work items in flight per CTA
+
+// Work item of a persistent CTA: tile t (this CTA owns t = blockIdx.x,
+// blockIdx.x + gridDim.x, ...) and lattice k, for every lattice the tile's
+// mask holds (bit 0 low-order, bit 1 high-order).
+struct Item {
+  int t, k;
+};
+
+__device__ __forceinline__ Item first_item(const uint8_t* mask, int ntiles) {
+  Item it{(int)blockIdx.x, 0};
+  if (it.t < ntiles && !(mask[it.t] & 1)) it.k = 1;
+  return it;
+}
+
+__device__ __forceinline__ Item next_item(Item it, const uint8_t* mask, int ntiles) {
+  if (it.k == 0 && (mask[it.t] & 2)) return Item{it.t, 1};
+  it.t += gridDim.x;
+  it.k = (it.t < ntiles && !(mask[it.t] & 1)) ? 1 : 0;
+  return it;
+}
+
+// Persistent stream-collide: each CTA walks its items through a kStages-deep
+// ring of staged buffers.  One elected thread keeps kStages TMA copies in
+// flight (the next items' planes load while the current item computes); all
+// threads compute the cells of the item's lattice, then free the stage.
 template <int NL, int NH, int P, class S, class R>
-__global__ void __launch_bounds__(kTX * kTY)
-k_stream_collide(const Params<R> p, const S* __restrict__ fin0, const S* __restrict__ fin1,
-                 S* __restrict__ fout0, S* __restrict__ fout1,
-                 const uint8_t* __restrict__ flag_cur, uint8_t* __restrict__ flag_nxt) {
-  const int x = blockIdx.x * kTX + threadIdx.x;
-  const int y = blockIdx.y * kTY + threadIdx.y;
-  if (x >= p.nx || y >= p.ny) return;
-  const int cell = x + p.nx * y;
-  const int fl = flag_cur[cell];
-  const int base = (y + p.G) * p.pitch + (x + kOX);
-  R ux = R(0), uy = R(0);
-  if (fl == 0)
-    stream_collide_cell<NL, P, S, R>(p, p.lat[0], fin0, fout0, base, ux, uy);
-  else
-    stream_collide_cell<NH, P, S, R>(p, p.lat[1], fin1, fout1, base, ux, uy);
-  if (p.crit == 1) flag_nxt[cell] = sqrt(ux * ux + uy * uy) > p.thr ? 1 : 0;
+__global__ void __launch_bounds__(kTX * kTY, 2)
+k_stream_collide(const Params<R> p, const __grid_constant__ CUtensorMap tm0,
+                 const __grid_constant__ CUtensorMap tm1, S* __restrict__ fout0,
+                 S* __restrict__ fout1, const uint8_t* __restrict__ flag_cur,
+                 uint8_t* __restrict__ flag_nxt, const uint8_t* __restrict__ tile_mask,
+                 int ntx, int ntiles, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[kStages];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
+  const int rows = kTY + 2 * p.G;  // staged rows: cells y0 - G .. y0 + kTY + G - 1
+  const int pl = rows * kTXP;      // staged elements per plane
+  const int stage = NH * NH * pl;  // staged elements per stage (room for the larger lattice)
+  S* sm = reinterpret_cast<S*>(smem_raw);
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  Item pc = first_item(tile_mask, ntiles);  // producer cursor (thread 0 only)
+  if (tid == 0)
+    for (int s = 0; s < kStages && pc.t < ntiles; ++s) {
+      const int Q = pc.k ? NH * NH : NL * NL;
+      mbar_expect_tx(&full[s], (uint32_t)(Q * pl * (int)sizeof(S)));
+      tma_load_3d(sm + s * stage, pc.k ? &tm1 : &tm0, &full[s], (pc.t % ntx) * kTX + kOX - kXH,
+                  (pc.t / ntx) * kTY, 0);
+      pc = next_item(pc, tile_mask, ntiles);
+    }
+  int j = 0;
+  for (Item it = first_item(tile_mask, ntiles); it.t < ntiles;
+       it = next_item(it, tile_mask, ntiles), ++j) {
+    const int s = j % kStages;
+    const int x0 = (it.t % ntx) * kTX, y0 = (it.t / ntx) * kTY;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool in = x < p.nx && y < p.ny;
+    const int fl = in ? flag_cur[x + p.nx * y] : 2;  // issued before the wait
+    if (!mbar_wait(&full[s], (uint32_t)((j / kStages) & 1))) {
+      // bounded: record, give the copy one more bounded wait, stop
+      if (tid == 0) atomicExch(err, 1);
+      mbar_wait(&full[s], (uint32_t)((j / kStages) & 1));
+      return;
+    }
+    if (fl == it.k) {
+      const S* cell = sm + s * stage + (ty + p.G) * kTXP + (tx + kXH);
+      const int obase = (y + p.G) * p.pitch + (x + kOX);
+      R ux, uy;
+      if (it.k == 0)
+        stream_collide_cell<NL, P, S, R>(p, p.lat[0], cell, pl, kTXP, fout0, obase, ux, uy);
+      else
+        stream_collide_cell<NH, P, S, R>(p, p.lat[1], cell, pl, kTXP, fout1, obase, ux, uy);
+      if (p.crit == 1) flag_nxt[x + p.nx * y] = sqrt(ux * ux + uy * uy) > p.thr ? 1 : 0;
+    }
+    __syncthreads();  // stage s is free again
+    if (tid == 0 && pc.t < ntiles) {
+      // order the CTA's shared-memory reads of stage s before the async-proxy write
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      const int Q = pc.k ? NH * NH : NL * NL;
+      mbar_expect_tx(&full[s], (uint32_t)(Q * pl * (int)sizeof(S)));
+      tma_load_3d(sm + s * stage, pc.k ? &tm1 : &tm0, &full[s], (pc.t % ntx) * kTX + kOX - kXH,
+                  (pc.t / ntx) * kTY, 0);
+      pc = next_item(pc, tile_mask, ntiles);
+    }
+  }
 }
 
 template <class S, class R>
-cudaError_t launch_stream_collide_impl(const Params<R>& p, int P, const S* fin0, const S* fin1,
-                                       S* fout0, S* fout1, const uint8_t* flag_cur,
-                                       uint8_t* flag_nxt, cudaStream_t st) {
+cudaError_t launch_stream_collide_impl(const Params<R>& p, int P, const CUtensorMap* tm0,
+                                       const CUtensorMap* tm1, S* fout0, S* fout1,
+                                       const uint8_t* flag_cur, uint8_t* flag_nxt,
+                                       const uint8_t* tile_mask, int* err, cudaStream_t st) {
   const dim3 blk(kTX, kTY);
-  const dim3 grd((p.nx + kTX - 1) / kTX, (p.ny + kTY - 1) / kTY);
+  const int ntx = (p.nx + kTX - 1) / kTX, nty = (p.ny + kTY - 1) / kTY;
+  const int ntiles = ntx * nty;
   const int nl = p.lat[0].n, nh = p.lat[1].n;
+  const size_t smem = (size_t)kStages * nh * nh * (kTY + 2 * p.G) * kTXP * sizeof(S);
+  int dev = 0, nsm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
 #define SLBM_SC_CASE(NL, NH, PP)                                                            \
   if (nl == NL && nh == NH && P == PP) {                                                    \
-    k_stream_collide<NL, NH, PP, S, R>                                                      \
-        <<<grd, blk, 0, st>>>(p, fin0, fin1, fout0, fout1, flag_cur, flag_nxt);             \
+    auto kern = k_stream_collide<NL, NH, PP, S, R>;                                         \
+    static size_t attr_set = 0; /* largest dynamic size granted so far */                   \
+    if (smem > attr_set) {                                                                  \
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                           (int)smem);                                      \
+      if (e != cudaSuccess) return e;                                                       \
+      attr_set = smem;                                                                      \
+    }                                                                                       \
+    int per_sm = 0;                                                                         \
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern,            \
+                                                                  kTX * kTY, smem);         \
+    if (e != cudaSuccess) return e;                                                         \
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;                                   \
+    const int grid = ntiles < per_sm * nsm ? ntiles : per_sm * nsm;                         \
+    kern<<<grid, blk, smem, st>>>(p, *tm0, *tm1, fout0, fout1, flag_cur, flag_nxt,          \
+                                  tile_mask, ntx, ntiles, err);                             \
     return cudaGetLastError();                                                              \
   }
 #define SLBM_SC_PAIR(NL, NH) \

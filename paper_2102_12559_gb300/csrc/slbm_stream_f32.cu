@@ -3,11 +3,22 @@
 
 namespace slbm {
 template <>
-cudaError_t launch_stream_collide<float, float>(const Params<float>& p, int P, const float* fin0,
-                                                const float* fin1, float* fout0, float* fout1,
-                                                const uint8_t* flag_cur, uint8_t* flag_nxt,
-                                                cudaStream_t st) {
-  return launch_stream_collide_impl<float, float>(p, P, fin0, fin1, fout0, fout1, flag_cur,
-                                                  flag_nxt, st);
+cudaError_t launch_stream_collide<float, float>(const Params<float>& p, int P, const void* tm0,
+                                          const void* tm1, float* fout0, float* fout1,
+                                          const uint8_t* flag_cur, uint8_t* flag_nxt,
+                                          const uint8_t* tile_mask, int* err, cudaStream_t st) {
+  return launch_stream_collide_impl<float, float>(p, P, static_cast<const CUtensorMap*>(tm0),
+                                            static_cast<const CUtensorMap*>(tm1), fout0, fout1,
+                                            flag_cur, flag_nxt, tile_mask, err, st);
+}
+
+size_t stream_stage_bytes(int elem_size, int nh, int G) {
+  return (size_t)nh * nh * (kTY + 2 * G) * kTXP * elem_size;
+}
+
+void stream_box(int G, int Q, unsigned box[3]) {
+  box[0] = kTXP;
+  box[1] = kTY + 2 * G;
+  box[2] = Q;
 }
 }  // namespace slbm
