@@ -179,7 +179,7 @@ struct Layout {
   int G, pitch, rows;
   long long plane;           // elements per plane, padded
   size_t pops[2][2];         // byte offsets [buffer][lattice]
-  size_t flags[2], flag_tmp, tile_mask, macro[4], partials, audit_out, err, bc[4][3];
+  size_t flags[2], flag_tmp, tile_mask[2], macro[4], partials, audit_out, err, bc[4][3];
   size_t total;
 };
 
@@ -240,7 +240,7 @@ Layout make_layout(const slbm_grid* g, int lo, int hi, int order, int precision)
   for (int f = 0; f < 2; ++f) { Lo.flags[f] = off; off = align_up(off + nc, 256); }
   Lo.flag_tmp = off; off = align_up(off + nc, 256);
   const size_t ntiles = (size_t)((g->nx + kTX - 1) / kTX) * ((g->ny + kTY - 1) / kTY);
-  Lo.tile_mask = off; off = align_up(off + ntiles, 256);
+  for (int m = 0; m < 2; ++m) { Lo.tile_mask[m] = off; off = align_up(off + ntiles, 256); }
   for (int m = 0; m < 4; ++m) { Lo.macro[m] = off; off = align_up(off + nc * 8, 256); }
   Lo.partials = off; off = align_up(off + 4 * 1024 * 8, 256);
   Lo.audit_out = off; off = align_up(off + 4 * 8, 256);
@@ -267,6 +267,7 @@ struct slbm_s {
   bool owns_ws;
   int dev;                       // CUDA device of the workspace
   int cur, fcur;                 // population buffer and flag buffer in use
+  int mcur;                      // tile-mask buffer the next stream launch reads
   int crit;
   double thr;
   int bc_kind[4];
@@ -349,13 +350,15 @@ cudaError_t ghosts(slbm_s* h, const uint8_t* flag) {
 }
 
 // Interface conversion of buffer `buf` plus the boundary cells' ghost images.
-cudaError_t convert(slbm_s* h, int buf, const uint8_t* fold, const uint8_t* fnew) {
-  uint8_t* mask = h->at<uint8_t>(h->lay.tile_mask);
+// Setup calls (mask_in null) also write the tile masks the next step reads.
+cudaError_t convert(slbm_s* h, int buf, const uint8_t* fold, const uint8_t* fnew,
+                    const uint8_t* mask_in = nullptr) {
+  uint8_t* mask = h->at<uint8_t>(h->lay.tile_mask[h->mcur]);
   if (h->precision == SLBM_FP64)
     return launch_post<double, double>(h->pd, (double*)h->pops(buf, 0), (double*)h->pops(buf, 1),
-                                       fold, fnew, bc_dev(h), 1, mask, h->st);
+                                       fold, fnew, bc_dev(h), 1, mask_in, mask, h->st);
   return launch_post<float, float>(h->pf, (float*)h->pops(buf, 0), (float*)h->pops(buf, 1), fold,
-                                   fnew, bc_dev(h), 1, mask, h->st);
+                                   fnew, bc_dev(h), 1, mask_in, mask, h->st);
 }
 
 // TMA descriptors of every population buffer: a 3-D tensor {pitch, rows, Q}
@@ -430,20 +433,22 @@ int step_once(slbm_s* h) {
   cudaError_t e;
   SLBM_CK(h, mark(h), "trace event");
   int* err = h->at<int>(h->lay.err);
-  const uint8_t* mask = h->at<uint8_t>(h->lay.tile_mask);
+  const uint8_t* mask = h->at<uint8_t>(h->lay.tile_mask[h->mcur]);
+  uint8_t* mask_next = h->at<uint8_t>(h->lay.tile_mask[h->mcur ^ 1]);
   if (h->precision == SLBM_FP64)
     e = launch_stream_collide<double, double>(h->pd, h->P, &h->tmap[b][0], &h->tmap[b][1],
                                               (double*)h->pops(nb, 0), (double*)h->pops(nb, 1),
-                                              fold, fnew, mask, err, h->st);
+                                              fold, fnew, mask, mask_next, bc_dev(h), err, h->st);
   else
     e = launch_stream_collide<float, float>(h->pf, h->P, &h->tmap[b][0], &h->tmap[b][1],
                                             (float*)h->pops(nb, 0), (float*)h->pops(nb, 1), fold,
-                                            fnew, mask, err, h->st);
+                                            fnew, mask, mask_next, bc_dev(h), err, h->st);
   SLBM_CK(h, e, "stream_collide launch");
   SLBM_CK(h, mark(h), "trace event");
-  SLBM_CK(h, convert(h, nb, fold, fnew), "post-step launch");
+  SLBM_CK(h, convert(h, nb, fold, fnew, mask_next), "post-step launch");
   SLBM_CK(h, mark(h), "trace event");
   h->cur = nb;
+  h->mcur ^= 1;
   if (h->crit) h->fcur ^= 1;
   h->steps++;
   return SLBM_OK;
@@ -571,6 +576,26 @@ bool create_args_ok(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int 
     return false;
   }
   const Layout lay = make_layout(g, lat_lo, lat_hi, interp_order, precision);
+  {  // the kernels take the single-tap pattern and the halo as compile-time facts
+    const Lattice1D a = make_1d(lat_lo), b = make_1d(lat_hi);
+    const double dt = pair_dt(a, b);
+    const int P = interp_order + 1;
+    bool ok = lay.G == stage_halo(P);
+    for (int k = 0; k < 2 && ok; ++k) {
+      const Lattice1D& L = k ? b : a;
+      for (int j = 0; j < L.n; ++j) {
+        int off, nt;
+        double w[kMaxP];
+        node_stencil(L.c[j] * dt, P, &off, &nt, w);
+        const bool snap = node_snapped(L.n, k == 1, j);
+        if ((nt == 1) != snap || (snap && off != snapped_offset(L.n, j))) ok = false;
+      }
+    }
+    if (!ok) {
+      snprintf(g_create_err, sizeof(g_create_err), "unsupported stencil pattern for this pair");
+      return false;
+    }
+  }
   if (g->nx < 2 * lay.G + 1 || g->ny < 2 * lay.G + 1) {
     snprintf(g_create_err, sizeof(g_create_err), "grid must be at least %d cells per side",
              2 * lay.G + 1);

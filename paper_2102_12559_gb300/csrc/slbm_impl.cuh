@@ -27,6 +27,20 @@ constexpr int kOX = 8;          // left pad of a row, elements (keeps 16-byte ro
 constexpr int kTX = 32;         // tile width  (one warp per row segment)
 constexpr int kTY = 8;          // tile height (8 warps per CTA)
 
+// Stencil shape known at compile time.  With CFL = 1 (Sec. IV) a node's
+// shift c_j dt is an exact integer only for the rest node (0) and, on the
+// lattice that sets max|c| (the high-order one), the two outer nodes (-+1);
+// those are single taps at a fixed offset.  The host checks its tables
+// against this at creation.
+__host__ __device__ constexpr bool node_snapped(int n, bool hi, int j) {
+  return (n % 2 == 1 && j == n / 2) || (hi && (j == 0 || j == n - 1));
+}
+__host__ __device__ constexpr int snapped_offset(int n, int j) {
+  return j == 0 ? 1 : (j == n - 1 ? -1 : 0);  // departure point x - c dt
+}
+// Ghost / staging halo of a P-point stencil with shifts of at most one cell.
+__host__ __device__ constexpr int stage_halo(int P) { return (P + 1) / 2; }
+
 // One lattice of the pair, in the arithmetic type R.
 template <class R>
 struct LatTab {
@@ -80,7 +94,8 @@ struct BcDev {
 template <class S, class R>
 cudaError_t launch_stream_collide(const Params<R>& p, int P, const void* tm0, const void* tm1,
                                   S* fout0, S* fout1, const uint8_t* flag_cur,
-                                  uint8_t* flag_nxt, const uint8_t* tile_mask, int* err,
+                                  uint8_t* flag_nxt, const uint8_t* tile_mask,
+                                  uint8_t* mask_next, const BcDev& bc, int* err,
                                   cudaStream_t st);
 
 // Bytes of dynamic shared memory the stream-collide kernel stages per CTA, and
@@ -89,13 +104,16 @@ size_t stream_stage_bytes(int elem_size, int nh, int G);
 void stream_box(int G, int Q, unsigned box[3]);
 
 // Post-step: interface conversion for band / flipped cells (flag_old = the
-// lattice each cell was computed in, flag_new = next step's flags), the
-// per-tile lattice mask of flag_new (bit 0: a low-order cell, bit 1: a
-// high-order cell) and, if `images`, the ghost images of boundary cells.
+// lattice each cell was computed in, flag_new = next step's flags) and, if
+// `images`, the ghost images of boundary cells.  Tile masks (bit 0: a
+// low-order cell, bit 1: a high-order cell, bit 2: a flip): after a step,
+// mask_in holds the stream kernel's masks of flag_new and quiet tiles are
+// skipped; in setup calls mask_in is null and the masks of flag_new are
+// written to tile_mask.
 template <class S, class R>
 cudaError_t launch_post(const Params<R>& p, S* f0, S* f1, const uint8_t* flag_old,
                         const uint8_t* flag_new, const BcDev& bc, int images,
-                        uint8_t* tile_mask, cudaStream_t st);
+                        const uint8_t* mask_in, uint8_t* tile_mask, cudaStream_t st);
 
 // Full ghost-ring fill of one buffer (setup paths: every ghost, including the
 // constant DIRICHLET states).

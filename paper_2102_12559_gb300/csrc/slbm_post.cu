@@ -5,15 +5,19 @@ namespace slbm {
 template <>
 cudaError_t launch_post<float, float>(const Params<float>& p, float* f0, float* f1,
                                       const uint8_t* flag_old, const uint8_t* flag_new,
-                                      const BcDev& bc, int images, uint8_t* tile_mask,
+                                      const BcDev& bc, int images, const uint8_t* mask_in,
+                                      uint8_t* tile_mask,
                                       cudaStream_t st) {
-  return launch_post_impl<float, float>(p, f0, f1, flag_old, flag_new, bc, images, tile_mask, st);
+  return launch_post_impl<float, float>(p, f0, f1, flag_old, flag_new, bc, images, mask_in, tile_mask,
+                                         st);
 }
 template <>
 cudaError_t launch_post<double, double>(const Params<double>& p, double* f0, double* f1,
                                         const uint8_t* flag_old, const uint8_t* flag_new,
-                                        const BcDev& bc, int images, uint8_t* tile_mask,
+                                        const BcDev& bc, int images, const uint8_t* mask_in,
+                                      uint8_t* tile_mask,
                                       cudaStream_t st) {
-  return launch_post_impl<double, double>(p, f0, f1, flag_old, flag_new, bc, images, tile_mask, st);
+  return launch_post_impl<double, double>(p, f0, f1, flag_old, flag_new, bc, images, mask_in, tile_mask,
+                                         st);
 }
 }  // namespace slbm

@@ -32,7 +32,7 @@
 
 #include <cuda.h>
 
-#include "slbm_eq.cuh"
+#include "slbm_ghost.cuh"
 
 namespace slbm {
 
@@ -92,12 +92,11 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, ui
 
 // ------------------------------------------------------------ the math
 
-// Interpolate along x over one row: node jx's stencil starting at `row`
-// (differential form v[r] + sum_{a != r} w[a] (v[a] - v[r]), r = (P-1)/2).
-template <int P, class S, class R>
+// One row of node jx's stencil (differential form v[r] + sum_{a != r}
+// w[a] (v[a] - v[r]), r = (P-1)/2, see LatTab).
+template <int N, bool HI, int P, class S, class R>
 __device__ __forceinline__ R row_interp(const S* row, const LatTab<R>& L, int jx) {
   constexpr int r = (P - 1) / 2;
-  if (L.ntap[jx] == 1) return static_cast<R>(row[0]);
   const R vr = static_cast<R>(row[r]);
   R t = vr;
 #pragma unroll
@@ -106,33 +105,41 @@ __device__ __forceinline__ R row_interp(const S* row, const LatTab<R>& L, int jx
   return t;
 }
 
-// Stream + collide one cell of lattice L (N nodes per axis) from the staged
-// planes (cell at `src`, planes `pl` apart, rows `pitch` apart), on deviations
-// s_i = f_i - W_i (streaming is affine in the shift; the collision uses the
-// deviation form of the product equilibrium, see slbm_eq.cuh).
-template <int N, int P, class S, class R>
+// Stream + collide one cell of lattice L (N nodes per axis, HI = the
+// high-order lattice) from the staged planes (cell at `src`, planes PL
+// elements apart, rows kTXP apart), on deviations s_i = f_i - W_i (streaming
+// is affine in the shift; the collision uses the deviation form of the
+// product equilibrium, see slbm_eq.cuh).
+template <int N, bool HI, int P, class S, class R>
 __device__ __forceinline__ void stream_collide_cell(const Params<R>& p, const LatTab<R>& L,
-                                                    const S* src, int pl, int pitch,
-                                                    S* __restrict__ fout, int obase, R& ux,
-                                                    R& uy) {
+                                                    const S* src, S* __restrict__ fout,
+                                                    int obase, R& ux, R& uy, R& drho) {
+  constexpr int PL = (kTY + 2 * stage_halo(P)) * kTXP;
   R f[N * N];
 #pragma unroll
   for (int jy = 0; jy < N; ++jy) {
 #pragma unroll
     for (int jx = 0; jx < N; ++jx) {
-      const S* q = src + (jx + N * jy) * pl + L.off[jx];
+      const S* q = src + (jx + N * jy) * PL;
+      constexpr int dummy = 0;
+      (void)dummy;
+      const int ox = node_snapped(N, HI, jx) ? snapped_offset(N, jx) : L.off[jx];
+      const int oy = node_snapped(N, HI, jy) ? snapped_offset(N, jy) : L.off[jy];
+      q += ox + oy * kTXP;
       R acc;
-      if (L.ntap[jy] == 1) {
-        acc = row_interp<P, S, R>(q + L.off[jy] * pitch, L, jx);
+      if (node_snapped(N, HI, jy)) {
+        acc = node_snapped(N, HI, jx) ? static_cast<R>(q[0]) : row_interp<N, HI, P, S, R>(q, L, jx);
       } else {
         constexpr int rr = (P - 1) / 2;
-        R r[P];
-#pragma unroll
-        for (int b = 0; b < P; ++b) r[b] = row_interp<P, S, R>(q + (L.off[jy] + b) * pitch, L, jx);
-        acc = r[rr];
+        R rv[P];
 #pragma unroll
         for (int b = 0; b < P; ++b)
-          if (b != rr) acc += L.w[jy][b] * (r[b] - r[rr]);
+          rv[b] = node_snapped(N, HI, jx) ? static_cast<R>(q[b * kTXP])
+                                          : row_interp<N, HI, P, S, R>(q + b * kTXP, L, jx);
+        acc = rv[rr];
+#pragma unroll
+        for (int b = 0; b < P; ++b)
+          if (b != rr) acc += L.w[jy][b] * (rv[b] - rv[rr]);
       }
       f[jx + N * jy] = acc;
     }
@@ -157,6 +164,7 @@ __device__ __forceinline__ void stream_collide_cell(const Params<R>& p, const La
   const R inv = R(1) / (R(1) + dr);
   ux = mx * inv;
   uy = my * inv;
+  drho = dr;
   R dx[N], dy[N];
   dphi<R>(L, N, ux, dx);
   dphi<R>(L, N, uy, dy);
@@ -173,7 +181,8 @@ __device__ __forceinline__ void stream_collide_cell(const Params<R>& p, const La
   }
 }
 
-constexpr int kStages = 2;  // staged work items in flight per CTA
+constexpr int kStages = 2;            // staged work items in flight per CTA
+constexpr int kMaxTilesPerCta = 4096;  // tile masks a persistent CTA keeps in shared memory
 
 // Work item of a persistent CTA: tile t (this CTA owns t = blockIdx.x,
 // blockIdx.x + gridDim.x, ...) and lattice k, for every lattice the tile's
@@ -182,16 +191,21 @@ struct Item {
   int t, k;
 };
 
+// `mask` holds the masks of this CTA's tiles by local index (t - blockIdx.x) / gridDim.x.
+__device__ __forceinline__ int local_mask(const uint8_t* mask, int t) {
+  return mask[(t - (int)blockIdx.x) / (int)gridDim.x];
+}
+
 __device__ __forceinline__ Item first_item(const uint8_t* mask, int ntiles) {
   Item it{(int)blockIdx.x, 0};
-  if (it.t < ntiles && !(mask[it.t] & 1)) it.k = 1;
+  if (it.t < ntiles && !(local_mask(mask, it.t) & 1)) it.k = 1;
   return it;
 }
 
 __device__ __forceinline__ Item next_item(Item it, const uint8_t* mask, int ntiles) {
-  if (it.k == 0 && (mask[it.t] & 2)) return Item{it.t, 1};
+  if (it.k == 0 && (local_mask(mask, it.t) & 2)) return Item{it.t, 1};
   it.t += gridDim.x;
-  it.k = (it.t < ntiles && !(mask[it.t] & 1)) ? 1 : 0;
+  it.k = (it.t < ntiles && !(local_mask(mask, it.t) & 1)) ? 1 : 0;
   return it;
 }
 
@@ -204,30 +218,37 @@ __global__ void __launch_bounds__(kTX * kTY, 2)
 k_stream_collide(const Params<R> p, const __grid_constant__ CUtensorMap tm0,
                  const __grid_constant__ CUtensorMap tm1, S* __restrict__ fout0,
                  S* __restrict__ fout1, const uint8_t* __restrict__ flag_cur,
-                 uint8_t* __restrict__ flag_nxt, const uint8_t* __restrict__ tile_mask,
-                 int ntx, int ntiles, int* __restrict__ err) {
+                 uint8_t* __restrict__ flag_nxt, const uint8_t* __restrict__ tile_mask_g,
+                 uint8_t* __restrict__ mask_next, int ntx, int ntiles, const BcDev bc,
+                 int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ uint8_t tmask[kMaxTilesPerCta];  // masks of this CTA's tiles, by local index
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
-  const int rows = kTY + 2 * p.G;  // staged rows: cells y0 - G .. y0 + kTY + G - 1
-  const int pl = rows * kTXP;      // staged elements per plane
-  const int stage = NH * NH * pl;  // staged elements per stage (room for the larger lattice)
+  for (int m = tid; blockIdx.x + m * gridDim.x < ntiles; m += kTX * kTY)
+    tmask[m] = tile_mask_g[blockIdx.x + m * gridDim.x];
+  constexpr int GH = stage_halo(P);
+  constexpr int pl = (kTY + 2 * GH) * kTXP;  // staged elements per plane (rows y0-GH ..)
+  constexpr int stage = NH * NH * pl;        // staged elements per stage (larger lattice)
   S* sm = reinterpret_cast<S*>(smem_raw);
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
     mbar_fence_init();
   }
   __syncthreads();
+  const uint8_t* tile_mask = tmask;
   Item pc = first_item(tile_mask, ntiles);  // producer cursor (thread 0 only)
   if (tid == 0)
     for (int s = 0; s < kStages && pc.t < ntiles; ++s) {
       const int Q = pc.k ? NH * NH : NL * NL;
       mbar_expect_tx(&full[s], (uint32_t)(Q * pl * (int)sizeof(S)));
       tma_load_3d(sm + s * stage, pc.k ? &tm1 : &tm0, &full[s], (pc.t % ntx) * kTX + kOX - kXH,
-                  (pc.t / ntx) * kTY, 0);
+                  (pc.t / ntx) * kTY + p.G - GH, 0);
       pc = next_item(pc, tile_mask, ntiles);
     }
   int j = 0;
+  int nf = -1;        // this thread's cell: next-step flag (-1 = not computed yet)
+  bool flip = false;  // ... and whether it differs from this step's flag
   for (Item it = first_item(tile_mask, ntiles); it.t < ntiles;
        it = next_item(it, tile_mask, ntiles), ++j) {
     const int s = j % kStages;
@@ -235,6 +256,7 @@ k_stream_collide(const Params<R> p, const __grid_constant__ CUtensorMap tm0,
     const int x = x0 + tx, y = y0 + ty;
     const bool in = x < p.nx && y < p.ny;
     const int fl = in ? flag_cur[x + p.nx * y] : 2;  // issued before the wait
+    if (it.k == 0 || !(local_mask(tile_mask, it.t) & 1)) nf = -1;  // first item of a tile
     if (!mbar_wait(&full[s], (uint32_t)((j / kStages) & 1))) {
       // bounded: record, give the copy one more bounded wait, stop
       if (tid == 0) atomicExch(err, 1);
@@ -242,14 +264,31 @@ k_stream_collide(const Params<R> p, const __grid_constant__ CUtensorMap tm0,
       return;
     }
     if (fl == it.k) {
-      const S* cell = sm + s * stage + (ty + p.G) * kTXP + (tx + kXH);
+      const S* cell = sm + s * stage + (ty + GH) * kTXP + (tx + kXH);
       const int obase = (y + p.G) * p.pitch + (x + kOX);
-      R ux, uy;
+      R ux, uy, dr;  // dr: density deviation (unused here)
       if (it.k == 0)
-        stream_collide_cell<NL, P, S, R>(p, p.lat[0], cell, pl, kTXP, fout0, obase, ux, uy);
+        stream_collide_cell<NL, false, P, S, R>(p, p.lat[0], cell, fout0, obase, ux, uy, dr);
       else
-        stream_collide_cell<NH, P, S, R>(p, p.lat[1], cell, pl, kTXP, fout1, obase, ux, uy);
-      if (p.crit == 1) flag_nxt[x + p.nx * y] = sqrt(ux * ux + uy * uy) > p.thr ? 1 : 0;
+        stream_collide_cell<NH, true, P, S, R>(p, p.lat[1], cell, fout1, obase, ux, uy, dr);
+
+      nf = fl;
+      if (p.crit == 1) {
+        nf = sqrt(ux * ux + uy * uy) > p.thr ? 1 : 0;
+        flag_nxt[x + p.nx * y] = (uint8_t)nf;
+      }
+      flip = nf != fl;
+    }
+    // after a tile's last item: the lattices its cells carry next step and
+    // whether any flipped (read by the post-step kernel to skip quiet tiles
+    // and by the next launch's producer)
+    const Item nx_it = next_item(it, tile_mask, ntiles);
+    if (nx_it.t != it.t) {
+      const int lo = __syncthreads_or(nf == 0);
+      const int hi = __syncthreads_or(nf == 1);
+      const int fp = __syncthreads_or(flip);
+      if (tid == 0) mask_next[it.t] = (uint8_t)(lo | (hi << 1) | (fp << 2));
+      flip = false;
     }
     __syncthreads();  // stage s is free again
     if (tid == 0 && pc.t < ntiles) {
@@ -258,7 +297,7 @@ k_stream_collide(const Params<R> p, const __grid_constant__ CUtensorMap tm0,
       const int Q = pc.k ? NH * NH : NL * NL;
       mbar_expect_tx(&full[s], (uint32_t)(Q * pl * (int)sizeof(S)));
       tma_load_3d(sm + s * stage, pc.k ? &tm1 : &tm0, &full[s], (pc.t % ntx) * kTX + kOX - kXH,
-                  (pc.t / ntx) * kTY, 0);
+                  (pc.t / ntx) * kTY + p.G - GH, 0);
       pc = next_item(pc, tile_mask, ntiles);
     }
   }
@@ -268,12 +307,14 @@ template <class S, class R>
 cudaError_t launch_stream_collide_impl(const Params<R>& p, int P, const CUtensorMap* tm0,
                                        const CUtensorMap* tm1, S* fout0, S* fout1,
                                        const uint8_t* flag_cur, uint8_t* flag_nxt,
-                                       const uint8_t* tile_mask, int* err, cudaStream_t st) {
+                                       const uint8_t* tile_mask, uint8_t* mask_next,
+                                       const BcDev& bc, int* err, cudaStream_t st) {
   const dim3 blk(kTX, kTY);
   const int ntx = (p.nx + kTX - 1) / kTX, nty = (p.ny + kTY - 1) / kTY;
   const int ntiles = ntx * nty;
   const int nl = p.lat[0].n, nh = p.lat[1].n;
-  const size_t smem = (size_t)kStages * nh * nh * (kTY + 2 * p.G) * kTXP * sizeof(S);
+  const size_t smem = (size_t)kStages * nh * nh * (kTY + 2 * stage_halo(P)) * kTXP * sizeof(S);
+  if (p.G < stage_halo(P)) return cudaErrorInvalidValue;  // ghost ring narrower than the stage halo
   int dev = 0, nsm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -293,8 +334,9 @@ cudaError_t launch_stream_collide_impl(const Params<R>& p, int P, const CUtensor
     if (e != cudaSuccess) return e;                                                         \
     if (per_sm < 1) return cudaErrorInvalidConfiguration;                                   \
     const int grid = ntiles < per_sm * nsm ? ntiles : per_sm * nsm;                         \
+    if ((ntiles + grid - 1) / grid > kMaxTilesPerCta) return cudaErrorInvalidValue;         \
     kern<<<grid, blk, smem, st>>>(p, *tm0, *tm1, fout0, fout1, flag_cur, flag_nxt,          \
-                                  tile_mask, ntx, ntiles, err);                             \
+                                  tile_mask, mask_next, ntx, ntiles, bc, err);              \
     return cudaGetLastError();                                                              \
   }
 #define SLBM_SC_PAIR(NL, NH) \

@@ -6,10 +6,12 @@ template <>
 cudaError_t launch_stream_collide<float, float>(const Params<float>& p, int P, const void* tm0,
                                           const void* tm1, float* fout0, float* fout1,
                                           const uint8_t* flag_cur, uint8_t* flag_nxt,
-                                          const uint8_t* tile_mask, int* err, cudaStream_t st) {
+                                          const uint8_t* tile_mask, uint8_t* mask_next,
+                                          const BcDev& bc, int* err, cudaStream_t st) {
   return launch_stream_collide_impl<float, float>(p, P, static_cast<const CUtensorMap*>(tm0),
                                             static_cast<const CUtensorMap*>(tm1), fout0, fout1,
-                                            flag_cur, flag_nxt, tile_mask, err, st);
+                                            flag_cur, flag_nxt, tile_mask, mask_next, bc, err,
+                                            st);
 }
 
 size_t stream_stage_bytes(int elem_size, int nh, int G) {
