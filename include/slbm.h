@@ -209,6 +209,32 @@ SLBM_API int slbm_set_state(slbm_t h, const void *buf, size_t bytes);
 SLBM_API int slbm_profile(slbm_t h, int enable);
 SLBM_API int slbm_profile_read(slbm_t h, double *ms, long long *steps);
 
+/* FP64 conservation sums of a dense population field without allocating
+ * anything (no cudaMalloc, cudaFree or allocating library call).  For callers
+ * that cannot allocate device memory: code running inside a CUDA stream
+ * capture (an allocation there would break the capture), hard real-time
+ * loops that only use memory reserved in advance, and frameworks that own all
+ * device memory.  The paper has no counterpart; this is a service entry point.
+ *   f:       device, FP32 full populations f_i (not deviations) of lattice
+ *            `lattice` (an SLBM_D2Q* value n, Q = n*n), plane-major:
+ *            f[i * nx * ny + x + nx * y].
+ *   out:     device, 4 doubles: sum rho, sum rho u_x, sum rho u_y, sum rho E
+ *            with rho E = sum |c_i|^2 / 2 f_i (the slbm_audit quantities).
+ *   cuda_stream: cudaStream_t (NULL = legacy default stream); asynchronous.
+ * The reduction's scratch is a static device array in this library of
+ * SLBM_NOALLOC_MAX_BLOCKS x 4 doubles (32 KiB), held by every GPU that loads
+ * the library until the process exits.  Every call overwrites the entries it
+ * uses before reading them; all calls share the array, so calls that overlap
+ * on the GPU (different streams or threads without ordering) race.
+ * nx * ny must not exceed SLBM_NOALLOC_MAX_CELLS (SLBM_EINVAL otherwise).
+ * The first call on a device (with that device current) looks up the
+ * array's device address with cudaGetSymbolAddress; make that first call
+ * before any stream capture.  Returns SLBM_OK, SLBM_EINVAL or SLBM_ECUDA. */
+#define SLBM_NOALLOC_MAX_BLOCKS 1024
+#define SLBM_NOALLOC_MAX_CELLS (1LL << 30)
+SLBM_API int slbm_audit_dense_noalloc(const float *f, int lattice, int nx, int ny, double *out,
+                                      void *cuda_stream);
+
 /* Message of the last failure on this handle ("" if none); h may be NULL for
  * the last creation failure of the calling thread. */
 SLBM_API const char *slbm_last_error(slbm_t h);

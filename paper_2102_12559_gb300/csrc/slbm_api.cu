@@ -254,6 +254,8 @@ Layout make_layout(const slbm_grid* g, int lo, int hi, int order, int precision)
 
 }  // namespace
 
+void slbm::host_gauss_hermite(int n, double* c, double* w) { gauss_hermite(n, c, w); }
+
 struct slbm_s {
   CUtensorMap tmap[2][2];        // TMA descriptors of the planes [buffer][lattice]
   slbm_grid g;

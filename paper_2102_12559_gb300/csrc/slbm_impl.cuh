@@ -143,4 +143,8 @@ cudaError_t launch_pack(const Params<R>& p, int k, int i0, int cnt, const S* f, 
 
 int audit_parts(int nx, int ny);
 
+// Host Gauss-Hermite nodes / weights of the n-node 1-D lattice (Table I),
+// computed as the roots of He_n (defined with the other host tables).
+void host_gauss_hermite(int n, double* c, double* w);
+
 }  // namespace slbm

@@ -32,7 +32,7 @@ EXPORTS = [
     "slbm_init_equilibrium", "slbm_set_flags", "slbm_get_flags", "slbm_set_criterion",
     "slbm_set_boundary", "slbm_step", "slbm_sync", "slbm_moments", "slbm_moments_device",
     "slbm_audit", "slbm_get_pops", "slbm_set_pops", "slbm_get_state", "slbm_set_state",
-    "slbm_profile", "slbm_profile_read", "slbm_last_error",
+    "slbm_profile", "slbm_profile_read", "slbm_audit_dense_noalloc", "slbm_last_error",
 ]
 SLBM_PROFILE_KERNELS = 2
 KERNEL_NAMES = ("stream_collide", "post_convert_ghosts")
@@ -97,6 +97,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.slbm_set_state.argtypes = [p, p, ctypes.c_size_t]
     L.slbm_profile.argtypes = [p, i]
     L.slbm_profile_read.argtypes = [p, p, P(ctypes.c_longlong)]
+    L.slbm_audit_dense_noalloc.argtypes = [p, i, i, i, p, p]
     L.slbm_last_error.argtypes = [p]
     L.slbm_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -253,6 +254,13 @@ def slbm_profile_read(h):
     n = ctypes.c_longlong(0)
     _check(load().slbm_profile_read(h, _ptr(ms), ctypes.byref(n)), h)
     return ms, n.value
+
+
+def slbm_audit_dense_noalloc(f_ptr, lattice, nx, ny, out_ptr, stream=0):
+    """Allocation-free FP64 audit of a dense FP32 population field (device
+    pointers; see include/slbm.h)."""
+    _check(load().slbm_audit_dense_noalloc(ctypes.c_void_p(f_ptr), lattice, nx, ny,
+                                           ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream)))
 
 
 def slbm_last_error(h=None) -> str:
