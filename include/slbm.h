@@ -202,10 +202,10 @@ SLBM_API int slbm_set_state(slbm_t h, const void *buf, size_t bytes);
  * and starts bracketing every kernel slbm_step launches with CUDA events on
  * the handle's stream; slbm_profile(h, 0) stops.  slbm_profile_read()
  * synchronises and returns, per kernel of the step sequence (index 0 =
- * stream-collide, 1 = interface conversion with the boundary ghost images),
- * the summed device milliseconds over the recorded steps, and the number of
+ * stream-collide, 1 = interface conversion, 2 = ghost-ring refresh), the
+ * summed device milliseconds over the recorded steps, and the number of
  * recorded steps.  ms must hold SLBM_PROFILE_KERNELS doubles. */
-#define SLBM_PROFILE_KERNELS 2
+#define SLBM_PROFILE_KERNELS 3
 SLBM_API int slbm_profile(slbm_t h, int enable);
 SLBM_API int slbm_profile_read(slbm_t h, double *ms, long long *steps);
 

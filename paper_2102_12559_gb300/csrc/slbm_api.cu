@@ -268,6 +268,7 @@ struct slbm_s {
   char* ws;
   bool owns_ws;
   int dev;                       // CUDA device of the workspace
+  int nsm;                       // its multiprocessor count
   int cur, fcur;                 // population buffer and flag buffer in use
   int mcur;                      // tile-mask buffer the next stream launch reads
   int crit;
@@ -427,7 +428,7 @@ cudaError_t mark(slbm_s* h) {
 }
 
 // One time step: stream-collide (old flags) -> interface conversion (new
-// flags) with the boundary cells' ghost images.
+// flags) -> ghost-ring refresh.
 int step_once(slbm_s* h) {
   const int b = h->cur, nb = b ^ 1;
   uint8_t* fold = h->flags(h->fcur);
@@ -448,6 +449,14 @@ int step_once(slbm_s* h) {
   SLBM_CK(h, e, "stream_collide launch");
   SLBM_CK(h, mark(h), "trace event");
   SLBM_CK(h, convert(h, nb, fold, fnew, mask_next), "post-step launch");
+  SLBM_CK(h, mark(h), "trace event");
+  if (h->precision == SLBM_FP64)
+    e = launch_halo<double, double>(h->pd, (double*)h->pops(nb, 0), (double*)h->pops(nb, 1), fnew,
+                                    bc_dev(h), h->st);
+  else
+    e = launch_halo<float, float>(h->pf, (float*)h->pops(nb, 0), (float*)h->pops(nb, 1), fnew,
+                                  bc_dev(h), h->st);
+  SLBM_CK(h, e, "halo launch");
   SLBM_CK(h, mark(h), "trace event");
   h->cur = nb;
   h->mcur ^= 1;
@@ -471,6 +480,7 @@ void fill_params(Params<R>& p, const slbm_s* h, const Lattice1D& a, const Lattic
   p.thr = (R)h->thr;
   p.omega = (R)(1.0 / h->tau);
   p.band = h->lay.G;
+  p.nsm = h->nsm;
   fill_lat(p.lat[0], a, dt, h->P);
   fill_lat(p.lat[1], b, dt, h->P);
   ConvTab<R>& t = p.conv;
@@ -643,6 +653,8 @@ int slbm_create_in(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int i
   slbm_s* h = new (std::nothrow) slbm_s();
   if (!h) return SLBM_ENOMEM;
   h->dev = attr.device;
+  h->nsm = 1;
+  cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev);
   h->g = *g;
   h->nlo = lat_lo;
   h->nhi = lat_hi;
@@ -726,7 +738,7 @@ int slbm_get_info(slbm_t h, slbm_info_t* info) {
   info->pitch = h->lay.pitch;
   info->rows = h->lay.rows;
   info->precision = h->precision;
-  info->kernels_per_step = 2;
+  info->kernels_per_step = 3;
   info->workspace_bytes = h->lay.total;
   info->steps = h->steps;
   return SLBM_OK;

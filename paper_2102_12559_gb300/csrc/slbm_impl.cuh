@@ -74,6 +74,7 @@ struct Params {
   R thr;                        // Mach threshold
   R omega;
   int band;                     // stencil reach in cells (band radius)
+  int nsm;                      // multiprocessors of the handle's device (launch sizing)
   LatTab<R> lat[2];             // 0 = low-order, 1 = high-order
   ConvTab<R> conv;
 };
@@ -120,6 +121,12 @@ cudaError_t launch_post(const Params<R>& p, S* f0, S* f1, const uint8_t* flag_ol
 template <class S, class R>
 cudaError_t launch_ghosts(const Params<R>& p, S* f0, S* f1, const uint8_t* flag,
                           const BcDev& bc, cudaStream_t st);
+
+// Per-step ghost refresh of one buffer: periodic / OUTFLOW copies of every
+// plane of both lattices and INLET equilibria (DIRICHLET ghosts are constant).
+template <class S, class R>
+cudaError_t launch_halo(const Params<R>& p, S* f0, S* f1, const uint8_t* flag, const BcDev& bc,
+                        cudaStream_t st);
 
 template <class S, class R>
 cudaError_t launch_init_eq(const Params<R>& p, S* f0, S* f1, const double* rho,

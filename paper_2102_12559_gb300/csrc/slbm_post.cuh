@@ -90,40 +90,18 @@ struct PostMath {
   }
 };
 
+constexpr int kPostMaxTiles = 1024;  // tiles one persistent post CTA may own
+
+// The work of one tile (tile origin x0, y0): stage the new flags of the tile
+// and its band-wide halo, convert band / flipped cells, and in setup calls
+// write the tile's lattice mask.
 template <int NL, int NH, class S, class R>
-__global__ void __launch_bounds__(kTX * kTY)
-k_post(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ flag_old,
-       const uint8_t* __restrict__ flag_new, const BcDev bc, int images,
-       const uint8_t* __restrict__ mask_in, uint8_t* __restrict__ tile_mask) {
-  __shared__ uint8_t sf[kTY + 2 * kBandMax][kTX + 2 * kBandMax];
+__device__ __forceinline__ void post_tile(const Params<R>& p, S* f0, S* f1,
+                                          const uint8_t* __restrict__ flag_old,
+                                          const uint8_t* __restrict__ flag_new, const BcDev& bc,
+                                          int images, bool setup, uint8_t* mask_out, int x0,
+                                          int y0, uint8_t (*sf)[kTX + 2 * kBandMax]) {
   const int B = p.band;
-  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
-  if (mask_in) {
-    // after a step the stream kernel has left each tile's next-step lattices
-    // and a flip bit: a tile with one lattice in its 3 x 3 tile neighbourhood
-    // (the band radius is below the tile size), no flip and no boundary cell
-    // has nothing to do.  The nine loads are independent (no load waits on
-    // another), out-of-grid neighbours read the tile itself.
-    const int ntx = gridDim.x, nty = gridDim.y;
-    int idx[9];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      int tx = (int)blockIdx.x + q % 3 - 1, ty = (int)blockIdx.y + q / 3 - 1;
-      if (tx < 0 || tx >= ntx) tx = p.periodic_x ? (tx < 0 ? tx + ntx : tx - ntx) : (int)blockIdx.x;
-      if (ty < 0 || ty >= nty) ty = p.periodic_y ? (ty < 0 ? ty + nty : ty - nty) : (int)blockIdx.y;
-      idx[q] = ty * ntx + tx;
-    }
-    int mv[9];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) mv[q] = __ldg(mask_in + idx[q]);
-    int lat = 0;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) lat |= mv[q] & 3;
-    bool work = (mv[4] & 4) != 0 || lat == 3;
-    work = work || (images && (x0 < p.G || x0 + kTX > p.nx - p.G || y0 < p.G ||
-                               y0 + kTY > p.ny - p.G));
-    if (!work) return;
-  }
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
   const bool in = x < p.nx && y < p.ny;
   const int old = in ? flag_old[x + p.nx * y] : 2;  // issued before the staging
@@ -151,58 +129,102 @@ k_post(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ flag_old,
   }
   __syncthreads();
   const int nw = in ? sf[threadIdx.y + B][threadIdx.x + B] : 2;
-  // which lattices the next step's tile holds (read by the stream kernel's
-  // producer to choose the planes it stages)
-  if (!mask_in) {  // setup call: derive the tile masks from the new flags here
+  if (setup) {  // the lattices the next step's tile holds (read by the stream kernel)
     const int any_lo = __syncthreads_or(nw == 0);
     const int any_hi = __syncthreads_or(nw == 1);
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-      tile_mask[blockIdx.y * gridDim.x + blockIdx.x] = (uint8_t)(any_lo | (any_hi << 1));
+    if (threadIdx.x == 0 && threadIdx.y == 0) *mask_out = (uint8_t)(any_lo | (any_hi << 1));
   }
-  if (!in) return;
-  bool band = false;
-  for (int dy = -B; dy <= B; ++dy)
-    for (int dx = -B; dx <= B; ++dx) {
-      const int v = sf[threadIdx.y + B + dy][threadIdx.x + B + dx];
-      band |= (v != 2) && (v != nw);
-    }
-  const int base = (y + p.G) * p.pitch + (x + kOX);
-  const bool conv = old != nw || band;
-  if (conv) {
-    R a[kMaxN][kMaxN], b[kMaxN][kMaxN];
-    using M = PostMath<NL, NH, R>;
-    if (old == 0) {
-      load_t<NL, S, R>(f0, p.plane, base, a);
-      M::lift(p, a, b);
-      store_t<NH, S, R>(f1, p.plane, base, b);
-      if (old != nw && band) {  // now high-order; low-order readers see its projection
-        M::project(p, b, a);
-        store_t<NL, S, R>(f0, p.plane, base, a);
+  if (in) {
+    bool band = false;
+    for (int dy = -B; dy <= B; ++dy)
+      for (int dx = -B; dx <= B; ++dx) {
+        const int v = sf[threadIdx.y + B + dy][threadIdx.x + B + dx];
+        band |= (v != 2) && (v != nw);
       }
-    } else {
-      load_t<NH, S, R>(f1, p.plane, base, b);
-      M::project(p, b, a);
-      store_t<NL, S, R>(f0, p.plane, base, a);
-      if (old != nw && band) {  // now low-order; high-order readers see its lifting
+    const int base = (y + p.G) * p.pitch + (x + kOX);
+    if (old != nw || band) {
+      R a[kMaxN][kMaxN], b[kMaxN][kMaxN];
+      using M = PostMath<NL, NH, R>;
+      if (old == 0) {
+        load_t<NL, S, R>(f0, p.plane, base, a);
         M::lift(p, a, b);
         store_t<NH, S, R>(f1, p.plane, base, b);
+        if (old != nw && band) {  // now high-order; low-order readers see its projection
+          M::project(p, b, a);
+          store_t<NL, S, R>(f0, p.plane, base, a);
+        }
+      } else {
+        load_t<NH, S, R>(f1, p.plane, base, b);
+        M::project(p, b, a);
+        store_t<NL, S, R>(f0, p.plane, base, a);
+        if (old != nw && band) {  // now low-order; high-order readers see its lifting
+          M::lift(p, a, b);
+          store_t<NH, S, R>(f1, p.plane, base, b);
+        }
       }
     }
   }
-  if (images && (x < p.G || x >= p.nx - p.G || y < p.G || y >= p.ny - p.G))
-    boundary_images<NL, NH, S, R>(p, f0, f1, bc, x, y, nw);
+  __syncthreads();  // sf is reused by the next tile
+}
+
+// Persistent post-step kernel: CTA c owns tiles c, c + gridDim.x, ...  After a
+// step (mask_in set) a prologue derives every owned tile's work flag from the
+// stream kernel's masks -- a flip in the tile, or both lattices in its 3 x 3
+// tile neighbourhood (the band radius is below the tile size) -- with all
+// mask loads independent; quiet tiles then cost nothing.  Setup calls
+// (mask_in null) visit every tile and write its lattice mask.  Ghost rings are
+// refreshed afterwards by the halo kernel.
+template <int NL, int NH, class S, class R>
+__global__ void __launch_bounds__(kTX * kTY)
+k_post(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ flag_old,
+       const uint8_t* __restrict__ flag_new, const BcDev bc, int images,
+       const uint8_t* __restrict__ mask_in, uint8_t* __restrict__ tile_mask, int ntx, int nty) {
+  __shared__ uint8_t sf[kTY + 2 * kBandMax][kTX + 2 * kBandMax];
+  __shared__ int work[kPostMaxTiles];
+  const int ntiles = ntx * nty;
+  const int tid = threadIdx.y * kTX + threadIdx.x;
+  const int M = ((int)blockIdx.x < ntiles) ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  for (int m = tid; m < M; m += kTX * kTY) work[m] = mask_in ? 0 : 1;
+  __syncthreads();
+  if (mask_in) {
+    for (int e = tid; e < 9 * M; e += kTX * kTY) {
+      const int m = e / 9, q = e % 9;
+      const int t = (int)blockIdx.x + m * (int)gridDim.x;
+      const int bx = t % ntx, by = t / ntx;
+      int tx = bx + q % 3 - 1, ty = by + q / 3 - 1;
+      if (tx < 0 || tx >= ntx) tx = p.periodic_x ? (tx < 0 ? tx + ntx : tx - ntx) : bx;
+      if (ty < 0 || ty >= nty) ty = p.periodic_y ? (ty < 0 ? ty + nty : ty - nty) : by;
+      const int mv = __ldg(mask_in + ty * ntx + tx);
+      // bit 0/1: lattices seen; bit 2: this tile flipped
+      atomicOr(&work[m], (mv & 3) | (q == 4 ? (mv & 4) : 0));
+    }
+    __syncthreads();
+  }
+  for (int m = 0; m < M; ++m) {
+    const int t = (int)blockIdx.x + m * (int)gridDim.x;
+    const int x0 = (t % ntx) * kTX, y0 = (t / ntx) * kTY;
+    const int wv = work[m];
+    if (mask_in && !((wv & 4) || (wv & 3) == 3)) continue;  // uniform per CTA
+    post_tile<NL, NH, S, R>(p, f0, f1, flag_old, flag_new, bc, images, mask_in == nullptr,
+                            tile_mask + t, x0, y0, sf);
+  }
 }
 
 template <class S, class R>
 cudaError_t launch_post_impl(const Params<R>& p, S* f0, S* f1, const uint8_t* flag_old,
                              const uint8_t* flag_new, const BcDev& bc, int images,
                              const uint8_t* mask_in, uint8_t* tile_mask, cudaStream_t st) {
-  const dim3 blk(kTX, kTY), grd((p.nx + kTX - 1) / kTX, (p.ny + kTY - 1) / kTY);
+  const int ntx = (p.nx + kTX - 1) / kTX, nty = (p.ny + kTY - 1) / kTY;
+  const int ntiles = ntx * nty;
+  int grid = p.nsm * 2;  // two resident CTAs per SM at this register count
+  if (grid > ntiles) grid = ntiles;
+  if ((ntiles + grid - 1) / grid > kPostMaxTiles) grid = (ntiles + kPostMaxTiles - 1) / kPostMaxTiles;
+  const dim3 blk(kTX, kTY);
   const int nl = p.lat[0].n, nh = p.lat[1].n;
 #define SLBM_POST_CASE(NL, NH)                                                              \
   if (nl == NL && nh == NH) {                                                               \
-    k_post<NL, NH, S, R>                                                                    \
-        <<<grd, blk, 0, st>>>(p, f0, f1, flag_old, flag_new, bc, images, mask_in, tile_mask); \
+    k_post<NL, NH, S, R><<<grid, blk, 0, st>>>(p, f0, f1, flag_old, flag_new, bc, images,    \
+                                                mask_in, tile_mask, ntx, nty);               \
     return cudaGetLastError();                                                              \
   }
   SLBM_POST_CASE(3, 4)

@@ -224,6 +224,7 @@ k_stream_collide(const Params<R> p, const __grid_constant__ CUtensorMap tm0,
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[kStages];
   __shared__ uint8_t tmask[kMaxTilesPerCta];  // masks of this CTA's tiles, by local index
+  __shared__ int tile_bits[2];                // next-step mask of the tile being finished
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
   for (int m = tid; blockIdx.x + m * gridDim.x < ntiles; m += kTX * kTY)
     tmask[m] = tile_mask_g[blockIdx.x + m * gridDim.x];
@@ -234,6 +235,7 @@ k_stream_collide(const Params<R> p, const __grid_constant__ CUtensorMap tm0,
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
     mbar_fence_init();
+    tile_bits[0] = tile_bits[1] = 0;
   }
   __syncthreads();
   const uint8_t* tile_mask = tmask;
@@ -246,17 +248,23 @@ k_stream_collide(const Params<R> p, const __grid_constant__ CUtensorMap tm0,
                   (pc.t / ntx) * kTY + p.G - GH, 0);
       pc = next_item(pc, tile_mask, ntiles);
     }
+  // this thread's cell flag for an item, loaded one item ahead
+  auto cell_flag = [&](const Item& q) -> int {
+    if (q.t >= ntiles) return 2;
+    const int xx = (q.t % ntx) * kTX + tx, yy = (q.t / ntx) * kTY + ty;
+    return (xx < p.nx && yy < p.ny) ? flag_cur[xx + p.nx * yy] : 2;
+  };
   int j = 0;
-  int nf = -1;        // this thread's cell: next-step flag (-1 = not computed yet)
-  bool flip = false;  // ... and whether it differs from this step's flag
-  for (Item it = first_item(tile_mask, ntiles); it.t < ntiles;
-       it = next_item(it, tile_mask, ntiles), ++j) {
+  int bits = 0;  // this thread's cell: bit 0/1 = next-step lattice, bit 2 = flipped
+  Item it = first_item(tile_mask, ntiles);
+  int fl_next = cell_flag(it);
+  for (; it.t < ntiles; ++j) {
+    const Item nx_it = next_item(it, tile_mask, ntiles);
+    const int fl = fl_next;
+    fl_next = cell_flag(nx_it);
     const int s = j % kStages;
     const int x0 = (it.t % ntx) * kTX, y0 = (it.t / ntx) * kTY;
     const int x = x0 + tx, y = y0 + ty;
-    const bool in = x < p.nx && y < p.ny;
-    const int fl = in ? flag_cur[x + p.nx * y] : 2;  // issued before the wait
-    if (it.k == 0 || !(local_mask(tile_mask, it.t) & 1)) nf = -1;  // first item of a tile
     if (!mbar_wait(&full[s], (uint32_t)((j / kStages) & 1))) {
       // bounded: record, give the copy one more bounded wait, stop
       if (tid == 0) atomicExch(err, 1);
@@ -272,25 +280,28 @@ k_stream_collide(const Params<R> p, const __grid_constant__ CUtensorMap tm0,
       else
         stream_collide_cell<NH, true, P, S, R>(p, p.lat[1], cell, fout1, obase, ux, uy, dr);
 
-      nf = fl;
+      int nf = fl;
       if (p.crit == 1) {
         nf = sqrt(ux * ux + uy * uy) > p.thr ? 1 : 0;
         flag_nxt[x + p.nx * y] = (uint8_t)nf;
       }
-      flip = nf != fl;
+      bits = (1 << nf) | (nf != fl ? 4 : 0);
     }
     // after a tile's last item: the lattices its cells carry next step and
     // whether any flipped (read by the post-step kernel to skip quiet tiles
-    // and by the next launch's producer)
-    const Item nx_it = next_item(it, tile_mask, ntiles);
-    if (nx_it.t != it.t) {
-      const int lo = __syncthreads_or(nf == 0);
-      const int hi = __syncthreads_or(nf == 1);
-      const int fp = __syncthreads_or(flip);
-      if (tid == 0) mask_next[it.t] = (uint8_t)(lo | (hi << 1) | (fp << 2));
-      flip = false;
+    // and by the next launch's producer), OR-reduced per warp, then through
+    // a shared word made visible by the stage-release barrier below
+    const bool tile_end = nx_it.t != it.t;
+    if (tile_end) {
+      const int wbits = __reduce_or_sync(0xffffffffu, bits);
+      if ((tid & 31) == 0 && wbits) atomicOr(&tile_bits[j & 1], wbits);
+      bits = 0;
     }
-    __syncthreads();  // stage s is free again
+    __syncthreads();  // stage s is free again; tile_bits complete
+    if (tile_end && tid == 0) {
+      mask_next[it.t] = (uint8_t)tile_bits[j & 1];
+      tile_bits[j & 1] = 0;
+    }
     if (tid == 0 && pc.t < ntiles) {
       // order the CTA's shared-memory reads of stage s before the async-proxy write
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -300,6 +311,7 @@ k_stream_collide(const Params<R> p, const __grid_constant__ CUtensorMap tm0,
                   (pc.t / ntx) * kTY + p.G - GH, 0);
       pc = next_item(pc, tile_mask, ntiles);
     }
+    it = nx_it;
   }
 }
 
@@ -315,9 +327,7 @@ cudaError_t launch_stream_collide_impl(const Params<R>& p, int P, const CUtensor
   const int nl = p.lat[0].n, nh = p.lat[1].n;
   const size_t smem = (size_t)kStages * nh * nh * (kTY + 2 * stage_halo(P)) * kTXP * sizeof(S);
   if (p.G < stage_halo(P)) return cudaErrorInvalidValue;  // ghost ring narrower than the stage halo
-  int dev = 0, nsm = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int nsm = p.nsm;
 #define SLBM_SC_CASE(NL, NH, PP)                                                            \
   if (nl == NL && nh == NH && P == PP) {                                                    \
     auto kern = k_stream_collide<NL, NH, PP, S, R>;                                         \
@@ -328,10 +338,14 @@ cudaError_t launch_stream_collide_impl(const Params<R>& p, int P, const CUtensor
       if (e != cudaSuccess) return e;                                                       \
       attr_set = smem;                                                                      \
     }                                                                                       \
-    int per_sm = 0;                                                                         \
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern,            \
-                                                                  kTX * kTY, smem);         \
-    if (e != cudaSuccess) return e;                                                         \
+    static size_t occ_smem = 0; /* occupancy is queried once per dynamic size */            \
+    static int per_sm = 0;                                                                  \
+    if (occ_smem != smem) {                                                                 \
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern,          \
+                                                                    kTX * kTY, smem);       \
+      if (e != cudaSuccess) return e;                                                       \
+      occ_smem = smem;                                                                      \
+    }                                                                                       \
     if (per_sm < 1) return cudaErrorInvalidConfiguration;                                   \
     const int grid = ntiles < per_sm * nsm ? ntiles : per_sm * nsm;                         \
     if ((ntiles + grid - 1) / grid > kMaxTilesPerCta) return cudaErrorInvalidValue;         \

@@ -34,8 +34,8 @@ EXPORTS = [
     "slbm_audit", "slbm_get_pops", "slbm_set_pops", "slbm_get_state", "slbm_set_state",
     "slbm_profile", "slbm_profile_read", "slbm_audit_dense_noalloc", "slbm_last_error",
 ]
-SLBM_PROFILE_KERNELS = 2
-KERNEL_NAMES = ("stream_collide", "post_convert_ghosts")
+SLBM_PROFILE_KERNELS = 3
+KERNEL_NAMES = ("stream_collide", "interface_convert", "halo")
 
 
 class slbm_grid(ctypes.Structure):
