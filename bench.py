@@ -41,7 +41,7 @@ NX, NY, SLOT, MA_JET, MA_CO, RE, THR = 1024, 512, 32, 0.5, 0.05, 1000.0, 0.3
 WORKLOAD = ("free jet 1024x512, FP32, D2Q9/D2Q25, cubic SL streaming, Mach>0.3 criterion "
             "every step, inlet/outflow/free-stream boundaries")
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_FILES = ["slbm_stream.cuh", "slbm_impl.cuh", "slbm_eq.cuh", "slbm_stream_f32.cu"]
+KERNEL_FILES = ["slbm_stream.cuh", "slbm_ghost.cuh", "slbm_impl.cuh", "slbm_eq.cuh", "slbm_stream_f32.cu"]
 
 
 def kernel_hash() -> str:
