@@ -26,6 +26,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "slbm_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
+# Frames: lattice frame, co-moving (PonD) thermal with C_v = D/2, co-moving
+# isothermal (T = T_L).
+FRAME_LATTICE = 0
+FRAME_POND = 1
+FRAME_POND_ISOTHERMAL = 2
+
 # Boundary kinds (same meaning as the solver library's, numbered independently).
 BC_OUTFLOW = 0
 BC_DIRICHLET = 1
@@ -73,14 +79,19 @@ def lib():
         L.orc_destroy.restype = None
         L.orc_dt.argtypes = [p]
         L.orc_dt.restype = d
-        L.orc_init_equilibrium.argtypes = [p, p, p, p]
+        L.orc_init_equilibrium.argtypes = [p, p, p, p, p]
+        L.orc_set_pond.argtypes = [p, d, i]
+        L.orc_nonconverged.argtypes = [p]
+        L.orc_nonconverged.restype = ctypes.c_long
+        L.orc_get_frame.argtypes = [p, p, p, p]
+        L.orc_set_frame.argtypes = [p, p, p, p]
         L.orc_set_flags.argtypes = [p, p]
         L.orc_get_flags.argtypes = [p, p]
         L.orc_get_flags.restype = None
         L.orc_set_criterion.argtypes = [p, i, d]
         L.orc_set_bc.argtypes = [p, i, i, p, p, p]
         L.orc_step.argtypes = [p, i]
-        L.orc_step_cells.argtypes = [p, i, p, p]
+        L.orc_step_cells.argtypes = [p, i, p, p, p]
         L.orc_moments.argtypes = [p, p, p, p, p]
         L.orc_audit.argtypes = [p, p]
         L.orc_get_pops.argtypes = [p, i, p]
@@ -183,11 +194,13 @@ def first_node(p: int, xd: float) -> int:
 class Oracle:
     """Whole-grid oracle state: nx x ny cells, low/high lattices n_lo < n_hi
     (3 = D2Q9, 4 = D2Q16, 5 = D2Q25), relaxation time tau (omega = 1/tau),
-    Lagrange order (points = order + 1), lattice frame."""
+    Lagrange order (points = order + 1), frame (FRAME_LATTICE, or one of the
+    co-moving frames of Sec. II.C, which need a periodic grid)."""
 
     def __init__(self, nx, ny, n_lo=3, n_hi=5, tau=0.6, order=3, periodic=(True, True),
                  frame=0, cfl=1.0):
         self.nx, self.ny = nx, ny
+        self.frame = frame
         self.n = (n_lo, n_hi)
         self.Q = (n_lo * n_lo, n_hi * n_hi)
         h = lib().orc_create(nx, ny, int(periodic[0]), int(periodic[1]), n_lo, n_hi,
@@ -206,9 +219,33 @@ class Oracle:
     def dt(self) -> float:
         return lib().orc_dt(self._h)
 
-    def init_equilibrium(self, rho, ux, uy):
+    def init_equilibrium(self, rho, ux, uy, T=None):
+        """Lattice frame: f^L(rho, u) (T must be None).  Co-moving frame:
+        rho W_i in the frame {u, T} (T = T_L when None), eq. (feqPond)."""
         r, a, b = _f64(rho).ravel(), _f64(ux).ravel(), _f64(uy).ravel()
-        _check(lib().orc_init_equilibrium(self._h, _ptr(r), _ptr(a), _ptr(b)), "init")
+        t = None if T is None else _f64(np.broadcast_to(T, r.reshape(self.ny, self.nx).shape)).ravel()
+        _check(lib().orc_init_equilibrium(self._h, _ptr(r), _ptr(a), _ptr(b),
+                                          None if t is None else _ptr(t)), "init")
+
+    def set_pond(self, tol: float, maxit: int):
+        """Predictor-corrector tolerance and iteration cap (co-moving frame)."""
+        _check(lib().orc_set_pond(self._h, tol, maxit), "set_pond")
+
+    def nonconverged(self) -> int:
+        """Cell updates whose predictor-corrector stopped at the cap."""
+        return int(lib().orc_nonconverged(self._h))
+
+    def get_frame(self):
+        """Frames (u_x, u_y, T) the cells' populations live in, each (ny, nx)."""
+        n = self.nx * self.ny
+        a, b, t = np.zeros(n), np.zeros(n), np.zeros(n)
+        _check(lib().orc_get_frame(self._h, _ptr(a), _ptr(b), _ptr(t)), "get_frame")
+        shp = (self.ny, self.nx)
+        return a.reshape(shp), b.reshape(shp), t.reshape(shp)
+
+    def set_frame(self, ux, uy, T):
+        a, b, t = (_f64(np.broadcast_to(v, (self.ny, self.nx))).ravel() for v in (ux, uy, T))
+        _check(lib().orc_set_frame(self._h, _ptr(a), _ptr(b), _ptr(t)), "set_frame")
 
     def set_flags(self, flags):
         f = np.ascontiguousarray(flags, dtype=np.uint8).ravel()
@@ -230,14 +267,17 @@ class Oracle:
     def step(self, n: int = 1):
         _check(lib().orc_step(self._h, n), "step")
 
-    def step_cells(self, cells) -> np.ndarray:
+    def step_cells(self, cells, with_frame: bool = False):
         """One step's post-collision vectors of the given cells (x + nx*y),
         without advancing the state: shape (m, 25), the first Q of the cell's
-        lattice valid."""
+        lattice valid.  with_frame (co-moving frame): also the (m, 3) frames
+        {u_x, u_y, T} the vectors live in."""
         c = np.ascontiguousarray(cells, dtype=np.int64)
         out = np.zeros((len(c), 25))
-        _check(lib().orc_step_cells(self._h, len(c), _ptr(c), _ptr(out)), "step_cells")
-        return out
+        lam = np.zeros((len(c), 3))
+        _check(lib().orc_step_cells(self._h, len(c), _ptr(c), _ptr(out),
+                                    _ptr(lam) if with_frame else None), "step_cells")
+        return (out, lam) if with_frame else out
 
     def moments(self):
         n = self.nx * self.ny

@@ -26,6 +26,15 @@
  *   - Eq. (Pond_f_equation) with omega_1 = omega_2: BGK relaxation to the
  *     lattice equilibrium.
  *   - The Mach refinement criterion of Sec. IV.A (threshold on |u| / c_s).
+ *   - The co-moving (PonD) frame of Sec. II.C: every node keeps its populations
+ *     in its own frame lambda = {u, T}; a cell reconstructs each population at
+ *     x - v_i dt with v_i = sqrt(theta) c_i + u of its current frame guess,
+ *     after carrying every collocation node's vector into that frame by
+ *     eq. (fll); the predictor-corrector of eqs. (correctorfieldsrho-u)
+ *     replaces the guess by the reconstructed moments until they agree.
+ *     Two variants: thermal (single f population, C_v = D/2 so the g
+ *     population of eq. (geqPond) vanishes identically) and isothermal
+ *     (T held at T_L).
  *
  * Readings where the paper is silent (each also listed in the design notes):
  *   - "third-order Lagrange polynomials": p = order + 1 collocation points per
@@ -40,6 +49,15 @@
  *     them: DIRICHLET = equilibrium at a fixed rho, u; INLET = fixed u with rho
  *     copied from the first interior node; OUTFLOW = copy of the nearest
  *     interior node.  A non-periodic y side takes precedence at corners.
+ *   - Co-moving frame: no snapping of departure points; the iteration stops
+ *     when max(|du_x|, |du_y|, |dT|) <= tol between the frame used and the
+ *     moments it produced, or after maxit reconstructions; the populations
+ *     and frame kept are those of the last reconstruction.  Collision relaxes
+ *     towards the equilibrium at the reconstructed rho, u, T expressed in
+ *     that frame (rho W_i itself once converged, eq. feqPond), so the
+ *     collision conserves rho, rho u (and rho E when thermal) exactly.
+ *     Lifting in a node's frame completes the moments with the equilibrium
+ *     at the node vector's own rho, u, T (T_L when isothermal).
  *
  * Data layout (private to this file): populations of one cell contiguous,
  * f[k][cell * Q_k + i], cell = x + nx * y, i = ix + n * iy with the 1-D nodes
@@ -371,7 +389,13 @@ typedef struct {
     olat L[2];                   /* 0 = low-order lattice q, 1 = high-order Q */
     double tau, omega, dt;
     int p;                       /* collocation points per axis */
-    int frame;                   /* 0 = lattice frame */
+    int frame;                   /* 0 = lattice frame, 1 = PonD thermal, 2 = PonD isothermal */
+    double *lam;                 /* PonD: frame {u_x, u_y, T} of every cell's populations */
+    double tol;                  /* predictor-corrector tolerance */
+    int maxit;                   /* predictor-corrector reconstructions at most */
+    long nonconv;                /* cell updates that stopped at maxit */
+    double *mom[2];              /* PonD: per-step memo of node moments M_lambda_s f_s */
+    uint8_t *hmom[2];
     double *f[2];                /* f[k][cell * Q_k + i]; meaningful where flag == k */
     uint8_t *flag;
     int crit_kind;               /* 0 = fixed flags, 1 = Mach criterion */
@@ -392,7 +416,8 @@ void orc_destroy(orc_t *s);
 orc_t *orc_create(int nx, int ny, int per_x, int per_y, int n_lo, int n_hi,
                   double tau, int order, int frame, double cfl)
 {
-    if (nx < 1 || ny < 1 || n_lo >= n_hi || tau <= 0.5 || order < 1 || order > 5 || frame != 0)
+    if (nx < 1 || ny < 1 || n_lo >= n_hi || tau <= 0.5 || order < 1 || order > 5 ||
+        frame < 0 || frame > 2 || (frame != 0 && !(per_x && per_y)))
         return NULL;
     orc_t *s = (orc_t *)calloc(1, sizeof(orc_t));
     if (!s) return NULL;
@@ -422,7 +447,19 @@ orc_t *orc_create(int nx, int ny, int per_x, int per_y, int n_lo, int n_hi,
         s->have[k] = (uint8_t *)calloc((long)s->px * s->py, 1);
     }
     for (int b = 0; b < 4; ++b) s->bc[b].kind = ORC_BC_OUTFLOW;
-    if (!s->f[0] || !s->f[1] || !s->flag || !s->memo[0] || !s->memo[1] || !s->have[0] || !s->have[1]) {
+    s->tol = 1e-12;
+    s->maxit = 50;
+    int pond_ok = 1;
+    if (frame != 0) {
+        s->lam = (double *)calloc(3 * nc, sizeof(double));
+        for (int k = 0; k < 2; ++k) {
+            s->mom[k] = (double *)calloc(nc * s->L[k].Q, sizeof(double));
+            s->hmom[k] = (uint8_t *)calloc(nc, 1);
+        }
+        pond_ok = s->lam && s->mom[0] && s->mom[1] && s->hmom[0] && s->hmom[1];
+        for (long c = 0; pond_ok && c < nc; ++c) s->lam[3 * c + 2] = 1.0;
+    }
+    if (!pond_ok || !s->f[0] || !s->f[1] || !s->flag || !s->memo[0] || !s->memo[1] || !s->have[0] || !s->have[1]) {
         orc_destroy(s);
         return NULL;
     }
@@ -432,7 +469,10 @@ orc_t *orc_create(int nx, int ny, int per_x, int per_y, int n_lo, int n_hi,
 void orc_destroy(orc_t *s)
 {
     if (!s) return;
-    for (int k = 0; k < 2; ++k) { free(s->f[k]); free(s->memo[k]); free(s->have[k]); }
+    for (int k = 0; k < 2; ++k) {
+        free(s->f[k]); free(s->memo[k]); free(s->have[k]); free(s->mom[k]); free(s->hmom[k]);
+    }
+    free(s->lam);
     for (int b = 0; b < 4; ++b) { free(s->bc[b].rho); free(s->bc[b].ux); free(s->bc[b].uy); }
     free(s->flag);
     free(s);
@@ -453,23 +493,47 @@ static void eq_lat(const orc_t *s, int k, double rho, double ux, double uy, doub
     matvec(L->Q, G, feq, f);
 }
 
-/* Convert the vector of lattice `from` into lattice `to` (lift or project),
- * lattice frame, athermal (T = T_L). */
-static void convert(const orc_t *s, int from, int to, const double *src, double *dst)
+static const double LATTICE_FRAME[3] = {0.0, 0.0, 1.0};
+
+/* Frame the populations of cell c live in: the lattice frame {0, T_L}, or the
+ * cell's own co-moving frame in PonD. */
+static const double *cell_frame(const orc_t *s, long c)
 {
-    double lat[3] = {0.0, 0.0, 1.0};
+    return s->frame ? s->lam + 3 * c : LATTICE_FRAME;
+}
+
+/* Convert the vector of lattice `from` into lattice `to` (lift or project) in
+ * the frame lam the vector lives in.  The completing equilibrium of a lift is
+ * at T = T_L except in the thermal co-moving model (kinetic T of f_q). */
+static void convert(const orc_t *s, int from, int to, const double *lam, const double *src,
+                    double *dst)
+{
     if (from == to) { memcpy(dst, src, sizeof(double) * s->L[to].Q); return; }
-    if (from == 0) lift(&s->L[0], &s->L[1], lat, 1.0, src, dst);
-    else project(&s->L[1], &s->L[0], lat, src, dst);
+    if (from == 0) lift(&s->L[0], &s->L[1], lam, s->frame == 1 ? -1.0 : 1.0, src, dst);
+    else project(&s->L[1], &s->L[0], lam, src, dst);
 }
 
 /* Every cell starts at the equilibrium of both lattices (both representations
- * valid), flags 0. */
-int orc_init_equilibrium(orc_t *s, const double *rho, const double *ux, const double *uy)
+ * valid), flags 0.  Lattice frame: f^L at (rho, u), T must be NULL (athermal).
+ * Co-moving frame: f = rho W_i in the frame {u, T} (eq. feqPond), T = T_L when
+ * NULL; the isothermal variant takes T = NULL only. */
+int orc_init_equilibrium(orc_t *s, const double *rho, const double *ux, const double *uy,
+                         const double *T)
 {
     long nc = (long)s->nx * s->ny;
+    if (T && s->frame != 1) return -1;
     for (long c = 0; c < nc; ++c)
-        for (int k = 0; k < 2; ++k) eq_lat(s, k, rho[c], ux[c], uy[c], s->f[k] + c * s->L[k].Q);
+        for (int k = 0; k < 2; ++k) {
+            double *f = s->f[k] + c * s->L[k].Q;
+            if (s->frame == 0) {
+                eq_lat(s, k, rho[c], ux[c], uy[c], f);
+            } else {
+                for (int i = 0; i < s->L[k].Q; ++i) f[i] = rho[c] * s->L[k].W[i];
+                s->lam[3 * c] = ux[c];
+                s->lam[3 * c + 1] = uy[c];
+                s->lam[3 * c + 2] = T ? T[c] : 1.0;
+            }
+        }
     memset(s->flag, 0, nc);
     return 0;
 }
@@ -481,7 +545,8 @@ int orc_set_flags(orc_t *s, const uint8_t *fl)
     for (long c = 0; c < nc; ++c) {
         int nf = fl[c] ? 1 : 0;
         if (nf != s->flag[c]) {
-            convert(s, s->flag[c], nf, s->f[s->flag[c]] + c * s->L[s->flag[c]].Q, s->f[nf] + c * s->L[nf].Q);
+            convert(s, s->flag[c], nf, cell_frame(s, c), s->f[s->flag[c]] + c * s->L[s->flag[c]].Q,
+                    s->f[nf] + c * s->L[nf].Q);
             s->flag[c] = (uint8_t)nf;
         }
     }
@@ -503,7 +568,7 @@ static void apply_criterion(orc_t *s)
         macro(&s->L[k], lat, s->f[k] + c * s->L[k].Q, &rho, &ux, &uy, &T);
         int nf = sqrt(ux * ux + uy * uy) > s->crit_thr ? 1 : 0;
         if (nf != k) {
-            convert(s, k, nf, s->f[k] + c * s->L[k].Q, s->f[nf] + c * s->L[nf].Q);
+            convert(s, k, nf, LATTICE_FRAME, s->f[k] + c * s->L[k].Q, s->f[nf] + c * s->L[nf].Q);
             s->flag[c] = (uint8_t)nf;
         }
     }
@@ -513,6 +578,7 @@ static void apply_criterion(orc_t *s)
  * current state and after every step from then on. */
 int orc_set_criterion(orc_t *s, int kind, double thr)
 {
+    if (kind != 0 && s->frame != 0) return -1;   /* the Mach criterion is athermal */
     s->crit_kind = kind;
     s->crit_thr = thr;
     if (kind == 1) apply_criterion(s);
@@ -557,7 +623,8 @@ static const double *node_vec(orc_t *s, long gx, long gy, int k)
         long c = cidx(s, gx, gy);
         if (s->flag[c] == k) return s->f[k] + c * Q;        /* native */
         if (!s->have[k][m]) {
-            convert(s, s->flag[c], k, s->f[s->flag[c]] + c * s->L[s->flag[c]].Q, out);
+            convert(s, s->flag[c], k, cell_frame(s, c), s->f[s->flag[c]] + c * s->L[s->flag[c]].Q,
+                    out);
             s->have[k][m] = 1;
         }
         return out;
@@ -625,48 +692,179 @@ static void update_cell(orc_t *s, long x, long y, double *out)
     for (int i = 0; i < L->Q; ++i) out[i] = fbar[i] + s->omega * (feq[i] - fbar[i]);
 }
 
+/* Moments M_{lambda_s} f_s (eq. momfshort) of node (gx, gy)'s vector in
+ * lattice k, taken in the node's own frame lambda_s; memoised per step.  Only
+ * for the co-moving frame, whose grids are periodic. */
+static const double *node_moments(orc_t *s, long gx, long gy, int k)
+{
+    gx = ((gx % s->nx) + s->nx) % s->nx;
+    gy = ((gy % s->ny) + s->ny) % s->ny;
+    long c = cidx(s, gx, gy);
+    int Q = s->L[k].Q;
+    double *m = s->mom[k] + c * Q;
+    if (!s->hmom[k][c]) {
+        double M[ORC_MAXQ * ORC_MAXQ];
+        moment_matrix(&s->L[k], cell_frame(s, c), M);
+        matvec(Q, M, node_vec(s, gx, gy, k), m);
+        s->hmom[k][c] = 1;
+    }
+    return m;
+}
+
+/* One co-moving-frame update of cell (x, y), Sec. II.C.
+ * Predictor: the cell's frame of the previous step.  Each pass reconstructs
+ * every population at its departure point x - v_i dt, v_i = sqrt(theta) c_i + u
+ * of the current frame guess lam (eqs. vi, advectionPond), where the
+ * collocation vectors are first carried into lam: G_{lambda_s}^{lam} f_s =
+ * M_lam^{-1} (M_{lambda_s} f_s) (eqs. fll, reconstructionPond).  The moments
+ * of the result (eqs. correctorfieldsrho-u) become the next guess until they
+ * agree with it to tol.  Then BGK (eq. Pond_f_equation, omega_1 = omega_2)
+ * towards the equilibrium at those moments expressed in lam.  Writes Q values
+ * to out and the frame they live in to lam_out. */
+static int update_cell_pond(orc_t *s, long x, long y, double *out, double *lam_out)
+{
+    long c = cidx(s, x, y);
+    int k = s->flag[c];
+    const olat *L = &s->L[k];
+    int p = s->p, Q = L->Q;
+    double lam[3], nl[3] = {0.0, 0.0, 1.0}, rho = 0.0;
+    double fbar[ORC_MAXQ], feq[ORC_MAXQ], ax[8], ay[8];
+    double Mt[ORC_MAXQ * ORC_MAXQ], Mti[ORC_MAXQ * ORC_MAXQ];
+    int converged = 0;
+    memcpy(lam, s->lam + 3 * c, sizeof(lam));
+    for (int it = 0; it < s->maxit; ++it) {
+        moment_matrix(L, lam, Mt);
+        if (orc_invert(Q, Mt, Mti)) return -1;
+        double st = sqrt(lam[2]);
+        for (int i = 0; i < Q; ++i) {
+            double xd = (double)x - (st * L->cx[i] + lam[0]) * s->dt;
+            double yd = (double)y - (st * L->cy[i] + lam[1]) * s->dt;
+            long x0 = orc_first_node(p, xd), y0 = orc_first_node(p, yd);
+            orc_lagrange(p, xd, x0, ax);
+            orc_lagrange(p, yd, y0, ay);
+            double acc = 0.0;
+            for (int t = 0; t < p; ++t)
+                for (int u = 0; u < p; ++u) {
+                    const double *m = node_moments(s, x0 + u, y0 + t, k);
+                    double gi = 0.0;                      /* (G_{lambda_s}^{lam} f_s)_i */
+                    for (int r = 0; r < Q; ++r) gi += Mti[i * Q + r] * m[r];
+                    acc += ax[u] * ay[t] * gi;
+                }
+            fbar[i] = acc;
+        }
+        double ux, uy, T;
+        macro(L, lam, fbar, &rho, &ux, &uy, &T);
+        if (s->frame == 2) T = 1.0;
+        nl[0] = ux; nl[1] = uy; nl[2] = T;
+        double d = fmax(fabs(ux - lam[0]), fmax(fabs(uy - lam[1]), fabs(T - lam[2])));
+        if (d <= s->tol) { converged = 1; break; }
+        if (it + 1 < s->maxit) memcpy(lam, nl, sizeof(lam));
+    }
+    if (!converged) s->nonconv++;
+    if (feq_in_frame(L, rho, nl[0], nl[1], nl[2], lam, feq)) return -1;
+    for (int i = 0; i < Q; ++i) out[i] = fbar[i] + s->omega * (feq[i] - fbar[i]);
+    memcpy(lam_out, lam, sizeof(lam));
+    return 0;
+}
+
 static void reset_memo(orc_t *s)
 {
-    for (int k = 0; k < 2; ++k) memset(s->have[k], 0, (size_t)s->px * s->py);
+    for (int k = 0; k < 2; ++k) {
+        memset(s->have[k], 0, (size_t)s->px * s->py);
+        if (s->hmom[k]) memset(s->hmom[k], 0, (size_t)s->nx * s->ny);
+    }
 }
 
 /* Advance n time steps. */
 int orc_step(orc_t *s, int n)
 {
     long nc = (long)s->nx * s->ny;
-    double *g[2];
+    double *g[2] = {NULL, NULL}, *glam = NULL;
+    int rc = 0;
     for (int k = 0; k < 2; ++k) {
         g[k] = (double *)malloc(sizeof(double) * nc * s->L[k].Q);
-        if (!g[k]) { free(g[0]); return -1; }
+        if (!g[k]) rc = -1;
     }
-    for (int it = 0; it < n; ++it) {
+    if (s->frame && !(glam = (double *)malloc(sizeof(double) * 3 * nc))) rc = -1;
+    for (int it = 0; it < n && rc == 0; ++it) {
         reset_memo(s);
-        for (long y = 0; y < s->ny; ++y)
+        for (long y = 0; y < s->ny && rc == 0; ++y)
             for (long x = 0; x < s->nx; ++x) {
                 long c = cidx(s, x, y);
                 int k = s->flag[c];
-                update_cell(s, x, y, g[k] + c * s->L[k].Q);
+                if (s->frame == 0) {
+                    update_cell(s, x, y, g[k] + c * s->L[k].Q);
+                } else if (update_cell_pond(s, x, y, g[k] + c * s->L[k].Q, glam + 3 * c)) {
+                    rc = -1;
+                    break;
+                }
             }
+        if (rc) break;
         for (int k = 0; k < 2; ++k) {
             double *t = s->f[k]; s->f[k] = g[k]; g[k] = t;
         }
+        if (s->frame) { double *t = s->lam; s->lam = glam; glam = t; }
         if (s->crit_kind == 1) apply_criterion(s);   /* flags for the next step */
         s->steps++;
     }
     free(g[0]);
     free(g[1]);
-    return 0;
+    free(glam);
+    return rc;
 }
 
 /* One step's post-collision vectors of a few cells, without changing the
- * state: out[j * 25 + i], i < Q of the cell's lattice (flag[c] tells which). */
-int orc_step_cells(orc_t *s, int m, const long *cells, double *out)
+ * state: out[j * 25 + i], i < Q of the cell's lattice (flag[c] tells which);
+ * in the co-moving frame lam_out[3 j ..] receives the frame they live in
+ * (lam_out may be NULL). */
+int orc_step_cells(orc_t *s, int m, const long *cells, double *out, double *lam_out)
 {
     reset_memo(s);
     for (int j = 0; j < m; ++j) {
         long c = cells[j];
         if (c < 0 || c >= (long)s->nx * s->ny) return -1;
-        update_cell(s, c % s->nx, c / s->nx, out + (long)j * ORC_MAXQ);
+        if (s->frame == 0) {
+            update_cell(s, c % s->nx, c / s->nx, out + (long)j * ORC_MAXQ);
+        } else {
+            double lam[3];
+            if (update_cell_pond(s, c % s->nx, c / s->nx, out + (long)j * ORC_MAXQ, lam)) return -1;
+            if (lam_out) memcpy(lam_out + 3 * j, lam, sizeof(lam));
+        }
+    }
+    return 0;
+}
+
+/* Predictor-corrector controls of the co-moving frame. */
+int orc_set_pond(orc_t *s, double tol, int maxit)
+{
+    if (!(tol >= 0.0) || maxit < 1) return -1;
+    s->tol = tol;
+    s->maxit = maxit;
+    return 0;
+}
+
+long orc_nonconverged(const orc_t *s) { return s->nonconv; }
+
+/* Frames {u_x, u_y, T} of the cells' populations (co-moving frame only). */
+int orc_get_frame(const orc_t *s, double *ux, double *uy, double *T)
+{
+    if (!s->frame) return -1;
+    for (long c = 0; c < (long)s->nx * s->ny; ++c) {
+        ux[c] = s->lam[3 * c];
+        uy[c] = s->lam[3 * c + 1];
+        T[c] = s->lam[3 * c + 2];
+    }
+    return 0;
+}
+
+int orc_set_frame(orc_t *s, const double *ux, const double *uy, const double *T)
+{
+    if (!s->frame) return -1;
+    for (long c = 0; c < (long)s->nx * s->ny; ++c) {
+        if (!(T[c] > 0.0)) return -1;
+        s->lam[3 * c] = ux[c];
+        s->lam[3 * c + 1] = uy[c];
+        s->lam[3 * c + 2] = T[c];
     }
     return 0;
 }
@@ -675,18 +873,18 @@ int orc_step_cells(orc_t *s, int m, const long *cells, double *out)
 int orc_moments(const orc_t *s, double *rho, double *ux, double *uy, double *T)
 {
     long nc = (long)s->nx * s->ny;
-    double lat[3] = {0.0, 0.0, 1.0};
     for (long c = 0; c < nc; ++c) {
         int k = s->flag[c];
         double r, a, b, t;
-        macro(&s->L[k], lat, s->f[k] + c * s->L[k].Q, &r, &a, &b, &t);
+        macro(&s->L[k], cell_frame(s, c), s->f[k] + c * s->L[k].Q, &r, &a, &b, &t);
         rho[c] = r; ux[c] = a; uy[c] = b;
         if (T) T[c] = t;
     }
     return 0;
 }
 
-/* Global sums rho, rho u_x, rho u_y, rho E with E = sum v^2/2 f / rho. */
+/* Global sums rho, rho u_x, rho u_y, rho E with E = sum v^2/2 f / rho and
+ * v_i = sqrt(theta) c_i + u of the frame each cell's populations live in. */
 int orc_audit(const orc_t *s, double out[4])
 {
     long nc = (long)s->nx * s->ny;
@@ -694,12 +892,15 @@ int orc_audit(const orc_t *s, double out[4])
     for (long c = 0; c < nc; ++c) {
         int k = s->flag[c];
         const olat *L = &s->L[k];
+        const double *lam = cell_frame(s, c);
+        double st = sqrt(lam[2]);
         for (int i = 0; i < L->Q; ++i) {
             double f = s->f[k][c * L->Q + i];
+            double vx = st * L->cx[i] + lam[0], vy = st * L->cy[i] + lam[1];
             a[0] += f;
-            a[1] += L->cx[i] * f;
-            a[2] += L->cy[i] * f;
-            a[3] += 0.5 * (L->cx[i] * L->cx[i] + L->cy[i] * L->cy[i]) * f;
+            a[1] += vx * f;
+            a[2] += vy * f;
+            a[3] += 0.5 * (vx * vx + vy * vy) * f;
         }
     }
     memcpy(out, a, sizeof(a));
