@@ -57,8 +57,11 @@ typedef struct slbm_s *slbm_t;
 #define SLBM_EINVAL     -1   /* bad argument: sizes, lattice pair, tau, order, side ... */
 #define SLBM_ENOMEM     -2   /* device or host allocation failed / workspace too small */
 #define SLBM_ECUDA      -3   /* a CUDA call failed; the handle is now unusable */
-#define SLBM_ENONFINITE -4   /* the audit found a non-finite sum */
-#define SLBM_ENOCONV    -5   /* reserved: frame iteration did not converge */
+#define SLBM_ENONFINITE -4   /* the audit found a non-finite sum, or a co-moving frame
+                                became non-positive / non-finite or moved a departure
+                                point beyond SLBM_POND_REACH cells (reported once) */
+#define SLBM_ENOCONV    -5   /* a co-moving predictor-corrector stopped at max_iter
+                                (reported once; the handle stays usable) */
 #define SLBM_ETIMEOUT   -6   /* a bounded device wait ran out; the handle is now unusable */
 #define SLBM_ESTATE     -7   /* call not valid in the handle's current state */
 
@@ -67,9 +70,25 @@ typedef struct slbm_s *slbm_t;
 #define SLBM_D2Q16 4
 #define SLBM_D2Q25 5
 
-/* Reference frame of the populations (Sec. II.C): the lattice frame
- * {u = 0, T = T_L}.  (The co-moving frame is not exposed by this version.) */
+/* Reference frame of the populations (Sec. II.C).
+ *  LATTICE  the fixed lattice frame {u = 0, T = T_L}: the athermal
+ *           semi-Lagrangian LBM with the lattice equilibrium f^L (eq. feqL0).
+ *  POND     the co-moving frame {u(x, t), T(x, t)} of every cell (eq. comoving):
+ *           v_i = sqrt(T) c_i + u (eq. vi), collocation vectors carried between
+ *           frames by eq. (fll), the frame found by the predictor-corrector of
+ *           eqs. (correctorfieldsrho-u), collision to rho W_i (eq. feqPond).
+ *           Thermal single-population model: C_v = D/2 (R = 1, D = 2), so the
+ *           g population of eq. (geqPond) vanishes identically and T follows
+ *           from the energy; gamma = 2.
+ *  POND_ISOTHERMAL  the co-moving frame {u(x, t), T_L}: T held at T_L.
+ * The co-moving frames need a periodic grid; the refinement criterion and
+ * boundaries belong to the lattice frame. */
 #define SLBM_FRAME_LATTICE 0
+#define SLBM_FRAME_POND 1
+#define SLBM_FRAME_POND_ISOTHERMAL 2
+
+/* Largest departure distance |v_i| dt, in cells, a co-moving step accepts. */
+#define SLBM_POND_REACH 5
 
 /* Storage / arithmetic precision of the populations. */
 #define SLBM_FP32 0          /* float storage, float arithmetic, FP64 conversion moments */
@@ -122,8 +141,8 @@ SLBM_API int slbm_workspace_bytes(const slbm_grid *g, int lat_lo, int lat_hi, in
 /* Create a handle.  lat_lo < lat_hi are SLBM_D2Q* values; tau > 1/2 is the
  * relaxation time in units of dt (omega = 1/tau, Sec. II.B); interp_order in
  * 1..5 is the Lagrange order (order + 1 collocation points per axis; 3 =
- * the paper's third-order polynomials, Sec. II.C); frame must be
- * SLBM_FRAME_LATTICE; precision SLBM_FP32 or SLBM_FP64; cuda_stream is a
+ * the paper's third-order polynomials, Sec. II.C); frame an SLBM_FRAME_*
+ * value; precision SLBM_FP32 or SLBM_FP64; cuda_stream is a
  * cudaStream_t (NULL = the legacy default stream).  The handle allocates its
  * own device workspace.  Populations start at rest (rho = 1, u = 0), flags 0,
  * criterion none, every non-periodic side OUTFLOW. */
@@ -142,9 +161,10 @@ SLBM_API int slbm_destroy(slbm_t h);
 
 SLBM_API int slbm_get_info(slbm_t h, slbm_info_t *info);
 
-/* Set every cell to the lattice equilibrium f^L(rho, u) (eq. feqL0) of BOTH
- * lattices; flags are kept.  rho, ux, uy: host, nx*ny each; T must be NULL
- * (athermal model, T = T_L). */
+/* Set every cell to the equilibrium of BOTH lattices; flags are kept.
+ * Lattice frame: f^L(rho, u) (eq. feqL0), T must be NULL (athermal model).
+ * Co-moving frames: rho W_i in the frame {u, T} (eq. feqPond); T (host, > 0)
+ * only for SLBM_FRAME_POND, NULL = T_L.  rho, ux, uy: host, nx*ny each. */
 SLBM_API int slbm_init_equilibrium(slbm_t h, const double *rho, const double *ux, const double *uy,
                           const double *T);
 
@@ -155,7 +175,8 @@ SLBM_API int slbm_get_flags(slbm_t h, uint8_t *flags);
 
 /* Refinement criterion (SLBM_CRIT_*), threshold on the Mach number |u| / c_s,
  * c_s = sqrt(T_L) = 1.  SLBM_CRIT_MACH is applied at once to the current
- * state (flips lifted / projected, asynchronous) and after every step. */
+ * state (flips lifted / projected, asynchronous) and after every step.
+ * Lattice frame only (SLBM_EINVAL otherwise). */
 SLBM_API int slbm_set_criterion(slbm_t h, int kind, double threshold);
 
 /* Boundary of a non-periodic side.  Arrays run along the side (ny entries
@@ -171,16 +192,18 @@ SLBM_API int slbm_step(slbm_t h, int n);
 SLBM_API int slbm_sync(slbm_t h);
 
 /* rho, u and the kinetic temperature T = (sum v^2 f / rho - u^2) / 2 of every
- * cell from its own lattice's populations (Sec. II.B).  Host outputs of nx*ny
- * doubles; any pointer may be NULL.  Synchronises. */
+ * cell from its own lattice's populations (Sec. II.B), with the particle
+ * velocities v_i of the frame the populations live in.  Host outputs of nx*ny
+ * doubles; any pointer may be NULL.  Synchronises; returns a pending
+ * SLBM_ENOCONV / SLBM_ENONFINITE report of the co-moving frame. */
 SLBM_API int slbm_moments(slbm_t h, double *rho, double *ux, double *uy, double *T);
 
 /* Same into device arrays of nx*ny doubles (asynchronous; NULL skips). */
 SLBM_API int slbm_moments_device(slbm_t h, double *rho, double *ux, double *uy, double *T);
 
 /* FP64 global sums over all cells: out = {sum rho, sum rho u_x, sum rho u_y,
- * sum rho E}, rho E = sum v^2/2 f.  Returns SLBM_ENONFINITE if any is not
- * finite.  Synchronises. */
+ * sum rho E}, rho E = sum v^2/2 f (v_i of each cell's frame).  Returns
+ * SLBM_ENONFINITE if any is not finite.  Synchronises. */
 SLBM_API int slbm_audit(slbm_t h, double out[4]);
 
 /* Populations of lattice k (0 = lat_lo, 1 = lat_hi) of every cell, host
@@ -194,15 +217,33 @@ SLBM_API int slbm_get_pops(slbm_t h, int k, double *out);
 SLBM_API int slbm_set_pops(slbm_t h, int k, const double *in);
 
 /* Snapshot / restore the full state (populations of both lattices, flags,
- * step count) in a host buffer.  Call with buf = NULL to get the size. */
+ * co-moving frames, step count) in a host buffer.  Call with buf = NULL to get
+ * the size. */
 SLBM_API int slbm_get_state(slbm_t h, void *buf, size_t *bytes);
 SLBM_API int slbm_set_state(slbm_t h, const void *buf, size_t bytes);
+
+/* Co-moving frames only (SLBM_EINVAL for a lattice-frame handle).
+ *
+ * slbm_set_pond: predictor-corrector controls (Sec. II.C): a cell update
+ * repeats the reconstruction until the frame it produces differs from the one
+ * used by at most tol in every one of u_x, u_y, T, or max_iter (1..1000)
+ * reconstructions were made; the last reconstruction's populations and frame
+ * are kept.  Defaults: tol 1e-12 (FP64) / 2e-6 (FP32), max_iter 20.
+ *
+ * slbm_get_frame / slbm_set_frame: the frame {u_x, u_y, T} each cell's
+ * populations live in, host nx*ny doubles each (T > 0; T = 1 for the
+ * isothermal frame).  Setting frames reinterprets the stored populations; set
+ * the frames before slbm_set_pops when writing a state. */
+SLBM_API int slbm_set_pond(slbm_t h, double tol, int max_iter);
+SLBM_API int slbm_get_frame(slbm_t h, double *ux, double *uy, double *T);
+SLBM_API int slbm_set_frame(slbm_t h, const double *ux, const double *uy, const double *T);
 
 /* Per-kernel timing (tracing).  slbm_profile(h, 1) clears previous records
  * and starts bracketing every kernel slbm_step launches with CUDA events on
  * the handle's stream; slbm_profile(h, 0) stops.  slbm_profile_read()
  * synchronises and returns, per kernel of the step sequence (index 0 =
- * stream-collide, 1 = interface conversion, 2 = ghost-ring refresh), the
+ * stream-collide, 1 = interface conversion, 2 = ghost-ring refresh; a
+ * co-moving step has no ghost ring, its index 2 reads 0), the
  * summed device milliseconds over the recorded steps, and the number of
  * recorded steps.  ms must hold SLBM_PROFILE_KERNELS doubles. */
 #define SLBM_PROFILE_KERNELS 3

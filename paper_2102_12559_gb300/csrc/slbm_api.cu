@@ -180,6 +180,7 @@ struct Layout {
   long long plane;           // elements per plane, padded
   size_t pops[2][2];         // byte offsets [buffer][lattice]
   size_t flags[2], flag_tmp, tile_mask[2], macro[4], partials, audit_out, err, bc[4][3];
+  size_t lam[2];             // co-moving frame planes {u_x, u_y, T} per buffer
   size_t total;
 };
 
@@ -248,6 +249,7 @@ Layout make_layout(const slbm_grid* g, int lo, int hi, int order, int precision)
   const size_t side = (size_t)std::max(g->nx, g->ny);
   for (int s = 0; s < 4; ++s)
     for (int q = 0; q < 3; ++q) { Lo.bc[s][q] = off; off = align_up(off + side * 8, 256); }
+  for (int b = 0; b < 2; ++b) { Lo.lam[b] = off; off = align_up(off + 3 * nc * es, 256); }
   Lo.total = off;
   return Lo;
 }
@@ -260,9 +262,15 @@ struct slbm_s {
   CUtensorMap tmap[2][2];        // TMA descriptors of the planes [buffer][lattice]
   slbm_grid g;
   int nlo, nhi, P, precision;
+  int frame;                     // SLBM_FRAME_*
   double tau;
   Params<float> pf;
   Params<double> pd;
+  PondParams<float> qf;          // co-moving frame tables
+  PondParams<double> qd;
+  double pond_tol;
+  int pond_maxit;
+  int pond_mixed;                // both lattices present (interface conversions per step)
   Layout lay;
   cudaStream_t st;
   char* ws;
@@ -285,6 +293,7 @@ struct slbm_s {
   template <class T> T* at(size_t off) { return reinterpret_cast<T*>(ws + off); }
   void* pops(int buf, int k) { return ws + lay.pops[buf][k]; }
   uint8_t* flags(int f) { return at<uint8_t>(lay.flags[f]); }
+  void* lam(int buf) { return ws + lay.lam[buf]; }
   size_t ncell() const { return (size_t)g.nx * g.ny; }
 };
 
@@ -401,16 +410,26 @@ int encode_tmaps(slbm_s* h) {
   return SLBM_OK;
 }
 
-// The device error word: a bounded wait that ran out makes the handle fail.
+// The device error word.  A bounded wait that ran out makes the handle fail;
+// the co-moving frame's reports are returned once and cleared.
 int check_device_error(slbm_s* h) {
   int v = 0;
   SLBM_CK(h, cudaMemcpyAsync(&v, h->at<int>(h->lay.err), sizeof(int), cudaMemcpyDeviceToHost,
                              h->st),
           "D2H copy");
   SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
-  if (v) {
+  if (v & kErrTimeout) {
     h->failed = 1;
     return fail(h, SLBM_ETIMEOUT, "a bounded device wait ran out (TMA copy did not complete)");
+  }
+  if (v) {
+    SLBM_CK(h, cudaMemsetAsync(h->at<int>(h->lay.err), 0, sizeof(int), h->st), "memset");
+    SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+    if (v & kErrFrame)
+      return fail(h, SLBM_ENONFINITE,
+                  "co-moving frame: non-positive or non-finite frame, or a departure point "
+                  "beyond the reach limit");
+    return fail(h, SLBM_ENOCONV, "co-moving frame: predictor-corrector did not converge");
   }
   return SLBM_OK;
 }
@@ -429,7 +448,51 @@ cudaError_t mark(slbm_s* h) {
 
 // One time step: stream-collide (old flags) -> interface conversion (new
 // flags) -> ghost-ring refresh.
+int pond_convert_band(slbm_s* h, int buf) {
+  if (!h->pond_mixed) return SLBM_OK;
+  const uint8_t* mask = h->at<uint8_t>(h->lay.tile_mask[0]);
+  cudaError_t e =
+      h->precision == SLBM_FP64
+          ? launch_pond_convert<double, double>(h->qd, (double*)h->pops(buf, 0),
+                                                (double*)h->pops(buf, 1),
+                                                (const double*)h->lam(buf), h->flags(h->fcur),
+                                                mask, h->st)
+          : launch_pond_convert<float, float>(h->qf, (float*)h->pops(buf, 0),
+                                              (float*)h->pops(buf, 1), (const float*)h->lam(buf),
+                                              h->flags(h->fcur), mask, h->st);
+  SLBM_CK(h, e, "co-moving conversion launch");
+  return SLBM_OK;
+}
+
+// One co-moving-frame step: predictor-corrector stream-collide, then the
+// interface conversions of the new state when both lattices are in use.
+int pond_step_once(slbm_s* h) {
+  const int b = h->cur, nb = b ^ 1;
+  int* err = h->at<int>(h->lay.err);
+  cudaError_t e;
+  SLBM_CK(h, mark(h), "trace event");
+  if (h->precision == SLBM_FP64)
+    e = launch_pond_step<double, double>(h->qd, (const double*)h->pops(b, 0),
+                                         (const double*)h->pops(b, 1), (const double*)h->lam(b),
+                                         (double*)h->pops(nb, 0), (double*)h->pops(nb, 1),
+                                         (double*)h->lam(nb), h->flags(h->fcur), err, h->st);
+  else
+    e = launch_pond_step<float, float>(h->qf, (const float*)h->pops(b, 0),
+                                       (const float*)h->pops(b, 1), (const float*)h->lam(b),
+                                       (float*)h->pops(nb, 0), (float*)h->pops(nb, 1),
+                                       (float*)h->lam(nb), h->flags(h->fcur), err, h->st);
+  SLBM_CK(h, e, "co-moving step launch");
+  SLBM_CK(h, mark(h), "trace event");
+  if (int rc = pond_convert_band(h, nb)) return rc;
+  SLBM_CK(h, mark(h), "trace event");
+  SLBM_CK(h, mark(h), "trace event");
+  h->cur = nb;
+  h->steps++;
+  return SLBM_OK;
+}
+
 int step_once(slbm_s* h) {
+  if (h->frame != SLBM_FRAME_LATTICE) return pond_step_once(h);
   const int b = h->cur, nb = b ^ 1;
   uint8_t* fold = h->flags(h->fcur);
   uint8_t* fnew = h->crit ? h->flags(h->fcur ^ 1) : fold;
@@ -504,11 +567,52 @@ void fill_params(Params<R>& p, const slbm_s* h, const Lattice1D& a, const Lattic
     for (int aa = 0; aa < b.n; ++aa) t.proj[j][aa] = (R)lagrange_eval(a.c, a.n, j, b.c[aa]);
 }
 
+template <class R>
+void fill_pond(PondParams<R>& q, const slbm_s* h, const Params<R>& p, const Lattice1D& a,
+               const Lattice1D& b, double dt) {
+  std::memset(&q, 0, sizeof(q));
+  q.nx = h->g.nx;
+  q.ny = h->g.ny;
+  q.G = h->lay.G;
+  q.pitch = h->lay.pitch;
+  q.plane = h->lay.plane;
+  q.nc = (long long)h->g.nx * h->g.ny;
+  q.omega = (R)(1.0 / h->tau);
+  q.dt = (R)dt;
+  q.tol = (R)h->pond_tol;
+  q.maxit = h->pond_maxit;
+  q.thermal = h->frame == SLBM_FRAME_POND ? 1 : 0;
+  q.P = h->P;
+  q.reach = (R)kPondReach;
+  for (int k = 0; k < 2; ++k) {
+    const Lattice1D& L = k ? b : a;
+    PondLat<R>& T = q.lat[k];
+    T.n = L.n;
+    for (int j = 0; j < L.n; ++j) {
+      T.c[j] = (R)L.c[j];
+      T.w[j] = (R)L.w[j];
+      for (int m = 0; m < L.n; ++m) {
+        T.inv[j][m] = m == j ? R(0) : (R)(1.0 / (L.c[j] - L.c[m]));
+        T.vinv[j][m] = (R)L.vinv[j][m];
+      }
+    }
+  }
+  for (int j = 0; j < kMaxN; ++j)
+    for (int m = 0; m < kMaxN; ++m) q.proj[j][m] = p.conv.proj[j][m];
+}
+
 void refresh_params(slbm_s* h) {
   const Lattice1D a = make_1d(h->nlo), b = make_1d(h->nhi);
   const double dt = pair_dt(a, b);
   fill_params(h->pf, h, a, b, dt);
   fill_params(h->pd, h, a, b, dt);
+  fill_pond(h->qf, h, h->pf, a, b, dt);
+  fill_pond(h->qd, h, h->pd, a, b, dt);
+}
+
+// Frame planes of the current buffer, or null in the lattice frame.
+const void* frame_planes(slbm_s* h) {
+  return h->frame != SLBM_FRAME_LATTICE ? h->lam(h->cur) : nullptr;
 }
 
 int upload(slbm_s* h, void* dst, const void* src, size_t bytes) {
@@ -556,11 +660,23 @@ int pack_any(slbm_s* h, int k, double* host, int unpack, const double* in) {
                                    : pack_all<float, float>(h, h->pf, k, host, unpack, in);
 }
 
-int init_eq_dev(slbm_s* h) {
+int init_eq_dev(slbm_s* h, bool with_T = false) {
   cudaError_t e;
   double* r = h->at<double>(h->lay.macro[0]);
   double* u = h->at<double>(h->lay.macro[1]);
   double* v = h->at<double>(h->lay.macro[2]);
+  if (h->frame != SLBM_FRAME_LATTICE) {
+    const double* T = with_T ? h->at<double>(h->lay.macro[3]) : nullptr;
+    e = h->precision == SLBM_FP64
+            ? launch_pond_init<double, double>(h->qd, (double*)h->pops(h->cur, 0),
+                                               (double*)h->pops(h->cur, 1),
+                                               (double*)h->lam(h->cur), r, u, v, T, h->st)
+            : launch_pond_init<float, float>(h->qf, (float*)h->pops(h->cur, 0),
+                                             (float*)h->pops(h->cur, 1), (float*)h->lam(h->cur),
+                                             r, u, v, T, h->st);
+    SLBM_CK(h, e, "init launch");
+    return SLBM_OK;
+  }
   if (h->precision == SLBM_FP64)
     e = launch_init_eq<double, double>(h->pd, (double*)h->pops(h->cur, 0),
                                        (double*)h->pops(h->cur, 1), r,
@@ -583,8 +699,13 @@ bool create_args_ok(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int 
     snprintf(g_create_err, sizeof(g_create_err), "tau must be a finite value > 1/2");
     return false;
   }
-  if (frame != SLBM_FRAME_LATTICE) {
-    snprintf(g_create_err, sizeof(g_create_err), "only SLBM_FRAME_LATTICE is supported");
+  if (frame != SLBM_FRAME_LATTICE && frame != SLBM_FRAME_POND &&
+      frame != SLBM_FRAME_POND_ISOTHERMAL) {
+    snprintf(g_create_err, sizeof(g_create_err), "unknown frame");
+    return false;
+  }
+  if (frame != SLBM_FRAME_LATTICE && !(g->periodic_x && g->periodic_y)) {
+    snprintf(g_create_err, sizeof(g_create_err), "the co-moving frame needs a periodic grid");
     return false;
   }
   const Layout lay = make_layout(g, lat_lo, lat_hi, interp_order, precision);
@@ -660,6 +781,9 @@ int slbm_create_in(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int i
   h->nhi = lat_hi;
   h->P = interp_order + 1;
   h->precision = precision;
+  h->frame = frame;
+  h->pond_tol = precision == SLBM_FP64 ? 1e-12 : 2e-6;
+  h->pond_maxit = 20;
   h->tau = tau;
   h->lay = lay;
   h->st = (cudaStream_t)cuda_stream;
@@ -738,7 +862,8 @@ int slbm_get_info(slbm_t h, slbm_info_t* info) {
   info->pitch = h->lay.pitch;
   info->rows = h->lay.rows;
   info->precision = h->precision;
-  info->kernels_per_step = 3;
+  info->kernels_per_step =
+      h->frame == SLBM_FRAME_LATTICE ? 3 : (h->pond_mixed ? 2 : 1);
   info->workspace_bytes = h->lay.total;
   info->steps = h->steps;
   return SLBM_OK;
@@ -748,13 +873,18 @@ int slbm_init_equilibrium(slbm_t h, const double* rho, const double* ux, const d
                           const double* T) {
   SLBM_GUARD(h);
   if (!rho || !ux || !uy) return fail(h, SLBM_EINVAL, "rho, ux, uy are required");
-  if (T) return fail(h, SLBM_EINVAL, "the athermal lattice-frame model takes T = NULL");
+  if (T && h->frame != SLBM_FRAME_POND)
+    return fail(h, SLBM_EINVAL, "only the thermal co-moving model takes T; pass NULL");
   const size_t b = h->ncell() * 8;
   int rc;
+  if (T)
+    for (size_t c = 0; c < h->ncell(); ++c)
+      if (!(T[c] > 0.0) || !std::isfinite(T[c])) return fail(h, SLBM_EINVAL, "T must be > 0");
   if ((rc = upload(h, h->at<double>(h->lay.macro[0]), rho, b))) return rc;
   if ((rc = upload(h, h->at<double>(h->lay.macro[1]), ux, b))) return rc;
   if ((rc = upload(h, h->at<double>(h->lay.macro[2]), uy, b))) return rc;
-  if ((rc = init_eq_dev(h))) return rc;
+  if (T && (rc = upload(h, h->at<double>(h->lay.macro[3]), T, b))) return rc;
+  if ((rc = init_eq_dev(h, T != nullptr))) return rc;
   // the caller may reuse its arrays on return
   SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
   return SLBM_OK;
@@ -768,6 +898,33 @@ int slbm_set_flags(slbm_t h, const uint8_t* flags) {
   uint8_t* tmp = h->at<uint8_t>(h->lay.flag_tmp);
   int rc;
   if ((rc = upload(h, tmp, norm.data(), norm.size()))) return rc;
+  if (h->frame != SLBM_FRAME_LATTICE) {
+    // every cell's other lattice from its current one (flipped cells take it
+    // as their new native vector), then the new flags, masks and band
+    cudaError_t e =
+        h->precision == SLBM_FP64
+            ? launch_pond_convert<double, double>(h->qd, (double*)h->pops(h->cur, 0),
+                                                  (double*)h->pops(h->cur, 1),
+                                                  (const double*)h->lam(h->cur),
+                                                  h->flags(h->fcur), nullptr, h->st)
+            : launch_pond_convert<float, float>(h->qf, (float*)h->pops(h->cur, 0),
+                                                (float*)h->pops(h->cur, 1),
+                                                (const float*)h->lam(h->cur), h->flags(h->fcur),
+                                                nullptr, h->st);
+    SLBM_CK(h, e, "co-moving conversion launch");
+    SLBM_CK(h, cudaMemcpyAsync(h->flags(h->fcur), tmp, norm.size(), cudaMemcpyDeviceToDevice,
+                               h->st),
+            "flag copy");
+    SLBM_CK(h, launch_pond_masks(h->g.nx, h->g.ny, h->flags(h->fcur),
+                                 h->at<uint8_t>(h->lay.tile_mask[0]), h->st),
+            "mask launch");
+    bool any0 = false, any1 = false;
+    for (uint8_t v : norm) (v ? any1 : any0) = true;
+    h->pond_mixed = any0 && any1;
+    if ((rc = pond_convert_band(h, h->cur))) return rc;
+    SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+    return SLBM_OK;
+  }
   SLBM_CK(h, convert(h, h->cur, h->flags(h->fcur), tmp), "convert launch");
   SLBM_CK(h, cudaMemcpyAsync(h->flags(h->fcur), tmp, norm.size(), cudaMemcpyDeviceToDevice, h->st),
           "flag copy");
@@ -790,6 +947,8 @@ int slbm_set_criterion(slbm_t h, int kind, double threshold) {
   SLBM_GUARD(h);
   if ((kind != SLBM_CRIT_NONE && kind != SLBM_CRIT_MACH) || !(threshold >= 0.0))
     return fail(h, SLBM_EINVAL, "criterion kind or threshold invalid");
+  if (kind != SLBM_CRIT_NONE && h->frame != SLBM_FRAME_LATTICE)
+    return fail(h, SLBM_EINVAL, "the Mach criterion belongs to the lattice frame");
   // flags live in buffer fcur either way; the other buffer is scratch
   h->crit = kind;
   h->thr = threshold;
@@ -860,11 +1019,11 @@ int slbm_moments_device(slbm_t h, double* rho, double* ux, double* uy, double* T
   if (h->precision == SLBM_FP64)
     e = launch_moments<double, double>(h->pd, (const double*)h->pops(h->cur, 0),
                                (const double*)h->pops(h->cur, 1), h->flags(h->fcur), rho, ux, uy, T,
-                               h->st);
+                               (const double*)frame_planes(h), h->st);
   else
     e = launch_moments<float, float>(h->pf, (const float*)h->pops(h->cur, 0),
                               (const float*)h->pops(h->cur, 1), h->flags(h->fcur), rho, ux, uy, T,
-                              h->st);
+                              (const float*)frame_planes(h), h->st);
   SLBM_CK(h, e, "moments launch");
   return SLBM_OK;
 }
@@ -895,11 +1054,11 @@ int slbm_audit(slbm_t h, double out[4]) {
   if (h->precision == SLBM_FP64)
     e = launch_audit<double, double>(h->pd, (const double*)h->pops(h->cur, 0),
                              (const double*)h->pops(h->cur, 1), h->flags(h->fcur), part, np, res,
-                             h->st);
+                             (const double*)frame_planes(h), h->st);
   else
     e = launch_audit<float, float>(h->pf, (const float*)h->pops(h->cur, 0),
                             (const float*)h->pops(h->cur, 1), h->flags(h->fcur), part, np, res,
-                            h->st);
+                            (const float*)frame_planes(h), h->st);
   SLBM_CK(h, e, "audit launch");
   SLBM_CK(h, cudaMemcpyAsync(out, res, 32, cudaMemcpyDeviceToHost, h->st), "D2H copy");
   SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
@@ -920,6 +1079,7 @@ int slbm_set_pops(slbm_t h, int k, const double* in) {
   if ((k != 0 && k != 1) || !in) return fail(h, SLBM_EINVAL, "lattice index or input invalid");
   int rc = pack_any(h, k, nullptr, 1, in);
   if (rc) return rc;
+  if (h->frame != SLBM_FRAME_LATTICE) return pond_convert_band(h, h->cur);
   SLBM_CK(h, convert(h, h->cur, h->flags(h->fcur), h->flags(h->fcur)), "post-step launch");
   SLBM_CK(h, ghosts(h, h->flags(h->fcur)), "ghost launch");
   return SLBM_OK;
@@ -937,14 +1097,15 @@ int slbm_get_state(slbm_t h, void* buf, size_t* bytes) {
   SLBM_GUARD(h);
   if (!bytes) return fail(h, SLBM_EINVAL, "bytes is required");
   const size_t nc = h->ncell();
+  const size_t nframe = h->frame != SLBM_FRAME_LATTICE ? 3 * nc * 8 : 0;
   const size_t need =
-      sizeof(StateHeader) + nc + nc * 8 * (size_t)(h->nlo * h->nlo + h->nhi * h->nhi);
+      sizeof(StateHeader) + nc + nc * 8 * (size_t)(h->nlo * h->nlo + h->nhi * h->nhi) + nframe;
   if (!buf) { *bytes = need; return SLBM_OK; }
   if (*bytes < need) return fail(h, SLBM_EINVAL, "state buffer too small");
   StateHeader hd{};
   std::memcpy(hd.magic, "SLBMST1", 8);
   hd.nx = h->g.nx; hd.ny = h->g.ny; hd.nlo = h->nlo; hd.nhi = h->nhi;
-  hd.precision = h->precision; hd.steps = h->steps;
+  hd.precision = h->precision; hd.pad = h->frame; hd.steps = h->steps;
   char* p = (char*)buf;
   std::memcpy(p, &hd, sizeof(hd));
   int rc = slbm_get_flags(h, (uint8_t*)(p + sizeof(hd)));
@@ -952,6 +1113,10 @@ int slbm_get_state(slbm_t h, void* buf, size_t* bytes) {
   double* pops = (double*)(p + sizeof(hd) + nc);
   if ((rc = slbm_get_pops(h, 0, pops))) return rc;
   if ((rc = slbm_get_pops(h, 1, pops + nc * h->nlo * h->nlo))) return rc;
+  if (nframe) {
+    double* fr = pops + nc * (size_t)(h->nlo * h->nlo + h->nhi * h->nhi);
+    if ((rc = slbm_get_frame(h, fr, fr + nc, fr + 2 * nc))) return rc;
+  }
   *bytes = need;
   return SLBM_OK;
 }
@@ -959,26 +1124,107 @@ int slbm_get_state(slbm_t h, void* buf, size_t* bytes) {
 int slbm_set_state(slbm_t h, const void* buf, size_t bytes) {
   SLBM_GUARD(h);
   const size_t nc = h->ncell();
+  const size_t nframe = h->frame != SLBM_FRAME_LATTICE ? 3 * nc * 8 : 0;
   const size_t need =
-      sizeof(StateHeader) + nc + nc * 8 * (size_t)(h->nlo * h->nlo + h->nhi * h->nhi);
+      sizeof(StateHeader) + nc + nc * 8 * (size_t)(h->nlo * h->nlo + h->nhi * h->nhi) + nframe;
   if (!buf || bytes < need) return fail(h, SLBM_EINVAL, "state buffer too small");
   StateHeader hd;
   std::memcpy(&hd, buf, sizeof(hd));
   if (std::memcmp(hd.magic, "SLBMST1", 8) || hd.nx != h->g.nx || hd.ny != h->g.ny ||
-      hd.nlo != h->nlo || hd.nhi != h->nhi || hd.precision != h->precision)
+      hd.nlo != h->nlo || hd.nhi != h->nhi || hd.precision != h->precision ||
+      hd.pad != h->frame)
     return fail(h, SLBM_EINVAL, "state does not match this handle");
   const char* p = (const char*)buf;
   int rc;
-  if ((rc = upload(h, h->flags(h->fcur), p + sizeof(hd), nc))) return rc;
+  if (h->frame != SLBM_FRAME_LATTICE) {
+    // flags (with their masks), frames, then populations and band conversions
+    std::vector<uint8_t> fl((const uint8_t*)(p + sizeof(hd)), (const uint8_t*)(p + sizeof(hd)) + nc);
+    if ((rc = upload(h, h->flags(h->fcur), fl.data(), nc))) return rc;
+    SLBM_CK(h, launch_pond_masks(h->g.nx, h->g.ny, h->flags(h->fcur),
+                                 h->at<uint8_t>(h->lay.tile_mask[0]), h->st),
+            "mask launch");
+    bool any0 = false, any1 = false;
+    for (uint8_t v : fl) (v ? any1 : any0) = true;
+    h->pond_mixed = any0 && any1;
+    const double* fr =
+        (const double*)(p + sizeof(hd) + nc) + nc * (size_t)(h->nlo * h->nlo + h->nhi * h->nhi);
+    if ((rc = slbm_set_frame(h, fr, fr + nc, fr + 2 * nc))) return rc;
+  } else if ((rc = upload(h, h->flags(h->fcur), p + sizeof(hd), nc))) {
+    return rc;
+  }
   const double* pops = (const double*)(p + sizeof(hd) + nc);
   if ((rc = pack_any(h, 0, nullptr, 1, pops))) return rc;
   if ((rc = pack_any(h, 1, nullptr, 1, pops + nc * h->nlo * h->nlo))) return rc;
-  // masks from the restored flags; the restored band populations are the
-  // conversions of the restored native ones, so recomputing them is exact
-  SLBM_CK(h, convert(h, h->cur, h->flags(h->fcur), h->flags(h->fcur)), "post-step launch");
-  SLBM_CK(h, ghosts(h, h->flags(h->fcur)), "ghost launch");
+  if (h->frame != SLBM_FRAME_LATTICE) {
+    if ((rc = pond_convert_band(h, h->cur))) return rc;
+  } else {
+    // masks from the restored flags; the restored band populations are the
+    // conversions of the restored native ones, so recomputing them is exact
+    SLBM_CK(h, convert(h, h->cur, h->flags(h->fcur), h->flags(h->fcur)), "post-step launch");
+    SLBM_CK(h, ghosts(h, h->flags(h->fcur)), "ghost launch");
+  }
   SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
   h->steps = hd.steps;
+  return SLBM_OK;
+}
+
+int slbm_set_pond(slbm_t h, double tol, int max_iter) {
+  SLBM_GUARD(h);
+  if (h->frame == SLBM_FRAME_LATTICE) return fail(h, SLBM_EINVAL, "lattice-frame handle");
+  if (!(tol >= 0.0) || !std::isfinite(tol) || max_iter < 1 || max_iter > 1000)
+    return fail(h, SLBM_EINVAL, "tol must be >= 0 and max_iter in 1..1000");
+  h->pond_tol = tol;
+  h->pond_maxit = max_iter;
+  refresh_params(h);
+  return SLBM_OK;
+}
+
+int slbm_get_frame(slbm_t h, double* ux, double* uy, double* T) {
+  SLBM_GUARD(h);
+  if (h->frame == SLBM_FRAME_LATTICE) return fail(h, SLBM_EINVAL, "lattice-frame handle");
+  if (!ux || !uy || !T) return fail(h, SLBM_EINVAL, "outputs are required");
+  double* d[3];
+  for (int q = 0; q < 3; ++q) d[q] = h->at<double>(h->lay.macro[q]);
+  cudaError_t e =
+      h->precision == SLBM_FP64
+          ? launch_pond_frame_io<double, double>(h->qd, (double*)h->lam(h->cur), d[0], d[1], d[2],
+                                                 0, h->st)
+          : launch_pond_frame_io<float, float>(h->qf, (float*)h->lam(h->cur), d[0], d[1], d[2], 0,
+                                               h->st);
+  SLBM_CK(h, e, "frame pack launch");
+  double* out[3] = {ux, uy, T};
+  for (int q = 0; q < 3; ++q)
+    SLBM_CK(h, cudaMemcpyAsync(out[q], d[q], h->ncell() * 8, cudaMemcpyDeviceToHost, h->st),
+            "D2H copy");
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  return SLBM_OK;
+}
+
+int slbm_set_frame(slbm_t h, const double* ux, const double* uy, const double* T) {
+  SLBM_GUARD(h);
+  if (h->frame == SLBM_FRAME_LATTICE) return fail(h, SLBM_EINVAL, "lattice-frame handle");
+  if (!ux || !uy || !T) return fail(h, SLBM_EINVAL, "inputs are required");
+  const size_t nc = h->ncell();
+  for (size_t c = 0; c < nc; ++c) {
+    if (!(T[c] > 0.0) || !std::isfinite(T[c]) || !std::isfinite(ux[c]) || !std::isfinite(uy[c]))
+      return fail(h, SLBM_EINVAL, "frames must be finite with T > 0");
+    if (h->frame == SLBM_FRAME_POND_ISOTHERMAL && T[c] != 1.0)
+      return fail(h, SLBM_EINVAL, "the isothermal frame has T = T_L = 1");
+  }
+  double* d[3];
+  for (int q = 0; q < 3; ++q) d[q] = h->at<double>(h->lay.macro[q]);
+  const double* in[3] = {ux, uy, T};
+  for (int q = 0; q < 3; ++q)
+    if (int rc = upload(h, d[q], in[q], nc * 8)) return rc;
+  cudaError_t e =
+      h->precision == SLBM_FP64
+          ? launch_pond_frame_io<double, double>(h->qd, (double*)h->lam(h->cur), d[0], d[1], d[2],
+                                                 1, h->st)
+          : launch_pond_frame_io<float, float>(h->qf, (float*)h->lam(h->cur), d[0], d[1], d[2], 1,
+                                               h->st);
+  SLBM_CK(h, e, "frame unpack launch");
+  if (int rc = pond_convert_band(h, h->cur)) return rc;
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
   return SLBM_OK;
 }
 
@@ -1011,3 +1257,5 @@ int slbm_profile_read(slbm_t h, double* ms, long long* steps) {
 const char* slbm_last_error(slbm_t h) { return h ? h->err : g_create_err; }
 
 }  // extern "C"
+
+static_assert(slbm::kPondReach == SLBM_POND_REACH, "co-moving reach limit mismatch");

@@ -79,6 +79,44 @@ struct Params {
   ConvTab<R> conv;
 };
 
+// Co-moving (PonD) frame, Sec. II.C.  Every cell keeps its populations (as
+// deviations from W_i) in its own frame lambda = {u_x, u_y, T}, stored in three
+// dense nx*ny planes (stride nc).  Grids are periodic; indices wrap.
+template <class R>
+struct PondLat {
+  int n;
+  R c[kMaxN];                   // 1-D velocities at T_L = 1
+  R w[kMaxN];                   // 1-D weights
+  R inv[kMaxN][kMaxN];          // 1 / (c_a - c_m) for a != m (Lagrange basis on the nodes)
+  R vinv[kMaxN][kMaxN];         // inverse Vandermonde: phi_a = sum_m vinv[a][m] h_m
+};
+
+template <class R>
+struct PondParams {
+  int nx, ny, G, pitch;
+  long long plane;              // population plane stride (elements)
+  long long nc;                 // frame plane stride (nx * ny)
+  R omega, dt;
+  R tol;                        // predictor-corrector tolerance on |du|, |dT|
+  int maxit;                    // reconstructions per cell update at most
+  int thermal;                  // 1: T from the energy (C_v = D/2); 0: T = T_L
+  int P;                        // collocation points per axis
+  R reach;                      // largest departure distance allowed, cells
+  PondLat<R> lat[2];
+  R proj[kMaxN][kMaxN];         // P[j][A], as ConvTab (frame-independent)
+};
+
+// Largest co-moving departure distance, cells.  Interface conversions cover
+// the 3 x 3 tile neighbourhood of every tile (tiles are kTY = 8 rows high), so
+// a stencil node may lie at most 8 rows away: reach + (P + 1) / 2 <= 8 for
+// P <= 6.
+constexpr double kPondReach = 5.0;
+
+// Device error word bits.
+constexpr int kErrTimeout = 1;  // a bounded wait ran out (the handle fails)
+constexpr int kErrNoConv = 2;   // a co-moving predictor-corrector stopped at maxit
+constexpr int kErrFrame = 4;    // non-positive / non-finite frame, or departure beyond reach
+
 // Boundary description (device arrays of the prescribed states, may be null).
 struct BcDev {
   int kind[4];                  // per side SLBM_BC_*
@@ -86,6 +124,26 @@ struct BcDev {
   const double* ux[4];
   const double* uy[4];
 };
+
+// Co-moving frame launchers (slbm_pond.cu).  lam: three frame planes.
+template <class S, class R>
+cudaError_t launch_pond_init(const PondParams<R>& p, S* f0, S* f1, S* lam, const double* rho,
+                             const double* ux, const double* uy, const double* T,
+                             cudaStream_t st);
+template <class S, class R>
+cudaError_t launch_pond_step(const PondParams<R>& p, const S* f0, const S* f1, const S* lam,
+                             S* g0, S* g1, S* lam_out, const uint8_t* flag, int* err,
+                             cudaStream_t st);
+cudaError_t launch_pond_masks(int nx, int ny, const uint8_t* flag, uint8_t* mask,
+                              cudaStream_t st);
+// mask null: convert every cell; else the cells of tiles whose 3 x 3 tile
+// neighbourhood holds both lattices.
+template <class S, class R>
+cudaError_t launch_pond_convert(const PondParams<R>& p, S* f0, S* f1, const S* lam,
+                                const uint8_t* flag, const uint8_t* mask, cudaStream_t st);
+template <class S, class R>
+cudaError_t launch_pond_frame_io(const PondParams<R>& p, S* lam, double* ux, double* uy,
+                                 double* T, int unpack, cudaStream_t st);
 
 // Launchers (defined in the kernel translation units).  S = storage type,
 // R = arithmetic type.  f0 / f1: base of one buffer for lattice 0 / 1.
@@ -134,7 +192,8 @@ cudaError_t launch_init_eq(const Params<R>& p, S* f0, S* f1, const double* rho,
 
 template <class S, class R>
 cudaError_t launch_moments(const Params<R>& p, const S* f0, const S* f1, const uint8_t* flag,
-                           double* rho, double* ux, double* uy, double* T, cudaStream_t st);
+                           double* rho, double* ux, double* uy, double* T, const S* lam,
+                           cudaStream_t st);
 
 template <class S, class R>
 cudaError_t launch_criterion(const Params<R>& p, const S* f0, const S* f1, const uint8_t* flag,
@@ -142,7 +201,8 @@ cudaError_t launch_criterion(const Params<R>& p, const S* f0, const S* f1, const
 
 template <class S, class R>
 cudaError_t launch_audit(const Params<R>& p, const S* f0, const S* f1, const uint8_t* flag,
-                         double* partials, int nparts, double* out4, cudaStream_t st);
+                         double* partials, int nparts, double* out4, const S* lam,
+                         cudaStream_t st);
 
 template <class S, class R>
 cudaError_t launch_pack(const Params<R>& p, int k, int i0, int cnt, const S* f, double* out,

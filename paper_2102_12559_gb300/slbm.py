@@ -21,7 +21,8 @@ from . import _build
 SLBM_OK, SLBM_EINVAL, SLBM_ENOMEM, SLBM_ECUDA = 0, -1, -2, -3
 SLBM_ENONFINITE, SLBM_ENOCONV, SLBM_ETIMEOUT, SLBM_ESTATE = -4, -5, -6, -7
 SLBM_D2Q9, SLBM_D2Q16, SLBM_D2Q25 = 3, 4, 5
-SLBM_FRAME_LATTICE = 0
+SLBM_FRAME_LATTICE, SLBM_FRAME_POND, SLBM_FRAME_POND_ISOTHERMAL = 0, 1, 2
+SLBM_POND_REACH = 5
 SLBM_FP32, SLBM_FP64 = 0, 1
 SLBM_BC_OUTFLOW, SLBM_BC_DIRICHLET, SLBM_BC_INLET = 0, 1, 2
 SLBM_SIDE_XMIN, SLBM_SIDE_XMAX, SLBM_SIDE_YMIN, SLBM_SIDE_YMAX = 0, 1, 2, 3
@@ -33,6 +34,7 @@ EXPORTS = [
     "slbm_set_boundary", "slbm_step", "slbm_sync", "slbm_moments", "slbm_moments_device",
     "slbm_audit", "slbm_get_pops", "slbm_set_pops", "slbm_get_state", "slbm_set_state",
     "slbm_profile", "slbm_profile_read", "slbm_audit_dense_noalloc", "slbm_last_error",
+    "slbm_set_pond", "slbm_get_frame", "slbm_set_frame",
 ]
 SLBM_PROFILE_KERNELS = 3
 KERNEL_NAMES = ("stream_collide", "interface_convert", "halo")
@@ -99,6 +101,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.slbm_profile_read.argtypes = [p, p, P(ctypes.c_longlong)]
     L.slbm_audit_dense_noalloc.argtypes = [p, i, i, i, p, p]
     L.slbm_last_error.argtypes = [p]
+    L.slbm_set_pond.argtypes = [p, d, i]
+    L.slbm_get_frame.argtypes = [p, p, p, p]
+    L.slbm_set_frame.argtypes = [p, p, p, p]
     L.slbm_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name != "slbm_last_error":
@@ -167,9 +172,26 @@ def slbm_get_info(h) -> slbm_info_t:
     return info
 
 
-def slbm_init_equilibrium(h, n, rho, ux, uy):
+def slbm_init_equilibrium(h, n, rho, ux, uy, T=None):
     r, a, b = _f64(rho, n), _f64(ux, n), _f64(uy, n)
-    _check(load().slbm_init_equilibrium(h, _ptr(r), _ptr(a), _ptr(b), None), h)
+    t = None if T is None else _f64(T, n)
+    _check(load().slbm_init_equilibrium(h, _ptr(r), _ptr(a), _ptr(b),
+                                        None if t is None else _ptr(t)), h)
+
+
+def slbm_set_pond(h, tol, max_iter):
+    _check(load().slbm_set_pond(h, float(tol), int(max_iter)), h)
+
+
+def slbm_get_frame(h, n):
+    out = [np.zeros(n) for _ in range(3)]
+    _check(load().slbm_get_frame(h, *(_ptr(a) for a in out)), h)
+    return out
+
+
+def slbm_set_frame(h, n, ux, uy, T):
+    a, b, t = _f64(ux, n), _f64(uy, n), _f64(T, n)
+    _check(load().slbm_set_frame(h, _ptr(a), _ptr(b), _ptr(t)), h)
 
 
 def slbm_set_flags(h, n, flags):
@@ -277,7 +299,8 @@ class Solver:
     (ny, nx) numpy arrays, x fastest."""
 
     def __init__(self, nx, ny, lat_lo=SLBM_D2Q9, lat_hi=SLBM_D2Q25, tau=0.6, interp_order=3,
-                 periodic=(True, True), precision=SLBM_FP32, stream=None, torch_workspace=True):
+                 periodic=(True, True), precision=SLBM_FP32, stream=None, torch_workspace=True,
+                 frame=SLBM_FRAME_LATTICE):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("slbm.Solver needs a CUDA device (no CPU fallback)")
@@ -286,6 +309,7 @@ class Solver:
         self.lat = (lat_lo, lat_hi)
         self.Q = (lat_lo * lat_lo, lat_hi * lat_hi)
         self.precision = precision
+        self.frame = frame
         st = torch.cuda.current_stream() if stream is None else stream
         self.stream = st
         self._ws = None
@@ -295,11 +319,11 @@ class Solver:
             self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
             ptr = (self._ws.data_ptr() + 255) // 256 * 256
             self.h = slbm_create_in(nx, ny, periodic[0], periodic[1], lat_lo, lat_hi, tau,
-                                    interp_order, SLBM_FRAME_LATTICE, precision, st.cuda_stream,
+                                    interp_order, frame, precision, st.cuda_stream,
                                     ptr, nbytes)
         else:
             self.h = slbm_create(nx, ny, periodic[0], periodic[1], lat_lo, lat_hi, tau,
-                                 interp_order, SLBM_FRAME_LATTICE, precision, st.cuda_stream)
+                                 interp_order, frame, precision, st.cuda_stream)
 
     def close(self):
         if getattr(self, "h", None) is not None:
@@ -321,8 +345,21 @@ class Solver:
     def dt(self) -> float:
         return self.info.dt
 
-    def init_equilibrium(self, rho, ux, uy):
-        slbm_init_equilibrium(self.h, self.n, rho, ux, uy)
+    def init_equilibrium(self, rho, ux, uy, T=None):
+        if T is not None:
+            T = np.broadcast_to(np.asarray(T, dtype=np.float64), (self.ny, self.nx))
+        slbm_init_equilibrium(self.h, self.n, rho, ux, uy, T)
+
+    def set_pond(self, tol, max_iter):
+        slbm_set_pond(self.h, tol, max_iter)
+
+    def get_frame(self):
+        s = (self.ny, self.nx)
+        return tuple(a.reshape(s) for a in slbm_get_frame(self.h, self.n))
+
+    def set_frame(self, ux, uy, T):
+        b = lambda v: np.broadcast_to(np.asarray(v, dtype=np.float64), (self.ny, self.nx))
+        slbm_set_frame(self.h, self.n, b(ux), b(uy), b(T))
 
     def set_flags(self, flags):
         slbm_set_flags(self.h, self.n, flags)

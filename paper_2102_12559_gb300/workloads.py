@@ -61,6 +61,19 @@ def perturbed(nx: int, ny: int, seed: int, amp_rho: float = 0.02, amp_u: float =
     return rho, ux, uy
 
 
+def perturbed_T(nx: int, ny: int, seed: int, amp: float = 0.05, T0: float = 1.0):
+    """Smooth random temperature field (a few seeded Fourier modes around T0),
+    for the thermal co-moving frame."""
+    rng = np.random.default_rng(seed)
+    X, Y = np.meshgrid(np.arange(nx, dtype=np.float64), np.arange(ny, dtype=np.float64))
+    T = np.full((ny, nx), T0)
+    for _ in range(3):
+        kx, ky = rng.integers(1, 3, size=2)
+        ph, a = rng.uniform(0, 2 * math.pi), rng.uniform(0.5, 1.0)
+        T += amp * a * np.sin(2 * math.pi * (kx * X / nx + ky * Y / ny) + ph) / 3
+    return T
+
+
 def random_flags(nx: int, ny: int, seed: int, blobs: int = 3, rmin: float = 3.0, rmax: float = 8.0):
     """A few random discs (periodic distance) of high-order cells."""
     rng = np.random.default_rng(seed)

@@ -47,13 +47,16 @@ def test_workspace_bytes_host_only(lib):
     dict(interp_order=0),
     dict(interp_order=6),
     dict(precision=7),
-    dict(frame=1),
+    dict(frame=3),                       # unknown frame
+    dict(frame=1, periodic_y=0),         # the co-moving frame needs a periodic grid
+    dict(frame=2, periodic_x=0),
     dict(nx=0),
 ])
 def test_invalid_arguments_rejected_before_cuda(lib, args):
-    a = dict(nx=32, ny=32, lat_lo=3, lat_hi=5, tau=0.6, interp_order=3, frame=0, precision=0)
+    a = dict(nx=32, ny=32, lat_lo=3, lat_hi=5, tau=0.6, interp_order=3, frame=0, precision=0,
+             periodic_x=1, periodic_y=1)
     a.update(args)
-    g = slbm.slbm_grid(a["nx"], 32, 1, 1)
+    g = slbm.slbm_grid(a["nx"], 32, a["periodic_x"], a["periodic_y"])
     h = ctypes.c_void_p()
     rc = lib.slbm_create(ctypes.byref(g), a["lat_lo"], a["lat_hi"], a["tau"], a["interp_order"],
                          a["frame"], a["precision"], None, ctypes.byref(h))
@@ -70,13 +73,14 @@ def test_null_handle_calls_fail_cleanly(lib):
 
 @pytest.mark.parametrize("lo,hi", [(3, 4), (3, 5), (4, 5)])
 @pytest.mark.parametrize("order", [1, 2, 3, 4, 5])
-def test_every_pair_and_order_passes_argument_checks(lib, lo, hi, order):
+@pytest.mark.parametrize("frame", [0, 1, 2])
+def test_every_pair_and_order_passes_argument_checks(lib, lo, hi, order, frame):
     """All argument checks (including the compile-time stencil pattern the
     kernels assume) accept every supported configuration; on a machine
     without a GPU the call then stops at the first CUDA call."""
     g = slbm.slbm_grid(40, 40, 1, 1)
     h = ctypes.c_void_p()
-    rc = lib.slbm_create(ctypes.byref(g), lo, hi, 0.6, order, 0, 0, None, ctypes.byref(h))
+    rc = lib.slbm_create(ctypes.byref(g), lo, hi, 0.6, order, frame, 0, None, ctypes.byref(h))
     assert rc != slbm.SLBM_EINVAL, slbm.slbm_last_error()
     if h.value:
         lib.slbm_destroy(h)
