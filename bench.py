@@ -207,6 +207,126 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def time_steps(solver, stream, steps, warmup):
+    """Mean device milliseconds of one step over `steps` back-to-back steps."""
+    import torch
+    solver.step(warmup)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    solver.step(steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    solver.sync()
+    return a.elapsed_time(b) / steps
+
+
+def profiled(g, steps):
+    """Per-kernel device milliseconds (summed) and step count over `steps`
+    traced steps (separate from the timed ones)."""
+    g.profile(True)
+    g.step(steps)
+    out = g.profile_read()
+    g.profile(False)
+    return out
+
+
+def run_study(args):
+    """Secondary measurements, one JSON line each (not the headline line).
+
+    strip: the efficiency study of Sec. IV.C -- N x N periodic grids, all-D2Q9,
+      all-D2Q25 and a hybrid whose left 10 % of columns are D2Q25; reports
+      t_Q25 / t_Q9 and t_Q25 / t_hyb next to the paper's 2.9 and 2.43.
+    vortex4096: the large random-vortex field (4096^2, 512 vortices, Mach 0.9
+      peak, Mach criterion), FP32 storage against FP16 deviation storage:
+      MLUPS of each and the relative L2 gap of rho and u after the same steps.
+    pond: the co-moving (PonD) frame step, thermal, 1024 x 512 periodic,
+      FP32, D2Q9 with a D2Q25 disc, a smooth seeded field around a Mach 1.5
+      mean flow at T = 1.
+    """
+    import torch
+    from paper_2102_12559_gb300 import slbm, workloads as WL
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    if args.workload == "strip":
+        for N in (128, 256, 512, 1024, 2048, 4096):
+            steps = max(20, min(2000, int(4e8 / (N * N))))
+            t, kms = {}, {}
+            for name in ("q9", "q25", "hyb"):
+                g = slbm.Solver(N, N, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=0.6, stream=stream)
+                g.init_equilibrium(*WL.perturbed(N, N, seed=1, amp_rho=0.02, amp_u=0.05))
+                fl = {"q9": np.zeros((N, N), np.uint8), "q25": np.ones((N, N), np.uint8),
+                      "hyb": WL.strip_flags(N, 0.1)}[name]
+                g.set_flags(fl)
+                t[name] = time_steps(g, stream, steps, 10)
+                kern, ksteps = profiled(g, min(steps, 100))
+                kms[name] = {n: kern[i] / max(ksteps, 1) for i, n in enumerate(slbm.KERNEL_NAMES)}
+                g.close()
+            print(json.dumps({
+                "study": "strip efficiency (Sec. IV.C)", "N": N, "steps": steps,
+                "ms_per_step": t, "mlups": {k: N * N / (v * 1e-3) / 1e6 for k, v in t.items()},
+                "kernels_ms_per_step": kms,
+                "t_q25_over_t_q9": t["q25"] / t["q9"], "t_q25_over_t_hyb": t["q25"] / t["hyb"],
+                "paper": {"t_q25_over_t_q9": 2.9, "t_q25_over_t_hyb_max": 2.43},
+                "l2": "not flushed (back-to-back steps)"}), flush=True)
+        return
+    if args.workload == "vortex4096":
+        # the large random-vortex field: FP32 storage against FP16 deviations
+        N = 4096
+        rho, ux, uy = WL.random_vortex_field(N, 512, seed=4, rmin=8.0, rmax=64.0, umax=0.9)
+        res = {}
+        for name, prec in (("fp32", slbm.SLBM_FP32), ("fp16", slbm.SLBM_FP16)):
+            g = slbm.Solver(N, N, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=0.6, stream=stream,
+                            precision=prec)
+            g.init_equilibrium(rho, ux, uy)
+            g.set_criterion(slbm.SLBM_CRIT_MACH, THR)
+            ms = time_steps(g, stream, args.steps, args.warmup)
+            kern, ksteps = profiled(g, min(args.steps, 50))
+            nhi = int(g.get_flags().sum())
+            mom = g.moments()
+            res[name] = dict(ms=ms, kern=[k / max(ksteps, 1) for k in kern], nhi=nhi, mom=mom)
+            g.close()
+        a, b = res["fp16"]["mom"], res["fp32"]["mom"]
+        rl2 = lambda x, y: float(np.linalg.norm((x - y).ravel()) / np.linalg.norm(y.ravel()))
+        for name in ("fp32", "fp16"):
+            r = res[name]
+            es = 2 if name == "fp16" else 4
+            bytes_sc = N * N * (2 * es * 9 + 2) + r["nhi"] * 2 * es * 16
+            print(json.dumps({
+                "study": "large random-vortex field", "workload": f"{N}x{N}, 512 vortices, "
+                "max Mach 0.9, Mach>0.3 criterion every step", "storage": name,
+                "steps_timed": args.steps, "total_steps": args.steps + args.warmup,
+                "ms_per_step": r["ms"], "mlups": N * N / (r["ms"] * 1e-3) / 1e6,
+                "high_order_fraction": r["nhi"] / (N * N),
+                "kernels_ms_per_step": dict(zip(slbm.KERNEL_NAMES, r["kern"])),
+                "stream_collide_gbs": bytes_sc / (r["kern"][0] * 1e-3) / 1e9}), flush=True)
+        print(json.dumps({"study": "large random-vortex field", "fp16_vs_fp32_rel_l2": {
+            "rho": rl2(a[0], b[0]), "u": rl2(np.stack(a[1:3]), np.stack(b[1:3]))}}), flush=True)
+        return
+    if args.workload == "pond":
+        nx, ny = 1024, 512
+        rho, ux, uy = WL.perturbed(nx, ny, seed=7, amp_rho=0.05, amp_u=0.2, U=(1.5 * np.sqrt(2.0), 0.0))
+        T = WL.perturbed_T(nx, ny, seed=8, amp=0.05)
+        disc = WL.random_flags(nx, ny, seed=3, blobs=4, rmin=24, rmax=48)
+        for name, fl in (("D2Q9", np.zeros((ny, nx), np.uint8)), ("D2Q9+D2Q25 discs", disc),
+                         ("D2Q25", np.ones((ny, nx), np.uint8))):
+            g = slbm.Solver(nx, ny, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=0.6, stream=stream,
+                            frame=slbm.SLBM_FRAME_POND)
+            g.init_equilibrium(rho, ux, uy, T)
+            g.set_flags(fl)
+            ms = time_steps(g, stream, args.steps, args.warmup)
+            kern, ksteps = profiled(g, min(args.steps, 20))
+            print(json.dumps({
+                "study": "co-moving frame (PonD) step", "workload": f"thermal PonD {nx}x{ny} {name}",
+                "mean_flow_mach": 1.5, "high_order_fraction": float(fl.mean()),
+                "steps": args.steps, "ms_per_step": ms, "mlups": nx * ny / (ms * 1e-3) / 1e6,
+                "kernels_ms_per_step": {n: kern[i] / max(ksteps, 1)
+                                        for i, n in enumerate(slbm.KERNEL_NAMES[:2])}}),
+                  flush=True)
+            g.close()
+        return
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -215,9 +335,14 @@ def main():
     ap.add_argument("--impl", default="slbm", choices=["slbm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--spinup", type=int, default=0, help="untimed steps before warm-up")
+    ap.add_argument("--workload", default="jet", choices=["jet", "strip", "pond", "vortex4096"],
+                    help="jet: the headline line; strip / pond: secondary studies")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.workload != "jet":
+        run_study(args)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -268,7 +393,6 @@ def main():
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize(dev)
-    solver.profile(True)
     evs = []
     for _ in range(args.steps):
         flush.zero_()
@@ -281,6 +405,14 @@ def main():
     if dist is not None:
         dist.barrier()
     total_ms = sum(s.elapsed_time(e) for s, e in evs)
+    # per-kernel device times from the library's event tracing, in a separate
+    # pass of the same workload (the tracing events would otherwise sit in the
+    # timed steps)
+    prof_steps = min(args.steps, 200)
+    solver.profile(True)
+    for _ in range(prof_steps):
+        flush.zero_()
+        solver.step(1)
     kern_ms, kern_steps = solver.profile_read()
     solver.profile(False)
     flags_after = solver.get_flags()

@@ -90,9 +90,12 @@ typedef struct slbm_s *slbm_t;
 /* Largest departure distance |v_i| dt, in cells, a co-moving step accepts. */
 #define SLBM_POND_REACH 5
 
-/* Storage / arithmetic precision of the populations. */
+/* Storage / arithmetic precision of the populations.  Every precision stores
+ * deviations s_i = f_i - W_i from the rest state (rho_0 = 1, u = 0). */
 #define SLBM_FP32 0          /* float storage, float arithmetic, FP64 conversion moments */
 #define SLBM_FP64 1          /* double storage and arithmetic */
+#define SLBM_FP16 2          /* half-precision storage of the deviations (half the bytes
+                                per cell update), float arithmetic; lattice frame only */
 
 /* Boundary kinds for a non-periodic side (ghost layer contents):
  *  OUTFLOW   zero-order extrapolation: copy of the nearest interior cell;
@@ -242,11 +245,11 @@ SLBM_API int slbm_set_frame(slbm_t h, const double *ux, const double *uy, const 
  * and starts bracketing every kernel slbm_step launches with CUDA events on
  * the handle's stream; slbm_profile(h, 0) stops.  slbm_profile_read()
  * synchronises and returns, per kernel of the step sequence (index 0 =
- * stream-collide, 1 = interface conversion, 2 = ghost-ring refresh; a
- * co-moving step has no ghost ring, its index 2 reads 0), the
- * summed device milliseconds over the recorded steps, and the number of
- * recorded steps.  ms must hold SLBM_PROFILE_KERNELS doubles. */
-#define SLBM_PROFILE_KERNELS 3
+ * stream-collide, 1 = post-step: interface conversion and, in the lattice
+ * frame, the ghost-ring refresh), the summed device milliseconds over the
+ * recorded steps, and the number of recorded steps.  ms must hold
+ * SLBM_PROFILE_KERNELS doubles. */
+#define SLBM_PROFILE_KERNELS 2
 SLBM_API int slbm_profile(slbm_t h, int enable);
 SLBM_API int slbm_profile_read(slbm_t h, double *ms, long long *steps);
 

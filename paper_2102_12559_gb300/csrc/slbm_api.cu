@@ -173,7 +173,9 @@ void fill_lat(LatTab<R>& T, const Lattice1D& L, double dt, int P) {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-int elem_size(int precision) { return precision == SLBM_FP64 ? 8 : 4; }
+int elem_size(int precision) {
+  return precision == SLBM_FP64 ? 8 : (precision == SLBM_FP16 ? 2 : 4);
+}
 
 struct Layout {
   int G, pitch, rows;
@@ -181,6 +183,11 @@ struct Layout {
   size_t pops[2][2];         // byte offsets [buffer][lattice]
   size_t flags[2], flag_tmp, tile_mask[2], macro[4], partials, audit_out, err, bc[4][3];
   size_t lam[2];             // co-moving frame planes {u_x, u_y, T} per buffer
+  size_t sched;              // two tile counters of the stream kernel's scheduler
+  size_t post_sync;          // 2 x 3 counters of the post-step kernel's grid-wide waits
+  size_t post_work;          // 2 x ntiles work words (stream kernel -> post-step kernel)
+  size_t post_counts;        // per-CTA work-tile counts of the post-step kernel
+  size_t post_list;          // its compacted work tiles, one int per tile
   size_t total;
 };
 
@@ -191,8 +198,8 @@ bool config_ok(const slbm_grid* g, int lo, int hi, int order, int precision, cha
     return false;
   }
   if (order < 1 || order > 5) { snprintf(err, 256, "interp_order must be in 1..5"); return false; }
-  if (precision != SLBM_FP32 && precision != SLBM_FP64) {
-    snprintf(err, 256, "precision must be SLBM_FP32 or SLBM_FP64");
+  if (precision != SLBM_FP32 && precision != SLBM_FP64 && precision != SLBM_FP16) {
+    snprintf(err, 256, "precision must be SLBM_FP32, SLBM_FP64 or SLBM_FP16");
     return false;
   }
   if (g->nx < 1 || g->ny < 1 || (long long)g->nx * g->ny > (1LL << 30)) {
@@ -250,6 +257,11 @@ Layout make_layout(const slbm_grid* g, int lo, int hi, int order, int precision)
   for (int s = 0; s < 4; ++s)
     for (int q = 0; q < 3; ++q) { Lo.bc[s][q] = off; off = align_up(off + side * 8, 256); }
   for (int b = 0; b < 2; ++b) { Lo.lam[b] = off; off = align_up(off + 3 * nc * es, 256); }
+  Lo.sched = off; off = align_up(off + 2 * sizeof(int), 256);
+  Lo.post_sync = off; off = align_up(off + 6 * sizeof(int), 256);
+  Lo.post_work = off; off = align_up(off + 2 * ntiles * sizeof(int), 256);
+  Lo.post_counts = off; off = align_up(off + 1024 * sizeof(int), 256);
+  Lo.post_list = off; off = align_up(off + ntiles * sizeof(int), 256);
   Lo.total = off;
   return Lo;
 }
@@ -283,6 +295,8 @@ struct slbm_s {
   double thr;
   int bc_kind[4];
   long long steps;
+  long long sc_launches;         // stream-collide launches (scheduler counter parity)
+  long long post_launches;       // post-step launches (their counter parity)
   int failed;
   char err[256];
   // tracing: events bracketing the kernels of each profiled step
@@ -343,19 +357,40 @@ BcDev bc_dev(slbm_s* h) {
   return b;
 }
 
+// Storage / arithmetic types of a lattice-frame handle, as a tag.
+template <class S_, class R_>
+struct Ty {
+  using S = S_;
+  using R = R_;
+};
+
+// f(Ty<S, R>{}, params) for the handle's storage type S and arithmetic type
+// R: FP64 -> (double, double), FP16 -> (half, float), FP32 -> (float, float).
+template <class F>
+auto with_types(slbm_s* h, F&& f) -> decltype(f(Ty<float, float>{}, h->pf)) {
+  switch (h->precision) {
+    case SLBM_FP64: return f(Ty<double, double>{}, h->pd);
+    case SLBM_FP16: return f(Ty<__half, float>{}, h->pf);
+    default: return f(Ty<float, float>{}, h->pf);
+  }
+}
+
+#define SLBM_TYPES(ty)                 \
+  using S = typename decltype(ty)::S; \
+  using R = typename decltype(ty)::R; \
+  (void)sizeof(R)
+
 // Full ghost fill of both buffers (setup paths).  The buffer in use gets its
 // exact ghosts; the other one gets the constant DIRICHLET states the step
 // never rewrites (its copies are refreshed by the post-step kernel).
 cudaError_t ghosts(slbm_s* h, const uint8_t* flag) {
   for (int b = 0; b < 2; ++b) {
     const int buf = b == 0 ? h->cur ^ 1 : h->cur;
-    cudaError_t e;
-    if (h->precision == SLBM_FP64)
-      e = launch_ghosts<double, double>(h->pd, (double*)h->pops(buf, 0), (double*)h->pops(buf, 1),
-                                        flag, bc_dev(h), h->st);
-    else
-      e = launch_ghosts<float, float>(h->pf, (float*)h->pops(buf, 0), (float*)h->pops(buf, 1), flag,
-                                      bc_dev(h), h->st);
+    const cudaError_t e = with_types(h, [&](auto ty, const auto& prm) {
+      SLBM_TYPES(ty);
+      return launch_ghosts<S, R>(prm, (S*)h->pops(buf, 0), (S*)h->pops(buf, 1), flag, bc_dev(h),
+                                 h->st);
+    });
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -366,11 +401,11 @@ cudaError_t ghosts(slbm_s* h, const uint8_t* flag) {
 cudaError_t convert(slbm_s* h, int buf, const uint8_t* fold, const uint8_t* fnew,
                     const uint8_t* mask_in = nullptr) {
   uint8_t* mask = h->at<uint8_t>(h->lay.tile_mask[h->mcur]);
-  if (h->precision == SLBM_FP64)
-    return launch_post<double, double>(h->pd, (double*)h->pops(buf, 0), (double*)h->pops(buf, 1),
-                                       fold, fnew, bc_dev(h), 1, mask_in, mask, h->st);
-  return launch_post<float, float>(h->pf, (float*)h->pops(buf, 0), (float*)h->pops(buf, 1), fold,
-                                   fnew, bc_dev(h), 1, mask_in, mask, h->st);
+  return with_types(h, [&](auto ty, const auto& prm) {
+    SLBM_TYPES(ty);
+    return launch_post<S, R>(prm, (S*)h->pops(buf, 0), (S*)h->pops(buf, 1), fold, fnew, bc_dev(h),
+                             1, mask_in, mask, h->st);
+  });
 }
 
 // TMA descriptors of every population buffer: a 3-D tensor {pitch, rows, Q}
@@ -392,7 +427,7 @@ int encode_tmaps(slbm_s* h) {
     for (int k = 0; k < 2; ++k) {
       const int n = k ? h->nhi : h->nlo;
       unsigned box[3];
-      stream_box(h->lay.G, n * n, box);
+      stream_box(es, h->lay.G, n * n, box);
       const cuuint64_t dims[3] = {(cuuint64_t)h->lay.pitch, (cuuint64_t)h->lay.rows,
                                   (cuuint64_t)(n * n)};
       const cuuint64_t strides[2] = {(cuuint64_t)h->lay.pitch * es,
@@ -401,7 +436,9 @@ int encode_tmaps(slbm_s* h) {
       const cuuint32_t estr[3] = {1, 1, 1};
       const CUresult r = encode(
           &h->tmap[b][k],
-          es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+          es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                  : (es == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32),
+          3,
           h->pops(b, k), dims, strides, boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -446,6 +483,10 @@ cudaError_t mark(slbm_s* h) {
   return cudaEventRecord(h->ev_pool[h->ev_used++], h->st);
 }
 
+int ntiles_of(const slbm_s* h) {
+  return ((h->g.nx + kTX - 1) / kTX) * ((h->g.ny + kTY - 1) / kTY);
+}
+
 // One time step: stream-collide (old flags) -> interface conversion (new
 // flags) -> ghost-ring refresh.
 int pond_convert_band(slbm_s* h, int buf) {
@@ -485,7 +526,6 @@ int pond_step_once(slbm_s* h) {
   SLBM_CK(h, mark(h), "trace event");
   if (int rc = pond_convert_band(h, nb)) return rc;
   SLBM_CK(h, mark(h), "trace event");
-  SLBM_CK(h, mark(h), "trace event");
   h->cur = nb;
   h->steps++;
   return SLBM_OK;
@@ -501,25 +541,28 @@ int step_once(slbm_s* h) {
   int* err = h->at<int>(h->lay.err);
   const uint8_t* mask = h->at<uint8_t>(h->lay.tile_mask[h->mcur]);
   uint8_t* mask_next = h->at<uint8_t>(h->lay.tile_mask[h->mcur ^ 1]);
-  if (h->precision == SLBM_FP64)
-    e = launch_stream_collide<double, double>(h->pd, h->P, &h->tmap[b][0], &h->tmap[b][1],
-                                              (double*)h->pops(nb, 0), (double*)h->pops(nb, 1),
-                                              fold, fnew, mask, mask_next, bc_dev(h), err, h->st);
-  else
-    e = launch_stream_collide<float, float>(h->pf, h->P, &h->tmap[b][0], &h->tmap[b][1],
-                                            (float*)h->pops(nb, 0), (float*)h->pops(nb, 1), fold,
-                                            fnew, mask, mask_next, bc_dev(h), err, h->st);
+  h->pf.seed = h->pd.seed = (uint32_t)h->steps;
+  h->pf.sched_parity = h->pd.sched_parity = (int)(h->sc_launches & 1);
+  h->sc_launches++;
+  e = with_types(h, [&](auto ty, const auto& prm) {
+    SLBM_TYPES(ty);
+    return launch_stream_collide<S, R>(prm, h->P, &h->tmap[b][0], &h->tmap[b][1],
+                                       (S*)h->pops(nb, 0), (S*)h->pops(nb, 1), fold, fnew, mask,
+                                       mask_next, bc_dev(h), err, h->st);
+  });
   SLBM_CK(h, e, "stream_collide launch");
   SLBM_CK(h, mark(h), "trace event");
-  SLBM_CK(h, convert(h, nb, fold, fnew, mask_next), "post-step launch");
-  SLBM_CK(h, mark(h), "trace event");
-  if (h->precision == SLBM_FP64)
-    e = launch_halo<double, double>(h->pd, (double*)h->pops(nb, 0), (double*)h->pops(nb, 1), fnew,
-                                    bc_dev(h), h->st);
-  else
-    e = launch_halo<float, float>(h->pf, (float*)h->pops(nb, 0), (float*)h->pops(nb, 1), fnew,
-                                  bc_dev(h), h->st);
-  SLBM_CK(h, e, "halo launch");
+  const int post_parity = (int)(h->post_launches & 1);
+  h->post_launches++;
+  const int* work = h->at<int>(h->lay.post_work) + (size_t)h->pf.sched_parity * ntiles_of(h);
+  e = with_types(h, [&](auto ty, const auto& prm) {
+    SLBM_TYPES(ty);
+    return launch_post_step<S, R>(prm, (S*)h->pops(nb, 0), (S*)h->pops(nb, 1), fold, fnew,
+                                  bc_dev(h), work, h->at<int>(h->lay.post_sync),
+                                  h->at<int>(h->lay.post_counts), h->at<int>(h->lay.post_list),
+                                  post_parity, err, h->st);
+  });
+  SLBM_CK(h, e, "post-step launch");
   SLBM_CK(h, mark(h), "trace event");
   h->cur = nb;
   h->mcur ^= 1;
@@ -544,6 +587,8 @@ void fill_params(Params<R>& p, const slbm_s* h, const Lattice1D& a, const Lattic
   p.omega = (R)(1.0 / h->tau);
   p.band = h->lay.G;
   p.nsm = h->nsm;
+  p.sched = reinterpret_cast<int*>(h->ws + h->lay.sched);
+  p.work = reinterpret_cast<int*>(h->ws + h->lay.post_work);
   fill_lat(p.lat[0], a, dt, h->P);
   fill_lat(p.lat[1], b, dt, h->P);
   ConvTab<R>& t = p.conv;
@@ -656,8 +701,10 @@ int pack_all(slbm_s* h, const Params<R>& prm, int k, double* host, int unpack,
 }
 
 int pack_any(slbm_s* h, int k, double* host, int unpack, const double* in) {
-  return h->precision == SLBM_FP64 ? pack_all<double, double>(h, h->pd, k, host, unpack, in)
-                                   : pack_all<float, float>(h, h->pf, k, host, unpack, in);
+  return with_types(h, [&](auto ty, const auto& prm) {
+    SLBM_TYPES(ty);
+    return pack_all<S, R>(h, prm, k, host, unpack, in);
+  });
 }
 
 int init_eq_dev(slbm_s* h, bool with_T = false) {
@@ -677,14 +724,11 @@ int init_eq_dev(slbm_s* h, bool with_T = false) {
     SLBM_CK(h, e, "init launch");
     return SLBM_OK;
   }
-  if (h->precision == SLBM_FP64)
-    e = launch_init_eq<double, double>(h->pd, (double*)h->pops(h->cur, 0),
-                                       (double*)h->pops(h->cur, 1), r,
-                               u, v, h->st);
-  else
-    e = launch_init_eq<float, float>(h->pf, (float*)h->pops(h->cur, 0), (float*)h->pops(h->cur, 1),
-                                     r, u,
-                              v, h->st);
+  e = with_types(h, [&](auto ty, const auto& prm) {
+    SLBM_TYPES(ty);
+    return launch_init_eq<S, R>(prm, (S*)h->pops(h->cur, 0), (S*)h->pops(h->cur, 1), r, u, v,
+                                h->st);
+  });
   SLBM_CK(h, e, "init launch");
   SLBM_CK(h, convert(h, h->cur, h->flags(h->fcur), h->flags(h->fcur)), "post-step launch");
   SLBM_CK(h, ghosts(h, h->flags(h->fcur)), "ghost launch");
@@ -702,6 +746,10 @@ bool create_args_ok(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int 
   if (frame != SLBM_FRAME_LATTICE && frame != SLBM_FRAME_POND &&
       frame != SLBM_FRAME_POND_ISOTHERMAL) {
     snprintf(g_create_err, sizeof(g_create_err), "unknown frame");
+    return false;
+  }
+  if (frame != SLBM_FRAME_LATTICE && precision == SLBM_FP16) {
+    snprintf(g_create_err, sizeof(g_create_err), "the co-moving frame runs in FP32 or FP64");
     return false;
   }
   if (frame != SLBM_FRAME_LATTICE && !(g->periodic_x && g->periodic_y)) {
@@ -863,7 +911,7 @@ int slbm_get_info(slbm_t h, slbm_info_t* info) {
   info->rows = h->lay.rows;
   info->precision = h->precision;
   info->kernels_per_step =
-      h->frame == SLBM_FRAME_LATTICE ? 3 : (h->pond_mixed ? 2 : 1);
+      h->frame == SLBM_FRAME_LATTICE ? 2 : (h->pond_mixed ? 2 : 1);
   info->workspace_bytes = h->lay.total;
   info->steps = h->steps;
   return SLBM_OK;
@@ -956,14 +1004,11 @@ int slbm_set_criterion(slbm_t h, int kind, double threshold) {
   if (kind == SLBM_CRIT_MACH) {
     // evaluate the criterion on the current state at once; flips are converted
     uint8_t* tmp = h->at<uint8_t>(h->lay.flag_tmp);
-    cudaError_t e =
-        h->precision == SLBM_FP64
-            ? launch_criterion<double, double>(h->pd, (const double*)h->pops(h->cur, 0),
-                                       (const double*)h->pops(h->cur, 1), h->flags(h->fcur), tmp,
-                                       h->st)
-            : launch_criterion<float, float>(h->pf, (const float*)h->pops(h->cur, 0),
-                                      (const float*)h->pops(h->cur, 1), h->flags(h->fcur), tmp,
-                                      h->st);
+    const cudaError_t e = with_types(h, [&](auto ty, const auto& prm) {
+      SLBM_TYPES(ty);
+      return launch_criterion<S, R>(prm, (const S*)h->pops(h->cur, 0),
+                                    (const S*)h->pops(h->cur, 1), h->flags(h->fcur), tmp, h->st);
+    });
     SLBM_CK(h, e, "criterion launch");
     SLBM_CK(h, convert(h, h->cur, h->flags(h->fcur), tmp), "convert launch");
     SLBM_CK(h, cudaMemcpyAsync(h->flags(h->fcur), tmp, h->ncell(), cudaMemcpyDeviceToDevice, h->st),
@@ -1016,14 +1061,12 @@ int slbm_sync(slbm_t h) {
 int slbm_moments_device(slbm_t h, double* rho, double* ux, double* uy, double* T) {
   SLBM_GUARD(h);
   cudaError_t e;
-  if (h->precision == SLBM_FP64)
-    e = launch_moments<double, double>(h->pd, (const double*)h->pops(h->cur, 0),
-                               (const double*)h->pops(h->cur, 1), h->flags(h->fcur), rho, ux, uy, T,
-                               (const double*)frame_planes(h), h->st);
-  else
-    e = launch_moments<float, float>(h->pf, (const float*)h->pops(h->cur, 0),
-                              (const float*)h->pops(h->cur, 1), h->flags(h->fcur), rho, ux, uy, T,
-                              (const float*)frame_planes(h), h->st);
+  e = with_types(h, [&](auto ty, const auto& prm) {
+    SLBM_TYPES(ty);
+    return launch_moments<S, R>(prm, (const S*)h->pops(h->cur, 0), (const S*)h->pops(h->cur, 1),
+                                h->flags(h->fcur), rho, ux, uy, T, (const S*)frame_planes(h),
+                                h->st);
+  });
   SLBM_CK(h, e, "moments launch");
   return SLBM_OK;
 }
@@ -1051,14 +1094,11 @@ int slbm_audit(slbm_t h, double out[4]) {
   double* part = h->at<double>(h->lay.partials);
   double* res = h->at<double>(h->lay.audit_out);
   cudaError_t e;
-  if (h->precision == SLBM_FP64)
-    e = launch_audit<double, double>(h->pd, (const double*)h->pops(h->cur, 0),
-                             (const double*)h->pops(h->cur, 1), h->flags(h->fcur), part, np, res,
-                             (const double*)frame_planes(h), h->st);
-  else
-    e = launch_audit<float, float>(h->pf, (const float*)h->pops(h->cur, 0),
-                            (const float*)h->pops(h->cur, 1), h->flags(h->fcur), part, np, res,
-                            (const float*)frame_planes(h), h->st);
+  e = with_types(h, [&](auto ty, const auto& prm) {
+    SLBM_TYPES(ty);
+    return launch_audit<S, R>(prm, (const S*)h->pops(h->cur, 0), (const S*)h->pops(h->cur, 1),
+                              h->flags(h->fcur), part, np, res, (const S*)frame_planes(h), h->st);
+  });
   SLBM_CK(h, e, "audit launch");
   SLBM_CK(h, cudaMemcpyAsync(out, res, 32, cudaMemcpyDeviceToHost, h->st), "D2H copy");
   SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");

@@ -3,7 +3,7 @@
 // path: GB300's FP64 rate is a small fraction of its FP32 rate, so doubles
 // appear only in moment sums and the audit).
 #include "../../include/slbm.h"
-#include "slbm_eq.cuh"
+#include "slbm_ghost.cuh"
 
 namespace slbm {
 
@@ -49,25 +49,6 @@ __device__ void write_eq_both(const Params<R>& p, S* f0, S* f1, int base, double
   for (int k = 0; k < 2; ++k) {
     eq_dev<R>(p.lat[k], p.lat[k].n, (R)(rho - 1.0), (R)ux, (R)uy, e);
     store_dev<S, R>(p.lat[k], k ? f1 : f0, p.plane, base, e);
-  }
-}
-
-// Ghost cell g of the ring (0 <= g < 2 G (nx + 2G) + 2 G ny) -> (gx, gy)
-// (32-bit arithmetic: the ring is far smaller than 2^31 cells).
-__device__ __forceinline__ void ghost_coords(int G, int nx, int ny, int g, int& gx, int& gy) {
-  const int W = nx + 2 * G;
-  const int nstrip = G * W;
-  if (g < nstrip) {
-    gy = -G + g / W; gx = -G + g % W;
-  } else if (g < 2 * nstrip) {
-    const int j = g - nstrip;
-    gy = ny + j / W; gx = -G + j % W;
-  } else if (g < 2 * nstrip + G * ny) {
-    const int j = g - 2 * nstrip;
-    gy = j / G; gx = -G + j % G;
-  } else {
-    const int j = g - 2 * nstrip - G * ny;
-    gy = j / G; gx = nx + j % G;
   }
 }
 
@@ -126,88 +107,6 @@ __global__ void k_ghosts(const Params<R> p, S* f0, S* f1, const uint8_t* __restr
     for (int i = 0; i < q1; ++i) v[i] = f1[(size_t)i * p.plane + sbase];
     for (int i = 0; i < q1; ++i) f1[(size_t)i * p.plane + gbase] = v[i];
   }
-}
-
-// Source of ghost (gx, gy) under the ghost rule: kind 0 = copy of interior
-// (sx, sy); 1 = INLET equilibrium (density of interior (sx, sy), velocity
-// bc[side][idx]); 2 = DIRICHLET (constant, written at setup).
-__device__ __forceinline__ int ghost_source(int nx, int ny, int px, int py, const BcDev& bc,
-                                            int gx, int gy, int& sx, int& sy, int& side,
-                                            int& idx) {
-  sx = px ? (gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx)) : gx;
-  sy = py ? (gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy)) : gy;
-  if (sy < 0 || sy >= ny) {  // non-periodic y side (wins at corners)
-    side = sy < 0 ? SLBM_SIDE_YMIN : SLBM_SIDE_YMAX;
-    const int xi = min(max(sx, 0), nx - 1), yi = sy < 0 ? 0 : ny - 1;
-    const int kind = bc.kind[side];
-    if (kind == SLBM_BC_OUTFLOW) {
-      sy = yi;
-    } else {
-      sx = xi; sy = yi; idx = xi;
-      return kind == SLBM_BC_INLET ? 1 : 2;
-    }
-  }
-  if (sx < 0 || sx >= nx) {  // non-periodic x side
-    side = sx < 0 ? SLBM_SIDE_XMIN : SLBM_SIDE_XMAX;
-    const int xi = sx < 0 ? 0 : nx - 1;
-    const int kind = bc.kind[side];
-    if (kind == SLBM_BC_OUTFLOW) {
-      sx = xi;
-    } else {
-      sx = xi; idx = sy;
-      return kind == SLBM_BC_INLET ? 1 : 2;
-    }
-  }
-  return 0;
-}
-
-// Per-step ghost refresh, one thread per (ghost cell, plane) for every plane
-// of both lattices, consecutive threads walking a strip of one plane (rows
-// coalesce).  Copy ghosts copy their interior source; INLET ghosts write the
-// plane's lattice equilibrium at the interior cell's density and the side's
-// velocity (each thread sums that cell's own populations and evaluates one
-// product term); DIRICHLET ghosts are constant and left alone.
-template <int NL, int NH, class S, class R>
-__global__ void __launch_bounds__(kThreads)
-k_halo(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ flag, const BcDev bc,
-       int nghost) {
-  constexpr int q0 = NL * NL, q1 = NH * NH;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nghost * (q0 + q1)) return;
-  const int plane = t / nghost;
-  int gx, gy, sx, sy, side = 0, idx = 0;
-  ghost_coords(p.G, p.nx, p.ny, t - plane * nghost, gx, gy);
-  const int kind = ghost_source(p.nx, p.ny, p.periodic_x, p.periodic_y, bc, gx, gy, sx, sy, side,
-                                idx);
-  if (kind == 2) return;
-  const int k = plane < q0 ? 0 : 1;
-  const int i = k ? plane - q0 : plane;
-  S* f = k ? f1 : f0;
-  const size_t off = (size_t)i * p.plane;
-  const int gbase = (gy + p.G) * p.pitch + (gx + kOX);
-  const int sbase = (sy + p.G) * p.pitch + (sx + kOX);
-  if (kind == 0) {
-    f[off + gbase] = f[off + sbase];
-    return;
-  }
-  // INLET: density deviation of the interior cell from its own lattice
-  R dr = R(0);
-  if (flag[sx + p.nx * sy]) {
-#pragma unroll
-    for (int j = 0; j < q1; ++j) dr += static_cast<R>(f1[(size_t)j * p.plane + sbase]);
-  } else {
-#pragma unroll
-    for (int j = 0; j < q0; ++j) dr += static_cast<R>(f0[(size_t)j * p.plane + sbase]);
-  }
-  const LatTab<R>& L = p.lat[k];
-  const int n = k ? NH : NL;
-  R dx[kMaxN], dy[kMaxN];
-  dphi<R>(L, n, (R)bc.ux[side][idx], dx);
-  dphi<R>(L, n, (R)bc.uy[side][idx], dy);
-  const int ix = i % n, iy = i / n;
-  const R px = L.w1[ix] + dx[ix], py = L.w1[iy] + dy[iy];
-  f[off + gbase] =
-      static_cast<S>(dr * px * py + L.w1[ix] * dy[iy] + dx[ix] * L.w1[iy] + dx[ix] * dy[iy]);
 }
 
 template <class S, class R>
@@ -374,26 +273,6 @@ cudaError_t launch_ghosts(const Params<R>& p, S* f0, S* f1, const uint8_t* flag,
 }
 
 template <class S, class R>
-cudaError_t launch_halo(const Params<R>& p, S* f0, S* f1, const uint8_t* flag, const BcDev& bc,
-                        cudaStream_t st) {
-  const long long ng = 2LL * p.G * (p.nx + 2 * p.G) + 2LL * p.G * p.ny;
-  const int nl = p.lat[0].n, nh = p.lat[1].n;
-  const long long total = ng * (nl * nl + nh * nh);
-  if (total >= (1LL << 31)) return cudaErrorInvalidValue;
-  const unsigned blocks = (unsigned)((total + kThreads - 1) / kThreads);
-#define SLBM_HALO_CASE(NL, NH)                                                              \
-  if (nl == NL && nh == NH) {                                                               \
-    k_halo<NL, NH, S, R><<<blocks, kThreads, 0, st>>>(p, f0, f1, flag, bc, (int)ng);        \
-    return cudaGetLastError();                                                              \
-  }
-  SLBM_HALO_CASE(3, 4)
-  SLBM_HALO_CASE(3, 5)
-  SLBM_HALO_CASE(4, 5)
-#undef SLBM_HALO_CASE
-  return cudaErrorInvalidValue;
-}
-
-template <class S, class R>
 cudaError_t launch_init_eq(const Params<R>& p, S* f0, S* f1, const double* rho, const double* ux,
                            const double* uy, cudaStream_t st) {
   k_init_eq<S, R><<<tile_grid(p), dim3(kTX, kTY), 0, st>>>(p, f0, f1, rho, ux, uy);
@@ -436,8 +315,6 @@ cudaError_t launch_pack(const Params<R>& p, int k, int i0, int cnt, const S* f, 
 #define SLBM_AUX_INST(S, R)                                                                  \
   template cudaError_t launch_ghosts<S, R>(const Params<R>&, S*, S*, const uint8_t*,         \
                                            const BcDev&, cudaStream_t);                      \
-  template cudaError_t launch_halo<S, R>(const Params<R>&, S*, S*, const uint8_t*,           \
-                                         const BcDev&, cudaStream_t);                        \
   template cudaError_t launch_init_eq<S, R>(const Params<R>&, S*, S*, const double*,         \
                                             const double*, const double*, cudaStream_t);     \
   template cudaError_t launch_moments<S, R>(const Params<R>&, const S*, const S*,            \
@@ -452,6 +329,7 @@ cudaError_t launch_pack(const Params<R>& p, int k, int i0, int cnt, const S* f, 
                                          int, S*, const double*, cudaStream_t);
 SLBM_AUX_INST(float, float)
 SLBM_AUX_INST(double, double)
+SLBM_AUX_INST(__half, float)
 #undef SLBM_AUX_INST
 
 }  // namespace slbm

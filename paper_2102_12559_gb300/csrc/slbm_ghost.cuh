@@ -14,6 +14,114 @@ namespace slbm {
 
 constexpr int kBandMax = 3;  // largest stencil reach (order 5)
 
+// Ghost cell g of the ring (0 <= g < 2 G (nx + 2G) + 2 G ny) -> (gx, gy)
+// (32-bit arithmetic: the ring is far smaller than 2^31 cells).
+__device__ __forceinline__ void ghost_coords(int G, int nx, int ny, int g, int& gx, int& gy) {
+  const int W = nx + 2 * G;
+  const int nstrip = G * W;
+  if (g < nstrip) {
+    gy = -G + g / W; gx = -G + g % W;
+  } else if (g < 2 * nstrip) {
+    const int j = g - nstrip;
+    gy = ny + j / W; gx = -G + j % W;
+  } else if (g < 2 * nstrip + G * ny) {
+    const int j = g - 2 * nstrip;
+    gy = j / G; gx = -G + j % G;
+  } else {
+    const int j = g - 2 * nstrip - G * ny;
+    gy = j / G; gx = nx + j % G;
+  }
+}
+
+// Source of ghost (gx, gy) under the ghost rule: kind 0 = copy of interior
+// (sx, sy); 1 = INLET equilibrium (density of interior (sx, sy), velocity
+// bc[side][idx]); 2 = DIRICHLET (constant, written at setup).
+__device__ __forceinline__ int ghost_source(int nx, int ny, int px, int py, const BcDev& bc,
+                                            int gx, int gy, int& sx, int& sy, int& side,
+                                            int& idx) {
+  sx = px ? (gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx)) : gx;
+  sy = py ? (gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy)) : gy;
+  if (sy < 0 || sy >= ny) {  // non-periodic y side (wins at corners)
+    side = sy < 0 ? SLBM_SIDE_YMIN : SLBM_SIDE_YMAX;
+    const int xi = min(max(sx, 0), nx - 1), yi = sy < 0 ? 0 : ny - 1;
+    const int kind = bc.kind[side];
+    if (kind == SLBM_BC_OUTFLOW) {
+      sy = yi;
+    } else {
+      sx = xi; sy = yi; idx = xi;
+      return kind == SLBM_BC_INLET ? 1 : 2;
+    }
+  }
+  if (sx < 0 || sx >= nx) {  // non-periodic x side
+    side = sx < 0 ? SLBM_SIDE_XMIN : SLBM_SIDE_XMAX;
+    const int xi = sx < 0 ? 0 : nx - 1;
+    const int kind = bc.kind[side];
+    if (kind == SLBM_BC_OUTFLOW) {
+      sx = xi;
+    } else {
+      sx = xi; idx = sy;
+      return kind == SLBM_BC_INLET ? 1 : 2;
+    }
+  }
+  return 0;
+}
+
+// Per-step ghost refresh of one element: ghost g (0 <= g < nghost) of the
+// ring, plane `plane` of both lattices' planes (lattice 0 first).  Copy
+// ghosts copy their interior source; INLET ghosts write the plane's lattice
+// equilibrium at the interior cell's density and the side's velocity (the
+// cell's own populations summed, one product term evaluated); DIRICHLET ghosts
+// are constant (written at setup) and left alone.  Interior values are read
+// through L2 (ld.global.cg): in the fused post-step kernel they were written
+// by other CTAs of the same launch.
+template <int NL, int NH, class S, class R>
+__device__ __forceinline__ void halo_element(const Params<R>& p, S* f0, S* f1,
+                                             const uint8_t* __restrict__ flag, const BcDev& bc,
+                                             int nghost, int g, int plane) {
+  constexpr int q0 = NL * NL, q1 = NH * NH;
+  int gx, gy, sx, sy, side = 0, idx = 0;
+  ghost_coords(p.G, p.nx, p.ny, g, gx, gy);
+  const int kind = ghost_source(p.nx, p.ny, p.periodic_x, p.periodic_y, bc, gx, gy, sx, sy, side,
+                                idx);
+  if (kind == 2) return;
+  const int k = plane < q0 ? 0 : 1;
+  const int i = k ? plane - q0 : plane;
+  S* f = k ? f1 : f0;
+  const size_t off = (size_t)i * p.plane;
+  const int gbase = (gy + p.G) * p.pitch + (gx + kOX);
+  const int sbase = (sy + p.G) * p.pitch + (sx + kOX);
+  if (kind == 0) {
+    f[off + gbase] = __ldcg(f + off + sbase);
+    return;
+  }
+  // INLET: density deviation of the interior cell from its own lattice
+  R dr = R(0);
+  if (__ldcg(flag + sx + p.nx * sy)) {
+#pragma unroll
+    for (int j = 0; j < q1; ++j) dr += static_cast<R>(__ldcg(f1 + (size_t)j * p.plane + sbase));
+  } else {
+#pragma unroll
+    for (int j = 0; j < q0; ++j) dr += static_cast<R>(__ldcg(f0 + (size_t)j * p.plane + sbase));
+  }
+  const LatTab<R>& L = p.lat[k];
+  const int n = k ? NH : NL;
+  const int ix = i % n, iy = i / n;
+  // dphi of this plane's two 1-D nodes only (no per-node arrays)
+  R hx[kMaxN], hy[kMaxN];
+  gauss_dev<R>((R)bc.ux[side][idx], hx);
+  gauss_dev<R>((R)bc.uy[side][idx], hy);
+  R dxi = R(0), dyi = R(0);
+#pragma unroll
+  for (int m = 1; m < kMaxN; ++m)
+    if (m < n) {
+      dxi += L.vinv[ix][m] * hx[m];
+      dyi += L.vinv[iy][m] * hy[m];
+    }
+  const R px = L.w1[ix] + dxi, py = L.w1[iy] + dyi;
+  f[off + gbase] = static_cast<S>(dr * px * py + L.w1[ix] * dyi + dxi * L.w1[iy] + dxi * dyi);
+}
+
+
 template <int N, class S, class R>
 __device__ __forceinline__ void load_t(const S* f, long long plane, int base, R (*s)[kMaxN]) {
 #pragma unroll

@@ -17,6 +17,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace slbm {
@@ -77,6 +78,10 @@ struct Params {
   int nsm;                      // multiprocessors of the handle's device (launch sizing)
   LatTab<R> lat[2];             // 0 = low-order, 1 = high-order
   ConvTab<R> conv;
+  uint32_t seed;                // per-step key of the FP16 stochastic rounding
+  int* sched;                   // two tile counters of the stream kernel's scheduler
+  int sched_parity;             // the counter (and work-bit half) this step uses
+  int* work;                    // 2 x ntiles post-step work bits, accumulated by the stream kernel
 };
 
 // Co-moving (PonD) frame, Sec. II.C.  Every cell keeps its populations (as
@@ -160,7 +165,7 @@ cudaError_t launch_stream_collide(const Params<R>& p, int P, const void* tm0, co
 // Bytes of dynamic shared memory the stream-collide kernel stages per CTA, and
 // the TMA box it loads: {kTX + 8, kTY + 2G, Q}.
 size_t stream_stage_bytes(int elem_size, int nh, int G);
-void stream_box(int G, int Q, unsigned box[3]);
+void stream_box(int elem_size, int G, int Q, unsigned box[3]);
 
 // Post-step: interface conversion for band / flipped cells (flag_old = the
 // lattice each cell was computed in, flag_new = next step's flags) and, if
@@ -182,9 +187,16 @@ cudaError_t launch_ghosts(const Params<R>& p, S* f0, S* f1, const uint8_t* flag,
 
 // Per-step ghost refresh of one buffer: periodic / OUTFLOW copies of every
 // plane of both lattices and INLET equilibria (DIRICHLET ghosts are constant).
+// Per-step post-step kernel (cooperative launch): interface conversion of
+// the tiles whose work word (accumulated by the stream kernel in `work`, the
+// step's half) marks work, spread evenly over the CTAs, then the ghost-ring
+// refresh.  sync: 6 ints (`parity` selects this launch's half); counts: 1024
+// ints; list: ntiles ints.
 template <class S, class R>
-cudaError_t launch_halo(const Params<R>& p, S* f0, S* f1, const uint8_t* flag, const BcDev& bc,
-                        cudaStream_t st);
+cudaError_t launch_post_step(const Params<R>& p, S* f0, S* f1, const uint8_t* flag_old,
+                             const uint8_t* flag_new, const BcDev& bc, const int* work,
+                             int* sync, int* counts, int* list, int parity, int* err,
+                             cudaStream_t st);
 
 template <class S, class R>
 cudaError_t launch_init_eq(const Params<R>& p, S* f0, S* f1, const double* rho,

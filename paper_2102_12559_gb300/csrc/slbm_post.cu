@@ -20,4 +20,27 @@ cudaError_t launch_post<double, double>(const Params<double>& p, double* f0, dou
   return launch_post_impl<double, double>(p, f0, f1, flag_old, flag_new, bc, images, mask_in, tile_mask,
                                          st);
 }
+template <>
+cudaError_t launch_post<__half, float>(const Params<float>& p, __half* f0, __half* f1,
+                                       const uint8_t* flag_old, const uint8_t* flag_new,
+                                       const BcDev& bc, int images, const uint8_t* mask_in,
+                                       uint8_t* tile_mask, cudaStream_t st) {
+  return launch_post_impl<__half, float>(p, f0, f1, flag_old, flag_new, bc, images, mask_in,
+                                         tile_mask, st);
+}
+
+#define SLBM_POSTSTEP_INST(S, R)                                                            \
+  template <>                                                                               \
+  cudaError_t launch_post_step<S, R>(const Params<R>& p, S* f0, S* f1,                      \
+                                     const uint8_t* flag_old, const uint8_t* flag_new,      \
+                                     const BcDev& bc, const int* work, int* sync,           \
+                                     int* counts, int* list, int parity, int* err,          \
+                                     cudaStream_t st) {                                     \
+    return launch_post_step_impl<S, R>(p, f0, f1, flag_old, flag_new, bc, work, sync,       \
+                                       counts, list, parity, err, st);                      \
+  }
+SLBM_POSTSTEP_INST(float, float)
+SLBM_POSTSTEP_INST(double, double)
+SLBM_POSTSTEP_INST(__half, float)
+#undef SLBM_POSTSTEP_INST
 }  // namespace slbm

@@ -36,8 +36,14 @@
 
 namespace slbm {
 
-constexpr int kXH = 4;                           // halo columns each side (>= G, 16-byte aligned)
-constexpr int kTXP = kTX + 2 * kXH;              // staged row length (40)
+// Staged row geometry per storage type: xh halo columns each side (>= G),
+// chosen so the TMA box starts 16 bytes aligned (tile x0 + kOX - xh is a
+// multiple of 16 / sizeof(S)); txp staged elements per row.
+template <class S>
+struct StageGeom {
+  static constexpr int xh = sizeof(S) == 2 ? 8 : 4;
+  static constexpr int txp = kTX + 2 * xh;
+};
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s bound on an mbarrier wait
 
 // ------------------------------------------------------------ PTX helpers
@@ -92,6 +98,36 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, ui
 
 // ------------------------------------------------------------ the math
 
+// Store conversion of a new population value.  FP32 / FP64: plain.  FP16:
+// stochastic rounding of the deviation -- the 13 dropped mantissa bits are
+// compared against a counter-based random number (an integer hash of the
+// element index and the step), so a value is rounded up with probability
+// equal to its distance from the truncated neighbour.  Round-to-nearest
+// errors of a smooth field repeat from cell to cell and step to step and add
+// up; these are unbiased and independent, and the interpolation averages
+// them away.  Half subnormals (|v| < 2^-14) round to nearest.
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+template <class S, class R>
+__device__ __forceinline__ S to_storage(R v, uint32_t) {
+  return static_cast<S>(v);
+}
+
+template <>
+__device__ __forceinline__ __half to_storage<__half, float>(float v, uint32_t key) {
+  if (!(fabsf(v) >= 6.103515625e-05f) || fabsf(v) >= 65504.0f) return __float2half_rn(v);
+  const uint32_t b = __float_as_uint(v);
+  const uint32_t r = hash32(key) & 0x1fffu;
+  return __float2half_rz(__uint_as_float((b + r) & ~0x1fffu));
+}
+
 // One row of node jx's stencil (differential form v[r] + sum_{a != r}
 // w[a] (v[a] - v[r]), r = (P-1)/2, see LatTab).
 template <int N, bool HI, int P, class S, class R>
@@ -107,13 +143,14 @@ __device__ __forceinline__ R row_interp(const S* row, const LatTab<R>& L, int jx
 
 // Stream + collide one cell of lattice L (N nodes per axis, HI = the
 // high-order lattice) from the staged planes (cell at `src`, planes PL
-// elements apart, rows kTXP apart), on deviations s_i = f_i - W_i (streaming
+// elements apart, rows StageGeom<S>::txp apart), on deviations s_i = f_i - W_i (streaming
 // is affine in the shift; the collision uses the deviation form of the
 // product equilibrium, see slbm_eq.cuh).
 template <int N, bool HI, int P, class S, class R>
 __device__ __forceinline__ void stream_collide_cell(const Params<R>& p, const LatTab<R>& L,
                                                     const S* src, S* __restrict__ fout,
                                                     int obase, R& ux, R& uy, R& drho) {
+  constexpr int kTXP = StageGeom<S>::txp;
   constexpr int PL = (kTY + 2 * stage_halo(P)) * kTXP;
   R f[N * N];
 #pragma unroll
@@ -176,43 +213,107 @@ __device__ __forceinline__ void stream_collide_cell(const Params<R>& p, const La
       const int i = jx + N * jy;
       const R px = L.w1[jx] + dx[jx];
       const R feq = dr * px * py + L.w1[jx] * dy[jy] + dx[jx] * L.w1[jy] + dx[jx] * dy[jy];
-      fout[(size_t)i * p.plane + obase] = static_cast<S>(f[i] + p.omega * (feq - f[i]));
+      const size_t idx = (size_t)i * p.plane + obase;
+      fout[idx] = to_storage<S, R>(f[i] + p.omega * (feq - f[i]),
+                                   (uint32_t)idx ^ (p.seed * 0x9e3779b9u));
     }
   }
 }
 
 constexpr int kStages = 2;            // staged work items in flight per CTA
-constexpr int kMaxTilesPerCta = 4096;  // tile masks a persistent CTA keeps in shared memory
 
-// Work item of a persistent CTA: tile t (this CTA owns t = blockIdx.x,
-// blockIdx.x + gridDim.x, ...) and lattice k, for every lattice the tile's
-// mask holds (bit 0 low-order, bit 1 high-order).
+// Work item: tile t (coordinates tx, ty) and lattice k, for every lattice the
+// tile's mask holds (bit 0 low-order, bit 1 high-order); t = ntiles ends the
+// walk.
 struct Item {
-  int t, k;
+  int t, tx, ty, k;
 };
 
-// `mask` holds the masks of this CTA's tiles by local index (t - blockIdx.x) / gridDim.x.
-__device__ __forceinline__ int local_mask(const uint8_t* mask, int t) {
-  return mask[(t - (int)blockIdx.x) / (int)gridDim.x];
+// Dynamic tile scheduler of one CTA (run by one thread).  Tiles are taken
+// from a global counter, so CTAs that draw expensive tiles (high-order
+// lattice, two lattices) take fewer of them: a cluster of high-order tiles
+// does not pile up on the CTAs a static stride would give it.  The counter's
+// result and the taken tile's mask are fetched one decision ahead, so their
+// latencies overlap the computation.
+struct TileScheduler {
+  int* ctr;
+  const uint8_t* mask_g;
+  int ntiles, ntx;
+  int t_next, m_next;  // next tile to use and its mask (fetched)
+  int t_after;         // the one after it (counter value in flight)
+  Item cur;            // last decided item
+  int cur_mask;
+
+  __device__ __forceinline__ int take() { return atomicAdd(ctr, 1); }
+  __device__ __forceinline__ void start() {
+    t_next = take();
+    m_next = t_next < ntiles ? mask_g[t_next] : 0;
+    t_after = take();
+    cur.t = -1;
+    cur.k = 1;
+    cur_mask = 0;
+  }
+  // The item after the last decided one.
+  __device__ __forceinline__ Item decide() {
+    if (cur.t >= ntiles) return cur;
+    if (cur.t >= 0 && cur.k == 0 && (cur_mask & 2)) {
+      cur.k = 1;
+      return cur;
+    }
+    const int t = t_next;
+    cur_mask = m_next;
+    // fetch the following tile's mask, take the one after
+    t_next = t_after < ntiles ? t_after : ntiles;
+    m_next = t_next < ntiles ? mask_g[t_next] : 0;
+    t_after = t_next < ntiles ? take() : ntiles;
+    if (t >= ntiles) {
+      cur = Item{ntiles, 0, 0, 0};
+      return cur;
+    }
+    cur = Item{t, t % ntx, t / ntx, (cur_mask & 1) ? 0 : 1};
+    return cur;
+  }
+};
+
+// Position of the k-th (0-based) set bit of b, k < popc(b): a binary search
+// on the population counts of halves.
+__device__ __forceinline__ int select_bit(uint32_t b, int k) {
+  int pos = 0;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const int c = __popc(b & ((1u << w) - 1u));
+    if (k >= c) {
+      k -= c;
+      b >>= w;
+      pos += w;
+    }
+  }
+  return pos;
 }
 
-__device__ __forceinline__ Item first_item(const uint8_t* mask, int ntiles) {
-  Item it{(int)blockIdx.x, 0};
-  if (it.t < ntiles && !(local_mask(mask, it.t) & 1)) it.k = 1;
-  return it;
+// Cell of the tile (raster index ty * 32 + tx) that thread `slot` computes
+// for an item whose cells of the item's lattice are given by the warps'
+// ballots b[0..7]: the slot-th set bit in raster order, or -1.  Threads take
+// the item's cells densely, so a lattice that covers a few cells of a tile
+// occupies a few warps instead of idling lanes in every warp.
+__device__ __forceinline__ int compact_cell(const uint32_t* b, int slot) {
+  int base = 0;
+#pragma unroll
+  for (int w = 0; w < kTY; ++w) {
+    const int c = __popc(b[w]);
+    if (slot < base + c) return w * kTX + select_bit(b[w], slot - base);
+    base += c;
+  }
+  return -1;
 }
 
-__device__ __forceinline__ Item next_item(Item it, const uint8_t* mask, int ntiles) {
-  if (it.k == 0 && (local_mask(mask, it.t) & 2)) return Item{it.t, 1};
-  it.t += gridDim.x;
-  it.k = (it.t < ntiles && !(local_mask(mask, it.t) & 1)) ? 1 : 0;
-  return it;
-}
+constexpr int kRing = 4;  // decided items visible to every thread: j .. j + 3
 
 // Persistent stream-collide: each CTA walks its items through a kStages-deep
-// ring of staged buffers.  One elected thread keeps kStages TMA copies in
-// flight (the next items' planes load while the current item computes); all
-// threads compute the cells of the item's lattice, then free the stage.
+// ring of staged buffers.  Thread 0 decides the items three ahead (dynamic
+// scheduler) and keeps kStages TMA copies in flight (the next items' planes
+// load while the current item computes); the threads compute the item's
+// cells, compacted onto the leading threads, then free the stage.
 template <int NL, int NH, int P, class S, class R>
 __global__ void __launch_bounds__(kTX * kTY, 2)
 k_stream_collide(const Params<R> p, const __grid_constant__ CUtensorMap tm0,
@@ -223,95 +324,131 @@ k_stream_collide(const Params<R> p, const __grid_constant__ CUtensorMap tm0,
                  int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[kStages];
-  __shared__ uint8_t tmask[kMaxTilesPerCta];  // masks of this CTA's tiles, by local index
-  __shared__ int tile_bits[2];                // next-step mask of the tile being finished
+  __shared__ Item ring[kRing];                // decided items, by index & (kRing - 1)
+  __shared__ int tile_bits[3];                // next-step mask of the tile being finished
+  __shared__ uint32_t ballots[2][kTY];        // cells of the item's lattice, per warp
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
-  for (int m = tid; blockIdx.x + m * gridDim.x < ntiles; m += kTX * kTY)
-    tmask[m] = tile_mask_g[blockIdx.x + m * gridDim.x];
   constexpr int GH = stage_halo(P);
+  constexpr int kTXP = StageGeom<S>::txp, kXH = StageGeom<S>::xh;
   constexpr int pl = (kTY + 2 * GH) * kTXP;  // staged elements per plane (rows y0-GH ..)
   constexpr int stage = NH * NH * pl;        // staged elements per stage (larger lattice)
   S* sm = reinterpret_cast<S*>(smem_raw);
+  TileScheduler sched;
+  auto issue = [&](const Item& q, int s) {
+    const int Q = q.k ? NH * NH : NL * NL;
+    mbar_expect_tx(&full[s], (uint32_t)(Q * pl * (int)sizeof(S)));
+    tma_load_3d(sm + s * stage, q.k ? &tm1 : &tm0, &full[s], q.tx * kTX + kOX - kXH,
+                q.ty * kTY + p.G - GH, 0);
+  };
   if (tid == 0) {
+    // this launch's counter p.sched[parity] was cleared by the previous launch;
+    // clear the other one for the next
+    if (blockIdx.x == 0) p.sched[p.sched_parity ^ 1] = 0;
     for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
     mbar_fence_init();
-    tile_bits[0] = tile_bits[1] = 0;
+    tile_bits[0] = tile_bits[1] = tile_bits[2] = 0;
+    sched = TileScheduler{p.sched + p.sched_parity, tile_mask_g, ntiles, ntx, 0, 0, 0, Item{}, 0};
+    sched.start();
+    for (int j = 0; j < kRing - 1; ++j) ring[j] = sched.decide();
+    for (int s = 0; s < kStages; ++s)
+      if (ring[s].t < ntiles) issue(ring[s], s);
   }
   __syncthreads();
-  const uint8_t* tile_mask = tmask;
-  Item pc = first_item(tile_mask, ntiles);  // producer cursor (thread 0 only)
-  if (tid == 0)
-    for (int s = 0; s < kStages && pc.t < ntiles; ++s) {
-      const int Q = pc.k ? NH * NH : NL * NL;
-      mbar_expect_tx(&full[s], (uint32_t)(Q * pl * (int)sizeof(S)));
-      tma_load_3d(sm + s * stage, pc.k ? &tm1 : &tm0, &full[s], (pc.t % ntx) * kTX + kOX - kXH,
-                  (pc.t / ntx) * kTY + p.G - GH, 0);
-      pc = next_item(pc, tile_mask, ntiles);
-    }
-  // this thread's cell flag for an item, loaded one item ahead
+  // this thread's raster cell flag for an item (2 outside the grid)
   auto cell_flag = [&](const Item& q) -> int {
     if (q.t >= ntiles) return 2;
-    const int xx = (q.t % ntx) * kTX + tx, yy = (q.t / ntx) * kTY + ty;
+    const int xx = q.tx * kTX + tx, yy = q.ty * kTY + ty;
     return (xx < p.nx && yy < p.ny) ? flag_cur[xx + p.nx * yy] : 2;
   };
-  int j = 0;
-  int bits = 0;  // this thread's cell: bit 0/1 = next-step lattice, bit 2 = flipped
-  Item it = first_item(tile_mask, ntiles);
-  int fl_next = cell_flag(it);
-  for (; it.t < ntiles; ++j) {
-    const Item nx_it = next_item(it, tile_mask, ntiles);
-    const int fl = fl_next;
-    fl_next = cell_flag(nx_it);
+  {
+    const Item it0 = ring[0];
+    const uint32_t b = __ballot_sync(0xffffffffu, cell_flag(it0) == it0.k);
+    if (tx == 0) ballots[0][ty] = b;
+  }
+  int fl_next = cell_flag(ring[1]);  // flags are loaded one item ahead
+  __syncthreads();
+  int bits = 0;  // cells this thread computed: bit 0/1 = next-step lattice, bit 2 = flipped
+  for (int j = 0;; ++j) {
+    const Item it = ring[j & (kRing - 1)];
+    if (it.t >= ntiles) break;
+    const Item nx_it = ring[(j + 1) & (kRing - 1)];
+    const Item nn_it = ring[(j + 2) & (kRing - 1)];
+    if (tid == 0) ring[(j + 3) & (kRing - 1)] = sched.decide();  // published by the barrier
     const int s = j % kStages;
-    const int x0 = (it.t % ntx) * kTX, y0 = (it.t / ntx) * kTY;
-    const int x = x0 + tx, y = y0 + ty;
+    const int x0 = it.tx * kTX, y0 = it.ty * kTY;
+    const int cell = compact_cell(ballots[j & 1], tid);
+    // ballot of the next item's cells (published by the barrier below)
+    {
+      const uint32_t b = __ballot_sync(0xffffffffu, fl_next == nx_it.k);
+      if (tx == 0) ballots[(j + 1) & 1][ty] = b;
+    }
     if (!mbar_wait(&full[s], (uint32_t)((j / kStages) & 1))) {
       // bounded: record, give the copy one more bounded wait, stop
       if (tid == 0) atomicExch(err, 1);
       mbar_wait(&full[s], (uint32_t)((j / kStages) & 1));
       return;
     }
-    if (fl == it.k) {
-      const S* cell = sm + s * stage + (ty + GH) * kTXP + (tx + kXH);
+    fl_next = cell_flag(nn_it);
+    if (cell >= 0) {
+      const int cx = cell & (kTX - 1), cy = cell / kTX;
+      const S* src = sm + s * stage + (cy + GH) * kTXP + (cx + kXH);
+      const int x = x0 + cx, y = y0 + cy;
       const int obase = (y + p.G) * p.pitch + (x + kOX);
       R ux, uy, dr;  // dr: density deviation (unused here)
       if (it.k == 0)
-        stream_collide_cell<NL, false, P, S, R>(p, p.lat[0], cell, fout0, obase, ux, uy, dr);
+        stream_collide_cell<NL, false, P, S, R>(p, p.lat[0], src, fout0, obase, ux, uy, dr);
       else
-        stream_collide_cell<NH, true, P, S, R>(p, p.lat[1], cell, fout1, obase, ux, uy, dr);
-
-      int nf = fl;
+        stream_collide_cell<NH, true, P, S, R>(p, p.lat[1], src, fout1, obase, ux, uy, dr);
+      int nf = it.k;
       if (p.crit == 1) {
         nf = sqrt(ux * ux + uy * uy) > p.thr ? 1 : 0;
         flag_nxt[x + p.nx * y] = (uint8_t)nf;
       }
-      bits = (1 << nf) | (nf != fl ? 4 : 0);
+      bits |= (1 << nf) | (nf != it.k ? 4 : 0);
     }
     // after a tile's last item: the lattices its cells carry next step and
     // whether any flipped (read by the post-step kernel to skip quiet tiles
-    // and by the next launch's producer), OR-reduced per warp, then through
+    // and by the next launch's scheduler), OR-reduced per warp, then through
     // a shared word made visible by the stage-release barrier below
     const bool tile_end = nx_it.t != it.t;
     if (tile_end) {
       const int wbits = __reduce_or_sync(0xffffffffu, bits);
-      if ((tid & 31) == 0 && wbits) atomicOr(&tile_bits[j & 1], wbits);
+      if (tx == 0 && wbits) atomicOr(&tile_bits[j % 3], wbits);
       bits = 0;
     }
-    __syncthreads();  // stage s is free again; tile_bits complete
-    if (tile_end && tid == 0) {
-      mask_next[it.t] = (uint8_t)tile_bits[j & 1];
-      tile_bits[j & 1] = 0;
+    // the slot the next item accumulates into was last read two items ago
+    if (tid == 0) tile_bits[(j + 1) % 3] = 0;
+    __syncthreads();  // stage s is free again; tile_bits, ballots and ring complete
+    if (tile_end && tid < 9) {
+      // the tile's next-step mask, and its contribution to the post-step
+      // kernel's work bits of the 3 x 3 tile neighbourhood: the lattices (all
+      // nine) and the flip bit (the tile itself); a tile has conversion work
+      // iff its word ends with both lattices or a flip
+      const int m = tile_bits[j % 3];
+      if (tid == 0) mask_next[it.t] = (uint8_t)m;
+      int ntx_ = it.tx + tid % 3 - 1, nty_ = it.ty + tid / 3 - 1;
+      const int nty = (ntiles + ntx - 1) / ntx;
+      bool ok = true;
+      if (ntx_ < 0 || ntx_ >= ntx) {
+        if (p.periodic_x) ntx_ = ntx_ < 0 ? ntx_ + ntx : ntx_ - ntx;
+        else ok = false;
+      }
+      if (nty_ < 0 || nty_ >= nty) {
+        if (p.periodic_y) nty_ = nty_ < 0 ? nty_ + nty : nty_ - nty;
+        else ok = false;
+      }
+      const int contrib = (m & 3) | (tid == 4 ? (m & 4) : 0);
+      if (ok && contrib) atomicOr(p.work + p.sched_parity * ntiles + nty_ * ntx + ntx_, contrib);
+      // the other half is the next step's: clear this tile's word there
+      if (tid == 0) p.work[(p.sched_parity ^ 1) * ntiles + it.t] = 0;
     }
-    if (tid == 0 && pc.t < ntiles) {
-      // order the CTA's shared-memory reads of stage s before the async-proxy write
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      const int Q = pc.k ? NH * NH : NL * NL;
-      mbar_expect_tx(&full[s], (uint32_t)(Q * pl * (int)sizeof(S)));
-      tma_load_3d(sm + s * stage, pc.k ? &tm1 : &tm0, &full[s], (pc.t % ntx) * kTX + kOX - kXH,
-                  (pc.t / ntx) * kTY + p.G - GH, 0);
-      pc = next_item(pc, tile_mask, ntiles);
+    if (tid == 0) {
+      if (nn_it.t < ntiles) {
+        // order the CTA's shared-memory reads of stage s before the async-proxy write
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(nn_it, s);
+      }
     }
-    it = nx_it;
   }
 }
 
@@ -325,7 +462,8 @@ cudaError_t launch_stream_collide_impl(const Params<R>& p, int P, const CUtensor
   const int ntx = (p.nx + kTX - 1) / kTX, nty = (p.ny + kTY - 1) / kTY;
   const int ntiles = ntx * nty;
   const int nl = p.lat[0].n, nh = p.lat[1].n;
-  const size_t smem = (size_t)kStages * nh * nh * (kTY + 2 * stage_halo(P)) * kTXP * sizeof(S);
+  const size_t smem =
+      (size_t)kStages * nh * nh * (kTY + 2 * stage_halo(P)) * StageGeom<S>::txp * sizeof(S);
   if (p.G < stage_halo(P)) return cudaErrorInvalidValue;  // ghost ring narrower than the stage halo
   const int nsm = p.nsm;
 #define SLBM_SC_CASE(NL, NH, PP)                                                            \
@@ -348,7 +486,6 @@ cudaError_t launch_stream_collide_impl(const Params<R>& p, int P, const CUtensor
     }                                                                                       \
     if (per_sm < 1) return cudaErrorInvalidConfiguration;                                   \
     const int grid = ntiles < per_sm * nsm ? ntiles : per_sm * nsm;                         \
-    if ((ntiles + grid - 1) / grid > kMaxTilesPerCta) return cudaErrorInvalidValue;         \
     kern<<<grid, blk, smem, st>>>(p, *tm0, *tm1, fout0, fout1, flag_cur, flag_nxt,          \
                                   tile_mask, mask_next, ntx, ntiles, bc, err);              \
     return cudaGetLastError();                                                              \

@@ -14,12 +14,16 @@ cudaError_t launch_stream_collide<float, float>(const Params<float>& p, int P, c
                                             st);
 }
 
-size_t stream_stage_bytes(int elem_size, int nh, int G) {
-  return (size_t)nh * nh * (kTY + 2 * G) * kTXP * elem_size;
+static int staged_row(int elem_size) {
+  return elem_size == 2 ? StageGeom<__half>::txp : StageGeom<float>::txp;
 }
 
-void stream_box(int G, int Q, unsigned box[3]) {
-  box[0] = kTXP;
+size_t stream_stage_bytes(int elem_size, int nh, int G) {
+  return (size_t)nh * nh * (kTY + 2 * G) * staged_row(elem_size) * elem_size;
+}
+
+void stream_box(int elem_size, int G, int Q, unsigned box[3]) {
+  box[0] = staged_row(elem_size);
   box[1] = kTY + 2 * G;
   box[2] = Q;
 }

@@ -23,7 +23,7 @@ SLBM_ENONFINITE, SLBM_ENOCONV, SLBM_ETIMEOUT, SLBM_ESTATE = -4, -5, -6, -7
 SLBM_D2Q9, SLBM_D2Q16, SLBM_D2Q25 = 3, 4, 5
 SLBM_FRAME_LATTICE, SLBM_FRAME_POND, SLBM_FRAME_POND_ISOTHERMAL = 0, 1, 2
 SLBM_POND_REACH = 5
-SLBM_FP32, SLBM_FP64 = 0, 1
+SLBM_FP32, SLBM_FP64, SLBM_FP16 = 0, 1, 2
 SLBM_BC_OUTFLOW, SLBM_BC_DIRICHLET, SLBM_BC_INLET = 0, 1, 2
 SLBM_SIDE_XMIN, SLBM_SIDE_XMAX, SLBM_SIDE_YMIN, SLBM_SIDE_YMAX = 0, 1, 2, 3
 SLBM_CRIT_NONE, SLBM_CRIT_MACH = 0, 1
@@ -36,8 +36,8 @@ EXPORTS = [
     "slbm_profile", "slbm_profile_read", "slbm_audit_dense_noalloc", "slbm_last_error",
     "slbm_set_pond", "slbm_get_frame", "slbm_set_frame",
 ]
-SLBM_PROFILE_KERNELS = 3
-KERNEL_NAMES = ("stream_collide", "interface_convert", "halo")
+SLBM_PROFILE_KERNELS = 2
+KERNEL_NAMES = ("stream_collide", "post_step")
 
 
 class slbm_grid(ctypes.Structure):
