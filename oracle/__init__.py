@@ -36,6 +36,7 @@ FRAME_POND_ISOTHERMAL = 2
 BC_OUTFLOW = 0
 BC_DIRICHLET = 1
 BC_INLET = 2
+BC_DIFFUSE = 3
 
 
 def build(force: bool = False) -> str:

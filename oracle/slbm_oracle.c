@@ -48,7 +48,10 @@
  *   - Boundary ghost nodes hold the boundary state in whichever lattice reads
  *     them: DIRICHLET = equilibrium at a fixed rho, u; INLET = fixed u with rho
  *     copied from the first interior node; OUTFLOW = copy of the nearest
- *     interior node.  A non-periodic y side takes precedence at corners.
+ *     interior node; DIFFUSE = diffuse-reflection wall (populations entering
+ *     the fluid at the wall-velocity equilibrium with zero net normal mass
+ *     flux against the first interior node, the others copied from it).  A
+ *     non-periodic y side takes precedence at corners.
  *   - Co-moving frame: no snapping of departure points; the iteration stops
  *     when max(|du_x|, |du_y|, |dT|) <= tol between the frame used and the
  *     moments it produced, or after maxit reconstructions; the populations
@@ -377,7 +380,7 @@ long orc_first_node(int p, double xd)
 
 /* ------------------------------------------------------------ the solver */
 
-enum { ORC_BC_OUTFLOW = 0, ORC_BC_DIRICHLET = 1, ORC_BC_INLET = 2 };
+enum { ORC_BC_OUTFLOW = 0, ORC_BC_DIRICHLET = 1, ORC_BC_INLET = 2, ORC_BC_DIFFUSE = 3 };
 
 typedef struct {
     int kind;
@@ -609,6 +612,32 @@ static double cell_rho(const orc_t *s, long c)
     return r;
 }
 
+/* Diffuse-reflection wall ghost (the kinetic wall of the Couette flow of
+ * Sec. IV.C; the paper names the condition without giving its formula).
+ * The wall's normal is `axis` (0 = x, 1 = y) with the fluid on the side of
+ * sign n.  Populations entering the fluid (c.n > 0) are the lattice
+ * equilibrium at the wall velocity (eq. feqL0), scaled so that the mass they
+ * carry into the fluid equals the mass the first interior node `base` sends
+ * into the wall (zero net normal flux); the others copy that node. */
+static void diffuse_ghost(const orc_t *s, int k, const double *base, int axis, double n,
+                          double uwx, double uwy, double *out)
+{
+    const olat *L = &s->L[k];
+    double feq[ORC_MAXQ];
+    eq_lat(s, k, 1.0, uwx, uwy, feq);
+    double out_flux = 0.0, in_unit = 0.0;
+    for (int i = 0; i < L->Q; ++i) {
+        double cn = (axis ? L->cy[i] : L->cx[i]) * n;
+        if (cn < 0.0) out_flux -= cn * base[i];
+        else if (cn > 0.0) in_unit += cn * feq[i];
+    }
+    double rho_w = out_flux / in_unit;
+    for (int i = 0; i < L->Q; ++i) {
+        double cn = (axis ? L->cy[i] : L->cx[i]) * n;
+        out[i] = cn > 0.0 ? rho_w * feq[i] : base[i];
+    }
+}
+
 /* Population vector of node (gx, gy) at the old time level, expressed in
  * lattice k (step 2 of Sec. III.D), with periodic wrap and boundary ghosts. */
 static const double *node_vec(orc_t *s, long gx, long gy, int k)
@@ -636,6 +665,9 @@ static const double *node_vec(orc_t *s, long gx, long gy, int k)
         long yi = gy < 0 ? 0 : s->ny - 1;
         if (b->kind == ORC_BC_OUTFLOW) {
             memcpy(out, node_vec(s, gx, yi, k), sizeof(double) * Q);
+        } else if (b->kind == ORC_BC_DIFFUSE) {
+            diffuse_ghost(s, k, node_vec(s, gx, yi, k), 1, gy < 0 ? 1.0 : -1.0, b->ux[xi],
+                          b->uy[xi], out);
         } else {
             double rho = b->kind == ORC_BC_INLET ? cell_rho(s, cidx(s, xi, yi)) : b->rho[xi];
             eq_lat(s, k, rho, b->ux[xi], b->uy[xi], out);
@@ -645,6 +677,9 @@ static const double *node_vec(orc_t *s, long gx, long gy, int k)
         long xi = gx < 0 ? 0 : s->nx - 1;
         if (b->kind == ORC_BC_OUTFLOW) {
             memcpy(out, node_vec(s, xi, gy, k), sizeof(double) * Q);
+        } else if (b->kind == ORC_BC_DIFFUSE) {
+            diffuse_ghost(s, k, node_vec(s, xi, gy, k), 0, gx < 0 ? 1.0 : -1.0, b->ux[gy],
+                          b->uy[gy], out);
         } else {
             double rho = b->kind == ORC_BC_INLET ? cell_rho(s, cidx(s, xi, gy)) : b->rho[gy];
             eq_lat(s, k, rho, b->ux[gy], b->uy[gy], out);
