@@ -101,11 +101,18 @@ typedef struct slbm_s *slbm_t;
  *  OUTFLOW   zero-order extrapolation: copy of the nearest interior cell;
  *  DIRICHLET lattice equilibrium at a prescribed rho, u ("free stream");
  *  INLET     lattice equilibrium at a prescribed u and the rho of the first
- *            interior cell (fixed velocity, zero pressure gradient, Sec. IV.A).
+ *            interior cell (fixed velocity, zero pressure gradient, Sec. IV.A);
+ *  DIFFUSE   diffuse-reflection wall moving with a prescribed velocity (the
+ *            kinetic wall of the Couette flow, Sec. IV.C): populations entering
+ *            the fluid are the lattice equilibrium at the wall velocity, scaled
+ *            so no net mass crosses the wall against the first interior cell;
+ *            the others copy that cell.  The axis along the wall must be
+ *            periodic.
  * A non-periodic y side takes precedence over an x side at the corners. */
 #define SLBM_BC_OUTFLOW   0
 #define SLBM_BC_DIRICHLET 1
 #define SLBM_BC_INLET     2
+#define SLBM_BC_DIFFUSE   3
 
 /* Sides. */
 #define SLBM_SIDE_XMIN 0
@@ -184,7 +191,7 @@ SLBM_API int slbm_set_criterion(slbm_t h, int kind, double threshold);
 
 /* Boundary of a non-periodic side.  Arrays run along the side (ny entries
  * for XMIN/XMAX, nx for YMIN/YMAX), host doubles, copied: DIRICHLET needs
- * rho, ux, uy; INLET needs ux, uy (rho NULL); OUTFLOW needs none. */
+ * rho, ux, uy; INLET and DIFFUSE need ux, uy (rho NULL); OUTFLOW needs none. */
 SLBM_API int slbm_set_boundary(slbm_t h, int side, int kind, const double *rho, const double *ux,
                       const double *uy);
 

@@ -1026,9 +1026,13 @@ int slbm_set_boundary(slbm_t h, int side, int kind, const double* rho, const dou
     return fail(h, SLBM_EINVAL, "side is periodic");
   if (kind == SLBM_BC_DIRICHLET && (!rho || !ux || !uy))
     return fail(h, SLBM_EINVAL, "DIRICHLET needs rho, ux, uy");
-  if (kind == SLBM_BC_INLET && (!ux || !uy)) return fail(h, SLBM_EINVAL, "INLET needs ux, uy");
-  if (kind != SLBM_BC_OUTFLOW && kind != SLBM_BC_DIRICHLET && kind != SLBM_BC_INLET)
+  if ((kind == SLBM_BC_INLET || kind == SLBM_BC_DIFFUSE) && (!ux || !uy))
+    return fail(h, SLBM_EINVAL, "INLET and DIFFUSE need ux, uy");
+  if (kind != SLBM_BC_OUTFLOW && kind != SLBM_BC_DIRICHLET && kind != SLBM_BC_INLET &&
+      kind != SLBM_BC_DIFFUSE)
     return fail(h, SLBM_EINVAL, "unknown boundary kind");
+  if (kind == SLBM_BC_DIFFUSE && !(side < 2 ? h->g.periodic_y : h->g.periodic_x))
+    return fail(h, SLBM_EINVAL, "a DIFFUSE wall needs the axis along it periodic");
   const size_t len = (size_t)(side < 2 ? h->g.ny : h->g.nx);
   const double* src[3] = {rho, ux, uy};
   for (int q = 0; q < 3; ++q)

@@ -64,42 +64,29 @@ __global__ void k_ghosts(const Params<R> p, S* f0, S* f1, const uint8_t* __restr
   if (idx >= total) return;
   int gx, gy;
   ghost_coords(G, p.nx, p.ny, idx, gx, gy);
-  int sx = gx, sy = gy;
-  if (p.periodic_x) sx = wrap(sx, p.nx);
-  if (p.periodic_y) sy = wrap(sy, p.ny);
-  bool eq = false;
-  double er = 1.0, eu = 0.0, ev = 0.0;
-  if (sy < 0 || sy >= p.ny) {  // non-periodic y side (wins at corners)
-    const int side = sy < 0 ? SLBM_SIDE_YMIN : SLBM_SIDE_YMAX;
-    const int xi = min(max(sx, 0), p.nx - 1), yi = sy < 0 ? 0 : p.ny - 1;
-    const int kind = bc.kind[side];
-    if (kind == SLBM_BC_OUTFLOW) {
-      sy = yi;
-    } else {
-      eq = true;
-      er = kind == SLBM_BC_INLET ? cell_rho<S, R>(p, f0, f1, flag, xi, yi) : bc.rho[side][xi];
-      eu = bc.ux[side][xi];
-      ev = bc.uy[side][xi];
-    }
-  }
-  if (!eq && (sx < 0 || sx >= p.nx)) {  // non-periodic x side
-    const int side = sx < 0 ? SLBM_SIDE_XMIN : SLBM_SIDE_XMAX;
-    const int xi = sx < 0 ? 0 : p.nx - 1;
-    const int kind = bc.kind[side];
-    if (kind == SLBM_BC_OUTFLOW) {
-      sx = xi;
-    } else {
-      eq = true;
-      er = kind == SLBM_BC_INLET ? cell_rho<S, R>(p, f0, f1, flag, xi, sy) : bc.rho[side][sy];
-      eu = bc.ux[side][sy];
-      ev = bc.uy[side][sy];
-    }
-  }
+  int sx, sy, side = 0, bidx = 0;
+  const int kind = ghost_source(p.nx, p.ny, p.periodic_x, p.periodic_y, bc, gx, gy, sx, sy, side,
+                                bidx);
   const int gbase = (gy + G) * p.pitch + (gx + kOX);
-  if (eq) {
-    write_eq_both<S, R>(p, f0, f1, gbase, er, eu, ev);
+  const int sbase = (sy + G) * p.pitch + (sx + kOX);
+  if (kind == 1 || kind == 2) {
+    const double er = kind == 1 ? cell_rho<S, R>(p, f0, f1, flag, sx, sy) : bc.rho[side][bidx];
+    write_eq_both<S, R>(p, f0, f1, gbase, er, bc.ux[side][bidx], bc.uy[side][bidx]);
+  } else if (kind == 3) {
+    // diffuse wall, both lattices, every population
+    const R uwx = (R)bc.ux[side][bidx], uwy = (R)bc.uy[side][bidx];
+    for (int k = 0; k < 2; ++k) {
+      S* f = k ? f1 : f0;
+      const int n = p.lat[k].n;
+      for (int i = 0; i < n * n; ++i) {
+        R v;
+        if (n == 3) v = diffuse_value<3, S, R>(p.lat[k], f, p.plane, sbase, side, uwx, uwy, i);
+        else if (n == 4) v = diffuse_value<4, S, R>(p.lat[k], f, p.plane, sbase, side, uwx, uwy, i);
+        else v = diffuse_value<5, S, R>(p.lat[k], f, p.plane, sbase, side, uwx, uwy, i);
+        f[(size_t)i * p.plane + gbase] = static_cast<S>(v);
+      }
+    }
   } else {
-    const int sbase = (sy + G) * p.pitch + (sx + kOX);
     const int q0 = p.lat[0].n * p.lat[0].n, q1 = p.lat[1].n * p.lat[1].n;
     S v[kMaxN * kMaxN];  // loads first, then stores (no serialised round trips)
     for (int i = 0; i < q0; ++i) v[i] = f0[(size_t)i * p.plane + sbase];

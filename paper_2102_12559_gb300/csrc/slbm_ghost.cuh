@@ -4,7 +4,8 @@
 // non-periodic y side takes precedence at corners; OUTFLOW ghosts copy the
 // nearest interior cell; INLET ghosts are the lattice equilibrium at the
 // prescribed velocity and the density of the first interior cell; DIRICHLET
-// ghosts are constant.
+// ghosts are constant; DIFFUSE ghosts are a diffuse-reflection wall
+// (diffuse_value).
 #pragma once
 
 #include "../../include/slbm.h"
@@ -35,7 +36,9 @@ __device__ __forceinline__ void ghost_coords(int G, int nx, int ny, int g, int& 
 
 // Source of ghost (gx, gy) under the ghost rule: kind 0 = copy of interior
 // (sx, sy); 1 = INLET equilibrium (density of interior (sx, sy), velocity
-// bc[side][idx]); 2 = DIRICHLET (constant, written at setup).
+// bc[side][idx]); 2 = DIRICHLET (constant, written at setup); 3 = DIFFUSE
+// wall against interior (sx, sy) with wall velocity bc[side][idx] (the axis
+// along the wall is periodic, so (sx, sy) is interior).
 __device__ __forceinline__ int ghost_source(int nx, int ny, int px, int py, const BcDev& bc,
                                             int gx, int gy, int& sx, int& sy, int& side,
                                             int& idx) {
@@ -49,7 +52,7 @@ __device__ __forceinline__ int ghost_source(int nx, int ny, int px, int py, cons
       sy = yi;
     } else {
       sx = xi; sy = yi; idx = xi;
-      return kind == SLBM_BC_INLET ? 1 : 2;
+      return kind == SLBM_BC_INLET ? 1 : (kind == SLBM_BC_DIFFUSE ? 3 : 2);
     }
   }
   if (sx < 0 || sx >= nx) {  // non-periodic x side
@@ -60,10 +63,54 @@ __device__ __forceinline__ int ghost_source(int nx, int ny, int px, int py, cons
       sx = xi;
     } else {
       sx = xi; idx = sy;
-      return kind == SLBM_BC_INLET ? 1 : 2;
+      return kind == SLBM_BC_INLET ? 1 : (kind == SLBM_BC_DIFFUSE ? 3 : 2);
     }
   }
   return 0;
+}
+
+// Diffuse-reflection wall ghost, population i of lattice L (N nodes per axis),
+// on deviations.  The wall of `side` has its normal along x (XMIN / XMAX) or y
+// (YMIN / YMAX), fluid on the side of sign n.  Populations entering the fluid
+// (c.n > 0) are the lattice equilibrium at the wall velocity (uwx, uwy), scaled
+// to rho_w so the mass they carry into the fluid equals the mass the interior
+// cell (deviations s at `sbase` in L's planes f) sends into the wall; the
+// others copy that cell.  With e_j = f^L_j(1, u_w) - W_j and the symmetric
+// sum A = sum_{c.n>0} (c.n) W_j = sum_{c.n<0} |c.n| W_j:
+//   rho_w - 1 = (sum_{c.n<0} |c.n| s_j - sum_{c.n>0} (c.n) e_j) / (A + sum_{c.n>0} (c.n) e_j).
+template <int N, class S, class R>
+__device__ __forceinline__ R diffuse_value(const LatTab<R>& L, const S* f, long long plane,
+                                           int sbase, int side, R uwx, R uwy, int i) {
+  const bool axis_y = side >= SLBM_SIDE_YMIN;
+  const R nsign = (side == SLBM_SIDE_XMIN || side == SLBM_SIDE_YMIN) ? R(1) : R(-1);
+  R dx[N], dy[N];
+  dphi<R>(L, N, uwx, dx);
+  dphi<R>(L, N, uwy, dy);
+  R s_out = R(0), e_in = R(0), a = R(0), s_i = R(0), e_i = R(0), cn_i = R(0), w_i = R(0);
+#pragma unroll
+  for (int jy = 0; jy < N; ++jy)
+#pragma unroll
+    for (int jx = 0; jx < N; ++jx) {
+      const int j = jx + N * jy;
+      const R cn = (axis_y ? L.c[jy] : L.c[jx]) * nsign;
+      const R w = L.w1[jx] * L.w1[jy];
+      const R e = L.w1[jx] * dy[jy] + dx[jx] * L.w1[jy] + dx[jx] * dy[jy];
+      const R sj = static_cast<R>(__ldcg(f + (size_t)j * plane + sbase));
+      if (cn < R(0)) s_out -= cn * sj;
+      if (cn > R(0)) {
+        e_in += cn * e;
+        a += cn * w;
+      }
+      if (j == i) {
+        s_i = sj;
+        e_i = e;
+        cn_i = cn;
+        w_i = w;
+      }
+    }
+  if (!(cn_i > R(0))) return s_i;
+  const R drw = (s_out - e_in) / (a + e_in);
+  return drw * (w_i + e_i) + e_i;
 }
 
 // Per-step ghost refresh of one element: ghost g (0 <= g < nghost) of the
@@ -92,6 +139,13 @@ __device__ __forceinline__ void halo_element(const Params<R>& p, S* f0, S* f1,
   const int sbase = (sy + p.G) * p.pitch + (sx + kOX);
   if (kind == 0) {
     f[off + gbase] = __ldcg(f + off + sbase);
+    return;
+  }
+  if (kind == 3) {
+    const R uwx = (R)bc.ux[side][idx], uwy = (R)bc.uy[side][idx];
+    f[off + gbase] = static_cast<S>(
+        k ? diffuse_value<NH, S, R>(p.lat[1], f1, p.plane, sbase, side, uwx, uwy, i)
+          : diffuse_value<NL, S, R>(p.lat[0], f0, p.plane, sbase, side, uwx, uwy, i));
     return;
   }
   // INLET: density deviation of the interior cell from its own lattice
