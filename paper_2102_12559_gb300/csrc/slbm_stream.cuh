@@ -205,14 +205,18 @@ __device__ __forceinline__ void stream_collide_cell(const Params<R>& p, const La
   R dx[N], dy[N];
   dphi<R>(L, N, ux, dx);
   dphi<R>(L, N, uy, dy);
+  R px[N];
+#pragma unroll
+  for (int jx = 0; jx < N; ++jx) px[jx] = L.w1[jx] + dx[jx];
 #pragma unroll
   for (int jy = 0; jy < N; ++jy) {
     const R py = L.w1[jy] + dy[jy];
+    const R ty = dr * py;
 #pragma unroll
     for (int jx = 0; jx < N; ++jx) {
       const int i = jx + N * jy;
-      const R px = L.w1[jx] + dx[jx];
-      const R feq = dr * px * py + L.w1[jx] * dy[jy] + dx[jx] * L.w1[jy] + dx[jx] * dy[jy];
+      // f^L - W = dr px py + w_x dphi_y + dphi_x (w_y + dphi_y)
+      const R feq = px[jx] * ty + L.w1[jx] * dy[jy] + dx[jx] * py;
       const size_t idx = (size_t)i * p.plane + obase;
       fout[idx] = to_storage<S, R>(f[i] + p.omega * (feq - f[i]),
                                    (uint32_t)idx ^ (p.seed * 0x9e3779b9u));
@@ -297,6 +301,10 @@ __device__ __forceinline__ int select_bit(uint32_t b, int k) {
 // the item's cells densely, so a lattice that covers a few cells of a tile
 // occupies a few warps instead of idling lanes in every warp.
 __device__ __forceinline__ int compact_cell(const uint32_t* b, int slot) {
+  uint32_t all = 0xffffffffu;
+#pragma unroll
+  for (int w = 0; w < kTY; ++w) all &= b[w];
+  if (all == 0xffffffffu) return slot;  // the lattice covers the whole tile
   int base = 0;
 #pragma unroll
   for (int w = 0; w < kTY; ++w) {
