@@ -123,6 +123,8 @@ typedef struct slbm_s *slbm_t;
 /* Refinement criteria (Sec. IV.A). */
 #define SLBM_CRIT_NONE 0     /* flags stay as set by slbm_set_flags */
 #define SLBM_CRIT_MACH 1     /* after every step: flag = (|u| / c_s > threshold), c_s = 1 */
+#define SLBM_CRIT_MLP  2     /* every `interval` steps: flag = (indicator logit > threshold),
+                                the learned indicator of slbm_set_indicator */
 
 typedef struct {
     int nx, ny;              /* cells, each >= 1 and >= the stencil width */
@@ -183,11 +185,37 @@ SLBM_API int slbm_init_equilibrium(slbm_t h, const double *rho, const double *ux
 SLBM_API int slbm_set_flags(slbm_t h, const uint8_t *flags);
 SLBM_API int slbm_get_flags(slbm_t h, uint8_t *flags);
 
-/* Refinement criterion (SLBM_CRIT_*), threshold on the Mach number |u| / c_s,
- * c_s = sqrt(T_L) = 1.  SLBM_CRIT_MACH is applied at once to the current
- * state (flips lifted / projected, asynchronous) and after every step.
+/* Refinement criterion (SLBM_CRIT_*).  SLBM_CRIT_MACH: threshold on the Mach
+ * number |u| / c_s, c_s = sqrt(T_L) = 1, applied at once to the current state
+ * (flips lifted / projected, asynchronous) and after every step.
+ * SLBM_CRIT_MLP: threshold on the learned indicator's logit (0 = probability
+ * 1/2), applied at once and every `interval` steps; needs slbm_set_indicator.
  * Lattice frame only (SLBM_EINVAL otherwise). */
 SLBM_API int slbm_set_criterion(slbm_t h, int kind, double threshold);
+
+/* Learned refinement indicator (lattice frame).  Not in the paper, which
+ * refines by plain Mach / Knudsen criteria (Sec. IV); the indicator is a small
+ * MLP trained to reproduce such a criterion from local moments and their
+ * gradients, with the plain criterion as its fallback (SLBM_CRIT_MACH) and
+ * the judge of its error.  Per cell, 16 features, each times a fixed scale:
+ *   rho - 1 (x10), u_x, u_y (x3), T - 1 (x10, kinetic T), the non-equilibrium
+ *   stress sum c_a c_b (f - f^L) for xx, xy, yy (x100), the non-equilibrium
+ *   energy flux 1/2 sum c_a |c|^2 (f - f^L) for x, y (x100), the central
+ *   differences d/dx, d/dy of rho, u_x, u_y (x100; periodic wrap, else the edge
+ *   cell repeated), |u| (x3) -- all from the cell's own lattice.
+ * Network: h1 = relu(x W1 + b1) (W1 16 x 32), h2 = relu(h1 W2 + b2) (W2 32 x 32),
+ * logit = h2 . w3 + b3; W1, W2 row-major (input index first), stored in FP16,
+ * inputs rounded to FP16, accumulation in FP32 (tensor cores).
+ * slbm_set_indicator copies the weights (host floats) to device memory it
+ * allocates and owns; `interval` >= 1 is the step interval at which
+ * SLBM_CRIT_MLP re-evaluates the flags.
+ * slbm_indicator_eval: features (nx*ny x 16 floats, cell-major), logits
+ * (nx*ny floats) and flags (logit > the criterion threshold, 0 unless set)
+ * of the current state to host arrays; any may be NULL (logits / flags need
+ * weights).  Synchronises; allocates temporary device memory. */
+SLBM_API int slbm_set_indicator(slbm_t h, const float *w1, const float *b1, const float *w2,
+                                const float *b2, const float *w3, float b3, int interval);
+SLBM_API int slbm_indicator_eval(slbm_t h, float *features, float *logits, uint8_t *flags);
 
 /* Boundary of a non-periodic side.  Arrays run along the side (ny entries
  * for XMIN/XMAX, nx for YMIN/YMAX), host doubles, copied: DIRICHLET needs

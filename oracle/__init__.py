@@ -202,6 +202,7 @@ class Oracle:
                  frame=0, cfl=1.0):
         self.nx, self.ny = nx, ny
         self.frame = frame
+        self.periodic = (bool(periodic[0]), bool(periodic[1]))
         self.n = (n_lo, n_hi)
         self.Q = (n_lo * n_lo, n_hi * n_hi)
         h = lib().orc_create(nx, ny, int(periodic[0]), int(periodic[1]), n_lo, n_hi,

@@ -293,6 +293,11 @@ struct slbm_s {
   int mcur;                      // tile-mask buffer the next stream launch reads
   int crit;
   double thr;
+  // learned indicator: weights on the device (owned), evaluation interval
+  void* ind_buf;
+  IndicatorDev ind;
+  int ind_interval;
+  double ind_thr;                // logit threshold of SLBM_CRIT_MLP
   int bc_kind[4];
   long long steps;
   long long sc_launches;         // stream-collide launches (scheduler counter parity)
@@ -535,7 +540,7 @@ int step_once(slbm_s* h) {
   if (h->frame != SLBM_FRAME_LATTICE) return pond_step_once(h);
   const int b = h->cur, nb = b ^ 1;
   uint8_t* fold = h->flags(h->fcur);
-  uint8_t* fnew = h->crit ? h->flags(h->fcur ^ 1) : fold;
+  uint8_t* fnew = h->crit == SLBM_CRIT_MACH ? h->flags(h->fcur ^ 1) : fold;
   cudaError_t e;
   SLBM_CK(h, mark(h), "trace event");
   int* err = h->at<int>(h->lay.err);
@@ -566,7 +571,7 @@ int step_once(slbm_s* h) {
   SLBM_CK(h, mark(h), "trace event");
   h->cur = nb;
   h->mcur ^= 1;
-  if (h->crit) h->fcur ^= 1;
+  if (h->crit == SLBM_CRIT_MACH) h->fcur ^= 1;
   h->steps++;
   return SLBM_OK;
 }
@@ -785,6 +790,40 @@ bool create_args_ok(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int 
   return true;
 }
 
+// Evaluate the learned indicator on the current state: moments into the
+// macro slots, then features + MLP; features / logits / flags to the given
+// device buffers (any may be null).
+int run_indicator(slbm_s* h, float* feat, float* logit, uint8_t* flags_out) {
+  double* d[3];
+  for (int m = 0; m < 3; ++m) d[m] = h->at<double>(h->lay.macro[m]);
+  cudaError_t e = with_types(h, [&](auto ty, const auto& prm) {
+    SLBM_TYPES(ty);
+    return launch_moments<S, R>(prm, (const S*)h->pops(h->cur, 0), (const S*)h->pops(h->cur, 1),
+                                h->flags(h->fcur), d[0], d[1], d[2], nullptr, nullptr, h->st);
+  });
+  SLBM_CK(h, e, "moments launch");
+  e = with_types(h, [&](auto ty, const auto& prm) {
+    SLBM_TYPES(ty);
+    return launch_indicator<S, R>(prm, (const S*)h->pops(h->cur, 0), (const S*)h->pops(h->cur, 1),
+                                  h->flags(h->fcur), d[0], d[1], d[2], h->ind, (float)h->ind_thr,
+                                  feat, logit, flags_out, h->st);
+  });
+  SLBM_CK(h, e, "indicator launch");
+  return SLBM_OK;
+}
+
+// New flags from the learned indicator, flips converted (as a criterion
+// switched on at set time).
+int apply_indicator(slbm_s* h) {
+  uint8_t* tmp = h->at<uint8_t>(h->lay.flag_tmp);
+  if (int rc = run_indicator(h, nullptr, nullptr, tmp)) return rc;
+  SLBM_CK(h, convert(h, h->cur, h->flags(h->fcur), tmp), "convert launch");
+  SLBM_CK(h, cudaMemcpyAsync(h->flags(h->fcur), tmp, h->ncell(), cudaMemcpyDeviceToDevice, h->st),
+          "flag copy");
+  SLBM_CK(h, ghosts(h, h->flags(h->fcur)), "ghost launch");
+  return SLBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -838,6 +877,7 @@ int slbm_create_in(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int i
   h->ws = (char*)workspace;
   h->owns_ws = false;
   h->thr = 0.3;
+  h->ind_interval = 1;
   for (int s = 0; s < 4; ++s) h->bc_kind[s] = SLBM_BC_OUTFLOW;
   refresh_params(h);
   if (encode_tmaps(h) != SLBM_OK) {
@@ -894,6 +934,7 @@ int slbm_destroy(slbm_t h) {
   int rc = SLBM_OK;
   if (cudaStreamSynchronize(h->st) != cudaSuccess) rc = SLBM_ECUDA;
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (h->ind_buf) cudaFree(h->ind_buf);
   if (h->owns_ws && cudaFree(h->ws) != cudaSuccess) rc = SLBM_ECUDA;
   delete h;
   return rc;
@@ -993,13 +1034,16 @@ int slbm_get_flags(slbm_t h, uint8_t* flags) {
 
 int slbm_set_criterion(slbm_t h, int kind, double threshold) {
   SLBM_GUARD(h);
-  if ((kind != SLBM_CRIT_NONE && kind != SLBM_CRIT_MACH) || !(threshold >= 0.0))
+  if ((kind != SLBM_CRIT_NONE && kind != SLBM_CRIT_MACH && kind != SLBM_CRIT_MLP) ||
+      !std::isfinite(threshold) || (kind == SLBM_CRIT_MACH && !(threshold >= 0.0)))
     return fail(h, SLBM_EINVAL, "criterion kind or threshold invalid");
+  if (kind == SLBM_CRIT_MLP && !h->ind_buf)
+    return fail(h, SLBM_EINVAL, "no indicator weights (slbm_set_indicator); use SLBM_CRIT_MACH");
   if (kind != SLBM_CRIT_NONE && h->frame != SLBM_FRAME_LATTICE)
     return fail(h, SLBM_EINVAL, "the Mach criterion belongs to the lattice frame");
   // flags live in buffer fcur either way; the other buffer is scratch
   h->crit = kind;
-  h->thr = threshold;
+  if (kind != SLBM_CRIT_MLP) h->thr = threshold;
   refresh_params(h);
   if (kind == SLBM_CRIT_MACH) {
     // evaluate the criterion on the current state at once; flips are converted
@@ -1015,7 +1059,79 @@ int slbm_set_criterion(slbm_t h, int kind, double threshold) {
             "flag copy");
     SLBM_CK(h, ghosts(h, h->flags(h->fcur)), "ghost launch");
   }
+  if (kind == SLBM_CRIT_MLP) {
+    h->ind_thr = threshold;
+    return apply_indicator(h);
+  }
   return SLBM_OK;
+}
+
+int slbm_set_indicator(slbm_t h, const float* w1, const float* b1, const float* w2,
+                       const float* b2, const float* w3, float b3, int interval) {
+  SLBM_GUARD(h);
+  if (!w1 || !b1 || !w2 || !b2 || !w3 || interval < 1 || !std::isfinite(b3))
+    return fail(h, SLBM_EINVAL, "indicator weights and interval >= 1 are required");
+  if (h->frame != SLBM_FRAME_LATTICE) return fail(h, SLBM_EINVAL, "lattice frame only");
+  const size_t nw1 = 16 * 32, nw2 = 32 * 32;
+  const size_t bytes = (nw1 + nw2) * sizeof(__half) + (32 + 32 + 32) * sizeof(float);
+  if (!h->ind_buf) SLBM_CK(h, cudaMalloc(&h->ind_buf, bytes), "indicator weights cudaMalloc");
+  std::vector<__half> hw(nw1 + nw2);
+  for (size_t i = 0; i < nw1; ++i) hw[i] = __float2half_rn(w1[i]);
+  for (size_t i = 0; i < nw2; ++i) hw[nw1 + i] = __float2half_rn(w2[i]);
+  std::vector<float> hf(96);
+  for (int i = 0; i < 32; ++i) {
+    hf[i] = b1[i];
+    hf[32 + i] = b2[i];
+    hf[64 + i] = w3[i];
+  }
+  char* base = (char*)h->ind_buf;
+  SLBM_CK(h, cudaMemcpyAsync(base, hw.data(), hw.size() * sizeof(__half), cudaMemcpyHostToDevice,
+                             h->st), "H2D copy");
+  float* fb = (float*)(base + hw.size() * sizeof(__half));
+  SLBM_CK(h, cudaMemcpyAsync(fb, hf.data(), hf.size() * sizeof(float), cudaMemcpyHostToDevice, h->st),
+          "H2D copy");
+  h->ind = IndicatorDev{(const __half*)base, fb, (const __half*)base + nw1, fb + 32, fb + 64, b3};
+  h->ind_interval = interval;
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");  // the host vectors are released
+  return SLBM_OK;
+}
+
+int slbm_indicator_eval(slbm_t h, float* features, float* logits, uint8_t* flags) {
+  SLBM_GUARD(h);
+  if (h->frame != SLBM_FRAME_LATTICE) return fail(h, SLBM_EINVAL, "lattice frame only");
+  if ((logits || flags) && !h->ind_buf)
+    return fail(h, SLBM_EINVAL, "no indicator weights (slbm_set_indicator)");
+  const size_t nc = h->ncell();
+  float* dfeat = nullptr;
+  float* dlog = nullptr;
+  uint8_t* dfl = nullptr;
+  if (features) SLBM_CK(h, cudaMalloc(&dfeat, nc * 16 * sizeof(float)), "cudaMalloc");
+  if (logits && cudaMalloc(&dlog, nc * sizeof(float)) != cudaSuccess) {
+    cudaFree(dfeat);
+    return fail(h, SLBM_ENOMEM, "cudaMalloc");
+  }
+  if (flags && cudaMalloc(&dfl, nc) != cudaSuccess) {
+    cudaFree(dfeat);
+    cudaFree(dlog);
+    return fail(h, SLBM_ENOMEM, "cudaMalloc");
+  }
+  IndicatorDev keep = h->ind;
+  if (!h->ind_buf) h->ind = IndicatorDev{nullptr, nullptr, nullptr, nullptr, nullptr, 0.f};
+  int rc = run_indicator(h, dfeat, dlog, dfl);
+  h->ind = keep;
+  if (!rc && features && cudaMemcpyAsync(features, dfeat, nc * 16 * sizeof(float),
+                                         cudaMemcpyDeviceToHost, h->st) != cudaSuccess)
+    rc = fail(h, SLBM_ECUDA, "D2H copy");
+  if (!rc && logits && cudaMemcpyAsync(logits, dlog, nc * sizeof(float), cudaMemcpyDeviceToHost,
+                                       h->st) != cudaSuccess)
+    rc = fail(h, SLBM_ECUDA, "D2H copy");
+  if (!rc && flags && cudaMemcpyAsync(flags, dfl, nc, cudaMemcpyDeviceToHost, h->st) != cudaSuccess)
+    rc = fail(h, SLBM_ECUDA, "D2H copy");
+  if (!rc && cudaStreamSynchronize(h->st) != cudaSuccess) rc = fail(h, SLBM_ECUDA, "sync");
+  cudaFree(dfeat);
+  cudaFree(dlog);
+  cudaFree(dfl);
+  return rc;
 }
 
 int slbm_set_boundary(slbm_t h, int side, int kind, const double* rho, const double* ux,
@@ -1052,6 +1168,8 @@ int slbm_step(slbm_t h, int n) {
   for (int s = 0; s < n; ++s) {
     int rc = step_once(h);
     if (rc) return rc;
+    if (h->crit == SLBM_CRIT_MLP && h->steps % h->ind_interval == 0 && (rc = apply_indicator(h)))
+      return rc;
   }
   return SLBM_OK;
 }

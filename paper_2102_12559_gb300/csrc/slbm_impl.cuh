@@ -150,6 +150,27 @@ template <class S, class R>
 cudaError_t launch_pond_frame_io(const PondParams<R>& p, S* lam, double* ux, double* uy,
                                  double* T, int unpack, cudaStream_t st);
 
+// Learned refinement indicator (slbm_indicator.cu): MLP 16 -> 32 -> 32 -> 1
+// with FP16 weights w1 (16 x 32) and w2 (32 x 32), row-major K x N, FP32 biases
+// and output weights.
+struct IndicatorDev {
+  const __half* w1;             // null: features only
+  const float* b1;
+  const __half* w2;
+  const float* b2;
+  const float* w3;
+  float b3;
+};
+
+// Features (nc x 16 FP32, cell-major), logits and flags (logit > thr) of the
+// current state; any output may be null.  mrho / mux / muy: the moments of
+// every cell (nc doubles each, from launch_moments).
+template <class S, class R>
+cudaError_t launch_indicator(const Params<R>& p, const S* f0, const S* f1, const uint8_t* flag,
+                             const double* mrho, const double* mux, const double* muy,
+                             const IndicatorDev& w, float thr, float* feat_out, float* logit_out,
+                             uint8_t* flag_out, cudaStream_t st);
+
 // Launchers (defined in the kernel translation units).  S = storage type,
 // R = arithmetic type.  f0 / f1: base of one buffer for lattice 0 / 1.
 // Stream-collide from the buffer described by the tensor maps tm0 / tm1

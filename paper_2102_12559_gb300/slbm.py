@@ -26,7 +26,7 @@ SLBM_POND_REACH = 5
 SLBM_FP32, SLBM_FP64, SLBM_FP16 = 0, 1, 2
 SLBM_BC_OUTFLOW, SLBM_BC_DIRICHLET, SLBM_BC_INLET, SLBM_BC_DIFFUSE = 0, 1, 2, 3
 SLBM_SIDE_XMIN, SLBM_SIDE_XMAX, SLBM_SIDE_YMIN, SLBM_SIDE_YMAX = 0, 1, 2, 3
-SLBM_CRIT_NONE, SLBM_CRIT_MACH = 0, 1
+SLBM_CRIT_NONE, SLBM_CRIT_MACH, SLBM_CRIT_MLP = 0, 1, 2
 
 EXPORTS = [
     "slbm_workspace_bytes", "slbm_create", "slbm_create_in", "slbm_destroy", "slbm_get_info",
@@ -35,6 +35,7 @@ EXPORTS = [
     "slbm_audit", "slbm_get_pops", "slbm_set_pops", "slbm_get_state", "slbm_set_state",
     "slbm_profile", "slbm_profile_read", "slbm_audit_dense_noalloc", "slbm_last_error",
     "slbm_set_pond", "slbm_get_frame", "slbm_set_frame",
+    "slbm_set_indicator", "slbm_indicator_eval",
 ]
 SLBM_PROFILE_KERNELS = 2
 KERNEL_NAMES = ("stream_collide", "post_step")
@@ -104,6 +105,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.slbm_set_pond.argtypes = [p, d, i]
     L.slbm_get_frame.argtypes = [p, p, p, p]
     L.slbm_set_frame.argtypes = [p, p, p, p]
+    L.slbm_set_indicator.argtypes = [p, p, p, p, p, p, ctypes.c_float, i]
+    L.slbm_indicator_eval.argtypes = [p, p, p, p]
     L.slbm_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name != "slbm_last_error":
@@ -177,6 +180,21 @@ def slbm_init_equilibrium(h, n, rho, ux, uy, T=None):
     t = None if T is None else _f64(T, n)
     _check(load().slbm_init_equilibrium(h, _ptr(r), _ptr(a), _ptr(b),
                                         None if t is None else _ptr(t)), h)
+
+
+def slbm_set_indicator(h, w1, b1, w2, b2, w3, b3, interval=10):
+    """MLP weights (16x32, 32, 32x32, 32, 32, scalar), host floats."""
+    a = [np.ascontiguousarray(v, dtype=np.float32).ravel() for v in (w1, b1, w2, b2, w3)]
+    assert [x.size for x in a] == [512, 32, 1024, 32, 32]
+    _check(load().slbm_set_indicator(h, *(_ptr(x) for x in a), float(b3), int(interval)), h)
+
+
+def slbm_indicator_eval(h, n, features=True, logits=False, flags=False):
+    fe = np.zeros((n, 16), np.float32) if features else None
+    lo = np.zeros(n, np.float32) if logits else None
+    fl = np.zeros(n, np.uint8) if flags else None
+    _check(load().slbm_indicator_eval(h, *(None if v is None else _ptr(v) for v in (fe, lo, fl))), h)
+    return fe, lo, fl
 
 
 def slbm_set_pond(h, tol, max_iter):
@@ -352,6 +370,18 @@ class Solver:
 
     def set_pond(self, tol, max_iter):
         slbm_set_pond(self.h, tol, max_iter)
+
+    def set_indicator(self, weights, interval=10):
+        """weights: dict w1 (16x32), b1 (32), w2 (32x32), b2 (32), w3 (32), b3."""
+        slbm_set_indicator(self.h, weights["w1"], weights["b1"], weights["w2"], weights["b2"],
+                           weights["w3"], weights["b3"], interval)
+
+    def indicator_eval(self, features=True, logits=False, flags=False):
+        """(features (ny, nx, 16), logits (ny, nx), flags (ny, nx)); unrequested are None."""
+        fe, lo, fl = slbm_indicator_eval(self.h, self.n, features, logits, flags)
+        s = (self.ny, self.nx)
+        return (None if fe is None else fe.reshape(self.ny, self.nx, 16),
+                None if lo is None else lo.reshape(s), None if fl is None else fl.reshape(s))
 
     def get_frame(self):
         s = (self.ny, self.nx)
