@@ -878,6 +878,7 @@ int slbm_create_in(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int i
   h->owns_ws = false;
   h->thr = 0.3;
   h->ind_interval = 1;
+  h->ind_thr = 0.0;
   for (int s = 0; s < 4; ++s) h->bc_kind[s] = SLBM_BC_OUTFLOW;
   refresh_params(h);
   if (encode_tmaps(h) != SLBM_OK) {

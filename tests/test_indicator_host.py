@@ -85,3 +85,46 @@ def test_forward_with_hand_set_weights():
     x[:, 15] = [0.25, 1.0, -1.0]
     np.testing.assert_allclose(OI.forward_fp16(w, x), [0.0, 1.5, -0.5], atol=1e-6)
     np.testing.assert_allclose(IND.forward(w, x)[0], [0.0, 1.5, -0.5], atol=1e-12)
+
+
+def test_nonequilibrium_features_closed_form():
+    """Perturbations that leave rho and u unchanged: a symmetric one along an
+    axis adds exactly a normal stress 2 c^2 eps and kinetic T 2 c^2 eps / (2 rho),
+    an antisymmetric one (corners against the axis pair) exactly a heat flux
+    1/2 * 4 c^3 eps along that axis (D2Q9, c = sqrt(3))."""
+    nx, ny = 8, 6
+    rho0, u0, v0 = 1.1, 0.2, -0.1
+    o = O.Oracle(nx, ny, 3, 5, tau=0.7)
+    o.init_equilibrium(*WL.uniform(nx, ny, rho0, u0, v0))
+    o.set_flags(np.zeros((ny, nx), np.uint8))
+    cx, cy, _ = O.lattice(3)
+    c = cx.max()
+    idx = lambda a, b: int(np.flatnonzero((np.sign(cx) == a) & (np.sign(cy) == b))[0])
+    e1, e2 = 1e-3, 2e-3
+    dx = np.zeros(9)
+    dx[[idx(1, 0), idx(-1, 0)]] += e1
+    dx[idx(0, 0)] -= 2 * e1
+    dx[[idx(1, 1), idx(1, -1)]] += e2
+    dx[[idx(-1, 1), idx(-1, -1)]] -= e2
+    dx[idx(1, 0)] -= 2 * e2
+    dx[idx(-1, 0)] += 2 * e2
+    dy = np.zeros(9)                                 # the same with the axes swapped
+    for i in range(9):
+        dy[idx(int(np.sign(cy[i])), int(np.sign(cx[i])))] = dx[i]
+    f = o.get_pops(0)
+    f[:, : nx // 2] += dx
+    f[:, nx // 2:] += dy
+    o.set_pops(0, f)
+    F = OI.features(o) / OI.SCALE
+    L, R = F[:, : nx // 2], F[:, nx // 2:]
+    np.testing.assert_allclose(F[..., 0], rho0 - 1, atol=1e-13)
+    np.testing.assert_allclose(F[..., 1], u0, atol=1e-13)
+    np.testing.assert_allclose(F[..., 2], v0, atol=1e-13)
+    np.testing.assert_allclose(F[..., 3], c * c * e1 / rho0, atol=1e-13)
+    np.testing.assert_allclose(L[..., 4], 2 * c * c * e1, atol=1e-13)
+    np.testing.assert_allclose(R[..., 6], 2 * c * c * e1, atol=1e-13)
+    np.testing.assert_allclose(L[..., 7], 2 * c ** 3 * e2, atol=1e-13)
+    np.testing.assert_allclose(R[..., 8], 2 * c ** 3 * e2, atol=1e-13)
+    for part, zero in ((L, (5, 6, 8)), (R, (4, 5, 7))):
+        assert np.abs(part[..., list(zero)]).max() < 1e-13
+    assert np.abs(F[..., 9:15]).max() < 1e-13
