@@ -207,14 +207,24 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def time_steps(solver, stream, steps, warmup):
-    """Mean device milliseconds of one step over `steps` back-to-back steps."""
+def time_steps(solver, stream, steps, warmup, audit_every=0):
+    """Mean device milliseconds of one step over `steps` back-to-back steps
+    (with `audit_every`, the FP64 audit after every that many steps and at the
+    end, inside the timed region)."""
     import torch
     solver.step(warmup)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     a.record(stream)
-    solver.step(steps)
+    if audit_every:
+        done = 0
+        while done < steps:
+            k = min(audit_every, steps - done)
+            solver.step(k)
+            solver.audit()
+            done += k
+    else:
+        solver.step(steps)
     b.record(stream)
     torch.cuda.synchronize()
     solver.sync()
@@ -238,8 +248,11 @@ def run_study(args):
       all-D2Q25 and a hybrid whose left 10 % of columns are D2Q25; reports
       t_Q25 / t_Q9 and t_Q25 / t_hyb next to the paper's 2.9 and 2.43.
     vortex4096: the large random-vortex field (4096^2, 512 vortices, Mach 0.9
-      peak, Mach criterion), FP32 storage against FP16 deviation storage:
-      MLUPS of each and the relative L2 gap of rho and u after the same steps.
+      peak): the plain FP32 form (Mach criterion every step) against FP16
+      deviation storage, and against FP16 storage with the learned indicator
+      every 10 steps (weights trained here on an all-D2Q25 384^2 run) and the
+      FP64 audit every 1000 steps; MLUPS of each and the relative L2 gap of
+      rho and u to the FP32 form after the same steps.
     pond: the co-moving (PonD) frame step, thermal, 1024 x 512 periodic,
       FP32, D2Q9 with a D2Q25 disc, a smooth seeded field around a Mach 1.5
       mean flow at T = 1.
@@ -271,37 +284,66 @@ def run_study(args):
                 "l2": "not flushed (back-to-back steps)"}), flush=True)
         return
     if args.workload == "vortex4096":
-        # the large random-vortex field: FP32 storage against FP16 deviations
+        # the large random-vortex field: the plain FP32 form (Mach criterion
+        # every step) against FP16 deviations, and against FP16 deviations with
+        # the learned indicator every 10 steps and the FP64 audit every 1000
+        from paper_2102_12559_gb300 import indicator as IND
         N = 4096
         rho, ux, uy = WL.random_vortex_field(N, 512, seed=4, rmin=8.0, rmax=64.0, umax=0.9)
+        # indicator weights: an all-D2Q25 run of the same generator on 384^2
+        n_tr = 384
+        t = slbm.Solver(n_tr, n_tr, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=0.6, stream=stream)
+        t.init_equilibrium(*WL.random_vortex_field(n_tr, 12, seed=5, rmin=8.0, rmax=64.0, umax=0.9))
+        t.set_flags(np.ones((n_tr, n_tr), np.uint8))
+        t.step(20)
+        x_tr = t.indicator_eval()[0].reshape(-1, 16).astype(np.float64)
+        _, mu, mv, _ = t.moments()
+        y_tr = (np.hypot(mu, mv) > THR).ravel().astype(np.float64)
+        t.close()
+        weights = IND.train(x_tr, y_tr, epochs=40, batch=512, seed=0, balance=False)
+        arms = (("fp32", slbm.SLBM_FP32, False), ("fp16", slbm.SLBM_FP16, False),
+                ("fp16+indicator", slbm.SLBM_FP16, True))
         res = {}
-        for name, prec in (("fp32", slbm.SLBM_FP32), ("fp16", slbm.SLBM_FP16)):
+        for name, prec, learned in arms:
             g = slbm.Solver(N, N, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=0.6, stream=stream,
                             precision=prec)
             g.init_equilibrium(rho, ux, uy)
-            g.set_criterion(slbm.SLBM_CRIT_MACH, THR)
-            ms = time_steps(g, stream, args.steps, args.warmup)
-            kern, ksteps = profiled(g, min(args.steps, 50))
-            nhi = int(g.get_flags().sum())
+            if learned:
+                g.set_indicator(weights, interval=10)
+                g.set_criterion(slbm.SLBM_CRIT_MLP, 0.0)
+                ms = time_steps(g, stream, args.steps, args.warmup, audit_every=1000)
+            else:
+                g.set_criterion(slbm.SLBM_CRIT_MACH, THR)
+                ms = time_steps(g, stream, args.steps, args.warmup)
+            kern, ksteps = profiled(g, 50)
+            flags = g.get_flags()
             mom = g.moments()
-            res[name] = dict(ms=ms, kern=[k / max(ksteps, 1) for k in kern], nhi=nhi, mom=mom)
+            res[name] = dict(ms=ms, kern=[k / max(ksteps, 1) for k in kern], nhi=int(flags.sum()),
+                             mom=mom, agree=float(np.mean(flags == (np.hypot(mom[1], mom[2]) > THR))))
             g.close()
-        a, b = res["fp16"]["mom"], res["fp32"]["mom"]
+        b = res["fp32"]["mom"]
         rl2 = lambda x, y: float(np.linalg.norm((x - y).ravel()) / np.linalg.norm(y.ravel()))
-        for name in ("fp32", "fp16"):
+        for name, prec, learned in arms:
             r = res[name]
-            es = 2 if name == "fp16" else 4
+            es = 4 if prec == slbm.SLBM_FP32 else 2
             bytes_sc = N * N * (2 * es * 9 + 2) + r["nhi"] * 2 * es * 16
-            print(json.dumps({
+            line = {
                 "study": "large random-vortex field", "workload": f"{N}x{N}, 512 vortices, "
-                "max Mach 0.9, Mach>0.3 criterion every step", "storage": name,
-                "steps_timed": args.steps, "total_steps": args.steps + args.warmup,
+                "max Mach 0.9", "arm": name,
+                "flags": "learned indicator every 10 steps, FP64 audit every 1000 steps" if learned
+                else "Mach > 0.3 criterion every step",
+                "steps_timed": args.steps, "total_steps": args.steps + args.warmup + 50,
                 "ms_per_step": r["ms"], "mlups": N * N / (r["ms"] * 1e-3) / 1e6,
+                "speedup_vs_fp32": res["fp32"]["ms"] / r["ms"],
                 "high_order_fraction": r["nhi"] / (N * N),
+                "flags_agree_with_plain_criterion": r["agree"],
                 "kernels_ms_per_step": dict(zip(slbm.KERNEL_NAMES, r["kern"])),
-                "stream_collide_gbs": bytes_sc / (r["kern"][0] * 1e-3) / 1e9}), flush=True)
-        print(json.dumps({"study": "large random-vortex field", "fp16_vs_fp32_rel_l2": {
-            "rho": rl2(a[0], b[0]), "u": rl2(np.stack(a[1:3]), np.stack(b[1:3]))}}), flush=True)
+                "stream_collide_gbs": bytes_sc / (r["kern"][0] * 1e-3) / 1e9}
+            if name != "fp32":
+                a = r["mom"]
+                line["rel_l2_vs_fp32"] = {"rho": rl2(a[0], b[0]),
+                                          "u": rl2(np.stack(a[1:3]), np.stack(b[1:3]))}
+            print(json.dumps(line), flush=True)
         return
     if args.workload == "pond":
         nx, ny = 1024, 512

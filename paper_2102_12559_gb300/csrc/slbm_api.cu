@@ -186,8 +186,8 @@ struct Layout {
   size_t sched;              // two tile counters of the stream kernel's scheduler
   size_t post_sync;          // 2 x 3 counters of the post-step kernel's grid-wide waits
   size_t post_work;          // 2 x ntiles work words (stream kernel -> post-step kernel)
-  size_t post_counts;        // per-CTA work-tile counts of the post-step kernel
-  size_t post_list;          // its compacted work tiles, one int per tile
+  size_t post_nlist;         // 2 counters: work tiles listed in each half of post_list
+  size_t post_list;          // 2 x ntiles: candidate work tiles (stream kernel -> post-step kernel)
   size_t total;
 };
 
@@ -260,8 +260,8 @@ Layout make_layout(const slbm_grid* g, int lo, int hi, int order, int precision)
   Lo.sched = off; off = align_up(off + 2 * sizeof(int), 256);
   Lo.post_sync = off; off = align_up(off + 6 * sizeof(int), 256);
   Lo.post_work = off; off = align_up(off + 2 * ntiles * sizeof(int), 256);
-  Lo.post_counts = off; off = align_up(off + 1024 * sizeof(int), 256);
-  Lo.post_list = off; off = align_up(off + ntiles * sizeof(int), 256);
+  Lo.post_nlist = off; off = align_up(off + 2 * sizeof(int), 256);
+  Lo.post_list = off; off = align_up(off + 2 * ntiles * sizeof(int), 256);
   Lo.total = off;
   return Lo;
 }
@@ -559,12 +559,15 @@ int step_once(slbm_s* h) {
   SLBM_CK(h, mark(h), "trace event");
   const int post_parity = (int)(h->post_launches & 1);
   h->post_launches++;
-  const int* work = h->at<int>(h->lay.post_work) + (size_t)h->pf.sched_parity * ntiles_of(h);
+  const int half = h->pf.sched_parity;
+  const size_t nt = (size_t)ntiles_of(h);
+  const int* work = h->at<int>(h->lay.post_work) + half * nt;
+  const int* list = h->at<int>(h->lay.post_list) + half * nt;
+  const int* nlist = h->at<int>(h->lay.post_nlist) + half;
   e = with_types(h, [&](auto ty, const auto& prm) {
     SLBM_TYPES(ty);
     return launch_post_step<S, R>(prm, (S*)h->pops(nb, 0), (S*)h->pops(nb, 1), fold, fnew,
-                                  bc_dev(h), work, h->at<int>(h->lay.post_sync),
-                                  h->at<int>(h->lay.post_counts), h->at<int>(h->lay.post_list),
+                                  bc_dev(h), work, list, nlist, h->at<int>(h->lay.post_sync),
                                   post_parity, err, h->st);
   });
   SLBM_CK(h, e, "post-step launch");
@@ -594,6 +597,8 @@ void fill_params(Params<R>& p, const slbm_s* h, const Lattice1D& a, const Lattic
   p.nsm = h->nsm;
   p.sched = reinterpret_cast<int*>(h->ws + h->lay.sched);
   p.work = reinterpret_cast<int*>(h->ws + h->lay.post_work);
+  p.wlist = reinterpret_cast<int*>(h->ws + h->lay.post_list);
+  p.wcount = reinterpret_cast<int*>(h->ws + h->lay.post_nlist);
   fill_lat(p.lat[0], a, dt, h->P);
   fill_lat(p.lat[1], b, dt, h->P);
   ConvTab<R>& t = p.conv;
@@ -790,37 +795,55 @@ bool create_args_ok(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int 
   return true;
 }
 
-// Evaluate the learned indicator on the current state: moments into the
-// macro slots, then features + MLP; features / logits / flags to the given
+// Evaluate the learned indicator on the current state: moment planes into
+// the macro slots, then features + MLP; features / logits / flags to the given
 // device buffers (any may be null).
 int run_indicator(slbm_s* h, float* feat, float* logit, uint8_t* flags_out) {
-  double* d[3];
+  double* d[3];  // scratch for the moment planes (nc values of the arithmetic type each)
   for (int m = 0; m < 3; ++m) d[m] = h->at<double>(h->lay.macro[m]);
   cudaError_t e = with_types(h, [&](auto ty, const auto& prm) {
     SLBM_TYPES(ty);
-    return launch_moments<S, R>(prm, (const S*)h->pops(h->cur, 0), (const S*)h->pops(h->cur, 1),
-                                h->flags(h->fcur), d[0], d[1], d[2], nullptr, nullptr, h->st);
-  });
-  SLBM_CK(h, e, "moments launch");
-  e = with_types(h, [&](auto ty, const auto& prm) {
-    SLBM_TYPES(ty);
     return launch_indicator<S, R>(prm, (const S*)h->pops(h->cur, 0), (const S*)h->pops(h->cur, 1),
-                                  h->flags(h->fcur), d[0], d[1], d[2], h->ind, (float)h->ind_thr,
-                                  feat, logit, flags_out, h->st);
+                                  h->flags(h->fcur), (R*)d[0], (R*)d[1], (R*)d[2], h->ind,
+                                  (float)h->ind_thr, feat, logit, flags_out, h->st);
   });
   SLBM_CK(h, e, "indicator launch");
   return SLBM_OK;
 }
 
-// New flags from the learned indicator, flips converted (as a criterion
-// switched on at set time).
+// New flags from the learned indicator into the second flag plane (unused
+// while the plain criterion is off), then the post-step machinery of a
+// stream step: tile masks, work words and the work list from the old and new
+// flags, and the post-step kernel converts the flipped and band cells of the
+// current buffer and refreshes its ghost ring.  The half of the work words and
+// list used is the one the next stream launch clears (its words per tile, its
+// counter at launch).
 int apply_indicator(slbm_s* h) {
-  uint8_t* tmp = h->at<uint8_t>(h->lay.flag_tmp);
-  if (int rc = run_indicator(h, nullptr, nullptr, tmp)) return rc;
-  SLBM_CK(h, convert(h, h->cur, h->flags(h->fcur), tmp), "convert launch");
-  SLBM_CK(h, cudaMemcpyAsync(h->flags(h->fcur), tmp, h->ncell(), cudaMemcpyDeviceToDevice, h->st),
-          "flag copy");
-  SLBM_CK(h, ghosts(h, h->flags(h->fcur)), "ghost launch");
+  uint8_t* fold = h->flags(h->fcur);
+  uint8_t* fnew = h->flags(h->fcur ^ 1);
+  if (int rc = run_indicator(h, nullptr, nullptr, fnew)) return rc;
+  const size_t nt = (size_t)ntiles_of(h);
+  const int half = (int)((h->sc_launches & 1) ^ 1);
+  int* work = h->at<int>(h->lay.post_work);
+  int* list = h->at<int>(h->lay.post_list);
+  int* nlist = h->at<int>(h->lay.post_nlist);
+  SLBM_CK(h, cudaMemsetAsync(work + half * nt, 0, nt * sizeof(int), h->st), "work clear");
+  SLBM_CK(h, cudaMemsetAsync(nlist + half, 0, sizeof(int), h->st), "work list clear");
+  SLBM_CK(h, launch_tile_work(h->g.nx, h->g.ny, h->g.periodic_x ? 1 : 0, h->g.periodic_y ? 1 : 0,
+                              fold, fnew, h->at<uint8_t>(h->lay.tile_mask[h->mcur]), work, list,
+                              nlist, half, h->st),
+          "tile work launch");
+  const int post_parity = (int)(h->post_launches & 1);
+  h->post_launches++;
+  int* err = h->at<int>(h->lay.err);
+  cudaError_t e = with_types(h, [&](auto ty, const auto& prm) {
+    SLBM_TYPES(ty);
+    return launch_post_step<S, R>(prm, (S*)h->pops(h->cur, 0), (S*)h->pops(h->cur, 1), fold, fnew,
+                                  bc_dev(h), work + half * nt, list + half * nt, nlist + half,
+                                  h->at<int>(h->lay.post_sync), post_parity, err, h->st);
+  });
+  SLBM_CK(h, e, "post-step launch");
+  h->fcur ^= 1;
   return SLBM_OK;
 }
 

@@ -250,6 +250,56 @@ int audit_parts(int nx, int ny) {
   return (int)(b < 1024 ? b : 1024);
 }
 
+// One CTA per 32 x 8 tile: bits (1 << new flag) | 4 if the flag flipped,
+// OR-reduced over the tile; thread q < 9 adds the tile's part to the work word
+// of neighbour q of its 3 x 3 tile neighbourhood (lattices from all nine, the
+// flip bit only to the tile itself), listing the tiles that become work.
+__global__ void __launch_bounds__(kTX * kTY)
+k_tile_work(int nx, int ny, int periodic_x, int periodic_y, const uint8_t* __restrict__ flag_old,
+            const uint8_t* __restrict__ flag_new, uint8_t* __restrict__ mask, int* work,
+            int* wlist, int* wcount, int half) {
+  const int x = blockIdx.x * kTX + threadIdx.x, y = blockIdx.y * kTY + threadIdx.y;
+  const int tid = threadIdx.y * kTX + threadIdx.x;
+  int bit = 0;
+  if (x < nx && y < ny) {
+    const long long c = x + (long long)nx * y;
+    const int o = flag_old[c], n = flag_new[c];
+    bit = (1 << n) | (o != n ? 4 : 0);
+  }
+  __shared__ int acc;
+  if (tid == 0) acc = 0;
+  __syncthreads();
+  const int w = __reduce_or_sync(0xffffffffu, bit);
+  if (threadIdx.x == 0 && w) atomicOr(&acc, w);
+  __syncthreads();
+  if (tid < 9) {
+    const int ntx = (int)gridDim.x, nty = (int)gridDim.y;
+    const int m = acc;
+    if (tid == 0) mask[blockIdx.x + ntx * blockIdx.y] = (uint8_t)m;
+    int tx = (int)blockIdx.x + tid % 3 - 1, ty = (int)blockIdx.y + tid / 3 - 1;
+    bool ok = true;
+    if (tx < 0 || tx >= ntx) {
+      if (periodic_x) tx = tx < 0 ? tx + ntx : tx - ntx;
+      else ok = false;
+    }
+    if (ty < 0 || ty >= nty) {
+      if (periodic_y) ty = ty < 0 ? ty + nty : ty - nty;
+      else ok = false;
+    }
+    const int contrib = (m & 3) | (tid == 4 ? (m & 4) : 0);
+    if (ok && contrib) add_work(work, wlist, wcount, half, ntx * nty, ty * ntx + tx, contrib);
+  }
+}
+
+cudaError_t launch_tile_work(int nx, int ny, int periodic_x, int periodic_y,
+                             const uint8_t* flag_old, const uint8_t* flag_new, uint8_t* mask,
+                             int* work, int* wlist, int* wcount, int half, cudaStream_t st) {
+  const dim3 grid((nx + kTX - 1) / kTX, (ny + kTY - 1) / kTY);
+  k_tile_work<<<grid, dim3(kTX, kTY), 0, st>>>(nx, ny, periodic_x, periodic_y, flag_old, flag_new,
+                                               mask, work, wlist, wcount, half);
+  return cudaGetLastError();
+}
+
 template <class S, class R>
 cudaError_t launch_ghosts(const Params<R>& p, S* f0, S* f1, const uint8_t* flag, const BcDev& bc,
                           cudaStream_t st) {

@@ -82,7 +82,30 @@ struct Params {
   int* sched;                   // two tile counters of the stream kernel's scheduler
   int sched_parity;             // the counter (and work-bit half) this step uses
   int* work;                    // 2 x ntiles post-step work bits, accumulated by the stream kernel
+  int* wlist;                   // 2 x ntiles: candidate work tiles (see add_work)
+  int* wcount;                  // 2 counters: entries of each half of wlist
 };
+
+// A tile has interface-conversion work iff its work word holds both lattices
+// (bits 0 and 1, OR-ed from its 3 x 3 tile neighbourhood) or a flip (bit 2).
+__device__ __forceinline__ bool post_work_word(int w) { return (w & 4) || (w & 3) == 3; }
+
+// OR `contrib` into the work word of tile t (half `half`).  The first
+// contribution that carries the high-order lattice or a flip (bits 1, 2)
+// lists t, so the list holds every work tile (each at most once) and also
+// tiles whose neighbourhood turns out all high-order, which the post-step
+// kernel skips by their final word.  Low-order-only contributions, the common
+// case, need no result and use a fire-and-forget atomic.
+__device__ __forceinline__ void add_work(int* work, int* wlist, int* wcount, int half, int ntiles,
+                                         int t, int contrib) {
+  int* w = work + (size_t)half * ntiles + t;
+  if (contrib & 6) {
+    if (!(atomicOr(w, contrib) & 6))
+      wlist[(size_t)half * ntiles + atomicAdd(wcount + half, 1)] = t;
+  } else {
+    atomicOr(w, contrib);
+  }
+}
 
 // Co-moving (PonD) frame, Sec. II.C.  Every cell keeps its populations (as
 // deviations from W_i) in its own frame lambda = {u_x, u_y, T}, stored in three
@@ -162,14 +185,15 @@ struct IndicatorDev {
   float b3;
 };
 
-// Features (nc x 16 FP32, cell-major), logits and flags (logit > thr) of the
-// current state; any output may be null.  mrho / mux / muy: the moments of
-// every cell (nc doubles each, from launch_moments).
+// Learned indicator on the current buffer: the moment planes rho, u_x, u_y
+// in the arithmetic type (mrho, mux, muy: nc values each, overwritten), then
+// features and the MLP; features (nc x 16 FP32), logits and flags (logit >
+// thr) to any of the non-null outputs.
 template <class S, class R>
 cudaError_t launch_indicator(const Params<R>& p, const S* f0, const S* f1, const uint8_t* flag,
-                             const double* mrho, const double* mux, const double* muy,
-                             const IndicatorDev& w, float thr, float* feat_out, float* logit_out,
-                             uint8_t* flag_out, cudaStream_t st);
+                             R* mrho, R* mux, R* muy, const IndicatorDev& w, float thr,
+                             float* feat_out, float* logit_out, uint8_t* flag_out,
+                             cudaStream_t st);
 
 // Launchers (defined in the kernel translation units).  S = storage type,
 // R = arithmetic type.  f0 / f1: base of one buffer for lattice 0 / 1.
@@ -206,17 +230,25 @@ template <class S, class R>
 cudaError_t launch_ghosts(const Params<R>& p, S* f0, S* f1, const uint8_t* flag,
                           const BcDev& bc, cudaStream_t st);
 
-// Per-step ghost refresh of one buffer: periodic / OUTFLOW copies of every
-// plane of both lattices and INLET equilibria (DIRICHLET ghosts are constant).
+// Tile masks and post-step work after flags changed between steps (the
+// learned indicator): per 32 x 8 tile the lattices of its new flags and
+// whether a flag flipped (mask, read by the next stream step), OR-ed into the
+// work words of its 3 x 3 tile neighbourhood as the stream kernel does, with
+// the work tiles listed (add_work).  Half `half` of work / wlist / wcount is
+// used and must be zero on entry.
+cudaError_t launch_tile_work(int nx, int ny, int periodic_x, int periodic_y,
+                             const uint8_t* flag_old, const uint8_t* flag_new, uint8_t* mask,
+                             int* work, int* wlist, int* wcount, int half, cudaStream_t st);
+
 // Per-step post-step kernel (cooperative launch): interface conversion of
-// the tiles whose work word (accumulated by the stream kernel in `work`, the
-// step's half) marks work, spread evenly over the CTAs, then the ghost-ring
-// refresh.  sync: 6 ints (`parity` selects this launch's half); counts: 1024
-// ints; list: ntiles ints.
+// the candidate tiles in `list` (*nlist entries, listed by the stream kernel
+// or the tile-work kernel) whose final word in `work` (the same half) is
+// work, spread evenly over the CTAs, then the ghost-ring refresh.  sync: 6
+// ints (`parity` selects this launch's half).
 template <class S, class R>
 cudaError_t launch_post_step(const Params<R>& p, S* f0, S* f1, const uint8_t* flag_old,
                              const uint8_t* flag_new, const BcDev& bc, const int* work,
-                             int* sync, int* counts, int* list, int parity, int* err,
+                             const int* list, const int* nlist, int* sync, int parity, int* err,
                              cudaStream_t st);
 
 template <class S, class R>

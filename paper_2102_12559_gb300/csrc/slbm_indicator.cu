@@ -35,8 +35,7 @@ __device__ __forceinline__ int clampwrap(int v, int n, int periodic) {
 // Features of cell (x, y) from its own lattice (N nodes per axis).
 template <int N, class S, class R>
 __device__ void cell_features_n(const Params<R>& p, const LatTab<R>& L, const S* f, int x, int y,
-                                const double* mrho, const double* mux, const double* muy,
-                                float* out) {
+                                const R* mrho, const R* mux, const R* muy, float* out) {
   const size_t base = (size_t)(y + p.G) * p.pitch + (x + kOX);
   R s[N * N];
   R dr = R(0), jx = R(0), jy = R(0), e2 = R(0);
@@ -87,12 +86,12 @@ __device__ void cell_features_n(const Params<R>& p, const LatTab<R>& L, const S*
   out[6] = (float)pyy;
   out[7] = (float)qx;
   out[8] = (float)qy;
-  out[9] = (float)(0.5 * (mrho[cxp] - mrho[cxm]));
-  out[10] = (float)(0.5 * (mrho[cyp] - mrho[cym]));
-  out[11] = (float)(0.5 * (mux[cxp] - mux[cxm]));
-  out[12] = (float)(0.5 * (mux[cyp] - mux[cym]));
-  out[13] = (float)(0.5 * (muy[cxp] - muy[cxm]));
-  out[14] = (float)(0.5 * (muy[cyp] - muy[cym]));
+  out[9] = (float)(R(0.5) * (mrho[cxp] - mrho[cxm]));
+  out[10] = (float)(R(0.5) * (mrho[cyp] - mrho[cym]));
+  out[11] = (float)(R(0.5) * (mux[cxp] - mux[cxm]));
+  out[12] = (float)(R(0.5) * (mux[cyp] - mux[cym]));
+  out[13] = (float)(R(0.5) * (muy[cxp] - muy[cxm]));
+  out[14] = (float)(R(0.5) * (muy[cyp] - muy[cym]));
   out[15] = (float)sqrt(ux * ux + uy * uy);
 #pragma unroll
   for (int q = 0; q < kFeat; ++q) out[q] *= c_scale[q];
@@ -100,8 +99,7 @@ __device__ void cell_features_n(const Params<R>& p, const LatTab<R>& L, const S*
 
 template <class S, class R>
 __device__ void cell_features(const Params<R>& p, const S* f0, const S* f1, int k, int x, int y,
-                              const double* mrho, const double* mux, const double* muy,
-                              float* out) {
+                              const R* mrho, const R* mux, const R* muy, float* out) {
   const LatTab<R>& L = p.lat[k];
   const S* f = k ? f1 : f0;
   switch (L.n) {
@@ -109,6 +107,50 @@ __device__ void cell_features(const Params<R>& p, const S* f0, const S* f1, int 
     case 4: cell_features_n<4, S, R>(p, L, f, x, y, mrho, mux, muy, out); break;
     default: cell_features_n<5, S, R>(p, L, f, x, y, mrho, mux, muy, out); break;
   }
+}
+
+// rho, u_x, u_y of one cell from its own lattice, in the arithmetic type
+// (the values the gradient features difference).
+template <int N, class S, class R>
+__device__ __forceinline__ void cell_ru(const Params<R>& p, const LatTab<R>& L, const S* f,
+                                        size_t base, R* out) {
+  R dr = R(0), jx = R(0), jy = R(0);
+#pragma unroll
+  for (int iy = 0; iy < N; ++iy)
+#pragma unroll
+    for (int ix = 0; ix < N; ++ix) {
+      const R v = static_cast<R>(f[(size_t)(ix + N * iy) * p.plane + base]);
+      dr += v;
+      jx += L.c[ix] * v;
+      jy += L.c[iy] * v;
+    }
+  const R rho = R(1) + dr;
+  out[0] = rho;
+  out[1] = jx / rho;
+  out[2] = jy / rho;
+}
+
+// Moment planes of the gradient features, one thread per cell.
+template <class S, class R>
+__global__ void __launch_bounds__(kTX * kTY)
+k_ind_moments(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restrict__ flag,
+              R* __restrict__ mrho, R* __restrict__ mux, R* __restrict__ muy) {
+  const int x = blockIdx.x * kTX + threadIdx.x, y = blockIdx.y * kTY + threadIdx.y;
+  if (x >= p.nx || y >= p.ny) return;
+  const long long c = x + (long long)p.nx * y;
+  const int k = flag[c];
+  const LatTab<R>& L = p.lat[k];
+  const S* f = k ? f1 : f0;
+  const size_t base = (size_t)(y + p.G) * p.pitch + (x + kOX);
+  R m[3];
+  switch (L.n) {
+    case 3: cell_ru<3, S, R>(p, L, f, base, m); break;
+    case 4: cell_ru<4, S, R>(p, L, f, base, m); break;
+    default: cell_ru<5, S, R>(p, L, f, base, m); break;
+  }
+  mrho[c] = m[0];
+  mux[c] = m[1];
+  muy[c] = m[2];
 }
 
 __device__ __forceinline__ uint32_t pack2(__half lo, __half hi) {
@@ -146,8 +188,8 @@ __device__ __forceinline__ void bfrag(const __half* W, int ncols, int k0, int nt
 template <class S, class R>
 __global__ void __launch_bounds__(kIndThreads)
 k_indicator(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restrict__ flag,
-            const double* __restrict__ mrho, const double* __restrict__ mux,
-            const double* __restrict__ muy, const __half* __restrict__ w1,
+            const R* __restrict__ mrho, const R* __restrict__ mux,
+            const R* __restrict__ muy, const __half* __restrict__ w1,
             const float* __restrict__ b1, const __half* __restrict__ w2,
             const float* __restrict__ b2, const float* __restrict__ w3, float b3, float thr,
             float* feat_out, float* logit_out, uint8_t* flag_out) {
@@ -251,9 +293,13 @@ k_indicator(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restri
 
 template <class S, class R>
 cudaError_t launch_indicator(const Params<R>& p, const S* f0, const S* f1, const uint8_t* flag,
-                             const double* mrho, const double* mux, const double* muy,
-                             const IndicatorDev& w, float thr, float* feat_out, float* logit_out,
-                             uint8_t* flag_out, cudaStream_t st) {
+                             R* mrho, R* mux, R* muy, const IndicatorDev& w, float thr,
+                             float* feat_out, float* logit_out, uint8_t* flag_out,
+                             cudaStream_t st) {
+  const dim3 tg((p.nx + kTX - 1) / kTX, (p.ny + kTY - 1) / kTY);
+  k_ind_moments<S, R><<<tg, dim3(kTX, kTY), 0, st>>>(p, f0, f1, flag, mrho, mux, muy);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   const long long nc = (long long)p.nx * p.ny;
   long long blocks = (nc + kIndThreads - 1) / kIndThreads;
   const long long cap = (long long)p.nsm * 16;
@@ -266,9 +312,8 @@ cudaError_t launch_indicator(const Params<R>& p, const S* f0, const S* f1, const
 
 #define SLBM_IND_INST(S, R)                                                                  \
   template cudaError_t launch_indicator<S, R>(const Params<R>&, const S*, const S*,          \
-                                              const uint8_t*, const double*, const double*,  \
-                                              const double*, const IndicatorDev&, float,     \
-                                              float*, float*, uint8_t*, cudaStream_t);
+                                              const uint8_t*, R*, R*, R*, const IndicatorDev&, \
+                                              float, float*, float*, uint8_t*, cudaStream_t);
 SLBM_IND_INST(float, float)
 SLBM_IND_INST(double, double)
 SLBM_IND_INST(__half, float)

@@ -20,26 +20,59 @@
 
 namespace slbm {
 
+// Accumulator of the lifting's moment sums.  In FP32 it is the compensated
+// dot product Dot2 of Ogita, Rump and Oishi ("Accurate sum and dot product",
+// SIAM J. Sci. Comput. 26, 2005): each product is split exactly with an FMA,
+// each addition with TwoSum, and the error terms are summed alongside, so the
+// result is as accurate as an accumulation in twice the working precision --
+// at FP32 rates, where GB300's FP64 rate is a small fraction of its FP32 rate.
+// In FP64 it sums plainly.
+template <class R>
+struct MomentAcc {
+  R s = R(0), c = R(0);
+  __device__ __forceinline__ void add(R a) {
+    if constexpr (sizeof(R) == 8) {
+      s += a;
+    } else {
+      const R t = s + a, z = t - s;
+      c += (s - (t - z)) + (a - z);
+      s = t;
+    }
+  }
+  __device__ __forceinline__ void add_product(R x, R y) {
+    if constexpr (sizeof(R) == 8) {
+      s = fma(x, y, s);
+    } else {
+      const R pr = x * y, pe = fmaf(x, y, -pr);
+      add(pr);
+      c += pe;
+    }
+  }
+  __device__ __forceinline__ R value() const { return s + c; }
+};
+
 template <int NQ, int NQQ, class R>
 struct PostMath {
-  // Lifting f_q -> f_Q on deviations: f^L_Q + L (f_q - f^L_q) L^T (moment sums FP64).
+  // Lifting f_q -> f_Q on deviations: f^L_Q + L (f_q - f^L_q) L^T (moment
+  // sums in twice the working precision for FP32, see MomentAcc).
   static __device__ __forceinline__ void lift(const Params<R>& p, const R (*sq)[kMaxN],
                                               R (*sQ)[kMaxN]) {
     const LatTab<R>& Lq = p.lat[0];
-    double dr = 0.0, mx = 0.0, my = 0.0;
+    MomentAcc<R> ar, ax, ay;
 #pragma unroll
     for (int iy = 0; iy < NQ; ++iy)
 #pragma unroll
       for (int ix = 0; ix < NQ; ++ix) {
-        const double v = (double)sq[iy][ix];
-        dr += v;
-        mx += (double)Lq.c[ix] * v;
-        my += (double)Lq.c[iy] * v;
+        const R v = sq[iy][ix];
+        ar.add(v);
+        ax.add_product(Lq.c[ix], v);
+        ay.add_product(Lq.c[iy], v);
       }
-    const R inv = R(1) / (R)(1.0 + dr);
-    const R ux = (R)mx * inv, uy = (R)my * inv;
+    const R dr = ar.value();
+    const R inv = R(1) / (R(1) + dr);
+    const R ux = ax.value() * inv, uy = ay.value() * inv;
     R eq[kMaxN][kMaxN], A[kMaxN][kMaxN];
-    eq_dev<R>(Lq, NQ, (R)dr, ux, uy, eq);
+    eq_dev<R>(Lq, NQ, dr, ux, uy, eq);
 #pragma unroll
     for (int iy = 0; iy < NQ; ++iy)
 #pragma unroll
@@ -232,126 +265,44 @@ __device__ __forceinline__ bool grid_wait(const int* ctr, int target, int* err) 
   return ok != 0;
 }
 
-constexpr int kPostMaxGrid = 4 * kTX * kTY;  // CTAs of the post-step kernel at most (1024)
-
 // Per-step post-step kernel (cooperative launch: every CTA resident).
-//  1. Work list.  The stream kernel has OR-ed, into one word per tile, the
-//     lattices of the tile's 3 x 3 tile neighbourhood and the tile's own flip
-//     bit; a tile has conversion work iff its word holds both lattices or a
-//     flip.  CTA b compacts the work tiles of its segment of the tiles
-//     (coalesced) into the segment's part of `list` and publishes the count.
-//  2. After a grid-wide wait, every CTA forms the prefix of the counts and
-//     converts the work tiles of global rank r = b, b + G, ... (post_tile),
-//     so clustered interfaces spread evenly over the GPU.
-//  3. After a second grid-wide wait (every conversion final), the ghost ring
-//     of both lattices (halo_element).
-// sync: [2][3] ints {CTAs scanned, CTAs converted, unused}; this launch uses
-// half `parity`, which the previous launch cleared, and clears the other.
-// counts: gridDim.x ints.  list: ntiles ints.
+//  1. Interface conversion.  The stream kernel has OR-ed, into one word per
+//     tile, the lattices of the tile's 3 x 3 tile neighbourhood and the tile's
+//     own flip bit, and listed the candidate tiles (add_work).  CTA b takes
+//     list entries b, b + G, ... and converts those whose word is work (both
+//     lattices or a flip; post_tile), so clustered interfaces spread evenly
+//     over the GPU.
+//  2. After a grid-wide wait (every conversion final), the ghost ring of
+//     both lattices (halo_element).
+// sync: [2][3] ints {CTAs converted, unused, unused}; this launch uses half
+// `parity`, which the previous launch cleared, and clears the other.
 template <int NL, int NH, class S, class R>
 __global__ void __launch_bounds__(kTX * kTY)
 k_post_step(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ flag_old,
             const uint8_t* __restrict__ flag_new, const BcDev bc, const int* __restrict__ work,
-            int ntx, int nty, int* sync, int* counts, int* list, int parity, int nghost,
-            int* err) {
+            const int* __restrict__ list, const int* __restrict__ nlist, int ntx, int* sync,
+            int parity, int nghost, int* err) {
   __shared__ uint8_t sf[kTY + 2 * kBandMax][kTX + 2 * kBandMax];
-  __shared__ int warp_cnt[kTY];
-  __shared__ int prefix[kPostMaxGrid + 1];
   const int tid = threadIdx.y * kTX + threadIdx.x;
-  const int lane = tid & 31, warp = tid >> 5;
   const int G = (int)gridDim.x, b = (int)blockIdx.x;
   int* c = sync + 3 * parity;
   if (b == 0 && tid == 0) {
     int* o = sync + 3 * (parity ^ 1);
     o[0] = o[1] = o[2] = 0;
   }
-  auto is_work = [](int w) { return (w & 4) || (w & 3) == 3; };
-  // 1. compact this CTA's segment [sa, sb): warp w takes a contiguous part in
-  //    32-tile chunks (coalesced), counting first, then writing
-  const int ntiles = ntx * nty;
-  const int per = (ntiles + G - 1) / G;
-  const int sa = min(ntiles, b * per), sb = min(ntiles, sa + per);
-  const int wper = ((sb - sa + kTY - 1) / kTY + 31) / 32 * 32;
-  const int wa = min(sb, sa + warp * wper), wb = min(sb, wa + wper);
-  int wc = 0;
-  for (int t0 = wa; t0 < wb; t0 += 32) {
-    const int t = t0 + lane;
-    wc += __popc(__ballot_sync(0xffffffffu, t < wb && is_work(__ldcg(work + t))));
-  }
-  if (lane == 0) warp_cnt[warp] = wc;
-  __syncthreads();
-  int wbase = 0, seg_total = 0;
-#pragma unroll
-  for (int w = 0; w < kTY; ++w) {
-    const int v = warp_cnt[w];
-    if (w < warp) wbase += v;
-    seg_total += v;
-  }
-  for (int t0 = wa; t0 < wb; t0 += 32) {
-    const int t = t0 + lane;
-    const bool wk = t < wb && is_work(__ldcg(work + t));
-    const uint32_t bal = __ballot_sync(0xffffffffu, wk);
-    if (wk) list[sa + wbase + __popc(bal & ((1u << lane) - 1u))] = t;
-    wbase += __popc(bal);
-  }
-  __syncthreads();
-  if (tid == 0) {
-    counts[b] = seg_total;
-    __threadfence();
-    atomicAdd(&c[0], 1);
-  }
-  if (!grid_wait(&c[0], G, err)) return;
-  // 2. prefix of the segment counts (thread tid sums entries 4 tid .. 4 tid + 3,
-  //    then a CTA-wide scan of those sums), then this CTA's share of the work
-  {
-    int v[4], sum = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = 4 * tid + q;
-      v[q] = i < G ? __ldcg(counts + i) : 0;
-      sum += v[q];
-    }
-    int inc = sum;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int u = __shfl_up_sync(0xffffffffu, inc, d);
-      if (lane >= d) inc += u;
-    }
-    if (lane == 31) warp_cnt[warp] = inc;
-    __syncthreads();
-    int run = inc - sum;
-#pragma unroll
-    for (int w = 0; w < kTY; ++w)
-      if (w < warp) run += warp_cnt[w];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = 4 * tid + q;
-      if (i < G) prefix[i] = run;
-      run += v[q];
-    }
-    if (4 * tid + 3 >= G - 1 && 4 * tid <= G - 1) prefix[G] = run;
-  }
-  __syncthreads();
-  const int total = prefix[G];
+  const int total = *nlist;
   for (int r = b; r < total; r += G) {
-    // segment holding global rank r: the last i with prefix[i] <= r
-    int lo = 0, hi = G - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (prefix[mid] <= r) lo = mid;
-      else hi = mid - 1;
-    }
-    const int t = __ldcg(list + min(ntiles, lo * per) + (r - prefix[lo]));
+    const int t = list[r];
+    if (!post_work_word(work[t])) continue;  // all high-order neighbourhood
     post_tile<NL, NH, S, R>(p, f0, f1, flag_old, flag_new, bc, 0, false, nullptr, (t % ntx) * kTX,
                             (t / ntx) * kTY, sf);
   }
   __syncthreads();
   if (tid == 0) {
     __threadfence();
-    atomicAdd(&c[1], 1);
+    atomicAdd(&c[0], 1);
   }
-  if (!grid_wait(&c[1], G, err)) return;
-  // 3. ghost ring
+  if (!grid_wait(&c[0], G, err)) return;
   const int q0 = NL * NL, q1 = NH * NH;
   const long long total_e = (long long)nghost * (q0 + q1);
   for (long long e = (long long)b * (kTX * kTY) + tid; e < total_e;
@@ -365,9 +316,9 @@ k_post_step(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ flag_ol
 template <class S, class R>
 cudaError_t launch_post_step_impl(const Params<R>& p, S* f0, S* f1, const uint8_t* flag_old,
                                   const uint8_t* flag_new, const BcDev& bc, const int* work,
-                                  int* sync, int* counts, int* list, int parity, int* err,
-                                  cudaStream_t st) {
-  const int ntx = (p.nx + kTX - 1) / kTX, nty = (p.ny + kTY - 1) / kTY;
+                                  const int* list, const int* nlist, int* sync, int parity,
+                                  int* err, cudaStream_t st) {
+  const int ntx = (p.nx + kTX - 1) / kTX;
   const int nghost = 2 * p.G * (p.nx + 2 * p.G) + 2 * p.G * p.ny;
   const int nl = p.lat[0].n, nh = p.lat[1].n;
   const dim3 blk(kTX, kTY);
@@ -380,8 +331,7 @@ cudaError_t launch_post_step_impl(const Params<R>& p, S* f0, S* f1, const uint8_
       if (e != cudaSuccess) return e;                                                         \
     }                                                                                         \
     if (per_sm < 1) return cudaErrorInvalidConfiguration;                                     \
-    int grid = (per_sm < 4 ? per_sm : 4) * p.nsm;                                             \
-    if (grid > kPostMaxGrid) grid = kPostMaxGrid;                                             \
+    const int grid = (per_sm < 4 ? per_sm : 4) * p.nsm;                                       \
     Params<R> pp = p;                                                                         \
     S* a0 = f0;                                                                               \
     S* a1 = f1;                                                                               \
@@ -389,12 +339,12 @@ cudaError_t launch_post_step_impl(const Params<R>& p, S* f0, S* f1, const uint8_
     const uint8_t* fn = flag_new;                                                             \
     BcDev b = bc;                                                                             \
     const int* wk = work;                                                                     \
-    int ntx_ = ntx, nty_ = nty, par = parity, ng = nghost;                                    \
+    const int* li = list;                                                                     \
+    const int* nli = nlist;                                                                   \
+    int ntx_ = ntx, par = parity, ng = nghost;                                                \
     int* sy = sync;                                                                           \
-    int* co = counts;                                                                         \
-    int* li = list;                                                                           \
     int* er = err;                                                                            \
-    void* args[] = {&pp, &a0, &a1, &fo, &fn, &b, &wk, &ntx_, &nty_, &sy, &co, &li, &par, &ng, &er}; \
+    void* args[] = {&pp, &a0, &a1, &fo, &fn, &b, &wk, &li, &nli, &ntx_, &sy, &par, &ng, &er}; \
     return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), blk, args, 0, st);      \
   }
   SLBM_POSTSTEP_CASE(3, 4)

@@ -99,13 +99,16 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, ui
 // ------------------------------------------------------------ the math
 
 // Store conversion of a new population value.  FP32 / FP64: plain.  FP16:
-// stochastic rounding of the deviation -- the 13 dropped mantissa bits are
-// compared against a counter-based random number (an integer hash of the
-// element index and the step), so a value is rounded up with probability
-// equal to its distance from the truncated neighbour.  Round-to-nearest
-// errors of a smooth field repeat from cell to cell and step to step and add
-// up; these are unbiased and independent, and the interpolation averages
-// them away.  Half subnormals (|v| < 2^-14) round to nearest.
+// stochastic rounding of the deviation -- a 13-bit random number r is added
+// to the 13 mantissa bits that FP16 drops before truncating, so a value is
+// rounded up with probability equal to its distance from the truncated
+// neighbour.  r comes from a counter-based generator: one integer hash of the
+// cell's index and the step per cell (hash32), then per population one
+// multiplicative hash of that key and the population index (pop_random).
+// Round-to-nearest errors of a smooth field repeat from cell to cell and step
+// to step and add up; these are unbiased and independent, and the
+// interpolation averages them away.  Half subnormals (|v| < 2^-14) round to
+// nearest.
 __device__ __forceinline__ uint32_t hash32(uint32_t x) {
   x ^= x >> 16;
   x *= 0x7feb352du;
@@ -115,16 +118,21 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
   return x;
 }
 
+// 13 random bits for population i of the cell with key `key` (the top bits
+// of a multiplicative hash of the key and i).
+__device__ __forceinline__ uint32_t pop_random(uint32_t key, int i) {
+  return ((key ^ ((uint32_t)i * 0x9e3779b9u)) * 0x85ebca6bu) >> 19;
+}
+
 template <class S, class R>
 __device__ __forceinline__ S to_storage(R v, uint32_t) {
   return static_cast<S>(v);
 }
 
 template <>
-__device__ __forceinline__ __half to_storage<__half, float>(float v, uint32_t key) {
+__device__ __forceinline__ __half to_storage<__half, float>(float v, uint32_t r) {
   if (!(fabsf(v) >= 6.103515625e-05f) || fabsf(v) >= 65504.0f) return __float2half_rn(v);
   const uint32_t b = __float_as_uint(v);
-  const uint32_t r = hash32(key) & 0x1fffu;
   return __float2half_rz(__uint_as_float((b + r) & ~0x1fffu));
 }
 
@@ -208,6 +216,7 @@ __device__ __forceinline__ void stream_collide_cell(const Params<R>& p, const La
   R px[N];
 #pragma unroll
   for (int jx = 0; jx < N; ++jx) px[jx] = L.w1[jx] + dx[jx];
+  const uint32_t key = hash32((uint32_t)obase ^ (p.seed * 0x9e3779b9u));  // FP16 rounding only
 #pragma unroll
   for (int jy = 0; jy < N; ++jy) {
     const R py = L.w1[jy] + dy[jy];
@@ -218,8 +227,7 @@ __device__ __forceinline__ void stream_collide_cell(const Params<R>& p, const La
       // f^L - W = dr px py + w_x dphi_y + dphi_x (w_y + dphi_y)
       const R feq = px[jx] * ty + L.w1[jx] * dy[jy] + dx[jx] * py;
       const size_t idx = (size_t)i * p.plane + obase;
-      fout[idx] = to_storage<S, R>(f[i] + p.omega * (feq - f[i]),
-                                   (uint32_t)idx ^ (p.seed * 0x9e3779b9u));
+      fout[idx] = to_storage<S, R>(f[i] + p.omega * (feq - f[i]), pop_random(key, i));
     }
   }
 }
@@ -351,7 +359,10 @@ k_stream_collide(const Params<R> p, const __grid_constant__ CUtensorMap tm0,
   if (tid == 0) {
     // this launch's counter p.sched[parity] was cleared by the previous launch;
     // clear the other one for the next
-    if (blockIdx.x == 0) p.sched[p.sched_parity ^ 1] = 0;
+    if (blockIdx.x == 0) {
+      p.sched[p.sched_parity ^ 1] = 0;
+      p.wcount[p.sched_parity ^ 1] = 0;  // the other work list, likewise
+    }
     for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
     mbar_fence_init();
     tile_bits[0] = tile_bits[1] = tile_bits[2] = 0;
@@ -376,6 +387,9 @@ k_stream_collide(const Params<R> p, const __grid_constant__ CUtensorMap tm0,
   int fl_next = cell_flag(ring[1]);  // flags are loaded one item ahead
   __syncthreads();
   int bits = 0;  // cells this thread computed: bit 0/1 = next-step lattice, bit 2 = flipped
+  // threads 0-8: a work-word atomic and a list slot whose results are used
+  // at the next tile end (tile -1: none)
+  int pend_t = -1, pend_was = 0, slot_t = -1, slot = 0;
   for (int j = 0;; ++j) {
     const Item it = ring[j & (kRing - 1)];
     if (it.t >= ntiles) break;
@@ -431,7 +445,7 @@ k_stream_collide(const Params<R> p, const __grid_constant__ CUtensorMap tm0,
       // the tile's next-step mask, and its contribution to the post-step
       // kernel's work bits of the 3 x 3 tile neighbourhood: the lattices (all
       // nine) and the flip bit (the tile itself); a tile has conversion work
-      // iff its word ends with both lattices or a flip
+      // iff its word ends with both lattices or a flip, and is then listed
       const int m = tile_bits[j % 3];
       if (tid == 0) mask_next[it.t] = (uint8_t)m;
       int ntx_ = it.tx + tid % 3 - 1, nty_ = it.ty + tid / 3 - 1;
@@ -445,8 +459,26 @@ k_stream_collide(const Params<R> p, const __grid_constant__ CUtensorMap tm0,
         if (p.periodic_y) nty_ = nty_ < 0 ? nty_ + nty : nty_ - nty;
         else ok = false;
       }
+      // listing as add_work, with each returning atomic's result used one
+      // tile later, so the CTA does not wait for it
+      const int half = p.sched_parity;
+      if (slot_t >= 0) p.wlist[(size_t)half * ntiles + slot] = slot_t;
+      slot_t = -1;
+      if (pend_t >= 0 && !(pend_was & 6)) {
+        slot = atomicAdd(p.wcount + half, 1);
+        slot_t = pend_t;
+      }
+      pend_t = -1;
       const int contrib = (m & 3) | (tid == 4 ? (m & 4) : 0);
-      if (ok && contrib) atomicOr(p.work + p.sched_parity * ntiles + nty_ * ntx + ntx_, contrib);
+      if (ok && contrib) {
+        int* w = p.work + (size_t)half * ntiles + nty_ * ntx + ntx_;
+        if (contrib & 6) {
+          pend_was = atomicOr(w, contrib);
+          pend_t = nty_ * ntx + ntx_;
+        } else {
+          atomicOr(w, contrib);
+        }
+      }
       // the other half is the next step's: clear this tile's word there
       if (tid == 0) p.work[(p.sched_parity ^ 1) * ntiles + it.t] = 0;
     }
@@ -457,6 +489,11 @@ k_stream_collide(const Params<R> p, const __grid_constant__ CUtensorMap tm0,
         issue(nn_it, s);
       }
     }
+  }
+  if (tid < 9) {  // the deferred listings of the last tile
+    const size_t h = (size_t)p.sched_parity * ntiles;
+    if (slot_t >= 0) p.wlist[h + slot] = slot_t;
+    if (pend_t >= 0 && !(pend_was & 6)) p.wlist[h + atomicAdd(p.wcount + p.sched_parity, 1)] = pend_t;
   }
 }
 
