@@ -184,6 +184,7 @@ struct Layout {
   size_t flags[2], flag_tmp, tile_mask[2], macro[4], partials, audit_out, err, bc[4][3];
   size_t lam[2];             // co-moving frame planes {u_x, u_y, T} per buffer
   size_t sched;              // two tile counters of the stream kernel's scheduler
+  size_t seed_ctr;           // FP16 rounding key counter
   size_t post_sync;          // 2 x 3 counters of the post-step kernel's grid-wide waits
   size_t post_work;          // 2 x ntiles work words (stream kernel -> post-step kernel)
   size_t post_nlist;         // 2 counters: work tiles listed in each half of post_list
@@ -258,6 +259,7 @@ Layout make_layout(const slbm_grid* g, int lo, int hi, int order, int precision)
     for (int q = 0; q < 3; ++q) { Lo.bc[s][q] = off; off = align_up(off + side * 8, 256); }
   for (int b = 0; b < 2; ++b) { Lo.lam[b] = off; off = align_up(off + 3 * nc * es, 256); }
   Lo.sched = off; off = align_up(off + 2 * sizeof(int), 256);
+  Lo.seed_ctr = off; off = align_up(off + sizeof(uint32_t), 256);
   Lo.post_sync = off; off = align_up(off + 6 * sizeof(int), 256);
   Lo.post_work = off; off = align_up(off + 2 * ntiles * sizeof(int), 256);
   Lo.post_nlist = off; off = align_up(off + 2 * sizeof(int), 256);
@@ -308,6 +310,14 @@ struct slbm_s {
   int profiling;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used;
+  // CUDA graphs of two lattice-frame steps, one per parity state (step_pair)
+  struct GraphEntry {
+    int key;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs;
+  cudaStream_t cap_st;           // private stream the graphs are captured on
+  int graphs_off;                // a capture failed: step with direct launches
 
   template <class T> T* at(size_t off) { return reinterpret_cast<T*>(ws + off); }
   void* pops(int buf, int k) { return ws + lay.pops[buf][k]; }
@@ -546,7 +556,6 @@ int step_once(slbm_s* h) {
   int* err = h->at<int>(h->lay.err);
   const uint8_t* mask = h->at<uint8_t>(h->lay.tile_mask[h->mcur]);
   uint8_t* mask_next = h->at<uint8_t>(h->lay.tile_mask[h->mcur ^ 1]);
-  h->pf.seed = h->pd.seed = (uint32_t)h->steps;
   h->pf.sched_parity = h->pd.sched_parity = (int)(h->sc_launches & 1);
   h->sc_launches++;
   e = with_types(h, [&](auto ty, const auto& prm) {
@@ -579,6 +588,63 @@ int step_once(slbm_s* h) {
   return SLBM_OK;
 }
 
+// Two lattice-frame steps as one CUDA graph launch: the four kernel launches
+// of two step_once calls, captured once per parity state (buffer, flag and
+// mask halves, scheduler and post-step counter parities) on a private stream
+// and replayed on the handle's stream.  After two steps every parity is back
+// where it was, so the replay only advances the counters.  Returns 1 (and
+// stops trying) if the capture is refused, so the caller steps directly.
+int step_pair(slbm_s* h) {
+  const int key = h->cur | h->mcur << 1 | h->fcur << 2 | (int)(h->sc_launches & 1) << 3 |
+                  (int)(h->post_launches & 1) << 4;
+  cudaGraphExec_t exec = nullptr;
+  for (const auto& e : h->graphs)
+    if (e.key == key) exec = e.exec;
+  if (!exec) {
+    if (!h->cap_st && cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+      h->cap_st = nullptr;
+      h->graphs_off = 1;
+      return 1;
+    }
+    // the host state two recorded steps advance
+    const int cur = h->cur, mcur = h->mcur, fcur = h->fcur;
+    const long long steps = h->steps, scl = h->sc_launches, pol = h->post_launches;
+    cudaStream_t st = h->st;
+    h->st = h->cap_st;
+    cudaGraph_t g = nullptr;
+    int rc = SLBM_OK;
+    cudaError_t e = cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      rc = step_once(h);
+      if (rc == SLBM_OK) rc = step_once(h);
+      e = cudaStreamEndCapture(h->cap_st, &g);
+    }
+    h->st = st;
+    h->cur = cur;
+    h->mcur = mcur;
+    h->fcur = fcur;
+    h->steps = steps;
+    h->sc_launches = scl;
+    h->post_launches = pol;
+    if (e == cudaSuccess && rc == SLBM_OK && g) e = cudaGraphInstantiate(&exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess || rc != SLBM_OK || !exec) {
+      // nothing recorded has run: clear the refusal and step directly
+      cudaGetLastError();
+      h->failed = 0;
+      h->err[0] = 0;
+      h->graphs_off = 1;
+      return 1;
+    }
+    h->graphs.push_back({key, exec});
+  }
+  SLBM_CK(h, cudaGraphLaunch(exec, h->st), "graph launch");
+  h->steps += 2;
+  h->sc_launches += 2;
+  h->post_launches += 2;
+  return SLBM_OK;
+}
+
 template <class R>
 void fill_params(Params<R>& p, const slbm_s* h, const Lattice1D& a, const Lattice1D& b, double dt) {
   std::memset(&p, 0, sizeof(p));
@@ -596,6 +662,7 @@ void fill_params(Params<R>& p, const slbm_s* h, const Lattice1D& a, const Lattic
   p.band = h->lay.G;
   p.nsm = h->nsm;
   p.sched = reinterpret_cast<int*>(h->ws + h->lay.sched);
+  p.seed_ctr = reinterpret_cast<uint32_t*>(h->ws + h->lay.seed_ctr);
   p.work = reinterpret_cast<int*>(h->ws + h->lay.post_work);
   p.wlist = reinterpret_cast<int*>(h->ws + h->lay.post_list);
   p.wcount = reinterpret_cast<int*>(h->ws + h->lay.post_nlist);
@@ -656,7 +723,15 @@ void fill_pond(PondParams<R>& q, const slbm_s* h, const Params<R>& p, const Latt
     for (int m = 0; m < kMaxN; ++m) q.proj[j][m] = p.conv.proj[j][m];
 }
 
+// Captured graphs hold kernel arguments by value: drop them whenever the
+// parameters or the boundary description change.
+void drop_graphs(slbm_s* h) {
+  for (auto& e : h->graphs) cudaGraphExecDestroy(e.exec);
+  h->graphs.clear();
+}
+
 void refresh_params(slbm_s* h) {
+  drop_graphs(h);
   const Lattice1D a = make_1d(h->nlo), b = make_1d(h->nhi);
   const double dt = pair_dt(a, b);
   fill_params(h->pf, h, a, b, dt);
@@ -958,6 +1033,8 @@ int slbm_destroy(slbm_t h) {
   int rc = SLBM_OK;
   if (cudaStreamSynchronize(h->st) != cudaSuccess) rc = SLBM_ECUDA;
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  drop_graphs(h);
+  if (h->cap_st) cudaStreamDestroy(h->cap_st);
   if (h->ind_buf) cudaFree(h->ind_buf);
   if (h->owns_ws && cudaFree(h->ws) != cudaSuccess) rc = SLBM_ECUDA;
   delete h;
@@ -1181,6 +1258,7 @@ int slbm_set_boundary(slbm_t h, int side, int kind, const double* rho, const dou
       if (rc) return rc;
     }
   h->bc_kind[side] = kind;
+  drop_graphs(h);
   SLBM_CK(h, ghosts(h, h->flags(h->fcur)), "ghost launch");
   SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
   return SLBM_OK;
@@ -1189,11 +1267,35 @@ int slbm_set_boundary(slbm_t h, int side, int kind, const double* rho, const dou
 int slbm_step(slbm_t h, int n) {
   SLBM_GUARD(h);
   if (n < 0) return fail(h, SLBM_EINVAL, "n must be >= 0");
-  for (int s = 0; s < n; ++s) {
-    int rc = step_once(h);
-    if (rc) return rc;
-    if (h->crit == SLBM_CRIT_MLP && h->steps % h->ind_interval == 0 && (rc = apply_indicator(h)))
-      return rc;
+  int s = 0;
+  while (s < n) {
+    // steps up to the next learned-indicator evaluation
+    int chunk = n - s;
+    if (h->crit == SLBM_CRIT_MLP) {
+      const int to_eval = h->ind_interval - (int)(h->steps % h->ind_interval);
+      if (to_eval < chunk) chunk = to_eval;
+    }
+    int done = 0;
+    // pairs of lattice-frame steps as graph launches once the kernels have
+    // run directly (their one-time attribute and occupancy set-up), unless
+    // tracing needs the per-kernel events
+    const bool graphs = h->frame == SLBM_FRAME_LATTICE && !h->profiling && !h->graphs_off &&
+                        h->sc_launches > 0;
+    while (graphs && !h->graphs_off && chunk - done >= 2) {
+      const int rc = step_pair(h);
+      if (rc == 1) break;
+      if (rc) return rc;
+      done += 2;
+    }
+    for (; done < chunk; ++done) {
+      const int rc = step_once(h);
+      if (rc) return rc;
+    }
+    s += chunk;
+    if (h->crit == SLBM_CRIT_MLP && h->steps % h->ind_interval == 0) {
+      const int rc = apply_indicator(h);
+      if (rc) return rc;
+    }
   }
   return SLBM_OK;
 }

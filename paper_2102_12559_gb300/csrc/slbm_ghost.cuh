@@ -113,24 +113,69 @@ __device__ __forceinline__ R diffuse_value(const LatTab<R>& L, const S* f, long 
   return drw * (w_i + e_i) + e_i;
 }
 
-// Per-step ghost refresh of one element: ghost g (0 <= g < nghost) of the
-// ring, plane `plane` of both lattices' planes (lattice 0 first).  Copy
-// ghosts copy their interior source; INLET ghosts write the plane's lattice
-// equilibrium at the interior cell's density and the side's velocity (the
-// cell's own populations summed, one product term evaluated); DIRICHLET ghosts
-// are constant (written at setup) and left alone.  Interior values are read
-// through L2 (ld.global.cg): in the fused post-step kernel they were written
-// by other CTAs of the same launch.
+// Ghost cells that change from step to step: the ring's strips in order --
+// bottom and top (G rows of nx + 2G), left and right (G columns of ny) --
+// except those of a non-periodic side with constant (DIRICHLET) ghosts.
+struct GhostStrips {
+  int start[4], len[4], n;  // active strips, their ring offsets and sizes
+  int total;                // ghost cells in the active strips
+};
+
+template <class R>
+__device__ __forceinline__ GhostStrips active_ghost_strips(const Params<R>& p, const BcDev& bc) {
+  const int W = p.nx + 2 * p.G;
+  const int len[4] = {p.G * W, p.G * W, p.G * p.ny, p.G * p.ny};
+  const bool on[4] = {p.periodic_y || bc.kind[SLBM_SIDE_YMIN] != SLBM_BC_DIRICHLET,
+                      p.periodic_y || bc.kind[SLBM_SIDE_YMAX] != SLBM_BC_DIRICHLET,
+                      p.periodic_x || bc.kind[SLBM_SIDE_XMIN] != SLBM_BC_DIRICHLET,
+                      p.periodic_x || bc.kind[SLBM_SIDE_XMAX] != SLBM_BC_DIRICHLET};
+  GhostStrips a{};
+  int off = 0;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (on[s]) {
+      a.start[a.n] = off;
+      a.len[a.n] = len[s];
+      a.total += len[s];
+      ++a.n;
+    }
+    off += len[s];
+  }
+  return a;
+}
+
+// Ring index of active ghost cell q (0 <= q < a.total).
+__device__ __forceinline__ int active_ghost(const GhostStrips& a, int q) {
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (s < a.n && q < a.len[s]) return a.start[s] + q;
+    if (s < a.n) q -= a.len[s];
+  }
+  return -1;
+}
+
+// Per-step ghost refresh of one element: ghost g of the ring, plane `plane`
+// of both lattices' planes (lattice 0 first).  Copy ghosts copy their
+// interior source; INLET ghosts write the plane's lattice equilibrium at the
+// interior cell's density and the side's velocity (the cell's own populations
+// summed, one product term evaluated); DIRICHLET ghosts are constant (written
+// at setup) and left alone.  Only elements whose source cell lies in a work
+// tile (dep = 1) or outside every work tile (dep = 0) are written (`work`:
+// the step's work words, ntx tiles per row).
+// Interior values are read through L2 (ld.global.cg): in the post-step kernel
+// other CTAs of the same launch may have written them.
 template <int NL, int NH, class S, class R>
 __device__ __forceinline__ void halo_element(const Params<R>& p, S* f0, S* f1,
                                              const uint8_t* __restrict__ flag, const BcDev& bc,
-                                             int nghost, int g, int plane) {
+                                             int g, int plane, const int* __restrict__ work,
+                                             int ntx, int dep) {
   constexpr int q0 = NL * NL, q1 = NH * NH;
   int gx, gy, sx, sy, side = 0, idx = 0;
   ghost_coords(p.G, p.nx, p.ny, g, gx, gy);
   const int kind = ghost_source(p.nx, p.ny, p.periodic_x, p.periodic_y, bc, gx, gy, sx, sy, side,
                                 idx);
   if (kind == 2) return;
+  if (post_work_word(work[(sy / kTY) * ntx + sx / kTX]) != (dep != 0)) return;
   const int k = plane < q0 ? 0 : 1;
   const int i = k ? plane - q0 : plane;
   S* f = k ? f1 : f0;

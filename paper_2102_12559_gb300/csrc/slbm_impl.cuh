@@ -78,7 +78,8 @@ struct Params {
   int nsm;                      // multiprocessors of the handle's device (launch sizing)
   LatTab<R> lat[2];             // 0 = low-order, 1 = high-order
   ConvTab<R> conv;
-  uint32_t seed;                // per-step key of the FP16 stochastic rounding
+  uint32_t* seed_ctr;           // step key of the FP16 stochastic rounding (device counter,
+                                // advanced by every post-step launch)
   int* sched;                   // two tile counters of the stream kernel's scheduler
   int sched_parity;             // the counter (and work-bit half) this step uses
   int* work;                    // 2 x ntiles post-step work bits, accumulated by the stream kernel

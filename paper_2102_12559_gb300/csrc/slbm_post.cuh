@@ -272,8 +272,14 @@ __device__ __forceinline__ bool grid_wait(const int* ctr, int target, int* err) 
 //     list entries b, b + G, ... and converts those whose word is work (both
 //     lattices or a flip; post_tile), so clustered interfaces spread evenly
 //     over the GPU.
-//  2. After a grid-wide wait (every conversion final), the ghost ring of
-//     both lattices (halo_element).
+//  2. The ghost ring of both lattices, one thread per (ghost cell, plane) of
+//     the strips that change (halo_element).  A ghost whose source cell
+//     lies in a tile without conversion work is final once the stream kernel
+//     has run, and is written at once by the last CTAs (the work list fills
+//     the first ones); the others after a grid-wide wait, when every
+//     conversion is final.  (A lattice's planes at a cell outside every work
+//     tile are read by no cell of that lattice, so their stale copies are
+//     never used.)
 // sync: [2][3] ints {CTAs converted, unused, unused}; this launch uses half
 // `parity`, which the previous launch cleared, and clears the other.
 template <int NL, int NH, class S, class R>
@@ -281,7 +287,7 @@ __global__ void __launch_bounds__(kTX * kTY)
 k_post_step(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ flag_old,
             const uint8_t* __restrict__ flag_new, const BcDev bc, const int* __restrict__ work,
             const int* __restrict__ list, const int* __restrict__ nlist, int ntx, int* sync,
-            int parity, int nghost, int* err) {
+            int parity, int* err) {
   __shared__ uint8_t sf[kTY + 2 * kBandMax][kTX + 2 * kBandMax];
   const int tid = threadIdx.y * kTX + threadIdx.x;
   const int G = (int)gridDim.x, b = (int)blockIdx.x;
@@ -289,6 +295,7 @@ k_post_step(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ flag_ol
   if (b == 0 && tid == 0) {
     int* o = sync + 3 * (parity ^ 1);
     o[0] = o[1] = o[2] = 0;
+    ++*p.seed_ctr;  // the next stream launch rounds with a new key
   }
   const int total = *nlist;
   for (int r = b; r < total; r += G) {
@@ -300,17 +307,24 @@ k_post_step(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ flag_ol
   __syncthreads();
   if (tid == 0) {
     __threadfence();
-    atomicAdd(&c[0], 1);
+    atomicAdd(&c[0], 1);  // this CTA's conversions are final
   }
+  // ghost elements (active ghost cell, plane), counted from the last CTA:
+  // those whose source is outside every work tile while the other CTAs
+  // finish converting, the others after the wait
+  const GhostStrips gs = active_ghost_strips(p, bc);
+  const long long total_e = (long long)gs.total * (NL * NL + NH * NH);
+  auto ghosts = [&](int dep) {
+    for (long long e = (long long)(G - 1 - b) * (kTX * kTY) + tid; e < total_e;
+         e += (long long)G * (kTX * kTY)) {
+      const int plane = (int)(e / gs.total);
+      const int g = active_ghost(gs, (int)(e - (long long)plane * gs.total));
+      halo_element<NL, NH, S, R>(p, f0, f1, flag_new, bc, g, plane, work, ntx, dep);
+    }
+  };
+  ghosts(0);
   if (!grid_wait(&c[0], G, err)) return;
-  const int q0 = NL * NL, q1 = NH * NH;
-  const long long total_e = (long long)nghost * (q0 + q1);
-  for (long long e = (long long)b * (kTX * kTY) + tid; e < total_e;
-       e += (long long)G * (kTX * kTY)) {
-    const int plane = (int)(e / nghost);
-    halo_element<NL, NH, S, R>(p, f0, f1, flag_new, bc, nghost, (int)(e - (long long)plane * nghost),
-                               plane);
-  }
+  ghosts(1);
 }
 
 template <class S, class R>
@@ -319,7 +333,6 @@ cudaError_t launch_post_step_impl(const Params<R>& p, S* f0, S* f1, const uint8_
                                   const int* list, const int* nlist, int* sync, int parity,
                                   int* err, cudaStream_t st) {
   const int ntx = (p.nx + kTX - 1) / kTX;
-  const int nghost = 2 * p.G * (p.nx + 2 * p.G) + 2 * p.G * p.ny;
   const int nl = p.lat[0].n, nh = p.lat[1].n;
   const dim3 blk(kTX, kTY);
 #define SLBM_POSTSTEP_CASE(NL, NH)                                                            \
@@ -341,10 +354,10 @@ cudaError_t launch_post_step_impl(const Params<R>& p, S* f0, S* f1, const uint8_
     const int* wk = work;                                                                     \
     const int* li = list;                                                                     \
     const int* nli = nlist;                                                                   \
-    int ntx_ = ntx, par = parity, ng = nghost;                                                \
+    int ntx_ = ntx, par = parity;                                                             \
     int* sy = sync;                                                                           \
     int* er = err;                                                                            \
-    void* args[] = {&pp, &a0, &a1, &fo, &fn, &b, &wk, &li, &nli, &ntx_, &sy, &par, &ng, &er}; \
+    void* args[] = {&pp, &a0, &a1, &fo, &fn, &b, &wk, &li, &nli, &ntx_, &sy, &par, &er};      \
     return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), blk, args, 0, st);      \
   }
   SLBM_POSTSTEP_CASE(3, 4)

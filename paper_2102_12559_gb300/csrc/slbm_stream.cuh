@@ -157,7 +157,8 @@ __device__ __forceinline__ R row_interp(const S* row, const LatTab<R>& L, int jx
 template <int N, bool HI, int P, class S, class R>
 __device__ __forceinline__ void stream_collide_cell(const Params<R>& p, const LatTab<R>& L,
                                                     const S* src, S* __restrict__ fout,
-                                                    int obase, R& ux, R& uy, R& drho) {
+                                                    int obase, uint32_t seed, R& ux, R& uy,
+                                                    R& drho) {
   constexpr int kTXP = StageGeom<S>::txp;
   constexpr int PL = (kTY + 2 * stage_halo(P)) * kTXP;
   R f[N * N];
@@ -216,7 +217,7 @@ __device__ __forceinline__ void stream_collide_cell(const Params<R>& p, const La
   R px[N];
 #pragma unroll
   for (int jx = 0; jx < N; ++jx) px[jx] = L.w1[jx] + dx[jx];
-  const uint32_t key = hash32((uint32_t)obase ^ (p.seed * 0x9e3779b9u));  // FP16 rounding only
+  const uint32_t key = hash32((uint32_t)obase ^ (seed * 0x9e3779b9u));  // FP16 rounding only
 #pragma unroll
   for (int jy = 0; jy < N; ++jy) {
     const R py = L.w1[jy] + dy[jy];
@@ -386,6 +387,7 @@ k_stream_collide(const Params<R> p, const __grid_constant__ CUtensorMap tm0,
   }
   int fl_next = cell_flag(ring[1]);  // flags are loaded one item ahead
   __syncthreads();
+  const uint32_t seed = *p.seed_ctr;  // FP16 rounding key of this step
   int bits = 0;  // cells this thread computed: bit 0/1 = next-step lattice, bit 2 = flipped
   // threads 0-8: a work-word atomic and a list slot whose results are used
   // at the next tile end (tile -1: none)
@@ -418,9 +420,9 @@ k_stream_collide(const Params<R> p, const __grid_constant__ CUtensorMap tm0,
       const int obase = (y + p.G) * p.pitch + (x + kOX);
       R ux, uy, dr;  // dr: density deviation (unused here)
       if (it.k == 0)
-        stream_collide_cell<NL, false, P, S, R>(p, p.lat[0], src, fout0, obase, ux, uy, dr);
+        stream_collide_cell<NL, false, P, S, R>(p, p.lat[0], src, fout0, obase, seed, ux, uy, dr);
       else
-        stream_collide_cell<NH, true, P, S, R>(p, p.lat[1], src, fout1, obase, ux, uy, dr);
+        stream_collide_cell<NH, true, P, S, R>(p, p.lat[1], src, fout1, obase, seed, ux, uy, dr);
       int nf = it.k;
       if (p.crit == 1) {
         nf = sqrt(ux * ux + uy * uy) > p.thr ? 1 : 0;
