@@ -97,6 +97,9 @@ def lib():
         L.orc_audit.argtypes = [p, p]
         L.orc_get_pops.argtypes = [p, i, p]
         L.orc_set_pops.argtypes = [p, i, p]
+        L.orc_set_twopop.argtypes = [p, d, d]
+        L.orc_get_gpops.argtypes = [p, i, p]
+        L.orc_set_gpops.argtypes = [p, i, p]
     return _lib
 
 
@@ -228,6 +231,22 @@ class Oracle:
         t = None if T is None else _f64(np.broadcast_to(T, r.reshape(self.ny, self.nx).shape)).ravel()
         _check(lib().orc_init_equilibrium(self._h, _ptr(r), _ptr(a), _ptr(b),
                                           None if t is None else _ptr(t)), "init")
+
+    def set_twopop(self, cv: float, tau2: float):
+        """Two-population co-moving model of Sec. II.B (thermal co-moving
+        frame only; before init_equilibrium): C_v = cv, omega_2 = 1 / tau2."""
+        _check(lib().orc_set_twopop(self._h, float(cv), float(tau2)), "set_twopop")
+
+    def get_gpops(self, k: int) -> np.ndarray:
+        """g populations of lattice k, shape (ny, nx, Q_k), absolute units."""
+        out = np.zeros(self.nx * self.ny * self.Q[k])
+        _check(lib().orc_get_gpops(self._h, k, _ptr(out)), "get_gpops")
+        return out.reshape(self.ny, self.nx, self.Q[k])
+
+    def set_gpops(self, k: int, g):
+        g = _f64(g).ravel()
+        assert g.size == self.nx * self.ny * self.Q[k]
+        _check(lib().orc_set_gpops(self._h, k, _ptr(g)), "set_gpops")
 
     def set_pond(self, tol: float, maxit: int):
         """Predictor-corrector tolerance and iteration cap (co-moving frame)."""

@@ -35,6 +35,16 @@
  *     Two variants: thermal (single f population, C_v = D/2 so the g
  *     population of eq. (geqPond) vanishes identically) and isothermal
  *     (T held at T_L).
+ *   - The two-population co-moving model of Sec. II.B (orc_set_twopop): f
+ *     and g populations (eqs. Pond_f_equation, Pond_g_equation) with C_v
+ *     free (gamma = (C_v + 1) / C_v), the equilibria of eqs. (feqPond,
+ *     geqPond), the quasi-equilibria of eqs. (fqeq, gqeq) built from the
+ *     non-equilibrium third-order tensor and heat flux, relaxation omega_1
+ *     towards the equilibria and omega_1 - omega_2 of the quasi-equilibrium
+ *     correction; the total energy of eq. (E) with the g populations in the
+ *     predictor-corrector of eqs. (correctorfieldsrho-u); g transferred,
+ *     reconstructed (eq. reconstructionPondg), lifted and projected as f
+ *     (Sec. III.C), its lift completed by g^eq at the node's rho, u, T.
  *
  * Readings where the paper is silent (each also listed in the design notes):
  *   - "third-order Lagrange polynomials": p = order + 1 collocation points per
@@ -61,6 +71,10 @@
  *     collision conserves rho, rho u (and rho E when thermal) exactly.
  *     Lifting in a node's frame completes the moments with the equilibrium
  *     at the node vector's own rho, u, T (T_L when isothermal).
+ *   - Two-population model: the quasi-equilibria are formed in the co-moving
+ *     frame {u, T} of the reconstructed moments (theta = T, R = T_L = 1) with
+ *     the tensors taken from the populations in the frame used, and carried
+ *     into that frame by the transfer matrix, like the equilibria.
  *
  * Data layout (private to this file): populations of one cell contiguous,
  * f[k][cell * Q_k + i], cell = x + nx * y, i = ix + n * iy with the 1-D nodes
@@ -292,6 +306,29 @@ static void macro(const olat *L, const double lam[3], const double *f,
     *T = (e / r - (*ux) * (*ux) - (*uy) * (*uy)) / 2.0;
 }
 
+/* rho, u and T of an (f, g) pair in frame lam, two-population model: the
+ * conservation laws of Sec. II.B with rho E = sum v^2/2 f + sum g and
+ * eq. (E), rho E = C_v rho T + rho u^2 / 2.  g = NULL: no g population
+ * (C_v = D/2 = 1, the single-population thermal model, same as macro). */
+static void macro2(const olat *L, const double lam[3], const double *f, const double *g,
+                   double cv, double *rho, double *ux, double *uy, double *T)
+{
+    double st = sqrt(lam[2]);
+    double r = 0.0, jx = 0.0, jy = 0.0, e = 0.0;
+    for (int i = 0; i < L->Q; ++i) {
+        double vx = st * L->cx[i] + lam[0], vy = st * L->cy[i] + lam[1];
+        r += f[i];
+        jx += vx * f[i];
+        jy += vy * f[i];
+        e += 0.5 * (vx * vx + vy * vy) * f[i];
+        if (g) e += g[i];
+    }
+    *rho = r;
+    *ux = jx / r;
+    *uy = jy / r;
+    *T = (e / r - 0.5 * ((*ux) * (*ux) + (*uy) * (*uy))) / (g ? cv : 1.0);
+}
+
 /* -------------------------------------------------- lifting / projection */
 
 /* Lifting f_q -> f_Q in frame lam (Sec. III.B, App. C):
@@ -320,6 +357,31 @@ static int lift(const olat *Lq, const olat *LQ, const double lam[3], double T_fi
     }
     if (orc_invert(Q, MQ, MQi)) return -1;
     matvec(Q, MQi, M, fQ);                       /* eq. (liftingF) */
+    return 0;
+}
+
+/* Lifting of the g populations (Sec. III.C: the mappings apply to g as to
+ * f): the q x q moments of g_q kept, the others from g^eq = (C_v - 1) T rho W
+ * (eq. geqPond) at the node's rho, u, T (st = {rho, u_x, u_y, T}), expressed
+ * in frame lam. */
+static int lift_g(const olat *Lq, const olat *LQ, const double lam[3], const double st[4],
+                  double cv, const double *gq, double *gQ)
+{
+    int nq = Lq->n, nQ = LQ->n, Q = LQ->Q;
+    double Mq[ORC_MAXQ * ORC_MAXQ], MQ[ORC_MAXQ * ORC_MAXQ], MQi[ORC_MAXQ * ORC_MAXQ];
+    double mq[ORC_MAXQ], geqQ[ORC_MAXQ], Meq[ORC_MAXQ], M[ORC_MAXQ];
+    moment_matrix(Lq, lam, Mq);
+    matvec(Lq->Q, Mq, gq, mq);
+    if (feq_in_frame(LQ, st[0], st[1], st[2], st[3], lam, geqQ)) return -1;
+    for (int i = 0; i < Q; ++i) geqQ[i] *= (cv - 1.0) * st[3];
+    moment_matrix(LQ, lam, MQ);
+    matvec(Q, MQ, geqQ, Meq);
+    for (int r = 0; r < Q; ++r) {
+        int a = r % nQ, b = r / nQ;
+        M[r] = (a < nq && b < nq) ? mq[a + nq * b] : Meq[r];
+    }
+    if (orc_invert(Q, MQ, MQi)) return -1;
+    matvec(Q, MQi, M, gQ);
     return 0;
 }
 
@@ -410,6 +472,12 @@ typedef struct {
     uint8_t *have[2];
     double Minv_lat[2][ORC_MAXQ * ORC_MAXQ];
     long steps;
+    /* two-population co-moving model (orc_set_twopop): g populations of
+     * eq. (Pond_g_equation) in absolute energy units, same layout as f */
+    int twopop;
+    double cv, omega2;           /* C_v (R = 1) and omega_2 */
+    double *g[2], *gmemo[2], *gmom[2];
+    uint8_t *ghave[2], *ghmom[2];
 } orc_t;
 
 static long cidx(const orc_t *s, long x, long y) { return x + (long)s->nx * y; }
@@ -474,6 +542,7 @@ void orc_destroy(orc_t *s)
     if (!s) return;
     for (int k = 0; k < 2; ++k) {
         free(s->f[k]); free(s->memo[k]); free(s->have[k]); free(s->mom[k]); free(s->hmom[k]);
+        free(s->g[k]); free(s->gmemo[k]); free(s->ghave[k]); free(s->gmom[k]); free(s->ghmom[k]);
     }
     free(s->lam);
     for (int b = 0; b < 4; ++b) { free(s->bc[b].rho); free(s->bc[b].ux); free(s->bc[b].uy); }
@@ -516,6 +585,31 @@ static void convert(const orc_t *s, int from, int to, const double *lam, const d
     else project(&s->L[1], &s->L[0], lam, src, dst);
 }
 
+/* rho, u_x, u_y, T of cell c from its native f (and g) in its own frame. */
+static void node_state(const orc_t *s, long c, double st[4])
+{
+    int k = s->flag[c];
+    const olat *L = &s->L[k];
+    macro2(L, s->lam + 3 * c, s->f[k] + c * L->Q, s->twopop ? s->g[k] + c * L->Q : NULL, s->cv,
+           &st[0], &st[1], &st[2], &st[3]);
+}
+
+/* Two-population model: cell c's f (which = 0) or g (which = 1) vector in
+ * lattice `to`, converted in the cell's frame; a lift completes with the
+ * equilibrium at the cell's rho, u, T (T from f and g). */
+static int convert2(const orc_t *s, long c, int to, int which, double *dst)
+{
+    int from = s->flag[c];
+    const double *lam = s->lam + 3 * c;
+    const double *src = (which ? s->g[from] : s->f[from]) + c * s->L[from].Q;
+    if (from == to) { memcpy(dst, src, sizeof(double) * s->L[to].Q); return 0; }
+    if (from == 1) return project(&s->L[1], &s->L[0], lam, src, dst);
+    double st[4];
+    node_state(s, c, st);
+    if (!which) return lift(&s->L[0], &s->L[1], lam, st[3], src, dst);
+    return lift_g(&s->L[0], &s->L[1], lam, st, s->cv, src, dst);
+}
+
 /* Every cell starts at the equilibrium of both lattices (both representations
  * valid), flags 0.  Lattice frame: f^L at (rho, u), T must be NULL (athermal).
  * Co-moving frame: f = rho W_i in the frame {u, T} (eq. feqPond), T = T_L when
@@ -531,7 +625,11 @@ int orc_init_equilibrium(orc_t *s, const double *rho, const double *ux, const do
             if (s->frame == 0) {
                 eq_lat(s, k, rho[c], ux[c], uy[c], f);
             } else {
+                double Tc = T ? T[c] : 1.0;
                 for (int i = 0; i < s->L[k].Q; ++i) f[i] = rho[c] * s->L[k].W[i];
+                if (s->twopop)                       /* eq. (geqPond) in the cell's frame */
+                    for (int i = 0; i < s->L[k].Q; ++i)
+                        s->g[k][c * s->L[k].Q + i] = (s->cv - 1.0) * Tc * rho[c] * s->L[k].W[i];
                 s->lam[3 * c] = ux[c];
                 s->lam[3 * c + 1] = uy[c];
                 s->lam[3 * c + 2] = T ? T[c] : 1.0;
@@ -548,8 +646,13 @@ int orc_set_flags(orc_t *s, const uint8_t *fl)
     for (long c = 0; c < nc; ++c) {
         int nf = fl[c] ? 1 : 0;
         if (nf != s->flag[c]) {
-            convert(s, s->flag[c], nf, cell_frame(s, c), s->f[s->flag[c]] + c * s->L[s->flag[c]].Q,
-                    s->f[nf] + c * s->L[nf].Q);
+            if (s->twopop) {
+                convert2(s, c, nf, 0, s->f[nf] + c * s->L[nf].Q);
+                convert2(s, c, nf, 1, s->g[nf] + c * s->L[nf].Q);
+            } else {
+                convert(s, s->flag[c], nf, cell_frame(s, c), s->f[s->flag[c]] + c * s->L[s->flag[c]].Q,
+                        s->f[nf] + c * s->L[nf].Q);
+            }
             s->flag[c] = (uint8_t)nf;
         }
     }
@@ -652,8 +755,11 @@ static const double *node_vec(orc_t *s, long gx, long gy, int k)
         long c = cidx(s, gx, gy);
         if (s->flag[c] == k) return s->f[k] + c * Q;        /* native */
         if (!s->have[k][m]) {
-            convert(s, s->flag[c], k, cell_frame(s, c), s->f[s->flag[c]] + c * s->L[s->flag[c]].Q,
-                    out);
+            if (s->twopop)
+                convert2(s, c, k, 0, out);
+            else
+                convert(s, s->flag[c], k, cell_frame(s, c), s->f[s->flag[c]] + c * s->L[s->flag[c]].Q,
+                        out);
             s->have[k][m] = 1;
         }
         return out;
@@ -746,6 +852,95 @@ static const double *node_moments(orc_t *s, long gx, long gy, int k)
     return m;
 }
 
+/* g vector of node (gx, gy) in lattice k (two-population model; co-moving
+ * grids are periodic) and its moments in the node's frame, memoised per step. */
+static const double *node_vec_g(orc_t *s, long gx, long gy, int k)
+{
+    gx = ((gx % s->nx) + s->nx) % s->nx;
+    gy = ((gy % s->ny) + s->ny) % s->ny;
+    long c = cidx(s, gx, gy);
+    int Q = s->L[k].Q;
+    if (s->flag[c] == k) return s->g[k] + c * Q;
+    double *out = s->gmemo[k] + c * Q;
+    if (!s->ghave[k][c]) {
+        convert2(s, c, k, 1, out);
+        s->ghave[k][c] = 1;
+    }
+    return out;
+}
+
+static const double *node_moments_g(orc_t *s, long gx, long gy, int k)
+{
+    gx = ((gx % s->nx) + s->nx) % s->nx;
+    gy = ((gy % s->ny) + s->ny) % s->ny;
+    long c = cidx(s, gx, gy);
+    int Q = s->L[k].Q;
+    double *m = s->gmom[k] + c * Q;
+    if (!s->ghmom[k][c]) {
+        double M[ORC_MAXQ * ORC_MAXQ];
+        moment_matrix(&s->L[k], cell_frame(s, c), M);
+        matvec(Q, M, node_vec_g(s, gx, gy, k), m);
+        s->ghmom[k][c] = 1;
+    }
+    return m;
+}
+
+/* Two-population collision (eqs. Pond_f_equation, Pond_g_equation) of the
+ * reconstructed fbar, gbar living in frame lam, at their moments rho, u, T:
+ * equilibria of eqs. (feqPond, geqPond) and quasi-equilibria of eqs. (fqeq,
+ * gqeq) formed in the co-moving frame {u, T} (theta = T with R = T_L = 1) and
+ * carried into lam; the tensors Qbar (third-order, of f - f^eq) and qbar (of
+ * g - g^eq) are taken with the velocities v_i - u of frame lam. */
+static int collide2(const orc_t *s, const olat *L, const double lam[3], double rho, double ux,
+                    double uy, double T, const double *fbar, const double *gbar, double *fout,
+                    double *gout)
+{
+    int Q = L->Q;
+    double feq[ORC_MAXQ], geq[ORC_MAXQ], df[ORC_MAXQ], dg[ORC_MAXQ], tf[ORC_MAXQ], tg[ORC_MAXQ];
+    double G[ORC_MAXQ * ORC_MAXQ], own[3] = {ux, uy, T};
+    if (feq_in_frame(L, rho, ux, uy, T, lam, feq)) return -1;
+    for (int i = 0; i < Q; ++i) geq[i] = (s->cv - 1.0) * T * feq[i];
+    /* Qbar_abc = sum (v-u)_a (v-u)_b (v-u)_c (f - f^eq), qbar_a = sum (v-u)_a (g - g^eq) */
+    double st = sqrt(lam[2]);
+    double Qb[2][2][2] = {{{0}}}, qb[2] = {0.0, 0.0};
+    for (int i = 0; i < Q; ++i) {
+        double w[2] = {st * L->cx[i] + lam[0] - ux, st * L->cy[i] + lam[1] - uy};
+        double nf = fbar[i] - feq[i], ng = gbar[i] - geq[i];
+        for (int a = 0; a < 2; ++a) {
+            qb[a] += w[a] * ng;
+            for (int b = 0; b < 2; ++b)
+                for (int c = 0; c < 2; ++c) Qb[a][b][c] += w[a] * w[b] * w[c] * nf;
+        }
+    }
+    /* eq. (fqeq): W_i Qbar:(theta^{3/2} c c c - R T theta^{1/2} sym(c (x) 1)) / (6 (RT)^3);
+     * eq. (gqeq): W_i theta^{1/2} qbar.c / (R T); in the co-moving frame {u, T} */
+    double th = T, RT = T;
+    for (int i = 0; i < Q; ++i) {
+        double c[2] = {L->cx[i], L->cy[i]};
+        double ccc = 0.0, sym = 0.0, qc = 0.0;
+        for (int a = 0; a < 2; ++a) {
+            qc += qb[a] * c[a];
+            for (int b = 0; b < 2; ++b)
+                for (int e = 0; e < 2; ++e) {
+                    ccc += Qb[a][b][e] * c[a] * c[b] * c[e];
+                    /* sym(c (x) 1)_abe = c_a d_be + c_b d_ae + c_e d_ab */
+                    sym += Qb[a][b][e] * (c[a] * (b == e) + c[b] * (a == e) + c[e] * (a == b));
+                }
+        }
+        df[i] = L->W[i] * (pow(th, 1.5) * ccc - RT * sqrt(th) * sym) / (6.0 * RT * RT * RT);
+        dg[i] = L->W[i] * sqrt(th) * qc / RT;
+    }
+    if (transfer(L, own, lam, G)) return -1;
+    matvec(Q, G, df, tf);                        /* f* - f^eq in frame lam */
+    matvec(Q, G, dg, tg);
+    double w1 = s->omega, w2 = s->omega2;
+    for (int i = 0; i < Q; ++i) {
+        fout[i] = fbar[i] + w1 * (feq[i] - fbar[i]) + (w1 - w2) * tf[i];
+        gout[i] = gbar[i] + w1 * (geq[i] - gbar[i]) + (w1 - w2) * tg[i];
+    }
+    return 0;
+}
+
 /* One co-moving-frame update of cell (x, y), Sec. II.C.
  * Predictor: the cell's frame of the previous step.  Each pass reconstructs
  * every population at its departure point x - v_i dt, v_i = sqrt(theta) c_i + u
@@ -756,14 +951,15 @@ static const double *node_moments(orc_t *s, long gx, long gy, int k)
  * agree with it to tol.  Then BGK (eq. Pond_f_equation, omega_1 = omega_2)
  * towards the equilibrium at those moments expressed in lam.  Writes Q values
  * to out and the frame they live in to lam_out. */
-static int update_cell_pond(orc_t *s, long x, long y, double *out, double *lam_out)
+static int update_cell_pond(orc_t *s, long x, long y, double *out, double *gout,
+                            double *lam_out)
 {
     long c = cidx(s, x, y);
     int k = s->flag[c];
     const olat *L = &s->L[k];
     int p = s->p, Q = L->Q;
     double lam[3], nl[3] = {0.0, 0.0, 1.0}, rho = 0.0;
-    double fbar[ORC_MAXQ], feq[ORC_MAXQ], ax[8], ay[8];
+    double fbar[ORC_MAXQ], gbar[ORC_MAXQ], feq[ORC_MAXQ], ax[8], ay[8];
     double Mt[ORC_MAXQ * ORC_MAXQ], Mti[ORC_MAXQ * ORC_MAXQ];
     int converged = 0;
     memcpy(lam, s->lam + 3 * c, sizeof(lam));
@@ -777,18 +973,25 @@ static int update_cell_pond(orc_t *s, long x, long y, double *out, double *lam_o
             long x0 = orc_first_node(p, xd), y0 = orc_first_node(p, yd);
             orc_lagrange(p, xd, x0, ax);
             orc_lagrange(p, yd, y0, ay);
-            double acc = 0.0;
+            double acc = 0.0, gacc = 0.0;
             for (int t = 0; t < p; ++t)
                 for (int u = 0; u < p; ++u) {
                     const double *m = node_moments(s, x0 + u, y0 + t, k);
                     double gi = 0.0;                      /* (G_{lambda_s}^{lam} f_s)_i */
                     for (int r = 0; r < Q; ++r) gi += Mti[i * Q + r] * m[r];
                     acc += ax[u] * ay[t] * gi;
+                    if (s->twopop) {                      /* eq. (reconstructionPondg) */
+                        const double *mg = node_moments_g(s, x0 + u, y0 + t, k);
+                        double hi = 0.0;
+                        for (int r = 0; r < Q; ++r) hi += Mti[i * Q + r] * mg[r];
+                        gacc += ax[u] * ay[t] * hi;
+                    }
                 }
             fbar[i] = acc;
+            gbar[i] = gacc;
         }
         double ux, uy, T;
-        macro(L, lam, fbar, &rho, &ux, &uy, &T);
+        macro2(L, lam, fbar, s->twopop ? gbar : NULL, s->cv, &rho, &ux, &uy, &T);
         if (s->frame == 2) T = 1.0;
         nl[0] = ux; nl[1] = uy; nl[2] = T;
         double d = fmax(fabs(ux - lam[0]), fmax(fabs(uy - lam[1]), fabs(T - lam[2])));
@@ -796,8 +999,12 @@ static int update_cell_pond(orc_t *s, long x, long y, double *out, double *lam_o
         if (it + 1 < s->maxit) memcpy(lam, nl, sizeof(lam));
     }
     if (!converged) s->nonconv++;
-    if (feq_in_frame(L, rho, nl[0], nl[1], nl[2], lam, feq)) return -1;
-    for (int i = 0; i < Q; ++i) out[i] = fbar[i] + s->omega * (feq[i] - fbar[i]);
+    if (s->twopop) {
+        if (collide2(s, L, lam, rho, nl[0], nl[1], nl[2], fbar, gbar, out, gout)) return -1;
+    } else {
+        if (feq_in_frame(L, rho, nl[0], nl[1], nl[2], lam, feq)) return -1;
+        for (int i = 0; i < Q; ++i) out[i] = fbar[i] + s->omega * (feq[i] - fbar[i]);
+    }
     memcpy(lam_out, lam, sizeof(lam));
     return 0;
 }
@@ -807,6 +1014,8 @@ static void reset_memo(orc_t *s)
     for (int k = 0; k < 2; ++k) {
         memset(s->have[k], 0, (size_t)s->px * s->py);
         if (s->hmom[k]) memset(s->hmom[k], 0, (size_t)s->nx * s->ny);
+        if (s->ghave[k]) memset(s->ghave[k], 0, (size_t)s->nx * s->ny);
+        if (s->ghmom[k]) memset(s->ghmom[k], 0, (size_t)s->nx * s->ny);
     }
 }
 
@@ -814,11 +1023,15 @@ static void reset_memo(orc_t *s)
 int orc_step(orc_t *s, int n)
 {
     long nc = (long)s->nx * s->ny;
-    double *g[2] = {NULL, NULL}, *glam = NULL;
+    double *g[2] = {NULL, NULL}, *gg[2] = {NULL, NULL}, *glam = NULL;
     int rc = 0;
     for (int k = 0; k < 2; ++k) {
         g[k] = (double *)malloc(sizeof(double) * nc * s->L[k].Q);
         if (!g[k]) rc = -1;
+        if (s->twopop) {                         /* next-step g populations */
+            gg[k] = (double *)calloc(nc * s->L[k].Q, sizeof(double));
+            if (!gg[k]) rc = -1;
+        }
     }
     if (s->frame && !(glam = (double *)malloc(sizeof(double) * 3 * nc))) rc = -1;
     for (int it = 0; it < n && rc == 0; ++it) {
@@ -829,7 +1042,9 @@ int orc_step(orc_t *s, int n)
                 int k = s->flag[c];
                 if (s->frame == 0) {
                     update_cell(s, x, y, g[k] + c * s->L[k].Q);
-                } else if (update_cell_pond(s, x, y, g[k] + c * s->L[k].Q, glam + 3 * c)) {
+                } else if (update_cell_pond(s, x, y, g[k] + c * s->L[k].Q,
+                                            s->twopop ? gg[k] + c * s->L[k].Q : NULL,
+                                            glam + 3 * c)) {
                     rc = -1;
                     break;
                 }
@@ -837,6 +1052,7 @@ int orc_step(orc_t *s, int n)
         if (rc) break;
         for (int k = 0; k < 2; ++k) {
             double *t = s->f[k]; s->f[k] = g[k]; g[k] = t;
+            if (s->twopop) { t = s->g[k]; s->g[k] = gg[k]; gg[k] = t; }
         }
         if (s->frame) { double *t = s->lam; s->lam = glam; glam = t; }
         if (s->crit_kind == 1) apply_criterion(s);   /* flags for the next step */
@@ -844,6 +1060,8 @@ int orc_step(orc_t *s, int n)
     }
     free(g[0]);
     free(g[1]);
+    free(gg[0]);
+    free(gg[1]);
     free(glam);
     return rc;
 }
@@ -861,8 +1079,9 @@ int orc_step_cells(orc_t *s, int m, const long *cells, double *out, double *lam_
         if (s->frame == 0) {
             update_cell(s, c % s->nx, c / s->nx, out + (long)j * ORC_MAXQ);
         } else {
-            double lam[3];
-            if (update_cell_pond(s, c % s->nx, c / s->nx, out + (long)j * ORC_MAXQ, lam)) return -1;
+            double lam[3], gtmp[ORC_MAXQ];
+            if (update_cell_pond(s, c % s->nx, c / s->nx, out + (long)j * ORC_MAXQ, gtmp, lam))
+                return -1;
             if (lam_out) memcpy(lam_out + 3 * j, lam, sizeof(lam));
         }
     }
@@ -904,22 +1123,25 @@ int orc_set_frame(orc_t *s, const double *ux, const double *uy, const double *T)
     return 0;
 }
 
-/* rho, u and kinetic T of every cell from its native populations. */
+/* rho, u and T of every cell from its native populations (kinetic T, or with
+ * the g populations and C_v in the two-population model). */
 int orc_moments(const orc_t *s, double *rho, double *ux, double *uy, double *T)
 {
     long nc = (long)s->nx * s->ny;
     for (long c = 0; c < nc; ++c) {
         int k = s->flag[c];
         double r, a, b, t;
-        macro(&s->L[k], cell_frame(s, c), s->f[k] + c * s->L[k].Q, &r, &a, &b, &t);
+        macro2(&s->L[k], cell_frame(s, c), s->f[k] + c * s->L[k].Q,
+               s->twopop ? s->g[k] + c * s->L[k].Q : NULL, s->cv, &r, &a, &b, &t);
         rho[c] = r; ux[c] = a; uy[c] = b;
         if (T) T[c] = t;
     }
     return 0;
 }
 
-/* Global sums rho, rho u_x, rho u_y, rho E with E = sum v^2/2 f / rho and
- * v_i = sqrt(theta) c_i + u of the frame each cell's populations live in. */
+/* Global sums rho, rho u_x, rho u_y, rho E with rho E = sum v^2/2 f (+ sum g
+ * in the two-population model) and v_i = sqrt(theta) c_i + u of the frame
+ * each cell's populations live in. */
 int orc_audit(const orc_t *s, double out[4])
 {
     long nc = (long)s->nx * s->ny;
@@ -936,6 +1158,7 @@ int orc_audit(const orc_t *s, double out[4])
             a[1] += vx * f;
             a[2] += vy * f;
             a[3] += 0.5 * (vx * vx + vy * vy) * f;
+            if (s->twopop) a[3] += s->g[k][c * L->Q + i];
         }
     }
     memcpy(out, a, sizeof(a));
@@ -952,5 +1175,42 @@ int orc_get_pops(const orc_t *s, int k, double *out)
 int orc_set_pops(orc_t *s, int k, const double *in)
 {
     memcpy(s->f[k], in, sizeof(double) * (size_t)s->nx * s->ny * s->L[k].Q);
+    return 0;
+}
+
+/* Switch the thermal co-moving model to the two-population model of
+ * Sec. II.B with C_v = cv (gamma = (cv + 1) / cv, R = 1) and omega_2 =
+ * 1 / tau2 (Pr = (tau - 1/2) / (tau2 - 1/2)).  Call before
+ * orc_init_equilibrium, which then sets g = g^eq of eq. (geqPond). */
+int orc_set_twopop(orc_t *s, double cv, double tau2)
+{
+    if (s->frame != 1 || !(cv > 0.0) || !(tau2 > 0.5) || s->twopop) return -1;
+    long nc = (long)s->nx * s->ny;
+    for (int k = 0; k < 2; ++k) {
+        size_t n = (size_t)nc * s->L[k].Q;
+        s->g[k] = (double *)calloc(n, sizeof(double));
+        s->gmemo[k] = (double *)calloc(n, sizeof(double));
+        s->gmom[k] = (double *)calloc(n, sizeof(double));
+        s->ghave[k] = (uint8_t *)calloc(nc, 1);
+        s->ghmom[k] = (uint8_t *)calloc(nc, 1);
+        if (!s->g[k] || !s->gmemo[k] || !s->gmom[k] || !s->ghave[k] || !s->ghmom[k]) return -1;
+    }
+    s->twopop = 1;
+    s->cv = cv;
+    s->omega2 = 1.0 / tau2;
+    return 0;
+}
+
+int orc_get_gpops(const orc_t *s, int k, double *out)
+{
+    if (!s->twopop) return -1;
+    memcpy(out, s->g[k], sizeof(double) * (size_t)s->nx * s->ny * s->L[k].Q);
+    return 0;
+}
+
+int orc_set_gpops(orc_t *s, int k, const double *in)
+{
+    if (!s->twopop) return -1;
+    memcpy(s->g[k], in, sizeof(double) * (size_t)s->nx * s->ny * s->L[k].Q);
     return 0;
 }

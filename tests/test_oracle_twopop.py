@@ -1,0 +1,211 @@
+"""Pins of the oracle's two-population co-moving model (Sec. II.B, eqs.
+Pond_f_equation / Pond_g_equation, feqPond / geqPond, fqeq / gqeq).
+
+No worked example is printed for it; the pins are what the model's
+definitions fix:
+- with C_v = D/2 = 1, omega_2 = omega_1 and g = 0 it is the single-population
+  thermal model, step for step;
+- a uniform state at rest in its own frame (f = rho W_i, g = (C_v - 1) T rho
+  W_i) is a fixed point, mixed lattices too;
+- in a uniform state the step is the collision alone, so a non-equilibrium
+  part that is a pure third-order Hermite term of f, or a first-order term of
+  g (the heat flux), relaxes by 1 - omega_2 per step, while a second-order
+  term of f (stress) or of g relaxes by 1 - omega_1: the quasi-equilibria
+  carry exactly the non-equilibrium third moment of f and first moment of g;
+- sound travels at sqrt(gamma T), gamma = (C_v + 1) / C_v;
+- an entropy wave (T perturbed at constant pressure) decays with the thermal
+  diffusivity kappa / (rho C_p) = (1/omega_2 - 1/2) T dt and a shear wave with
+  the kinematic viscosity (1/omega_1 - 1/2) T dt, so Pr = C_p mu / kappa
+  follows from the two relaxation times;
+- discrete Galilean invariance (a boost of one cell per step).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2102_12559_gb300 import workloads as WL
+
+
+def state(o):
+    fl = o.get_flags()
+    out = []
+    for k in (0, 1):
+        m = (fl == k)[..., None]
+        out.append(np.where(m, o.get_pops(k), 0.0))
+        if o_twopop(o):
+            out.append(np.where(m, o.get_gpops(k), 0.0))
+    return out
+
+
+def o_twopop(o):
+    return getattr(o, "_twopop", False)
+
+
+def make(nx, ny, lo, hi, tau, cv=None, tau2=None):
+    o = O.Oracle(nx, ny, lo, hi, tau=tau, frame=O.FRAME_POND)
+    if cv is not None:
+        o.set_twopop(cv, tau2)
+        o._twopop = True
+    return o
+
+
+def test_reduces_to_the_single_population_model():
+    nx, ny = 16, 8
+    r, u, v = WL.perturbed(nx, ny, seed=3, amp_rho=0.05, amp_u=0.2, U=(0.3, 0.1))
+    T = WL.perturbed_T(nx, ny, seed=4, amp=0.05)
+    fl = np.zeros((ny, nx), np.uint8)
+    fl[2:6, 4:9] = 1
+    runs = []
+    for two in (False, True):
+        o = make(nx, ny, 4, 5, 0.7, *((1.0, 0.7) if two else (None, None)))
+        o.init_equilibrium(r, u, v, T)
+        o.set_flags(fl)
+        o.step(3)
+        runs.append(o)
+    a, b = runs
+    for k in (0, 1):
+        m = (fl == k)[..., None]
+        assert np.abs(np.where(m, a.get_pops(k) - b.get_pops(k), 0)).max() < 1e-13
+        assert np.abs(np.where(m, b.get_gpops(k), 0)).max() < 1e-13      # g stays 0
+    np.testing.assert_allclose(a.audit(), b.audit(), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("lo,hi", [(3, 5), (4, 5)])
+def test_uniform_state_in_its_own_frame_is_steady(lo, hi):
+    nx, ny = 12, 8
+    o = make(nx, ny, lo, hi, 0.7, 1.5, 0.9)
+    one = np.ones((ny, nx))
+    o.init_equilibrium(1.2 * one, 0.4 * one, -0.2 * one, 1.3 * one)
+    fl = np.zeros((ny, nx), np.uint8)
+    fl[2:6, 3:8] = 1
+    o.set_flags(fl)
+    before = state(o)
+    o.step(3)
+    for x, y in zip(before, state(o)):
+        assert np.abs(x - y).max() < 1e-13
+    ux, uy, t = o.get_frame()
+    assert np.abs(ux - 0.4).max() < 1e-13 and np.abs(uy + 0.2).max() < 1e-13
+    assert np.abs(t - 1.3).max() < 1e-13
+    # g^eq of eq. (geqPond): (C_v - 1) T rho W_i
+    W = O.lattice(lo)[2]
+    g0 = o.get_gpops(0)[fl == 0]
+    np.testing.assert_allclose(g0, np.broadcast_to(0.5 * 1.3 * 1.2 * W, g0.shape), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("n", [4, 5])
+def test_quasi_equilibria_set_the_relaxation_rates(n):
+    """Uniform state in frame u = (0.3, -0.2), T = 1.2 with one Hermite
+    non-equilibrium term at a time; one step multiplies it by 1 - omega_2
+    (third order of f, first order of g) or 1 - omega_1 (second order)."""
+    nx, ny, tau, tau2, cv = 4, 4, 0.7, 1.1, 1.5
+    w1, w2 = 1 / tau, 1 / tau2
+    cx, cy, W = O.lattice(n)
+    one = np.ones((ny, nx))
+    rho, T = 1.1, 1.2
+    cases = [
+        ("f", W * (cx ** 3 - 3 * cx), 1 - w2),          # He3_xxx
+        ("f", W * (cx ** 2 * cy - cy), 1 - w2),         # He3_xxy
+        ("f", W * cx * cy, 1 - w1),                     # He2_xy
+        ("f", W * (cx ** 2 - cy ** 2), 1 - w1),         # normal stress
+        ("g", W * cy, 1 - w2),                          # heat flux of g
+        ("g", W * (cx ** 2 - 1), 1 - w1),
+    ]
+    for which, d, ratio in cases:
+        k = 0 if n == 4 else 1                      # D2Q16 / D2Q25 of the pair (4, 5)
+        o = make(nx, ny, 4, 5, tau, cv, tau2)
+        o.init_equilibrium(rho * one, 0.3 * one, -0.2 * one, T * one)
+        if k:
+            o.set_flags(np.ones((ny, nx), np.uint8))
+        eps = 1e-3
+        f = o.get_pops(k)
+        g = o.get_gpops(k)
+        feq, geq = f.copy(), g.copy()
+        if which == "f":
+            o.set_pops(k, f + eps * d)
+        else:
+            o.set_gpops(k, g + eps * T * d)
+        o.step(1)
+        got = (o.get_pops(k) - feq) if which == "f" else (o.get_gpops(k) - geq)
+        want = ratio * eps * (d if which == "f" else T * d)
+        np.testing.assert_allclose(got, np.broadcast_to(want, got.shape), rtol=0, atol=1e-13)
+        other = (o.get_gpops(k) - geq) if which == "f" else (o.get_pops(k) - feq)
+        assert np.abs(other).max() < 1e-13
+
+
+def decay(kind, tau, tau2, cv=1.5, n=4, nx=32, steps=240):
+    """Fourier amplitude of T (entropy wave at constant pressure) or of u_y
+    (shear wave) against time; returns the fitted decay rate / k^2."""
+    ny, A = 2, 1e-3
+    x = np.arange(nx)[None, :].repeat(ny, 0)
+    kk = 2 * np.pi / nx
+    z = np.zeros((ny, nx))
+    if kind == "entropy":
+        T = 1 + A * np.cos(kk * x)
+        rho, uy = 1.0 / T, z
+    else:
+        T, rho, uy = 1 + z, 1 + z, A * np.cos(kk * x)
+    o = make(nx, ny, n, 5, tau, cv, tau2)
+    o.init_equilibrium(rho, z, uy, T)
+    ts, ys = [], []
+    for s in range(steps):
+        m = o.moments()
+        sig = m[3][0] - 1 if kind == "entropy" else m[2][0]
+        ts.append(s * o.dt)
+        ys.append(np.sum(sig * np.cos(kk * np.arange(nx))) * 2 / nx)
+        o.step(1)
+    ts, ys = np.array(ts), np.array(ys)
+    lam = -np.polyfit(ts[20:], np.log(np.abs(ys[20:])), 1)[0]
+    return lam / kk ** 2, o.dt
+
+
+def test_thermal_diffusivity_and_prandtl_number():
+    tau, tau2 = 0.8, 1.3
+    alpha, dt = decay("entropy", tau, tau2)
+    nu, _ = decay("shear", tau, tau2)
+    assert abs(alpha / ((tau2 - 0.5) * dt) - 1) < 0.03
+    assert abs(nu / ((tau - 0.5) * dt) - 1) < 0.03
+    cv = 1.5
+    pr = (cv + 1) * nu / ((cv + 1) * alpha)                 # C_p mu / kappa with rho = T = 1
+    assert abs(pr / ((tau - 0.5) / (tau2 - 0.5)) - 1) < 0.05
+
+
+@pytest.mark.parametrize("cv", [1.5, 2.5])
+def test_sound_speed_gamma(cv):
+    gamma = (cv + 1) / cv
+    nx, ny, A = 32, 2, 1e-3
+    x = np.arange(nx)[None, :].repeat(ny, 0)
+    kk = 2 * np.pi / nx
+    rho = 1 + A * np.cos(kk * x)
+    T = 1 + (gamma - 1) * A * np.cos(kk * x)                # adiabatic
+    z = np.zeros_like(rho)
+    o = make(nx, ny, 4, 5, 0.51, cv, 0.51)
+    o.init_equilibrium(rho, z, z, T)
+    c_guess = np.sqrt(gamma)
+    ts, ys = [], []
+    for s in range(int(1.1 * nx / c_guess / o.dt)):
+        r = o.moments()[0]
+        ts.append(s * o.dt)
+        ys.append(np.sum((r[0] - 1) * np.cos(kk * np.arange(nx))) * 2 / nx)
+        o.step(1)
+    from scipy.optimize import curve_fit
+    f = lambda t, a, g, w: a * np.exp(-g * t) * np.cos(w * t)
+    p, _ = curve_fit(f, np.array(ts), np.array(ys), p0=[A, 0.0, kk * c_guess])
+    assert abs(p[2] / kk / c_guess - 1) < 2e-3
+
+
+def test_galilean_boost_by_one_cell_per_step():
+    nx, ny, steps = 16, 8, 2
+    xg, yg = np.meshgrid(np.arange(nx), np.arange(ny))
+    ux = 0.05 * np.sin(2 * np.pi * yg / ny + 0.3)
+    uy = 0.04 * np.sin(2 * np.pi * xg / nx + 1.0)
+    rho = 1 + 0.02 * np.cos(2 * np.pi * (xg / nx + yg / ny))
+    T = 1 + 0.05 * np.sin(2 * np.pi * xg / nx)
+    runs = []
+    for U in (0.0, 1.0):
+        o = make(nx, ny, 4, 5, 0.7, 1.5, 0.9)
+        o.init_equilibrium(rho, ux + U / o.dt, uy, T)
+        o.step(steps)
+        runs.append(o)
+    a, b = runs
+    for get in (lambda o: o.get_pops(0), lambda o: o.get_gpops(0)):
+        np.testing.assert_allclose(get(b), np.roll(get(a), steps, axis=1), rtol=0, atol=5e-12)
