@@ -276,6 +276,29 @@ SLBM_API int slbm_set_pond(slbm_t h, double tol, int max_iter);
 SLBM_API int slbm_get_frame(slbm_t h, double *ux, double *uy, double *T);
 SLBM_API int slbm_set_frame(slbm_t h, const double *ux, const double *uy, const double *T);
 
+/* Two-population co-moving model (Sec. II.B, eqs. Pond_f_equation and
+ * Pond_g_equation; SLBM_FRAME_POND handles only, else SLBM_EINVAL).
+ *
+ * slbm_set_twopop: switch the thermal co-moving model to f and g populations
+ * with specific heat C_v = cv > 0 (R = 1, so gamma = (cv + 1) / cv and
+ * C_v = 1 with g = 0 is the single-population model) and the second
+ * relaxation time tau2 > 1/2 (omega_2 = 1 / tau2 relaxes the quasi-equilibria
+ * of eqs. fqeq / gqeq, so the Prandtl number is (tau - 1/2) / (tau2 - 1/2)).
+ * Allocates device memory for the g planes of both lattices and buffers
+ * (owned by the handle, freed by slbm_destroy); once per handle, before
+ * slbm_init_equilibrium, which then sets g = (C_v - 1) T rho W_i (eq. geqPond)
+ * in each cell's frame.  T from slbm_moments and the energy of slbm_audit
+ * include the g populations.  slbm_get_state / slbm_set_state do not carry
+ * the g planes.
+ *
+ * slbm_get_gpops / slbm_set_gpops: the g populations of lattice k in the
+ * frame each cell's populations live in, absolute units, host doubles in the
+ * layout of slbm_get_pops (plane-major: g_i of cell c at [i * nx*ny + c]).
+ * Writing recomputes the interface cells' other lattice, as slbm_set_pops. */
+SLBM_API int slbm_set_twopop(slbm_t h, double cv, double tau2);
+SLBM_API int slbm_get_gpops(slbm_t h, int k, double *out);
+SLBM_API int slbm_set_gpops(slbm_t h, int k, const double *in);
+
 /* Per-kernel timing (tracing).  slbm_profile(h, 1) clears previous records
  * and starts bracketing every kernel slbm_step launches with CUDA events on
  * the handle's stream; slbm_profile(h, 0) stops.  slbm_profile_read()

@@ -285,6 +285,11 @@ struct slbm_s {
   double pond_tol;
   int pond_maxit;
   int pond_mixed;                // both lattices present (interface conversions per step)
+  // two-population co-moving model (slbm_set_twopop): C_v, tau_2 and the g
+  // planes of both buffers and lattices, laid out like the f planes (owned)
+  int twopop;
+  double cv, tau2;
+  char* gbuf;
   Layout lay;
   cudaStream_t st;
   char* ws;
@@ -323,6 +328,13 @@ struct slbm_s {
   void* pops(int buf, int k) { return ws + lay.pops[buf][k]; }
   uint8_t* flags(int f) { return at<uint8_t>(lay.flags[f]); }
   void* lam(int buf) { return ws + lay.lam[buf]; }
+  // g planes of buffer buf, lattice k (null without the two-population model)
+  void* gp(int buf, int k) {
+    if (!twopop) return nullptr;
+    const size_t es = precision == SLBM_FP64 ? 8 : 4;
+    const size_t q = (size_t)(nlo * nlo + nhi * nhi);
+    return gbuf + es * (size_t)lay.plane * ((size_t)buf * q + (k ? (size_t)(nlo * nlo) : 0));
+  }
   size_t ncell() const { return (size_t)g.nx * g.ny; }
 };
 
@@ -510,11 +522,13 @@ int pond_convert_band(slbm_s* h, int buf) {
   cudaError_t e =
       h->precision == SLBM_FP64
           ? launch_pond_convert<double, double>(h->qd, (double*)h->pops(buf, 0),
-                                                (double*)h->pops(buf, 1),
+                                                (double*)h->pops(buf, 1), (double*)h->gp(buf, 0),
+                                                (double*)h->gp(buf, 1),
                                                 (const double*)h->lam(buf), h->flags(h->fcur),
                                                 mask, h->st)
           : launch_pond_convert<float, float>(h->qf, (float*)h->pops(buf, 0),
-                                              (float*)h->pops(buf, 1), (const float*)h->lam(buf),
+                                              (float*)h->pops(buf, 1), (float*)h->gp(buf, 0),
+                                              (float*)h->gp(buf, 1), (const float*)h->lam(buf),
                                               h->flags(h->fcur), mask, h->st);
   SLBM_CK(h, e, "co-moving conversion launch");
   return SLBM_OK;
@@ -528,15 +542,17 @@ int pond_step_once(slbm_s* h) {
   cudaError_t e;
   SLBM_CK(h, mark(h), "trace event");
   if (h->precision == SLBM_FP64)
-    e = launch_pond_step<double, double>(h->qd, (const double*)h->pops(b, 0),
-                                         (const double*)h->pops(b, 1), (const double*)h->lam(b),
-                                         (double*)h->pops(nb, 0), (double*)h->pops(nb, 1),
-                                         (double*)h->lam(nb), h->flags(h->fcur), err, h->st);
+    e = launch_pond_step<double, double>(
+        h->qd, (const double*)h->pops(b, 0), (const double*)h->pops(b, 1),
+        (const double*)h->gp(b, 0), (const double*)h->gp(b, 1), (const double*)h->lam(b),
+        (double*)h->pops(nb, 0), (double*)h->pops(nb, 1), (double*)h->gp(nb, 0),
+        (double*)h->gp(nb, 1), (double*)h->lam(nb), h->flags(h->fcur), err, h->st);
   else
-    e = launch_pond_step<float, float>(h->qf, (const float*)h->pops(b, 0),
-                                       (const float*)h->pops(b, 1), (const float*)h->lam(b),
-                                       (float*)h->pops(nb, 0), (float*)h->pops(nb, 1),
-                                       (float*)h->lam(nb), h->flags(h->fcur), err, h->st);
+    e = launch_pond_step<float, float>(
+        h->qf, (const float*)h->pops(b, 0), (const float*)h->pops(b, 1),
+        (const float*)h->gp(b, 0), (const float*)h->gp(b, 1), (const float*)h->lam(b),
+        (float*)h->pops(nb, 0), (float*)h->pops(nb, 1), (float*)h->gp(nb, 0),
+        (float*)h->gp(nb, 1), (float*)h->lam(nb), h->flags(h->fcur), err, h->st);
   SLBM_CK(h, e, "co-moving step launch");
   SLBM_CK(h, mark(h), "trace event");
   if (int rc = pond_convert_band(h, nb)) return rc;
@@ -666,6 +682,7 @@ void fill_params(Params<R>& p, const slbm_s* h, const Lattice1D& a, const Lattic
   p.work = reinterpret_cast<int*>(h->ws + h->lay.post_work);
   p.wlist = reinterpret_cast<int*>(h->ws + h->lay.post_list);
   p.wcount = reinterpret_cast<int*>(h->ws + h->lay.post_nlist);
+  p.cv = h->twopop ? h->cv : 1.0;
   fill_lat(p.lat[0], a, dt, h->P);
   fill_lat(p.lat[1], b, dt, h->P);
   ConvTab<R>& t = p.conv;
@@ -704,6 +721,10 @@ void fill_pond(PondParams<R>& q, const slbm_s* h, const Params<R>& p, const Latt
   q.tol = (R)h->pond_tol;
   q.maxit = h->pond_maxit;
   q.thermal = h->frame == SLBM_FRAME_POND ? 1 : 0;
+  q.twopop = h->twopop;
+  q.cv = (R)(h->twopop ? h->cv : 1.0);
+  q.cvm1 = (R)(h->twopop ? h->cv - 1.0 : 0.0);
+  q.omega2 = (R)(h->twopop ? 1.0 / h->tau2 : 1.0 / h->tau);
   q.P = h->P;
   q.reach = (R)kPondReach;
   for (int k = 0; k < 2; ++k) {
@@ -802,9 +823,11 @@ int init_eq_dev(slbm_s* h, bool with_T = false) {
     e = h->precision == SLBM_FP64
             ? launch_pond_init<double, double>(h->qd, (double*)h->pops(h->cur, 0),
                                                (double*)h->pops(h->cur, 1),
+                                               (double*)h->gp(h->cur, 0), (double*)h->gp(h->cur, 1),
                                                (double*)h->lam(h->cur), r, u, v, T, h->st)
             : launch_pond_init<float, float>(h->qf, (float*)h->pops(h->cur, 0),
-                                             (float*)h->pops(h->cur, 1), (float*)h->lam(h->cur),
+                                             (float*)h->pops(h->cur, 1), (float*)h->gp(h->cur, 0),
+                                             (float*)h->gp(h->cur, 1), (float*)h->lam(h->cur),
                                              r, u, v, T, h->st);
     SLBM_CK(h, e, "init launch");
     return SLBM_OK;
@@ -1036,6 +1059,7 @@ int slbm_destroy(slbm_t h) {
   drop_graphs(h);
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
   if (h->ind_buf) cudaFree(h->ind_buf);
+  if (h->gbuf) cudaFree(h->gbuf);
   if (h->owns_ws && cudaFree(h->ws) != cudaSuccess) rc = SLBM_ECUDA;
   delete h;
   return rc;
@@ -1095,10 +1119,13 @@ int slbm_set_flags(slbm_t h, const uint8_t* flags) {
         h->precision == SLBM_FP64
             ? launch_pond_convert<double, double>(h->qd, (double*)h->pops(h->cur, 0),
                                                   (double*)h->pops(h->cur, 1),
+                                                  (double*)h->gp(h->cur, 0),
+                                                  (double*)h->gp(h->cur, 1),
                                                   (const double*)h->lam(h->cur),
                                                   h->flags(h->fcur), nullptr, h->st)
             : launch_pond_convert<float, float>(h->qf, (float*)h->pops(h->cur, 0),
                                                 (float*)h->pops(h->cur, 1),
+                                                (float*)h->gp(h->cur, 0), (float*)h->gp(h->cur, 1),
                                                 (const float*)h->lam(h->cur), h->flags(h->fcur),
                                                 nullptr, h->st);
     SLBM_CK(h, e, "co-moving conversion launch");
@@ -1313,7 +1340,7 @@ int slbm_moments_device(slbm_t h, double* rho, double* ux, double* uy, double* T
     SLBM_TYPES(ty);
     return launch_moments<S, R>(prm, (const S*)h->pops(h->cur, 0), (const S*)h->pops(h->cur, 1),
                                 h->flags(h->fcur), rho, ux, uy, T, (const S*)frame_planes(h),
-                                h->st);
+                                h->st, (const S*)h->gp(h->cur, 0), (const S*)h->gp(h->cur, 1));
   });
   SLBM_CK(h, e, "moments launch");
   return SLBM_OK;
@@ -1345,7 +1372,8 @@ int slbm_audit(slbm_t h, double out[4]) {
   e = with_types(h, [&](auto ty, const auto& prm) {
     SLBM_TYPES(ty);
     return launch_audit<S, R>(prm, (const S*)h->pops(h->cur, 0), (const S*)h->pops(h->cur, 1),
-                              h->flags(h->fcur), part, np, res, (const S*)frame_planes(h), h->st);
+                              h->flags(h->fcur), part, np, res, (const S*)frame_planes(h), h->st,
+                              (const S*)h->gp(h->cur, 0), (const S*)h->gp(h->cur, 1));
   });
   SLBM_CK(h, e, "audit launch");
   SLBM_CK(h, cudaMemcpyAsync(out, res, 32, cudaMemcpyDeviceToHost, h->st), "D2H copy");
@@ -1454,6 +1482,71 @@ int slbm_set_state(slbm_t h, const void* buf, size_t bytes) {
   SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
   h->steps = hd.steps;
   return SLBM_OK;
+}
+
+int slbm_set_twopop(slbm_t h, double cv, double tau2) {
+  SLBM_GUARD(h);
+  if (h->frame != SLBM_FRAME_POND) return fail(h, SLBM_EINVAL, "two populations need the thermal co-moving frame");
+  if (!(cv > 0.0) || !(tau2 > 0.5)) return fail(h, SLBM_EINVAL, "need C_v > 0 and tau2 > 1/2");
+  if (h->twopop) return fail(h, SLBM_EINVAL, "the two-population model is already set");
+  const size_t es = h->precision == SLBM_FP64 ? 8 : 4;
+  const size_t bytes =
+      2 * es * (size_t)h->lay.plane * (size_t)(h->nlo * h->nlo + h->nhi * h->nhi);
+  int dev_prev = -1;
+  cudaGetDevice(&dev_prev);
+  if (dev_prev != h->dev) cudaSetDevice(h->dev);
+  void* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, bytes);
+  if (dev_prev >= 0 && dev_prev != h->dev) cudaSetDevice(dev_prev);
+  SLBM_CK(h, e, "g planes allocation");
+  h->gbuf = (char*)buf;
+  SLBM_CK(h, cudaMemsetAsync(h->gbuf, 0, bytes, h->st), "g planes clear");
+  h->twopop = 1;
+  h->cv = cv;
+  h->tau2 = tau2;
+  refresh_params(h);
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  return SLBM_OK;
+}
+
+namespace {
+int gpops_io(slbm_t h, int k, double* out, const double* in) {
+  if (!h->twopop) return fail(h, SLBM_EINVAL, "no two-population model on this handle");
+  if ((k != 0 && k != 1) || !(out || in)) return fail(h, SLBM_EINVAL, "lattice index or buffer invalid");
+  const int n = k ? h->nhi : h->nlo;
+  const size_t nc = h->ncell();
+  double* stage = h->at<double>(h->lay.macro[0]);
+  for (int i = 0; i < n * n; ++i) {
+    cudaError_t e;
+    if (in) {
+      if (int rc = upload(h, stage, in + (size_t)i * nc, nc * 8)) return rc;
+    }
+    e = h->precision == SLBM_FP64
+            ? launch_pond_gio<double, double>(h->qd, k, i, (double*)h->gp(h->cur, k),
+                                              (const double*)h->lam(h->cur), stage, in ? 1 : 0,
+                                              h->st)
+            : launch_pond_gio<float, float>(h->qf, k, i, (float*)h->gp(h->cur, k),
+                                            (const float*)h->lam(h->cur), stage, in ? 1 : 0,
+                                            h->st);
+    SLBM_CK(h, e, "g plane launch");
+    if (out)
+      SLBM_CK(h, cudaMemcpyAsync(out + (size_t)i * nc, stage, nc * 8, cudaMemcpyDeviceToHost, h->st),
+              "D2H copy");
+    SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  }
+  return SLBM_OK;
+}
+}  // namespace
+
+int slbm_get_gpops(slbm_t h, int k, double* out) {
+  SLBM_GUARD(h);
+  return gpops_io(h, k, out, nullptr);
+}
+
+int slbm_set_gpops(slbm_t h, int k, const double* in) {
+  SLBM_GUARD(h);
+  if (int rc = gpops_io(h, k, nullptr, in)) return rc;
+  return pond_convert_band(h, h->cur);
 }
 
 int slbm_set_pond(slbm_t h, double tol, int max_iter) {

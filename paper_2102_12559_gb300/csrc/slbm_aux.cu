@@ -107,13 +107,16 @@ k_init_eq(const Params<R> p, S* f0, S* f1, const double* __restrict__ rho,
   write_eq_both<S, R>(p, f0, f1, (y + p.G) * p.pitch + (x + kOX), rho[c], ux[c], uy[c]);
 }
 
-// rho, momentum and sum v^2/2 f of a cell's own lattice, in FP64.  lam
-// (three frame planes of stride nx*ny, or null for the lattice frame) gives
-// the co-moving frame {u, T} the populations live in: v_i = sqrt(T) c_i + u.
+// rho, momentum and total energy (sum v^2/2 f, plus sum g in the
+// two-population model) of a cell's own lattice, in FP64.  lam (three frame
+// planes of stride nx*ny, or null for the lattice frame) gives the co-moving
+// frame {u, T} the populations live in: v_i = sqrt(T) c_i + u.  e0 / e1: the g
+// planes (g / T - (C_v - 1) W_i), or null.
 template <class S, class R>
 __device__ void cell_moments(const Params<R>& p, const S* f0, const S* f1, int k, int base,
                              double& r, double& jx, double& jy, double& e,
-                             const S* lam = nullptr, long long c = 0) {
+                             const S* lam = nullptr, long long c = 0, const S* e0 = nullptr,
+                             const S* e1 = nullptr) {
   const LatTab<R>& L = p.lat[k];
   const S* f = k ? f1 : f0;
   r = 1.0;
@@ -136,24 +139,32 @@ __device__ void cell_moments(const Params<R>& p, const S* f0, const S* f1, int k
     e = T * e + st * (ux * jx + uy * jy) + 0.5 * r * (ux * ux + uy * uy);
     jx = r * ux + st * jx;
     jy = r * uy + st * jy;
+    const S* g = k ? e1 : e0;
+    if (g) {  // sum g = T (sum e + C_v - 1)
+      double sg = p.cv - 1.0;
+      for (int i = 0; i < L.n * L.n; ++i) sg += (double)g[(size_t)i * p.plane + base];
+      e += T * sg;
+    }
   }
 }
 
 template <class S, class R>
 __global__ void __launch_bounds__(kTX * kTY)
 k_moments(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restrict__ flag,
-          double* rho, double* ux, double* uy, double* T, const S* lam) {
+          double* rho, double* ux, double* uy, double* T, const S* lam, const S* e0,
+          const S* e1) {
   const int x = blockIdx.x * kTX + threadIdx.x;
   const int y = blockIdx.y * kTY + threadIdx.y;
   if (x >= p.nx || y >= p.ny) return;
   const int c = x + p.nx * y;
   double r, jx, jy, e;
-  cell_moments<S, R>(p, f0, f1, flag[c], (y + p.G) * p.pitch + (x + kOX), r, jx, jy, e, lam, c);
+  cell_moments<S, R>(p, f0, f1, flag[c], (y + p.G) * p.pitch + (x + kOX), r, jx, jy, e, lam, c,
+                     e0, e1);
   const double u = jx / r, v = jy / r;
   if (rho) rho[c] = r;
   if (ux) ux[c] = u;
   if (uy) uy[c] = v;
-  if (T) T[c] = (2.0 * e / r - u * u - v * v) / 2.0;
+  if (T) T[c] = e0 ? (e / r - 0.5 * (u * u + v * v)) / p.cv : (2.0 * e / r - u * u - v * v) / 2.0;
 }
 
 // Mach criterion of Sec. IV.A on the current state (flag = |u| > thr, c_s = 1).
@@ -176,7 +187,7 @@ k_criterion(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restri
 template <class S, class R>
 __global__ void __launch_bounds__(kThreads)
 k_audit_partial(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restrict__ flag,
-                double* partials, const S* lam) {
+                double* partials, const S* lam, const S* e0, const S* e1) {
   __shared__ double sh[4][kThreads];
   double a[4] = {0.0, 0.0, 0.0, 0.0};
   const long long ncell = (long long)p.nx * p.ny;
@@ -184,7 +195,8 @@ k_audit_partial(const Params<R> p, const S* f0, const S* f1, const uint8_t* __re
        c += (long long)gridDim.x * kThreads) {
     const int x = (int)(c % p.nx), y = (int)(c / p.nx);
     double r, jx, jy, e;
-    cell_moments<S, R>(p, f0, f1, flag[c], (y + p.G) * p.pitch + (x + kOX), r, jx, jy, e, lam, c);
+    cell_moments<S, R>(p, f0, f1, flag[c], (y + p.G) * p.pitch + (x + kOX), r, jx, jy, e, lam, c,
+                       e0, e1);
     a[0] += r; a[1] += jx; a[2] += jy; a[3] += e;
   }
   for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = a[q];
@@ -319,8 +331,9 @@ cudaError_t launch_init_eq(const Params<R>& p, S* f0, S* f1, const double* rho, 
 template <class S, class R>
 cudaError_t launch_moments(const Params<R>& p, const S* f0, const S* f1, const uint8_t* flag,
                            double* rho, double* ux, double* uy, double* T, const S* lam,
-                           cudaStream_t st) {
-  k_moments<S, R><<<tile_grid(p), dim3(kTX, kTY), 0, st>>>(p, f0, f1, flag, rho, ux, uy, T, lam);
+                           cudaStream_t st, const S* e0, const S* e1) {
+  k_moments<S, R><<<tile_grid(p), dim3(kTX, kTY), 0, st>>>(p, f0, f1, flag, rho, ux, uy, T, lam,
+                                                           e0, e1);
   return cudaGetLastError();
 }
 
@@ -334,8 +347,8 @@ cudaError_t launch_criterion(const Params<R>& p, const S* f0, const S* f1, const
 template <class S, class R>
 cudaError_t launch_audit(const Params<R>& p, const S* f0, const S* f1, const uint8_t* flag,
                          double* partials, int nparts, double* out4, const S* lam,
-                         cudaStream_t st) {
-  k_audit_partial<S, R><<<nparts, kThreads, 0, st>>>(p, f0, f1, flag, partials, lam);
+                         cudaStream_t st, const S* e0, const S* e1) {
+  k_audit_partial<S, R><<<nparts, kThreads, 0, st>>>(p, f0, f1, flag, partials, lam, e0, e1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_audit_final<<<1, kThreads, 0, st>>>(partials, nparts, out4);
@@ -356,12 +369,13 @@ cudaError_t launch_pack(const Params<R>& p, int k, int i0, int cnt, const S* f, 
                                             const double*, const double*, cudaStream_t);     \
   template cudaError_t launch_moments<S, R>(const Params<R>&, const S*, const S*,            \
                                             const uint8_t*, double*, double*, double*,       \
-                                            double*, const S*, cudaStream_t);                \
+                                            double*, const S*, cudaStream_t, const S*,       \
+                                            const S*);                                       \
   template cudaError_t launch_criterion<S, R>(const Params<R>&, const S*, const S*,          \
                                               const uint8_t*, uint8_t*, cudaStream_t);       \
   template cudaError_t launch_audit<S, R>(const Params<R>&, const S*, const S*,              \
                                           const uint8_t*, double*, int, double*, const S*,   \
-                                          cudaStream_t);                                     \
+                                          cudaStream_t, const S*, const S*);                 \
   template cudaError_t launch_pack<S, R>(const Params<R>&, int, int, int, const S*, double*, \
                                          int, S*, const double*, cudaStream_t);
 SLBM_AUX_INST(float, float)

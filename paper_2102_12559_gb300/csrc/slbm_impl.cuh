@@ -85,6 +85,7 @@ struct Params {
   int* work;                    // 2 x ntiles post-step work bits, accumulated by the stream kernel
   int* wlist;                   // 2 x ntiles: candidate work tiles (see add_work)
   int* wcount;                  // 2 counters: entries of each half of wlist
+  double cv;                    // C_v of the two-population co-moving model, else 1
 };
 
 // A tile has interface-conversion work iff its work word holds both lattices
@@ -129,6 +130,8 @@ struct PondParams {
   R tol;                        // predictor-corrector tolerance on |du|, |dT|
   int maxit;                    // reconstructions per cell update at most
   int thermal;                  // 1: T from the energy (C_v = D/2); 0: T = T_L
+  int twopop;                   // 1: two-population model (g planes, C_v, omega_2)
+  R cv, cvm1, omega2;           // C_v, C_v - 1, omega_2 of the two-population model
   int P;                        // collocation points per axis
   R reach;                      // largest departure distance allowed, cells
   PondLat<R> lat[2];
@@ -156,23 +159,32 @@ struct BcDev {
 
 // Co-moving frame launchers (slbm_pond.cu).  lam: three frame planes.
 template <class S, class R>
-cudaError_t launch_pond_init(const PondParams<R>& p, S* f0, S* f1, S* lam, const double* rho,
-                             const double* ux, const double* uy, const double* T,
-                             cudaStream_t st);
+cudaError_t launch_pond_init(const PondParams<R>& p, S* f0, S* f1, S* e0, S* e1, S* lam,
+                             const double* rho, const double* ux, const double* uy,
+                             const double* T, cudaStream_t st);
+// One co-moving step: f planes f0 / f1 (and, two-population model, g planes
+// e0 / e1) with frames lam -> g0 / g1 (eo0 / eo1) with frames lam_out.  The g
+// planes hold g / T_frame - (C_v - 1) W_i (deviation of the g populations in
+// units of the frame temperature); null when the model has one population.
 template <class S, class R>
-cudaError_t launch_pond_step(const PondParams<R>& p, const S* f0, const S* f1, const S* lam,
-                             S* g0, S* g1, S* lam_out, const uint8_t* flag, int* err,
-                             cudaStream_t st);
+cudaError_t launch_pond_step(const PondParams<R>& p, const S* f0, const S* f1, const S* e0,
+                             const S* e1, const S* lam, S* g0, S* g1, S* eo0, S* eo1,
+                             S* lam_out, const uint8_t* flag, int* err, cudaStream_t st);
 cudaError_t launch_pond_masks(int nx, int ny, const uint8_t* flag, uint8_t* mask,
                               cudaStream_t st);
 // mask null: convert every cell; else the cells of tiles whose 3 x 3 tile
 // neighbourhood holds both lattices.
 template <class S, class R>
-cudaError_t launch_pond_convert(const PondParams<R>& p, S* f0, S* f1, const S* lam,
+cudaError_t launch_pond_convert(const PondParams<R>& p, S* f0, S* f1, S* e0, S* e1, const S* lam,
                                 const uint8_t* flag, const uint8_t* mask, cudaStream_t st);
 template <class S, class R>
 cudaError_t launch_pond_frame_io(const PondParams<R>& p, S* lam, double* ux, double* uy,
                                  double* T, int unpack, cudaStream_t st);
+// Plane i of lattice k's g planes e to / from absolute g = T_frame (s + (C_v - 1) W_i)
+// (nc doubles, cell-major within the plane).
+template <class S, class R>
+cudaError_t launch_pond_gio(const PondParams<R>& p, int k, int i, S* e, const S* lam, double* buf,
+                            int unpack, cudaStream_t st);
 
 // Learned refinement indicator (slbm_indicator.cu): MLP 16 -> 32 -> 32 -> 1
 // with FP16 weights w1 (16 x 32) and w2 (32 x 32), row-major K x N, FP32 biases
@@ -259,7 +271,7 @@ cudaError_t launch_init_eq(const Params<R>& p, S* f0, S* f1, const double* rho,
 template <class S, class R>
 cudaError_t launch_moments(const Params<R>& p, const S* f0, const S* f1, const uint8_t* flag,
                            double* rho, double* ux, double* uy, double* T, const S* lam,
-                           cudaStream_t st);
+                           cudaStream_t st, const S* e0 = nullptr, const S* e1 = nullptr);
 
 template <class S, class R>
 cudaError_t launch_criterion(const Params<R>& p, const S* f0, const S* f1, const uint8_t* flag,
@@ -268,7 +280,7 @@ cudaError_t launch_criterion(const Params<R>& p, const S* f0, const S* f1, const
 template <class S, class R>
 cudaError_t launch_audit(const Params<R>& p, const S* f0, const S* f1, const uint8_t* flag,
                          double* partials, int nparts, double* out4, const S* lam,
-                         cudaStream_t st);
+                         cudaStream_t st, const S* e0 = nullptr, const S* e1 = nullptr);
 
 template <class S, class R>
 cudaError_t launch_pack(const Params<R>& p, int k, int i0, int cnt, const S* f, double* out,

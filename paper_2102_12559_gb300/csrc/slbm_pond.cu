@@ -28,6 +28,17 @@
 // dphi = phi - w without cancellation.  The equilibria use the raw Gaussian
 // moments h_m(u, T) of N(u, T), orders < n.
 //
+// Two-population model (Sec. II.B, eqs. Pond_f_equation / Pond_g_equation):
+// the g populations are kept as e_i = g_i / T_frame - (C_v - 1) W_i, so the
+// node's rest state is e = 0 like s = 0 for f.  Carried into a target frame
+// with r^2 = T_s / T they become r^2 G e_s + (C_v - 1)(r^2 (G W - W) +
+// (r^2 - 1) W).  T follows from the total energy (eq. E) with the g sum, and
+// the collision adds (omega_1 - omega_2)(f* - f^eq) and (omega_1 - omega_2)
+// (g* - g^eq) with the quasi-equilibria of eqs. (fqeq, gqeq) formed in the
+// frame used (the co-moving frame to the predictor-corrector tolerance):
+// f* - f^eq = W_i / 6 A:He3(c_i), A = sum c c c (f - f^eq); g* - g^eq = W_i q.c_i
+// with q = sum c (g - g^eq), in the frame's units.
+//
 // Wrapping: the grid is periodic and departure points may move several cells
 // (|v| dt grows with u and T), so node indices wrap with a modulo instead of
 // reading a ghost ring.
@@ -116,13 +127,14 @@ __device__ __forceinline__ int stencil(int P, R xd, R* a) {
 // collocation node it reads) are in lattice L with N nodes per axis.
 template <int N, class S, class R>
 __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* __restrict__ f,
-                          const S* __restrict__ lam, S* __restrict__ g, S* __restrict__ lam_out,
-                          int x, int y, int* err) {
+                          const S* __restrict__ e, const S* __restrict__ lam, S* __restrict__ g,
+                          S* __restrict__ eo, S* __restrict__ lam_out, int x, int y, int* err) {
   const long long c = (long long)x + (long long)p.nx * y;
   R ux = (R)lam[c], uy = (R)lam[p.nc + c], T = (R)lam[2 * p.nc + c];
   R d[N][N];                    // reconstructed deviations, [b][a]
+  R dg[N][N];                   // g deviations (two-population model)
   for (int b = 0; b < N; ++b)
-    for (int a = 0; a < N; ++a) d[b][a] = R(0);
+    for (int a = 0; a < N; ++a) d[b][a] = dg[b][a] = R(0);
   R dr = R(0), s1x = R(0), s1y = R(0), dT = R(0);
   bool ok = true, conv = false;
   for (int it = 0; it < p.maxit; ++it) {
@@ -140,11 +152,11 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
         if (fabs(vx * p.dt) > p.reach) ok = false;
         R ax[kMaxP];
         const int x0 = stencil<R>(p.P, (R)x - vx * p.dt, ax);
-        R acc = R(0);
+        R acc = R(0), gacc = R(0);
 #pragma unroll 1
         for (int t = 0; t < p.P; ++t) {
           const int yi = wrapm(y0 + t, p.ny);
-          R acc_t = R(0);
+          R acc_t = R(0), gacc_t = R(0);
 #pragma unroll 1
           for (int u = 0; u < p.P; ++u) {
             const int xi = wrapm(x0 + u, p.nx);
@@ -171,12 +183,28 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
             }
             // G W - W
             const R pxa = dphi1<N, R>(L, a, dx, dTs), pyb = dphi1<N, R>(L, b, dy, dTs);
-            v += L.w[a] * pyb + pxa * L.w[b] + pxa * pyb;
+            const R gw = L.w[a] * pyb + pxa * L.w[b] + pxa * pyb;
+            v += gw;
             acc_t += ax[u] * v;
+            if (p.twopop) {  // r^2 G e_s + (C_v - 1)(r^2 (G W - W) + (r^2 - 1) W)
+              R vg = R(0);
+#pragma unroll
+              for (int k = 0; k < N; ++k) {
+                R row = R(0);
+#pragma unroll
+                for (int j = 0; j < N; ++j) row += gx[j] * (R)e[(size_t)(j + N * k) * p.plane + base];
+                vg += gy[k] * row;
+              }
+              const R r2 = r * r;
+              vg = r2 * vg + p.cvm1 * (r2 * gw + dTs * L.w[a] * L.w[b]);
+              gacc_t += ax[u] * vg;
+            }
           }
           acc += ay[t] * acc_t;
+          gacc += ay[t] * gacc_t;
         }
         d[b][a] = acc;
+        dg[b][a] = gacc;
       }
     }
     // moments in the frame used: rho = 1 + sum d, relative velocity S1 / rho,
@@ -196,7 +224,18 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
     const R rho = R(1) + s0;
     s1x = sx / rho;
     s1y = sy / rho;
-    dT = p.thermal ? (s2 - rho * (s1x * s1x + s1y * s1y)) / (R(2) * rho) : R(0);
+    if (p.twopop) {
+      // rho C_v T / T_frame = 1 + s2'/2 - rho s1^2/2 + sum g / T_frame (eq. E)
+      R sg = R(0);
+#pragma unroll
+      for (int b = 0; b < N; ++b)
+#pragma unroll
+        for (int a = 0; a < N; ++a) sg += dg[b][a];
+      dT = (R(0.5) * s2 - R(0.5) * rho * (s1x * s1x + s1y * s1y) + sg - p.cvm1 * s0) /
+           (rho * p.cv);
+    } else {
+      dT = p.thermal ? (s2 - rho * (s1x * s1x + s1y * s1y)) / (R(2) * rho) : R(0);
+    }
     const R dux = st * s1x, duy = st * s1y, dTabs = T * dT;
     const R diff = fmax(fabs(dux), fmax(fabs(duy), fabs(dTabs)));
     if (!(diff == diff)) { ok = false; break; }
@@ -215,14 +254,57 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
   dphi_t<N, R>(L, s1x, dT, ex);
   dphi_t<N, R>(L, s1y, dT, ey);
   const size_t base = (size_t)(y + p.G) * p.pitch + (x + kOX);
+  auto feq = [&](int a, int b) {
+    const R pa = L.w[a] + ex[a], pb = L.w[b] + ey[b];
+    return dr * pa * pb + L.w[a] * ey[b] + ex[a] * L.w[b] + ex[a] * ey[b];
+  };
+  if (!p.twopop) {
 #pragma unroll
-  for (int b = 0; b < N; ++b)
+    for (int b = 0; b < N; ++b)
 #pragma unroll
-    for (int a = 0; a < N; ++a) {
-      const R pa = L.w[a] + ex[a], pb = L.w[b] + ey[b];
-      const R eq = dr * pa * pb + L.w[a] * ey[b] + ex[a] * L.w[b] + ex[a] * ey[b];
-      g[(size_t)(a + N * b) * p.plane + base] = (S)(d[b][a] + p.omega * (eq - d[b][a]));
-    }
+      for (int a = 0; a < N; ++a) {
+        const R eq = feq(a, b);
+        g[(size_t)(a + N * b) * p.plane + base] = (S)(d[b][a] + p.omega * (eq - d[b][a]));
+      }
+  } else {
+    // g^eq = (C_v - 1) (T / T_frame) f^eq (eq. geqPond), as a deviation; the
+    // non-equilibrium tensors A = sum c c c (f - f^eq), q = sum c (g - g^eq)
+    R Axxx = R(0), Axxy = R(0), Axyy = R(0), Ayyy = R(0), qx = R(0), qy = R(0);
+#pragma unroll
+    for (int b = 0; b < N; ++b)
+#pragma unroll
+      for (int a = 0; a < N; ++a) {
+        const R eq = feq(a, b);
+        const R ca = L.c[a], cb = L.c[b];
+        const R nf = d[b][a] - eq;
+        Axxx += ca * ca * ca * nf;
+        Axxy += ca * ca * cb * nf;
+        Axyy += ca * cb * cb * nf;
+        Ayyy += cb * cb * cb * nf;
+        const R eg = p.cvm1 * ((R(1) + dT) * eq + dT * L.w[a] * L.w[b]);
+        const R ng = dg[b][a] - eg;
+        qx += ca * ng;
+        qy += cb * ng;
+      }
+    const R Bx = Axxx + Axyy, By = Axxy + Ayyy;  // A_x.., A_y.. contracted
+    const R w12 = p.omega - p.omega2;
+#pragma unroll
+    for (int b = 0; b < N; ++b)
+#pragma unroll
+      for (int a = 0; a < N; ++a) {
+        const R eq = feq(a, b);
+        const R ca = L.c[a], cb = L.c[b], W = L.w[a] * L.w[b];
+        // eq. (fqeq): W/6 A:(c c c - sym(c (x) 1)); eq. (gqeq): W q.c
+        const R fst = W * (Axxx * ca * ca * ca + R(3) * Axxy * ca * ca * cb +
+                           R(3) * Axyy * ca * cb * cb + Ayyy * cb * cb * cb -
+                           R(3) * (Bx * ca + By * cb)) / R(6);
+        const R gst = W * (qx * ca + qy * cb);
+        const R eg = p.cvm1 * ((R(1) + dT) * eq + dT * W);
+        const size_t o = (size_t)(a + N * b) * p.plane + base;
+        g[o] = (S)(d[b][a] + p.omega * (eq - d[b][a]) + w12 * fst);
+        eo[o] = (S)(dg[b][a] + p.omega * (eg - dg[b][a]) + w12 * gst);
+      }
+  }
   lam_out[c] = (S)ux;
   lam_out[p.nc + c] = (S)uy;
   lam_out[2 * p.nc + c] = (S)T;
@@ -231,23 +313,24 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
 template <int NL, int NH, class S, class R>
 __global__ void __launch_bounds__(kThreads)
 k_pond_step(const PondParams<R> p, const S* __restrict__ f0, const S* __restrict__ f1,
-            const S* __restrict__ lam, S* __restrict__ g0, S* __restrict__ g1,
+            const S* __restrict__ e0, const S* __restrict__ e1, const S* __restrict__ lam,
+            S* __restrict__ g0, S* __restrict__ g1, S* __restrict__ eo0, S* __restrict__ eo1,
             S* __restrict__ lam_out, const uint8_t* __restrict__ flag, int* err) {
   const int x = blockIdx.x * kTX + threadIdx.x;
   const int y = blockIdx.y * kTY + threadIdx.y;
   if (x >= p.nx || y >= p.ny) return;
   if (flag[(long long)x + (long long)p.nx * y])
-    pond_cell<NH, S, R>(p, p.lat[1], f1, lam, g1, lam_out, x, y, err);
+    pond_cell<NH, S, R>(p, p.lat[1], f1, e1, lam, g1, eo1, lam_out, x, y, err);
   else
-    pond_cell<NL, S, R>(p, p.lat[0], f0, lam, g0, lam_out, x, y, err);
+    pond_cell<NL, S, R>(p, p.lat[0], f0, e0, lam, g0, eo0, lam_out, x, y, err);
 }
 
 // Rest-frame equilibrium of both lattices (s = (rho - 1) W_i) and the frame.
 template <class S, class R>
 __global__ void __launch_bounds__(kThreads)
-k_pond_init(const PondParams<R> p, S* f0, S* f1, S* lam, const double* __restrict__ rho,
-            const double* __restrict__ ux, const double* __restrict__ uy,
-            const double* __restrict__ T) {
+k_pond_init(const PondParams<R> p, S* f0, S* f1, S* e0, S* e1, S* lam,
+            const double* __restrict__ rho, const double* __restrict__ ux,
+            const double* __restrict__ uy, const double* __restrict__ T) {
   const int x = blockIdx.x * kTX + threadIdx.x;
   const int y = blockIdx.y * kTY + threadIdx.y;
   if (x >= p.nx || y >= p.ny) return;
@@ -257,9 +340,13 @@ k_pond_init(const PondParams<R> p, S* f0, S* f1, S* lam, const double* __restric
   for (int k = 0; k < 2; ++k) {
     const PondLat<R>& L = p.lat[k];
     S* f = k ? f1 : f0;
+    S* e = k ? e1 : e0;  // g = (C_v - 1) T rho W_i in the cell's own frame (eq. geqPond)
     for (int b = 0; b < L.n; ++b)
-      for (int a = 0; a < L.n; ++a)
-        f[(size_t)(a + L.n * b) * p.plane + base] = (S)(dr * (double)L.w[a] * (double)L.w[b]);
+      for (int a = 0; a < L.n; ++a) {
+        const double w = (double)L.w[a] * (double)L.w[b];
+        f[(size_t)(a + L.n * b) * p.plane + base] = (S)(dr * w);
+        if (p.twopop) e[(size_t)(a + L.n * b) * p.plane + base] = (S)((double)p.cvm1 * dr * w);
+      }
   }
   lam[c] = (S)ux[c];
   lam[p.nc + c] = (S)uy[c];
@@ -340,13 +427,13 @@ __device__ void lift_matrix(const PondLat<R>& Lq, const PondLat<R>& LQ, double s
 // its completing equilibrium is taken at the vector's own relative velocity
 // and temperature (T_L when isothermal).
 template <int NQ, int NQQ, class S, class R>
-__device__ void pond_convert_cell(const PondParams<R>& p, S* f0, S* f1, int k, size_t base,
-                                  const S* lam, long long c) {
+__device__ void pond_convert_cell(const PondParams<R>& p, S* f0, S* f1, S* e0, S* e1, int k,
+                                  size_t base, const S* lam, long long c) {
   const PondLat<R>& Lq = p.lat[0];
   const PondLat<R>& LQ = p.lat[1];
   if (k == 0) {
     R s[NQ][NQ];
-    double m0 = 0.0, mx = 0.0, my = 0.0, m2 = 0.0;
+    double m0 = 0.0, mx = 0.0, my = 0.0, m2 = 0.0, mg = 0.0;
 #pragma unroll
     for (int b = 0; b < NQ; ++b)
 #pragma unroll
@@ -358,80 +445,102 @@ __device__ void pond_convert_cell(const PondParams<R>& p, S* f0, S* f1, int k, s
         my += (double)Lq.c[b] * (double)v;
         m2 += ((double)Lq.c[a] * (double)Lq.c[a] + (double)Lq.c[b] * (double)Lq.c[b] - 2.0) *
               (double)v;
+        if (p.twopop) mg += (double)e0[(size_t)(a + NQ * b) * p.plane + base];
       }
     const double rho = 1.0 + m0;
     const R ux = (R)(mx / rho), uy = (R)(my / rho);
-    const R dT = p.thermal ? (R)((m2 - rho * ((mx / rho) * (mx / rho) + (my / rho) * (my / rho))) /
-                                 (2.0 * rho))
-                           : R(0);
+    const double u2 = (mx / rho) * (mx / rho) + (my / rho) * (my / rho);
+    R dT = R(0);
+    if (p.twopop)  // the node's T from the total energy (eq. E), as in the step
+      dT = (R)((0.5 * m2 - 0.5 * rho * u2 + mg - (double)p.cvm1 * m0) / (rho * (double)p.cv));
+    else if (p.thermal)
+      dT = (R)((m2 - rho * u2) / (2.0 * rho));
     const R dr = (R)m0;
     R qx[NQ], qy[NQ], Qx[NQQ], Qy[NQQ];
     dphi_t<NQ, R>(Lq, ux, dT, qx);
     dphi_t<NQ, R>(Lq, uy, dT, qy);
     dphi_t<NQQ, R>(LQ, ux, dT, Qx);
     dphi_t<NQQ, R>(LQ, uy, dT, Qy);
-    // non-equilibrium part of the q vector
-#pragma unroll
-    for (int b = 0; b < NQ; ++b)
-#pragma unroll
-      for (int a = 0; a < NQ; ++a) {
-        const R pa = Lq.w[a] + qx[a], pb = Lq.w[b] + qy[b];
-        s[b][a] -= dr * pa * pb + Lq.w[a] * qy[b] + qx[a] * Lq.w[b] + qx[a] * qy[b];
-      }
-    // L_x (f_q - f^eq_q) L_y^T + f^eq_Q
     const double sq = sqrt((double)lam[2 * p.nc + c]);
     R Lx[NQQ][NQ], Ly[NQQ][NQ];
     lift_matrix<NQ, NQQ, R>(Lq, LQ, sq, (double)lam[c], Lx);
     lift_matrix<NQ, NQQ, R>(Lq, LQ, sq, (double)lam[p.nc + c], Ly);
-    R t[NQ][NQQ];
+    // pass 0: f; pass 1: g, whose equilibrium is (C_v - 1)(1 + dT) f^eq (eq.
+    // geqPond, in units of the frame temperature) as a deviation
+    for (int pass = 0; pass < (p.twopop ? 2 : 1); ++pass) {
+      const R sc = pass ? p.cvm1 * (R(1) + dT) : R(1), sw = pass ? p.cvm1 * dT : R(0);
+      if (pass)
 #pragma unroll
-    for (int b = 0; b < NQ; ++b)
+        for (int b = 0; b < NQ; ++b)
 #pragma unroll
-      for (int A = 0; A < NQQ; ++A) {
-        R v = R(0);
+          for (int a = 0; a < NQ; ++a) s[b][a] = (R)e0[(size_t)(a + NQ * b) * p.plane + base];
+      // non-equilibrium part of the q vector
 #pragma unroll
-        for (int a = 0; a < NQ; ++a) v += Lx[A][a] * s[b][a];
-        t[b][A] = v;
-      }
+      for (int b = 0; b < NQ; ++b)
 #pragma unroll
-    for (int B = 0; B < NQQ; ++B)
+        for (int a = 0; a < NQ; ++a) {
+          const R pa = Lq.w[a] + qx[a], pb = Lq.w[b] + qy[b];
+          const R eq = dr * pa * pb + Lq.w[a] * qy[b] + qx[a] * Lq.w[b] + qx[a] * qy[b];
+          s[b][a] -= sc * eq + sw * Lq.w[a] * Lq.w[b];
+        }
+      // L_x (f_q - f^eq_q) L_y^T + f^eq_Q
+      R t[NQ][NQQ];
 #pragma unroll
-      for (int A = 0; A < NQQ; ++A) {
-        R v = R(0);
+      for (int b = 0; b < NQ; ++b)
 #pragma unroll
-        for (int b = 0; b < NQ; ++b) v += Ly[B][b] * t[b][A];
-        const R pa = LQ.w[A] + Qx[A], pb = LQ.w[B] + Qy[B];
-        v += dr * pa * pb + LQ.w[A] * Qy[B] + Qx[A] * LQ.w[B] + Qx[A] * Qy[B];
-        f1[(size_t)(A + NQQ * B) * p.plane + base] = (S)v;
-      }
+        for (int A = 0; A < NQQ; ++A) {
+          R v = R(0);
+#pragma unroll
+          for (int a = 0; a < NQ; ++a) v += Lx[A][a] * s[b][a];
+          t[b][A] = v;
+        }
+      S* out = pass ? e1 : f1;
+#pragma unroll
+      for (int B = 0; B < NQQ; ++B)
+#pragma unroll
+        for (int A = 0; A < NQQ; ++A) {
+          R v = R(0);
+#pragma unroll
+          for (int b = 0; b < NQ; ++b) v += Ly[B][b] * t[b][A];
+          const R pa = LQ.w[A] + Qx[A], pb = LQ.w[B] + Qy[B];
+          const R eq = dr * pa * pb + LQ.w[A] * Qy[B] + Qx[A] * LQ.w[B] + Qx[A] * Qy[B];
+          v += sc * eq + sw * LQ.w[A] * LQ.w[B];
+          out[(size_t)(A + NQQ * B) * p.plane + base] = (S)v;
+        }
+    }
   } else {
-    // P s_Q P^T (P W_Q P^T = W_q: projection keeps the moments of order < nq)
-    R t[NQQ][NQ];
+    // P s_Q P^T (P W_Q P^T = W_q: projection keeps the moments of order < nq);
+    // the same for the g planes
+    for (int pass = 0; pass < (p.twopop ? 2 : 1); ++pass) {
+      const S* in = pass ? e1 : f1;
+      S* out = pass ? e0 : f0;
+      R t[NQQ][NQ];
 #pragma unroll
-    for (int B = 0; B < NQQ; ++B)
+      for (int B = 0; B < NQQ; ++B)
 #pragma unroll
-      for (int a = 0; a < NQ; ++a) {
-        R v = R(0);
+        for (int a = 0; a < NQ; ++a) {
+          R v = R(0);
 #pragma unroll
-        for (int A = 0; A < NQQ; ++A)
-          v += p.proj[a][A] * (R)f1[(size_t)(A + NQQ * B) * p.plane + base];
-        t[B][a] = v;
-      }
+          for (int A = 0; A < NQQ; ++A)
+            v += p.proj[a][A] * (R)in[(size_t)(A + NQQ * B) * p.plane + base];
+          t[B][a] = v;
+        }
 #pragma unroll
-    for (int b = 0; b < NQ; ++b)
+      for (int b = 0; b < NQ; ++b)
 #pragma unroll
-      for (int a = 0; a < NQ; ++a) {
-        R v = R(0);
+        for (int a = 0; a < NQ; ++a) {
+          R v = R(0);
 #pragma unroll
-        for (int B = 0; B < NQQ; ++B) v += p.proj[b][B] * t[B][a];
-        f0[(size_t)(a + NQ * b) * p.plane + base] = (S)v;
-      }
+          for (int B = 0; B < NQQ; ++B) v += p.proj[b][B] * t[B][a];
+          out[(size_t)(a + NQ * b) * p.plane + base] = (S)v;
+        }
+    }
   }
 }
 
 template <int NQ, int NQQ, class S, class R>
 __global__ void __launch_bounds__(kThreads)
-k_pond_convert(const PondParams<R> p, S* f0, S* f1, const S* __restrict__ lam,
+k_pond_convert(const PondParams<R> p, S* f0, S* f1, S* e0, S* e1, const S* __restrict__ lam,
                const uint8_t* __restrict__ flag, const uint8_t* __restrict__ mask) {
   const int x = blockIdx.x * kTX + threadIdx.x;
   const int y = blockIdx.y * kTY + threadIdx.y;
@@ -447,7 +556,8 @@ k_pond_convert(const PondParams<R> p, S* f0, S* f1, const S* __restrict__ lam,
   if (x >= p.nx || y >= p.ny) return;
   const long long c = (long long)x + (long long)p.nx * y;
   const int k = flag[c] ? 1 : 0;
-  pond_convert_cell<NQ, NQQ, S, R>(p, f0, f1, k, (size_t)(y + p.G) * p.pitch + (x + kOX), lam, c);
+  pond_convert_cell<NQ, NQQ, S, R>(p, f0, f1, e0, e1, k, (size_t)(y + p.G) * p.pitch + (x + kOX),
+                                   lam, c);
 }
 
 template <class S, class R>
@@ -462,43 +572,63 @@ k_pond_frame_io(const PondParams<R> p, S* lam, double* ux, double* uy, double* T
   }
 }
 
+// Plane i of lattice k's g planes to / from absolute g (cell-major doubles).
+template <class S, class R>
+__global__ void __launch_bounds__(kThreads)
+k_pond_gio(const PondParams<R> p, int k, int i, S* e, const S* __restrict__ lam, double* buf,
+           int unpack) {
+  const long long c = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (c >= p.nc) return;
+  const PondLat<R>& L = p.lat[k];
+  const int x = (int)(c % p.nx), y = (int)(c / p.nx);
+  const size_t o = (size_t)i * p.plane + (size_t)(y + p.G) * p.pitch + (x + kOX);
+  const double W = (double)L.w[i % L.n] * (double)L.w[i / L.n];
+  const double T = (double)lam[2 * p.nc + c];
+  if (unpack) e[o] = (S)(buf[c] / T - (double)p.cvm1 * W);
+  else buf[c] = T * ((double)e[o] + (double)p.cvm1 * W);
+}
+
 dim3 tile_grid(int nx, int ny) { return dim3((nx + kTX - 1) / kTX, (ny + kTY - 1) / kTY); }
 
 template <int NL, int NH, class S, class R>
-cudaError_t step_pair(const PondParams<R>& p, const S* f0, const S* f1, const S* lam, S* g0, S* g1,
-                      S* lam_out, const uint8_t* flag, int* err, cudaStream_t st) {
+cudaError_t step_pair(const PondParams<R>& p, const S* f0, const S* f1, const S* e0, const S* e1,
+                      const S* lam, S* g0, S* g1, S* eo0, S* eo1, S* lam_out, const uint8_t* flag,
+                      int* err, cudaStream_t st) {
   k_pond_step<NL, NH, S, R><<<tile_grid(p.nx, p.ny), dim3(kTX, kTY), 0, st>>>(
-      p, f0, f1, lam, g0, g1, lam_out, flag, err);
+      p, f0, f1, e0, e1, lam, g0, g1, eo0, eo1, lam_out, flag, err);
   return cudaGetLastError();
 }
 
 template <int NL, int NH, class S, class R>
-cudaError_t convert_pair(const PondParams<R>& p, S* f0, S* f1, const S* lam, const uint8_t* flag,
-                         const uint8_t* mask, cudaStream_t st) {
-  k_pond_convert<NL, NH, S, R><<<tile_grid(p.nx, p.ny), dim3(kTX, kTY), 0, st>>>(p, f0, f1, lam,
-                                                                                 flag, mask);
+cudaError_t convert_pair(const PondParams<R>& p, S* f0, S* f1, S* e0, S* e1, const S* lam,
+                         const uint8_t* flag, const uint8_t* mask, cudaStream_t st) {
+  k_pond_convert<NL, NH, S, R><<<tile_grid(p.nx, p.ny), dim3(kTX, kTY), 0, st>>>(
+      p, f0, f1, e0, e1, lam, flag, mask);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 template <class S, class R>
-cudaError_t launch_pond_init(const PondParams<R>& p, S* f0, S* f1, S* lam, const double* rho,
-                             const double* ux, const double* uy, const double* T,
-                             cudaStream_t st) {
-  k_pond_init<S, R><<<tile_grid(p.nx, p.ny), dim3(kTX, kTY), 0, st>>>(p, f0, f1, lam, rho, ux, uy,
-                                                                      T);
+cudaError_t launch_pond_init(const PondParams<R>& p, S* f0, S* f1, S* e0, S* e1, S* lam,
+                             const double* rho, const double* ux, const double* uy,
+                             const double* T, cudaStream_t st) {
+  k_pond_init<S, R><<<tile_grid(p.nx, p.ny), dim3(kTX, kTY), 0, st>>>(p, f0, f1, e0, e1, lam, rho,
+                                                                      ux, uy, T);
   return cudaGetLastError();
 }
 
 template <class S, class R>
-cudaError_t launch_pond_step(const PondParams<R>& p, const S* f0, const S* f1, const S* lam,
-                             S* g0, S* g1, S* lam_out, const uint8_t* flag, int* err,
-                             cudaStream_t st) {
+cudaError_t launch_pond_step(const PondParams<R>& p, const S* f0, const S* f1, const S* e0,
+                             const S* e1, const S* lam, S* g0, S* g1, S* eo0, S* eo1,
+                             S* lam_out, const uint8_t* flag, int* err, cudaStream_t st) {
   const int lo = p.lat[0].n, hi = p.lat[1].n;
-  if (lo == 3 && hi == 4) return step_pair<3, 4, S, R>(p, f0, f1, lam, g0, g1, lam_out, flag, err, st);
-  if (lo == 3 && hi == 5) return step_pair<3, 5, S, R>(p, f0, f1, lam, g0, g1, lam_out, flag, err, st);
-  if (lo == 4 && hi == 5) return step_pair<4, 5, S, R>(p, f0, f1, lam, g0, g1, lam_out, flag, err, st);
+  if (lo == 3 && hi == 4)
+    return step_pair<3, 4, S, R>(p, f0, f1, e0, e1, lam, g0, g1, eo0, eo1, lam_out, flag, err, st);
+  if (lo == 3 && hi == 5)
+    return step_pair<3, 5, S, R>(p, f0, f1, e0, e1, lam, g0, g1, eo0, eo1, lam_out, flag, err, st);
+  if (lo == 4 && hi == 5)
+    return step_pair<4, 5, S, R>(p, f0, f1, e0, e1, lam, g0, g1, eo0, eo1, lam_out, flag, err, st);
   return cudaErrorInvalidValue;
 }
 
@@ -509,13 +639,21 @@ cudaError_t launch_pond_masks(int nx, int ny, const uint8_t* flag, uint8_t* mask
 }
 
 template <class S, class R>
-cudaError_t launch_pond_convert(const PondParams<R>& p, S* f0, S* f1, const S* lam,
+cudaError_t launch_pond_convert(const PondParams<R>& p, S* f0, S* f1, S* e0, S* e1, const S* lam,
                                 const uint8_t* flag, const uint8_t* mask, cudaStream_t st) {
   const int lo = p.lat[0].n, hi = p.lat[1].n;
-  if (lo == 3 && hi == 4) return convert_pair<3, 4, S, R>(p, f0, f1, lam, flag, mask, st);
-  if (lo == 3 && hi == 5) return convert_pair<3, 5, S, R>(p, f0, f1, lam, flag, mask, st);
-  if (lo == 4 && hi == 5) return convert_pair<4, 5, S, R>(p, f0, f1, lam, flag, mask, st);
+  if (lo == 3 && hi == 4) return convert_pair<3, 4, S, R>(p, f0, f1, e0, e1, lam, flag, mask, st);
+  if (lo == 3 && hi == 5) return convert_pair<3, 5, S, R>(p, f0, f1, e0, e1, lam, flag, mask, st);
+  if (lo == 4 && hi == 5) return convert_pair<4, 5, S, R>(p, f0, f1, e0, e1, lam, flag, mask, st);
   return cudaErrorInvalidValue;
+}
+
+template <class S, class R>
+cudaError_t launch_pond_gio(const PondParams<R>& p, int k, int i, S* e, const S* lam, double* buf,
+                            int unpack, cudaStream_t st) {
+  const unsigned blocks = (unsigned)((p.nc + kThreads - 1) / kThreads);
+  k_pond_gio<S, R><<<blocks, kThreads, 0, st>>>(p, k, i, e, lam, buf, unpack);
+  return cudaGetLastError();
 }
 
 template <class S, class R>
@@ -527,16 +665,19 @@ cudaError_t launch_pond_frame_io(const PondParams<R>& p, S* lam, double* ux, dou
 }
 
 #define SLBM_POND_INST(S, R)                                                                    \
-  template cudaError_t launch_pond_init<S, R>(const PondParams<R>&, S*, S*, S*, const double*, \
+  template cudaError_t launch_pond_init<S, R>(const PondParams<R>&, S*, S*, S*, S*, S*,         \
                                               const double*, const double*, const double*,     \
-                                              cudaStream_t);                                   \
+                                              const double*, cudaStream_t);                    \
   template cudaError_t launch_pond_step<S, R>(const PondParams<R>&, const S*, const S*,        \
-                                              const S*, S*, S*, S*, const uint8_t*, int*,      \
-                                              cudaStream_t);                                   \
-  template cudaError_t launch_pond_convert<S, R>(const PondParams<R>&, S*, S*, const S*,       \
-                                                 const uint8_t*, const uint8_t*, cudaStream_t); \
+                                              const S*, const S*, const S*, S*, S*, S*, S*,    \
+                                              S*, const uint8_t*, int*, cudaStream_t);         \
+  template cudaError_t launch_pond_convert<S, R>(const PondParams<R>&, S*, S*, S*, S*,         \
+                                                 const S*, const uint8_t*, const uint8_t*,     \
+                                                 cudaStream_t);                                \
   template cudaError_t launch_pond_frame_io<S, R>(const PondParams<R>&, S*, double*, double*,  \
-                                                  double*, int, cudaStream_t);
+                                                  double*, int, cudaStream_t);                 \
+  template cudaError_t launch_pond_gio<S, R>(const PondParams<R>&, int, int, S*, const S*,     \
+                                             double*, int, cudaStream_t);
 SLBM_POND_INST(float, float)
 SLBM_POND_INST(double, double)
 #undef SLBM_POND_INST

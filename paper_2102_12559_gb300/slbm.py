@@ -36,6 +36,7 @@ EXPORTS = [
     "slbm_profile", "slbm_profile_read", "slbm_audit_dense_noalloc", "slbm_last_error",
     "slbm_set_pond", "slbm_get_frame", "slbm_set_frame",
     "slbm_set_indicator", "slbm_indicator_eval",
+    "slbm_set_twopop", "slbm_get_gpops", "slbm_set_gpops",
 ]
 SLBM_PROFILE_KERNELS = 2
 KERNEL_NAMES = ("stream_collide", "post_step")
@@ -103,6 +104,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.slbm_audit_dense_noalloc.argtypes = [p, i, i, i, p, p]
     L.slbm_last_error.argtypes = [p]
     L.slbm_set_pond.argtypes = [p, d, i]
+    L.slbm_set_twopop.argtypes = [p, d, d]
+    L.slbm_get_gpops.argtypes = [p, i, p]
+    L.slbm_set_gpops.argtypes = [p, i, p]
     L.slbm_get_frame.argtypes = [p, p, p, p]
     L.slbm_set_frame.argtypes = [p, p, p, p]
     L.slbm_set_indicator.argtypes = [p, p, p, p, p, p, ctypes.c_float, i]
@@ -199,6 +203,21 @@ def slbm_indicator_eval(h, n, features=True, logits=False, flags=False):
 
 def slbm_set_pond(h, tol, max_iter):
     _check(load().slbm_set_pond(h, float(tol), int(max_iter)), h)
+
+
+def slbm_set_twopop(h, cv, tau2):
+    _check(load().slbm_set_twopop(h, float(cv), float(tau2)), h)
+
+
+def slbm_get_gpops(h, k, Q, n):
+    out = np.zeros(Q * n)
+    _check(load().slbm_get_gpops(h, k, _ptr(out)), h)
+    return out
+
+
+def slbm_set_gpops(h, k, Q, n, pops):
+    a = _f64(pops, Q * n)
+    _check(load().slbm_set_gpops(h, k, _ptr(a)), h)
 
 
 def slbm_get_frame(h, n):
@@ -370,6 +389,21 @@ class Solver:
 
     def set_pond(self, tol, max_iter):
         slbm_set_pond(self.h, tol, max_iter)
+
+    def set_twopop(self, cv, tau2):
+        """Two-population co-moving model (before init_equilibrium)."""
+        slbm_set_twopop(self.h, cv, tau2)
+
+    def get_gpops(self, k):
+        """g populations of lattice k as (ny, nx, Q_k), absolute units."""
+        Q = self.Q[k]
+        a = slbm_get_gpops(self.h, k, Q, self.n).reshape(Q, self.ny, self.nx)
+        return np.moveaxis(a, 0, -1)
+
+    def set_gpops(self, k, pops):
+        Q = self.Q[k]
+        a = np.moveaxis(np.asarray(pops, dtype=np.float64).reshape(self.ny, self.nx, Q), -1, 0)
+        slbm_set_gpops(self.h, k, Q, self.n, np.ascontiguousarray(a))
 
     def set_indicator(self, weights, interval=10):
         """weights: dict w1 (16x32), b1 (32), w2 (32x32), b2 (32), w3 (32), b3."""
