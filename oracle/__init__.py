@@ -98,6 +98,8 @@ def lib():
         L.orc_get_pops.argtypes = [p, i, p]
         L.orc_set_pops.argtypes = [p, i, p]
         L.orc_set_twopop.argtypes = [p, d, d]
+        L.orc_set_pond_ends.argtypes = [p, p, p]
+        L.orc_set_viscosity_law.argtypes = [p, d, d, d, d]
         L.orc_get_gpops.argtypes = [p, i, p]
         L.orc_set_gpops.argtypes = [p, i, p]
     return _lib
@@ -236,6 +238,17 @@ class Oracle:
         """Two-population co-moving model of Sec. II.B (thermal co-moving
         frame only; before init_equilibrium): C_v = cv, omega_2 = 1 / tau2."""
         _check(lib().orc_set_twopop(self._h, float(cv), float(tau2)), "set_twopop")
+
+    def set_pond_ends(self, left, right):
+        """Co-moving frame on a non-periodic x axis: fixed states {rho, u_x,
+        u_y, T} beyond the left and right ends (set twopop first)."""
+        a, b = _f64(left), _f64(right)
+        _check(lib().orc_set_pond_ends(self._h, _ptr(a), _ptr(b)), "set_pond_ends")
+
+    def set_viscosity_law(self, mu1: float, T1: float, s_exp: float, pr: float):
+        """mu = mu1 (T / T1)^s_exp and fixed Pr (two-population model)."""
+        _check(lib().orc_set_viscosity_law(self._h, float(mu1), float(T1), float(s_exp),
+                                           float(pr)), "set_viscosity_law")
 
     def get_gpops(self, k: int) -> np.ndarray:
         """g populations of lattice k, shape (ny, nx, Q_k), absolute units."""

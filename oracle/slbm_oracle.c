@@ -478,6 +478,16 @@ typedef struct {
     double cv, omega2;           /* C_v (R = 1) and omega_2 */
     double *g[2], *gmemo[2], *gmom[2];
     uint8_t *ghave[2], *ghmom[2];
+    /* co-moving frame with a non-periodic x axis: fixed end states (rho, u_x,
+     * u_y, T) beyond x < 0 (side 0) and x >= nx (side 1), and the moments of
+     * their vectors rho W_i (and g^eq) in their own frames, per lattice */
+    double ends[2][4];
+    double bmom[2][2][ORC_MAXQ], bgmom[2][2][ORC_MAXQ];
+    int ends_set;
+    /* hard-sphere viscosity law (two-population model): mu = mu1 (T/T1)^s,
+     * omega_1 from mu = (1/omega_1 - 1/2) rho T dt, Pr fixed */
+    int hs;
+    double mu1, T1, s_exp, pr;
 } orc_t;
 
 static long cidx(const orc_t *s, long x, long y) { return x + (long)s->nx * y; }
@@ -488,7 +498,7 @@ orc_t *orc_create(int nx, int ny, int per_x, int per_y, int n_lo, int n_hi,
                   double tau, int order, int frame, double cfl)
 {
     if (nx < 1 || ny < 1 || n_lo >= n_hi || tau <= 0.5 || order < 1 || order > 5 ||
-        frame < 0 || frame > 2 || (frame != 0 && !(per_x && per_y)))
+        frame < 0 || frame > 2 || (frame != 0 && !per_y))
         return NULL;
     orc_t *s = (orc_t *)calloc(1, sizeof(orc_t));
     if (!s) return NULL;
@@ -838,6 +848,7 @@ static void update_cell(orc_t *s, long x, long y, double *out)
  * for the co-moving frame, whose grids are periodic. */
 static const double *node_moments(orc_t *s, long gx, long gy, int k)
 {
+    if (!s->per_x && (gx < 0 || gx >= s->nx)) return s->bmom[gx < 0 ? 0 : 1][k];
     gx = ((gx % s->nx) + s->nx) % s->nx;
     gy = ((gy % s->ny) + s->ny) % s->ny;
     long c = cidx(s, gx, gy);
@@ -871,6 +882,7 @@ static const double *node_vec_g(orc_t *s, long gx, long gy, int k)
 
 static const double *node_moments_g(orc_t *s, long gx, long gy, int k)
 {
+    if (!s->per_x && (gx < 0 || gx >= s->nx)) return s->bgmom[gx < 0 ? 0 : 1][k];
     gx = ((gx % s->nx) + s->nx) % s->nx;
     gy = ((gy % s->ny) + s->ny) % s->ny;
     long c = cidx(s, gx, gy);
@@ -934,6 +946,12 @@ static int collide2(const orc_t *s, const olat *L, const double lam[3], double r
     matvec(Q, G, df, tf);                        /* f* - f^eq in frame lam */
     matvec(Q, G, dg, tg);
     double w1 = s->omega, w2 = s->omega2;
+    if (s->hs) {  /* mu = (1/omega_1 - 1/2) rho T dt, kappa = C_p mu / Pr (Sec. II.B, IV.C) */
+        double mu = s->mu1 * pow(T / s->T1, s->s_exp);
+        double tau1 = mu / (rho * T * s->dt) + 0.5;
+        w1 = 1.0 / tau1;
+        w2 = 1.0 / ((tau1 - 0.5) / s->pr + 0.5);
+    }
     for (int i = 0; i < Q; ++i) {
         fout[i] = fbar[i] + w1 * (feq[i] - fbar[i]) + (w1 - w2) * tf[i];
         gout[i] = gbar[i] + w1 * (geq[i] - gbar[i]) + (w1 - w2) * tg[i];
@@ -1034,6 +1052,7 @@ int orc_step(orc_t *s, int n)
         }
     }
     if (s->frame && !(glam = (double *)malloc(sizeof(double) * 3 * nc))) rc = -1;
+    if (s->frame && !s->per_x && !s->ends_set) rc = -1;   /* end states required */
     for (int it = 0; it < n && rc == 0; ++it) {
         reset_memo(s);
         for (long y = 0; y < s->ny && rc == 0; ++y)
@@ -1212,5 +1231,47 @@ int orc_set_gpops(orc_t *s, int k, const double *in)
 {
     if (!s->twopop) return -1;
     memcpy(s->g[k], in, sizeof(double) * (size_t)s->nx * s->ny * s->L[k].Q);
+    return 0;
+}
+
+/* Co-moving frame with a non-periodic x axis (the quasi-one-dimensional shock
+ * of Sec. IV.C): collocation nodes beyond either end hold the fixed state
+ * end[side] = {rho, u_x, u_y, T} at rest in its own frame (f = rho W_i,
+ * g = (C_v - 1) T rho W_i, eqs. feqPond, geqPond).  Set the two-population
+ * model first when it is used. */
+int orc_set_pond_ends(orc_t *s, const double left[4], const double right[4])
+{
+    if (!s->frame || s->per_x) return -1;
+    for (int side = 0; side < 2; ++side) {
+        const double *e = side ? right : left;
+        if (!(e[0] > 0.0) || !(e[3] > 0.0)) return -1;
+        memcpy(s->ends[side], e, sizeof(s->ends[side]));
+        double lam[3] = {e[1], e[2], e[3]};
+        for (int k = 0; k < 2; ++k) {
+            const olat *L = &s->L[k];
+            double M[ORC_MAXQ * ORC_MAXQ], v[ORC_MAXQ];
+            moment_matrix(L, lam, M);
+            for (int i = 0; i < L->Q; ++i) v[i] = e[0] * L->W[i];
+            matvec(L->Q, M, v, s->bmom[side][k]);
+            for (int i = 0; i < L->Q; ++i) v[i] *= s->twopop ? (s->cv - 1.0) * e[3] : 0.0;
+            matvec(L->Q, M, v, s->bgmom[side][k]);
+        }
+    }
+    s->ends_set = 1;
+    return 0;
+}
+
+/* Hard-sphere-like viscosity law of the shock case (Sec. IV.C): mu = mu1 (T /
+ * T1)^s_exp, relaxation omega_1 from mu = (1/omega_1 - 1/2) rho T dt and
+ * omega_2 from a fixed Prandtl number pr = C_p mu / kappa, per cell update,
+ * at the reconstructed rho and T.  Two-population model only. */
+int orc_set_viscosity_law(orc_t *s, double mu1, double T1, double s_exp, double pr)
+{
+    if (!s->twopop || !(mu1 > 0.0) || !(T1 > 0.0) || !(pr > 0.0)) return -1;
+    s->hs = 1;
+    s->mu1 = mu1;
+    s->T1 = T1;
+    s->s_exp = s_exp;
+    s->pr = pr;
     return 0;
 }

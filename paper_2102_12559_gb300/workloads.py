@@ -183,3 +183,50 @@ def disc_flags(N: int, r: float):
     X, Y = np.meshgrid(x, x)
     c = N / 2.0
     return (((X - c) ** 2 + (Y - c) ** 2) < r * r).astype(np.uint8)
+
+
+def rankine_hugoniot(mach: float, gamma: float = 5.0 / 3.0, rho1: float = 1.0, T1: float = 1.0):
+    """Upstream and downstream states {rho, u, T} of a stationary normal shock
+    of an ideal gas (R = 1) with upstream Mach number `mach` relative to the
+    upstream sound speed sqrt(gamma T1), from the Rankine-Hugoniot jump
+    relations (the initial and end states of the shock structure problem)."""
+    m2 = mach * mach
+    r = (gamma + 1) * m2 / ((gamma - 1) * m2 + 2)            # rho2 / rho1
+    pr = 1 + 2 * gamma / (gamma + 1) * (m2 - 1)               # p2 / p1
+    u1 = mach * math.sqrt(gamma * T1)
+    return (rho1, u1, T1), (rho1 * r, u1 / r, T1 * pr / r)
+
+
+def shock_batch(count: int = 256, seed: int = 2, mach_range=(1.2, 4.0), len_range=(1024, 8192),
+                gamma: float = 5.0 / 3.0, width: float = 20.0, cells_per_mfp: float = 50.0):
+    """A batch of independent quasi-one-dimensional shock instances: upstream
+    Mach numbers uniform in mach_range, lengths uniform in len_range (cells),
+    Rankine-Hugoniot states joined by a tanh ramp of `width` cells at the
+    middle.  The upstream mean free path of hard spheres,
+    lambda_1 = 16 / (5 sqrt(2 pi gamma)) mu_1 a_1 / p_1, is `cells_per_mfp`
+    cells (the paper resolves it with 50), which fixes mu_1.  Returns per
+    instance: length, Mach, the two end states and mu_1, T_1, and a function
+    giving the initial rho, u, T of an instance on its cells."""
+    rng = np.random.default_rng(seed)
+    mach = rng.uniform(*mach_range, count)
+    lens = rng.integers(len_range[0], len_range[1] + 1, count)
+    out = []
+    for M, L in zip(mach, lens):
+        s1, s2 = rankine_hugoniot(float(M), gamma)
+        a1 = math.sqrt(gamma * s1[2])
+        p1 = s1[0] * s1[2]
+        mu1 = cells_per_mfp * p1 * 5 * math.sqrt(2 * math.pi * gamma) / (16 * a1)
+        out.append({"len": int(L), "mach": float(M), "left": s1, "right": s2, "mu1": mu1,
+                    "T1": s1[2]})
+    return out
+
+
+def shock_profile(inst: dict, nx: int, width: float = 20.0):
+    """rho, u, T of one instance on nx cells (cells beyond its length hold the
+    downstream state): the tanh ramp between the end states at the middle."""
+    L = inst["len"]
+    x = np.arange(nx, dtype=np.float64)
+    w = 0.5 * (1 + np.tanh((x - 0.5 * L) / width))
+    w[L:] = 1.0
+    (r1, u1, t1), (r2, u2, t2) = inst["left"], inst["right"]
+    return r1 + (r2 - r1) * w, u1 + (u2 - u1) * w, t1 + (t2 - t1) * w

@@ -209,3 +209,57 @@ def test_galilean_boost_by_one_cell_per_step():
     a, b = runs
     for get in (lambda o: o.get_pops(0), lambda o: o.get_gpops(0)):
         np.testing.assert_allclose(get(b), np.roll(get(a), steps, axis=1), rtol=0, atol=5e-12)
+
+
+@pytest.mark.parametrize("lo,hi", [(3, 5), (4, 5)])
+def test_fixed_ends_hold_a_matching_uniform_state(lo, hi):
+    """Non-periodic x with end states equal to the interior's uniform state
+    (moving, hot): the state is a fixed point, interfaces included."""
+    nx, ny = 20, 1
+    st = (1.2, 0.8, -0.1, 1.3)
+    o = O.Oracle(nx, ny, lo, hi, tau=0.7, frame=O.FRAME_POND, periodic=(False, True))
+    o.set_twopop(1.5, 0.9)
+    o.set_pond_ends(st, st)
+    one = np.ones((ny, nx))
+    o.init_equilibrium(st[0] * one, st[1] * one, st[2] * one, st[3] * one)
+    fl = np.zeros((ny, nx), np.uint8)
+    fl[:, 6:12] = 1
+    o.set_flags(fl)
+    o._twopop = True
+    before = state(o)
+    o.step(3)
+    for x, y in zip(before, state(o)):
+        assert np.abs(x - y).max() < 1e-13
+
+
+def test_viscosity_law_sets_the_relaxation_rate():
+    """mu = mu1 (T/T1)^s: in a uniform non-equilibrium state the stress term
+    decays by 1 - omega_1 with omega_1 from mu = (1/omega_1 - 1/2) rho T dt,
+    the heat-flux term by 1 - omega_2 with Pr = 2/3."""
+    nx, ny = 4, 4
+    rho, T, mu1, T1, s, pr = 1.3, 1.7, 0.8, 1.0, 0.5, 2.0 / 3.0
+    cx, cy, W = O.lattice(4)
+    one = np.ones((ny, nx))
+    for d, kind in ((W * cx * cy, 1), (W * (cx ** 3 - 3 * cx), 2)):
+        o = make(nx, ny, 4, 5, 0.7, 1.5, 0.9)
+        o.set_viscosity_law(mu1, T1, s, pr)
+        o.init_equilibrium(rho * one, 0.2 * one, 0.1 * one, T * one)
+        f = o.get_pops(0)
+        o.set_pops(0, f + 1e-3 * d)
+        o.step(1)
+        tau1 = mu1 * (T / T1) ** s / (rho * T * o.dt) + 0.5
+        w = 1 / tau1 if kind == 1 else 1 / ((tau1 - 0.5) / pr + 0.5)
+        np.testing.assert_allclose(o.get_pops(0) - f, np.broadcast_to((1 - w) * 1e-3 * d, f.shape),
+                                   rtol=0, atol=1e-13)
+
+
+def test_rankine_hugoniot_states():
+    """The shock inputs: textbook jumps at Ma = 2, gamma = 5/3, and equal
+    mass, momentum and energy fluxes on both sides (R = 1, C_v = 3/2)."""
+    (r1, u1, t1), (r2, u2, t2) = WL.rankine_hugoniot(2.0)
+    assert abs(r2 / r1 - 16 / 7) < 1e-12 and abs(t2 / t1 - 2.078125) < 1e-12
+    cv = 1.5
+    for a, b in ((r1 * u1, r2 * u2),
+                 (r1 * u1 ** 2 + r1 * t1, r2 * u2 ** 2 + r2 * t2),
+                 (u1 * (r1 * (cv * t1 + u1 ** 2 / 2) + r1 * t1), u2 * (r2 * (cv * t2 + u2 ** 2 / 2) + r2 * t2))):
+        assert abs(a - b) < 1e-12 * abs(a)
