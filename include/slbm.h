@@ -299,6 +299,27 @@ SLBM_API int slbm_set_twopop(slbm_t h, double cv, double tau2);
 SLBM_API int slbm_get_gpops(slbm_t h, int k, double *out);
 SLBM_API int slbm_set_gpops(slbm_t h, int k, const double *in);
 
+/* Batched quasi-one-dimensional instances (the shock structure problem of
+ * Sec. IV.C; co-moving frames only).
+ *
+ * slbm_set_rows: every row y of the grid becomes an independent instance,
+ * uniform across y (its y interpolation is the identity), with len[y] active
+ * cells (interp_order + 1 <= len[y] <= nx; cells beyond are left alone) and
+ * fixed end states beyond x < 0 and x >= len[y]: ends[8 y .. 8 y + 3] =
+ * {rho, u_x, u_y, T} on the left, ends[8 y + 4 .. 8 y + 7] on the right, each
+ * at rest in its own frame (f = rho W_i, g = (C_v - 1) T rho W_i).  Host
+ * arrays, copied.  The interface conversions and the step treat each row on
+ * its own.  One launch per step advances all rows.
+ *
+ * slbm_set_viscosity_law: two-population model only.  Per row y the dynamic
+ * viscosity mu = mu1[y] (T / T1[y])^s_exp (s_exp = 1/2 for hard spheres) sets
+ * omega_1 at every cell update from mu = (1/omega_1 - 1/2) rho T dt at the
+ * reconstructed rho and T, and omega_2 from the fixed Prandtl number pr
+ * (1/omega_2 - 1/2 = (1/omega_1 - 1/2) / pr).  Host arrays of ny doubles. */
+SLBM_API int slbm_set_rows(slbm_t h, const int *len, const double *ends);
+SLBM_API int slbm_set_viscosity_law(slbm_t h, const double *mu1, const double *T1, double s_exp,
+                                    double pr);
+
 /* Per-kernel timing (tracing).  slbm_profile(h, 1) clears previous records
  * and starts bracketing every kernel slbm_step launches with CUDA events on
  * the handle's stream; slbm_profile(h, 0) stops.  slbm_profile_read()

@@ -290,6 +290,13 @@ struct slbm_s {
   int twopop;
   double cv, tau2;
   char* gbuf;
+  // batched quasi-one-dimensional rows (slbm_set_rows) and the viscosity law
+  // (slbm_set_viscosity_law): device arrays row_len (ny ints), row_ends
+  // (8 ny doubles), row_visc (2 ny doubles) in one owned allocation
+  int rows, hs;
+  double s_exp, pr;
+  char* rowbuf;
+  size_t rb_len, rb_ends, rb_visc;
   Layout lay;
   cudaStream_t st;
   char* ws;
@@ -725,6 +732,13 @@ void fill_pond(PondParams<R>& q, const slbm_s* h, const Params<R>& p, const Latt
   q.cv = (R)(h->twopop ? h->cv : 1.0);
   q.cvm1 = (R)(h->twopop ? h->cv - 1.0 : 0.0);
   q.omega2 = (R)(h->twopop ? 1.0 / h->tau2 : 1.0 / h->tau);
+  q.rows = h->rows;
+  q.row_len = h->rowbuf ? reinterpret_cast<const int*>(h->rowbuf + h->rb_len) : nullptr;
+  q.row_ends = h->rowbuf ? reinterpret_cast<const double*>(h->rowbuf + h->rb_ends) : nullptr;
+  q.hs = h->hs;
+  q.row_visc = h->rowbuf ? reinterpret_cast<const double*>(h->rowbuf + h->rb_visc) : nullptr;
+  q.s_exp = (R)h->s_exp;
+  q.inv_pr = (R)(h->hs ? 1.0 / h->pr : 1.0);
   q.P = h->P;
   q.reach = (R)kPondReach;
   for (int k = 0; k < 2; ++k) {
@@ -1060,6 +1074,7 @@ int slbm_destroy(slbm_t h) {
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
   if (h->ind_buf) cudaFree(h->ind_buf);
   if (h->gbuf) cudaFree(h->gbuf);
+  if (h->rowbuf) cudaFree(h->rowbuf);
   if (h->owns_ws && cudaFree(h->ws) != cudaSuccess) rc = SLBM_ECUDA;
   delete h;
   return rc;
@@ -1481,6 +1496,69 @@ int slbm_set_state(slbm_t h, const void* buf, size_t bytes) {
   }
   SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
   h->steps = hd.steps;
+  return SLBM_OK;
+}
+
+namespace {
+// The handle's row arrays (allocated on first use, on the handle's device).
+int ensure_rowbuf(slbm_t h) {
+  if (h->rowbuf) return SLBM_OK;
+  const size_t ny = (size_t)h->g.ny;
+  h->rb_len = 0;
+  h->rb_ends = (ny * sizeof(int) + 255) / 256 * 256;
+  h->rb_visc = h->rb_ends + (8 * ny * sizeof(double) + 255) / 256 * 256;
+  const size_t bytes = h->rb_visc + 2 * ny * sizeof(double);
+  int dev_prev = -1;
+  cudaGetDevice(&dev_prev);
+  if (dev_prev != h->dev) cudaSetDevice(h->dev);
+  void* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, bytes);
+  if (dev_prev >= 0 && dev_prev != h->dev) cudaSetDevice(dev_prev);
+  SLBM_CK(h, e, "row arrays allocation");
+  h->rowbuf = (char*)buf;
+  SLBM_CK(h, cudaMemsetAsync(h->rowbuf, 0, bytes, h->st), "row arrays clear");
+  return SLBM_OK;
+}
+}  // namespace
+
+int slbm_set_rows(slbm_t h, const int* len, const double* ends) {
+  SLBM_GUARD(h);
+  if (h->frame == SLBM_FRAME_LATTICE) return fail(h, SLBM_EINVAL, "rows need a co-moving frame");
+  if (!len || !ends) return fail(h, SLBM_EINVAL, "len and ends are required");
+  for (int r = 0; r < h->g.ny; ++r) {
+    if (len[r] < h->P || len[r] > h->g.nx) return fail(h, SLBM_EINVAL, "row length out of range");
+    for (int side = 0; side < 2; ++side)
+      if (!(ends[8 * r + 4 * side] > 0.0) || !(ends[8 * r + 4 * side + 3] > 0.0))
+        return fail(h, SLBM_EINVAL, "end states need rho > 0 and T > 0");
+  }
+  if (int rc = ensure_rowbuf(h)) return rc;
+  if (int rc = upload(h, h->rowbuf + h->rb_len, len, (size_t)h->g.ny * sizeof(int))) return rc;
+  if (int rc = upload(h, h->rowbuf + h->rb_ends, ends, (size_t)h->g.ny * 8 * sizeof(double)))
+    return rc;
+  h->rows = 1;
+  refresh_params(h);
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  return SLBM_OK;
+}
+
+int slbm_set_viscosity_law(slbm_t h, const double* mu1, const double* T1, double s_exp,
+                           double pr) {
+  SLBM_GUARD(h);
+  if (!h->twopop) return fail(h, SLBM_EINVAL, "the viscosity law needs the two-population model");
+  if (!mu1 || !T1 || !(pr > 0.0)) return fail(h, SLBM_EINVAL, "mu1, T1 and pr > 0 are required");
+  std::vector<double> v(2 * (size_t)h->g.ny);
+  for (int r = 0; r < h->g.ny; ++r) {
+    if (!(mu1[r] > 0.0) || !(T1[r] > 0.0)) return fail(h, SLBM_EINVAL, "need mu1 > 0 and T1 > 0");
+    v[2 * r] = mu1[r];
+    v[2 * r + 1] = T1[r];
+  }
+  if (int rc = ensure_rowbuf(h)) return rc;
+  if (int rc = upload(h, h->rowbuf + h->rb_visc, v.data(), v.size() * sizeof(double))) return rc;
+  h->hs = 1;
+  h->s_exp = s_exp;
+  h->pr = pr;
+  refresh_params(h);
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
   return SLBM_OK;
 }
 

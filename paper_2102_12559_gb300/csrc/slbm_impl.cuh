@@ -132,6 +132,17 @@ struct PondParams {
   int thermal;                  // 1: T from the energy (C_v = D/2); 0: T = T_L
   int twopop;                   // 1: two-population model (g planes, C_v, omega_2)
   R cv, cvm1, omega2;           // C_v, C_v - 1, omega_2 of the two-population model
+  // batched quasi-one-dimensional instances (slbm_set_rows): every row is an
+  // independent instance, uniform across y, with row_len[y] active cells and
+  // fixed end states row_ends[8 y ..] = left {rho, u_x, u_y, T}, right {...}
+  int rows;
+  const int* row_len;
+  const double* row_ends;
+  // viscosity law (two-population model): mu = row_visc[2 y] (T / row_visc[2 y + 1])^s_exp,
+  // omega_1 from mu = (1/omega_1 - 1/2) rho T dt, omega_2 from Pr = 1 / inv_pr
+  int hs;
+  const double* row_visc;
+  R s_exp, inv_pr;
   int P;                        // collocation points per axis
   R reach;                      // largest departure distance allowed, cells
   PondLat<R> lat[2];

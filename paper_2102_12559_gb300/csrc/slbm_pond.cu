@@ -131,6 +131,11 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
                           S* __restrict__ eo, S* __restrict__ lam_out, int x, int y, int* err) {
   const long long c = (long long)x + (long long)p.nx * y;
   R ux = (R)lam[c], uy = (R)lam[p.nc + c], T = (R)lam[2 * p.nc + c];
+  // batched rows: the instance is uniform in y (the y interpolation of a
+  // constant is the constant) and has fixed end states beyond 0 and len
+  const int len = p.rows ? p.row_len[y] : p.nx;
+  const double* ends = p.rows ? p.row_ends + 8 * y : nullptr;
+  const int Py = p.rows ? 1 : p.P;
   R d[N][N];                    // reconstructed deviations, [b][a]
   R dg[N][N];                   // g deviations (two-population model)
   for (int b = 0; b < N; ++b)
@@ -145,7 +150,11 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
       const R vy = st * L.c[b] + uy;
       if (fabs(vy * p.dt) > p.reach) ok = false;
       R ay[kMaxP];
-      const int y0 = stencil<R>(p.P, (R)y - vy * p.dt, ay);
+      int y0 = stencil<R>(p.P, (R)y - vy * p.dt, ay);
+      if (p.rows) {
+        y0 = y;
+        ay[0] = R(1);
+      }
 #pragma unroll 1
       for (int a = 0; a < N; ++a) {
         const R vx = st * L.c[a] + ux;
@@ -154,14 +163,22 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
         const int x0 = stencil<R>(p.P, (R)x - vx * p.dt, ax);
         R acc = R(0), gacc = R(0);
 #pragma unroll 1
-        for (int t = 0; t < p.P; ++t) {
-          const int yi = wrapm(y0 + t, p.ny);
+        for (int t = 0; t < Py; ++t) {
+          const int yi = p.rows ? y : wrapm(y0 + t, p.ny);
           R acc_t = R(0), gacc_t = R(0);
 #pragma unroll 1
           for (int u = 0; u < p.P; ++u) {
-            const int xi = wrapm(x0 + u, p.nx);
-            const long long cs = (long long)xi + (long long)p.nx * yi;
-            const R sux = (R)lam[cs], suy = (R)lam[p.nc + cs], sT = (R)lam[2 * p.nc + cs];
+            int xi = x0 + u;
+            const double* E = nullptr;  // fixed end state of a node beyond the instance
+            if (p.rows) {
+              if (xi < 0) E = ends;
+              else if (xi >= len) E = ends + 4;
+            } else {
+              xi = wrapm(xi, p.nx);
+            }
+            const long long cs = E ? 0 : (long long)xi + (long long)p.nx * yi;
+            const R sux = E ? (R)E[1] : (R)lam[cs], suy = E ? (R)E[2] : (R)lam[p.nc + cs];
+            const R sT = E ? (R)E[3] : (R)lam[2 * p.nc + cs];
             const R r = sqrt(sT) * ist;
             const R dx = (sux - ux) * ist, dy = (suy - uy) * ist;
             const R dTs = (sT - T) / T;                   // r^2 - 1
@@ -171,32 +188,41 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
               gx[j] = basis<N, R>(L, a, r * L.c[j] + dx);
               gy[j] = basis<N, R>(L, b, r * L.c[j] + dy);
             }
-            // G s_s
-            const size_t base = (size_t)(yi + p.G) * p.pitch + (xi + kOX);
-            R v = R(0);
-#pragma unroll
-            for (int k = 0; k < N; ++k) {
-              R row = R(0);
-#pragma unroll
-              for (int j = 0; j < N; ++j) row += gx[j] * (R)f[(size_t)(j + N * k) * p.plane + base];
-              v += gy[k] * row;
-            }
             // G W - W
             const R pxa = dphi1<N, R>(L, a, dx, dTs), pyb = dphi1<N, R>(L, b, dy, dTs);
             const R gw = L.w[a] * pyb + pxa * L.w[b] + pxa * pyb;
-            v += gw;
-            acc_t += ax[u] * v;
-            if (p.twopop) {  // r^2 G e_s + (C_v - 1)(r^2 (G W - W) + (r^2 - 1) W)
-              R vg = R(0);
+            const R Wab = L.w[a] * L.w[b];
+            // G s_s; an end state is rho_b W, so G s_s = (rho_b - 1)(W + G W - W)
+            const size_t base = (size_t)(yi + p.G) * p.pitch + (xi + kOX);
+            R v = R(0);
+            if (E) {
+              v = ((R)E[0] - R(1)) * (Wab + gw);
+            } else {
 #pragma unroll
               for (int k = 0; k < N; ++k) {
                 R row = R(0);
 #pragma unroll
-                for (int j = 0; j < N; ++j) row += gx[j] * (R)e[(size_t)(j + N * k) * p.plane + base];
-                vg += gy[k] * row;
+                for (int j = 0; j < N; ++j) row += gx[j] * (R)f[(size_t)(j + N * k) * p.plane + base];
+                v += gy[k] * row;
+              }
+            }
+            v += gw;
+            acc_t += ax[u] * v;
+            if (p.twopop) {  // r^2 G e_s + (C_v - 1)(r^2 (G W - W) + (r^2 - 1) W)
+              R vg = R(0);
+              if (E) {
+                vg = p.cvm1 * ((R)E[0] - R(1)) * (Wab + gw);
+              } else {
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                  R row = R(0);
+#pragma unroll
+                  for (int j = 0; j < N; ++j) row += gx[j] * (R)e[(size_t)(j + N * k) * p.plane + base];
+                  vg += gy[k] * row;
+                }
               }
               const R r2 = r * r;
-              vg = r2 * vg + p.cvm1 * (r2 * gw + dTs * L.w[a] * L.w[b]);
+              vg = r2 * vg + p.cvm1 * (r2 * gw + dTs * Wab);
               gacc_t += ax[u] * vg;
             }
           }
@@ -287,7 +313,15 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
         qy += cb * ng;
       }
     const R Bx = Axxx + Axyy, By = Axxy + Ayyy;  // A_x.., A_y.. contracted
-    const R w12 = p.omega - p.omega2;
+    R w1 = p.omega, w2 = p.omega2;
+    if (p.hs) {  // mu = (1/omega_1 - 1/2) rho T dt with mu from the viscosity law
+      const R Tabs = T * (R(1) + dT), rho = R(1) + dr;
+      const R mu = (R)p.row_visc[2 * y] * pow(Tabs / (R)p.row_visc[2 * y + 1], p.s_exp);
+      const R tau1 = mu / (rho * Tabs * p.dt) + R(0.5);
+      w1 = R(1) / tau1;
+      w2 = R(1) / ((tau1 - R(0.5)) * p.inv_pr + R(0.5));
+    }
+    const R w12 = w1 - w2;
 #pragma unroll
     for (int b = 0; b < N; ++b)
 #pragma unroll
@@ -301,8 +335,8 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
         const R gst = W * (qx * ca + qy * cb);
         const R eg = p.cvm1 * ((R(1) + dT) * eq + dT * W);
         const size_t o = (size_t)(a + N * b) * p.plane + base;
-        g[o] = (S)(d[b][a] + p.omega * (eq - d[b][a]) + w12 * fst);
-        eo[o] = (S)(dg[b][a] + p.omega * (eg - dg[b][a]) + w12 * gst);
+        g[o] = (S)(d[b][a] + w1 * (eq - d[b][a]) + w12 * fst);
+        eo[o] = (S)(dg[b][a] + w1 * (eg - dg[b][a]) + w12 * gst);
       }
   }
   lam_out[c] = (S)ux;
@@ -319,6 +353,7 @@ k_pond_step(const PondParams<R> p, const S* __restrict__ f0, const S* __restrict
   const int x = blockIdx.x * kTX + threadIdx.x;
   const int y = blockIdx.y * kTY + threadIdx.y;
   if (x >= p.nx || y >= p.ny) return;
+  if (p.rows && x >= p.row_len[y]) return;  // beyond the row's instance
   if (flag[(long long)x + (long long)p.nx * y])
     pond_cell<NH, S, R>(p, p.lat[1], f1, e1, lam, g1, eo1, lam_out, x, y, err);
   else
@@ -554,6 +589,7 @@ k_pond_convert(const PondParams<R> p, S* f0, S* f1, S* e0, S* e1, const S* __res
     if (bits != 3) return;
   }
   if (x >= p.nx || y >= p.ny) return;
+  if (p.rows && x >= p.row_len[y]) return;
   const long long c = (long long)x + (long long)p.nx * y;
   const int k = flag[c] ? 1 : 0;
   pond_convert_cell<NQ, NQQ, S, R>(p, f0, f1, e0, e1, k, (size_t)(y + p.G) * p.pitch + (x + kOX),

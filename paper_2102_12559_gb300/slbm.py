@@ -36,7 +36,8 @@ EXPORTS = [
     "slbm_profile", "slbm_profile_read", "slbm_audit_dense_noalloc", "slbm_last_error",
     "slbm_set_pond", "slbm_get_frame", "slbm_set_frame",
     "slbm_set_indicator", "slbm_indicator_eval",
-    "slbm_set_twopop", "slbm_get_gpops", "slbm_set_gpops",
+    "slbm_set_twopop", "slbm_get_gpops", "slbm_set_gpops", "slbm_set_rows",
+    "slbm_set_viscosity_law",
 ]
 SLBM_PROFILE_KERNELS = 2
 KERNEL_NAMES = ("stream_collide", "post_step")
@@ -107,6 +108,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.slbm_set_twopop.argtypes = [p, d, d]
     L.slbm_get_gpops.argtypes = [p, i, p]
     L.slbm_set_gpops.argtypes = [p, i, p]
+    L.slbm_set_rows.argtypes = [p, p, p]
+    L.slbm_set_viscosity_law.argtypes = [p, p, p, d, d]
     L.slbm_get_frame.argtypes = [p, p, p, p]
     L.slbm_set_frame.argtypes = [p, p, p, p]
     L.slbm_set_indicator.argtypes = [p, p, p, p, p, p, ctypes.c_float, i]
@@ -207,6 +210,19 @@ def slbm_set_pond(h, tol, max_iter):
 
 def slbm_set_twopop(h, cv, tau2):
     _check(load().slbm_set_twopop(h, float(cv), float(tau2)), h)
+
+
+def slbm_set_rows(h, ny, lens, ends):
+    a = np.ascontiguousarray(np.asarray(lens, dtype=np.int32).ravel())
+    b = _f64(ends, 8 * ny)
+    if a.size != ny:
+        raise ValueError("one length per row")
+    _check(load().slbm_set_rows(h, _ptr(a), _ptr(b)), h)
+
+
+def slbm_set_viscosity_law(h, ny, mu1, T1, s_exp, pr):
+    a, b = _f64(mu1, ny), _f64(T1, ny)
+    _check(load().slbm_set_viscosity_law(h, _ptr(a), _ptr(b), float(s_exp), float(pr)), h)
 
 
 def slbm_get_gpops(h, k, Q, n):
@@ -393,6 +409,15 @@ class Solver:
     def set_twopop(self, cv, tau2):
         """Two-population co-moving model (before init_equilibrium)."""
         slbm_set_twopop(self.h, cv, tau2)
+
+    def set_rows(self, lens, ends):
+        """Rows as independent quasi-1-D instances: lengths (ny) and end
+        states (ny, 2, 4) = left / right {rho, u_x, u_y, T}."""
+        slbm_set_rows(self.h, self.ny, lens, np.asarray(ends, dtype=np.float64).reshape(-1))
+
+    def set_viscosity_law(self, mu1, T1, s_exp=0.5, pr=2.0 / 3.0):
+        slbm_set_viscosity_law(self.h, self.ny, np.broadcast_to(mu1, (self.ny,)),
+                               np.broadcast_to(T1, (self.ny,)), s_exp, pr)
 
     def get_gpops(self, k):
         """g populations of lattice k as (ny, nx, Q_k), absolute units."""

@@ -1,0 +1,82 @@
+"""GPU parity of batched quasi-one-dimensional co-moving instances (the shock
+structure setting of Sec. IV.C): every row of the grid an independent
+instance with its own length and fixed end states, two-population model with
+the hard-sphere viscosity law, D2Q16 with D2Q25 inside the shock.  Each row
+is compared with an oracle run of that instance alone (len x 1 grid, periodic
+y, fixed ends).  Inputs: Rankine-Hugoniot end states joined by a tanh ramp,
+short instances (40-64 cells) with a mean free path of 4 cells so the
+relaxation times stay moderate; Mach 1.3-3.
+
+Tolerances: FP64 1e-11 relative L2 on rho, u_x, T per row after 4 steps
+(only rounding order and the frame of the quasi-equilibria differ); FP32
+1e-5; u_y, zero in exact arithmetic, below the same fraction of max |u_x|."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2102_12559_gb300 import workloads as WL
+from paper_2102_12559_gb300 import slbm
+
+pytestmark = pytest.mark.gpu
+
+CV, PR = 1.5, 2.0 / 3.0
+
+
+def instances():
+    b = WL.shock_batch(6, seed=5, mach_range=(1.3, 3.0), len_range=(40, 64), cells_per_mfp=4.0)
+    return b
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def flags_of(inst, nx, w=8):
+    L = inst["len"]
+    x = np.arange(nx)
+    return ((np.abs(x - 0.5 * L) < w) & (x < L)).astype(np.uint8)
+
+
+@pytest.mark.parametrize("precision,tol", [(slbm.SLBM_FP64, 1e-11), (slbm.SLBM_FP32, 1e-5)])
+def test_rows_match_single_instance_oracle(precision, tol):
+    b = instances()
+    nx, ny, steps = 64, len(b), 4
+    g = slbm.Solver(nx, ny, 4, 5, tau=0.7, precision=precision, frame=slbm.SLBM_FRAME_POND)
+    g.set_twopop(CV, 0.8)
+    prof = [WL.shock_profile(i, nx) for i in b]
+    rho = np.stack([p[0] for p in prof]); ux = np.stack([p[1] for p in prof])
+    T = np.stack([p[2] for p in prof])
+    g.init_equilibrium(rho, ux, np.zeros_like(rho), T)
+    ends = np.array([[(i["left"][0], i["left"][1], 0.0, i["left"][2]),
+                      (i["right"][0], i["right"][1], 0.0, i["right"][2])] for i in b])
+    g.set_rows([i["len"] for i in b], ends)
+    g.set_viscosity_law([i["mu1"] for i in b], [i["T1"] for i in b], 0.5, PR)
+    g.set_flags(np.stack([flags_of(i, nx) for i in b]))
+    g.step(steps)
+    gm = g.moments()
+    for r, inst in enumerate(b):
+        L = inst["len"]
+        o = O.Oracle(L, 1, 4, 5, tau=0.7, frame=O.FRAME_POND, periodic=(False, True))
+        o.set_twopop(CV, 0.8)
+        o.set_pond_ends(ends[r, 0], ends[r, 1])
+        o.set_viscosity_law(inst["mu1"], inst["T1"], 0.5, PR)
+        o.init_equilibrium(rho[r:r + 1, :L], ux[r:r + 1, :L], np.zeros((1, L)), T[r:r + 1, :L])
+        o.set_flags(flags_of(inst, nx)[None, :L])
+        o.step(steps)
+        om = o.moments()
+        for q in (0, 1, 3):                                # rho, u_x, T
+            assert rel_l2(gm[q][r, :L], om[q][0]) < tol, (r, q, rel_l2(gm[q][r, :L], om[q][0]))
+        # u_y stays zero up to rounding on both sides
+        assert np.abs(gm[2][r, :L]).max() < tol * np.abs(om[1]).max()
+
+
+def test_rows_rules():
+    g = slbm.Solver(64, 8, 4, 5, tau=0.7, frame=slbm.SLBM_FRAME_POND)
+    ends = np.ones((8, 2, 4))
+    with pytest.raises(slbm.SlbmError):
+        g.set_rows([64, 64, 2, 64, 64, 64, 64, 64], ends)  # shorter than the stencil
+    with pytest.raises(slbm.SlbmError):
+        g.set_viscosity_law(1.0, 1.0)                      # needs the two-population model
+    h = slbm.Solver(64, 8, 4, 5, tau=0.7)
+    with pytest.raises(slbm.SlbmError):
+        h.set_rows([64] * 8, np.ones((8, 2, 4)))          # lattice frame
