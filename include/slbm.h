@@ -317,6 +317,14 @@ SLBM_API int slbm_set_gpops(slbm_t h, int k, const double *in);
  * reconstructed rho and T, and omega_2 from the fixed Prandtl number pr
  * (1/omega_2 - 1/2 = (1/omega_1 - 1/2) / pr).  Host arrays of ny doubles. */
 SLBM_API int slbm_set_rows(slbm_t h, const int *len, const double *ends);
+
+/* Autotuner of the co-moving step kernel (co-moving frames only): times
+ * `reps` launches of the step for each thread-block shape of 256 threads
+ * (32 x 8, 64 x 4, 128 x 2, 256 x 1, 16 x 16) on the current state -- the
+ * kernel reads one buffer and writes the other, so the state is unchanged --
+ * and keeps the fastest; its shape to *bx, *by (either may be NULL).
+ * Synchronises. */
+SLBM_API int slbm_tune(slbm_t h, int reps, int *bx, int *by);
 SLBM_API int slbm_set_viscosity_law(slbm_t h, const double *mu1, const double *T1, double s_exp,
                                     double pr);
 

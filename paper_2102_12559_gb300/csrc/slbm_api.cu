@@ -297,6 +297,7 @@ struct slbm_s {
   double s_exp, pr;
   char* rowbuf;
   size_t rb_len, rb_ends, rb_visc;
+  int pond_bx, pond_by;          // block shape of the co-moving step (slbm_tune)
   Layout lay;
   cudaStream_t st;
   char* ws;
@@ -543,11 +544,9 @@ int pond_convert_band(slbm_s* h, int buf) {
 
 // One co-moving-frame step: predictor-corrector stream-collide, then the
 // interface conversions of the new state when both lattices are in use.
-int pond_step_once(slbm_s* h) {
-  const int b = h->cur, nb = b ^ 1;
+cudaError_t pond_launch(slbm_s* h, int b, int nb) {
   int* err = h->at<int>(h->lay.err);
   cudaError_t e;
-  SLBM_CK(h, mark(h), "trace event");
   if (h->precision == SLBM_FP64)
     e = launch_pond_step<double, double>(
         h->qd, (const double*)h->pops(b, 0), (const double*)h->pops(b, 1),
@@ -560,7 +559,13 @@ int pond_step_once(slbm_s* h) {
         (const float*)h->gp(b, 0), (const float*)h->gp(b, 1), (const float*)h->lam(b),
         (float*)h->pops(nb, 0), (float*)h->pops(nb, 1), (float*)h->gp(nb, 0),
         (float*)h->gp(nb, 1), (float*)h->lam(nb), h->flags(h->fcur), err, h->st);
-  SLBM_CK(h, e, "co-moving step launch");
+  return e;
+}
+
+int pond_step_once(slbm_s* h) {
+  const int b = h->cur, nb = b ^ 1;
+  SLBM_CK(h, mark(h), "trace event");
+  SLBM_CK(h, pond_launch(h, b, nb), "co-moving step launch");
   SLBM_CK(h, mark(h), "trace event");
   if (int rc = pond_convert_band(h, nb)) return rc;
   SLBM_CK(h, mark(h), "trace event");
@@ -611,10 +616,10 @@ int step_once(slbm_s* h) {
   return SLBM_OK;
 }
 
-// Two lattice-frame steps as one CUDA graph launch: the four kernel launches
-// of two step_once calls, captured once per parity state (buffer, flag and
-// mask halves, scheduler and post-step counter parities) on a private stream
-// and replayed on the handle's stream.  After two steps every parity is back
+// Two steps as one CUDA graph launch: the kernel launches of two step_once
+// calls, captured once per parity state (buffer, flag and mask halves,
+// scheduler and post-step counter parities) on a private stream and replayed
+// on the handle's stream.  (Co-moving steps alternate the buffer only.)  After two steps every parity is back
 // where it was, so the replay only advances the counters.  Returns 1 (and
 // stops trying) if the capture is refused, so the caller steps directly.
 int step_pair(slbm_s* h) {
@@ -663,8 +668,10 @@ int step_pair(slbm_s* h) {
   }
   SLBM_CK(h, cudaGraphLaunch(exec, h->st), "graph launch");
   h->steps += 2;
-  h->sc_launches += 2;
-  h->post_launches += 2;
+  if (h->frame == SLBM_FRAME_LATTICE) {
+    h->sc_launches += 2;
+    h->post_launches += 2;
+  }
   return SLBM_OK;
 }
 
@@ -739,6 +746,8 @@ void fill_pond(PondParams<R>& q, const slbm_s* h, const Params<R>& p, const Latt
   q.row_visc = h->rowbuf ? reinterpret_cast<const double*>(h->rowbuf + h->rb_visc) : nullptr;
   q.s_exp = (R)h->s_exp;
   q.inv_pr = (R)(h->hs ? 1.0 / h->pr : 1.0);
+  q.bx = h->pond_bx;
+  q.by = h->pond_by;
   q.P = h->P;
   q.reach = (R)kPondReach;
   for (int k = 0; k < 2; ++k) {
@@ -1153,6 +1162,7 @@ int slbm_set_flags(slbm_t h, const uint8_t* flags) {
     bool any0 = false, any1 = false;
     for (uint8_t v : norm) (v ? any1 : any0) = true;
     h->pond_mixed = any0 && any1;
+    drop_graphs(h);  // the step's kernel set depends on pond_mixed
     if ((rc = pond_convert_band(h, h->cur))) return rc;
     SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
     return SLBM_OK;
@@ -1318,11 +1328,11 @@ int slbm_step(slbm_t h, int n) {
       if (to_eval < chunk) chunk = to_eval;
     }
     int done = 0;
-    // pairs of lattice-frame steps as graph launches once the kernels have
-    // run directly (their one-time attribute and occupancy set-up), unless
-    // tracing needs the per-kernel events
-    const bool graphs = h->frame == SLBM_FRAME_LATTICE && !h->profiling && !h->graphs_off &&
-                        h->sc_launches > 0;
+    // pairs of steps as graph launches once the kernels have run directly
+    // (their one-time attribute and occupancy set-up), unless tracing needs
+    // the per-kernel events
+    const bool graphs = !h->profiling && !h->graphs_off &&
+                        (h->frame == SLBM_FRAME_LATTICE ? h->sc_launches > 0 : h->steps > 0);
     while (graphs && !h->graphs_off && chunk - done >= 2) {
       const int rc = step_pair(h);
       if (rc == 1) break;
@@ -1477,6 +1487,7 @@ int slbm_set_state(slbm_t h, const void* buf, size_t bytes) {
     bool any0 = false, any1 = false;
     for (uint8_t v : fl) (v ? any1 : any0) = true;
     h->pond_mixed = any0 && any1;
+    drop_graphs(h);  // the step's kernel set depends on pond_mixed
     const double* fr =
         (const double*)(p + sizeof(hd) + nc) + nc * (size_t)(h->nlo * h->nlo + h->nhi * h->nhi);
     if ((rc = slbm_set_frame(h, fr, fr + nc, fr + 2 * nc))) return rc;
@@ -1559,6 +1570,54 @@ int slbm_set_viscosity_law(slbm_t h, const double* mu1, const double* T1, double
   h->pr = pr;
   refresh_params(h);
   SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  return SLBM_OK;
+}
+
+int slbm_tune(slbm_t h, int reps, int* bx, int* by) {
+  SLBM_GUARD(h);
+  if (h->frame == SLBM_FRAME_LATTICE)
+    return fail(h, SLBM_EINVAL, "the lattice-frame step has a fixed tile design");
+  if (reps < 1) return fail(h, SLBM_EINVAL, "reps must be >= 1");
+  static const int shapes[5][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {16, 16}};
+  cudaEvent_t ea, eb;
+  SLBM_CK(h, cudaEventCreate(&ea), "event");
+  SLBM_CK(h, cudaEventCreate(&eb), "event");
+  float best = -1.0f;
+  int bi = 0;
+  int rc = SLBM_OK;
+  for (int c = 0; c < 5 && rc == SLBM_OK; ++c) {
+    h->pond_bx = shapes[c][0];
+    h->pond_by = shapes[c][1];
+    refresh_params(h);
+    // the step kernel reads buffer cur and writes the other: repeating it
+    // leaves the state as it was
+    cudaError_t e = pond_launch(h, h->cur, h->cur ^ 1);
+    if (e == cudaSuccess) e = cudaEventRecord(ea, h->st);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = pond_launch(h, h->cur, h->cur ^ 1);
+    if (e == cudaSuccess) e = cudaEventRecord(eb, h->st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(eb);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ea, eb);
+    if (e != cudaSuccess) {
+      rc = fail(h, SLBM_ECUDA, "tuning launch", e);
+      break;
+    }
+    if (best < 0.0f || ms < best) {
+      best = ms;
+      bi = c;
+    }
+  }
+  cudaEventDestroy(ea);
+  cudaEventDestroy(eb);
+  if (rc) return rc;
+  h->pond_bx = shapes[bi][0];
+  h->pond_by = shapes[bi][1];
+  refresh_params(h);
+  // the timing launches may have flagged unconverged updates of the scratch buffer
+  SLBM_CK(h, cudaMemsetAsync(h->at<int>(h->lay.err), 0, sizeof(int), h->st), "error word clear");
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  if (bx) *bx = h->pond_bx;
+  if (by) *by = h->pond_by;
   return SLBM_OK;
 }
 

@@ -143,6 +143,7 @@ struct PondParams {
   int hs;
   const double* row_visc;
   R s_exp, inv_pr;
+  int bx, by;                   // thread-block shape of the step kernel (bx * by = 256)
   int P;                        // collocation points per axis
   R reach;                      // largest departure distance allowed, cells
   PondLat<R> lat[2];

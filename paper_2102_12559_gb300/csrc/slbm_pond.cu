@@ -350,8 +350,9 @@ k_pond_step(const PondParams<R> p, const S* __restrict__ f0, const S* __restrict
             const S* __restrict__ e0, const S* __restrict__ e1, const S* __restrict__ lam,
             S* __restrict__ g0, S* __restrict__ g1, S* __restrict__ eo0, S* __restrict__ eo1,
             S* __restrict__ lam_out, const uint8_t* __restrict__ flag, int* err) {
-  const int x = blockIdx.x * kTX + threadIdx.x;
-  const int y = blockIdx.y * kTY + threadIdx.y;
+  // one thread per cell; the block shape is a tuning choice (p.bx x p.by)
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= p.nx || y >= p.ny) return;
   if (p.rows && x >= p.row_len[y]) return;  // beyond the row's instance
   if (flag[(long long)x + (long long)p.nx * y])
@@ -630,8 +631,11 @@ template <int NL, int NH, class S, class R>
 cudaError_t step_pair(const PondParams<R>& p, const S* f0, const S* f1, const S* e0, const S* e1,
                       const S* lam, S* g0, S* g1, S* eo0, S* eo1, S* lam_out, const uint8_t* flag,
                       int* err, cudaStream_t st) {
-  k_pond_step<NL, NH, S, R><<<tile_grid(p.nx, p.ny), dim3(kTX, kTY), 0, st>>>(
-      p, f0, f1, e0, e1, lam, g0, g1, eo0, eo1, lam_out, flag, err);
+  const int bx = p.bx > 0 ? p.bx : kTX, by = p.bx > 0 ? p.by : kTY;
+  if (bx * by != kThreads) return cudaErrorInvalidConfiguration;
+  const dim3 grid((p.nx + bx - 1) / bx, (p.ny + by - 1) / by);
+  k_pond_step<NL, NH, S, R><<<grid, dim3(bx, by), 0, st>>>(p, f0, f1, e0, e1, lam, g0, g1, eo0,
+                                                           eo1, lam_out, flag, err);
   return cudaGetLastError();
 }
 

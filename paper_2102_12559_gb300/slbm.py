@@ -37,7 +37,7 @@ EXPORTS = [
     "slbm_set_pond", "slbm_get_frame", "slbm_set_frame",
     "slbm_set_indicator", "slbm_indicator_eval",
     "slbm_set_twopop", "slbm_get_gpops", "slbm_set_gpops", "slbm_set_rows",
-    "slbm_set_viscosity_law",
+    "slbm_set_viscosity_law", "slbm_tune",
 ]
 SLBM_PROFILE_KERNELS = 2
 KERNEL_NAMES = ("stream_collide", "post_step")
@@ -110,6 +110,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.slbm_set_gpops.argtypes = [p, i, p]
     L.slbm_set_rows.argtypes = [p, p, p]
     L.slbm_set_viscosity_law.argtypes = [p, p, p, d, d]
+    L.slbm_tune.argtypes = [p, i, p, p]
     L.slbm_get_frame.argtypes = [p, p, p, p]
     L.slbm_set_frame.argtypes = [p, p, p, p]
     L.slbm_set_indicator.argtypes = [p, p, p, p, p, p, ctypes.c_float, i]
@@ -223,6 +224,12 @@ def slbm_set_rows(h, ny, lens, ends):
 def slbm_set_viscosity_law(h, ny, mu1, T1, s_exp, pr):
     a, b = _f64(mu1, ny), _f64(T1, ny)
     _check(load().slbm_set_viscosity_law(h, _ptr(a), _ptr(b), float(s_exp), float(pr)), h)
+
+
+def slbm_tune(h, reps):
+    bx, by = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().slbm_tune(h, int(reps), ctypes.byref(bx), ctypes.byref(by)), h)
+    return bx.value, by.value
 
 
 def slbm_get_gpops(h, k, Q, n):
@@ -418,6 +425,10 @@ class Solver:
     def set_viscosity_law(self, mu1, T1, s_exp=0.5, pr=2.0 / 3.0):
         slbm_set_viscosity_law(self.h, self.ny, np.broadcast_to(mu1, (self.ny,)),
                                np.broadcast_to(T1, (self.ny,)), s_exp, pr)
+
+    def tune(self, reps=5):
+        """Pick the fastest block shape of the co-moving step; returns it."""
+        return slbm_tune(self.h, reps)
 
     def get_gpops(self, k):
         """g populations of lattice k as (ny, nx, Q_k), absolute units."""
