@@ -593,6 +593,16 @@ k_pond_convert(const PondParams<R> p, S* f0, S* f1, S* e0, S* e1, const S* __res
   if (p.rows && x >= p.row_len[y]) return;
   const long long c = (long long)x + (long long)p.nx * y;
   const int k = flag[c] ? 1 : 0;
+  if (mask && p.rows) {
+    // a row reads only itself: convert only cells that a cell of the other
+    // lattice within the largest departure plus the stencil half-width reads
+    const int B = (int)p.reach + (p.P + 1) / 2;
+    const int lo = max(0, x - B), hi = min(p.row_len[y] - 1, x + B);
+    bool other = false;
+    for (int xi = lo; xi <= hi && !other; ++xi)
+      other = (flag[(long long)xi + (long long)p.nx * y] ? 1 : 0) != k;
+    if (!other) return;
+  }
   pond_convert_cell<NQ, NQQ, S, R>(p, f0, f1, e0, e1, k, (size_t)(y + p.G) * p.pitch + (x + kOX),
                                    lam, c);
 }
