@@ -328,6 +328,16 @@ SLBM_API int slbm_tune(slbm_t h, int reps, int *bx, int *by);
 SLBM_API int slbm_set_viscosity_law(slbm_t h, const double *mu1, const double *T1, double s_exp,
                                     double pr);
 
+/* Knudsen refinement criterion of Sec. IV.C on batched rows (needs slbm_set_rows,
+ * slbm_set_twopop and slbm_set_viscosity_law): a cell is high-order iff
+ * Kn = lambda |d rho / dx| / rho > thr, with central differences (the end
+ * states' density beyond the ends) and the local hard-sphere mean free path
+ * lambda = 16 / (5 sqrt(2 pi gamma)) mu a / p (mu from the row's law,
+ * a = sqrt(gamma T), p = rho T, gamma = (C_v + 1) / C_v).  Applied at once and
+ * after every `interval` steps of slbm_step; flipped cells are lifted or
+ * projected as by slbm_set_flags. */
+SLBM_API int slbm_set_kn_criterion(slbm_t h, double thr, int interval);
+
 /* Per-kernel timing (tracing).  slbm_profile(h, 1) clears previous records
  * and starts bracketing every kernel slbm_step launches with CUDA events on
  * the handle's stream; slbm_profile(h, 0) stops.  slbm_profile_read()

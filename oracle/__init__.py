@@ -100,6 +100,7 @@ def lib():
         L.orc_set_twopop.argtypes = [p, d, d]
         L.orc_set_pond_ends.argtypes = [p, p, p]
         L.orc_set_viscosity_law.argtypes = [p, d, d, d, d]
+        L.orc_set_kn_criterion.argtypes = [p, d, i]
         L.orc_get_gpops.argtypes = [p, i, p]
         L.orc_set_gpops.argtypes = [p, i, p]
     return _lib
@@ -249,6 +250,10 @@ class Oracle:
         """mu = mu1 (T / T1)^s_exp and fixed Pr (two-population model)."""
         _check(lib().orc_set_viscosity_law(self._h, float(mu1), float(T1), float(s_exp),
                                            float(pr)), "set_viscosity_law")
+
+    def set_kn_criterion(self, thr: float, interval: int):
+        """Knudsen refinement (Sec. IV.C) at once and every `interval` steps."""
+        _check(lib().orc_set_kn_criterion(self._h, float(thr), int(interval)), "set_kn_criterion")
 
     def get_gpops(self, k: int) -> np.ndarray:
         """g populations of lattice k, shape (ny, nx, Q_k), absolute units."""

@@ -488,6 +488,10 @@ typedef struct {
      * omega_1 from mu = (1/omega_1 - 1/2) rho T dt, Pr fixed */
     int hs;
     double mu1, T1, s_exp, pr;
+    /* Knudsen refinement criterion (Sec. IV.C): every kn_interval steps */
+    int kn;
+    double kn_thr;
+    int kn_interval;
 } orc_t;
 
 static long cidx(const orc_t *s, long x, long y) { return x + (long)s->nx * y; }
@@ -1037,6 +1041,40 @@ static void reset_memo(orc_t *s)
     }
 }
 
+/* Knudsen refinement criterion of Sec. IV.C on a quasi-one-dimensional
+ * instance: Kn = lambda / L with L = |rho / (d rho / dx)| (central
+ * differences, the fixed end states beyond the ends), the local mean free
+ * path of hard spheres lambda = 16 / (5 sqrt(2 pi gamma)) mu a / p with
+ * mu = mu1 (T / T1)^s, a = sqrt(gamma T), p = rho T, gamma = (C_v + 1) / C_v;
+ * high-order iff Kn > thr, flipped cells lifted or projected. */
+static void apply_kn(orc_t *s)
+{
+    long nc = (long)s->nx * s->ny;
+    double *rho = (double *)malloc(sizeof(double) * nc), *T = (double *)malloc(sizeof(double) * nc);
+    uint8_t *fl = (uint8_t *)malloc(nc);
+    if (!rho || !T || !fl) { free(rho); free(T); free(fl); return; }
+    for (long c = 0; c < nc; ++c) {
+        double st[4];
+        node_state(s, c, st);
+        rho[c] = st[0];
+        T[c] = st[3];
+    }
+    double gam = (s->cv + 1.0) / s->cv;
+    for (long y = 0; y < s->ny; ++y)
+        for (long x = 0; x < s->nx; ++x) {
+            long c = cidx(s, x, y);
+            double rl = x > 0 ? rho[c - 1] : s->ends[0][0];
+            double rr = x < s->nx - 1 ? rho[c + 1] : s->ends[1][0];
+            double drdx = 0.5 * (rr - rl);
+            double mu = s->mu1 * pow(T[c] / s->T1, s->s_exp);
+            double lam = 16.0 / (5.0 * sqrt(2.0 * 3.14159265358979323846 * gam)) * mu * sqrt(gam * T[c]) / (rho[c] * T[c]);
+            double kn = lam * fabs(drdx) / rho[c];
+            fl[c] = kn > s->kn_thr ? 1 : 0;
+        }
+    orc_set_flags(s, fl);
+    free(rho); free(T); free(fl);
+}
+
 /* Advance n time steps. */
 int orc_step(orc_t *s, int n)
 {
@@ -1075,6 +1113,7 @@ int orc_step(orc_t *s, int n)
         }
         if (s->frame) { double *t = s->lam; s->lam = glam; glam = t; }
         if (s->crit_kind == 1) apply_criterion(s);   /* flags for the next step */
+        if (s->kn && (s->steps + 1) % s->kn_interval == 0) apply_kn(s);
         s->steps++;
     }
     free(g[0]);
@@ -1273,5 +1312,17 @@ int orc_set_viscosity_law(orc_t *s, double mu1, double T1, double s_exp, double 
     s->T1 = T1;
     s->s_exp = s_exp;
     s->pr = pr;
+    return 0;
+}
+
+/* Knudsen refinement criterion (apply_kn) every `interval` steps, and at once;
+ * needs the viscosity law and fixed end states. */
+int orc_set_kn_criterion(orc_t *s, double thr, int interval)
+{
+    if (!s->hs || !s->ends_set || interval < 1 || !(thr > 0.0)) return -1;
+    s->kn = 1;
+    s->kn_thr = thr;
+    s->kn_interval = interval;
+    apply_kn(s);
     return 0;
 }

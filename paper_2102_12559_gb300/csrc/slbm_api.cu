@@ -298,6 +298,8 @@ struct slbm_s {
   char* rowbuf;
   size_t rb_len, rb_ends, rb_visc;
   int pond_bx, pond_by;          // block shape of the co-moving step (slbm_tune)
+  int kn_on, kn_interval;        // Knudsen refinement of batched rows (slbm_set_kn_criterion)
+  double kn_thr;
   Layout lay;
   cudaStream_t st;
   char* ws;
@@ -1316,6 +1318,64 @@ int slbm_set_boundary(slbm_t h, int side, int kind, const double* rho, const dou
   return SLBM_OK;
 }
 
+namespace {
+// Knudsen criterion on the current buffer: new flags into the temporary
+// plane, every cell's other lattice from its current one (flipped cells take
+// it as their new native vector), then the new flags, masks and band.
+int apply_kn(slbm_s* h) {
+  uint8_t* tmp = h->at<uint8_t>(h->lay.flag_tmp);
+  cudaError_t e =
+      h->precision == SLBM_FP64
+          ? launch_pond_kn<double, double>(h->qd, (const double*)h->pops(h->cur, 0),
+                                           (const double*)h->pops(h->cur, 1),
+                                           (const double*)h->gp(h->cur, 0),
+                                           (const double*)h->gp(h->cur, 1),
+                                           (const double*)h->lam(h->cur), h->flags(h->fcur),
+                                           h->kn_thr, tmp, h->st)
+          : launch_pond_kn<float, float>(h->qf, (const float*)h->pops(h->cur, 0),
+                                         (const float*)h->pops(h->cur, 1),
+                                         (const float*)h->gp(h->cur, 0),
+                                         (const float*)h->gp(h->cur, 1),
+                                         (const float*)h->lam(h->cur), h->flags(h->fcur),
+                                         h->kn_thr, tmp, h->st);
+  SLBM_CK(h, e, "Knudsen criterion launch");
+  e = h->precision == SLBM_FP64
+          ? launch_pond_convert<double, double>(h->qd, (double*)h->pops(h->cur, 0),
+                                                (double*)h->pops(h->cur, 1),
+                                                (double*)h->gp(h->cur, 0),
+                                                (double*)h->gp(h->cur, 1),
+                                                (const double*)h->lam(h->cur), h->flags(h->fcur),
+                                                nullptr, h->st)
+          : launch_pond_convert<float, float>(h->qf, (float*)h->pops(h->cur, 0),
+                                              (float*)h->pops(h->cur, 1), (float*)h->gp(h->cur, 0),
+                                              (float*)h->gp(h->cur, 1),
+                                              (const float*)h->lam(h->cur), h->flags(h->fcur),
+                                              nullptr, h->st);
+  SLBM_CK(h, e, "co-moving conversion launch");
+  SLBM_CK(h, cudaMemcpyAsync(h->flags(h->fcur), tmp, h->ncell(), cudaMemcpyDeviceToDevice, h->st),
+          "flag copy");
+  SLBM_CK(h, launch_pond_masks(h->g.nx, h->g.ny, h->flags(h->fcur),
+                               h->at<uint8_t>(h->lay.tile_mask[0]), h->st),
+          "mask launch");
+  return pond_convert_band(h, h->cur);
+}
+}  // namespace
+
+int slbm_set_kn_criterion(slbm_t h, double thr, int interval) {
+  SLBM_GUARD(h);
+  if (!h->rows || !h->hs || !h->twopop)
+    return fail(h, SLBM_EINVAL, "the Knudsen criterion needs batched rows and the viscosity law");
+  if (!(thr > 0.0) || interval < 1) return fail(h, SLBM_EINVAL, "need thr > 0 and interval >= 1");
+  h->kn_on = 1;
+  h->kn_thr = thr;
+  h->kn_interval = interval;
+  h->pond_mixed = 1;  // flags may change every interval: keep the band conversion on
+  drop_graphs(h);
+  if (int rc = apply_kn(h)) return rc;
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  return check_device_error(h);
+}
+
 int slbm_step(slbm_t h, int n) {
   SLBM_GUARD(h);
   if (n < 0) return fail(h, SLBM_EINVAL, "n must be >= 0");
@@ -1325,6 +1385,10 @@ int slbm_step(slbm_t h, int n) {
     int chunk = n - s;
     if (h->crit == SLBM_CRIT_MLP) {
       const int to_eval = h->ind_interval - (int)(h->steps % h->ind_interval);
+      if (to_eval < chunk) chunk = to_eval;
+    }
+    if (h->kn_on) {
+      const int to_eval = h->kn_interval - (int)(h->steps % h->kn_interval);
       if (to_eval < chunk) chunk = to_eval;
     }
     int done = 0;
@@ -1346,6 +1410,10 @@ int slbm_step(slbm_t h, int n) {
     s += chunk;
     if (h->crit == SLBM_CRIT_MLP && h->steps % h->ind_interval == 0) {
       const int rc = apply_indicator(h);
+      if (rc) return rc;
+    }
+    if (h->kn_on && h->steps % h->kn_interval == 0) {
+      const int rc = apply_kn(h);
       if (rc) return rc;
     }
   }

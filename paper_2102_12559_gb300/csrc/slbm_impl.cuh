@@ -192,6 +192,11 @@ cudaError_t launch_pond_convert(const PondParams<R>& p, S* f0, S* f1, S* e0, S* 
 template <class S, class R>
 cudaError_t launch_pond_frame_io(const PondParams<R>& p, S* lam, double* ux, double* uy,
                                  double* T, int unpack, cudaStream_t st);
+// Knudsen refinement criterion on batched rows (Sec. IV.C): new flags to out.
+template <class S, class R>
+cudaError_t launch_pond_kn(const PondParams<R>& p, const S* f0, const S* f1, const S* e0,
+                           const S* e1, const S* lam, const uint8_t* flag, double thr,
+                           uint8_t* out, cudaStream_t st);
 // Plane i of lattice k's g planes e to / from absolute g = T_frame (s + (C_v - 1) W_i)
 // (nc doubles, cell-major within the plane).
 template <class S, class R>

@@ -619,6 +619,72 @@ k_pond_frame_io(const PondParams<R> p, S* lam, double* ux, double* uy, double* T
   }
 }
 
+// rho and absolute T of a cell from its own lattice (N nodes per axis), its
+// g planes (two-population model) and its frame (as the step's moments).
+template <int N, class S, class R>
+__device__ __forceinline__ void cell_rho_T(const PondParams<R>& p, const PondLat<R>& L,
+                                           const S* f, const S* e, const S* lam, long long c,
+                                           size_t base, R& rho, R& T) {
+  R s0 = R(0), sx = R(0), sy = R(0), s2 = R(0), sg = R(0);
+#pragma unroll
+  for (int b = 0; b < N; ++b)
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+      const size_t o = (size_t)(a + N * b) * p.plane + base;
+      const R v = (R)f[o];
+      s0 += v;
+      sx += L.c[a] * v;
+      sy += L.c[b] * v;
+      s2 += (L.c[a] * L.c[a] + L.c[b] * L.c[b] - R(2)) * v;
+      if (p.twopop) sg += (R)e[o];
+    }
+  rho = R(1) + s0;
+  const R s1x = sx / rho, s1y = sy / rho;
+  const R dT = p.twopop ? (R(0.5) * s2 - R(0.5) * rho * (s1x * s1x + s1y * s1y) + sg - p.cvm1 * s0) /
+                              (rho * p.cv)
+                        : (s2 - rho * (s1x * s1x + s1y * s1y)) / (R(2) * rho);
+  T = (R)lam[2 * p.nc + c] * (R(1) + dT);
+}
+
+// Knudsen refinement criterion of Sec. IV.C on batched rows: Kn = lambda / L,
+// L = |rho / (d rho / dx)| by central differences (the end states' density
+// beyond the ends), lambda = 16 / (5 sqrt(2 pi gamma)) mu a / p of hard
+// spheres with the row's viscosity law, a = sqrt(gamma T), p = rho T; the new
+// flag is Kn > thr (cells beyond the instance keep theirs).
+template <int NL, int NH, class S, class R>
+__global__ void __launch_bounds__(kThreads)
+k_pond_kn(const PondParams<R> p, const S* __restrict__ f0, const S* __restrict__ f1,
+          const S* __restrict__ e0, const S* __restrict__ e1, const S* __restrict__ lam,
+          const uint8_t* __restrict__ flag, R thr, uint8_t* __restrict__ out) {
+  const int x = blockIdx.x * kTX + threadIdx.x;
+  const int y = blockIdx.y * kTY + threadIdx.y;
+  if (x >= p.nx || y >= p.ny) return;
+  const long long c = (long long)x + (long long)p.nx * y;
+  const int len = p.row_len[y];
+  if (x >= len) {
+    out[c] = flag[c];
+    return;
+  }
+  auto state = [&](int xi, R& rho, R& T) {
+    const long long ci = (long long)xi + (long long)p.nx * y;
+    const size_t base = (size_t)(y + p.G) * p.pitch + (xi + kOX);
+    if (flag[ci]) cell_rho_T<NH, S, R>(p, p.lat[1], f1, e1, lam, ci, base, rho, T);
+    else cell_rho_T<NL, S, R>(p, p.lat[0], f0, e0, lam, ci, base, rho, T);
+  };
+  R rho, T, rl, rr, Tn;
+  state(x, rho, T);
+  if (x > 0) state(x - 1, rl, Tn);
+  else rl = (R)p.row_ends[8 * y];
+  if (x < len - 1) state(x + 1, rr, Tn);
+  else rr = (R)p.row_ends[8 * y + 4];
+  const R gam = (p.cv + R(1)) / p.cv;
+  const R mu = (R)p.row_visc[2 * y] * pow(T / (R)p.row_visc[2 * y + 1], p.s_exp);
+  const R lmf = R(16) / (R(5) * sqrt(R(2) * R(3.14159265358979323846) * gam)) * mu *
+                sqrt(gam * T) / (rho * T);
+  const R kn = lmf * fabs(R(0.5) * (rr - rl)) / rho;
+  out[c] = kn > thr ? 1 : 0;
+}
+
 // Plane i of lattice k's g planes to / from absolute g (cell-major doubles).
 template <class S, class R>
 __global__ void __launch_bounds__(kThreads)
@@ -699,6 +765,19 @@ cudaError_t launch_pond_convert(const PondParams<R>& p, S* f0, S* f1, S* e0, S* 
 }
 
 template <class S, class R>
+cudaError_t launch_pond_kn(const PondParams<R>& p, const S* f0, const S* f1, const S* e0,
+                           const S* e1, const S* lam, const uint8_t* flag, double thr,
+                           uint8_t* out, cudaStream_t st) {
+  const int lo = p.lat[0].n, hi = p.lat[1].n;
+  const dim3 g = tile_grid(p.nx, p.ny), b(kTX, kTY);
+  if (lo == 3 && hi == 4) k_pond_kn<3, 4, S, R><<<g, b, 0, st>>>(p, f0, f1, e0, e1, lam, flag, (R)thr, out);
+  else if (lo == 3 && hi == 5) k_pond_kn<3, 5, S, R><<<g, b, 0, st>>>(p, f0, f1, e0, e1, lam, flag, (R)thr, out);
+  else if (lo == 4 && hi == 5) k_pond_kn<4, 5, S, R><<<g, b, 0, st>>>(p, f0, f1, e0, e1, lam, flag, (R)thr, out);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+template <class S, class R>
 cudaError_t launch_pond_gio(const PondParams<R>& p, int k, int i, S* e, const S* lam, double* buf,
                             int unpack, cudaStream_t st) {
   const unsigned blocks = (unsigned)((p.nc + kThreads - 1) / kThreads);
@@ -727,7 +806,10 @@ cudaError_t launch_pond_frame_io(const PondParams<R>& p, S* lam, double* ux, dou
   template cudaError_t launch_pond_frame_io<S, R>(const PondParams<R>&, S*, double*, double*,  \
                                                   double*, int, cudaStream_t);                 \
   template cudaError_t launch_pond_gio<S, R>(const PondParams<R>&, int, int, S*, const S*,     \
-                                             double*, int, cudaStream_t);
+                                             double*, int, cudaStream_t);                     \
+  template cudaError_t launch_pond_kn<S, R>(const PondParams<R>&, const S*, const S*,          \
+                                            const S*, const S*, const S*, const uint8_t*,      \
+                                            double, uint8_t*, cudaStream_t);
 SLBM_POND_INST(float, float)
 SLBM_POND_INST(double, double)
 #undef SLBM_POND_INST

@@ -37,7 +37,7 @@ EXPORTS = [
     "slbm_set_pond", "slbm_get_frame", "slbm_set_frame",
     "slbm_set_indicator", "slbm_indicator_eval",
     "slbm_set_twopop", "slbm_get_gpops", "slbm_set_gpops", "slbm_set_rows",
-    "slbm_set_viscosity_law", "slbm_tune",
+    "slbm_set_viscosity_law", "slbm_tune", "slbm_set_kn_criterion",
 ]
 SLBM_PROFILE_KERNELS = 2
 KERNEL_NAMES = ("stream_collide", "post_step")
@@ -111,6 +111,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.slbm_set_rows.argtypes = [p, p, p]
     L.slbm_set_viscosity_law.argtypes = [p, p, p, d, d]
     L.slbm_tune.argtypes = [p, i, p, p]
+    L.slbm_set_kn_criterion.argtypes = [p, d, i]
     L.slbm_get_frame.argtypes = [p, p, p, p]
     L.slbm_set_frame.argtypes = [p, p, p, p]
     L.slbm_set_indicator.argtypes = [p, p, p, p, p, p, ctypes.c_float, i]
@@ -425,6 +426,10 @@ class Solver:
     def set_viscosity_law(self, mu1, T1, s_exp=0.5, pr=2.0 / 3.0):
         slbm_set_viscosity_law(self.h, self.ny, np.broadcast_to(mu1, (self.ny,)),
                                np.broadcast_to(T1, (self.ny,)), s_exp, pr)
+
+    def set_kn_criterion(self, thr=0.02, interval=10):
+        """Knudsen refinement of batched rows, at once and every `interval` steps."""
+        _check(load().slbm_set_kn_criterion(self.h, float(thr), int(interval)), self.h)
 
     def tune(self, reps=5):
         """Pick the fastest block shape of the co-moving step; returns it."""

@@ -116,3 +116,33 @@ def test_tuner_keeps_the_state_and_the_results():
         np.testing.assert_array_equal(x, y)
     for k in (0, 1):
         np.testing.assert_array_equal(a.get_gpops(k), c.get_gpops(k))
+
+
+@pytest.mark.parametrize("precision,tol", [(slbm.SLBM_FP64, 1e-11), (slbm.SLBM_FP32, 1e-5)])
+def test_knudsen_refinement_matches_oracle(precision, tol):
+    """Knudsen criterion (Kn > 0.02, every 2 steps) on the batch against the
+    oracle's criterion on each instance: identical flags, moments within the
+    tolerance after 6 steps."""
+    b = instances()
+    nx, steps = 64, 6
+    g = batch_solver(b, nx, precision)
+    g.set_flags(np.zeros((len(b), nx), np.uint8))
+    g.set_kn_criterion(0.02, 2)
+    g.step(steps)
+    gm, gf = g.moments(), g.get_flags()
+    assert gf.sum() > 0
+    for r, inst in enumerate(b):
+        L = inst["len"]
+        rho, ux, T = WL.shock_profile(inst, nx)
+        o = O.Oracle(L, 1, 4, 5, tau=0.7, frame=O.FRAME_POND, periodic=(False, True))
+        o.set_twopop(CV, 0.8)
+        o.set_pond_ends((inst["left"][0], inst["left"][1], 0.0, inst["left"][2]),
+                        (inst["right"][0], inst["right"][1], 0.0, inst["right"][2]))
+        o.set_viscosity_law(inst["mu1"], inst["T1"], 0.5, PR)
+        o.init_equilibrium(rho[None, :L], ux[None, :L], np.zeros((1, L)), T[None, :L])
+        o.set_kn_criterion(0.02, 2)
+        o.step(steps)
+        np.testing.assert_array_equal(gf[r, :L], o.get_flags()[0])
+        om = o.moments()
+        for q in (0, 1, 3):
+            assert rel_l2(gm[q][r, :L], om[q][0]) < tol

@@ -263,3 +263,31 @@ def test_rankine_hugoniot_states():
                  (r1 * u1 ** 2 + r1 * t1, r2 * u2 ** 2 + r2 * t2),
                  (u1 * (r1 * (cv * t1 + u1 ** 2 / 2) + r1 * t1), u2 * (r2 * (cv * t2 + u2 ** 2 / 2) + r2 * t2))):
         assert abs(a - b) < 1e-12 * abs(a)
+
+
+@pytest.mark.parametrize("L,refined", [(2000.0, True), (3000.0, False)])
+def test_knudsen_criterion_against_the_mean_free_path(L, refined):
+    """An instance built with an upstream mean free path of 50 cells
+    (mu_1 from lambda_1, as the shock inputs do) and a density slope 1/L
+    at rho = 1, T = T_1 has Kn = 50 / L there: refined at Kn = 0.025 > 0.02,
+    not at 0.0167; a uniform state is never refined."""
+    nx = 201
+    inst = WL.shock_batch(1, seed=1, mach_range=(1.5, 1.5), len_range=(nx, nx))[0]
+    x = np.arange(nx)[None, :].astype(float)
+    rho = 1 + (x - 100) / L
+    o = O.Oracle(nx, 1, 4, 5, tau=0.7, frame=O.FRAME_POND, periodic=(False, True))
+    o.set_twopop(1.5, 0.8)
+    o.set_pond_ends((rho[0, 0] - 1 / L, 0.0, 0.0, 1.0), (rho[0, -1] + 1 / L, 0.0, 0.0, 1.0))
+    o.set_viscosity_law(inst["mu1"], 1.0, 0.5, 2 / 3)
+    o.init_equilibrium(rho, 0 * rho, 0 * rho, 1 + 0 * rho)
+    o.set_kn_criterion(0.02, 1)
+    assert bool(o.get_flags()[0, 100]) == refined
+    u = O.Oracle(nx, 1, 4, 5, tau=0.7, frame=O.FRAME_POND, periodic=(False, True))
+    u.set_twopop(1.5, 0.8)
+    u.set_pond_ends((1.0, 0.3, 0.0, 1.0), (1.0, 0.3, 0.0, 1.0))
+    u.set_viscosity_law(inst["mu1"], 1.0, 0.5, 2 / 3)
+    one = np.ones((1, nx))
+    u.init_equilibrium(one, 0.3 * one, 0 * one, one)
+    u.set_kn_criterion(0.02, 1)
+    u.step(2)
+    assert u.get_flags().sum() == 0
