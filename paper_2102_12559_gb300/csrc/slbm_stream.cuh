@@ -43,6 +43,9 @@ template <class S>
 struct StageGeom {
   static constexpr int xh = sizeof(S) == 2 ? 8 : 4;
   static constexpr int txp = kTX + 2 * xh;
+  // resident CTAs per SM the kernel is compiled for: FP16 stages are half the
+  // size, so three CTAs fit in shared memory (and 80 registers a thread)
+  static constexpr int min_blocks = sizeof(S) == 2 ? 3 : 2;
 };
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s bound on an mbarrier wait
 
@@ -332,7 +335,7 @@ constexpr int kRing = 4;  // decided items visible to every thread: j .. j + 3
 // load while the current item computes); the threads compute the item's
 // cells, compacted onto the leading threads, then free the stage.
 template <int NL, int NH, int P, class S, class R>
-__global__ void __launch_bounds__(kTX * kTY, 2)
+__global__ void __launch_bounds__(kTX * kTY, StageGeom<S>::min_blocks)
 k_stream_collide(const Params<R> p, const __grid_constant__ CUtensorMap tm0,
                  const __grid_constant__ CUtensorMap tm1, S* __restrict__ fout0,
                  S* __restrict__ fout1, const uint8_t* __restrict__ flag_cur,
