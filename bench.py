@@ -167,6 +167,22 @@ def cpu_baseline(J, tau):
                       f"single thread, {el:.1f} s"}
 
 
+def max_over_ranks(values, dist, device):
+    """The per-rank timings reduced to their maximum over ranks (every rank
+    gets the result); dist None: a single process."""
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def job_mlups(world: int, ncell: int, steps: int, ms: float) -> float:
+    """Whole-job throughput of `world` replicas, each advancing `ncell` cells
+    `steps` times in `ms` milliseconds (the slowest rank's time)."""
+    return world * ncell * steps / (ms * 1e-3) / 1e6
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 CPU oracle, each step a bounded sample of the
     workload (the post-collision update of a fixed random sample of cells)."""
@@ -566,17 +582,14 @@ def main():
     h2d = NX * NY * (3 * 8) + 2 * NY * 8 + 2 * 3 * NX * 8
     d2h = NX * NY * 3 * 8
 
-    t_local = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    total_ms, e2e_ms = float(t_local[0]), float(t_local[1])
+    total_ms, e2e_ms = max_over_ranks((total_ms, e2e_ms), dist, dev)
     if rank != 0:
         dist.destroy_process_group()
         return
 
     ncell = NX * NY
-    value = world * ncell * args.steps / (total_ms * 1e-3) / 1e6
-    e2e_value = world * ncell * e2e_steps / (e2e_ms * 1e-3) / 1e6
+    value = job_mlups(world, ncell, args.steps, total_ms)
+    e2e_value = job_mlups(world, ncell, e2e_steps, e2e_ms)
     nhi = 0.5 * (int(flags_before.sum()) + int(flags_after.sum()))
     # algorithmic bytes of one stream-collide launch (FP32): read + write Q
     # populations per cell, read the flag, write the next flag
