@@ -145,6 +145,90 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
   for (int it = 0; it < p.maxit; ++it) {
     if (!(T > R(0)) || !isfinite(ux) || !isfinite(uy)) { ok = false; break; }
     const R st = sqrt(T), ist = R(1) / st;
+    if (p.rows) {
+      // batched rows: the collocation nodes of population (a, b) lie on the
+      // cell's row and depend on a only, so per (a, node) the node's frame
+      // terms, the x basis and the x contraction sum_j G_x[j] s[j][k] are
+      // shared by every b (same arithmetic, fewer evaluations)
+#pragma unroll 1
+      for (int b = 0; b < N; ++b)
+        if (fabs((st * L.c[b] + uy) * p.dt) > p.reach) ok = false;
+#pragma unroll 1
+      for (int a = 0; a < N; ++a) {
+        const R vx = st * L.c[a] + ux;
+        if (fabs(vx * p.dt) > p.reach) ok = false;
+        R ax[kMaxP];
+        const int x0 = stencil<R>(p.P, (R)x - vx * p.dt, ax);
+        R accf[N], accg[N];
+#pragma unroll
+        for (int b = 0; b < N; ++b) accf[b] = accg[b] = R(0);
+#pragma unroll 1
+        for (int u = 0; u < p.P; ++u) {
+          const int xi = x0 + u;
+          const double* E = xi < 0 ? ends : (xi >= len ? ends + 4 : nullptr);
+          const long long cs = E ? 0 : (long long)xi + (long long)p.nx * y;
+          const R sux = E ? (R)E[1] : (R)lam[cs], suy = E ? (R)E[2] : (R)lam[p.nc + cs];
+          const R sT = E ? (R)E[3] : (R)lam[2 * p.nc + cs];
+          const R r = sqrt(sT) * ist;
+          const R dx = (sux - ux) * ist, dy = (suy - uy) * ist;
+          const R dTs = (sT - T) / T;
+          const R r2 = r * r;
+          R gx[N];
+#pragma unroll
+          for (int j = 0; j < N; ++j) gx[j] = basis<N, R>(L, a, r * L.c[j] + dx);
+          const R pxa = dphi1<N, R>(L, a, dx, dTs);
+          const size_t base = (size_t)(y + p.G) * p.pitch + (xi + kOX);
+          R rowf[N], rowg[N];
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            R rf = R(0), rg = R(0);
+            if (!E) {
+#pragma unroll
+              for (int j = 0; j < N; ++j) {
+                rf += gx[j] * (R)f[(size_t)(j + N * k) * p.plane + base];
+                if (p.twopop) rg += gx[j] * (R)e[(size_t)(j + N * k) * p.plane + base];
+              }
+            }
+            rowf[k] = rf;
+            rowg[k] = rg;
+          }
+#pragma unroll
+          for (int b = 0; b < N; ++b) {
+            R gy[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) gy[j] = basis<N, R>(L, b, r * L.c[j] + dy);
+            const R pyb = dphi1<N, R>(L, b, dy, dTs);
+            const R gw = L.w[a] * pyb + pxa * L.w[b] + pxa * pyb;
+            const R Wab = L.w[a] * L.w[b];
+            R v = R(0);
+            if (E) {
+              v = ((R)E[0] - R(1)) * (Wab + gw);
+            } else {
+#pragma unroll
+              for (int k = 0; k < N; ++k) v += gy[k] * rowf[k];
+            }
+            v += gw;
+            accf[b] += ax[u] * v;
+            if (p.twopop) {
+              R vg = R(0);
+              if (E) {
+                vg = p.cvm1 * ((R)E[0] - R(1)) * (Wab + gw);
+              } else {
+#pragma unroll
+                for (int k = 0; k < N; ++k) vg += gy[k] * rowg[k];
+              }
+              vg = r2 * vg + p.cvm1 * (r2 * gw + dTs * Wab);
+              accg[b] += ax[u] * vg;
+            }
+          }
+        }
+#pragma unroll
+        for (int b = 0; b < N; ++b) {
+          d[b][a] = accf[b];
+          dg[b][a] = accg[b];
+        }
+      }
+    } else
 #pragma unroll 1
     for (int b = 0; b < N; ++b) {
       const R vy = st * L.c[b] + uy;
