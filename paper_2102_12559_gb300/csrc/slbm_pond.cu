@@ -583,8 +583,22 @@ __device__ void pond_convert_cell(const PondParams<R>& p, S* f0, S* f1, S* e0, S
     dphi_t<NQQ, R>(LQ, uy, dT, Qy);
     const double sq = sqrt((double)lam[2 * p.nc + c]);
     R Lx[NQQ][NQ], Ly[NQQ][NQ];
-    lift_matrix<NQ, NQQ, R>(Lq, LQ, sq, (double)lam[c], Lx);
-    lift_matrix<NQ, NQQ, R>(Lq, LQ, sq, (double)lam[p.nc + c], Ly);
+    // at zero frame velocity along an axis the matrix is the lattice-frame
+    // lift, independent of the temperature (the quasi-1-D rows have u_y = 0
+    // up to rounding; below the arithmetic's resolution the two agree)
+    const double u_zero = (sizeof(R) == 4 ? 1e-6 : 1e-12) * sq;
+    auto axis_matrix = [&](double u, R (*Lm)[NQ]) {
+      if (fabs(u) <= u_zero) {
+#pragma unroll
+        for (int A = 0; A < NQQ; ++A)
+#pragma unroll
+          for (int j = 0; j < NQ; ++j) Lm[A][j] = p.lift0[A][j];
+      } else {
+        lift_matrix<NQ, NQQ, R>(Lq, LQ, sq, u, Lm);
+      }
+    };
+    axis_matrix((double)lam[c], Lx);
+    axis_matrix((double)lam[p.nc + c], Ly);
     // pass 0: f; pass 1: g, whose equilibrium is (C_v - 1)(1 + dT) f^eq (eq.
     // geqPond, in units of the frame temperature) as a deviation
     for (int pass = 0; pass < (p.twopop ? 2 : 1); ++pass) {
