@@ -125,7 +125,7 @@ __device__ __forceinline__ int stencil(int P, R xd, R* a) {
 
 // One co-moving update of cell (x, y) whose populations (and those of every
 // collocation node it reads) are in lattice L with N nodes per axis.
-template <int N, class S, class R>
+template <int N, bool ROWS, class S, class R>
 __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* __restrict__ f,
                           const S* __restrict__ e, const S* __restrict__ lam, S* __restrict__ g,
                           S* __restrict__ eo, S* __restrict__ lam_out, int x, int y, int* err) {
@@ -135,6 +135,11 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
   // constant is the constant) and has fixed end states beyond 0 and len
   const int len = p.rows ? p.row_len[y] : p.nx;
   const double* ends = p.rows ? p.row_ends + 8 * y : nullptr;
+  // the row's end states in the arithmetic type, converted once per cell
+  R endv[2][4] = {{R(0), R(0), R(0), R(0)}, {R(0), R(0), R(0), R(0)}};
+  if (p.rows)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) endv[q / 4][q % 4] = (R)ends[q];
   const int Py = p.rows ? 1 : p.P;
   R d[N][N];                    // reconstructed deviations, [b][a]
   R dg[N][N];                   // g deviations (two-population model)
@@ -145,7 +150,7 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
   for (int it = 0; it < p.maxit; ++it) {
     if (!(T > R(0)) || !isfinite(ux) || !isfinite(uy)) { ok = false; break; }
     const R st = sqrt(T), ist = R(1) / st;
-    if (p.rows) {
+    if constexpr (ROWS) {
       // batched rows: the collocation nodes of population (a, b) lie on the
       // cell's row and depend on a only, so per (a, node) the node's frame
       // terms, the x basis and the x contraction sum_j G_x[j] s[j][k] are
@@ -165,10 +170,20 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
 #pragma unroll 1
         for (int u = 0; u < p.P; ++u) {
           const int xi = x0 + u;
-          const double* E = xi < 0 ? ends : (xi >= len ? ends + 4 : nullptr);
+          const int side = xi < 0 ? 0 : (xi >= len ? 1 : -1);  // an end state, or a cell
+          const bool E = side >= 0;
           const long long cs = E ? 0 : (long long)xi + (long long)p.nx * y;
-          const R sux = E ? (R)E[1] : (R)lam[cs], suy = E ? (R)E[2] : (R)lam[p.nc + cs];
-          const R sT = E ? (R)E[3] : (R)lam[2 * p.nc + cs];
+          R sux, suy, sT, erho = R(0);
+          if (E) {
+            erho = endv[side][0];
+            sux = endv[side][1];
+            suy = endv[side][2];
+            sT = endv[side][3];
+          } else {
+            sux = (R)lam[cs];
+            suy = (R)lam[p.nc + cs];
+            sT = (R)lam[2 * p.nc + cs];
+          }
           const R r = sqrt(sT) * ist;
           const R dx = (sux - ux) * ist, dy = (suy - uy) * ist;
           const R dTs = (sT - T) / T;
@@ -202,7 +217,7 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
             const R Wab = L.w[a] * L.w[b];
             R v = R(0);
             if (E) {
-              v = ((R)E[0] - R(1)) * (Wab + gw);
+              v = (erho - R(1)) * (Wab + gw);
             } else {
 #pragma unroll
               for (int k = 0; k < N; ++k) v += gy[k] * rowf[k];
@@ -212,7 +227,7 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
             if (p.twopop) {
               R vg = R(0);
               if (E) {
-                vg = p.cvm1 * ((R)E[0] - R(1)) * (Wab + gw);
+                vg = p.cvm1 * (erho - R(1)) * (Wab + gw);
               } else {
 #pragma unroll
                 for (int k = 0; k < N; ++k) vg += gy[k] * rowg[k];
@@ -228,7 +243,7 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
           dg[b][a] = accg[b];
         }
       }
-    } else
+    } else {
 #pragma unroll 1
     for (int b = 0; b < N; ++b) {
       const R vy = st * L.c[b] + uy;
@@ -317,6 +332,7 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
         dg[b][a] = gacc;
       }
     }
+    }
     // moments in the frame used: rho = 1 + sum d, relative velocity S1 / rho,
     // relative temperature 1 + dT (sum W c^2 = 1 per axis)
     R s0 = R(0), sx = R(0), sy = R(0), s2 = R(0);
@@ -400,7 +416,8 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
     R w1 = p.omega, w2 = p.omega2;
     if (p.hs) {  // mu = (1/omega_1 - 1/2) rho T dt with mu from the viscosity law
       const R Tabs = T * (R(1) + dT), rho = R(1) + dr;
-      const R mu = (R)p.row_visc[2 * y] * pow(Tabs / (R)p.row_visc[2 * y + 1], p.s_exp);
+      const R mu1 = (R)p.row_visc[2 * y], T1 = (R)p.row_visc[2 * y + 1];
+      const R mu = mu1 * pow(Tabs / T1, p.s_exp);
       const R tau1 = mu / (rho * Tabs * p.dt) + R(0.5);
       w1 = R(1) / tau1;
       w2 = R(1) / ((tau1 - R(0.5)) * p.inv_pr + R(0.5));
@@ -428,7 +445,7 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
   lam_out[2 * p.nc + c] = (S)T;
 }
 
-template <int NL, int NH, class S, class R>
+template <int NL, int NH, bool ROWS, class S, class R>
 __global__ void __launch_bounds__(kThreads)
 k_pond_step(const PondParams<R> p, const S* __restrict__ f0, const S* __restrict__ f1,
             const S* __restrict__ e0, const S* __restrict__ e1, const S* __restrict__ lam,
@@ -440,9 +457,9 @@ k_pond_step(const PondParams<R> p, const S* __restrict__ f0, const S* __restrict
   if (x >= p.nx || y >= p.ny) return;
   if (p.rows && x >= p.row_len[y]) return;  // beyond the row's instance
   if (flag[(long long)x + (long long)p.nx * y])
-    pond_cell<NH, S, R>(p, p.lat[1], f1, e1, lam, g1, eo1, lam_out, x, y, err);
+    pond_cell<NH, ROWS, S, R>(p, p.lat[1], f1, e1, lam, g1, eo1, lam_out, x, y, err);
   else
-    pond_cell<NL, S, R>(p, p.lat[0], f0, e0, lam, g0, eo0, lam_out, x, y, err);
+    pond_cell<NL, ROWS, S, R>(p, p.lat[0], f0, e0, lam, g0, eo0, lam_out, x, y, err);
 }
 
 // Rest-frame equilibrium of both lattices (s = (rho - 1) W_i) and the frame.
@@ -808,8 +825,14 @@ cudaError_t step_pair(const PondParams<R>& p, const S* f0, const S* f1, const S*
   const int bx = p.bx > 0 ? p.bx : kTX, by = p.bx > 0 ? p.by : kTY;
   if (bx * by != kThreads) return cudaErrorInvalidConfiguration;
   const dim3 grid((p.nx + bx - 1) / bx, (p.ny + by - 1) / by);
-  k_pond_step<NL, NH, S, R><<<grid, dim3(bx, by), 0, st>>>(p, f0, f1, e0, e1, lam, g0, g1, eo0,
-                                                           eo1, lam_out, flag, err);
+  // batched rows get their own instantiation (no 2-D stencil code: a smaller kernel)
+  if (p.rows)
+    k_pond_step<NL, NH, true, S, R><<<grid, dim3(bx, by), 0, st>>>(p, f0, f1, e0, e1, lam, g0, g1,
+                                                                   eo0, eo1, lam_out, flag, err);
+  else
+    k_pond_step<NL, NH, false, S, R><<<grid, dim3(bx, by), 0, st>>>(p, f0, f1, e0, e1, lam, g0,
+                                                                    g1, eo0, eo1, lam_out, flag,
+                                                                    err);
   return cudaGetLastError();
 }
 
