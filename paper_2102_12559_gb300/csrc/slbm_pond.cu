@@ -125,7 +125,7 @@ __device__ __forceinline__ int stencil(int P, R xd, R* a) {
 
 // One co-moving update of cell (x, y) whose populations (and those of every
 // collocation node it reads) are in lattice L with N nodes per axis.
-template <int N, bool ROWS, class S, class R>
+template <int N, bool ROWS, bool TWO, class S, class R>
 __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* __restrict__ f,
                           const S* __restrict__ e, const S* __restrict__ lam, S* __restrict__ g,
                           S* __restrict__ eo, S* __restrict__ lam_out, int x, int y, int* err) {
@@ -201,7 +201,7 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
 #pragma unroll
               for (int j = 0; j < N; ++j) {
                 rf += gx[j] * (R)f[(size_t)(j + N * k) * p.plane + base];
-                if (p.twopop) rg += gx[j] * (R)e[(size_t)(j + N * k) * p.plane + base];
+                if constexpr (TWO) rg += gx[j] * (R)e[(size_t)(j + N * k) * p.plane + base];
               }
             }
             rowf[k] = rf;
@@ -224,7 +224,7 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
             }
             v += gw;
             accf[b] += ax[u] * v;
-            if (p.twopop) {
+            if constexpr (TWO) {
               R vg = R(0);
               if (E) {
                 vg = p.cvm1 * (erho - R(1)) * (Wab + gw);
@@ -307,7 +307,7 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
             }
             v += gw;
             acc_t += ax[u] * v;
-            if (p.twopop) {  // r^2 G e_s + (C_v - 1)(r^2 (G W - W) + (r^2 - 1) W)
+            if constexpr (TWO) {  // r^2 G e_s + (C_v - 1)(r^2 (G W - W) + (r^2 - 1) W)
               R vg = R(0);
               if (E) {
                 vg = p.cvm1 * ((R)E[0] - R(1)) * (Wab + gw);
@@ -350,7 +350,7 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
     const R rho = R(1) + s0;
     s1x = sx / rho;
     s1y = sy / rho;
-    if (p.twopop) {
+    if constexpr (TWO) {
       // rho C_v T / T_frame = 1 + s2'/2 - rho s1^2/2 + sum g / T_frame (eq. E)
       R sg = R(0);
 #pragma unroll
@@ -384,7 +384,7 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
     const R pa = L.w[a] + ex[a], pb = L.w[b] + ey[b];
     return dr * pa * pb + L.w[a] * ey[b] + ex[a] * L.w[b] + ex[a] * ey[b];
   };
-  if (!p.twopop) {
+  if constexpr (!TWO) {
 #pragma unroll
     for (int b = 0; b < N; ++b)
 #pragma unroll
@@ -445,7 +445,7 @@ __device__ void pond_cell(const PondParams<R>& p, const PondLat<R>& L, const S* 
   lam_out[2 * p.nc + c] = (S)T;
 }
 
-template <int NL, int NH, bool ROWS, class S, class R>
+template <int NL, int NH, bool ROWS, bool TWO, class S, class R>
 __global__ void __launch_bounds__(kThreads)
 k_pond_step(const PondParams<R> p, const S* __restrict__ f0, const S* __restrict__ f1,
             const S* __restrict__ e0, const S* __restrict__ e1, const S* __restrict__ lam,
@@ -457,9 +457,9 @@ k_pond_step(const PondParams<R> p, const S* __restrict__ f0, const S* __restrict
   if (x >= p.nx || y >= p.ny) return;
   if (p.rows && x >= p.row_len[y]) return;  // beyond the row's instance
   if (flag[(long long)x + (long long)p.nx * y])
-    pond_cell<NH, ROWS, S, R>(p, p.lat[1], f1, e1, lam, g1, eo1, lam_out, x, y, err);
+    pond_cell<NH, ROWS, TWO, S, R>(p, p.lat[1], f1, e1, lam, g1, eo1, lam_out, x, y, err);
   else
-    pond_cell<NL, ROWS, S, R>(p, p.lat[0], f0, e0, lam, g0, eo0, lam_out, x, y, err);
+    pond_cell<NL, ROWS, TWO, S, R>(p, p.lat[0], f0, e0, lam, g0, eo0, lam_out, x, y, err);
 }
 
 // Rest-frame equilibrium of both lattices (s = (rho - 1) W_i) and the frame.
@@ -825,14 +825,17 @@ cudaError_t step_pair(const PondParams<R>& p, const S* f0, const S* f1, const S*
   const int bx = p.bx > 0 ? p.bx : kTX, by = p.bx > 0 ? p.by : kTY;
   if (bx * by != kThreads) return cudaErrorInvalidConfiguration;
   const dim3 grid((p.nx + bx - 1) / bx, (p.ny + by - 1) / by);
-  // batched rows get their own instantiation (no 2-D stencil code: a smaller kernel)
-  if (p.rows)
-    k_pond_step<NL, NH, true, S, R><<<grid, dim3(bx, by), 0, st>>>(p, f0, f1, e0, e1, lam, g0, g1,
-                                                                   eo0, eo1, lam_out, flag, err);
-  else
-    k_pond_step<NL, NH, false, S, R><<<grid, dim3(bx, by), 0, st>>>(p, f0, f1, e0, e1, lam, g0,
-                                                                    g1, eo0, eo1, lam_out, flag,
-                                                                    err);
+  // batched rows and the two-population model get their own instantiations
+  // (each kernel carries only the code it runs: less instruction fetch)
+#define SLBM_POND_STEP(ROWS, TWO)                                                               \
+  k_pond_step<NL, NH, ROWS, TWO, S, R><<<grid, dim3(bx, by), 0, st>>>(p, f0, f1, e0, e1, lam, g0, \
+                                                                      g1, eo0, eo1, lam_out,   \
+                                                                      flag, err)
+  if (p.rows && p.twopop) SLBM_POND_STEP(true, true);
+  else if (p.rows) SLBM_POND_STEP(true, false);
+  else if (p.twopop) SLBM_POND_STEP(false, true);
+  else SLBM_POND_STEP(false, false);
+#undef SLBM_POND_STEP
   return cudaGetLastError();
 }
 
