@@ -766,10 +766,7 @@ void fill_pond(PondParams<R>& q, const slbm_s* h, const Params<R>& p, const Latt
     }
   }
   for (int j = 0; j < kMaxN; ++j)
-    for (int m = 0; m < kMaxN; ++m) {
-      q.proj[j][m] = p.conv.proj[j][m];
-      q.lift0[j][m] = p.conv.lift[j][m];
-    }
+    for (int m = 0; m < kMaxN; ++m) q.proj[j][m] = p.conv.proj[j][m];
 }
 
 // Captured graphs hold kernel arguments by value: drop them whenever the

@@ -148,7 +148,6 @@ struct PondParams {
   R reach;                      // largest departure distance allowed, cells
   PondLat<R> lat[2];
   R proj[kMaxN][kMaxN];         // P[j][A], as ConvTab (frame-independent)
-  R lift0[kMaxN][kMaxN];        // lifting matrix of one axis at zero frame velocity (ConvTab.lift)
 };
 
 // Largest co-moving departure distance, cells.  Interface conversions cover

@@ -513,46 +513,42 @@ k_pond_masks(int nx, int ny, const uint8_t* __restrict__ flag, uint8_t* __restri
 // Lm = M_Q^-1[:, :nq] M_q in the frame's raw-moment matrices:
 // Lm[A][j] = sum_{m < nq} coef_A[m] v_j^m, where coef_A are the monomial
 // coefficients (in v) of the Q-lattice Lagrange basis polynomial
-// l_A((v - u) / s).  At u = 0 this is the lattice-frame L.  FP64: the
-// expansion in powers of v cancels for large |u|.
+// l_A((v - u) / s).  At u = 0 this is the lattice-frame L.  Expanding in
+// powers of v cancels for large |u|, so it is computed in closed form.  With
+// w = u / s and v_j = s (c_j + w) the q-lattice velocities of the frame, the
+// polynomial P_A(v) = l_A((v - u) / s) has P_A(v_j) = l_A(c_j), so the
+// truncation to degrees < nq is
+//   Lm[A][j] = l_A(c_j) - sum_{m = nq}^{nQ - 1} k_A[m] (c_j + w)^m,
+//   k_A[m] = sum_{k >= m} V_Q^-1[A][k] binom(k, m) (-w)^(k - m),
+// the coefficients of P_A in powers of v / s.  Every term is of the size of
+// the result, so the arithmetic type suffices.
 template <int NQ, int NQQ, class R>
-__device__ void lift_matrix(const PondLat<R>& Lq, const PondLat<R>& LQ, double s, double u,
-                            R (*Lm)[NQ]) {
-  double binom[NQQ][NQQ];
-#pragma unroll
-  for (int k = 0; k < NQQ; ++k)
-#pragma unroll
-    for (int m = 0; m < NQQ; ++m)
-      binom[k][m] = (m == 0 || m == k) ? 1.0 : (m > k ? 0.0 : binom[k - 1][m - 1] + binom[k - 1][m]);
-  const double is = 1.0 / s;
-  double pis[NQQ], pu[NQQ];      // s^-k, (-u)^k
-  pis[0] = 1.0;
-  pu[0] = 1.0;
-#pragma unroll
-  for (int k = 1; k < NQQ; ++k) {
-    pis[k] = pis[k - 1] * is;
-    pu[k] = pu[k - 1] * (-u);
-  }
+__device__ __forceinline__ void lift_matrix_w(const PondLat<R>& Lq, const PondLat<R>& LQ, R w,
+                                              R (*Lm)[NQ]) {
 #pragma unroll
   for (int A = 0; A < NQQ; ++A) {
-    double coef[NQ];
+    R kA[NQQ];
 #pragma unroll
-    for (int m = 0; m < NQ; ++m) {
-      double acc = 0.0;
+    for (int m = NQ; m < NQQ; ++m) {
+      R acc = R(0), pw = R(1), bin = R(1);  // (-w)^(k-m), binom(k, m) for k = m, m+1, ...
 #pragma unroll
-      for (int k = m; k < NQQ; ++k) acc += (double)LQ.vinv[A][k] * pis[k] * binom[k][m] * pu[k - m];
-      coef[m] = acc;
+      for (int k = m; k < NQQ; ++k) {
+        acc += LQ.vinv[A][k] * bin * pw;
+        pw *= -w;
+        bin = bin * R(k + 1) / R(k + 1 - m);
+      }
+      kA[m] = acc;
     }
 #pragma unroll
     for (int j = 0; j < NQ; ++j) {
-      const double v = s * (double)Lq.c[j] + u;
-      double acc = 0.0, vm = 1.0;
+      const R x = Lq.c[j] + w;
+      R v = basis<NQQ, R>(LQ, A, Lq.c[j]), xm = R(1);
 #pragma unroll
-      for (int m = 0; m < NQ; ++m) {
-        acc += coef[m] * vm;
-        vm *= v;
+      for (int m = 1; m < NQQ; ++m) {
+        xm *= x;
+        if (m >= NQ) v -= kA[m] * xm;
       }
-      Lm[A][j] = (R)acc;
+      Lm[A][j] = v;
     }
   }
 }
@@ -600,22 +596,8 @@ __device__ void pond_convert_cell(const PondParams<R>& p, S* f0, S* f1, S* e0, S
     dphi_t<NQQ, R>(LQ, uy, dT, Qy);
     const double sq = sqrt((double)lam[2 * p.nc + c]);
     R Lx[NQQ][NQ], Ly[NQQ][NQ];
-    // at zero frame velocity along an axis the matrix is the lattice-frame
-    // lift, independent of the temperature (the quasi-1-D rows have u_y = 0
-    // up to rounding; below the arithmetic's resolution the two agree)
-    const double u_zero = (sizeof(R) == 4 ? 1e-6 : 1e-12) * sq;
-    auto axis_matrix = [&](double u, R (*Lm)[NQ]) {
-      if (fabs(u) <= u_zero) {
-#pragma unroll
-        for (int A = 0; A < NQQ; ++A)
-#pragma unroll
-          for (int j = 0; j < NQ; ++j) Lm[A][j] = p.lift0[A][j];
-      } else {
-        lift_matrix<NQ, NQQ, R>(Lq, LQ, sq, u, Lm);
-      }
-    };
-    axis_matrix((double)lam[c], Lx);
-    axis_matrix((double)lam[p.nc + c], Ly);
+    lift_matrix_w<NQ, NQQ, R>(Lq, LQ, (R)((double)lam[c] / sq), Lx);
+    lift_matrix_w<NQ, NQQ, R>(Lq, LQ, (R)((double)lam[p.nc + c] / sq), Ly);
     // pass 0: f; pass 1: g, whose equilibrium is (C_v - 1)(1 + dT) f^eq (eq.
     // geqPond, in units of the frame temperature) as a deviation
     for (int pass = 0; pass < (p.twopop ? 2 : 1); ++pass) {
