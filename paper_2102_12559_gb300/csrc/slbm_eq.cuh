@@ -61,4 +61,35 @@ __device__ __forceinline__ void eq_dev(const LatTab<R>& L, int n, R dr, R ux, R 
   }
 }
 
+// Accumulator of the lifting's moment sums.  In FP32 it is the compensated
+// dot product Dot2 of Ogita, Rump and Oishi ("Accurate sum and dot product",
+// SIAM J. Sci. Comput. 26, 2005): each product is split exactly with an FMA,
+// each addition with TwoSum, and the error terms are summed alongside, so the
+// result is as accurate as an accumulation in twice the working precision --
+// at FP32 rates, where GB300's FP64 rate is a small fraction of its FP32 rate.
+// In FP64 it sums plainly.
+template <class R>
+struct MomentAcc {
+  R s = R(0), c = R(0);
+  __device__ __forceinline__ void add(R a) {
+    if constexpr (sizeof(R) == 8) {
+      s += a;
+    } else {
+      const R t = s + a, z = t - s;
+      c += (s - (t - z)) + (a - z);
+      s = t;
+    }
+  }
+  __device__ __forceinline__ void add_product(R x, R y) {
+    if constexpr (sizeof(R) == 8) {
+      s = fma(x, y, s);
+    } else {
+      const R pr = x * y, pe = fmaf(x, y, -pr);
+      add(pr);
+      c += pe;
+    }
+  }
+  __device__ __forceinline__ R value() const { return s + c; }
+};
+
 }  // namespace slbm

@@ -43,7 +43,7 @@
 // (|v| dt grows with u and T), so node indices wrap with a modulo instead of
 // reading a ghost ring.
 #include "../../include/slbm.h"
-#include "slbm_impl.cuh"
+#include "slbm_eq.cuh"
 
 namespace slbm {
 
@@ -566,29 +566,30 @@ __device__ void pond_convert_cell(const PondParams<R>& p, S* f0, S* f1, S* e0, S
   const PondLat<R>& LQ = p.lat[1];
   if (k == 0) {
     R s[NQ][NQ];
-    double m0 = 0.0, mx = 0.0, my = 0.0, m2 = 0.0, mg = 0.0;
+    // moment sums in twice the working precision for FP32 (MomentAcc)
+    MomentAcc<R> a0, ax, ay, a2, ag;
 #pragma unroll
     for (int b = 0; b < NQ; ++b)
 #pragma unroll
       for (int a = 0; a < NQ; ++a) {
         const R v = (R)f0[(size_t)(a + NQ * b) * p.plane + base];
         s[b][a] = v;
-        m0 += (double)v;
-        mx += (double)Lq.c[a] * (double)v;
-        my += (double)Lq.c[b] * (double)v;
-        m2 += ((double)Lq.c[a] * (double)Lq.c[a] + (double)Lq.c[b] * (double)Lq.c[b] - 2.0) *
-              (double)v;
-        if (p.twopop) mg += (double)e0[(size_t)(a + NQ * b) * p.plane + base];
+        a0.add(v);
+        ax.add_product(Lq.c[a], v);
+        ay.add_product(Lq.c[b], v);
+        a2.add_product(Lq.c[a] * Lq.c[a] + Lq.c[b] * Lq.c[b] - R(2), v);
+        if (p.twopop) ag.add((R)e0[(size_t)(a + NQ * b) * p.plane + base]);
       }
-    const double rho = 1.0 + m0;
-    const R ux = (R)(mx / rho), uy = (R)(my / rho);
-    const double u2 = (mx / rho) * (mx / rho) + (my / rho) * (my / rho);
+    const R m0 = a0.value(), m2 = a2.value(), mg = ag.value();
+    const R rho = R(1) + m0;
+    const R ux = ax.value() / rho, uy = ay.value() / rho;
+    const R u2 = ux * ux + uy * uy;
     R dT = R(0);
     if (p.twopop)  // the node's T from the total energy (eq. E), as in the step
-      dT = (R)((0.5 * m2 - 0.5 * rho * u2 + mg - (double)p.cvm1 * m0) / (rho * (double)p.cv));
+      dT = (R(0.5) * m2 - R(0.5) * rho * u2 + mg - p.cvm1 * m0) / (rho * p.cv);
     else if (p.thermal)
-      dT = (R)((m2 - rho * u2) / (2.0 * rho));
-    const R dr = (R)m0;
+      dT = (m2 - rho * u2) / (R(2) * rho);
+    const R dr = m0;
     R qx[NQ], qy[NQ], Qx[NQQ], Qy[NQQ];
     dphi_t<NQ, R>(Lq, ux, dT, qx);
     dphi_t<NQ, R>(Lq, uy, dT, qy);
