@@ -185,7 +185,7 @@ struct Layout {
   size_t lam[2];             // co-moving frame planes {u_x, u_y, T} per buffer
   size_t sched;              // two tile counters of the stream kernel's scheduler
   size_t seed_ctr;           // FP16 rounding key counter
-  size_t post_sync;          // 2 x 3 counters of the post-step kernel's grid-wide waits
+  size_t gh_start, gh_idx, gh_tiles;  // per-tile ghost lists (GhostTables)
   size_t post_work;          // 2 x ntiles work words (stream kernel -> post-step kernel)
   size_t post_nlist;         // 2 counters: work tiles listed in each half of post_list
   size_t post_list;          // 2 x ntiles: candidate work tiles (stream kernel -> post-step kernel)
@@ -260,7 +260,10 @@ Layout make_layout(const slbm_grid* g, int lo, int hi, int order, int precision)
   for (int b = 0; b < 2; ++b) { Lo.lam[b] = off; off = align_up(off + 3 * nc * es, 256); }
   Lo.sched = off; off = align_up(off + 2 * sizeof(int), 256);
   Lo.seed_ctr = off; off = align_up(off + sizeof(uint32_t), 256);
-  Lo.post_sync = off; off = align_up(off + 6 * sizeof(int), 256);
+  const size_t ring = 2 * (size_t)Lo.G * (g->nx + 2 * Lo.G) + 2 * (size_t)Lo.G * g->ny;
+  Lo.gh_start = off; off = align_up(off + (ntiles + 1) * sizeof(int), 256);
+  Lo.gh_idx = off; off = align_up(off + ring * sizeof(int), 256);
+  Lo.gh_tiles = off; off = align_up(off + ntiles * sizeof(int), 256);
   Lo.post_work = off; off = align_up(off + 2 * ntiles * sizeof(int), 256);
   Lo.post_nlist = off; off = align_up(off + 2 * sizeof(int), 256);
   Lo.post_list = off; off = align_up(off + 2 * ntiles * sizeof(int), 256);
@@ -318,7 +321,8 @@ struct slbm_s {
   int bc_kind[4];
   long long steps;
   long long sc_launches;         // stream-collide launches (scheduler counter parity)
-  long long post_launches;       // post-step launches (their counter parity)
+  long long post_launches;       // post-step launches
+  int gh_ntiles;                 // tiles with ghost images (GhostTables::ntiles)
   int failed;
   char err[256];
   // tracing: events bracketing the kernels of each profiled step
@@ -392,6 +396,59 @@ BcDev bc_dev(slbm_s* h) {
     b.uy[s] = h->at<double>(h->lay.bc[s][2]);
   }
   return b;
+}
+
+int ntiles_of(const slbm_s* h) {
+  return ((h->g.nx + kTX - 1) / kTX) * ((h->g.ny + kTY - 1) / kTY);
+}
+
+GhostTables ghost_tables(slbm_s* h) {
+  return GhostTables{h->at<int>(h->lay.gh_start), h->at<int>(h->lay.gh_idx),
+                     h->at<int>(h->lay.gh_tiles), h->gh_ntiles};
+}
+
+// Per-tile ghost lists of the post-step kernel for the current boundary
+// kinds: the source tile of every ring cell from the device's ghost rule,
+// sorted here by tile (ring order within a tile).  Synchronous (set-up only).
+int build_ghost_tables(slbm_s* h) {
+  const int G = h->lay.G, nx = h->g.nx, ny = h->g.ny;
+  const size_t ring = 2 * (size_t)G * (nx + 2 * G) + 2 * (size_t)G * ny;
+  const int nt = ntiles_of(h);
+  int* d_idx = h->at<int>(h->lay.gh_idx);
+  SLBM_CK(h, launch_ghost_src(G, nx, ny, h->g.periodic_x ? 1 : 0, h->g.periodic_y ? 1 : 0,
+                              bc_dev(h), d_idx, h->st),
+          "ghost source launch");
+  std::vector<int> src(ring), start(nt + 1, 0), idx, tiles;
+  if (ring)
+    SLBM_CK(h, cudaMemcpyAsync(src.data(), d_idx, ring * sizeof(int), cudaMemcpyDeviceToHost, h->st),
+            "D2H copy");
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  for (size_t g = 0; g < ring; ++g) {
+    if (src[g] >= nt) return fail(h, SLBM_ECUDA, "ghost source outside the grid");
+    if (src[g] >= 0) start[src[g] + 1]++;
+  }
+  for (int t = 0; t < nt; ++t) {
+    if (start[t + 1]) tiles.push_back(t);
+    start[t + 1] += start[t];
+  }
+  idx.resize(start[nt]);
+  std::vector<int> fill(start.begin(), start.end() - 1);
+  for (size_t g = 0; g < ring; ++g)
+    if (src[g] >= 0) idx[fill[src[g]]++] = (int)g;
+  SLBM_CK(h, cudaMemcpyAsync(h->at<int>(h->lay.gh_start), start.data(), start.size() * sizeof(int),
+                             cudaMemcpyHostToDevice, h->st),
+          "H2D copy");
+  if (!idx.empty())
+    SLBM_CK(h, cudaMemcpyAsync(d_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice,
+                               h->st),
+            "H2D copy");
+  if (!tiles.empty())
+    SLBM_CK(h, cudaMemcpyAsync(h->at<int>(h->lay.gh_tiles), tiles.data(),
+                               tiles.size() * sizeof(int), cudaMemcpyHostToDevice, h->st),
+            "H2D copy");
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");  // the host vectors are released
+  h->gh_ntiles = (int)tiles.size();
+  return SLBM_OK;
 }
 
 // Storage / arithmetic types of a lattice-frame handle, as a tag.
@@ -520,9 +577,6 @@ cudaError_t mark(slbm_s* h) {
   return cudaEventRecord(h->ev_pool[h->ev_used++], h->st);
 }
 
-int ntiles_of(const slbm_s* h) {
-  return ((h->g.nx + kTX - 1) / kTX) * ((h->g.ny + kTY - 1) / kTY);
-}
 
 // One time step: stream-collide (old flags) -> interface conversion (new
 // flags) -> ghost-ring refresh.
@@ -596,7 +650,6 @@ int step_once(slbm_s* h) {
   });
   SLBM_CK(h, e, "stream_collide launch");
   SLBM_CK(h, mark(h), "trace event");
-  const int post_parity = (int)(h->post_launches & 1);
   h->post_launches++;
   const int half = h->pf.sched_parity;
   const size_t nt = (size_t)ntiles_of(h);
@@ -606,8 +659,7 @@ int step_once(slbm_s* h) {
   e = with_types(h, [&](auto ty, const auto& prm) {
     SLBM_TYPES(ty);
     return launch_post_step<S, R>(prm, (S*)h->pops(nb, 0), (S*)h->pops(nb, 1), fold, fnew,
-                                  bc_dev(h), work, list, nlist, h->at<int>(h->lay.post_sync),
-                                  post_parity, err, h->st);
+                                  bc_dev(h), work, list, nlist, ghost_tables(h), h->st);
   });
   SLBM_CK(h, e, "post-step launch");
   SLBM_CK(h, mark(h), "trace event");
@@ -625,8 +677,7 @@ int step_once(slbm_s* h) {
 // where it was, so the replay only advances the counters.  Returns 1 (and
 // stops trying) if the capture is refused, so the caller steps directly.
 int step_pair(slbm_s* h) {
-  const int key = h->cur | h->mcur << 1 | h->fcur << 2 | (int)(h->sc_launches & 1) << 3 |
-                  (int)(h->post_launches & 1) << 4;
+  const int key = h->cur | h->mcur << 1 | h->fcur << 2 | (int)(h->sc_launches & 1) << 3;
   cudaGraphExec_t exec = nullptr;
   for (const auto& e : h->graphs)
     if (e.key == key) exec = e.exec;
@@ -956,14 +1007,12 @@ int apply_indicator(slbm_s* h) {
                               fold, fnew, h->at<uint8_t>(h->lay.tile_mask[h->mcur]), work, list,
                               nlist, half, h->st),
           "tile work launch");
-  const int post_parity = (int)(h->post_launches & 1);
   h->post_launches++;
-  int* err = h->at<int>(h->lay.err);
   cudaError_t e = with_types(h, [&](auto ty, const auto& prm) {
     SLBM_TYPES(ty);
     return launch_post_step<S, R>(prm, (S*)h->pops(h->cur, 0), (S*)h->pops(h->cur, 1), fold, fnew,
                                   bc_dev(h), work + half * nt, list + half * nt, nlist + half,
-                                  h->at<int>(h->lay.post_sync), post_parity, err, h->st);
+                                  ghost_tables(h), h->st);
   });
   SLBM_CK(h, e, "post-step launch");
   h->fcur ^= 1;
@@ -1040,6 +1089,7 @@ int slbm_create_in(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int i
   }
   std::vector<double> one(h->ncell(), 1.0), zero(h->ncell(), 0.0);
   int rc = slbm_init_equilibrium(h, one.data(), zero.data(), zero.data(), nullptr);
+  if (rc == SLBM_OK) rc = build_ghost_tables(h);
   if (rc == SLBM_OK) rc = slbm_sync(h);
   if (rc != SLBM_OK) {
     snprintf(g_create_err, sizeof(g_create_err), "%s", h->err);
@@ -1314,8 +1364,7 @@ int slbm_set_boundary(slbm_t h, int side, int kind, const double* rho, const dou
   h->bc_kind[side] = kind;
   drop_graphs(h);
   SLBM_CK(h, ghosts(h, h->flags(h->fcur)), "ghost launch");
-  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
-  return SLBM_OK;
+  return build_ghost_tables(h);
 }
 
 namespace {

@@ -303,6 +303,27 @@ k_tile_work(int nx, int ny, int periodic_x, int periodic_y, const uint8_t* __res
   }
 }
 
+// Source tile of every ghost ring cell (set-up of the post-step kernel's
+// per-tile ghost lists): the same ghost rule as every ghost writer.
+__global__ void k_ghost_src(int G, int nx, int ny, int periodic_x, int periodic_y, const BcDev bc,
+                            int* __restrict__ out, int ring) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ring) return;
+  int gx, gy, sx, sy, side = 0, idx = 0;
+  ghost_coords(G, nx, ny, g, gx, gy);
+  const int kind = ghost_source(nx, ny, periodic_x, periodic_y, bc, gx, gy, sx, sy, side, idx);
+  const int ntx = (nx + kTX - 1) / kTX;
+  out[g] = kind == 2 ? -1 : (sy / kTY) * ntx + sx / kTX;
+}
+
+cudaError_t launch_ghost_src(int G, int nx, int ny, int periodic_x, int periodic_y,
+                             const BcDev& bc, int* out, cudaStream_t st) {
+  const int ring = 2 * G * (nx + 2 * G) + 2 * G * ny;
+  if (ring == 0) return cudaSuccess;
+  k_ghost_src<<<(ring + 127) / 128, 128, 0, st>>>(G, nx, ny, periodic_x, periodic_y, bc, out, ring);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tile_work(int nx, int ny, int periodic_x, int periodic_y,
                              const uint8_t* flag_old, const uint8_t* flag_new, uint8_t* mask,
                              int* work, int* wlist, int* wcount, int half, cudaStream_t st) {

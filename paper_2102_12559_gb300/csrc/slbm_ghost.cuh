@@ -113,102 +113,17 @@ __device__ __forceinline__ R diffuse_value(const LatTab<R>& L, const S* f, long 
   return drw * (w_i + e_i) + e_i;
 }
 
-// Ghost cells that change from step to step: the ring's strips in order --
-// bottom and top (G rows of nx + 2G), left and right (G columns of ny) --
-// except those of a non-periodic side with constant (DIRICHLET) ghosts.
-struct GhostStrips {
-  int start[4], len[4], n;  // active strips, their ring offsets and sizes
-  int total;                // ghost cells in the active strips
-};
-
-template <class R>
-__device__ __forceinline__ GhostStrips active_ghost_strips(const Params<R>& p, const BcDev& bc) {
-  const int W = p.nx + 2 * p.G;
-  const int len[4] = {p.G * W, p.G * W, p.G * p.ny, p.G * p.ny};
-  const bool on[4] = {p.periodic_y || bc.kind[SLBM_SIDE_YMIN] != SLBM_BC_DIRICHLET,
-                      p.periodic_y || bc.kind[SLBM_SIDE_YMAX] != SLBM_BC_DIRICHLET,
-                      p.periodic_x || bc.kind[SLBM_SIDE_XMIN] != SLBM_BC_DIRICHLET,
-                      p.periodic_x || bc.kind[SLBM_SIDE_XMAX] != SLBM_BC_DIRICHLET};
-  GhostStrips a{};
-  int off = 0;
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    if (on[s]) {
-      a.start[a.n] = off;
-      a.len[a.n] = len[s];
-      a.total += len[s];
-      ++a.n;
-    }
-    off += len[s];
-  }
-  return a;
-}
-
-// Ring index of active ghost cell q (0 <= q < a.total).
-__device__ __forceinline__ int active_ghost(const GhostStrips& a, int q) {
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    if (s < a.n && q < a.len[s]) return a.start[s] + q;
-    if (s < a.n) q -= a.len[s];
-  }
-  return -1;
-}
-
-// Per-step ghost refresh of one element: ghost g of the ring, plane `plane`
-// of both lattices' planes (lattice 0 first).  Copy ghosts copy their
-// interior source; INLET ghosts write the plane's lattice equilibrium at the
-// interior cell's density and the side's velocity (the cell's own populations
-// summed, one product term evaluated); DIRICHLET ghosts are constant (written
-// at setup) and left alone.  Only elements whose source cell lies in a work
-// tile (dep = 1) or outside every work tile (dep = 0) are written (`work`:
-// the step's work words, ntx tiles per row).
-// Interior values are read through L2 (ld.global.cg): in the post-step kernel
-// other CTAs of the same launch may have written them.
-template <int NL, int NH, class S, class R>
-__device__ __forceinline__ void halo_element(const Params<R>& p, S* f0, S* f1,
-                                             const uint8_t* __restrict__ flag, const BcDev& bc,
-                                             int g, int plane, const int* __restrict__ work,
-                                             int ntx, int dep) {
-  constexpr int q0 = NL * NL, q1 = NH * NH;
-  int gx, gy, sx, sy, side = 0, idx = 0;
-  ghost_coords(p.G, p.nx, p.ny, g, gx, gy);
-  const int kind = ghost_source(p.nx, p.ny, p.periodic_x, p.periodic_y, bc, gx, gy, sx, sy, side,
-                                idx);
-  if (kind == 2) return;
-  if (post_work_word(work[(sy / kTY) * ntx + sx / kTX]) != (dep != 0)) return;
-  const int k = plane < q0 ? 0 : 1;
-  const int i = k ? plane - q0 : plane;
-  S* f = k ? f1 : f0;
-  const size_t off = (size_t)i * p.plane;
-  const int gbase = (gy + p.G) * p.pitch + (gx + kOX);
-  const int sbase = (sy + p.G) * p.pitch + (sx + kOX);
-  if (kind == 0) {
-    f[off + gbase] = __ldcg(f + off + sbase);
-    return;
-  }
-  if (kind == 3) {
-    const R uwx = (R)bc.ux[side][idx], uwy = (R)bc.uy[side][idx];
-    f[off + gbase] = static_cast<S>(
-        k ? diffuse_value<NH, S, R>(p.lat[1], f1, p.plane, sbase, side, uwx, uwy, i)
-          : diffuse_value<NL, S, R>(p.lat[0], f0, p.plane, sbase, side, uwx, uwy, i));
-    return;
-  }
-  // INLET: density deviation of the interior cell from its own lattice
-  R dr = R(0);
-  if (__ldcg(flag + sx + p.nx * sy)) {
-#pragma unroll
-    for (int j = 0; j < q1; ++j) dr += static_cast<R>(__ldcg(f1 + (size_t)j * p.plane + sbase));
-  } else {
-#pragma unroll
-    for (int j = 0; j < q0; ++j) dr += static_cast<R>(__ldcg(f0 + (size_t)j * p.plane + sbase));
-  }
+// INLET ghost value of population i of lattice k: the lattice equilibrium
+// at density deviation dr and velocity (ux, uy), on deviations (one product
+// term of the equilibrium evaluated, no per-node arrays).
+template <int NL, int NH, class R>
+__device__ __forceinline__ R inlet_value(const Params<R>& p, int k, int i, R dr, R ux, R uy) {
   const LatTab<R>& L = p.lat[k];
   const int n = k ? NH : NL;
   const int ix = i % n, iy = i / n;
-  // dphi of this plane's two 1-D nodes only (no per-node arrays)
   R hx[kMaxN], hy[kMaxN];
-  gauss_dev<R>((R)bc.ux[side][idx], hx);
-  gauss_dev<R>((R)bc.uy[side][idx], hy);
+  gauss_dev<R>(ux, hx);
+  gauss_dev<R>(uy, hy);
   R dxi = R(0), dyi = R(0);
 #pragma unroll
   for (int m = 1; m < kMaxN; ++m)
@@ -217,9 +132,8 @@ __device__ __forceinline__ void halo_element(const Params<R>& p, S* f0, S* f1,
       dyi += L.vinv[iy][m] * hy[m];
     }
   const R px = L.w1[ix] + dxi, py = L.w1[iy] + dyi;
-  f[off + gbase] = static_cast<S>(dr * px * py + L.w1[ix] * dyi + dxi * L.w1[iy] + dxi * dyi);
+  return dr * px * py + L.w1[ix] * dyi + dxi * L.w1[iy] + dxi * dyi;
 }
-
 
 template <int N, class S, class R>
 __device__ __forceinline__ void load_t(const S* f, long long plane, int base, R (*s)[kMaxN]) {

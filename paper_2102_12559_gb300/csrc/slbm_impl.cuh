@@ -270,15 +270,32 @@ cudaError_t launch_tile_work(int nx, int ny, int periodic_x, int periodic_y,
                              const uint8_t* flag_old, const uint8_t* flag_new, uint8_t* mask,
                              int* work, int* wlist, int* wcount, int half, cudaStream_t st);
 
-// Per-step post-step kernel (cooperative launch): interface conversion of
-// the candidate tiles in `list` (*nlist entries, listed by the stream kernel
-// or the tile-work kernel) whose final word in `work` (the same half) is
-// work, spread evenly over the CTAs, then the ghost-ring refresh.  sync: 6
-// ints (`parity` selects this launch's half).
+// Per-tile ghost lists: the ring cells (ghost_coords order) idx[start[t] ..
+// start[t + 1]) have their source cell (ghost_source) in tile t; tiles[0 ..
+// ntiles) are the tiles with at least one.  DIRICHLET ghosts, constant, are
+// in no list.
+struct GhostTables {
+  const int* start;  // ntiles_total + 1
+  const int* idx;
+  const int* tiles;
+  int ntiles;
+};
+
+// Source tile of every ghost ring cell under the ghost rule (-1: a constant
+// DIRICHLET ghost), ntx tiles per row: out[0 .. ring) with
+// ring = 2 G (nx + 2 G) + 2 G ny.  The host sorts these into GhostTables.
+cudaError_t launch_ghost_src(int G, int nx, int ny, int periodic_x, int periodic_y,
+                             const BcDev& bc, int* out, cudaStream_t st);
+
+// Per-step post-step kernel: interface conversion of the candidate tiles in
+// `list` (*nlist entries, listed by the stream kernel or the tile-work
+// kernel) whose final word in `work` (the same half) is work, spread evenly
+// over the CTAs, and the ghost images of every tile in `gt`, each written by
+// the CTA that owns its source tile (after the tile's conversion, if any).
 template <class S, class R>
 cudaError_t launch_post_step(const Params<R>& p, S* f0, S* f1, const uint8_t* flag_old,
                              const uint8_t* flag_new, const BcDev& bc, const int* work,
-                             const int* list, const int* nlist, int* sync, int parity, int* err,
+                             const int* list, const int* nlist, const GhostTables& gt,
                              cudaStream_t st);
 
 template <class S, class R>

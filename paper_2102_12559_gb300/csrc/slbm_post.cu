@@ -29,15 +29,15 @@ cudaError_t launch_post<__half, float>(const Params<float>& p, __half* f0, __hal
                                          tile_mask, st);
 }
 
-#define SLBM_POSTSTEP_INST(S, R)                                                            \
-  template <>                                                                               \
-  cudaError_t launch_post_step<S, R>(const Params<R>& p, S* f0, S* f1,                      \
-                                     const uint8_t* flag_old, const uint8_t* flag_new,      \
-                                     const BcDev& bc, const int* work, const int* list,    \
-                                     const int* nlist, int* sync, int parity, int* err,     \
-                                     cudaStream_t st) {                                     \
-    return launch_post_step_impl<S, R>(p, f0, f1, flag_old, flag_new, bc, work, list,       \
-                                       nlist, sync, parity, err, st);                       \
+#define SLBM_POSTSTEP_INST(S, R)                                                             \
+  template <>                                                                                \
+  cudaError_t launch_post_step<S, R>(const Params<R>& p, S* f0, S* f1,                       \
+                                     const uint8_t* flag_old, const uint8_t* flag_new,       \
+                                     const BcDev& bc, const int* work, const int* list,     \
+                                     const int* nlist, const GhostTables& gt,               \
+                                     cudaStream_t st) {                                      \
+    return launch_post_step_impl<S, R>(p, f0, f1, flag_old, flag_new, bc, work, list, nlist, \
+                                       gt, st);                                              \
   }
 SLBM_POSTSTEP_INST(float, float)
 SLBM_POSTSTEP_INST(double, double)

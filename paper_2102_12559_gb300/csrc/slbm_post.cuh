@@ -212,122 +212,152 @@ k_post(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ flag_old,
   }
 }
 
-constexpr long long kGridWaitCycles = 2000000000LL;  // ~1 s bound on a grid-wide wait
-
-// Grid-wide wait of the cooperative post-step kernel: thread 0 of each CTA
-// spins (bounded) until *ctr reaches target, then the CTA proceeds.  Returns
-// false, with the timeout bit in *err, if the bound ran out.
-__device__ __forceinline__ bool grid_wait(const int* ctr, int target, int* err) {
-  __shared__ int ok;
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    ok = 1;
-    const long long t0 = clock64();
-    while (*(const volatile int*)ctr < target)
-      if (clock64() - t0 > kGridWaitCycles) {
-        atomicOr(err, kErrTimeout);
-        ok = 0;
-        break;
+// Ghost images of the sources in one tile: the n ring cells idx[0..n) whose
+// source cell lies in the tile, every plane of both lattices.  Under the
+// ghost rule (ghost_source) copy ghosts copy their interior source; INLET
+// ghosts are the plane's lattice equilibrium at the source's density (its own
+// lattice's populations summed) and the side's velocity; DIFFUSE ghosts are
+// diffuse_value; DIRICHLET ghosts are constant and in no list.  Per chunk of
+// up to one ghost cell per thread: the cells' source, target and inputs into
+// shared memory, then the elements (ghost cell, plane) over the threads, four
+// at a time with every load before the stores (the stores may alias the loads
+// for the compiler, which would otherwise serialise one L2 round trip per
+// element).  Interior values are read through L2 (ld.global.cg): other
+// threads of the CTA have just written them.
+template <int NL, int NH, class S, class R>
+__device__ __forceinline__ void tile_ghosts(const Params<R>& p, S* f0, S* f1,
+                                            const uint8_t* __restrict__ flag, const BcDev& bc,
+                                            const int* __restrict__ idx, int n) {
+  constexpr int q0 = NL * NL, q1 = NH * NH, Q = q0 + q1, T = kTX * kTY, U = 4;
+  __shared__ int s_kind[T], s_gb[T], s_sb[T], s_side[T];
+  __shared__ R s_dr[T], s_ux[T], s_uy[T];
+  const int tid = threadIdx.y * kTX + threadIdx.x;
+  for (int c0 = 0; c0 < n; c0 += T) {
+    const int m = n - c0 < T ? n - c0 : T;
+    if (tid < m) {
+      int gx, gy, sx, sy, side = 0, bi = 0;
+      ghost_coords(p.G, p.nx, p.ny, idx[c0 + tid], gx, gy);
+      const int kind = ghost_source(p.nx, p.ny, p.periodic_x, p.periodic_y, bc, gx, gy, sx, sy,
+                                    side, bi);
+      const int sb = (sy + p.G) * p.pitch + (sx + kOX);
+      s_kind[tid] = kind;
+      s_gb[tid] = (gy + p.G) * p.pitch + (gx + kOX);
+      s_sb[tid] = sb;
+      s_side[tid] = side;
+      if (kind == 1 || kind == 3) {
+        s_ux[tid] = (R)bc.ux[side][bi];
+        s_uy[tid] = (R)bc.uy[side][bi];
       }
-    __threadfence();
+      if (kind == 1) {  // density deviation of the source from its own lattice
+        R dr = R(0);
+        if (__ldcg(flag + sx + p.nx * sy)) {
+#pragma unroll
+          for (int j = 0; j < q1; ++j) dr += static_cast<R>(__ldcg(f1 + (size_t)j * p.plane + sb));
+        } else {
+#pragma unroll
+          for (int j = 0; j < q0; ++j) dr += static_cast<R>(__ldcg(f0 + (size_t)j * p.plane + sb));
+        }
+        s_dr[tid] = dr;
+      }
+    }
+    __syncthreads();
+    for (int e0 = tid; e0 < m * Q; e0 += U * T) {
+      S val[U];
+      S* dst[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * T;
+        dst[u] = nullptr;
+        if (e >= m * Q) continue;
+        const int plane = e / m, j = e - plane * m;
+        const int kind = s_kind[j];
+        if (kind == 2) continue;
+        const int k = plane < q0 ? 0 : 1;
+        const int i = k ? plane - q0 : plane;
+        S* f = k ? f1 : f0;
+        const size_t off = (size_t)i * p.plane;
+        dst[u] = f + off + s_gb[j];
+        if (kind == 0) {
+          val[u] = __ldcg(f + off + s_sb[j]);
+        } else if (kind == 3) {
+          val[u] = static_cast<S>(
+              k ? diffuse_value<NH, S, R>(p.lat[1], f1, p.plane, s_sb[j], s_side[j], s_ux[j],
+                                          s_uy[j], i)
+                : diffuse_value<NL, S, R>(p.lat[0], f0, p.plane, s_sb[j], s_side[j], s_ux[j],
+                                          s_uy[j], i));
+        } else {
+          val[u] = static_cast<S>(inlet_value<NL, NH, R>(p, k, i, s_dr[j], s_ux[j], s_uy[j]));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (dst[u]) *dst[u] = val[u];
+    }
+    __syncthreads();  // the chunk's shared arrays are reused
   }
-  __syncthreads();
-  return ok != 0;
 }
 
-// Per-step post-step kernel (cooperative launch: every CTA resident).
+// Per-step post-step kernel.
 //  1. Interface conversion.  The stream kernel has OR-ed, into one word per
 //     tile, the lattices of the tile's 3 x 3 tile neighbourhood and the tile's
 //     own flip bit, and listed the candidate tiles (add_work).  CTA b takes
-//     list entries b, b + G, ... and converts those whose word is work (both
-//     lattices or a flip; post_tile), so clustered interfaces spread evenly
+//     items b, b + G, ...; list items whose word is work (both lattices or a
+//     flip) are converted (post_tile), so clustered interfaces spread evenly
 //     over the GPU.
-//  2. The ghost ring of both lattices, one thread per (ghost cell, plane) of
-//     the strips that change (halo_element).  A ghost whose source cell
-//     lies in a tile without conversion work is final once the stream kernel
-//     has run, and is written at once by the last CTAs (the work list fills
-//     the first ones); the others after a grid-wide wait, when every
-//     conversion is final.  (A lattice's planes at a cell outside every work
+//  2. Ghost images.  Every ghost element depends on one interior cell (its
+//     source), so the CTA that converts a tile writes, after the tile's
+//     barrier, the ghosts whose source lies in that tile (per-tile lists
+//     gh_start / gh_idx over the ring, built at set-up from the ghost rule);
+//     the other border tiles (gh_tiles, items after the list) write theirs at
+//     once, their sources being final when the stream kernel ends.  No CTA
+//     waits for another.  (A lattice's planes at a cell outside every work
 //     tile are read by no cell of that lattice, so their stale copies are
 //     never used.)
-// sync: [2][3] ints {CTAs converted, unused, unused}; this launch uses half
-// `parity`, which the previous launch cleared, and clears the other.
 template <int NL, int NH, class S, class R>
 __global__ void __launch_bounds__(kTX * kTY)
 k_post_step(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ flag_old,
             const uint8_t* __restrict__ flag_new, const BcDev bc, const int* __restrict__ work,
-            const int* __restrict__ list, const int* __restrict__ nlist, int ntx, int* sync,
-            int parity, int* err) {
+            const int* __restrict__ list, const int* __restrict__ nlist, int ntx,
+            const int* __restrict__ gh_start, const int* __restrict__ gh_idx,
+            const int* __restrict__ gh_tiles, int n_ghtiles) {
   __shared__ uint8_t sf[kTY + 2 * kBandMax][kTX + 2 * kBandMax];
   const int tid = threadIdx.y * kTX + threadIdx.x;
-  const int G = (int)gridDim.x, b = (int)blockIdx.x;
-  int* c = sync + 3 * parity;
-  if (b == 0 && tid == 0) {
-    int* o = sync + 3 * (parity ^ 1);
-    o[0] = o[1] = o[2] = 0;
-    ++*p.seed_ctr;  // the next stream launch rounds with a new key
-  }
-  const int total = *nlist;
-  for (int r = b; r < total; r += G) {
-    const int t = list[r];
-    if (!post_work_word(work[t])) continue;  // all high-order neighbourhood
-    post_tile<NL, NH, S, R>(p, f0, f1, flag_old, flag_new, bc, 0, false, nullptr, (t % ntx) * kTX,
-                            (t / ntx) * kTY, sf);
-  }
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    atomicAdd(&c[0], 1);  // this CTA's conversions are final
-  }
-  // ghost elements (active ghost cell, plane), counted from the last CTA:
-  // those whose source is outside every work tile while the other CTAs
-  // finish converting, the others after the wait
-  const GhostStrips gs = active_ghost_strips(p, bc);
-  const long long total_e = (long long)gs.total * (NL * NL + NH * NH);
-  auto ghosts = [&](int dep) {
-    for (long long e = (long long)(G - 1 - b) * (kTX * kTY) + tid; e < total_e;
-         e += (long long)G * (kTX * kTY)) {
-      const int plane = (int)(e / gs.total);
-      const int g = active_ghost(gs, (int)(e - (long long)plane * gs.total));
-      halo_element<NL, NH, S, R>(p, f0, f1, flag_new, bc, g, plane, work, ntx, dep);
+  const int G = (int)gridDim.x;
+  if (blockIdx.x == 0 && tid == 0) ++*p.seed_ctr;  // the next stream launch rounds with a new key
+  const int nl = *nlist;
+  const int total = nl + n_ghtiles;
+  for (int r = (int)blockIdx.x; r < total; r += G) {
+    int t;
+    if (r < nl) {
+      t = list[r];
+      if (!post_work_word(work[t])) continue;  // all high-order neighbourhood
+      // ends with a barrier: the tile's conversions are visible to the CTA
+      post_tile<NL, NH, S, R>(p, f0, f1, flag_old, flag_new, bc, 0, false, nullptr,
+                              (t % ntx) * kTX, (t / ntx) * kTY, sf);
+    } else {
+      t = gh_tiles[r - nl];
+      if (post_work_word(work[t])) continue;  // written after its conversion
     }
-  };
-  ghosts(0);
-  if (!grid_wait(&c[0], G, err)) return;
-  ghosts(1);
+    const int g0 = gh_start[t];
+    tile_ghosts<NL, NH, S, R>(p, f0, f1, flag_new, bc, gh_idx + g0, gh_start[t + 1] - g0);
+  }
 }
 
 template <class S, class R>
 cudaError_t launch_post_step_impl(const Params<R>& p, S* f0, S* f1, const uint8_t* flag_old,
                                   const uint8_t* flag_new, const BcDev& bc, const int* work,
-                                  const int* list, const int* nlist, int* sync, int parity,
-                                  int* err, cudaStream_t st) {
+                                  const int* list, const int* nlist, const GhostTables& gt,
+                                  cudaStream_t st) {
   const int ntx = (p.nx + kTX - 1) / kTX;
   const int nl = p.lat[0].n, nh = p.lat[1].n;
   const dim3 blk(kTX, kTY);
-#define SLBM_POSTSTEP_CASE(NL, NH)                                                            \
-  if (nl == NL && nh == NH) {                                                                 \
-    auto kern = k_post_step<NL, NH, S, R>;                                                    \
-    static int per_sm = -1; /* co-resident CTAs per SM, queried once */                       \
-    if (per_sm < 0) {                                                                         \
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTX * kTY, 0); \
-      if (e != cudaSuccess) return e;                                                         \
-    }                                                                                         \
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;                                     \
-    const int grid = (per_sm < 4 ? per_sm : 4) * p.nsm;                                       \
-    Params<R> pp = p;                                                                         \
-    S* a0 = f0;                                                                               \
-    S* a1 = f1;                                                                               \
-    const uint8_t* fo = flag_old;                                                             \
-    const uint8_t* fn = flag_new;                                                             \
-    BcDev b = bc;                                                                             \
-    const int* wk = work;                                                                     \
-    const int* li = list;                                                                     \
-    const int* nli = nlist;                                                                   \
-    int ntx_ = ntx, par = parity;                                                             \
-    int* sy = sync;                                                                           \
-    int* er = err;                                                                            \
-    void* args[] = {&pp, &a0, &a1, &fo, &fn, &b, &wk, &li, &nli, &ntx_, &sy, &par, &er};      \
-    return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), blk, args, 0, st);      \
+  const int grid = 4 * p.nsm;  // items are taken by stride; four CTAs fit per SM
+#define SLBM_POSTSTEP_CASE(NL, NH)                                                          \
+  if (nl == NL && nh == NH) {                                                               \
+    k_post_step<NL, NH, S, R><<<grid, blk, 0, st>>>(p, f0, f1, flag_old, flag_new, bc, work, \
+                                                     list, nlist, ntx, gt.start, gt.idx,     \
+                                                     gt.tiles, gt.ntiles);                   \
+    return cudaGetLastError();                                                              \
   }
   SLBM_POSTSTEP_CASE(3, 4)
   SLBM_POSTSTEP_CASE(3, 5)
