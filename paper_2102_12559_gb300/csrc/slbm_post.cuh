@@ -96,17 +96,21 @@ constexpr int kPostMaxTiles = 1024;  // tiles one persistent post CTA may own
 
 // The work of one tile (tile origin x0, y0): stage the new flags of the tile
 // and its band-wide halo, convert band / flipped cells, and in setup calls
-// write the tile's lattice mask.
+// write the tile's lattice mask.  The work word (if `work_word` is given; a
+// tile whose word is not work returns false after the first barrier) is
+// fetched with the staged flags, so their latencies overlap.
 template <int NL, int NH, class S, class R>
-__device__ __forceinline__ void post_tile(const Params<R>& p, S* f0, S* f1,
+__device__ __forceinline__ bool post_tile(const Params<R>& p, S* f0, S* f1,
                                           const uint8_t* __restrict__ flag_old,
                                           const uint8_t* __restrict__ flag_new, const BcDev& bc,
                                           int images, bool setup, uint8_t* mask_out, int x0,
-                                          int y0, uint8_t (*sf)[kTX + 2 * kBandMax]) {
+                                          int y0, uint8_t (*sf)[kTX + 2 * kBandMax],
+                                          const int* work_word = nullptr) {
   const int B = p.band;
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
   const bool in = x < p.nx && y < p.ny;
-  const int old = in ? flag_old[x + p.nx * y] : 2;  // issued before the staging
+  const int wv = work_word ? *work_word : 4;
+  const int old = in ? flag_old[x + p.nx * y] : 2;
   // new flags of the tile and its band-wide halo (outside the grid: a
   // non-periodic side reads as "same as the cell", i.e. never a band reason)
 #pragma unroll
@@ -130,6 +134,10 @@ __device__ __forceinline__ void post_tile(const Params<R>& p, S* f0, S* f1,
     sf[ly][lx] = v;
   }
   __syncthreads();
+  if (!post_work_word(wv)) {  // all high-order neighbourhood (uniform per CTA)
+    __syncthreads();          // sf is reused by the next tile
+    return false;
+  }
   const int nw = in ? sf[threadIdx.y + B][threadIdx.x + B] : 2;
   if (setup) {  // the lattices the next step's tile holds (read by the stream kernel)
     const int any_lo = __syncthreads_or(nw == 0);
@@ -140,8 +148,8 @@ __device__ __forceinline__ void post_tile(const Params<R>& p, S* f0, S* f1,
     bool band = false;
     for (int dy = -B; dy <= B; ++dy)
       for (int dx = -B; dx <= B; ++dx) {
-        const int v = sf[threadIdx.y + B + dy][threadIdx.x + B + dx];
-        band |= (v != 2) && (v != nw);
+        const int u = sf[threadIdx.y + B + dy][threadIdx.x + B + dx];
+        band |= (u != 2) && (u != nw);
       }
     const int base = (y + p.G) * p.pitch + (x + kOX);
     if (old != nw || band) {
@@ -167,6 +175,7 @@ __device__ __forceinline__ void post_tile(const Params<R>& p, S* f0, S* f1,
     }
   }
   __syncthreads();  // sf is reused by the next tile
+  return true;
 }
 
 // Persistent post-step kernel: CTA c owns tiles c, c + gridDim.x, ...  After a
@@ -321,25 +330,41 @@ k_post_step(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ flag_ol
             const int* __restrict__ gh_start, const int* __restrict__ gh_idx,
             const int* __restrict__ gh_tiles, int n_ghtiles) {
   __shared__ uint8_t sf[kTY + 2 * kBandMax][kTX + 2 * kBandMax];
+  __shared__ int gb[2];  // ghost list bounds of the list item being converted
   const int tid = threadIdx.y * kTX + threadIdx.x;
   const int G = (int)gridDim.x;
   if (blockIdx.x == 0 && tid == 0) ++*p.seed_ctr;  // the next stream launch rounds with a new key
+  // the count and this CTA's first list entry are fetched together (each half
+  // of the list holds ntiles entries, so the entry is always in bounds)
+  const int ntiles = ntx * ((p.ny + kTY - 1) / kTY);
   const int nl = *nlist;
+  const int t_first = (int)blockIdx.x < ntiles ? list[blockIdx.x] : 0;
   const int total = nl + n_ghtiles;
   for (int r = (int)blockIdx.x; r < total; r += G) {
-    int t;
     if (r < nl) {
-      t = list[r];
-      if (!post_work_word(work[t])) continue;  // all high-order neighbourhood
+      const int t = r == (int)blockIdx.x ? t_first : list[r];
+      // the tile's ghost list bounds are fetched with its work word and flags
+      // (through shared memory: published by post_tile's barriers)
+      if (tid == 0) {
+        gb[0] = gh_start[t];
+        gb[1] = gh_start[t + 1];
+      }
       // ends with a barrier: the tile's conversions are visible to the CTA
-      post_tile<NL, NH, S, R>(p, f0, f1, flag_old, flag_new, bc, 0, false, nullptr,
-                              (t % ntx) * kTX, (t / ntx) * kTY, sf);
+      if (!post_tile<NL, NH, S, R>(p, f0, f1, flag_old, flag_new, bc, 0, false, nullptr,
+                                   (t % ntx) * kTX, (t / ntx) * kTY, sf, work + t))
+        continue;  // all high-order neighbourhood
     } else {
-      t = gh_tiles[r - nl];
+      const int t = gh_tiles[r - nl];
       if (post_work_word(work[t])) continue;  // written after its conversion
+      if (tid == 0) {
+        gb[0] = gh_start[t];
+        gb[1] = gh_start[t + 1];
+      }
+      __syncthreads();
     }
-    const int g0 = gh_start[t];
-    tile_ghosts<NL, NH, S, R>(p, f0, f1, flag_new, bc, gh_idx + g0, gh_start[t + 1] - g0);
+    const int g0 = gb[0], n = gb[1] - g0;
+    tile_ghosts<NL, NH, S, R>(p, f0, f1, flag_new, bc, gh_idx + g0, n);
+    __syncthreads();  // gb is rewritten by the next item
   }
 }
 
