@@ -162,6 +162,58 @@ def test_free_jet_boundaries_fp64():
         assert rel_l2(a, b) < 1e-11
 
 
+def _set_side(s, side, kind, n):
+    """Boundary `kind` ("inlet", "outflow" or "dirichlet") on `side` of the
+    solver or the oracle (n cells along the side)."""
+    orc = isinstance(s, O.Oracle)
+    if kind == "dirichlet":
+        args = (np.full(n, 1.02), np.full(n, 0.05), np.zeros(n))
+        code = O.BC_DIRICHLET if orc else slbm.SLBM_BC_DIRICHLET
+    elif kind == "inlet":
+        args = (None, np.linspace(0.02, 0.12, n), np.full(n, -0.01))
+        code = O.BC_INLET if orc else slbm.SLBM_BC_INLET
+    else:
+        args = ()
+        code = O.BC_OUTFLOW if orc else slbm.SLBM_BC_OUTFLOW
+    (s.set_bc if orc else s.set_boundary)(side, code, *args)
+
+
+@pytest.mark.parametrize("periodic,kinds", [
+    ((False, False), ("inlet", "outflow", "outflow", "inlet")),
+    ((False, False), ("outflow", "inlet", "dirichlet", "outflow")),
+    ((True, False), (None, None, "inlet", "outflow")),
+])
+def test_mixed_boundaries_ragged_fp64(periodic, kinds):
+    """Every non-periodic ghost kind, and periodic images beside them, on a
+    ragged grid (45 x 27 against the 32 x 8 tiles) with moving interfaces:
+    each ghost is written by the CTA that owns its source tile (after that
+    tile's conversion when it has one), corner ghosts follow the y side's
+    rule, and cells that flip next to the border feed their ghosts with
+    their converted populations."""
+    nx, ny = 45, 27
+    g, o = pair(nx, ny, tau=0.58, periodic=periodic)
+    rho, ux, uy = WL.perturbed(nx, ny, seed=21, amp_rho=0.03, amp_u=0.4, U=(0.12, 0.05))
+    fl = WL.random_flags(nx, ny, seed=5, blobs=3, rmin=3, rmax=6)
+    for s in (g, o):
+        s.init_equilibrium(rho, ux, uy)
+        s.set_flags(fl)
+        for side, kind in enumerate(kinds):
+            if kind:
+                _set_side(s, side, kind, ny if side < 2 else nx)
+        s.set_criterion(1, 0.2)
+    flips = 0
+    for _ in range(3):
+        before = g.get_flags().copy()
+        both(g, o, "step", 8)
+        np.testing.assert_array_equal(g.get_flags(), o.get_flags())
+        flips += int((g.get_flags() != before).sum())
+    f = o.get_flags()
+    assert flips > 0 and 0 < f.sum() < nx * ny
+    assert f[:, :3].any() and f[:, -3:].any() and f[:3, :].any() and f[-3:, :].any()
+    for a, b in zip(g.moments(), o.moments()):
+        assert rel_l2(a, b) < 1e-11
+
+
 @pytest.mark.parametrize("k", [0, 1])
 def test_single_lattice_conservation_fp64(k):
     N = 40
