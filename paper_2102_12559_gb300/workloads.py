@@ -221,6 +221,20 @@ def shock_batch(count: int = 256, seed: int = 2, mach_range=(1.2, 4.0), len_rang
     return out
 
 
+def couette_batch(count: int = 128, seed: int = 3, h_range=(64, 512), kn_range=(0.01, 1.0),
+                  wall_speed: float = 0.1):
+    """A batch of independent Couette channels: heights H uniform in h_range
+    (cells between the walls), Knudsen numbers Kn = lambda / H log-uniform in
+    kn_range, walls moving at -wall_speed (y = 0) and +wall_speed (y = H - 1)
+    along the streamwise axis.  Returns per channel H, Kn and the two wall
+    speeds."""
+    rng = np.random.default_rng(seed)
+    hs = rng.integers(h_range[0], h_range[1] + 1, count)
+    kn = np.exp(rng.uniform(math.log(kn_range[0]), math.log(kn_range[1]), count))
+    return [{"H": int(h), "kn": float(k), "uw_lo": -wall_speed, "uw_hi": wall_speed}
+            for h, k in zip(hs, kn)]
+
+
 def shock_profile(inst: dict, nx: int, width: float = 20.0):
     """rho, u, T of one instance on nx cells (cells beyond its length hold the
     downstream state): the tanh ramp between the end states at the middle."""
