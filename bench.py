@@ -453,7 +453,6 @@ def run_study(args):
               flush=True)
         return
     if args.workload == "couette":
-        import time
         batch = WL.couette_batch(count=128, seed=3)
         nxc = 8  # streamwise period: the API needs at least 2 G + 1 = 5 cells per side
         kn_hi = 0.1  # channels above it run D2Q25, the others D2Q9
@@ -477,11 +476,22 @@ def run_study(args):
         for g in hs:
             g.step(args.warmup)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        # CUDA events on the default stream, which the channel streams wait on
+        # at the start and which waits on all of them at the end
+        main = torch.cuda.current_stream()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(main)
+        for st in streams:
+            st.wait_event(a)
         for g in hs:
             g.step(args.steps)
+        for st in streams:
+            e = torch.cuda.Event()
+            e.record(st)
+            main.wait_event(e)
+        b.record(main)
         torch.cuda.synchronize()
-        sec = time.perf_counter() - t0
+        sec = a.elapsed_time(b) * 1e-3
         cells = sum(nxc * ch["H"] for ch in batch)
         # antisymmetric walls: every channel's mean streamwise velocity stays 0
         drift = max(abs(float(g.moments()[1].mean())) for g in hs) / 0.1
@@ -493,7 +503,8 @@ def run_study(args):
                         "-0.1 / +0.1, FP32, one handle per channel on 16 streams",
             "d2q25_channels": sum(c["kn"] > kn_hi for c in batch), "cells": cells,
             "steps": args.steps, "ms_per_step": sec / args.steps * 1e3,
-            "mlups": cells * args.steps / sec / 1e6, "timing": "wall clock, device synchronised",
+            "mlups": cells * args.steps / sec / 1e6,
+            "timing": "CUDA events on the default stream joined with the 16 channel streams",
             "finite": finite, "max_mean_u_over_wall_speed": drift}), flush=True)
         for g in hs:
             g.close()
