@@ -329,7 +329,7 @@ struct slbm_s {
   int profiling;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used;
-  // CUDA graphs of two lattice-frame steps, one per parity state (step_pair)
+  // CUDA graphs of 2 or 16 steps, one per parity state and length (step_pair)
   struct GraphEntry {
     int key;
     cudaGraphExec_t exec;
@@ -670,14 +670,19 @@ int step_once(slbm_s* h) {
   return SLBM_OK;
 }
 
-// Two steps as one CUDA graph launch: the kernel launches of two step_once
-// calls, captured once per parity state (buffer, flag and mask halves,
-// scheduler and post-step counter parities) on a private stream and replayed
-// on the handle's stream.  (Co-moving steps alternate the buffer only.)  After two steps every parity is back
-// where it was, so the replay only advances the counters.  Returns 1 (and
+constexpr int kGraphPairs = 8;  // pairs of steps in a long graph
+
+// m pairs of steps as one CUDA graph launch: the kernel launches of 2 m
+// step_once calls, captured once per parity state (buffer, flag and mask
+// halves, scheduler counter and work-list halves) and length on a private
+// stream and replayed on the handle's stream.  (Co-moving steps alternate the
+// buffer only.)  After two steps every parity is back where it was, so the
+// replay only advances the counters.  Longer graphs cut the host's launches
+// for small grids, where one step takes a few microseconds.  Returns 1 (and
 // stops trying) if the capture is refused, so the caller steps directly.
-int step_pair(slbm_s* h) {
-  const int key = h->cur | h->mcur << 1 | h->fcur << 2 | (int)(h->sc_launches & 1) << 3;
+int step_pair(slbm_s* h, int m) {
+  const int key =
+      h->cur | h->mcur << 1 | h->fcur << 2 | (int)(h->sc_launches & 1) << 3 | m << 4;
   cudaGraphExec_t exec = nullptr;
   for (const auto& e : h->graphs)
     if (e.key == key) exec = e.exec;
@@ -687,7 +692,7 @@ int step_pair(slbm_s* h) {
       h->graphs_off = 1;
       return 1;
     }
-    // the host state two recorded steps advance
+    // the host state the recorded steps advance
     const int cur = h->cur, mcur = h->mcur, fcur = h->fcur;
     const long long steps = h->steps, scl = h->sc_launches, pol = h->post_launches;
     cudaStream_t st = h->st;
@@ -696,8 +701,7 @@ int step_pair(slbm_s* h) {
     int rc = SLBM_OK;
     cudaError_t e = cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      rc = step_once(h);
-      if (rc == SLBM_OK) rc = step_once(h);
+      for (int i = 0; i < 2 * m && rc == SLBM_OK; ++i) rc = step_once(h);
       e = cudaStreamEndCapture(h->cap_st, &g);
     }
     h->st = st;
@@ -720,10 +724,10 @@ int step_pair(slbm_s* h) {
     h->graphs.push_back({key, exec});
   }
   SLBM_CK(h, cudaGraphLaunch(exec, h->st), "graph launch");
-  h->steps += 2;
+  h->steps += 2 * m;
   if (h->frame == SLBM_FRAME_LATTICE) {
-    h->sc_launches += 2;
-    h->post_launches += 2;
+    h->sc_launches += 2 * m;
+    h->post_launches += 2 * m;
   }
   return SLBM_OK;
 }
@@ -1447,10 +1451,12 @@ int slbm_step(slbm_t h, int n) {
     const bool graphs = !h->profiling && !h->graphs_off &&
                         (h->frame == SLBM_FRAME_LATTICE ? h->sc_launches > 0 : h->steps > 0);
     while (graphs && !h->graphs_off && chunk - done >= 2) {
-      const int rc = step_pair(h);
+      // 2 kGraphPairs steps per graph while that many remain, then pairs
+      const int m = chunk - done >= 2 * kGraphPairs ? kGraphPairs : 1;
+      const int rc = step_pair(h, m);
       if (rc == 1) break;
       if (rc) return rc;
-      done += 2;
+      done += 2 * m;
     }
     for (; done < chunk; ++done) {
       const int rc = step_once(h);

@@ -376,7 +376,12 @@ cudaError_t launch_post_step_impl(const Params<R>& p, S* f0, S* f1, const uint8_
   const int ntx = (p.nx + kTX - 1) / kTX;
   const int nl = p.lat[0].n, nh = p.lat[1].n;
   const dim3 blk(kTX, kTY);
-  const int grid = 4 * p.nsm;  // items are taken by stride; four CTAs fit per SM
+  // items are taken by stride; four CTAs fit per SM, and a small grid needs no
+  // more CTAs than it can have items (list entries + border tiles), which
+  // leaves the GPU to concurrent launches of other handles
+  const int nty = (p.ny + kTY - 1) / kTY;
+  const int items = ntx * nty + gt.ntiles;
+  const int grid = items < 4 * p.nsm ? items : 4 * p.nsm;
 #define SLBM_POSTSTEP_CASE(NL, NH)                                                          \
   if (nl == NL && nh == NH) {                                                               \
     k_post_step<NL, NH, S, R><<<grid, blk, 0, st>>>(p, f0, f1, flag_old, flag_new, bc, work, \
