@@ -321,7 +321,6 @@ struct slbm_s {
   int bc_kind[4];
   long long steps;
   long long sc_launches;         // stream-collide launches (scheduler counter parity)
-  long long post_launches;       // post-step launches
   int gh_ntiles;                 // tiles with ghost images (GhostTables::ntiles)
   int failed;
   char err[256];
@@ -650,7 +649,6 @@ int step_once(slbm_s* h) {
   });
   SLBM_CK(h, e, "stream_collide launch");
   SLBM_CK(h, mark(h), "trace event");
-  h->post_launches++;
   const int half = h->pf.sched_parity;
   const size_t nt = (size_t)ntiles_of(h);
   const int* work = h->at<int>(h->lay.post_work) + half * nt;
@@ -694,7 +692,7 @@ int step_pair(slbm_s* h, int m) {
     }
     // the host state the recorded steps advance
     const int cur = h->cur, mcur = h->mcur, fcur = h->fcur;
-    const long long steps = h->steps, scl = h->sc_launches, pol = h->post_launches;
+    const long long steps = h->steps, scl = h->sc_launches;
     cudaStream_t st = h->st;
     h->st = h->cap_st;
     cudaGraph_t g = nullptr;
@@ -710,7 +708,6 @@ int step_pair(slbm_s* h, int m) {
     h->fcur = fcur;
     h->steps = steps;
     h->sc_launches = scl;
-    h->post_launches = pol;
     if (e == cudaSuccess && rc == SLBM_OK && g) e = cudaGraphInstantiate(&exec, g, 0);
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess || rc != SLBM_OK || !exec) {
@@ -725,10 +722,7 @@ int step_pair(slbm_s* h, int m) {
   }
   SLBM_CK(h, cudaGraphLaunch(exec, h->st), "graph launch");
   h->steps += 2 * m;
-  if (h->frame == SLBM_FRAME_LATTICE) {
-    h->sc_launches += 2 * m;
-    h->post_launches += 2 * m;
-  }
+  if (h->frame == SLBM_FRAME_LATTICE) h->sc_launches += 2 * m;
   return SLBM_OK;
 }
 
@@ -1011,7 +1005,6 @@ int apply_indicator(slbm_s* h) {
                               fold, fnew, h->at<uint8_t>(h->lay.tile_mask[h->mcur]), work, list,
                               nlist, half, h->st),
           "tile work launch");
-  h->post_launches++;
   cudaError_t e = with_types(h, [&](auto ty, const auto& prm) {
     SLBM_TYPES(ty);
     return launch_post_step<S, R>(prm, (S*)h->pops(h->cur, 0), (S*)h->pops(h->cur, 1), fold, fnew,
