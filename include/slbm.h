@@ -223,7 +223,13 @@ SLBM_API int slbm_indicator_eval(slbm_t h, float *features, float *logits, uint8
 SLBM_API int slbm_set_boundary(slbm_t h, int side, int kind, const double *rho, const double *ux,
                       const double *uy);
 
-/* Advance n >= 0 time steps (asynchronous). */
+/* Advance n >= 0 time steps (asynchronous).  Per lattice-frame step: the
+ * stream-collide kernel, then the post-step kernel (interface conversions and
+ * the ghost ring).  Once the kernels have run directly, runs of 16 (then 2)
+ * steps are replayed as CUDA graphs captured on a private stream; n = 1,
+ * traced steps and a refused capture launch directly, with bit-identical
+ * results.  A learned indicator or Knudsen criterion splits the steps into
+ * chunks between its evaluations. */
 SLBM_API int slbm_step(slbm_t h, int n);
 
 /* Wait for the handle's stream. */
