@@ -197,7 +197,8 @@ SLBM_API int slbm_set_criterion(slbm_t h, int kind, double threshold);
  * refines by plain Mach / Knudsen criteria (Sec. IV); the indicator is a small
  * MLP trained to reproduce such a criterion from local moments and their
  * gradients, with the plain criterion as its fallback (SLBM_CRIT_MACH) and
- * the judge of its error.  Per cell, 16 features, each times a fixed scale:
+ * the reference its error is measured against.  Per cell, 16 features, each
+ * times a fixed scale:
  *   rho - 1 (x10), u_x, u_y (x3), T - 1 (x10, kinetic T), the non-equilibrium
  *   stress sum c_a c_b (f - f^L) for xx, xy, yy (x100), the non-equilibrium
  *   energy flux 1/2 sum c_a |c|^2 (f - f^L) for x, y (x100), the central

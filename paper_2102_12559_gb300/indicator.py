@@ -5,7 +5,7 @@ decides the lattice of a cell (high-order when the logit is positive).  Its
 features are computed on the GPU by ``Solver.indicator_eval`` (16 scaled local
 moments and gradients, see include/slbm.h); its labels are the plain
 criterion evaluated on states of all-high-order runs, so the plain criterion
-is both the target and the judge of the indicator's error.  Inference runs on
+is both the target and the reference the indicator's error is measured against.  Inference runs on
 the GPU (tensor cores, FP16 weights and inputs, FP32 accumulation).
 
 Training here is written out by hand: forward pass, the logistic loss, its
