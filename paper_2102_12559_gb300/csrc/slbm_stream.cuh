@@ -48,6 +48,7 @@ struct StageGeom {
   static constexpr int min_blocks = sizeof(S) == 2 ? 3 : 2;
 };
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s bound on an mbarrier wait
+constexpr int kMaxDevices = 64;                 // device ordinals the launch caches cover
 
 // ------------------------------------------------------------ PTX helpers
 
@@ -516,24 +517,30 @@ cudaError_t launch_stream_collide_impl(const Params<R>& p, int P, const CUtensor
       (size_t)kStages * nh * nh * (kTY + 2 * stage_halo(P)) * StageGeom<S>::txp * sizeof(S);
   if (p.G < stage_halo(P)) return cudaErrorInvalidValue;  // ghost ring narrower than the stage halo
   const int nsm = p.nsm;
+  // the dynamic shared-memory attribute and the occupancy are per device:
+  // cached per device ordinal (handles of one process may live on several)
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return cudaErrorInvalidDevice;
 #define SLBM_SC_CASE(NL, NH, PP)                                                            \
   if (nl == NL && nh == NH && P == PP) {                                                    \
     auto kern = k_stream_collide<NL, NH, PP, S, R>;                                         \
-    static size_t attr_set = 0; /* largest dynamic size granted so far */                   \
-    if (smem > attr_set) {                                                                  \
+    static size_t attr_set[kMaxDevices] = {}; /* largest dynamic size granted so far */     \
+    if (smem > attr_set[dev]) {                                                             \
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                            (int)smem);                                      \
       if (e != cudaSuccess) return e;                                                       \
-      attr_set = smem;                                                                      \
+      attr_set[dev] = smem;                                                                 \
     }                                                                                       \
-    static size_t occ_smem = 0; /* occupancy is queried once per dynamic size */            \
-    static int per_sm = 0;                                                                  \
-    if (occ_smem != smem) {                                                                 \
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern,          \
+    static size_t occ_smem[kMaxDevices] = {}; /* occupancy queried once per size */         \
+    static int occ_per_sm[kMaxDevices] = {};                                                \
+    if (occ_smem[dev] != smem) {                                                            \
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_per_sm[dev], kern, \
                                                                     kTX * kTY, smem);       \
       if (e != cudaSuccess) return e;                                                       \
-      occ_smem = smem;                                                                      \
+      occ_smem[dev] = smem;                                                                 \
     }                                                                                       \
+    const int per_sm = occ_per_sm[dev];                                                     \
     if (per_sm < 1) return cudaErrorInvalidConfiguration;                                   \
     const int grid = ntiles < per_sm * nsm ? ntiles : per_sm * nsm;                         \
     kern<<<grid, blk, smem, st>>>(p, *tm0, *tm1, fout0, fout1, flag_cur, flag_nxt,          \
