@@ -1,28 +1,40 @@
 #!/usr/bin/env python
 """Throughput of the multi-scale semi-Lagrangian LBM step on GB300.
 
-Workload (default): the 2-D free jet, 1024 x 512 cells, FP32 populations,
-D2Q9 / D2Q25 pair, cubic Lagrange streaming, inlet slot 32 cells at Mach 0.5
-in a Mach 0.05 co-flow with a seeded 1 % inlet perturbation, outflow
-extrapolation, free-stream top / bottom, Re = 1000 on the slot, and the Mach
-> 0.3 refinement criterion applied after every step.  One bench step = one
-time step of the whole path (interface conversion, fused stream-collide with
-the criterion, ghost / boundary fill) through the C ABI.
+Headline workload (default): the large random-vortex field -- 4096 x 4096
+periodic cells, 512 Gaussian vortices with random centres, radii 8-64 cells
+and signs, rescaled to a peak Mach number of 0.9 (seed 4), rho = 1, D2Q9 /
+D2Q25 pair, cubic Lagrange streaming, tau = 0.6.  One bench step = one time
+step of the whole path (fused stream-collide with the refinement criterion,
+interface conversion, ghost refresh) through the C ABI.
 
-Timing: W untimed warm-up steps, then K steps each timed with CUDA events on
-the solver's stream, with L2 flushed (a 256 MiB memset) before every timed
-step.  Per-kernel device times come from the library's own event tracing.
+  value            the plain FP32 form: FP32 populations, Mach > 0.3 criterion
+                   after every step.
+  reduced arm      FP16 storage of the deviations f_i - W_i (FP32 arithmetic),
+                   the learned indicator re-flagging every 10 steps, the FP64
+                   conservation audit every 1000 steps (and at the end).
+  parity           every arm run 200 steps from the same initial state and
+                   compared (relative L2 of rho and u) with the FP64 build of
+                   the same library, itself at parity with the FP64 oracle.
+
+Timing: W untimed warm-up steps, then K back-to-back steps bracketed by CUDA
+events on the solver's stream.  The populations (1.2 GB read and written per
+step in FP32) are larger than the 129 MB L2, so L2 is not flushed.
+Per-kernel device times come from the library's own event tracing in a
+separate pass.
 
 Launch: ``python bench.py`` (1 GPU) or under torchrun with --gpus N: every
 rank advances its own replica of the workload (the path is not sharded
 across GPUs), value = cell updates of all ranks / max-over-ranks time.
-``--impl reference`` times the FP64 CPU oracle on a bounded sample instead.
+``--impl reference`` times the FP64 CPU oracle on the same workload's cells
+instead.  ``--workload`` selects a secondary study (one JSON line each).
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
 import json
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -35,15 +47,25 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "multi-scale SL-LBM MLUPS"
+METRIC = "multi-scale SL-LBM MLUPS & % HBM roofline vs plain FP32, at \u22641e-4 rel L2"
 UNIT = "MLUPS"
-NX, NY, SLOT, MA_JET, MA_CO, RE, THR = 1024, 512, 32, 0.5, 0.05, 1000.0, 0.3
-WORKLOAD = ("free jet 1024x512, FP32, D2Q9/D2Q25, cubic SL streaming, Mach>0.3 criterion "
-            "every step, inlet/outflow/free-stream boundaries")
+THR = 0.3
+# the large random-vortex field
+VN, VCOUNT, VSEED, VRMIN, VRMAX, VUMAX, VTAU = 4096, 512, 4, 8.0, 64.0, 0.9, 0.6
+VORTEX = (f"large random-vortex field {VN}x{VN} periodic, {VCOUNT} Gaussian vortices (radii "
+          f"{VRMIN:g}-{VRMAX:g} cells, random signs, peak Mach {VUMAX}, seed {VSEED}), D2Q9/D2Q25, "
+          f"cubic SL streaming, tau {VTAU}")
+# oracle sample: crops of the large field
+CPU_N = 512
+PARITY_STEPS = 200
+E2E_STEPS = 10000  # the large field's horizon
+# the free jet (secondary study)
+NX, NY, SLOT, MA_JET, MA_CO, RE = 1024, 512, 32, 0.5, 0.05, 1000.0
+JET = ("free jet 1024x512, FP32, D2Q9/D2Q25, cubic SL streaming, Mach>0.3 criterion "
+       "every step, inlet/outflow/free-stream boundaries")
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_FILES = ["slbm_stream.cuh", "slbm_ghost.cuh", "slbm_impl.cuh", "slbm_eq.cuh", "slbm_stream_f32.cu"]
-
-
+PROFILE_SUMMARY = "stream_collide_vortex4096.md"
 def kernel_hash() -> str:
     h = hashlib.sha256()
     for f in KERNEL_FILES:
@@ -90,7 +112,7 @@ def read_peaks():
 def read_traffic(khash: str):
     """DRAM bytes per stream-collide launch from the committed ncu summary,
     valid only if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "stream_collide_jet1024x512.md")
+    path = os.path.join(ROOT, "profiles", PROFILE_SUMMARY)
     try:
         txt = open(path).read()
     except OSError:
@@ -157,25 +179,6 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(J, tau):
-    """The FP64 oracle as it stands, one full time step of the same workload."""
-    import oracle as O
-    o = O.Oracle(NX, NY, 3, 5, tau=tau, order=3, periodic=(False, False))
-    o.init_equilibrium(J["rho"], J["ux"], J["uy"])
-    o.set_bc(0, O.BC_INLET, None, J["in_ux"], J["in_uy"])
-    o.set_bc(1, O.BC_OUTFLOW)
-    for side in (2, 3):
-        o.set_bc(side, O.BC_DIRICHLET, np.full(NX, J["fs_rho"]), np.full(NX, J["fs_ux"]),
-                 np.full(NX, J["fs_uy"]))
-    o.set_criterion(1, THR)
-    t = time.perf_counter()
-    o.step(1)
-    el = time.perf_counter() - t
-    return {"value": NX * NY / el / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one full time step of the {NX}x{NY} jet ({NX * NY} cell updates), FP64, "
-                      f"single thread, {el:.1f} s"}
-
-
 def max_over_ranks(values, dist, device):
     """The per-rank timings reduced to their maximum over ranks (every rank
     gets the result); dist None: a single process."""
@@ -190,46 +193,6 @@ def job_mlups(world: int, ncell: int, steps: int, ms: float) -> float:
     """Whole-job throughput of `world` replicas, each advancing `ncell` cells
     `steps` times in `ms` milliseconds (the slowest rank's time)."""
     return world * ncell * steps / (ms * 1e-3) / 1e6
-
-
-def run_reference(args, rank, world):
-    """Reference arm: the FP64 CPU oracle, each step a bounded sample of the
-    workload (the post-collision update of a fixed random sample of cells)."""
-    if rank != 0:
-        return
-    import oracle as O
-    from paper_2102_12559_gb300 import workloads as WL
-    J = WL.free_jet(NX, NY, slot=SLOT, ma_jet=MA_JET, ma_co=MA_CO)
-    o = O.Oracle(NX, NY, 3, 5, tau=0.6, order=3, periodic=(False, False))
-    tau = jet_tau(o.dt)
-    o = O.Oracle(NX, NY, 3, 5, tau=tau, order=3, periodic=(False, False))
-    o.init_equilibrium(J["rho"], J["ux"], J["uy"])
-    o.set_bc(0, O.BC_INLET, None, J["in_ux"], J["in_uy"])
-    o.set_bc(1, O.BC_OUTFLOW)
-    for side in (2, 3):
-        o.set_bc(side, O.BC_DIRICHLET, np.full(NX, J["fs_rho"]), np.full(NX, J["fs_ux"]),
-                 np.full(NX, J["fs_uy"]))
-    o.set_criterion(1, THR)
-    sample = 8192
-    cells = np.random.default_rng(0).choice(NX * NY, sample, replace=False)
-    for _ in range(args.warmup):
-        o.step_cells(cells)
-    t = time.perf_counter()
-    for _ in range(args.steps):
-        o.step_cells(cells)
-    el = time.perf_counter() - t
-    value = sample * args.steps / el / 1e6
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "nx": NX, "ny": NY},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{sample} random cells of the {NX}x{NY} jet per step "
-                                   "(one step's update of each), FP64, single thread"},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
 
 
 def time_steps(solver, stream, steps, warmup, audit_every=0):
@@ -266,18 +229,343 @@ def profiled(g, steps):
     return out
 
 
+# ------------------------------------------------------------------ oracle timing
+# (module-level so that spawned worker processes can import them)
+
+_ORC = {}
+
+
+def _oracle_crop(fields, n: int, k: int):
+    """The k-th n x n crop (along the diagonal) of the large field."""
+    o = (k * n) % VN
+    return [np.ascontiguousarray(f[o:o + n, o:o + n]) for f in fields]
+
+
+def _oracle_setup(crop):
+    """An n x n crop of the large field in the FP64 oracle, taken as
+    periodic, Mach criterion on (the crop's flags are set at once)."""
+    import oracle as O
+    rho, ux, uy = crop
+    n = rho.shape[0]
+    o = O.Oracle(n, n, 3, 5, tau=VTAU, order=3, periodic=(True, True))
+    o.init_equilibrium(rho, ux, uy)
+    o.set_criterion(1, THR)
+    return o
+
+
+def _oracle_steps(job):
+    """Worker: `steps` full oracle steps of its crop; (cells, seconds)."""
+    crop, steps = job
+    o = _oracle_setup(crop)
+    t = time.perf_counter()
+    o.step(steps)
+    return crop[0].size * steps, time.perf_counter() - t
+
+
+def _oracle_pool_init(crops, sample: int):
+    import multiprocessing as _mp
+    ident = _mp.current_process()._identity
+    k = (ident[0] - 1) if ident else 0
+    crop = crops[k % len(crops)]
+    _ORC["o"] = _oracle_setup(crop)
+    _ORC["cells"] = np.random.default_rng(k).choice(crop[0].size, sample, replace=False)
+
+
+def _oracle_sample_step(_):
+    """Worker: one step's update of the worker's fixed cell sample; seconds."""
+    t = time.perf_counter()
+    _ORC["o"].step_cells(_ORC["cells"])
+    return time.perf_counter() - t
+
+
+def vortex_fields():
+    from paper_2102_12559_gb300 import workloads as WL
+    return WL.random_vortex_field(VN, VCOUNT, seed=VSEED, rmin=VRMIN, rmax=VRMAX, umax=VUMAX)
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(fields):
+    """The FP64 oracle as it stands, on the host cores: full time steps of
+    512 x 512 crops of the large field (taken as periodic), one process
+    alone, then one process per host core at once (each on its own crop),
+    processes started with spawn."""
+    ctx = mp.get_context("spawn")
+    cores = host_cores()
+    steps1, stepsn = 2, 1
+    with ctx.Pool(1) as pool:
+        cells, el = pool.map(_oracle_steps, [(_oracle_crop(fields, CPU_N, 0), steps1)])[0]
+    one = cells / el / 1e6
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_steps, [(_oracle_crop(fields, CPU_N, i), stepsn)
+                                       for i in range(cores)], chunksize=1)
+    alln = sum(c / e for c, e in res) / 1e6
+    return {"value": alln, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"full FP64 time steps of {CPU_N}x{CPU_N} crops of the same field (taken as "
+                      f"periodic, Mach criterion): {cores} processes at once, {stepsn} step each on "
+                      f"its own crop (sum of their rates); one process alone: {one:.4f} MLUPS over "
+                      f"{steps1} steps",
+            "single_core": {"value": one, "unit": UNIT, "cores": 1}}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle on the host cores, every step a
+    bounded sample of the workload -- one process per host core, each updating
+    a fixed random sample of 1024 cells of its own 512 x 512 crop of the large
+    field (the step's post-collision vectors, state not advanced)."""
+    if rank != 0:
+        return
+    cores = host_cores()
+    sample = 1024
+    fields = vortex_fields()
+    crops = [_oracle_crop(fields, CPU_N, i) for i in range(cores)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores, initializer=_oracle_pool_init, initargs=(crops, sample)) as pool:
+        for _ in range(args.warmup):
+            pool.map(_oracle_sample_step, range(cores), chunksize=1)
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            pool.map(_oracle_sample_step, range(cores), chunksize=1)
+        el = time.perf_counter() - t
+    value = cores * sample * args.steps / el / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": VORTEX, "nx": VN, "ny": VN},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"per step, {cores} processes each update {sample} random cells "
+                                   f"of their own {CPU_N}x{CPU_N} crop of the field "
+                                   "(one step's update of each), FP64"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def rel_l2(a, b) -> float:
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def mom_gap(a, b) -> dict:
+    """Relative L2 gaps of rho, u (the vector field) and its components."""
+    return {"rho": rel_l2(a[0], b[0]), "u": rel_l2(np.stack(a[1:3]), np.stack(b[1:3])),
+            "ux": rel_l2(a[1], b[1]), "uy": rel_l2(a[2], b[2])}
+
+
+def train_indicator(slbm, WL, stream):
+    """Indicator weights from an all-D2Q25 384^2 run of the same generator
+    (12 vortices, seed 5, 20 steps), labelled by the plain Mach criterion."""
+    from paper_2102_12559_gb300 import indicator as IND
+    n_tr = 384
+    t = slbm.Solver(n_tr, n_tr, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=VTAU, stream=stream)
+    t.init_equilibrium(*WL.random_vortex_field(n_tr, 12, seed=5, rmin=VRMIN, rmax=VRMAX, umax=VUMAX))
+    t.set_flags(np.ones((n_tr, n_tr), np.uint8))
+    t.step(20)
+    x_tr = t.indicator_eval()[0].reshape(-1, 16).astype(np.float64)
+    _, mu, mv, _ = t.moments()
+    y_tr = (np.hypot(mu, mv) > THR).ravel().astype(np.float64)
+    t.close()
+    return IND.train(x_tr, y_tr, epochs=40, batch=512, seed=0, balance=False)
+
+
+def vortex_arm(slbm, stream, fields, precision, weights=None):
+    """A solver on the large field: Mach criterion every step, or (weights)
+    the learned indicator every 10 steps."""
+    g = slbm.Solver(VN, VN, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=VTAU, interp_order=3,
+                    precision=precision, stream=stream)
+    g.init_equilibrium(*fields)
+    if weights is not None:
+        g.set_indicator(weights, interval=10)
+        g.set_criterion(slbm.SLBM_CRIT_MLP, 0.0)
+    else:
+        g.set_criterion(slbm.SLBM_CRIT_MACH, THR)
+    return g
+
+
+def headline(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    fields = vortex_fields()
+    # the oracle's processes start before the first GPU call
+    cpu = cpu_baseline(fields) if (world == 1 and not args.no_cpu_baseline) else None
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2102_12559_gb300 import slbm, workloads as WL
+    stream = torch.cuda.current_stream(dev)
+    ncell = VN * VN
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+
+    # ---- the plain FP32 form: K back-to-back steps after W warm-up steps
+    g = vortex_arm(slbm, stream, fields, slbm.SLBM_FP32)
+    g.step(args.warmup)
+    torch.cuda.synchronize(dev)
+    flags_before = g.get_flags()
+    clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    g.step(args.steps)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    total_ms = a.elapsed_time(b)
+    g.sync()
+    flags_after = g.get_flags()
+    kern, ksteps = profiled(g, min(args.steps, 50))
+    kern_ms = [k / max(ksteps, 1) for k in kern]
+    kps = g.info.kernels_per_step
+    g.close()
+
+    # ---- end to end through the C ABI with pinned host buffers: the H2D of
+    # rho and u, the criterion, E steps and the D2H of rho and u
+    pin = [torch.from_numpy(np.ascontiguousarray(f, dtype=np.float64).ravel()).pin_memory()
+           for f in fields]
+    outs = [torch.empty(ncell, dtype=torch.float64).pin_memory() for _ in range(4)]
+    g = slbm.Solver(VN, VN, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=VTAU, interp_order=3,
+                    precision=slbm.SLBM_FP32, stream=stream)
+    torch.cuda.synchronize(dev)
+    e2e_steps = args.e2e_steps
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    slbm.slbm_init_equilibrium(g.h, ncell, pin[0].numpy(), pin[1].numpy(), pin[2].numpy())
+    slbm.slbm_set_criterion(g.h, slbm.SLBM_CRIT_MACH, THR)
+    slbm.slbm_step(g.h, e2e_steps)
+    slbm.slbm_moments(g.h, ncell, *[o.numpy() for o in outs])
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    e2e_ms = ev0.elapsed_time(ev1)
+    g.close()
+    h2d, d2h = ncell * 3 * 8, ncell * 4 * 8
+
+    total_ms, e2e_ms = max_over_ranks((total_ms, e2e_ms), dist, dev)
+    if rank != 0:
+        dist.barrier()
+        dist.destroy_process_group()
+        return
+
+    # ---- reduced-precision arms (rank 0): FP16 storage alone, and FP16 with
+    # the learned indicator every 10 steps and the FP64 audit every 1000
+    weights = train_indicator(slbm, WL, stream)
+    arms = {}
+    for name, learned in (("fp16", False), ("fp16+indicator+audit", True)):
+        r = vortex_arm(slbm, stream, fields, slbm.SLBM_FP16, weights if learned else None)
+        r.step(args.warmup)
+        ms = time_steps(r, stream, args.steps, 0, audit_every=1000 if learned else 0)
+        kr, kst = profiled(r, min(args.steps, 50))
+        arms[name] = {"ms": ms, "kern": [k / max(kst, 1) for k in kr]}
+        r.close()
+
+    # ---- parity: every arm PARITY_STEPS steps from the initial state against
+    # the FP64 build of the library
+    moms = {}
+    for name, prec, learned in (("fp64", slbm.SLBM_FP64, False), ("fp32", slbm.SLBM_FP32, False),
+                                ("fp16", slbm.SLBM_FP16, False),
+                                ("fp16+indicator+audit", slbm.SLBM_FP16, True)):
+        r = vortex_arm(slbm, stream, fields, prec, weights if learned else None)
+        if learned:
+            r.step(PARITY_STEPS)
+            r.audit()
+        else:
+            r.step(PARITY_STEPS)
+        fl = r.get_flags()
+        moms[name] = (r.moments(), fl)
+        r.close()
+    ref, ref_fl = moms["fp64"]
+
+    def arm_line(name, ms, kern):
+        m, fl = moms[name]
+        return {"value": ncell / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms,
+                "speedup_vs_fp32": (total_ms / args.steps) / ms,
+                "kernels_ms_per_step": dict(zip(slbm.KERNEL_NAMES, kern)),
+                "rel_l2_vs_fp64_at_200_steps": mom_gap(m[:3], ref[:3]),
+                "rel_l2_vs_fp32_at_200_steps": mom_gap(m[:3], moms["fp32"][0][:3]),
+                "flags_agree_with_fp64_run": float(np.mean(fl == ref_fl)),
+                "high_order_fraction_at_200_steps": float(fl.mean())}
+
+    value = job_mlups(world, ncell, args.steps, total_ms)
+    e2e_value = job_mlups(world, ncell, e2e_steps, e2e_ms)
+    nhi = 0.5 * (int(flags_before.sum()) + int(flags_after.sum()))
+    # algorithmic bytes of one stream-collide launch (FP32): read + write Q
+    # populations per cell, read the flag, write the next flag
+    bytes_sc = ncell * (8 * 9 + 2) + nhi * 8 * (25 - 9)
+    sc_ms = kern_ms[0]
+    achieved = bytes_sc / (sc_ms * 1e-3) / 1e9
+    peak, peak_src = read_peaks()
+    khash = kernel_hash()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": VORTEX, "nx": VN, "ny": VN, "lattices": "D2Q9/D2Q25",
+                   "interp_order": 3, "tau": VTAU, "criterion": f"Mach>{THR} after every step",
+                   "high_order_fraction": nhi / ncell,
+                   "l2": "not flushed: the populations (1.2 GB read and written per step) are "
+                         "larger than L2",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": read_traffic(khash),
+                     "kernel": "stream_collide", "algorithmic_bytes_per_launch": bytes_sc,
+                     "launch_ms": sc_ms, "peak_source": peak_src, "kernel_source_hash": khash},
+        "kernels_ms_per_step": dict(zip(slbm.KERNEL_NAMES, kern_ms)),
+        "reduced_precision_arm": dict(
+            arm_line("fp16+indicator+audit", arms["fp16+indicator+audit"]["ms"],
+                     arms["fp16+indicator+audit"]["kern"]),
+            form="FP16 storage of f_i - W_i with FP32 arithmetic, learned indicator every 10 steps, "
+                 "FP64 audit every 1000 steps and at the end"),
+        "fp16_storage_arm": dict(arm_line("fp16", arms["fp16"]["ms"], arms["fp16"]["kern"]),
+                                 form="FP16 storage of f_i - W_i, Mach criterion every step"),
+        "fp32_parity": {"rel_l2_vs_fp64_at_200_steps": mom_gap(moms["fp32"][0][:3], ref[:3]),
+                        "flags_agree_with_fp64_run": float(np.mean(moms["fp32"][1] == ref_fl)),
+                        "reference": "FP64 build of the library (at 1e-11 parity with the FP64 "
+                                     "oracle), Mach criterion every step, 200 steps"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
+                "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
+                "path": "slbm_init_equilibrium (pinned host rho, u) + slbm_set_criterion + "
+                        "slbm_step + slbm_moments (pinned host rho, u, T), FP32"},
+        "gpu_launches": args.steps * kps,
+        "clocks": clk,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def run_study(args):
     """Secondary measurements, one JSON line each (not the headline line).
+
+    jet: the free jet 1024 x 512 (FP32, inlet / outflow / free stream, Mach
+      criterion every step), cold-L2 and back-to-back step times.
 
     strip: the efficiency study of Sec. IV.C -- N x N periodic grids, all-D2Q9,
       all-D2Q25 and a hybrid whose left 10 % of columns are D2Q25; reports
       t_Q25 / t_Q9 and t_Q25 / t_hyb next to the paper's 2.9 and 2.43.
-    vortex4096: the large random-vortex field (4096^2, 512 vortices, Mach 0.9
-      peak): the plain FP32 form (Mach criterion every step) against FP16
-      deviation storage, and against FP16 storage with the learned indicator
-      every 10 steps (weights trained here on an all-D2Q25 384^2 run) and the
-      FP64 audit every 1000 steps; MLUPS of each and the relative L2 gap of
-      rho and u to the FP32 form after the same steps.
     pond: the co-moving (PonD) frame step, thermal, 1024 x 512 periodic,
       FP32, D2Q9 with a D2Q25 disc, a smooth seeded field around a Mach 1.5
       mean flow at T = 1.
@@ -296,6 +584,50 @@ def run_study(args):
     from paper_2102_12559_gb300 import slbm, workloads as WL
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
+    if args.workload == "jet":
+        # the free jet 1024 x 512 (FP32, Mach criterion every step): per-step
+        # times with a 256 MiB L2 flush before each step
+        J = WL.free_jet(NX, NY, slot=SLOT, ma_jet=MA_JET, ma_co=MA_CO)
+        probe = slbm.Solver(8, 8, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=0.6)
+        tau = jet_tau(probe.dt)
+        probe.close()
+        g = slbm.Solver(NX, NY, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=tau, interp_order=3,
+                        periodic=(False, False), precision=slbm.SLBM_FP32, stream=stream)
+        g.init_equilibrium(J["rho"], J["ux"], J["uy"])
+        setup_jet(g, slbm, J)
+        g.set_criterion(slbm.SLBM_CRIT_MACH, THR)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        for _ in range(args.warmup):
+            flush.zero_()
+            g.step(1)
+        torch.cuda.synchronize()
+        evs = []
+        for _ in range(args.steps):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            g.step(1)
+            e.record(stream)
+            evs.append((s, e))
+        torch.cuda.synchronize()
+        ms = sum(s.elapsed_time(e) for s, e in evs) / args.steps
+        g.profile(True)
+        for _ in range(min(args.steps, 200)):
+            flush.zero_()
+            g.step(1)
+        kern_ms, kern_steps = g.profile_read()
+        g.profile(False)
+        nhi = int(g.get_flags().sum())
+        btb = time_steps(g, stream, args.steps, 10)
+        print(json.dumps({
+            "study": "free jet", "workload": JET, "tau": tau, "steps": args.steps,
+            "ms_per_step_cold_l2": ms, "mlups_cold_l2": NX * NY / (ms * 1e-3) / 1e6,
+            "ms_per_step_back_to_back": btb, "mlups_back_to_back": NX * NY / (btb * 1e-3) / 1e6,
+            "high_order_fraction": nhi / (NX * NY),
+            "kernels_ms_per_step": {n: float(kern_ms[i] / max(kern_steps, 1))
+                                    for i, n in enumerate(slbm.KERNEL_NAMES)}}), flush=True)
+        g.close()
+        return
     if args.workload == "strip":
         for N in (128, 256, 512, 1024, 2048, 4096):
             steps = max(20, min(2000, int(4e8 / (N * N))))
@@ -317,68 +649,6 @@ def run_study(args):
                 "t_q25_over_t_q9": t["q25"] / t["q9"], "t_q25_over_t_hyb": t["q25"] / t["hyb"],
                 "paper": {"t_q25_over_t_q9": 2.9, "t_q25_over_t_hyb_max": 2.43},
                 "l2": "not flushed (back-to-back steps)"}), flush=True)
-        return
-    if args.workload == "vortex4096":
-        # the large random-vortex field: the plain FP32 form (Mach criterion
-        # every step) against FP16 deviations, and against FP16 deviations with
-        # the learned indicator every 10 steps and the FP64 audit every 1000
-        from paper_2102_12559_gb300 import indicator as IND
-        N = 4096
-        rho, ux, uy = WL.random_vortex_field(N, 512, seed=4, rmin=8.0, rmax=64.0, umax=0.9)
-        # indicator weights: an all-D2Q25 run of the same generator on 384^2
-        n_tr = 384
-        t = slbm.Solver(n_tr, n_tr, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=0.6, stream=stream)
-        t.init_equilibrium(*WL.random_vortex_field(n_tr, 12, seed=5, rmin=8.0, rmax=64.0, umax=0.9))
-        t.set_flags(np.ones((n_tr, n_tr), np.uint8))
-        t.step(20)
-        x_tr = t.indicator_eval()[0].reshape(-1, 16).astype(np.float64)
-        _, mu, mv, _ = t.moments()
-        y_tr = (np.hypot(mu, mv) > THR).ravel().astype(np.float64)
-        t.close()
-        weights = IND.train(x_tr, y_tr, epochs=40, batch=512, seed=0, balance=False)
-        arms = (("fp32", slbm.SLBM_FP32, False), ("fp16", slbm.SLBM_FP16, False),
-                ("fp16+indicator", slbm.SLBM_FP16, True))
-        res = {}
-        for name, prec, learned in arms:
-            g = slbm.Solver(N, N, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=0.6, stream=stream,
-                            precision=prec)
-            g.init_equilibrium(rho, ux, uy)
-            if learned:
-                g.set_indicator(weights, interval=10)
-                g.set_criterion(slbm.SLBM_CRIT_MLP, 0.0)
-                ms = time_steps(g, stream, args.steps, args.warmup, audit_every=1000)
-            else:
-                g.set_criterion(slbm.SLBM_CRIT_MACH, THR)
-                ms = time_steps(g, stream, args.steps, args.warmup)
-            kern, ksteps = profiled(g, 50)
-            flags = g.get_flags()
-            mom = g.moments()
-            res[name] = dict(ms=ms, kern=[k / max(ksteps, 1) for k in kern], nhi=int(flags.sum()),
-                             mom=mom, agree=float(np.mean(flags == (np.hypot(mom[1], mom[2]) > THR))))
-            g.close()
-        b = res["fp32"]["mom"]
-        rl2 = lambda x, y: float(np.linalg.norm((x - y).ravel()) / np.linalg.norm(y.ravel()))
-        for name, prec, learned in arms:
-            r = res[name]
-            es = 4 if prec == slbm.SLBM_FP32 else 2
-            bytes_sc = N * N * (2 * es * 9 + 2) + r["nhi"] * 2 * es * 16
-            line = {
-                "study": "large random-vortex field", "workload": f"{N}x{N}, 512 vortices, "
-                "max Mach 0.9", "arm": name,
-                "flags": "learned indicator every 10 steps, FP64 audit every 1000 steps" if learned
-                else "Mach > 0.3 criterion every step",
-                "steps_timed": args.steps, "total_steps": args.steps + args.warmup + 50,
-                "ms_per_step": r["ms"], "mlups": N * N / (r["ms"] * 1e-3) / 1e6,
-                "speedup_vs_fp32": res["fp32"]["ms"] / r["ms"],
-                "high_order_fraction": r["nhi"] / (N * N),
-                "flags_agree_with_plain_criterion": r["agree"],
-                "kernels_ms_per_step": dict(zip(slbm.KERNEL_NAMES, r["kern"])),
-                "stream_collide_gbs": bytes_sc / (r["kern"][0] * 1e-3) / 1e9}
-            if name != "fp32":
-                a = r["mom"]
-                line["rel_l2_vs_fp32"] = {"rho": rl2(a[0], b[0]),
-                                          "u": rl2(np.stack(a[1:3]), np.stack(b[1:3]))}
-            print(json.dumps(line), flush=True)
         return
     if args.workload == "shock":
         # batched shock structures: 256 quasi-1-D instances in one grid (one
@@ -540,161 +810,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="slbm", choices=["slbm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--spinup", type=int, default=0, help="untimed steps before warm-up")
-    ap.add_argument("--workload", default="jet",
-                    choices=["jet", "strip", "pond", "vortex4096", "shock", "couette"],
-                    help="jet: the headline line; strip / pond: secondary studies")
+    ap.add_argument("--e2e-steps", type=int, default=E2E_STEPS,
+                    help="steps of the end-to-end measurement (default: the field's horizon)")
+    ap.add_argument("--workload", default="vortex4096",
+                    choices=["vortex4096", "jet", "strip", "pond", "shock", "couette"],
+                    help="vortex4096: the headline line; the others: secondary studies")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.workload != "jet":
+    if args.workload != "vortex4096":
         run_study(args)
         return
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-
-    if args.impl == "reference":
-        run_reference(args, rank, world)
-        return
-
-    import torch
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-
-    from paper_2102_12559_gb300 import slbm, workloads as WL
-    J = WL.free_jet(NX, NY, slot=SLOT, ma_jet=MA_JET, ma_co=MA_CO)
-    stream = torch.cuda.current_stream(dev)
-    solver = slbm.Solver(NX, NY, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=0.6, interp_order=3,
-                         periodic=(False, False), precision=slbm.SLBM_FP32, stream=stream)
-    tau = jet_tau(solver.dt)
-    solver.close()
-    solver = slbm.Solver(NX, NY, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=tau, interp_order=3,
-                         periodic=(False, False), precision=slbm.SLBM_FP32, stream=stream)
-    solver.init_equilibrium(J["rho"], J["ux"], J["uy"])
-    setup_jet(solver, slbm, J)
-    solver.set_criterion(slbm.SLBM_CRIT_MACH, THR)
-    if args.spinup:
-        solver.step(args.spinup)
-
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    uuid = None
-    try:
-        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        uuid = None
-    clocks = ClockSampler(uuid)
-
-    for _ in range(args.warmup):
-        flush.zero_()
-        solver.step(1)
-    torch.cuda.synchronize(dev)
-    flags_before = solver.get_flags()
-
-    clocks.start()
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    evs = []
-    for _ in range(args.steps):
-        flush.zero_()
-        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s.record(stream)
-        solver.step(1)
-        e.record(stream)
-        evs.append((s, e))
-    torch.cuda.synchronize(dev)
-    if dist is not None:
-        dist.barrier()
-    total_ms = sum(s.elapsed_time(e) for s, e in evs)
-    # per-kernel device times from the library's event tracing, in a separate
-    # pass of the same workload (the tracing events would otherwise sit in the
-    # timed steps)
-    prof_steps = min(args.steps, 200)
-    solver.profile(True)
-    for _ in range(prof_steps):
-        flush.zero_()
-        solver.step(1)
-    kern_ms, kern_steps = solver.profile_read()
-    solver.profile(False)
-    flags_after = solver.get_flags()
-
-    # ---- end to end through the C ABI with host buffers (pinned), copies timed
-    pin = {k: torch.from_numpy(np.ascontiguousarray(J[k], dtype=np.float64)).pin_memory().numpy()
-           for k in ("rho", "ux", "uy")}
-    outs = [torch.empty(NX * NY, dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
-    torch.cuda.synchronize(dev)
-    e2e_steps = args.steps
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    flush_evs = []
-    ev0.record(stream)
-    solver.init_equilibrium(pin["rho"], pin["ux"], pin["uy"])
-    setup_jet(solver, slbm, J)
-    solver.set_criterion(slbm.SLBM_CRIT_MACH, THR)
-    for _ in range(e2e_steps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        flush.zero_()
-        b.record(stream)
-        flush_evs.append((a, b))
-        solver.step(1)
-    slbm.slbm_moments(solver.h, NX * NY, outs[0], outs[1], outs[2], None)
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    clk = clocks.stop()
-    e2e_ms = ev0.elapsed_time(ev1) - sum(a.elapsed_time(b) for a, b in flush_evs)
-    h2d = NX * NY * (3 * 8) + 2 * NY * 8 + 2 * 3 * NX * 8
-    d2h = NX * NY * 3 * 8
-
-    total_ms, e2e_ms = max_over_ranks((total_ms, e2e_ms), dist, dev)
-    if rank != 0:
-        dist.destroy_process_group()
-        return
-
-    ncell = NX * NY
-    value = job_mlups(world, ncell, args.steps, total_ms)
-    e2e_value = job_mlups(world, ncell, e2e_steps, e2e_ms)
-    nhi = 0.5 * (int(flags_before.sum()) + int(flags_after.sum()))
-    # algorithmic bytes of one stream-collide launch (FP32): read + write Q
-    # populations per cell, read the flag, write the next flag
-    bytes_sc = ncell * (8 * 9 + 2) + nhi * 8 * (25 - 9)
-    sc_ms = kern_ms[0] / max(kern_steps, 1)
-    achieved = bytes_sc / (sc_ms * 1e-3) / 1e9
-    peak, peak_src = read_peaks()
-    khash = kernel_hash()
-    traffic = read_traffic(khash)
-    kps = solver.info.kernels_per_step
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "lattices": "D2Q9/D2Q25",
-                   "interp_order": 3, "tau": tau, "criterion": f"Mach>{THR}",
-                   "high_order_fraction": nhi / ncell,
-                   "l2": "flushed (256 MiB memset) before every timed step",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "stream_collide",
-                     "algorithmic_bytes_per_launch": bytes_sc, "launch_ms": sc_ms,
-                     "peak_source": peak_src, "kernel_source_hash": khash},
-        "kernels_ms_per_step": {n: float(kern_ms[i] / max(kern_steps, 1))
-                                for i, n in enumerate(slbm.KERNEL_NAMES)},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / e2e_steps,
-                "d2h_bytes_per_step": d2h / e2e_steps},
-        "gpu_launches": args.steps * kps,
-        "clocks": clk,
-    }
-    if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(J, tau)
-    print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    headline(args)
 
 
 if __name__ == "__main__":

@@ -377,7 +377,11 @@ SLBM_API int slbm_profile_read(slbm_t h, double *ms, long long *steps);
  * nx * ny must not exceed SLBM_NOALLOC_MAX_CELLS (SLBM_EINVAL otherwise).
  * The first call on a device (with that device current) looks up the
  * array's device address with cudaGetSymbolAddress; make that first call
- * before any stream capture.  Returns SLBM_OK, SLBM_EINVAL or SLBM_ECUDA. */
+ * before any stream capture.  A failed lookup is not cached (the next call
+ * retries it) and its error is cleared; an error the caller left in the
+ * runtime's last-error state is neither reported nor cleared (only this
+ * call's own launches are checked).  Returns SLBM_OK, SLBM_EINVAL or
+ * SLBM_ECUDA. */
 #define SLBM_NOALLOC_MAX_BLOCKS 1024
 #define SLBM_NOALLOC_MAX_CELLS (1LL << 30)
 SLBM_API int slbm_audit_dense_noalloc(const float *f, int lattice, int nx, int ny, double *out,

@@ -8,6 +8,7 @@
 // still run it.  Host code cannot hand the array's name to a kernel (on the
 // host it is only a stand-in symbol), so the first call on each device looks
 // up its device address with cudaGetSymbolAddress, with that device current.
+// A failed lookup is not remembered: the next call tries again.
 #include <mutex>
 
 #include "../../include/slbm.h"
@@ -24,12 +25,25 @@ constexpr int kMaxDevices = 64;
 // to start at zero; calls that overlap on the GPU share it and race.
 static __device__ __align__(256) double g_partials[4 * kBlocks];
 
-struct DeviceScratch {
-  std::once_flag once;
-  double* ptr = nullptr;
-  cudaError_t err = cudaSuccess;
-};
-DeviceScratch g_scratch[kMaxDevices];
+// Device address of g_partials per device ordinal, cached once found.
+std::mutex g_scratch_mu;
+double* g_scratch[kMaxDevices] = {};
+
+// g_partials' address on the current device `dev`, or null if the lookup
+// failed (its error is cleared from the runtime's last-error state, which
+// belongs to the caller).
+double* scratch_on(int dev) {
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_partials) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    g_scratch[dev] = static_cast<double*>(p);
+  }
+  return g_scratch[dev];
+}
 
 struct Velocities {
   double c[slbm::kMaxN];
@@ -92,18 +106,27 @@ extern "C" int slbm_audit_dense_noalloc(const float* f, int lattice, int nx, int
     cudaGetLastError();
     return SLBM_ECUDA;
   }
-  DeviceScratch& s = g_scratch[dev];
-  std::call_once(s.once, [&s] {
-    s.err = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.ptr), g_partials);
-  });
-  if (s.err != cudaSuccess || !s.ptr) return SLBM_ECUDA;
+  double* partials = scratch_on(dev);
+  if (!partials) return SLBM_ECUDA;
   Velocities v{};
   double w[slbm::kMaxN];
   slbm::host_gauss_hermite(lattice, v.c, w);
   const long long want = (ncell + kThreads - 1) / kThreads;
-  const int blocks = (int)(want < kBlocks ? want : kBlocks);
+  int blocks = (int)(want < kBlocks ? want : kBlocks);
+  int n = lattice;
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  k_audit_dense_partial<<<blocks, kThreads, 0, st>>>(f, lattice, ncell, v, s.ptr);
-  k_audit_dense_final<<<1, kThreads, 0, st>>>(s.ptr, blocks, out);
-  return cudaGetLastError() == cudaSuccess ? SLBM_OK : SLBM_ECUDA;
+  // each launch's own status (an error left by an earlier call of the caller
+  // is neither reported nor cleared here)
+  void* a1[] = {(void*)&f, (void*)&n, (void*)&ncell, (void*)&v, (void*)&partials};
+  cudaError_t e = cudaLaunchKernel((const void*)k_audit_dense_partial, dim3(blocks),
+                                   dim3(kThreads), a1, 0, st);
+  if (e == cudaSuccess) {
+    void* a2[] = {(void*)&partials, (void*)&blocks, (void*)&out};
+    e = cudaLaunchKernel((const void*)k_audit_dense_final, dim3(1), dim3(kThreads), a2, 0, st);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // this call's own launch error
+    return SLBM_ECUDA;
+  }
+  return SLBM_OK;
 }

@@ -103,10 +103,13 @@ def test_convected_vortex_200_steps(vortex_oracle, precision, tol):
     mom = g.moments()
     ref = vortex_oracle["mom"]
     errs = [rel_l2(a, b) for a, b in zip(mom, ref)]
-    # u is a vector field: relative L2 of (u_x, u_y) together
-    eu = rel_l2(np.stack([mom[1], mom[2]]), np.stack([ref[1], ref[2]]))
-    print(f"precision={precision} rel L2 rho,ux,uy,T = {errs}, vector u = {eu}")
-    assert max(errs[0], eu, errs[3]) < tol, (errs, eu)
+    # the vortex itself, without the uniform Mach 0.1 advection that
+    # dominates |u|: u_x - U0 and u_y, each on its own
+    U0 = 0.1
+    ev = [rel_l2(mom[1] - U0, ref[1] - U0), rel_l2(mom[2], ref[2])]
+    print(f"precision={precision} rel L2 rho,ux,uy,T = {errs}, vortex u_x - U0, u_y = {ev}")
+    assert max(errs) < tol, errs
+    assert max(ev) < tol, ev
     np.testing.assert_array_equal(g.get_flags(), vortex_oracle["flags"])
 
 

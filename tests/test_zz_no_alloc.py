@@ -15,6 +15,14 @@ from paper_2102_12559_gb300 import slbm, workloads as WL
 pytestmark = pytest.mark.gpu
 
 
+def WL_lattice(k):
+    """1-D velocities and weights of lattice k (0: D2Q9, 1: D2Q25), Table I,
+    from numpy's Gauss-HermiteE rule (probabilists' Hermite, unit variance)."""
+    n = (3, 5)[k]
+    c, w = np.polynomial.hermite_e.hermegauss(n)
+    return c, w / np.sqrt(2 * np.pi)
+
+
 def _dense_field(g, k, torch):
     """Full populations of lattice k as dense FP32 device planes."""
     pops = g.get_pops(k)                       # (ny, nx, Q), f64, full f
@@ -32,6 +40,13 @@ def test_noalloc_audit_matches_handle_audit(k, flag):
     g.step(3)
     ref = g.audit()                           # all cells carry lattice k
     field = _dense_field(g, k, torch)
+    # independent of CUDA: the same FP32 planes summed in FP64 by numpy
+    planes = field.cpu().numpy().astype(np.float64).reshape(n_q := field.shape[0], -1)
+    c, _ = WL_lattice(k)
+    cx, cy = np.tile(c, len(c)), np.repeat(c, len(c))
+    host = np.array([planes.sum(), (cx[:, None] * planes).sum(), (cy[:, None] * planes).sum(),
+                     (0.5 * (cx * cx + cy * cy)[:, None] * planes).sum()])
+    assert n_q == len(cx)
     out = torch.zeros(4, dtype=torch.float64, device="cuda")
     n = (slbm.SLBM_D2Q9, slbm.SLBM_D2Q25)[k]
     st = torch.cuda.current_stream().cuda_stream
@@ -42,6 +57,8 @@ def test_noalloc_audit_matches_handle_audit(k, flag):
         got = out.cpu().numpy()
         # FP32 copies of the populations: relative agreement to ~1e-7 per value
         np.testing.assert_allclose(got, ref, rtol=2e-6, atol=2e-6 * abs(ref[0]))
+        # the same FP32 values in another summation order: FP64 rounding only
+        np.testing.assert_allclose(got, host, rtol=1e-12, atol=1e-12 * abs(host[0]))
 
 
 def test_noalloc_audit_rejects_bad_arguments():
