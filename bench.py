@@ -560,6 +560,9 @@ def headline(args):
 def run_study(args):
     """Secondary measurements, one JSON line each (not the headline line).
 
+    vortex-fp32: the headline's plain FP32 form alone, on an N x N field of the
+      same generator and vortex density (--size N).
+
     jet: the free jet 1024 x 512 (FP32, inlet / outflow / free stream, Mach
       criterion every step), cold-L2 and back-to-back step times.
 
@@ -584,6 +587,31 @@ def run_study(args):
     from paper_2102_12559_gb300 import slbm, workloads as WL
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
+    if args.workload == "vortex-fp32":
+        # the headline's plain FP32 form alone on an N x N field of the same
+        # generator and vortex density (N = --size): W + K back-to-back steps
+        # and the per-kernel split (used for profiler captures)
+        n = args.size
+        count = max(1, VCOUNT * n * n // (VN * VN))
+        fields = WL.random_vortex_field(n, count, seed=VSEED, rmin=VRMIN, rmax=VRMAX, umax=VUMAX)
+        g = slbm.Solver(n, n, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=VTAU, interp_order=3,
+                        precision=slbm.SLBM_FP32, stream=stream)
+        g.init_equilibrium(*fields)
+        g.set_criterion(slbm.SLBM_CRIT_MACH, THR)
+        ms = time_steps(g, stream, args.steps, args.warmup)
+        kern, ksteps = profiled(g, min(args.steps, 50))
+        nhi = int(g.get_flags().sum())
+        sc_ms = kern[0] / max(ksteps, 1)
+        bytes_sc = n * n * (8 * 9 + 2) + nhi * 8 * (25 - 9)
+        print(json.dumps({
+            "study": "plain FP32 form of the random-vortex field", "n": n, "vortices": count,
+            "steps": args.steps, "ms_per_step": ms, "mlups": n * n / (ms * 1e-3) / 1e6,
+            "high_order_fraction": nhi / (n * n),
+            "kernels_ms_per_step": {k: kern[i] / max(ksteps, 1)
+                                    for i, k in enumerate(slbm.KERNEL_NAMES)},
+            "stream_collide_gbs": bytes_sc / (sc_ms * 1e-3) / 1e9}), flush=True)
+        g.close()
+        return
     if args.workload == "jet":
         # the free jet 1024 x 512 (FP32, Mach criterion every step): per-step
         # times with a 256 MiB L2 flush before each step
@@ -810,10 +838,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="slbm", choices=["slbm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", type=int, default=VN, help="grid side of the vortex-fp32 study")
     ap.add_argument("--e2e-steps", type=int, default=E2E_STEPS,
                     help="steps of the end-to-end measurement (default: the field's horizon)")
     ap.add_argument("--workload", default="vortex4096",
-                    choices=["vortex4096", "jet", "strip", "pond", "shock", "couette"],
+                    choices=["vortex4096", "vortex-fp32", "jet", "strip", "pond", "shock",
+                             "couette"],
                     help="vortex4096: the headline line; the others: secondary studies")
     args = ap.parse_args()
     if args.warmup < 3:

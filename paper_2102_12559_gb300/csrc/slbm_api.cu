@@ -19,7 +19,6 @@
 #include <new>
 #include <vector>
 
-#include <cuda.h>
 #include <cudaTypedefs.h>
 
 #include "../../include/slbm.h"
@@ -276,7 +275,6 @@ Layout make_layout(const slbm_grid* g, int lo, int hi, int order, int precision)
 void slbm::host_gauss_hermite(int n, double* c, double* w) { gauss_hermite(n, c, w); }
 
 struct slbm_s {
-  CUtensorMap tmap[2][2];        // TMA descriptors of the planes [buffer][lattice]
   slbm_grid g;
   int nlo, nhi, P, precision;
   int frame;                     // SLBM_FRAME_*
@@ -501,45 +499,6 @@ cudaError_t convert(slbm_s* h, int buf, const uint8_t* fold, const uint8_t* fnew
   });
 }
 
-// TMA descriptors of every population buffer: a 3-D tensor {pitch, rows, Q}
-// elements per lattice and buffer, box {kTX + 8, kTY + 2G, Q} (the tile, its
-// halo and every plane), no swizzle, zero fill out of bounds.
-int encode_tmaps(slbm_s* h) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
-                                         &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn)
-      return fail(h, SLBM_ECUDA, "cuTensorMapEncodeTiled is not available");
-    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
-  const int es = elem_size(h->precision);
-  for (int b = 0; b < 2; ++b)
-    for (int k = 0; k < 2; ++k) {
-      const int n = k ? h->nhi : h->nlo;
-      unsigned box[3];
-      stream_box(es, h->lay.G, n * n, box);
-      const cuuint64_t dims[3] = {(cuuint64_t)h->lay.pitch, (cuuint64_t)h->lay.rows,
-                                  (cuuint64_t)(n * n)};
-      const cuuint64_t strides[2] = {(cuuint64_t)h->lay.pitch * es,
-                                     (cuuint64_t)h->lay.plane * es};
-      const cuuint32_t boxd[3] = {box[0], box[1], box[2]};
-      const cuuint32_t estr[3] = {1, 1, 1};
-      const CUresult r = encode(
-          &h->tmap[b][k],
-          es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
-                  : (es == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32),
-          3,
-          h->pops(b, k), dims, strides, boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r != CUDA_SUCCESS) return fail(h, SLBM_ECUDA, "cuTensorMapEncodeTiled failed");
-    }
-  return SLBM_OK;
-}
-
 // The device error word.  A bounded wait that ran out makes the handle fail;
 // the co-moving frame's reports are returned once and cleared.
 int check_device_error(slbm_s* h) {
@@ -636,16 +595,15 @@ int step_once(slbm_s* h) {
   uint8_t* fnew = h->crit == SLBM_CRIT_MACH ? h->flags(h->fcur ^ 1) : fold;
   cudaError_t e;
   SLBM_CK(h, mark(h), "trace event");
-  int* err = h->at<int>(h->lay.err);
   const uint8_t* mask = h->at<uint8_t>(h->lay.tile_mask[h->mcur]);
   uint8_t* mask_next = h->at<uint8_t>(h->lay.tile_mask[h->mcur ^ 1]);
   h->pf.sched_parity = h->pd.sched_parity = (int)(h->sc_launches & 1);
   h->sc_launches++;
   e = with_types(h, [&](auto ty, const auto& prm) {
     SLBM_TYPES(ty);
-    return launch_stream_collide<S, R>(prm, h->P, &h->tmap[b][0], &h->tmap[b][1],
-                                       (S*)h->pops(nb, 0), (S*)h->pops(nb, 1), fold, fnew, mask,
-                                       mask_next, bc_dev(h), err, h->st);
+    return launch_stream_collide<S, R>(prm, h->P, (const S*)h->pops(b, 0),
+                                       (const S*)h->pops(b, 1), (S*)h->pops(nb, 0),
+                                       (S*)h->pops(nb, 1), fold, fnew, mask, mask_next, h->st);
   });
   SLBM_CK(h, e, "stream_collide launch");
   SLBM_CK(h, mark(h), "trace event");
@@ -1073,11 +1031,6 @@ int slbm_create_in(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int i
   h->ind_thr = 0.0;
   for (int s = 0; s < 4; ++s) h->bc_kind[s] = SLBM_BC_OUTFLOW;
   refresh_params(h);
-  if (encode_tmaps(h) != SLBM_OK) {
-    snprintf(g_create_err, sizeof(g_create_err), "%s", h->err);
-    delete h;
-    return SLBM_ECUDA;
-  }
   // zero everything (finite stale values), flags 0, then rest state rho = 1, u = 0
   if (cudaMemsetAsync(h->ws, 0, lay.total, h->st) != cudaSuccess) {
     snprintf(g_create_err, sizeof(g_create_err), "workspace clear failed");

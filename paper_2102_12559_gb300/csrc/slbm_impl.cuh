@@ -24,7 +24,7 @@ namespace slbm {
 
 constexpr int kMaxN = 5;        // largest 1-D node count (D1Q5)
 constexpr int kMaxP = 6;        // largest stencil (order 5)
-constexpr int kOX = 8;          // left pad of a row, elements (keeps 16-byte row starts)
+constexpr int kOX = 32;         // left pad of a row, elements (32-column tiles start on a 128-byte line in FP32)
 constexpr int kTX = 32;         // tile width  (one warp per row segment)
 constexpr int kTY = 8;          // tile height (8 warps per CTA)
 
@@ -226,21 +226,16 @@ cudaError_t launch_indicator(const Params<R>& p, const S* f0, const S* f1, const
                              cudaStream_t st);
 
 // Launchers (defined in the kernel translation units).  S = storage type,
-// R = arithmetic type.  f0 / f1: base of one buffer for lattice 0 / 1.
-// Stream-collide from the buffer described by the tensor maps tm0 / tm1
-// (TMA descriptors of lattice 0 / 1 planes: {pitch, rows, Q} elements) into
-// fout0 / fout1.  `err` receives 1 if a bounded wait ran out.
+// R = arithmetic type.  fin0 / fin1 and fout0 / fout1: base of the input and
+// output buffers' planes of lattice 0 / 1.  Stream-collide of every cell
+// (each in its flag_cur lattice) into the output buffer; with the criterion
+// on, the next flags to flag_nxt; the next-step tile masks to mask_next and
+// the post-step work words / list (Params::work, wlist, wcount).
 template <class S, class R>
-cudaError_t launch_stream_collide(const Params<R>& p, int P, const void* tm0, const void* tm1,
+cudaError_t launch_stream_collide(const Params<R>& p, int P, const S* fin0, const S* fin1,
                                   S* fout0, S* fout1, const uint8_t* flag_cur,
                                   uint8_t* flag_nxt, const uint8_t* tile_mask,
-                                  uint8_t* mask_next, const BcDev& bc, int* err,
-                                  cudaStream_t st);
-
-// Bytes of dynamic shared memory the stream-collide kernel stages per CTA, and
-// the TMA box it loads: {kTX + 8, kTY + 2G, Q}.
-size_t stream_stage_bytes(int elem_size, int nh, int G);
-void stream_box(int elem_size, int G, int Q, unsigned box[3]);
+                                  uint8_t* mask_next, cudaStream_t st);
 
 // Post-step: interface conversion for band / flipped cells (flag_old = the
 // lattice each cell was computed in, flag_new = next step's flags) and, if

@@ -1,4 +1,4 @@
-// slbm_stream.cuh -- fused stream-collide kernel (sm_103a, TMA-staged).
+// slbm_stream.cuh -- fused stream-collide kernel (sm_103a).
 //
 // One time step of every cell, lattice frame (Sec. II.C "Lattice reference
 // frame" and Sec. III.D):
@@ -18,87 +18,44 @@
 //      deviations s_i = f_i - W_i.
 //   3. optionally the Mach criterion of Sec. IV.A for the next step's flag.
 //
-// Work is split into 32 x 8 tiles, one cell per thread; a warp is one 32-cell
-// row segment.  A persistent CTA (two per SM) walks its tiles; for each
-// lattice a tile holds, one elected thread loads every plane of that lattice
-// for the tile and its halo -- a [Q][8 + 2G][40] box -- with a single 3-D TMA
-// copy (cp.async.bulk.tensor) into a shared-memory stage, completion signalled
-// on an mbarrier, while the previous stage computes.  Threads stream from
-// shared memory, where a warp's 32 consecutive taps hit 32 distinct banks.
-// Each (tile, lattice) item runs only that lattice's Q-specific code on the
-// lanes whose cells carry it, so no warp diverges on Q and a tile of one
-// lattice costs one pass.
+// Work is split into strips of 32 columns by up to four 32 x 8 tiles (fewer
+// on small grids, so that every SM gets enough warps).  Every warp works on
+// its own: it takes the next strip from a global counter and, for each
+// lattice the strip's tiles hold, sweeps the strip's rows top to bottom with
+// one lane per column.
+//   * A population whose shift has a fractional y part keeps the
+//     x-interpolations of the P rows of its stencil in registers and
+//     interpolates one new row per output row, so each input row is
+//     x-interpolated once per population instead of once per cell that reads
+//     it.
+//   * Taps are read straight from the population planes through the
+//     read-only path: rows start 128-byte aligned (kOX), so a warp's 32
+//     columns of a plane row are one cache line and the neighbouring lanes'
+//     overlapping taps hit L1; two rows ahead of the sweep, a few lanes
+//     prefetch the lines of every plane into L1.
+//   * Each row's cells collide in registers and are stored on the lanes
+//     whose cell carries the lattice.
+// There is no block-wide synchronisation: warps meet only at the strip
+// counter and at the per-tile work words of the post-step kernel.
+// (Staging the rows through shared memory -- per-warp TMA row rings, or
+// block-wide tiles -- was measured slower: the rings cap the resident warps
+// and the block-wide tiles pay barriers per tile.)
 #pragma once
 
-#include <cuda.h>
+#include <mutex>
 
 #include "slbm_ghost.cuh"
 
 namespace slbm {
 
-// Staged row geometry per storage type: xh halo columns each side (>= G),
-// chosen so the TMA box starts 16 bytes aligned (tile x0 + kOX - xh is a
-// multiple of 16 / sizeof(S)); txp staged elements per row.
+constexpr int kStripTiles = 4;              // tiles per strip at most (strip height 32 rows)
+constexpr int kStripWarps = 4;              // warps per CTA
+// resident CTAs per SM the kernel is compiled for (FP64, the parity build, keeps
+// its registers)
 template <class S>
-struct StageGeom {
-  static constexpr int xh = sizeof(S) == 2 ? 8 : 4;
-  static constexpr int txp = kTX + 2 * xh;
-  // resident CTAs per SM the kernel is compiled for: FP16 stages are half the
-  // size, so three CTAs fit in shared memory (and 80 registers a thread)
-  static constexpr int min_blocks = sizeof(S) == 2 ? 3 : 2;
-};
-constexpr long long kWaitCycles = 2000000000LL;  // ~1 s bound on an mbarrier wait
-constexpr int kMaxDevices = 64;                 // device ordinals the launch caches cover
-
-// ------------------------------------------------------------ PTX helpers
-
-__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_fence_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait: false after ~kWaitCycles without completion.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > kWaitCycles) return false;
-  return true;
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, uint64_t* bar,
-                                            int c0, int c1, int c2) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
-      : "memory");
-}
+constexpr int strip_blocks() { return sizeof(S) == 8 ? 3 : 4; }
+constexpr int kMaxDevices = 64;             // device ordinals the launch caches cover
+constexpr int kPrefetchRows = 2;            // rows ahead a sweep prefetches into L1
 
 // ------------------------------------------------------------ the math
 
@@ -140,60 +97,110 @@ __device__ __forceinline__ __half to_storage<__half, float>(float v, uint32_t r)
   return __float2half_rz(__uint_as_float((b + r) & ~0x1fffu));
 }
 
-// One row of node jx's stencil (differential form v[r] + sum_{a != r}
-// w[a] (v[a] - v[r]), r = (P-1)/2, see LatTab).
-template <int N, bool HI, int P, class S, class R>
-__device__ __forceinline__ R row_interp(const S* row, const LatTab<R>& L, int jx) {
+// One row of node jx's stencil at plane row pointer `row` (elements a = 0 ..
+// P-1 of the stencil), differential form v[r] + sum_{a != r} w[a] (v[a] -
+// v[r]), r = (P-1)/2 (see LatTab).
+template <int P, class S, class R>
+__device__ __forceinline__ R row_interp(const S* __restrict__ row, const R* w) {
   constexpr int r = (P - 1) / 2;
-  const R vr = static_cast<R>(row[r]);
+  const R vr = static_cast<R>(__ldg(row + r));
   R t = vr;
 #pragma unroll
   for (int a = 0; a < P; ++a)
-    if (a != r) t += L.w[jx][a] * (static_cast<R>(row[a]) - vr);
+    if (a != r) t += w[a] * (static_cast<R>(__ldg(row + a)) - vr);
   return t;
 }
 
-// Stream + collide one cell of lattice L (N nodes per axis, HI = the
-// high-order lattice) from the staged planes (cell at `src`, planes PL
-// elements apart, rows StageGeom<S>::txp apart), on deviations s_i = f_i - W_i (streaming
-// is affine in the shift; the collision uses the deviation form of the
-// product equilibrium, see slbm_eq.cuh).
-template <int N, bool HI, int P, class S, class R>
-__device__ __forceinline__ void stream_collide_cell(const Params<R>& p, const LatTab<R>& L,
-                                                    const S* src, S* __restrict__ fout,
-                                                    int obase, uint32_t seed, R& ux, R& uy,
-                                                    R& drho) {
-  constexpr int kTXP = StageGeom<S>::txp;
-  constexpr int PL = (kTY + 2 * stage_halo(P)) * kTXP;
-  R f[N * N];
+// Value of population I's stencil row at plane row pointer `row`: a single
+// tap (integer x shift) or the x-interpolation.
+template <int N, bool HI, int P, int I, class S, class R>
+__device__ __forceinline__ R tap_row(const LatTab<R>& L, const S* __restrict__ row) {
+  constexpr int jx = I % N;
+  if constexpr (node_snapped(N, HI, jx))
+    return static_cast<R>(__ldg(row));
+  else
+    return row_interp<P, S, R>(row, L.w[jx]);
+}
+
+// x offset (first column relative to the cell) of population I's stencil
+template <int N, bool HI, int I, class R>
+__device__ __forceinline__ int x_off(const LatTab<R>& L) {
+  constexpr int jx = I % N;
+  if constexpr (node_snapped(N, HI, jx)) return snapped_offset(N, jx);
+  else return L.off[jx];
+}
+
+// A population is windowed when its y shift is fractional (P stencil rows).
+template <int N, bool HI, int I>
+__host__ __device__ constexpr bool windowed() { return !node_snapped(N, HI, I / N); }
+
+// Sweep state of one lattice: the y windows of the windowed populations
+// (P - 1 kept rows each; entries of the other populations are unused).
+template <int N, int P, class R>
+struct Windows {
+  R v[N * N][P - 1];
+};
+
+// Element pointer of plane i at (row r, column of `col`): col points at the
+// lane's column in plane 0 of row 0 (ghost offsets included).  Offsets are
+// 32-bit: the launcher requires Q * plane < 2^31 elements.
+template <class S>
+__device__ __forceinline__ const S* plane_row(const S* col, int plane, int pitch, int i, int r) {
+  return col + (i * plane + r * pitch);
+}
+
+template <int N, bool HI, int P, class S, class R, int I = 0>
+__device__ __forceinline__ void prime(const LatTab<R>& L, const S* col, int plane, int pitch,
+                                      int ys, Windows<N, P, R>& W) {
+  if constexpr (I < N * N) {
+    if constexpr (windowed<N, HI, I>()) {
+      const int r0 = ys + L.off[I / N];
+      const S* q = plane_row(col, plane, pitch, I, r0) + x_off<N, HI, I, R>(L);
 #pragma unroll
-  for (int jy = 0; jy < N; ++jy) {
-#pragma unroll
-    for (int jx = 0; jx < N; ++jx) {
-      const S* q = src + (jx + N * jy) * PL;
-      constexpr int dummy = 0;
-      (void)dummy;
-      const int ox = node_snapped(N, HI, jx) ? snapped_offset(N, jx) : L.off[jx];
-      const int oy = node_snapped(N, HI, jy) ? snapped_offset(N, jy) : L.off[jy];
-      q += ox + oy * kTXP;
-      R acc;
-      if (node_snapped(N, HI, jy)) {
-        acc = node_snapped(N, HI, jx) ? static_cast<R>(q[0]) : row_interp<N, HI, P, S, R>(q, L, jx);
-      } else {
-        constexpr int rr = (P - 1) / 2;
-        R rv[P];
-#pragma unroll
-        for (int b = 0; b < P; ++b)
-          rv[b] = node_snapped(N, HI, jx) ? static_cast<R>(q[b * kTXP])
-                                          : row_interp<N, HI, P, S, R>(q + b * kTXP, L, jx);
-        acc = rv[rr];
-#pragma unroll
-        for (int b = 0; b < P; ++b)
-          if (b != rr) acc += L.w[jy][b] * (rv[b] - rv[rr]);
-      }
-      f[jx + N * jy] = acc;
+      for (int b = 0; b < P - 1; ++b) W.v[I][b] = tap_row<N, HI, P, I, S, R>(L, q + b * pitch);
     }
+    prime<N, HI, P, S, R, I + 1>(L, col, plane, pitch, ys, W);
   }
+}
+
+// Streamed value of every population at output row y (windows advanced).
+template <int N, bool HI, int P, class S, class R, int I = 0>
+__device__ __forceinline__ void stream_row(const LatTab<R>& L, const S* col, int plane, int pitch,
+                                           int y, Windows<N, P, R>& W, R* f) {
+  if constexpr (I < N * N) {
+    constexpr int jy = I / N;
+    if constexpr (windowed<N, HI, I>()) {
+      constexpr int rr = (P - 1) / 2;
+      const S* q = plane_row(col, plane, pitch, I, y + L.off[jy] + P - 1) + x_off<N, HI, I, R>(L);
+      const R vn = tap_row<N, HI, P, I, S, R>(L, q);
+      R v[P];
+#pragma unroll
+      for (int b = 0; b < P - 1; ++b) v[b] = W.v[I][b];
+      v[P - 1] = vn;
+      R acc = v[rr];
+#pragma unroll
+      for (int b = 0; b < P; ++b)
+        if (b != rr) acc += L.w[jy][b] * (v[b] - v[rr]);
+      f[I] = acc;
+#pragma unroll
+      for (int b = 0; b < P - 2; ++b) W.v[I][b] = W.v[I][b + 1];
+      W.v[I][P - 2] = vn;
+    } else {
+      const S* q = plane_row(col, plane, pitch, I, y + snapped_offset(N, jy)) +
+                   x_off<N, HI, I, R>(L);
+      f[I] = tap_row<N, HI, P, I, S, R>(L, q);
+    }
+    stream_row<N, HI, P, S, R, I + 1>(L, col, plane, pitch, y, W, f);
+  }
+}
+
+// Collision of one cell of lattice L on its streamed deviations f: rho, u,
+// the product-form equilibrium and BGK (see slbm_eq.cuh); the new values go
+// to `o` (plane stride `plane`) when `store`.
+template <int N, class S, class R>
+__device__ __forceinline__ void collide(const Params<R>& p, const LatTab<R>& L, R* f,
+                                        S* __restrict__ o, bool store, uint32_t key, R& ux,
+                                        R& uy) {
   // density deviation and momentum through row / column sums of the N x N block
   R dr = R(0), mx = R(0), my = R(0);
 #pragma unroll
@@ -214,14 +221,12 @@ __device__ __forceinline__ void stream_collide_cell(const Params<R>& p, const La
   const R inv = R(1) / (R(1) + dr);
   ux = mx * inv;
   uy = my * inv;
-  drho = dr;
   R dx[N], dy[N];
   dphi<R>(L, N, ux, dx);
   dphi<R>(L, N, uy, dy);
   R px[N];
 #pragma unroll
   for (int jx = 0; jx < N; ++jx) px[jx] = L.w1[jx] + dx[jx];
-  const uint32_t key = hash32((uint32_t)obase ^ (seed * 0x9e3779b9u));  // FP16 rounding only
 #pragma unroll
   for (int jy = 0; jy < N; ++jy) {
     const R py = L.w1[jy] + dy[jy];
@@ -231,320 +236,228 @@ __device__ __forceinline__ void stream_collide_cell(const Params<R>& p, const La
       const int i = jx + N * jy;
       // f^L - W = dr px py + w_x dphi_y + dphi_x (w_y + dphi_y)
       const R feq = px[jx] * ty + L.w1[jx] * dy[jy] + dx[jx] * py;
-      const size_t idx = (size_t)i * p.plane + obase;
-      fout[idx] = to_storage<S, R>(f[i] + p.omega * (feq - f[i]), pop_random(key, i));
+      f[i] += p.omega * (feq - f[i]);
+    }
+  }
+  if (store) {
+    const int pl = (int)p.plane;
+#pragma unroll
+    for (int i = 0; i < N * N; ++i) o[i * pl] = to_storage<S, R>(f[i], pop_random(key, i));
+  }
+}
+
+// Prefetch of input row r of the Q planes for the warp's 32 columns (the
+// lines holding columns x0 - G .. x0 + 31 + G): lane l < 2 Q asks for line
+// l / Q of plane l % Q, so one or two instructions cover a row.
+template <int Q, class S>
+__device__ __forceinline__ void prefetch_row(const S* fin, int plane, int pitch, int G, int x0,
+                                             int r, int lane) {
+  constexpr int kLine = 128 / (int)sizeof(S);  // elements per cache line
+#pragma unroll
+  for (int l0 = 0; l0 < 2 * Q; l0 += 32) {
+    const int l = l0 + lane;
+    if (l < 2 * Q) {
+      const int i = l % Q, half = l / Q;
+      const int c = x0 + kOX - G + half * kLine;  // within the row (an address in the plane)
+      const S* a = fin + (i * plane + (r + G) * pitch + (c < pitch ? c : pitch - 1));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
     }
   }
 }
 
-constexpr int kStages = 2;            // staged work items in flight per CTA
-
-// Work item: tile t (coordinates tx, ty) and lattice k, for every lattice the
-// tile's mask holds (bit 0 low-order, bit 1 high-order); t = ntiles ends the
-// walk.
-struct Item {
-  int t, tx, ty, k;
-};
-
-// Dynamic tile scheduler of one CTA (run by one thread).  Tiles are taken
-// from a global counter, so CTAs that draw expensive tiles (high-order
-// lattice, two lattices) take fewer of them: a cluster of high-order tiles
-// does not pile up on the CTAs a static stride would give it.  The counter's
-// result and the taken tile's mask are fetched one decision ahead, so their
-// latencies overlap the computation.
-struct TileScheduler {
-  int* ctr;
-  const uint8_t* mask_g;
-  int ntiles, ntx;
-  int t_next, m_next;  // next tile to use and its mask (fetched)
-  int t_after;         // the one after it (counter value in flight)
-  Item cur;            // last decided item
-  int cur_mask;
-
-  __device__ __forceinline__ int take() { return atomicAdd(ctr, 1); }
-  __device__ __forceinline__ void start() {
-    t_next = take();
-    m_next = t_next < ntiles ? mask_g[t_next] : 0;
-    t_after = take();
-    cur.t = -1;
-    cur.k = 1;
-    cur_mask = 0;
-  }
-  // The item after the last decided one.
-  __device__ __forceinline__ Item decide() {
-    if (cur.t >= ntiles) return cur;
-    if (cur.t >= 0 && cur.k == 0 && (cur_mask & 2)) {
-      cur.k = 1;
-      return cur;
-    }
-    const int t = t_next;
-    cur_mask = m_next;
-    // fetch the following tile's mask, take the one after
-    t_next = t_after < ntiles ? t_after : ntiles;
-    m_next = t_next < ntiles ? mask_g[t_next] : 0;
-    t_after = t_next < ntiles ? take() : ntiles;
-    if (t >= ntiles) {
-      cur = Item{ntiles, 0, 0, 0};
-      return cur;
-    }
-    cur = Item{t, t % ntx, t / ntx, (cur_mask & 1) ? 0 : 1};
-    return cur;
-  }
-};
-
-// Position of the k-th (0-based) set bit of b, k < popc(b): a binary search
-// on the population counts of halves.
-__device__ __forceinline__ int select_bit(uint32_t b, int k) {
-  int pos = 0;
-#pragma unroll
-  for (int w = 16; w >= 1; w >>= 1) {
-    const int c = __popc(b & ((1u << w) - 1u));
-    if (k >= c) {
-      k -= c;
-      b >>= w;
-      pos += w;
-    }
-  }
-  return pos;
-}
-
-// Cell of the tile (raster index ty * 32 + tx) that thread `slot` computes
-// for an item whose cells of the item's lattice are given by the warps'
-// ballots b[0..7]: the slot-th set bit in raster order, or -1.  Threads take
-// the item's cells densely, so a lattice that covers a few cells of a tile
-// occupies a few warps instead of idling lanes in every warp.
-__device__ __forceinline__ int compact_cell(const uint32_t* b, int slot) {
-  uint32_t all = 0xffffffffu;
-#pragma unroll
-  for (int w = 0; w < kTY; ++w) all &= b[w];
-  if (all == 0xffffffffu) return slot;  // the lattice covers the whole tile
-  int base = 0;
-#pragma unroll
-  for (int w = 0; w < kTY; ++w) {
-    const int c = __popc(b[w]);
-    if (slot < base + c) return w * kTX + select_bit(b[w], slot - base);
-    base += c;
-  }
-  return -1;
-}
-
-constexpr int kRing = 4;  // decided items visible to every thread: j .. j + 3
-
-// Persistent stream-collide: each CTA walks its items through a kStages-deep
-// ring of staged buffers.  Thread 0 decides the items three ahead (dynamic
-// scheduler) and keeps kStages TMA copies in flight (the next items' planes
-// load while the current item computes); the threads compute the item's
-// cells, compacted onto the leading threads, then free the stage.
-template <int NL, int NH, int P, class S, class R>
-__global__ void __launch_bounds__(kTX * kTY, StageGeom<S>::min_blocks)
-k_stream_collide(const Params<R> p, const __grid_constant__ CUtensorMap tm0,
-                 const __grid_constant__ CUtensorMap tm1, S* __restrict__ fout0,
-                 S* __restrict__ fout1, const uint8_t* __restrict__ flag_cur,
-                 uint8_t* __restrict__ flag_nxt, const uint8_t* __restrict__ tile_mask_g,
-                 uint8_t* __restrict__ mask_next, int ntx, int ntiles, const BcDev bc,
-                 int* __restrict__ err) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full[kStages];
-  __shared__ Item ring[kRing];                // decided items, by index & (kRing - 1)
-  __shared__ int tile_bits[3];                // next-step mask of the tile being finished
-  __shared__ uint32_t ballots[2][kTY];        // cells of the item's lattice, per warp
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
-  constexpr int GH = stage_halo(P);
-  constexpr int kTXP = StageGeom<S>::txp, kXH = StageGeom<S>::xh;
-  constexpr int pl = (kTY + 2 * GH) * kTXP;  // staged elements per plane (rows y0-GH ..)
-  constexpr int stage = NH * NH * pl;        // staged elements per stage (larger lattice)
-  S* sm = reinterpret_cast<S*>(smem_raw);
-  TileScheduler sched;
-  auto issue = [&](const Item& q, int s) {
-    const int Q = q.k ? NH * NH : NL * NL;
-    mbar_expect_tx(&full[s], (uint32_t)(Q * pl * (int)sizeof(S)));
-    tma_load_3d(sm + s * stage, q.k ? &tm1 : &tm0, &full[s], q.tx * kTX + kOX - kXH,
-                q.ty * kTY + p.G - GH, 0);
-  };
-  if (tid == 0) {
-    // this launch's counter p.sched[parity] was cleared by the previous launch;
-    // clear the other one for the next
-    if (blockIdx.x == 0) {
-      p.sched[p.sched_parity ^ 1] = 0;
-      p.wcount[p.sched_parity ^ 1] = 0;  // the other work list, likewise
-    }
-    for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
-    mbar_fence_init();
-    tile_bits[0] = tile_bits[1] = tile_bits[2] = 0;
-    sched = TileScheduler{p.sched + p.sched_parity, tile_mask_g, ntiles, ntx, 0, 0, 0, Item{}, 0};
-    sched.start();
-    for (int j = 0; j < kRing - 1; ++j) ring[j] = sched.decide();
-    for (int s = 0; s < kStages; ++s)
-      if (ring[s].t < ntiles) issue(ring[s], s);
-  }
-  __syncthreads();
-  // this thread's raster cell flag for an item (2 outside the grid)
-  auto cell_flag = [&](const Item& q) -> int {
-    if (q.t >= ntiles) return 2;
-    const int xx = q.tx * kTX + tx, yy = q.ty * kTY + ty;
-    return (xx < p.nx && yy < p.ny) ? flag_cur[xx + p.nx * yy] : 2;
-  };
-  {
-    const Item it0 = ring[0];
-    const uint32_t b = __ballot_sync(0xffffffffu, cell_flag(it0) == it0.k);
-    if (tx == 0) ballots[0][ty] = b;
-  }
-  int fl_next = cell_flag(ring[1]);  // flags are loaded one item ahead
-  __syncthreads();
-  const uint32_t seed = *p.seed_ctr;  // FP16 rounding key of this step
-  int bits = 0;  // cells this thread computed: bit 0/1 = next-step lattice, bit 2 = flipped
-  // threads 0-8: a work-word atomic and a list slot whose results are used
-  // at the next tile end (tile -1: none)
-  int pend_t = -1, pend_was = 0, slot_t = -1, slot = 0;
-  for (int j = 0;; ++j) {
-    const Item it = ring[j & (kRing - 1)];
-    if (it.t >= ntiles) break;
-    const Item nx_it = ring[(j + 1) & (kRing - 1)];
-    const Item nn_it = ring[(j + 2) & (kRing - 1)];
-    if (tid == 0) ring[(j + 3) & (kRing - 1)] = sched.decide();  // published by the barrier
-    const int s = j % kStages;
-    const int x0 = it.tx * kTX, y0 = it.ty * kTY;
-    const int cell = compact_cell(ballots[j & 1], tid);
-    // ballot of the next item's cells (published by the barrier below)
+// One lattice's sweep of a strip: output rows ys .. ye-1 of column x (lane),
+// every cell of the lattice streamed, collided and stored; the next flag
+// (criterion) written; per tile q of the strip, the OR of the cells' bits
+// (bit 0/1: next-step lattice, bit 2: flipped) into tb[q].
+template <int N, bool HI, int P, class S, class R>
+__device__ __forceinline__ void sweep(const Params<R>& p, const LatTab<R>& L, int k,
+                                      const S* __restrict__ fin, S* __restrict__ fout,
+                                      const uint8_t* __restrict__ flag_cur,
+                                      uint8_t* __restrict__ flag_nxt, int x, int y0, int ys,
+                                      int ye, uint32_t seed, int* tb) {
+  const bool xin = x < p.nx;
+  const int xl = xin ? x : p.nx - 1;  // loads of lanes past the edge stay in the row
+  const S* col = fin + (p.G * p.pitch + xl + kOX);
+  const int plane = (int)p.plane;
+  Windows<N, P, R> W;
+  prime<N, HI, P, S, R>(L, col, plane, p.pitch, ys, W);
+  int bits = 0;
+  const int x0 = x & ~(kTX - 1), lane = threadIdx.x & 31;
+  const int rlast = ye + stage_halo(P) - 1;  // last input row the sweep reads
+  for (int y = ys; y < ye; ++y) {
+    R f[N * N];
     {
-      const uint32_t b = __ballot_sync(0xffffffffu, fl_next == nx_it.k);
-      if (tx == 0) ballots[(j + 1) & 1][ty] = b;
+      const int r = y + stage_halo(P) + kPrefetchRows;
+      if (r <= rlast) prefetch_row<N * N, S>(fin, plane, p.pitch, p.G, x0, r, lane);
     }
-    if (!mbar_wait(&full[s], (uint32_t)((j / kStages) & 1))) {
-      // bounded: record, give the copy one more bounded wait, stop
-      if (tid == 0) atomicExch(err, 1);
-      mbar_wait(&full[s], (uint32_t)((j / kStages) & 1));
-      return;
-    }
-    fl_next = cell_flag(nn_it);
-    if (cell >= 0) {
-      const int cx = cell & (kTX - 1), cy = cell / kTX;
-      const S* src = sm + s * stage + (cy + GH) * kTXP + (cx + kXH);
-      const int x = x0 + cx, y = y0 + cy;
-      const int obase = (y + p.G) * p.pitch + (x + kOX);
-      R ux, uy, dr;  // dr: density deviation (unused here)
-      if (it.k == 0)
-        stream_collide_cell<NL, false, P, S, R>(p, p.lat[0], src, fout0, obase, seed, ux, uy, dr);
-      else
-        stream_collide_cell<NH, true, P, S, R>(p, p.lat[1], src, fout1, obase, seed, ux, uy, dr);
-      int nf = it.k;
+    stream_row<N, HI, P, S, R>(L, col, plane, p.pitch, y, W, f);
+    const bool act = xin && flag_cur[y * p.nx + x] == k;
+    const int ob = (y + p.G) * p.pitch + (x + kOX);
+    const uint32_t key = hash32((uint32_t)ob ^ (seed * 0x9e3779b9u));  // FP16 rounding only
+    R ux, uy;
+    collide<N, S, R>(p, L, f, fout + ob, act, key, ux, uy);
+    if (act) {
+      int nf = k;
       if (p.crit == 1) {
         nf = sqrt(ux * ux + uy * uy) > p.thr ? 1 : 0;
-        flag_nxt[x + p.nx * y] = (uint8_t)nf;
+        flag_nxt[y * p.nx + x] = (uint8_t)nf;
       }
-      bits |= (1 << nf) | (nf != it.k ? 4 : 0);
+      bits |= (1 << nf) | (nf != k ? 4 : 0);
     }
-    // after a tile's last item: the lattices its cells carry next step and
-    // whether any flipped (read by the post-step kernel to skip quiet tiles
-    // and by the next launch's scheduler), OR-reduced per warp, then through
-    // a shared word made visible by the stage-release barrier below
-    const bool tile_end = nx_it.t != it.t;
-    if (tile_end) {
-      const int wbits = __reduce_or_sync(0xffffffffu, bits);
-      if (tx == 0 && wbits) atomicOr(&tile_bits[j % 3], wbits);
+    // after a tile's last row: its bits, OR-reduced over the warp
+    if (((y - y0) & (kTY - 1)) == kTY - 1 || y == ye - 1) {
+      const int wb = __reduce_or_sync(0xffffffffu, bits);
+      if ((threadIdx.x & 31) == 0) tb[(y - y0) / kTY] |= wb;
       bits = 0;
     }
-    // the slot the next item accumulates into was last read two items ago
-    if (tid == 0) tile_bits[(j + 1) % 3] = 0;
-    __syncthreads();  // stage s is free again; tile_bits, ballots and ring complete
-    if (tile_end && tid < 9) {
-      // the tile's next-step mask, and its contribution to the post-step
-      // kernel's work bits of the 3 x 3 tile neighbourhood: the lattices (all
-      // nine) and the flip bit (the tile itself); a tile has conversion work
-      // iff its word ends with both lattices or a flip, and is then listed
-      const int m = tile_bits[j % 3];
-      if (tid == 0) mask_next[it.t] = (uint8_t)m;
-      int ntx_ = it.tx + tid % 3 - 1, nty_ = it.ty + tid / 3 - 1;
-      const int nty = (ntiles + ntx - 1) / ntx;
-      bool ok = true;
-      if (ntx_ < 0 || ntx_ >= ntx) {
-        if (p.periodic_x) ntx_ = ntx_ < 0 ? ntx_ + ntx : ntx_ - ntx;
-        else ok = false;
-      }
-      if (nty_ < 0 || nty_ >= nty) {
-        if (p.periodic_y) nty_ = nty_ < 0 ? nty_ + nty : nty_ - nty;
-        else ok = false;
-      }
-      // listing as add_work, with each returning atomic's result used one
-      // tile later, so the CTA does not wait for it
-      const int half = p.sched_parity;
-      if (slot_t >= 0) p.wlist[(size_t)half * ntiles + slot] = slot_t;
-      slot_t = -1;
-      if (pend_t >= 0 && !(pend_was & 6)) {
-        slot = atomicAdd(p.wcount + half, 1);
-        slot_t = pend_t;
-      }
-      pend_t = -1;
-      const int contrib = (m & 3) | (tid == 4 ? (m & 4) : 0);
-      if (ok && contrib) {
-        int* w = p.work + (size_t)half * ntiles + nty_ * ntx + ntx_;
-        if (contrib & 6) {
-          pend_was = atomicOr(w, contrib);
-          pend_t = nty_ * ntx + ntx_;
-        } else {
-          atomicOr(w, contrib);
-        }
-      }
-      // the other half is the next step's: clear this tile's word there
-      if (tid == 0) p.work[(p.sched_parity ^ 1) * ntiles + it.t] = 0;
-    }
-    if (tid == 0) {
-      if (nn_it.t < ntiles) {
-        // order the CTA's shared-memory reads of stage s before the async-proxy write
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue(nn_it, s);
-      }
-    }
-  }
-  if (tid < 9) {  // the deferred listings of the last tile
-    const size_t h = (size_t)p.sched_parity * ntiles;
-    if (slot_t >= 0) p.wlist[h + slot] = slot_t;
-    if (pend_t >= 0 && !(pend_was & 6)) p.wlist[h + atomicAdd(p.wcount + p.sched_parity, 1)] = pend_t;
   }
 }
 
-template <class S, class R>
-cudaError_t launch_stream_collide_impl(const Params<R>& p, int P, const CUtensorMap* tm0,
-                                       const CUtensorMap* tm1, S* fout0, S* fout1,
-                                       const uint8_t* flag_cur, uint8_t* flag_nxt,
-                                       const uint8_t* tile_mask, uint8_t* mask_next,
-                                       const BcDev& bc, int* err, cudaStream_t st) {
-  const dim3 blk(kTX, kTY);
-  const int ntx = (p.nx + kTX - 1) / kTX, nty = (p.ny + kTY - 1) / kTY;
+// Persistent stream-collide: warps take strips from the global counter
+// p.sched[parity] (cleared by the previous launch; this launch clears the
+// other one) and sweep them lattice by lattice; then, per tile of the strip,
+// write its next-step mask (lattices and flip bit, read by the next launch and
+// the post-step kernel) and OR its lattices into the post-step work words of
+// its 3 x 3 tile neighbourhood (its flip bit into its own), listing the tiles
+// that gain work (add_work, with each returning atomic's result used one tile
+// later so the warp does not wait for it).
+template <int NL, int NH, int P, class S, class R>
+__global__ void __launch_bounds__(kStripWarps * 32, strip_blocks<S>())
+k_stream_collide(const Params<R> p, const S* __restrict__ fin0, const S* __restrict__ fin1,
+                 S* __restrict__ fout0, S* __restrict__ fout1,
+                 const uint8_t* __restrict__ flag_cur, uint8_t* __restrict__ flag_nxt,
+                 const uint8_t* __restrict__ tile_mask_g, uint8_t* __restrict__ mask_next,
+                 int ntx, int nty, int stiles, int nstrips) {
+  __shared__ int s_tb[kStripWarps][kStripTiles];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ntiles = ntx * nty;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    p.sched[p.sched_parity ^ 1] = 0;
+    p.wcount[p.sched_parity ^ 1] = 0;  // the other work list, likewise
+  }
+  const uint32_t seed = *p.seed_ctr;  // FP16 rounding key of this step
+  int* tb = s_tb[warp];
+  // lanes 0-8: a work-word atomic and a list slot whose results are used at
+  // the next tile (tile -1: none)
+  int pend_t = -1, pend_was = 0, slot_t = -1, slot = 0;
+  const int half = p.sched_parity;
+  for (;;) {
+    int s = 0;
+    if (lane == 0) s = atomicAdd(p.sched + p.sched_parity, 1);
+    s = __shfl_sync(0xffffffffu, s, 0);
+    if (s >= nstrips) break;
+    const int sx = s % ntx, ty0 = (s / ntx) * stiles;
+    const int nt = nty - ty0 < stiles ? nty - ty0 : stiles;  // tiles in the strip
+    const int m = lane < nt ? tile_mask_g[(ty0 + lane) * ntx + sx] : 0;
+    const uint32_t has_lo = __ballot_sync(0xffffffffu, m & 1);
+    const uint32_t has_hi = __ballot_sync(0xffffffffu, m & 2);
+    if (lane < kStripTiles) tb[lane] = 0;
+    __syncwarp();
+    const int x = sx * kTX + lane, y0 = ty0 * kTY;
+    // each lattice over the rows of its first to its last tile in the strip
+    if (has_lo) {
+      const int ys = y0 + (__ffs(has_lo) - 1) * kTY;
+      const int ye = min(y0 + (32 - __clz(has_lo)) * kTY, p.ny);
+      sweep<NL, false, P, S, R>(p, p.lat[0], 0, fin0, fout0, flag_cur, flag_nxt, x, y0, ys, ye,
+                                seed, tb);
+    }
+    if (has_hi) {
+      const int ys = y0 + (__ffs(has_hi) - 1) * kTY;
+      const int ye = min(y0 + (32 - __clz(has_hi)) * kTY, p.ny);
+      sweep<NH, true, P, S, R>(p, p.lat[1], 1, fin1, fout1, flag_cur, flag_nxt, x, y0, ys, ye,
+                               seed, tb);
+    }
+    __syncwarp();
+    for (int q = 0; q < nt; ++q) {
+      const int t = (ty0 + q) * ntx + sx;
+      const int mk = tb[q];
+      if (lane == 0) {
+        mask_next[t] = (uint8_t)mk;
+        p.work[(size_t)(p.sched_parity ^ 1) * ntiles + t] = 0;  // the next step's half
+      }
+      if (lane < 9) {
+        int ntx_ = sx + lane % 3 - 1, nty_ = ty0 + q + lane / 3 - 1;
+        bool in = true;
+        if (ntx_ < 0 || ntx_ >= ntx) {
+          if (p.periodic_x) ntx_ = ntx_ < 0 ? ntx_ + ntx : ntx_ - ntx;
+          else in = false;
+        }
+        if (nty_ < 0 || nty_ >= nty) {
+          if (p.periodic_y) nty_ = nty_ < 0 ? nty_ + nty : nty_ - nty;
+          else in = false;
+        }
+        if (slot_t >= 0) p.wlist[(size_t)half * ntiles + slot] = slot_t;
+        slot_t = -1;
+        if (pend_t >= 0 && !(pend_was & 6)) {
+          slot = atomicAdd(p.wcount + half, 1);
+          slot_t = pend_t;
+        }
+        pend_t = -1;
+        const int contrib = (mk & 3) | (lane == 4 ? (mk & 4) : 0);
+        if (in && contrib) {
+          int* w = p.work + (size_t)half * ntiles + nty_ * ntx + ntx_;
+          if (contrib & 6) {
+            pend_was = atomicOr(w, contrib);
+            pend_t = nty_ * ntx + ntx_;
+          } else {
+            atomicOr(w, contrib);
+          }
+        }
+      }
+    }
+    __syncwarp();  // tb is reset by the next strip
+  }
+  if (lane < 9) {  // the deferred listings of the last tile
+    const size_t h = (size_t)half * ntiles;
+    if (slot_t >= 0) p.wlist[h + slot] = slot_t;
+    if (pend_t >= 0 && !(pend_was & 6)) p.wlist[h + atomicAdd(p.wcount + half, 1)] = pend_t;
+  }
+}
+
+// Launch cache of one instantiation on one device: the occupancy, queried
+// once under a lock.
+struct LaunchCache {
+  std::mutex mu;
+  int per_sm[kMaxDevices] = {};
+};
+
+template <class S, class R>
+cudaError_t launch_stream_collide_impl(const Params<R>& p, int P, const S* fin0, const S* fin1,
+                                       S* fout0, S* fout1, const uint8_t* flag_cur,
+                                       uint8_t* flag_nxt, const uint8_t* tile_mask,
+                                       uint8_t* mask_next, cudaStream_t st) {
+  const int ntx = (p.nx + kTX - 1) / kTX, nty = (p.ny + kTY - 1) / kTY;
+  // strip height: the most tiles (up to four) that still give every SM
+  // about 32 strips
+  int stiles = kStripTiles;
+  while (stiles > 1 && (long long)ntx * ((nty + stiles - 1) / stiles) < 32LL * p.nsm) stiles /= 2;
+  const int nstrips = ntx * ((nty + stiles - 1) / stiles);
   const int nl = p.lat[0].n, nh = p.lat[1].n;
-  const size_t smem =
-      (size_t)kStages * nh * nh * (kTY + 2 * stage_halo(P)) * StageGeom<S>::txp * sizeof(S);
-  if (p.G < stage_halo(P)) return cudaErrorInvalidValue;  // ghost ring narrower than the stage halo
-  const int nsm = p.nsm;
-  // the dynamic shared-memory attribute and the occupancy are per device:
-  // cached per device ordinal (handles of one process may live on several)
+  if (p.G < stage_halo(P)) return cudaErrorInvalidValue;  // ghost ring narrower than the stencil
+  // 32-bit element offsets within one lattice's planes
+  if ((long long)nh * nh * p.plane >= (1LL << 31)) return cudaErrorInvalidValue;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return cudaErrorInvalidDevice;
 #define SLBM_SC_CASE(NL, NH, PP)                                                            \
   if (nl == NL && nh == NH && P == PP) {                                                    \
     auto kern = k_stream_collide<NL, NH, PP, S, R>;                                         \
-    static size_t attr_set[kMaxDevices] = {}; /* largest dynamic size granted so far */     \
-    if (smem > attr_set[dev]) {                                                             \
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                           (int)smem);                                      \
-      if (e != cudaSuccess) return e;                                                       \
-      attr_set[dev] = smem;                                                                 \
+    static LaunchCache cache;                                                               \
+    int per_sm = 0;                                                                         \
+    {                                                                                       \
+      std::lock_guard<std::mutex> lock(cache.mu);                                           \
+      if (cache.per_sm[dev] < 1) {                                                          \
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(                \
+            &cache.per_sm[dev], kern, kStripWarps * 32, 0);                                 \
+        if (e != cudaSuccess) return e;                                                     \
+      }                                                                                     \
+      per_sm = cache.per_sm[dev];                                                           \
     }                                                                                       \
-    static size_t occ_smem[kMaxDevices] = {}; /* occupancy queried once per size */         \
-    static int occ_per_sm[kMaxDevices] = {};                                                \
-    if (occ_smem[dev] != smem) {                                                            \
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_per_sm[dev], kern, \
-                                                                    kTX * kTY, smem);       \
-      if (e != cudaSuccess) return e;                                                       \
-      occ_smem[dev] = smem;                                                                 \
-    }                                                                                       \
-    const int per_sm = occ_per_sm[dev];                                                     \
     if (per_sm < 1) return cudaErrorInvalidConfiguration;                                   \
-    const int grid = ntiles < per_sm * nsm ? ntiles : per_sm * nsm;                         \
-    kern<<<grid, blk, smem, st>>>(p, *tm0, *tm1, fout0, fout1, flag_cur, flag_nxt,          \
-                                  tile_mask, mask_next, ntx, ntiles, bc, err);              \
+    const int want = (nstrips + kStripWarps - 1) / kStripWarps;                             \
+    const int grid = want < per_sm * p.nsm ? want : per_sm * p.nsm;                         \
+    kern<<<grid, kStripWarps * 32, 0, st>>>(p, fin0, fin1, fout0, fout1, flag_cur, flag_nxt, \
+                                            tile_mask, mask_next, ntx, nty, stiles, nstrips); \
     return cudaGetLastError();                                                              \
   }
 #define SLBM_SC_PAIR(NL, NH) \

@@ -4,14 +4,12 @@
 
 namespace slbm {
 template <>
-cudaError_t launch_stream_collide<__half, float>(const Params<float>& p, int P, const void* tm0,
-                                                 const void* tm1, __half* fout0, __half* fout1,
-                                                 const uint8_t* flag_cur, uint8_t* flag_nxt,
-                                                 const uint8_t* tile_mask, uint8_t* mask_next,
-                                                 const BcDev& bc, int* err, cudaStream_t st) {
-  return launch_stream_collide_impl<__half, float>(p, P, static_cast<const CUtensorMap*>(tm0),
-                                                   static_cast<const CUtensorMap*>(tm1), fout0,
-                                                   fout1, flag_cur, flag_nxt, tile_mask,
-                                                   mask_next, bc, err, st);
+cudaError_t launch_stream_collide<__half, float>(const Params<float>& p, int P, const __half* fin0,
+                                        const __half* fin1, __half* fout0, __half* fout1,
+                                        const uint8_t* flag_cur, uint8_t* flag_nxt,
+                                        const uint8_t* tile_mask, uint8_t* mask_next,
+                                        cudaStream_t st) {
+  return launch_stream_collide_impl<__half, float>(p, P, fin0, fin1, fout0, fout1, flag_cur, flag_nxt,
+                                          tile_mask, mask_next, st);
 }
 }  // namespace slbm
