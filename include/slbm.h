@@ -157,7 +157,11 @@ SLBM_API int slbm_workspace_bytes(const slbm_grid *g, int lat_lo, int lat_hi, in
  * value; precision SLBM_FP32 or SLBM_FP64; cuda_stream is a
  * cudaStream_t (NULL = the legacy default stream).  The handle allocates its
  * own device workspace.  Populations start at rest (rho = 1, u = 0), flags 0,
- * criterion none, every non-periodic side OUTFLOW. */
+ * criterion none, every non-periodic side OUTFLOW.  SLBM_EINVAL for bad
+ * arguments, among them a grid narrower than 2 G + 1 cells per side (G = the
+ * stencil reach) and, in the lattice frame, a periodic axis whose last
+ * partial 32 x 8 tile is narrower than G (nx % 32 and ny % 8 must be 0 or at
+ * least G). */
 SLBM_API int slbm_create(const slbm_grid *g, int lat_lo, int lat_hi, double tau, int interp_order,
                 int frame, int precision, void *cuda_stream, slbm_t *out);
 

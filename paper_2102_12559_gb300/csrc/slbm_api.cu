@@ -922,6 +922,16 @@ bool create_args_ok(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int 
              2 * lay.G + 1);
     return false;
   }
+  // lattice frame: interface work is found per 32 x 8 tile from the tiles next
+  // to it, so across a periodic side the last (partial) tile must span the
+  // stencil reach
+  if (frame == SLBM_FRAME_LATTICE &&
+      ((g->periodic_x && g->nx % kTX != 0 && g->nx % kTX < lay.G) ||
+       (g->periodic_y && g->ny % kTY != 0 && g->ny % kTY < lay.G))) {
+    snprintf(g_create_err, sizeof(g_create_err),
+             "periodic grid: nx %% %d and ny %% %d must be 0 or at least %d", kTX, kTY, lay.G);
+    return false;
+  }
   return true;
 }
 

@@ -144,33 +144,67 @@ __device__ __forceinline__ bool post_tile(const Params<R>& p, S* f0, S* f1,
     const int any_hi = __syncthreads_or(nw == 1);
     if (threadIdx.x == 0 && threadIdx.y == 0) *mask_out = (uint8_t)(any_lo | (any_hi << 1));
   }
+  // cells that need a conversion, compacted onto the leading threads (the
+  // ones computed in the low-order lattice first), so that one or two warps
+  // of the tile do the arithmetic: entry = cell | old << 8 | nw << 9 | band << 10
+  __shared__ int s_conv[kTX * kTY];
+  __shared__ int s_cnt[2][kTY];
+  const int tid = threadIdx.y * kTX + threadIdx.x;
+  bool conv = false, band = false;
   if (in) {
-    bool band = false;
     for (int dy = -B; dy <= B; ++dy)
       for (int dx = -B; dx <= B; ++dx) {
         const int u = sf[threadIdx.y + B + dy][threadIdx.x + B + dx];
         band |= (u != 2) && (u != nw);
       }
-    const int base = (y + p.G) * p.pitch + (x + kOX);
-    if (old != nw || band) {
-      R a[kMaxN][kMaxN], b[kMaxN][kMaxN];
-      using M = PostMath<NL, NH, R>;
-      if (old == 0) {
-        load_t<NL, S, R>(f0, p.plane, base, a);
-        M::lift(p, a, b);
-        store_t<NH, S, R>(f1, p.plane, base, b);
-        if (old != nw && band) {  // now high-order; low-order readers see its projection
-          M::project(p, b, a);
-          store_t<NL, S, R>(f0, p.plane, base, a);
-        }
-      } else {
-        load_t<NH, S, R>(f1, p.plane, base, b);
+    conv = old != nw || band;
+  }
+  const unsigned b0 = __ballot_sync(0xffffffffu, conv && old == 0);
+  const unsigned b1 = __ballot_sync(0xffffffffu, conv && old != 0);
+  if (threadIdx.x == 0) {
+    s_cnt[0][threadIdx.y] = __popc(b0);
+    s_cnt[1][threadIdx.y] = __popc(b1);
+  }
+  __syncthreads();
+  int n0 = 0, n1 = 0, pre0 = 0, pre1 = 0;
+#pragma unroll
+  for (int w = 0; w < kTY; ++w) {
+    const int c0 = s_cnt[0][w], c1 = s_cnt[1][w];
+    if (w < (int)threadIdx.y) {
+      pre0 += c0;
+      pre1 += c1;
+    }
+    n0 += c0;
+    n1 += c1;
+  }
+  if (conv) {
+    const unsigned lt = (1u << threadIdx.x) - 1u;
+    const int slot = old == 0 ? pre0 + __popc(b0 & lt) : n0 + pre1 + __popc(b1 & lt);
+    s_conv[slot] = tid | (old << 8) | (nw << 9) | ((int)band << 10);
+  }
+  __syncthreads();
+  if (tid < n0 + n1) {
+    const int e = s_conv[tid];
+    const int cell = e & 255, o = (e >> 8) & 1, nn = (e >> 9) & 1, bd = (e >> 10) & 1;
+    const int cx = x0 + (cell & (kTX - 1)), cy = y0 + cell / kTX;
+    const int base = (cy + p.G) * p.pitch + (cx + kOX);
+    R a[kMaxN][kMaxN], b[kMaxN][kMaxN];
+    using M = PostMath<NL, NH, R>;
+    if (o == 0) {
+      load_t<NL, S, R>(f0, p.plane, base, a);
+      M::lift(p, a, b);
+      store_t<NH, S, R>(f1, p.plane, base, b);
+      if (o != nn && bd) {  // now high-order; low-order readers see its projection
         M::project(p, b, a);
         store_t<NL, S, R>(f0, p.plane, base, a);
-        if (old != nw && band) {  // now low-order; high-order readers see its lifting
-          M::lift(p, a, b);
-          store_t<NH, S, R>(f1, p.plane, base, b);
-        }
+      }
+    } else {
+      load_t<NH, S, R>(f1, p.plane, base, b);
+      M::project(p, b, a);
+      store_t<NL, S, R>(f0, p.plane, base, a);
+      if (o != nn && bd) {  // now low-order; high-order readers see its lifting
+        M::lift(p, a, b);
+        store_t<NH, S, R>(f1, p.plane, base, b);
       }
     }
   }

@@ -265,6 +265,12 @@ __device__ __forceinline__ void prefetch_row(const S* fin, int plane, int pitch,
   }
 }
 
+// Bit position, in a tile's strip word, of the next-step lattices (2 bits:
+// low / high) of its cells within the band radius of side (sx, sy) -- sx, sy
+// in {0, 1, 2} = left / whole / right, top / whole / bottom; (1, 1) is not
+// used (the tile's own lattices are bits 0-1).
+__host__ __device__ constexpr int side_shift(int sx, int sy) { return 8 + 2 * (sx + 3 * sy); }
+
 // One lattice's sweep of a strip: output rows ys .. ye-1 of column x (lane),
 // every cell of the lattice streamed, collided and stored; the next flag
 // (criterion) written; per tile q of the strip, the OR of the cells' bits
@@ -281,7 +287,7 @@ __device__ __forceinline__ void sweep(const Params<R>& p, const LatTab<R>& L, in
   const int plane = (int)p.plane;
   Windows<N, P, R> W;
   prime<N, HI, P, S, R>(L, col, plane, p.pitch, ys, W);
-  int bits = 0;
+  int bits = 0, sides = 0;
   const int x0 = x & ~(kTX - 1), lane = threadIdx.x & 31;
   const int rlast = ye + stage_halo(P) - 1;  // last input row the sweep reads
   for (int y = ys; y < ye; ++y) {
@@ -296,19 +302,44 @@ __device__ __forceinline__ void sweep(const Params<R>& p, const LatTab<R>& L, in
     const uint32_t key = hash32((uint32_t)ob ^ (seed * 0x9e3779b9u));  // FP16 rounding only
     R ux, uy;
     collide<N, S, R>(p, L, f, fout + ob, act, key, ux, uy);
+    int nf = k;
     if (act) {
-      int nf = k;
       if (p.crit == 1) {
         nf = sqrt(ux * ux + uy * uy) > p.thr ? 1 : 0;
         flag_nxt[y * p.nx + x] = (uint8_t)nf;
       }
       bits |= (1 << nf) | (nf != k ? 4 : 0);
     }
+    // the next-step lattices of the row's cells near the tile's sides
+    // (warp-uniform): within `band` columns of the left / right side, and, in
+    // the first / last `band` rows of the tile, of the top / bottom side
+    {
+      const unsigned blo = __ballot_sync(0xffffffffu, act && nf == 0);
+      const unsigned bhi = __ballot_sync(0xffffffffu, act && nf == 1);
+      // the tile's valid columns 0 .. w-1 and rows 0 .. h-1 (a tile at the
+      // grid's right / bottom edge may be partial: its facing strips are
+      // then its last valid columns / rows, next to the periodic image)
+      const int w = min(kTX, p.nx - x0), r = (y - y0) & (kTY - 1);
+      const int h = min(kTY, p.ny - (y - r));
+      const unsigned all = w >= 32 ? ~0u : (1u << w) - 1u;
+      const unsigned lm = (1u << p.band) - 1u;
+      const unsigned rm = all & ~(w > p.band ? (1u << (w - p.band)) - 1u : 0u);
+      const int row = (blo ? 1 : 0) | (bhi ? 2 : 0);
+      const int lf = ((blo & lm) ? 1 : 0) | ((bhi & lm) ? 2 : 0);
+      const int rt = ((blo & rm) ? 1 : 0) | ((bhi & rm) ? 2 : 0);
+      int e = (lf << side_shift(0, 1)) | (rt << side_shift(2, 1));
+      if (r < p.band)
+        e |= (lf << side_shift(0, 0)) | (row << side_shift(1, 0)) | (rt << side_shift(2, 0));
+      if (r >= h - p.band)
+        e |= (lf << side_shift(0, 2)) | (row << side_shift(1, 2)) | (rt << side_shift(2, 2));
+      sides |= e;
+    }
     // after a tile's last row: its bits, OR-reduced over the warp
     if (((y - y0) & (kTY - 1)) == kTY - 1 || y == ye - 1) {
       const int wb = __reduce_or_sync(0xffffffffu, bits);
-      if ((threadIdx.x & 31) == 0) tb[(y - y0) / kTY] |= wb;
+      if ((threadIdx.x & 31) == 0) tb[(y - y0) / kTY] |= wb | sides;
       bits = 0;
+      sides = 0;
     }
   }
 }
@@ -372,7 +403,7 @@ k_stream_collide(const Params<R> p, const S* __restrict__ fin0, const S* __restr
       const int t = (ty0 + q) * ntx + sx;
       const int mk = tb[q];
       if (lane == 0) {
-        mask_next[t] = (uint8_t)mk;
+        mask_next[t] = (uint8_t)(mk & 7);
         p.work[(size_t)(p.sched_parity ^ 1) * ntiles + t] = 0;  // the next step's half
       }
       if (lane < 9) {
@@ -393,7 +424,12 @@ k_stream_collide(const Params<R> p, const S* __restrict__ fin0, const S* __restr
           slot_t = pend_t;
         }
         pend_t = -1;
-        const int contrib = (mk & 3) | (lane == 4 ? (mk & 4) : 0);
+        // to the neighbour at (dx, dy) = (lane % 3 - 1, lane / 3 - 1): the
+        // lattices of this tile's cells within the band radius of the side
+        // or corner facing it; to itself, its own lattices and flip bit.  A
+        // tile's word then holds both lattices iff one of its cells is within
+        // the band radius of a cell of the other lattice.
+        const int contrib = lane == 4 ? (mk & 7) : (mk >> side_shift(lane % 3, lane / 3)) & 3;
         if (in && contrib) {
           int* w = p.work + (size_t)half * ntiles + nty_ * ntx + ntx_;
           if (contrib & 6) {
