@@ -371,12 +371,17 @@ k_post_step(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ flag_ol
   // the count and this CTA's first list entry are fetched together (each half
   // of the list holds ntiles entries, so the entry is always in bounds)
   const int ntiles = ntx * ((p.ny + kTY - 1) / kTY);
-  const int nl = *nlist;
+  // every index read from the stream kernel's outputs is checked before it
+  // addresses anything: the count against the list's capacity, each entry
+  // against the tile count (a tile is listed at most once per step, so a
+  // valid list never exceeds either)
+  const int nl = min(max(*nlist, 0), ntiles);
   const int t_first = (int)blockIdx.x < ntiles ? list[blockIdx.x] : 0;
   const int total = nl + n_ghtiles;
   for (int r = (int)blockIdx.x; r < total; r += G) {
     if (r < nl) {
       const int t = r == (int)blockIdx.x ? t_first : list[r];
+      if (t < 0 || t >= ntiles) continue;  // uniform per CTA: no barrier is skipped by part of it
       // the tile's ghost list bounds are fetched with its work word and flags
       // (through shared memory: published by post_tile's barriers)
       if (tid == 0) {

@@ -71,6 +71,22 @@ def test_convected_vortex_200_steps_fp16(vortex_oracle):
     assert er < 1e-4 and eu < 1e-3
 
 
+@pytest.mark.xfail(strict=True, reason="the reduced-precision target of 1e-4 relative L2 on u "
+                   "is not met by 11-bit storage of f_i - W_i: measured 6e-4 on this vortex")
+def test_convected_vortex_fp16_meets_1e4_on_u(vortex_oracle):
+    """The 1e-4 relative L2 aimed at for the reduced-precision form, on u.
+    Kept as an expected failure so the gap stays visible: the stored
+    deviations (~0.02 here, the Mach 0.1 advection) carry 11 significant
+    bits, whose rounding alone moves u by ~1e-4 relative per step."""
+    L = 64
+    g = slbm.Solver(L, L, 3, 5, tau=vortex_oracle["tau"], interp_order=3, precision=FP16)
+    g.init_equilibrium(*vortex_oracle["fields"])
+    g.set_flags(vortex_oracle["disc"])
+    g.step(200)
+    mom, ref = g.moments(), vortex_oracle["mom"]
+    assert rel_l2(np.stack(mom[1:3]), np.stack(ref[1:3])) < 1e-4
+
+
 @pytest.mark.parametrize("n_lo,n_hi", [(3, 4), (3, 5), (4, 5)])
 def test_one_step_fp16_close_to_oracle(n_lo, n_hi):
     nx, ny = 37, 29
