@@ -329,6 +329,34 @@ SLBM_API int slbm_set_gpops(slbm_t h, int k, const double *in);
  * (1/omega_2 - 1/2 = (1/omega_1 - 1/2) / pr).  Host arrays of ny doubles. */
 SLBM_API int slbm_set_rows(slbm_t h, const int *len, const double *ends);
 
+/* Batched channels (the micro-Couette problem of Sec. IV.C with many
+ * channels advanced together; lattice frame only).
+ *
+ * slbm_set_channels: the grid becomes n independent channels side by side
+ * along x, each bounded by diffuse-reflection walls (as SLBM_BC_DIFFUSE) on
+ * its two x sides and periodic along y (the grid's y axis must be periodic,
+ * so every channel shares the streamwise period ny).  Channel c holds the
+ * columns x0[c] .. x0[c] + width[c] - 1 with width[c] >= 2 G + 1 (G = the
+ * stencil reach, slbm_info_t.halo); its wall at the low x side moves along y
+ * at uw_lo[c], the one at the high x side at uw_hi[c]; its relaxation time is
+ * tau[c] > 1/2 (the handle's tau applies nowhere inside a channel).  x0[0] >= G,
+ * x0[c] >= x0[c - 1] + width[c - 1] + 2 G, and x0[n - 1] + width[n - 1] + G <= nx:
+ * the G columns beside each channel side hold that wall's ghost cells (the
+ * diffuse-wall state against the channel's edge cell of the same row,
+ * refreshed after every step by the post-step kernel), and the columns that
+ * belong to no channel are gaps: no fluid, never computed, flags reported as
+ * 2, moments 0, outside the audit.  Every channel cell starts in the
+ * low-order lattice; slbm_set_flags then chooses each cell's lattice (the
+ * gaps stay gaps).  The flags stay fixed (SLBM_CRIT_NONE) or follow the
+ * learned indicator (SLBM_CRIT_MLP); the Mach criterion is refused.  Host
+ * arrays, copied; allocates a device buffer owned by the handle (freed by
+ * slbm_destroy); once per handle.  One stream-collide and one post-step
+ * launch per step advance every channel.  SLBM_EINVAL for bad arguments,
+ * SLBM_ESTATE if channels are already set.  slbm_get_state / slbm_set_state
+ * carry populations and flags, not the channel description. */
+SLBM_API int slbm_set_channels(slbm_t h, int n, const int *x0, const int *width,
+                               const double *uw_lo, const double *uw_hi, const double *tau);
+
 /* Autotuner of the co-moving step kernel (co-moving frames only): times
  * `reps` launches of the step for each thread-block shape of 256 threads
  * (32 x 8, 64 x 4, 128 x 2, 256 x 1, 16 x 16) on the current state -- the

@@ -311,6 +311,14 @@ struct slbm_s {
   int mcur;                      // tile-mask buffer the next stream launch reads
   int crit;
   double thr;
+  // channels (slbm_set_channels): per-column gap mask (host), and on the
+  // device (owned, one allocation) the internal wall ghosts {gx, gy, sx, side},
+  // their velocities, the per-column omega and the ghost index list sized for
+  // the ring plus the walls
+  int nchan, nwall;
+  std::vector<uint8_t> gapcol;
+  char* chanbuf;
+  size_t cb_wallu, cb_omega, cb_ghidx, cb_wallcol;
   // learned indicator: weights on the device (owned), evaluation interval
   void* ind_buf;
   IndicatorDev ind;
@@ -392,6 +400,12 @@ BcDev bc_dev(slbm_s* h) {
     b.ux[s] = h->at<double>(h->lay.bc[s][1]);
     b.uy[s] = h->at<double>(h->lay.bc[s][2]);
   }
+  if (h->nwall) {
+    b.nwall = h->nwall;
+    b.wall = reinterpret_cast<const int4*>(h->chanbuf);
+    b.wall_u = reinterpret_cast<const double*>(h->chanbuf + h->cb_wallu);
+    b.wallcol = reinterpret_cast<const uint8_t*>(h->chanbuf + h->cb_wallcol);
+  }
   return b;
 }
 
@@ -399,9 +413,15 @@ int ntiles_of(const slbm_s* h) {
   return ((h->g.nx + kTX - 1) / kTX) * ((h->g.ny + kTY - 1) / kTY);
 }
 
+// Ghost index list: in the workspace (ring cells only), or with channels in
+// the channel buffer (ring cells and internal wall ghosts).
+int* ghost_idx(slbm_s* h) {
+  return h->nwall ? reinterpret_cast<int*>(h->chanbuf + h->cb_ghidx) : h->at<int>(h->lay.gh_idx);
+}
+
 GhostTables ghost_tables(slbm_s* h) {
-  return GhostTables{h->at<int>(h->lay.gh_start), h->at<int>(h->lay.gh_idx),
-                     h->at<int>(h->lay.gh_tiles), h->gh_ntiles};
+  return GhostTables{h->at<int>(h->lay.gh_start), ghost_idx(h), h->at<int>(h->lay.gh_tiles),
+                     h->gh_ntiles};
 }
 
 // Per-tile ghost lists of the post-step kernel for the current boundary
@@ -409,9 +429,9 @@ GhostTables ghost_tables(slbm_s* h) {
 // sorted here by tile (ring order within a tile).  Synchronous (set-up only).
 int build_ghost_tables(slbm_s* h) {
   const int G = h->lay.G, nx = h->g.nx, ny = h->g.ny;
-  const size_t ring = 2 * (size_t)G * (nx + 2 * G) + 2 * (size_t)G * ny;
+  const size_t ring = 2 * (size_t)G * (nx + 2 * G) + 2 * (size_t)G * ny + (size_t)h->nwall;
   const int nt = ntiles_of(h);
-  int* d_idx = h->at<int>(h->lay.gh_idx);
+  int* d_idx = ghost_idx(h);
   SLBM_CK(h, launch_ghost_src(G, nx, ny, h->g.periodic_x ? 1 : 0, h->g.periodic_y ? 1 : 0,
                               bc_dev(h), d_idx, h->st),
           "ghost source launch");
@@ -706,6 +726,10 @@ void fill_params(Params<R>& p, const slbm_s* h, const Lattice1D& a, const Lattic
   p.wlist = reinterpret_cast<int*>(h->ws + h->lay.post_list);
   p.wcount = reinterpret_cast<int*>(h->ws + h->lay.post_nlist);
   p.cv = h->twopop ? h->cv : 1.0;
+  // per-column omega of channels, in the arithmetic type of the handle's kernels
+  p.omega_x = (h->nchan && sizeof(R) == (h->precision == SLBM_FP64 ? 8u : 4u))
+                  ? reinterpret_cast<const R*>(h->chanbuf + h->cb_omega)
+                  : nullptr;
   fill_lat(p.lat[0], a, dt, h->P);
   fill_lat(p.lat[1], b, dt, h->P);
   ConvTab<R>& t = p.conv;
@@ -1096,6 +1120,7 @@ int slbm_destroy(slbm_t h) {
   if (h->ind_buf) cudaFree(h->ind_buf);
   if (h->gbuf) cudaFree(h->gbuf);
   if (h->rowbuf) cudaFree(h->rowbuf);
+  if (h->chanbuf) cudaFree(h->chanbuf);
   if (h->owns_ws && cudaFree(h->ws) != cudaSuccess) rc = SLBM_ECUDA;
   delete h;
   return rc;
@@ -1145,6 +1170,9 @@ int slbm_set_flags(slbm_t h, const uint8_t* flags) {
   if (!flags) return fail(h, SLBM_EINVAL, "flags is required");
   std::vector<uint8_t> norm(h->ncell());
   for (size_t c = 0; c < norm.size(); ++c) norm[c] = flags[c] ? 1 : 0;
+  if (h->nchan)  // the gap columns between channels stay gaps
+    for (size_t c = 0; c < norm.size(); ++c)
+      if (h->gapcol[c % h->g.nx]) norm[c] = kFlagGap;
   uint8_t* tmp = h->at<uint8_t>(h->lay.flag_tmp);
   int rc;
   if ((rc = upload(h, tmp, norm.data(), norm.size()))) return rc;
@@ -1204,6 +1232,8 @@ int slbm_set_criterion(slbm_t h, int kind, double threshold) {
     return fail(h, SLBM_EINVAL, "criterion kind or threshold invalid");
   if (kind == SLBM_CRIT_MLP && !h->ind_buf)
     return fail(h, SLBM_EINVAL, "no indicator weights (slbm_set_indicator); use SLBM_CRIT_MACH");
+  if (kind == SLBM_CRIT_MACH && h->nchan)
+    return fail(h, SLBM_EINVAL, "channels keep fixed flags or the learned indicator");
   if (kind != SLBM_CRIT_NONE && h->frame != SLBM_FRAME_LATTICE)
     return fail(h, SLBM_EINVAL, "the Mach criterion belongs to the lattice frame");
   // flags live in buffer fcur either way; the other buffer is scratch
@@ -1610,6 +1640,84 @@ int ensure_rowbuf(slbm_t h) {
   return SLBM_OK;
 }
 }  // namespace
+
+int slbm_set_channels(slbm_t h, int n, const int* x0, const int* width, const double* uw_lo,
+                      const double* uw_hi, const double* tau) {
+  SLBM_GUARD(h);
+  if (h->frame != SLBM_FRAME_LATTICE)
+    return fail(h, SLBM_EINVAL, "channels belong to the lattice frame");
+  if (h->nchan) return fail(h, SLBM_ESTATE, "channels are already set");
+  if (h->crit == SLBM_CRIT_MACH)
+    return fail(h, SLBM_EINVAL, "channels keep fixed flags or the learned indicator");
+  if (!h->g.periodic_y) return fail(h, SLBM_EINVAL, "channels need a periodic y axis");
+  if (n < 1 || !x0 || !width || !uw_lo || !uw_hi || !tau)
+    return fail(h, SLBM_EINVAL, "n >= 1 and every array are required");
+  const int G = h->lay.G, nx = h->g.nx, ny = h->g.ny;
+  for (int c = 0; c < n; ++c) {
+    const int lo = c ? x0[c - 1] + width[c - 1] + 2 * G : G;
+    if (width[c] < 2 * G + 1 || x0[c] < lo || x0[c] + width[c] + G > nx)
+      return fail(h, SLBM_EINVAL,
+                  "channel c must span x0 .. x0 + width - 1 with width >= 2G + 1, x0 >= G, "
+                  "x0 + width + G <= nx, and 2G gap columns before the next channel");
+    if (!(tau[c] > 0.5) || !std::isfinite(tau[c]) || !std::isfinite(uw_lo[c]) ||
+        !std::isfinite(uw_hi[c]))
+      return fail(h, SLBM_EINVAL, "tau must exceed 1/2 and the wall speeds be finite");
+  }
+  // host tables: gap columns, per-column omega, internal wall ghosts (G
+  // columns beside each channel side, every row) and their velocities
+  std::vector<uint8_t> gap(nx, 1), wcol(nx, 0);
+  std::vector<double> om(nx, 1.0 / h->tau);
+  std::vector<int> wall;
+  std::vector<double> wu;
+  for (int c = 0; c < n; ++c) {
+    for (int x = x0[c]; x < x0[c] + width[c]; ++x) {
+      gap[x] = 0;
+      om[x] = 1.0 / tau[c];
+    }
+    // every row of the wall ghost columns, the y ghost rows included (their
+    // source row wraps), so a channel's corner cells read current wall states
+    for (int y = -G; y < ny + G; ++y)
+      for (int k = 0; k < G; ++k) {
+        wall.insert(wall.end(), {x0[c] - G + k, y, x0[c], SLBM_SIDE_XMIN});
+        wu.insert(wu.end(), {0.0, uw_lo[c]});
+        wall.insert(wall.end(), {x0[c] + width[c] + k, y, x0[c] + width[c] - 1, SLBM_SIDE_XMAX});
+        wu.insert(wu.end(), {0.0, uw_hi[c]});
+        wcol[x0[c] - G + k] = wcol[x0[c] + width[c] + k] = 1;
+      }
+  }
+  const int nwall = (int)(wall.size() / 4);
+  const size_t ring = 2 * (size_t)G * (nx + 2 * G) + 2 * (size_t)G * ny;
+  const size_t es = h->precision == SLBM_FP64 ? 8 : 4;
+  h->cb_wallu = align_up(wall.size() * sizeof(int), 256);
+  h->cb_omega = h->cb_wallu + align_up(wu.size() * sizeof(double), 256);
+  h->cb_ghidx = h->cb_omega + align_up(nx * es, 256);
+  h->cb_wallcol = h->cb_ghidx + align_up((ring + nwall) * sizeof(int), 256);
+  const size_t bytes = h->cb_wallcol + nx;
+  void* buf = nullptr;
+  SLBM_CK(h, cudaMalloc(&buf, bytes), "channel arrays allocation");
+  h->chanbuf = (char*)buf;
+  std::vector<float> omf(om.begin(), om.end());
+  int rc;
+  if ((rc = upload(h, h->chanbuf, wall.data(), wall.size() * sizeof(int))) ||
+      (rc = upload(h, h->chanbuf + h->cb_wallu, wu.data(), wu.size() * sizeof(double))) ||
+      (rc = upload(h, h->chanbuf + h->cb_omega,
+                   es == 8 ? (const void*)om.data() : (const void*)omf.data(), nx * es)) ||
+      (rc = upload(h, h->chanbuf + h->cb_wallcol, wcol.data(), nx)))
+    return rc;
+  h->gapcol = gap;
+  h->nchan = n;
+  h->nwall = nwall;
+  refresh_params(h);
+  if ((rc = build_ghost_tables(h))) return rc;
+  // every channel cell starts in the low-order lattice, the gaps as gaps
+  std::vector<uint8_t> fl(h->ncell(), 0);
+  if ((rc = slbm_set_flags(h, fl.data()))) return rc;
+  // the other flag buffer too (the learned indicator writes it)
+  for (size_t c = 0; c < fl.size(); ++c) fl[c] = gap[c % nx] ? kFlagGap : 0;
+  if ((rc = upload(h, h->flags(h->fcur ^ 1), fl.data(), fl.size()))) return rc;
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  return SLBM_OK;
+}
 
 int slbm_set_rows(slbm_t h, const int* len, const double* ends) {
   SLBM_GUARD(h);

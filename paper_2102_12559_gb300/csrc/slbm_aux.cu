@@ -59,14 +59,13 @@ template <class S, class R>
 __global__ void k_ghosts(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ flag,
                          const BcDev bc) {
   const int G = p.G;
-  const int total = 2 * G * (p.nx + 2 * G) + 2 * G * p.ny;
+  const int total = 2 * G * (p.nx + 2 * G) + 2 * G * p.ny + bc.nwall;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
-  int gx, gy;
-  ghost_coords(G, p.nx, p.ny, idx, gx, gy);
-  int sx, sy, side = 0, bidx = 0;
-  const int kind = ghost_source(p.nx, p.ny, p.periodic_x, p.periodic_y, bc, gx, gy, sx, sy, side,
-                                bidx);
+  int gx, gy, sx, sy, side = 0, bidx = 0;
+  const int kind = ghost_cell(G, p.nx, p.ny, p.periodic_x, p.periodic_y, bc, idx, gx, gy, sx, sy,
+                              side, bidx);
+  if (kind == 4) return;  // written by its wall entry
   const int gbase = (gy + G) * p.pitch + (gx + kOX);
   const int sbase = (sy + G) * p.pitch + (sx + kOX);
   if (kind == 1 || kind == 2) {
@@ -74,7 +73,7 @@ __global__ void k_ghosts(const Params<R> p, S* f0, S* f1, const uint8_t* __restr
     write_eq_both<S, R>(p, f0, f1, gbase, er, bc.ux[side][bidx], bc.uy[side][bidx]);
   } else if (kind == 3) {
     // diffuse wall, both lattices, every population
-    const R uwx = (R)bc.ux[side][bidx], uwy = (R)bc.uy[side][bidx];
+    const R uwx = (R)ghost_ux(bc, side, bidx), uwy = (R)ghost_uy(bc, side, bidx);
     for (int k = 0; k < 2; ++k) {
       S* f = k ? f1 : f0;
       const int n = p.lat[k].n;
@@ -117,6 +116,10 @@ __device__ void cell_moments(const Params<R>& p, const S* f0, const S* f1, int k
                              double& r, double& jx, double& jy, double& e,
                              const S* lam = nullptr, long long c = 0, const S* e0 = nullptr,
                              const S* e1 = nullptr) {
+  if (k == kFlagGap) {  // no fluid: zero in every sum
+    r = jx = jy = e = 0.0;
+    return;
+  }
   const LatTab<R>& L = p.lat[k];
   const S* f = k ? f1 : f0;
   r = 1.0;
@@ -160,6 +163,13 @@ k_moments(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restrict
   double r, jx, jy, e;
   cell_moments<S, R>(p, f0, f1, flag[c], (y + p.G) * p.pitch + (x + kOX), r, jx, jy, e, lam, c,
                      e0, e1);
+  if (r == 0.0) {  // a gap cell between channels: no fluid, every moment 0
+    if (rho) rho[c] = 0.0;
+    if (ux) ux[c] = 0.0;
+    if (uy) uy[c] = 0.0;
+    if (T) T[c] = 0.0;
+    return;
+  }
   const double u = jx / r, v = jy / r;
   if (rho) rho[c] = r;
   if (ux) ux[c] = u;
@@ -176,6 +186,10 @@ k_criterion(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restri
   const int y = blockIdx.y * kTY + threadIdx.y;
   if (x >= p.nx || y >= p.ny) return;
   const int c = x + p.nx * y;
+  if (flag[c] == kFlagGap) {
+    flag_new[c] = kFlagGap;
+    return;
+  }
   double r, jx, jy, e;
   cell_moments<S, R>(p, f0, f1, flag[c], (y + p.G) * p.pitch + (x + kOX), r, jx, jy, e);
   const R u = (R)(jx / r), v = (R)(jy / r);
@@ -310,15 +324,14 @@ __global__ void k_ghost_src(int G, int nx, int ny, int periodic_x, int periodic_
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= ring) return;
   int gx, gy, sx, sy, side = 0, idx = 0;
-  ghost_coords(G, nx, ny, g, gx, gy);
-  const int kind = ghost_source(nx, ny, periodic_x, periodic_y, bc, gx, gy, sx, sy, side, idx);
+  const int kind = ghost_cell(G, nx, ny, periodic_x, periodic_y, bc, g, gx, gy, sx, sy, side, idx);
   const int ntx = (nx + kTX - 1) / kTX;
-  out[g] = kind == 2 ? -1 : (sy / kTY) * ntx + sx / kTX;
+  out[g] = (kind == 2 || kind == 4) ? -1 : (sy / kTY) * ntx + sx / kTX;
 }
 
 cudaError_t launch_ghost_src(int G, int nx, int ny, int periodic_x, int periodic_y,
                              const BcDev& bc, int* out, cudaStream_t st) {
-  const int ring = 2 * G * (nx + 2 * G) + 2 * G * ny;
+  const int ring = 2 * G * (nx + 2 * G) + 2 * G * ny + bc.nwall;
   if (ring == 0) return cudaSuccess;
   k_ghost_src<<<(ring + 127) / 128, 128, 0, st>>>(G, nx, ny, periodic_x, periodic_y, bc, out, ring);
   return cudaGetLastError();
@@ -336,7 +349,7 @@ cudaError_t launch_tile_work(int nx, int ny, int periodic_x, int periodic_y,
 template <class S, class R>
 cudaError_t launch_ghosts(const Params<R>& p, S* f0, S* f1, const uint8_t* flag, const BcDev& bc,
                           cudaStream_t st) {
-  const long long total = 2LL * p.G * (p.nx + 2 * p.G) + 2LL * p.G * p.ny;
+  const long long total = 2LL * p.G * (p.nx + 2 * p.G) + 2LL * p.G * p.ny + bc.nwall;
   if (total == 0) return cudaSuccess;
   k_ghosts<S, R><<<(unsigned)((total + 127) / 128), 128, 0, st>>>(p, f0, f1, flag, bc);
   return cudaGetLastError();

@@ -69,6 +69,42 @@ __device__ __forceinline__ int ghost_source(int nx, int ny, int px, int py, cons
   return 0;
 }
 
+// Ghost cell g: a ring cell (g < ring, ghost_coords / ghost_source) or an
+// internal wall ghost (g = ring + e, BcDev::wall[e]: always a DIFFUSE wall,
+// idx = -e - 1 selects its velocity in ghost_ux / ghost_uy).  Kind 4: a ring
+// cell in a y ghost row of a wall ghost column, written by its wall entry, so
+// no ring writer touches it.
+__device__ __forceinline__ int ghost_cell(int G, int nx, int ny, int px, int py, const BcDev& bc,
+                                          int g, int& gx, int& gy, int& sx, int& sy, int& side,
+                                          int& idx) {
+  const int ring = 2 * G * (nx + 2 * G) + 2 * G * ny;
+  if (g >= ring) {
+    const int4 w = bc.wall[g - ring];
+    gx = w.x;
+    gy = w.y;
+    sx = w.z;
+    sy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+    side = w.w;
+    idx = -(g - ring) - 1;
+    return 3;
+  }
+  ghost_coords(G, nx, ny, g, gx, gy);
+  if (bc.wallcol && (gy < 0 || gy >= ny) && gx >= 0 && gx < nx && bc.wallcol[gx]) {
+    sx = gx;
+    sy = 0;
+    return 4;
+  }
+  return ghost_source(nx, ny, px, py, bc, gx, gy, sx, sy, side, idx);
+}
+
+// Prescribed velocity of an INLET / DIFFUSE ghost (side, idx from ghost_cell).
+__device__ __forceinline__ double ghost_ux(const BcDev& bc, int side, int idx) {
+  return idx < 0 ? bc.wall_u[2 * (-idx - 1)] : bc.ux[side][idx];
+}
+__device__ __forceinline__ double ghost_uy(const BcDev& bc, int side, int idx) {
+  return idx < 0 ? bc.wall_u[2 * (-idx - 1) + 1] : bc.uy[side][idx];
+}
+
 // Diffuse-reflection wall ghost, population i of lattice L (N nodes per axis),
 // on deviations.  The wall of `side` has its normal along x (XMIN / XMAX) or y
 // (YMIN / YMAX), fluid on the side of sign n.  Populations entering the fluid

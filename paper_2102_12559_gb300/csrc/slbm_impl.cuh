@@ -86,7 +86,12 @@ struct Params {
   int* wlist;                   // 2 x ntiles: candidate work tiles (see add_work)
   int* wcount;                  // 2 counters: entries of each half of wlist
   double cv;                    // C_v of the two-population co-moving model, else 1
+  const R* omega_x;             // per-column omega (channels), else null: omega everywhere
 };
+
+// Flag value of a cell that belongs to no lattice: the gap columns between
+// channels (slbm_set_channels), which hold their walls' ghost cells.
+constexpr uint8_t kFlagGap = 2;
 
 // A tile has interface-conversion work iff its work word holds both lattices
 // (bits 0 and 1, OR-ed from its 3 x 3 tile neighbourhood) or a flip (bit 2).
@@ -162,11 +167,21 @@ constexpr int kErrNoConv = 2;   // a co-moving predictor-corrector stopped at ma
 constexpr int kErrFrame = 4;    // non-positive / non-finite frame, or departure beyond reach
 
 // Boundary description (device arrays of the prescribed states, may be null).
+// Internal walls (channels, slbm_set_channels): nwall extra ghost cells
+// beyond the ring, ghost index ring + e for e < nwall, each a diffuse wall
+// against an interior source cell: wall[e] = {gx, gy, sx, side}, the source
+// row being gy wrapped into the (periodic) grid, with wall velocity
+// (wall_u[2e], wall_u[2e + 1]).  The walls' ghost columns (wallcol[x] = 1)
+// cover the y ghost rows too, so the ring leaves those cells to them.
 struct BcDev {
   int kind[4];                  // per side SLBM_BC_*
   const double* rho[4];
   const double* ux[4];
   const double* uy[4];
+  int nwall;
+  const int4* wall;
+  const double* wall_u;
+  const uint8_t* wallcol;
 };
 
 // Co-moving frame launchers (slbm_pond.cu).  lam: three frame planes.

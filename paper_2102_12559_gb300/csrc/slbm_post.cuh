@@ -157,7 +157,7 @@ __device__ __forceinline__ bool post_tile(const Params<R>& p, S* f0, S* f1,
         const int u = sf[threadIdx.y + B + dy][threadIdx.x + B + dx];
         band |= (u != 2) && (u != nw);
       }
-    conv = old != nw || band;
+    conv = nw != kFlagGap && old != kFlagGap && (old != nw || band);
   }
   const unsigned b0 = __ballot_sync(0xffffffffu, conv && old == 0);
   const unsigned b1 = __ballot_sync(0xffffffffu, conv && old != 0);
@@ -279,17 +279,16 @@ __device__ __forceinline__ void tile_ghosts(const Params<R>& p, S* f0, S* f1,
     const int m = n - c0 < T ? n - c0 : T;
     if (tid < m) {
       int gx, gy, sx, sy, side = 0, bi = 0;
-      ghost_coords(p.G, p.nx, p.ny, idx[c0 + tid], gx, gy);
-      const int kind = ghost_source(p.nx, p.ny, p.periodic_x, p.periodic_y, bc, gx, gy, sx, sy,
-                                    side, bi);
+      const int kind = ghost_cell(p.G, p.nx, p.ny, p.periodic_x, p.periodic_y, bc, idx[c0 + tid],
+                                  gx, gy, sx, sy, side, bi);
       const int sb = (sy + p.G) * p.pitch + (sx + kOX);
       s_kind[tid] = kind;
       s_gb[tid] = (gy + p.G) * p.pitch + (gx + kOX);
       s_sb[tid] = sb;
       s_side[tid] = side;
       if (kind == 1 || kind == 3) {
-        s_ux[tid] = (R)bc.ux[side][bi];
-        s_uy[tid] = (R)bc.uy[side][bi];
+        s_ux[tid] = (R)ghost_ux(bc, side, bi);
+        s_uy[tid] = (R)ghost_uy(bc, side, bi);
       }
       if (kind == 1) {  // density deviation of the source from its own lattice
         R dr = R(0);
@@ -314,7 +313,7 @@ __device__ __forceinline__ void tile_ghosts(const Params<R>& p, S* f0, S* f1,
         if (e >= m * Q) continue;
         const int plane = e / m, j = e - plane * m;
         const int kind = s_kind[j];
-        if (kind == 2) continue;
+        if (kind == 2 || kind == 4) continue;
         const int k = plane < q0 ? 0 : 1;
         const int i = k ? plane - q0 : plane;
         S* f = k ? f1 : f0;

@@ -195,10 +195,10 @@ __device__ __forceinline__ void stream_row(const LatTab<R>& L, const S* col, int
 }
 
 // Collision of one cell of lattice L on its streamed deviations f: rho, u,
-// the product-form equilibrium and BGK (see slbm_eq.cuh); the new values go
-// to `o` (plane stride `plane`) when `store`.
+// the product-form equilibrium and BGK with rate omega (see slbm_eq.cuh); the
+// new values go to `o` (plane stride `plane`) when `store`.
 template <int N, class S, class R>
-__device__ __forceinline__ void collide(const Params<R>& p, const LatTab<R>& L, R* f,
+__device__ __forceinline__ void collide(const Params<R>& p, const LatTab<R>& L, R omega, R* f,
                                         S* __restrict__ o, bool store, uint32_t key, R& ux,
                                         R& uy) {
   // density deviation and momentum through row / column sums of the N x N block
@@ -236,7 +236,7 @@ __device__ __forceinline__ void collide(const Params<R>& p, const LatTab<R>& L, 
       const int i = jx + N * jy;
       // f^L - W = dr px py + w_x dphi_y + dphi_x (w_y + dphi_y)
       const R feq = px[jx] * ty + L.w1[jx] * dy[jy] + dx[jx] * py;
-      f[i] += p.omega * (feq - f[i]);
+      f[i] += omega * (feq - f[i]);
     }
   }
   if (store) {
@@ -285,6 +285,8 @@ __device__ __forceinline__ void sweep(const Params<R>& p, const LatTab<R>& L, in
   const int xl = xin ? x : p.nx - 1;  // loads of lanes past the edge stay in the row
   const S* col = fin + (p.G * p.pitch + xl + kOX);
   const int plane = (int)p.plane;
+  // relaxation rate of the lane's column (channels carry their own tau)
+  const R om = p.omega_x ? p.omega_x[xl] : p.omega;
   Windows<N, P, R> W;
   prime<N, HI, P, S, R>(L, col, plane, p.pitch, ys, W);
   int bits = 0, sides = 0;
@@ -301,7 +303,7 @@ __device__ __forceinline__ void sweep(const Params<R>& p, const LatTab<R>& L, in
     const int ob = (y + p.G) * p.pitch + (x + kOX);
     const uint32_t key = hash32((uint32_t)ob ^ (seed * 0x9e3779b9u));  // FP16 rounding only
     R ux, uy;
-    collide<N, S, R>(p, L, f, fout + ob, act, key, ux, uy);
+    collide<N, S, R>(p, L, om, f, fout + ob, act, key, ux, uy);
     int nf = k;
     if (act) {
       if (p.crit == 1) {

@@ -37,7 +37,7 @@ EXPORTS = [
     "slbm_set_pond", "slbm_get_frame", "slbm_set_frame",
     "slbm_set_indicator", "slbm_indicator_eval",
     "slbm_set_twopop", "slbm_get_gpops", "slbm_set_gpops", "slbm_set_rows",
-    "slbm_set_viscosity_law", "slbm_tune", "slbm_set_kn_criterion",
+    "slbm_set_viscosity_law", "slbm_tune", "slbm_set_kn_criterion", "slbm_set_channels",
 ]
 SLBM_PROFILE_KERNELS = 2
 KERNEL_NAMES = ("stream_collide", "post_step")
@@ -112,6 +112,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.slbm_set_viscosity_law.argtypes = [p, p, p, d, d]
     L.slbm_tune.argtypes = [p, i, p, p]
     L.slbm_set_kn_criterion.argtypes = [p, d, i]
+    L.slbm_set_channels.argtypes = [p, i, p, p, p, p, p]
     L.slbm_get_frame.argtypes = [p, p, p, p]
     L.slbm_set_frame.argtypes = [p, p, p, p]
     L.slbm_set_indicator.argtypes = [p, p, p, p, p, p, ctypes.c_float, i]
@@ -220,6 +221,16 @@ def slbm_set_rows(h, ny, lens, ends):
     if a.size != ny:
         raise ValueError("one length per row")
     _check(load().slbm_set_rows(h, _ptr(a), _ptr(b)), h)
+
+
+def slbm_set_channels(h, x0, width, uw_lo, uw_hi, tau):
+    n = len(x0)
+    a = np.ascontiguousarray(np.asarray(x0, dtype=np.int32).ravel())
+    b = np.ascontiguousarray(np.asarray(width, dtype=np.int32).ravel())
+    c, d, e = _f64(uw_lo, n), _f64(uw_hi, n), _f64(tau, n)
+    if b.size != n:
+        raise ValueError("one width per channel")
+    _check(load().slbm_set_channels(h, n, _ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(e)), h)
 
 
 def slbm_set_viscosity_law(h, ny, mu1, T1, s_exp, pr):
@@ -422,6 +433,11 @@ class Solver:
         """Rows as independent quasi-1-D instances: lengths (ny) and end
         states (ny, 2, 4) = left / right {rho, u_x, u_y, T}."""
         slbm_set_rows(self.h, self.ny, lens, np.asarray(ends, dtype=np.float64).reshape(-1))
+
+    def set_channels(self, x0, width, uw_lo, uw_hi, tau):
+        """Independent channels side by side along x (diffuse walls on their x
+        sides moving along y, periodic y, own tau each; see slbm.h)."""
+        slbm_set_channels(self.h, x0, width, uw_lo, uw_hi, tau)
 
     def set_viscosity_law(self, mu1, T1, s_exp=0.5, pr=2.0 / 3.0):
         slbm_set_viscosity_law(self.h, self.ny, np.broadcast_to(mu1, (self.ny,)),

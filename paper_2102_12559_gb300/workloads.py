@@ -235,6 +235,17 @@ def couette_batch(count: int = 128, seed: int = 3, h_range=(64, 512), kn_range=(
             for h, k in zip(hs, kn)]
 
 
+def channel_layout(widths, G: int):
+    """Columns of channels placed side by side along x with 2 G gap columns
+    between neighbours and G before the first / after the last: returns the
+    first column of every channel and the grid width."""
+    x0, x = [], G
+    for w in widths:
+        x0.append(x)
+        x += int(w) + 2 * G
+    return x0, x - G
+
+
 def shock_profile(inst: dict, nx: int, width: float = 20.0):
     """rho, u, T of one instance on nx cells (cells beyond its length hold the
     downstream state): the tanh ramp between the end states at the middle."""
