@@ -579,8 +579,8 @@ def run_study(args):
       the autotuner; D2Q25 within 4 lambda_1 of the shock with D2Q16 (or D2Q9)
       elsewhere, against D2Q25 everywhere.
     couette: the batched high-Knudsen Couette channels -- 128 independent
-      channels (8 x H, H 64-512, Kn 0.01-1 log-uniform, diffuse walls moving
-      at -0.1 / +0.1), one handle each on 16 CUDA streams; D2Q25 in channels
+      channels (H x 8, H 64-512, Kn 0.01-1 log-uniform, diffuse walls moving
+      at -0.1 / +0.1), side by side in one grid of one handle; D2Q25 in channels
       with Kn > 0.1, D2Q9 in the others.
     """
     import torch
@@ -752,60 +752,52 @@ def run_study(args):
         return
     if args.workload == "couette":
         batch = WL.couette_batch(count=128, seed=3)
-        nxc = 8  # streamwise period: the API needs at least 2 G + 1 = 5 cells per side
         kn_hi = 0.1  # channels above it run D2Q25, the others D2Q9
-        streams = [torch.cuda.Stream() for _ in range(16)]
+        # one grid: the channels side by side along x (wall-normal), the
+        # streamwise axis y periodic with 8 cells, 2 G gap columns between
+        # neighbours; every channel its own relaxation time
+        G, ny = 2, 8
+        widths = [ch["H"] for ch in batch]
+        x0, nx = WL.channel_layout(widths, G)
         probe = slbm.Solver(8, 8, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=0.6)
         dt = probe.dt
         probe.close()
-        hs = []
-        for i, ch in enumerate(batch):
-            H = ch["H"]
-            g = slbm.Solver(nxc, H, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25,
-                            tau=couette_tau(ch["kn"], H, dt), periodic=(True, False),
-                            stream=streams[i % len(streams)])
-            g.init_equilibrium(*WL.uniform(nxc, H))
-            g.set_flags(np.full((H, nxc), 1 if ch["kn"] > kn_hi else 0, np.uint8))
-            g.set_boundary(slbm.SLBM_SIDE_YMIN, slbm.SLBM_BC_DIFFUSE, None,
-                           np.full(nxc, ch["uw_lo"]), np.zeros(nxc))
-            g.set_boundary(slbm.SLBM_SIDE_YMAX, slbm.SLBM_BC_DIFFUSE, None,
-                           np.full(nxc, ch["uw_hi"]), np.zeros(nxc))
-            hs.append(g)
-        for g in hs:
-            g.step(args.warmup)
+        taus = [couette_tau(ch["kn"], ch["H"], dt) for ch in batch]
+        g = slbm.Solver(nx, ny, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=0.6, periodic=(False, True))
+        g.init_equilibrium(*WL.uniform(nx, ny))
+        g.set_channels(x0, widths, [ch["uw_lo"] for ch in batch], [ch["uw_hi"] for ch in batch],
+                       taus)
+        fl = np.zeros((ny, nx), np.uint8)
+        for c, ch in enumerate(batch):
+            if ch["kn"] > kn_hi:
+                fl[:, x0[c]:x0[c] + widths[c]] = 1
+        g.set_flags(fl)
+        g.step(args.warmup)
         torch.cuda.synchronize()
-        # CUDA events on the default stream, which the channel streams wait on
-        # at the start and which waits on all of them at the end
-        main = torch.cuda.current_stream()
+        st = g.stream
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(main)
-        for st in streams:
-            st.wait_event(a)
-        for g in hs:
-            g.step(args.steps)
-        for st in streams:
-            e = torch.cuda.Event()
-            e.record(st)
-            main.wait_event(e)
-        b.record(main)
+        a.record(st)
+        g.step(args.steps)
+        b.record(st)
         torch.cuda.synchronize()
         sec = a.elapsed_time(b) * 1e-3
-        cells = sum(nxc * ch["H"] for ch in batch)
+        cells = sum(ny * w for w in widths)
         # antisymmetric walls: every channel's mean streamwise velocity stays 0
-        drift = max(abs(float(g.moments()[1].mean())) for g in hs) / 0.1
-        finite = all(all(np.isfinite(m).all() for m in g.moments()[:3]) for g in hs)
+        m = g.moments()
+        drift = max(abs(float(m[2][:, x0[c]:x0[c] + widths[c]].mean()))
+                    for c in range(len(batch))) / 0.1
+        finite = all(np.isfinite(v).all() for v in m[:3])
         print(json.dumps({
             "study": "batched Couette channels (Sec. IV.C)",
-            "workload": f"{len(batch)} channels {nxc} x H, H {min(c['H'] for c in batch)}-"
-                        f"{max(c['H'] for c in batch)}, Kn 0.01-1 log-uniform, diffuse walls at "
-                        "-0.1 / +0.1, FP32, one handle per channel on 16 streams",
+            "workload": f"{len(batch)} channels H x {ny}, H {min(widths)}-{max(widths)}, "
+                        "Kn 0.01-1 log-uniform, diffuse walls at -0.1 / +0.1, FP32, one "
+                        f"{nx} x {ny} grid (channels along x, 2 G gap columns)",
             "d2q25_channels": sum(c["kn"] > kn_hi for c in batch), "cells": cells,
             "steps": args.steps, "ms_per_step": sec / args.steps * 1e3,
             "mlups": cells * args.steps / sec / 1e6,
-            "timing": "CUDA events on the default stream joined with the 16 channel streams",
+            "timing": "CUDA events on the handle's stream",
             "finite": finite, "max_mean_u_over_wall_speed": drift}), flush=True)
-        for g in hs:
-            g.close()
+        g.close()
         return
     if args.workload == "pond":
         nx, ny = 1024, 512
