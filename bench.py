@@ -357,20 +357,124 @@ def mom_gap(a, b) -> dict:
             "ux": rel_l2(a[1], b[1]), "uy": rel_l2(a[2], b[2])}
 
 
+KN_HI = 0.1  # plain rule of the Couette batch: channels above it run D2Q25
+COUETTE_NY = 4  # streamwise period of the Couette channels, cells
+
+
+def couette_solver(slbm, WL, batch, mode, weights=None, stream=None):
+    """The batched Couette channels in one handle: side by side along x
+    (wall-normal), streamwise y periodic with COUETTE_NY cells, 2 G gap
+    columns, each channel its own tau.  mode: "plain" (D2Q25 in the channels
+    with Kn > KN_HI, fixed), "all" (D2Q25 everywhere, fixed) or "mlp" (the
+    learned indicator sets the flags every 10 steps, from D2Q9 at rest)."""
+    G, ny = 2, COUETTE_NY
+    widths = [ch["H"] for ch in batch]
+    x0, nx = WL.channel_layout(widths, G)
+    probe = slbm.Solver(8, 8, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=0.6)
+    dt = probe.dt
+    probe.close()
+    taus = [couette_tau(ch["kn"], ch["H"], dt) for ch in batch]
+    g = slbm.Solver(nx, ny, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=0.6, periodic=(False, True),
+                    stream=stream)
+    g.init_equilibrium(*WL.uniform(nx, ny))
+    g.set_channels(x0, widths, [ch["uw_lo"] for ch in batch], [ch["uw_hi"] for ch in batch],
+                   taus)
+    fl = np.zeros((ny, nx), np.uint8)
+    for c, ch in enumerate(batch):
+        if mode == "all" or (mode == "plain" and ch["kn"] > KN_HI):
+            fl[:, x0[c]:x0[c] + widths[c]] = 1
+    g.set_flags(fl)
+    if mode == "mlp":
+        g.set_indicator(weights, interval=10)
+        g.set_criterion(slbm.SLBM_CRIT_MLP, 0.0)
+    return g, x0, widths
+
+
+def plain_couette_flags(batch, x0, widths, shape):
+    fl = np.zeros(shape, np.uint8)
+    for c, ch in enumerate(batch):
+        if ch["kn"] > KN_HI:
+            fl[:, x0[c]:x0[c] + widths[c]] = 1
+    return fl
+
+
 def train_indicator(slbm, WL, stream):
-    """Indicator weights from an all-D2Q25 384^2 run of the same generator
-    (12 vortices, seed 5, 20 steps), labelled by the plain Mach criterion."""
+    """Indicator weights trained on the GPU (slbm_mlp_train) from states of
+    all-D2Q25 runs labelled by the method's own lattice loss (what D2Q9 loses
+    in one step, above the indicator's threshold): a 384^2 random-vortex field
+    of the benchmark's generator (12 vortices, seed 5) after 20 steps, and a
+    batch of 32 Couette channels (seed 11, a different draw than the
+    benchmark's) after 300, 1500 and 6000 steps.  Returns the weights and a
+    report of the training set and fit."""
     from paper_2102_12559_gb300 import indicator as IND
+    xs, ys = [], []
     n_tr = 384
     t = slbm.Solver(n_tr, n_tr, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=VTAU, stream=stream)
     t.init_equilibrium(*WL.random_vortex_field(n_tr, 12, seed=5, rmin=VRMIN, rmax=VRMAX, umax=VUMAX))
     t.set_flags(np.ones((n_tr, n_tr), np.uint8))
     t.step(20)
-    x_tr = t.indicator_eval()[0].reshape(-1, 16).astype(np.float64)
-    _, mu, mv, _ = t.moments()
-    y_tr = (np.hypot(mu, mv) > THR).ravel().astype(np.float64)
+    xs.append(t.indicator_eval()[0].reshape(-1, 16))
+    ys.append(IND.labels(t.lattice_loss()).ravel())
     t.close()
-    return IND.train(x_tr, y_tr, epochs=40, batch=512, seed=0, balance=False)
+    tb = WL.couette_batch(count=32, seed=11)
+    c, x0, widths = couette_solver(slbm, WL, tb, "all", stream=stream)
+    inside = np.zeros(c.nx, bool)
+    for k, w in enumerate(widths):
+        inside[x0[k]:x0[k] + w] = True
+    done = 0
+    for at in (300, 1500, 6000):
+        c.step(at - done)
+        done = at
+        fe = c.indicator_eval()[0][:, inside].reshape(-1, 16)
+        lab = IND.labels(c.lattice_loss()[:, inside]).ravel()
+        done += 1
+        xs.append(fe)
+        ys.append(lab)
+    c.close()
+    x = np.concatenate(xs).astype(np.float64)
+    y = np.concatenate(ys)
+    w, losses = IND.train_gpu(x, y, epochs=20, batch=512, lr=3e-3, seed=0, balance=True)
+    hit = IND.forward(w, x)[0] > 0
+    pos = y > 0.5
+    report = {"samples": int(len(y)), "positive_fraction": float(y.mean()),
+              "gpu_steps": int(len(losses)), "first_loss": float(losses[0]),
+              "last_loss": float(np.mean(losses[-50:])),
+              "train_agreement": float(np.mean(hit == pos)),
+              "train_balanced_accuracy": float(0.5 * (hit[pos].mean() + (~hit[~pos]).mean())),
+              "labels": f"lattice loss > {IND.LOSS_THRESHOLD} on all-D2Q25 states",
+              "trainer": "slbm_mlp_train (one-block Adam kernel, FP16 operands, FP32 accumulation)"}
+    return w, report
+
+
+def decision_gaps(a, b, c, mask=None):
+    """Disagreement rates between three 0 / 1 flag fields (over `mask`)."""
+    m = np.ones(a.shape, bool) if mask is None else mask
+    a, b, c = a[m] > 0, b[m] > 0, c[m] > 0
+    return float(np.mean(a != b)), float(np.mean(a != c)), float(np.mean(b != c))
+
+
+def indicator_check_vortex(slbm, fields, weights, stream):
+    """The learned indicator's decisions on the benchmark field: an all-D2Q25
+    FP32 run of PARITY_STEPS steps, then per cell the indicator's flag, the
+    plain Mach criterion and the method's label (lattice loss above the
+    threshold) on that state."""
+    from paper_2102_12559_gb300 import indicator as IND
+    g = slbm.Solver(VN, VN, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=VTAU, stream=stream)
+    g.init_equilibrium(*fields)
+    g.set_flags(np.ones((VN, VN), np.uint8))
+    g.step(PARITY_STEPS)
+    g.set_indicator(weights, interval=10)
+    _, _, ind = g.indicator_eval(features=False, flags=True)
+    _, mu, mv, _ = g.moments()
+    mach = np.hypot(mu, mv) > THR
+    lab = IND.labels(g.lattice_loss()) > 0.5
+    g.close()
+    d_im, d_il, d_ml = decision_gaps(ind, mach, lab)
+    return {"state": f"all-D2Q25 FP32 run, {PARITY_STEPS} steps",
+            "indicator_vs_plain_mach": d_im, "indicator_vs_lattice_loss_label": d_il,
+            "plain_mach_vs_lattice_loss_label": d_ml,
+            "fraction_flagged": {"indicator": float(ind.mean()), "plain_mach": float(mach.mean()),
+                                 "label": float(lab.mean())}}
 
 
 def vortex_arm(slbm, stream, fields, precision, weights=None):
@@ -469,7 +573,8 @@ def headline(args):
 
     # ---- reduced-precision arms (rank 0): FP16 storage alone, and FP16 with
     # the learned indicator every 10 steps and the FP64 audit every 1000
-    weights = train_indicator(slbm, WL, stream)
+    weights, ind_train = train_indicator(slbm, WL, stream)
+    ind_vortex = indicator_check_vortex(slbm, fields, weights, stream)
     arms = {}
     for name, learned in (("fp16", False), ("fp16+indicator+audit", True)):
         r = vortex_arm(slbm, stream, fields, slbm.SLBM_FP16, weights if learned else None)
@@ -538,6 +643,7 @@ def headline(args):
                  "FP64 audit every 1000 steps and at the end"),
         "fp16_storage_arm": dict(arm_line("fp16", arms["fp16"]["ms"], arms["fp16"]["kern"]),
                                  form="FP16 storage of f_i - W_i, Mach criterion every step"),
+        "indicator": {"training": ind_train, "on_this_field": ind_vortex},
         "fp32_parity": {"rel_l2_vs_fp64_at_200_steps": mom_gap(moms["fp32"][0][:3], ref[:3]),
                         "flags_agree_with_fp64_run": float(np.mean(moms["fp32"][1] == ref_fl)),
                         "reference": "FP64 build of the library (at 1e-11 parity with the FP64 "
@@ -579,9 +685,10 @@ def run_study(args):
       the autotuner; D2Q25 within 4 lambda_1 of the shock with D2Q16 (or D2Q9)
       elsewhere, against D2Q25 everywhere.
     couette: the batched high-Knudsen Couette channels -- 128 independent
-      channels (H x 8, H 64-512, Kn 0.01-1 log-uniform, diffuse walls moving
-      at -0.1 / +0.1), side by side in one grid of one handle; D2Q25 in channels
-      with Kn > 0.1, D2Q9 in the others.
+      channels (H x 4, H 64-512, Kn 0.01-1 log-uniform, diffuse walls moving
+      at -0.1 / +0.1), side by side in one grid of one handle, in three arms:
+      the plain rule (D2Q25 in channels with Kn > 0.1), the learned indicator
+      (trained on the GPU from lattice-loss labels) and all-D2Q25 (reference).
     """
     import torch
     from paper_2102_12559_gb300 import slbm, workloads as WL
@@ -751,53 +858,84 @@ def run_study(args):
               flush=True)
         return
     if args.workload == "couette":
+        from paper_2102_12559_gb300 import indicator as IND
         batch = WL.couette_batch(count=128, seed=3)
-        kn_hi = 0.1  # channels above it run D2Q25, the others D2Q9
-        # one grid: the channels side by side along x (wall-normal), the
-        # streamwise axis y periodic with 8 cells, 2 G gap columns between
-        # neighbours; every channel its own relaxation time
-        G, ny = 2, 8
-        widths = [ch["H"] for ch in batch]
-        x0, nx = WL.channel_layout(widths, G)
-        probe = slbm.Solver(8, 8, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=0.6)
-        dt = probe.dt
-        probe.close()
-        taus = [couette_tau(ch["kn"], ch["H"], dt) for ch in batch]
-        g = slbm.Solver(nx, ny, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=0.6, periodic=(False, True))
-        g.init_equilibrium(*WL.uniform(nx, ny))
-        g.set_channels(x0, widths, [ch["uw_lo"] for ch in batch], [ch["uw_hi"] for ch in batch],
-                       taus)
-        fl = np.zeros((ny, nx), np.uint8)
-        for c, ch in enumerate(batch):
-            if ch["kn"] > kn_hi:
-                fl[:, x0[c]:x0[c] + widths[c]] = 1
-        g.set_flags(fl)
-        g.step(args.warmup)
-        torch.cuda.synchronize()
-        st = g.stream
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(st)
-        g.step(args.steps)
-        b.record(st)
-        torch.cuda.synchronize()
-        sec = a.elapsed_time(b) * 1e-3
-        cells = sum(ny * w for w in widths)
-        # antisymmetric walls: every channel's mean streamwise velocity stays 0
-        m = g.moments()
-        drift = max(abs(float(m[2][:, x0[c]:x0[c] + widths[c]].mean()))
-                    for c in range(len(batch))) / 0.1
-        finite = all(np.isfinite(v).all() for v in m[:3])
+        weights, ind_train = train_indicator(slbm, WL, stream)
+        arms, states = {}, {}
+        for mode in ("plain", "mlp", "all"):
+            g, x0, widths = couette_solver(slbm, WL, batch, mode, weights, stream=stream)
+            ny, nx = COUETTE_NY, g.nx
+            g.step(args.warmup)
+            torch.cuda.synchronize()
+            st = g.stream
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            g.step(args.steps)
+            b.record(st)
+            torch.cuda.synchronize()
+            sec = a.elapsed_time(b) * 1e-3
+            kr, kst = profiled(g, min(args.steps, 200))
+            cells = sum(ny * w for w in widths)
+            m = g.moments()
+            fl = g.get_flags()
+            arms[mode] = {"ms_per_step": sec / args.steps * 1e3,
+                          "mlups": cells * args.steps / sec / 1e6,
+                          "kernels_ms_per_step": dict(zip(slbm.KERNEL_NAMES,
+                                                          [k / max(kst, 1) for k in kr]))}
+            extra = {}
+            if mode == "all":  # the method's labels and the indicator's view of this state
+                g.set_indicator(weights, interval=10)
+                extra["ind"] = g.indicator_eval(features=False, flags=True)[2]
+                extra["lab"] = IND.labels(g.lattice_loss()) > 0.5
+            states[mode] = (m, fl, extra)
+            g.close()
+        inside = np.zeros((COUETTE_NY, nx), bool)
+        wall = np.zeros((COUETTE_NY, nx), bool)
+        kn_col = np.zeros(nx)
+        for c, w in enumerate(widths):
+            inside[:, x0[c]:x0[c] + w] = True
+            wall[:, x0[c]:x0[c] + 4] = wall[:, x0[c] + w - 4:x0[c] + w] = True
+            kn_col[x0[c]:x0[c] + w] = batch[c]["kn"]
+        kn = np.broadcast_to(kn_col, (COUETTE_NY, nx))
+        ref = states["all"][0]
+        u_ref = np.stack(ref[1:3])[:, inside]
+        plain_fl = plain_couette_flags(batch, x0, widths, (COUETTE_NY, nx))
+        ind_fl = states["mlp"][1]
+        lab, ind_all = states["all"][2]["lab"], states["all"][2]["ind"]
+        for mode in ("plain", "mlp"):
+            u = np.stack(states[mode][0][1:3])[:, inside]
+            arms[mode]["rel_l2_u_vs_all_d2q25"] = float(np.linalg.norm(u - u_ref) /
+                                                        np.linalg.norm(u_ref))
+            arms[mode]["high_order_fraction"] = float((states[mode][1][inside] == 1).mean())
+        d_ip, d_il, d_pl = decision_gaps(ind_fl, plain_fl, lab, inside)
+        bands = {}
+        for lo, hi in ((0.01, 0.03), (0.03, 0.1), (0.1, 0.3), (0.3, 1.0)):
+            sel = inside & (kn > lo) & (kn <= hi)
+            bands[f"Kn {lo}-{hi}"] = {
+                "indicator_near_walls": float((ind_fl[sel & wall] == 1).mean()),
+                "indicator_centre": float((ind_fl[sel & ~wall] == 1).mean()),
+                "label_near_walls": float(lab[sel & wall].mean()),
+                "label_centre": float(lab[sel & ~wall].mean())}
         print(json.dumps({
-            "study": "batched Couette channels (Sec. IV.C)",
-            "workload": f"{len(batch)} channels H x {ny}, H {min(widths)}-{max(widths)}, "
+            "study": "batched Couette channels (Sec. IV.C) with the learned indicator",
+            "workload": f"{len(batch)} channels H x {COUETTE_NY}, H {min(widths)}-{max(widths)}, "
                         "Kn 0.01-1 log-uniform, diffuse walls at -0.1 / +0.1, FP32, one "
-                        f"{nx} x {ny} grid (channels along x, 2 G gap columns)",
-            "d2q25_channels": sum(c["kn"] > kn_hi for c in batch), "cells": cells,
-            "steps": args.steps, "ms_per_step": sec / args.steps * 1e3,
-            "mlups": cells * args.steps / sec / 1e6,
+                        f"{nx} x {COUETTE_NY} grid (channels along x, 2 G gap columns)",
+            "cells": int(inside.sum()), "steps": args.steps,
             "timing": "CUDA events on the handle's stream",
-            "finite": finite, "max_mean_u_over_wall_speed": drift}), flush=True)
-        g.close()
+            "arms": arms,
+            "arm_forms": {"plain": f"D2Q25 in the channels with Kn > {KN_HI} (fixed)",
+                          "mlp": "learned indicator every 10 steps (SLBM_CRIT_MLP), from D2Q9 "
+                                 "at rest",
+                          "all": "D2Q25 everywhere (the accuracy reference)"},
+            "indicator_decisions_at_end": {
+                "indicator_vs_plain_rule": d_ip, "indicator_vs_lattice_loss_label": d_il,
+                "plain_rule_vs_lattice_loss_label": d_pl,
+                "indicator_on_all_d2q25_state_vs_label":
+                    decision_gaps(ind_all, lab, plain_fl, inside)[0],
+                "by_knudsen_band": bands},
+            "indicator_training": ind_train,
+            "finite": all(np.isfinite(v).all() for v in ref[:3])}), flush=True)
         return
     if args.workload == "pond":
         nx, ny = 1024, 512

@@ -127,7 +127,7 @@ typedef struct slbm_s *slbm_t;
                                 the learned indicator of slbm_set_indicator */
 
 typedef struct {
-    int nx, ny;              /* cells, each >= 1 and >= the stencil width */
+    int nx, ny;              /* cells (minimum: see slbm_create) */
     int periodic_x;          /* 1 = periodic along x, 0 = boundary sides XMIN/XMAX */
     int periodic_y;          /* 1 = periodic along y, 0 = boundary sides YMIN/YMAX */
 } slbm_grid;
@@ -159,7 +159,8 @@ SLBM_API int slbm_workspace_bytes(const slbm_grid *g, int lat_lo, int lat_hi, in
  * own device workspace.  Populations start at rest (rho = 1, u = 0), flags 0,
  * criterion none, every non-periodic side OUTFLOW.  SLBM_EINVAL for bad
  * arguments, among them a grid narrower than 2 G + 1 cells per side (G = the
- * stencil reach) and, in the lattice frame, a periodic axis whose last
+ * stencil reach; G along a periodic side in the lattice frame) and, in the
+ * lattice frame, a periodic axis whose last
  * partial 32 x 8 tile is narrower than G (nx % 32 and ny % 8 must be 0 or at
  * least G). */
 SLBM_API int slbm_create(const slbm_grid *g, int lat_lo, int lat_hi, double tau, int interp_order,
@@ -221,6 +222,52 @@ SLBM_API int slbm_set_criterion(slbm_t h, int kind, double threshold);
 SLBM_API int slbm_set_indicator(slbm_t h, const float *w1, const float *b1, const float *w2,
                                 const float *b2, const float *w3, float b3, int interval);
 SLBM_API int slbm_indicator_eval(slbm_t h, float *features, float *logits, uint8_t *flags);
+
+/* Per-cell lattice loss: what the low-order lattice loses in one step, the
+ * indicator's training label (Sec. III.B-D).  From a lattice-frame state in
+ * which every cell is high-order (flags 1; gap columns between channels
+ * allowed) and fixed flags (SLBM_CRIT_NONE), two steps are taken from the same
+ * start: a = one step of the all-high-order state, b = the lift (Sec. III.B)
+ * of one step of its projection (Sec. III.C, every cell low-order).  Output,
+ * per cell (host, nx*ny doubles, x + nx*y):
+ *   loss = || a - b ||_2 / rho_a   (norm over the high-order populations),
+ * 0 in gap cells.  The handle ends at a, one step advanced (the step counter
+ * counts one).  Nothing is lost by a uniform flow at any Mach number, nor by
+ * the raw moments m_ab (a, b < n_lo) the low-order lattice carries; the loss
+ * holds the non-equilibrium of the higher raw moments (Knudsen layers) and
+ * what the low-order lattice's aliased fluxes (c^3 = 3c on D2Q9's nodes) get
+ * wrong at high Mach number.  Allocates two population-sized temporaries;
+ * synchronises.  SLBM_EINVAL: not lattice frame, a criterion is on, or a
+ * non-gap cell is low-order. */
+SLBM_API int slbm_lattice_loss(slbm_t h, double *loss);
+
+/* Training of the indicator: mini-batch Adam on the mean logistic loss
+ * log(1 + exp(-s z)), s = 2y - 1, of the network above, on the GPU (one
+ * thread block runs every step: forward pass, back-propagation and the Adam
+ * update).  Not tied to a handle; runs on the current CUDA device.
+ *   x: n x 16 features (host floats, row-major, as slbm_indicator_eval
+ *      returns them), y: n labels, each 0 or 1;
+ *   idx: steps x batch sample indices in [0, n) (host ints, the rows of step s
+ *      at idx[s * batch ...]): the mini-batches, drawn by the caller;
+ *   batch: 128, 256, 384 or 512;
+ *   hyper = {lr, beta1, beta2, eps}: lr > 0, 0 <= beta < 1, eps > 0;
+ *   t0: Adam steps already taken (step s uses the bias corrections of
+ *      t0 + s + 1);
+ *   params: the 1633 parameters W1 (16 x 32 row-major, input index first),
+ *      b1 (32), W2 (32 x 32), b2 (32), w3 (32), b3 (1), host floats, in / out;
+ *   adam: first then second moments (2 x 1633 host floats, zeros to start),
+ *      in / out;
+ *   loss: the mean loss of every step's batch before its update (steps
+ *      floats, or NULL); grad: the last step's gradient (1633 floats, or NULL).
+ * Precision: features, W1, W2, the hidden activations and their gradients
+ * rounded to FP16, products accumulated in FP32 on the tensor cores; biases,
+ * the output layer, the master weights and Adam in FP32.  cuda_stream: a
+ * cudaStream_t, or NULL.  Allocates and frees device memory; synchronises
+ * the stream.  SLBM_EINVAL on any invalid argument (checked before any device
+ * work), SLBM_ENOMEM, SLBM_ECUDA. */
+SLBM_API int slbm_mlp_train(const float *x, const float *y, long long n, const int *idx, int steps,
+                            int batch, const double hyper[4], int t0, float *params, float *adam,
+                            float *loss, float *grad, void *cuda_stream);
 
 /* Boundary of a non-periodic side.  Arrays run along the side (ny entries
  * for XMIN/XMAX, nx for YMIN/YMAX), host doubles, copied: DIRICHLET needs

@@ -941,9 +941,14 @@ bool create_args_ok(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int 
       return false;
     }
   }
-  if (g->nx < 2 * lay.G + 1 || g->ny < 2 * lay.G + 1) {
-    snprintf(g_create_err, sizeof(g_create_err), "grid must be at least %d cells per side",
-             2 * lay.G + 1);
+  // in the lattice frame a periodic side's ghost images wrap once (n >= G);
+  // a bounded side, and every side of a co-moving grid, needs 2 G + 1
+  const bool lat = frame == SLBM_FRAME_LATTICE;
+  if (g->nx < (lat && g->periodic_x ? lay.G : 2 * lay.G + 1) ||
+      g->ny < (lat && g->periodic_y ? lay.G : 2 * lay.G + 1)) {
+    snprintf(g_create_err, sizeof(g_create_err),
+             "grid must be at least %d cells per side (%d along a periodic lattice-frame side)",
+             2 * lay.G + 1, lay.G);
     return false;
   }
   // lattice frame: interface work is found per 32 x 8 tile from the tiles next
@@ -1327,6 +1332,110 @@ int slbm_indicator_eval(slbm_t h, float* features, float* logits, uint8_t* flags
   cudaFree(dlog);
   cudaFree(dfl);
   return rc;
+}
+
+int slbm_lattice_loss(slbm_t h, double* loss) {
+  SLBM_GUARD(h);
+  if (!loss) return fail(h, SLBM_EINVAL, "loss is required");
+  if (h->frame != SLBM_FRAME_LATTICE) return fail(h, SLBM_EINVAL, "lattice frame only");
+  if (h->crit != SLBM_CRIT_NONE)
+    return fail(h, SLBM_EINVAL, "the lattice loss needs fixed flags (SLBM_CRIT_NONE)");
+  const size_t nc = h->ncell();
+  std::vector<uint8_t> fl(nc);
+  int rc = slbm_get_flags(h, fl.data());
+  if (rc) return rc;
+  for (uint8_t v : fl)
+    if (v != 1 && v != kFlagGap)
+      return fail(h, SLBM_EINVAL, "the lattice loss starts from an all-high-order state");
+  const size_t es = h->precision == SLBM_FP64 ? 8 : (h->precision == SLBM_FP16 ? 2 : 4);
+  const size_t bytes = (size_t)(h->nhi * h->nhi) * h->lay.plane * es;
+  char* tmp = nullptr;
+  if (cudaMalloc(&tmp, 2 * bytes + nc * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, SLBM_ENOMEM, "cudaMalloc");
+  }
+  char* start = tmp;           // f_Q(t), ghost ring included
+  char* stepped = tmp + bytes;  // f_Q(t + 1)
+  double* dloss = reinterpret_cast<double*>(tmp + 2 * bytes);
+  std::vector<uint8_t> lo(nc, 0), hi(nc, 1);
+  auto d2d = [&](void* dst, const void* src) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, h->st);
+  };
+  // high-order step; back to the start; projected step; lifting
+  rc = d2d(start, h->pops(h->cur, 1)) != cudaSuccess ? fail(h, SLBM_ECUDA, "D2D copy") : SLBM_OK;
+  if (!rc) rc = slbm_step(h, 1);
+  if (!rc && d2d(stepped, h->pops(h->cur, 1)) != cudaSuccess) rc = fail(h, SLBM_ECUDA, "D2D copy");
+  if (!rc && d2d(h->pops(h->cur, 1), start) != cudaSuccess) rc = fail(h, SLBM_ECUDA, "D2D copy");
+  if (!rc) rc = slbm_set_flags(h, lo.data());
+  if (!rc) rc = slbm_step(h, 1);
+  if (!rc) rc = slbm_set_flags(h, hi.data());
+  if (!rc) {
+    const cudaError_t e = with_types(h, [&](auto ty, const auto& prm) {
+      SLBM_TYPES(ty);
+      return launch_lattice_loss<S, R>(prm, (const S*)stepped, (const S*)h->pops(h->cur, 1),
+                                       h->flags(h->fcur), dloss, h->st);
+    });
+    if (e != cudaSuccess) rc = fail(h, SLBM_ECUDA, "lattice loss launch", e);
+  }
+  // the handle continues from the high-order step
+  if (!rc && d2d(h->pops(h->cur, 1), stepped) != cudaSuccess) rc = fail(h, SLBM_ECUDA, "D2D copy");
+  if (!rc && cudaMemcpyAsync(loss, dloss, nc * sizeof(double), cudaMemcpyDeviceToHost, h->st) !=
+                 cudaSuccess)
+    rc = fail(h, SLBM_ECUDA, "D2H copy");
+  if (!rc && cudaStreamSynchronize(h->st) != cudaSuccess) rc = fail(h, SLBM_ECUDA, "sync");
+  if (!rc) h->steps -= 1;  // one step of the state, not two
+  cudaFree(tmp);
+  return rc;
+}
+
+int slbm_mlp_train(const float* x, const float* y, long long n, const int* idx, int steps,
+                   int batch, const double hyper[4], int t0, float* params, float* adam,
+                   float* loss, float* grad, void* cuda_stream) {
+  if (!x || !y || !idx || !params || !adam || !hyper || n < 1 || steps < 0 || t0 < 0 ||
+      batch < 128 || batch > kMlpMaxBatch || batch % 128)
+    return SLBM_EINVAL;
+  const double lr = hyper[0], b1 = hyper[1], b2 = hyper[2], eps = hyper[3];
+  if (!(lr > 0.0) || !std::isfinite(lr) || !(b1 >= 0.0 && b1 < 1.0) || !(b2 >= 0.0 && b2 < 1.0) ||
+      !(eps > 0.0) || !std::isfinite(eps))
+    return SLBM_EINVAL;
+  const size_t nidx = (size_t)steps * (size_t)batch;
+  for (size_t i = 0; i < nidx; ++i)
+    if (idx[i] < 0 || idx[i] >= n) return SLBM_EINVAL;
+  for (long long i = 0; i < n; ++i)
+    if (!(y[i] == 0.f || y[i] == 1.f)) return SLBM_EINVAL;
+  if (steps == 0) return SLBM_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const size_t bx = (size_t)n * 16 * sizeof(float), by = (size_t)n * sizeof(float);
+  const size_t bi = nidx * sizeof(int), bp = kMlpParams * sizeof(float);
+  const size_t bl = (size_t)steps * sizeof(float);
+  auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+  char* d = nullptr;
+  if (cudaMalloc(&d, al(bx) + al(by) + al(bi) + 4 * al(bp) + al(bl)) != cudaSuccess) {
+    cudaGetLastError();
+    return SLBM_ENOMEM;
+  }
+  float* dx = reinterpret_cast<float*>(d);
+  float* dy = reinterpret_cast<float*>(d + al(bx));
+  int* di = reinterpret_cast<int*>(d + al(bx) + al(by));
+  float* dp = reinterpret_cast<float*>(d + al(bx) + al(by) + al(bi));
+  float* da = dp + al(bp) / sizeof(float);            // 2 x kMlpParams
+  float* dg = da + 2 * al(bp) / sizeof(float);
+  float* dl = dg + al(bp) / sizeof(float);
+  cudaError_t e = cudaMemcpyAsync(dx, x, bx, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dy, y, by, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(di, idx, bi, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dp, params, bp, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(da, adam, 2 * bp, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = launch_mlp_train(dx, dy, di, steps, batch, (float)lr, (float)b1, (float)b2, (float)eps, t0,
+                         dp, da, loss ? dl : nullptr, grad ? dg : nullptr, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(params, dp, bp, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(adam, da, 2 * bp, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, dl, bl, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && grad) e = cudaMemcpyAsync(grad, dg, bp, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  return e == cudaSuccess ? SLBM_OK : SLBM_ECUDA;
 }
 
 int slbm_set_boundary(slbm_t h, int side, int kind, const double* rho, const double* ux,

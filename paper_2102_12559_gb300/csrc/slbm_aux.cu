@@ -290,7 +290,7 @@ k_tile_work(int nx, int ny, int periodic_x, int periodic_y, const uint8_t* __res
   if (x < nx && y < ny) {
     const long long c = x + (long long)nx * y;
     const int o = flag_old[c], n = flag_new[c];
-    bit = (1 << n) | (o != n ? 4 : 0);
+    if (n != kFlagGap) bit = (1 << n) | (o != n ? 4 : 0);  // gap cells are no work
   }
   __shared__ int acc;
   if (tid == 0) acc = 0;

@@ -240,6 +240,24 @@ cudaError_t launch_indicator(const Params<R>& p, const S* f0, const S* f1, const
                              float* feat_out, float* logit_out, uint8_t* flag_out,
                              cudaStream_t st);
 
+// Per-cell lattice loss || a - b ||_2 / rho_a over the high-order planes of
+// two population buffers a, b (same layout as the handle's planes of lattice
+// 1); gap cells get 0.  out: nc doubles.
+template <class S, class R>
+cudaError_t launch_lattice_loss(const Params<R>& p, const S* a, const S* b, const uint8_t* flag,
+                                double* out, cudaStream_t st);
+
+// Indicator training (slbm_indicator.cu): `steps` Adam steps of mini-batch
+// `batch` in one single-block launch.  Device arrays: x (n x 16 FP32
+// features), y (n labels), idx (steps x batch sample indices, validated by the
+// caller), params (kMlpParams FP32, in / out), adam (2 x kMlpParams, in / out),
+// loss (steps, or null), grad (kMlpParams, the last step's gradient, or null).
+constexpr int kMlpParams = 16 * 32 + 32 + 32 * 32 + 32 + 32 + 1;
+constexpr int kMlpMaxBatch = 512;
+cudaError_t launch_mlp_train(const float* x, const float* y, const int* idx, int steps, int batch,
+                             float lr, float beta1, float beta2, float eps, int t0, float* params,
+                             float* adam, float* loss, float* grad, cudaStream_t st);
+
 // Launchers (defined in the kernel translation units).  S = storage type,
 // R = arithmetic type.  fin0 / fin1 and fout0 / fout1: base of the input and
 // output buffers' planes of lattice 0 / 1.  Stream-collide of every cell

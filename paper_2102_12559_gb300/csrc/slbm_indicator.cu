@@ -35,7 +35,8 @@ __device__ __forceinline__ int clampwrap(int v, int n, int periodic) {
 // Features of cell (x, y) from its own lattice (N nodes per axis).
 template <int N, class S, class R>
 __device__ void cell_features_n(const Params<R>& p, const LatTab<R>& L, const S* f, int x, int y,
-                                const R* mrho, const R* mux, const R* muy, float* out) {
+                                const uint8_t* flag, const R* mrho, const R* mux, const R* muy,
+                                float* out) {
   const size_t base = (size_t)(y + p.G) * p.pitch + (x + kOX);
   R s[N * N];
   R dr = R(0), jx = R(0), jy = R(0), e2 = R(0);
@@ -75,8 +76,15 @@ __device__ void cell_features_n(const Params<R>& p, const LatTab<R>& L, const S*
   }
   const int xm = clampwrap(x - 1, p.nx, p.periodic_x), xp = clampwrap(x + 1, p.nx, p.periodic_x);
   const int ym = clampwrap(y - 1, p.ny, p.periodic_y), yp = clampwrap(y + 1, p.ny, p.periodic_y);
-  const long long cxm = xm + (long long)p.nx * y, cxp = xp + (long long)p.nx * y;
-  const long long cym = x + (long long)p.nx * ym, cyp = x + (long long)p.nx * yp;
+  const long long c = x + (long long)p.nx * y;
+  // a gap neighbour (the wall side of a channel) counts as the edge: the cell
+  // itself is repeated, as at a non-periodic side
+  long long cxm = xm + (long long)p.nx * y, cxp = xp + (long long)p.nx * y;
+  long long cym = x + (long long)p.nx * ym, cyp = x + (long long)p.nx * yp;
+  if (flag[cxm] == kFlagGap) cxm = c;
+  if (flag[cxp] == kFlagGap) cxp = c;
+  if (flag[cym] == kFlagGap) cym = c;
+  if (flag[cyp] == kFlagGap) cyp = c;
   out[0] = (float)dr;
   out[1] = (float)ux;
   out[2] = (float)uy;
@@ -99,13 +107,14 @@ __device__ void cell_features_n(const Params<R>& p, const LatTab<R>& L, const S*
 
 template <class S, class R>
 __device__ void cell_features(const Params<R>& p, const S* f0, const S* f1, int k, int x, int y,
-                              const R* mrho, const R* mux, const R* muy, float* out) {
+                              const uint8_t* flag, const R* mrho, const R* mux, const R* muy,
+                              float* out) {
   const LatTab<R>& L = p.lat[k];
   const S* f = k ? f1 : f0;
   switch (L.n) {
-    case 3: cell_features_n<3, S, R>(p, L, f, x, y, mrho, mux, muy, out); break;
-    case 4: cell_features_n<4, S, R>(p, L, f, x, y, mrho, mux, muy, out); break;
-    default: cell_features_n<5, S, R>(p, L, f, x, y, mrho, mux, muy, out); break;
+    case 3: cell_features_n<3, S, R>(p, L, f, x, y, flag, mrho, mux, muy, out); break;
+    case 4: cell_features_n<4, S, R>(p, L, f, x, y, flag, mrho, mux, muy, out); break;
+    default: cell_features_n<5, S, R>(p, L, f, x, y, flag, mrho, mux, muy, out); break;
   }
 }
 
@@ -139,6 +148,12 @@ k_ind_moments(const Params<R> p, const S* f0, const S* f1, const uint8_t* __rest
   if (x >= p.nx || y >= p.ny) return;
   const long long c = x + (long long)p.nx * y;
   const int k = flag[c];
+  if (k == kFlagGap) {  // no fluid between channels: zero gradients at their walls
+    mrho[c] = R(1);
+    mux[c] = R(0);
+    muy[c] = R(0);
+    return;
+  }
   const LatTab<R>& L = p.lat[k];
   const S* f = k ? f1 : f0;
   const size_t base = (size_t)(y + p.G) * p.pitch + (x + kOX);
@@ -214,9 +229,12 @@ k_indicator(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restri
     float fe[kFeat];
 #pragma unroll
     for (int q = 0; q < kFeat; ++q) fe[q] = 0.f;
-    if (c < nc) {
+    const int fc = c < nc ? flag[c] : (int)kFlagGap;
+    if (fc != kFlagGap) {
       const int x = (int)(c % p.nx), y = (int)(c / p.nx);
-      cell_features<S, R>(p, f0, f1, flag[c], x, y, mrho, mux, muy, fe);
+      cell_features<S, R>(p, f0, f1, fc, x, y, flag, mrho, mux, muy, fe);
+    }
+    if (c < nc) {
       if (feat_out)
 #pragma unroll
         for (int q = 0; q < kFeat; ++q) feat_out[c * kFeat + q] = fe[q];
@@ -274,18 +292,370 @@ k_indicator(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restri
         o1 += __shfl_xor_sync(0xffffffffu, o1, 2);
         if (t == 0) {
           const long long ca = base + r0, cb = base + r1;
+          // gap cells keep their flag and get logit 0
           if (ca < nc) {
-            if (logit_out) logit_out[ca] = o0 + b3;
-            if (flag_out) flag_out[ca] = (o0 + b3) > thr ? 1 : 0;
+            const bool gap = flag[ca] == kFlagGap;
+            if (logit_out) logit_out[ca] = gap ? 0.f : o0 + b3;
+            if (flag_out) flag_out[ca] = gap ? kFlagGap : ((o0 + b3) > thr ? 1 : 0);
           }
           if (cb < nc) {
-            if (logit_out) logit_out[cb] = o1 + b3;
-            if (flag_out) flag_out[cb] = (o1 + b3) > thr ? 1 : 0;
+            const bool gap = flag[cb] == kFlagGap;
+            if (logit_out) logit_out[cb] = gap ? 0.f : o1 + b3;
+            if (flag_out) flag_out[cb] = gap ? kFlagGap : ((o1 + b3) > thr ? 1 : 0);
           }
         }
       }
     }
     __syncwarp();  // sfeat is rewritten next pass
+  }
+}
+
+// Per-cell lattice loss between two buffers of the high-order planes (the
+// stored values are deviations f - W, so the weights cancel in a - b and
+// rho_a = 1 + sum a); FP64 sums.
+template <class S, class R>
+__global__ void __launch_bounds__(kTX * kTY)
+k_lattice_loss(const Params<R> p, const S* __restrict__ a, const S* __restrict__ b,
+               const uint8_t* __restrict__ flag, double* __restrict__ out) {
+  const int x = blockIdx.x * kTX + threadIdx.x, y = blockIdx.y * kTY + threadIdx.y;
+  if (x >= p.nx || y >= p.ny) return;
+  const long long c = x + (long long)p.nx * y;
+  if (flag[c] == kFlagGap) {
+    out[c] = 0.0;
+    return;
+  }
+  const size_t base = (size_t)(y + p.G) * p.pitch + (x + kOX);
+  const int q = p.lat[1].n * p.lat[1].n;
+  double sa = 0.0, d2 = 0.0;
+  for (int i = 0; i < q; ++i) {
+    const double va = (double)static_cast<R>(a[(size_t)i * p.plane + base]);
+    const double vb = (double)static_cast<R>(b[(size_t)i * p.plane + base]);
+    sa += va;
+    d2 += (va - vb) * (va - vb);
+  }
+  out[c] = sqrt(d2) / (1.0 + sa);
+}
+
+// ------------------------------------------------------------------ training
+//
+// Mini-batch Adam on the logistic loss, every step in one thread block (the
+// steps are sequential, and a batch of at most 512 rows is a few MFLOP).  Per
+// step:
+//  F. warp w takes batch rows [w B/8, (w + 1) B/8) in m16 tiles: gathers the
+//     rows' features (rounded to FP16) and labels, runs the forward pass with
+//     each layer's C fragments reused as the next layer's A fragments, the
+//     loss, and back-propagation: dlogit = p - y (the 1/B of the mean is
+//     applied to the FP32 gradient, so the FP16 operands stay O(1)),
+//     dZ2 = dlogit w3 [Z2 > 0], dH1 = dZ2 W2^T on the tensor cores,
+//     dZ1 = dH1 [Z1 > 0].  Bias and output-layer gradients are summed in FP32
+//     registers; X, H1, dZ2 and dZ1 go to shared memory transposed (FP16,
+//     batch rows contiguous) for
+//  G. the weight gradients dW2 = H1^T dZ2 (8 m16n8 tiles, one per warp) and
+//     dW1 = X^T dZ1 (4 tiles, each over two halves of the batch), contracted
+//     over the batch on the tensor cores;
+//  A. Adam on every parameter (FP32 master weights and moments), then the
+//     FP16 copies of W1 and W2 for the next step.
+constexpr int kTrainWarps = 8;
+constexpr int kTrainThreads = 32 * kTrainWarps;
+constexpr int kOffB1 = kFeat * kHid, kOffW2 = kOffB1 + kHid, kOffB2 = kOffW2 + kHid * kHid;
+constexpr int kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + kHid;
+static_assert(kOffB3 + 1 == kMlpParams, "parameter layout");
+constexpr int kParamPad = (kMlpParams + 3) / 4 * 4;
+constexpr int kPartStride = 100;  // per warp: db1 (32), db2 (32), dw3 (32), db3, loss
+
+size_t train_smem_bytes(int batch) {
+  const size_t ld = (size_t)batch + 8;
+  return sizeof(float) * (3 * kParamPad + kHid * kHid + 2 * kFeat * kHid +
+                          kTrainWarps * kPartStride) +
+         sizeof(__half) * (kFeat * kHid + kHid * kHid + (kFeat + 3 * kHid) * ld);
+}
+
+__device__ __forceinline__ uint32_t lds32(const __half* p) {
+  return *reinterpret_cast<const uint32_t*>(p);
+}
+
+// B fragment of the transposed weight W^T (W row-major K x N, here the
+// contraction runs over W's columns): lane (g, t) holds W[8 nt + g][k0 + 2t .. + 1]
+// and W[8 nt + g][k0 + 2t + 8 .. + 9].
+__device__ __forceinline__ void bfrag_t(const __half* W, int ncols, int k0, int nt, int g, int t,
+                                        uint32_t& b0, uint32_t& b1) {
+  const __half* r = W + (8 * nt + g) * ncols + k0 + 2 * t;
+  b0 = lds32(r);
+  b1 = lds32(r + 8);
+}
+
+__device__ __forceinline__ float softplus(float v) {  // log(1 + e^v), stable
+  return fmaxf(v, 0.f) + log1pf(expf(-fabsf(v)));
+}
+
+// sum over the 8 lanes of a column group (lanes with the same t)
+__device__ __forceinline__ float sum_g(float v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 8);
+  v += __shfl_xor_sync(0xffffffffu, v, 16);
+  return v;
+}
+
+__global__ void __launch_bounds__(kTrainThreads, 1)
+k_mlp_train(const float* __restrict__ x, const float* __restrict__ y,
+            const int* __restrict__ idx, int steps, int B, float lr, float beta1, float beta2,
+            float eps, int t0, float* __restrict__ params, float* __restrict__ adam,
+            float* __restrict__ loss_out, float* __restrict__ grad_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int ld = B + 8;
+  float* sw = reinterpret_cast<float*>(smem);  // master weights
+  float* sm = sw + kParamPad;                  // Adam first moments
+  float* sv = sm + kParamPad;                  // Adam second moments
+  float* sg2 = sv + kParamPad;                 // dW2 (32 x 32)
+  float* sg1 = sg2 + kHid * kHid;              // dW1, two batch halves (2 x 16 x 32)
+  float* sp = sg1 + 2 * kFeat * kHid;          // per-warp partial sums
+  __half* sw1h = reinterpret_cast<__half*>(sp + kTrainWarps * kPartStride);
+  __half* sw2h = sw1h + kFeat * kHid;
+  __half* sXt = sw2h + kHid * kHid;  // X^T (16 x ld)
+  __half* sH1t = sXt + kFeat * ld;   // H1^T (32 x ld)
+  __half* sD2t = sH1t + kHid * ld;   // dZ2^T
+  __half* sD1t = sD2t + kHid * ld;   // dZ1^T
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  for (int q = tid; q < kMlpParams; q += kTrainThreads) {
+    const float w = params[q];
+    sw[q] = w;
+    sm[q] = adam[q];
+    sv[q] = adam[kMlpParams + q];
+    if (q < kOffB1) sw1h[q] = __float2half_rn(w);
+    else if (q >= kOffW2 && q < kOffB2) sw2h[q - kOffW2] = __float2half_rn(w);
+  }
+  __syncthreads();
+  const int RW = B / kTrainWarps;
+  const float invB = 1.f / (float)B;
+  for (int step = 0; step < steps; ++step) {
+    const int* bidx = idx + (long long)step * B;
+    // ---- F: forward and back-propagation over the warp's rows
+    uint32_t B1[4][2], B2[2][4][2], BT[2][4][2];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) bfrag(sw1h, kHid, 0, nt, g, t, B1[nt][0], B1[nt][1]);
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        bfrag(sw2h, kHid, 16 * kk, nt, g, t, B2[kk][nt][0], B2[kk][nt][1]);
+        bfrag_t(sw2h, kHid, 16 * kk, nt, g, t, BT[kk][nt][0], BT[kk][nt][1]);
+      }
+    float acc_b1[4][2] = {}, acc_b2[4][2] = {}, acc_w3[4][2] = {};
+    float acc_b3 = 0.f, acc_loss = 0.f;
+    for (int mt = 0; mt < RW / 16; ++mt) {
+      const int r0 = warp * RW + 16 * mt + g, r1 = r0 + 8;
+      const long long s0 = bidx[r0], s1 = bidx[r1];
+      const float2 xa = *reinterpret_cast<const float2*>(x + s0 * kFeat + 2 * t);
+      const float2 xb = *reinterpret_cast<const float2*>(x + s1 * kFeat + 2 * t);
+      const float2 xc = *reinterpret_cast<const float2*>(x + s0 * kFeat + 2 * t + 8);
+      const float2 xd = *reinterpret_cast<const float2*>(x + s1 * kFeat + 2 * t + 8);
+      const float y0 = y[s0], y1 = y[s1];
+      const __half ha0 = __float2half_rn(xa.x), ha1 = __float2half_rn(xa.y);
+      const __half hb0 = __float2half_rn(xb.x), hb1 = __float2half_rn(xb.y);
+      const __half hc0 = __float2half_rn(xc.x), hc1 = __float2half_rn(xc.y);
+      const __half hd0 = __float2half_rn(xd.x), hd1 = __float2half_rn(xd.y);
+      const uint32_t A[4] = {pack2(ha0, ha1), pack2(hb0, hb1), pack2(hc0, hc1), pack2(hd0, hd1)};
+      sXt[(2 * t) * ld + r0] = ha0;
+      sXt[(2 * t + 1) * ld + r0] = ha1;
+      sXt[(2 * t) * ld + r1] = hb0;
+      sXt[(2 * t + 1) * ld + r1] = hb1;
+      sXt[(2 * t + 8) * ld + r0] = hc0;
+      sXt[(2 * t + 9) * ld + r0] = hc1;
+      sXt[(2 * t + 8) * ld + r1] = hd0;
+      sXt[(2 * t + 9) * ld + r1] = hd1;
+      // layer 1
+      float z1[4][4];
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const float ba = sw[kOffB1 + 8 * nt + 2 * t], bb = sw[kOffB1 + 8 * nt + 2 * t + 1];
+        z1[nt][0] = ba; z1[nt][1] = bb; z1[nt][2] = ba; z1[nt][3] = bb;
+        mma16816(z1[nt], A, B1[nt][0], B1[nt][1]);
+      }
+      // H1 = relu(Z1) in FP16: layer 2's A fragments, and H1^T for dW2
+      __half h1[4][4];
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) h1[nt][q] = __float2half_rn(fmaxf(z1[nt][q], 0.f));
+        const int col = 8 * nt + 2 * t;
+        sH1t[col * ld + r0] = h1[nt][0];
+        sH1t[(col + 1) * ld + r0] = h1[nt][1];
+        sH1t[col * ld + r1] = h1[nt][2];
+        sH1t[(col + 1) * ld + r1] = h1[nt][3];
+      }
+      float z2[4][4];
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const float ba = sw[kOffB2 + 8 * nt + 2 * t], bb = sw[kOffB2 + 8 * nt + 2 * t + 1];
+        z2[nt][0] = ba; z2[nt][1] = bb; z2[nt][2] = ba; z2[nt][3] = bb;
+      }
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {
+        const uint32_t A2[4] = {pack2(h1[2 * kk][0], h1[2 * kk][1]),
+                                pack2(h1[2 * kk][2], h1[2 * kk][3]),
+                                pack2(h1[2 * kk + 1][0], h1[2 * kk + 1][1]),
+                                pack2(h1[2 * kk + 1][2], h1[2 * kk + 1][3])};
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) mma16816(z2[nt], A2, B2[kk][nt][0], B2[kk][nt][1]);
+      }
+      // output layer (FP32), reduced over the four lanes of a row group
+      float o0 = 0.f, o1 = 0.f;
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const float wa = sw[kOffW3 + 8 * nt + 2 * t], wb = sw[kOffW3 + 8 * nt + 2 * t + 1];
+        o0 += fmaxf(z2[nt][0], 0.f) * wa + fmaxf(z2[nt][1], 0.f) * wb;
+        o1 += fmaxf(z2[nt][2], 0.f) * wa + fmaxf(z2[nt][3], 0.f) * wb;
+      }
+      o0 += __shfl_xor_sync(0xffffffffu, o0, 1);
+      o0 += __shfl_xor_sync(0xffffffffu, o0, 2);
+      o1 += __shfl_xor_sync(0xffffffffu, o1, 1);
+      o1 += __shfl_xor_sync(0xffffffffu, o1, 2);
+      const float zl0 = o0 + sw[kOffB3], zl1 = o1 + sw[kOffB3];
+      // logistic loss log(1 + exp(-s z)), s = 2y - 1; dloss/dz = sigmoid(z) - y
+      const float d0 = 1.f / (1.f + expf(-zl0)) - y0, d1 = 1.f / (1.f + expf(-zl1)) - y1;
+      if (t == 0) {  // each row once
+        acc_loss += softplus(-(2.f * y0 - 1.f) * zl0) + softplus(-(2.f * y1 - 1.f) * zl1);
+        acc_b3 += d0 + d1;
+      }
+      float dz2[4][4];
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const float wa = sw[kOffW3 + 8 * nt + 2 * t], wb = sw[kOffW3 + 8 * nt + 2 * t + 1];
+        acc_w3[nt][0] += d0 * fmaxf(z2[nt][0], 0.f) + d1 * fmaxf(z2[nt][2], 0.f);
+        acc_w3[nt][1] += d0 * fmaxf(z2[nt][1], 0.f) + d1 * fmaxf(z2[nt][3], 0.f);
+        dz2[nt][0] = z2[nt][0] > 0.f ? d0 * wa : 0.f;
+        dz2[nt][1] = z2[nt][1] > 0.f ? d0 * wb : 0.f;
+        dz2[nt][2] = z2[nt][2] > 0.f ? d1 * wa : 0.f;
+        dz2[nt][3] = z2[nt][3] > 0.f ? d1 * wb : 0.f;
+        acc_b2[nt][0] += dz2[nt][0] + dz2[nt][2];
+        acc_b2[nt][1] += dz2[nt][1] + dz2[nt][3];
+      }
+      __half hd2[4][4];
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) hd2[nt][q] = __float2half_rn(dz2[nt][q]);
+        const int col = 8 * nt + 2 * t;
+        sD2t[col * ld + r0] = hd2[nt][0];
+        sD2t[(col + 1) * ld + r0] = hd2[nt][1];
+        sD2t[col * ld + r1] = hd2[nt][2];
+        sD2t[(col + 1) * ld + r1] = hd2[nt][3];
+      }
+      // dH1 = dZ2 W2^T
+      float dh1[4][4] = {};
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {
+        const uint32_t A3[4] = {pack2(hd2[2 * kk][0], hd2[2 * kk][1]),
+                                pack2(hd2[2 * kk][2], hd2[2 * kk][3]),
+                                pack2(hd2[2 * kk + 1][0], hd2[2 * kk + 1][1]),
+                                pack2(hd2[2 * kk + 1][2], hd2[2 * kk + 1][3])};
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) mma16816(dh1[nt], A3, BT[kk][nt][0], BT[kk][nt][1]);
+      }
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        float dz1[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dz1[q] = z1[nt][q] > 0.f ? dh1[nt][q] : 0.f;
+        acc_b1[nt][0] += dz1[0] + dz1[2];
+        acc_b1[nt][1] += dz1[1] + dz1[3];
+        const int col = 8 * nt + 2 * t;
+        sD1t[col * ld + r0] = __float2half_rn(dz1[0]);
+        sD1t[(col + 1) * ld + r0] = __float2half_rn(dz1[1]);
+        sD1t[col * ld + r1] = __float2half_rn(dz1[2]);
+        sD1t[(col + 1) * ld + r1] = __float2half_rn(dz1[3]);
+      }
+    }
+    // the warp's partial sums of the bias and output-layer gradients
+    float* pw = sp + warp * kPartStride;
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const float v1 = sum_g(acc_b1[nt][j]), v2 = sum_g(acc_b2[nt][j]),
+                    v3 = sum_g(acc_w3[nt][j]);
+        if (g == 0) {
+          pw[8 * nt + 2 * t + j] = v1;
+          pw[32 + 8 * nt + 2 * t + j] = v2;
+          pw[64 + 8 * nt + 2 * t + j] = v3;
+        }
+      }
+    {
+      const float vb = sum_g(acc_b3), vl = sum_g(acc_loss);
+      if (lane == 0) {
+        pw[96] = vb;
+        pw[97] = vl;
+      }
+    }
+    __syncthreads();
+    // ---- G: weight gradients, contraction over the batch
+    {
+      const int mi = warp >> 2, ni = warp & 3;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int k0 = 0; k0 < B; k0 += 16) {
+        const __half* h = sH1t + (16 * mi + g) * ld + k0 + 2 * t;
+        const uint32_t A[4] = {lds32(h), lds32(h + 8 * ld), lds32(h + 8), lds32(h + 8 * ld + 8)};
+        const __half* d = sD2t + (8 * ni + g) * ld + k0 + 2 * t;
+        mma16816(acc, A, lds32(d), lds32(d + 8));
+      }
+      const int i0 = 16 * mi + g, j0 = 8 * ni + 2 * t;
+      sg2[i0 * kHid + j0] = acc[0];
+      sg2[i0 * kHid + j0 + 1] = acc[1];
+      sg2[(i0 + 8) * kHid + j0] = acc[2];
+      sg2[(i0 + 8) * kHid + j0 + 1] = acc[3];
+      const int hh = warp >> 2;
+      float a1[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int k0 = hh * (B / 2); k0 < (hh + 1) * (B / 2); k0 += 16) {
+        const __half* h = sXt + g * ld + k0 + 2 * t;
+        const uint32_t A[4] = {lds32(h), lds32(h + 8 * ld), lds32(h + 8), lds32(h + 8 * ld + 8)};
+        const __half* d = sD1t + (8 * ni + g) * ld + k0 + 2 * t;
+        mma16816(a1, A, lds32(d), lds32(d + 8));
+      }
+      float* s1 = sg1 + hh * kFeat * kHid;
+      s1[g * kHid + j0] = a1[0];
+      s1[g * kHid + j0 + 1] = a1[1];
+      s1[(g + 8) * kHid + j0] = a1[2];
+      s1[(g + 8) * kHid + j0 + 1] = a1[3];
+    }
+    __syncthreads();
+    // ---- A: Adam (bias corrections of step t0 + step + 1)
+    const float bc1 = 1.f - powf(beta1, (float)(t0 + step + 1));
+    const float bc2 = 1.f - powf(beta2, (float)(t0 + step + 1));
+    for (int q = tid; q < kMlpParams; q += kTrainThreads) {
+      float gq = 0.f;
+      if (q < kOffB1) {
+        gq = sg1[q] + sg1[kFeat * kHid + q];
+      } else if (q >= kOffW2 && q < kOffB2) {
+        gq = sg2[q - kOffW2];
+      } else {
+        const int slot = q < kOffW2 ? q - kOffB1
+                         : q < kOffW3 ? 32 + q - kOffB2
+                         : q < kOffB3 ? 64 + q - kOffW3 : 96;
+        for (int w = 0; w < kTrainWarps; ++w) gq += sp[w * kPartStride + slot];
+      }
+      gq *= invB;
+      if (grad_out && step == steps - 1) grad_out[q] = gq;
+      const float m = beta1 * sm[q] + (1.f - beta1) * gq;
+      const float v = beta2 * sv[q] + (1.f - beta2) * gq * gq;
+      sm[q] = m;
+      sv[q] = v;
+      const float w = sw[q] - lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+      sw[q] = w;
+      if (q < kOffB1) sw1h[q] = __float2half_rn(w);
+      else if (q >= kOffW2 && q < kOffB2) sw2h[q - kOffW2] = __float2half_rn(w);
+    }
+    if (tid == 0 && loss_out) {
+      float l = 0.f;
+      for (int w = 0; w < kTrainWarps; ++w) l += sp[w * kPartStride + 97];
+      loss_out[step] = l * invB;
+    }
+    __syncthreads();
+  }
+  for (int q = tid; q < kMlpParams; q += kTrainThreads) {
+    params[q] = sw[q];
+    adam[q] = sm[q];
+    adam[kMlpParams + q] = sv[q];
   }
 }
 
@@ -310,10 +680,34 @@ cudaError_t launch_indicator(const Params<R>& p, const S* f0, const S* f1, const
   return cudaGetLastError();
 }
 
+template <class S, class R>
+cudaError_t launch_lattice_loss(const Params<R>& p, const S* a, const S* b, const uint8_t* flag,
+                                double* out, cudaStream_t st) {
+  const dim3 tg((p.nx + kTX - 1) / kTX, (p.ny + kTY - 1) / kTY);
+  k_lattice_loss<S, R><<<tg, dim3(kTX, kTY), 0, st>>>(p, a, b, flag, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_train(const float* x, const float* y, const int* idx, int steps, int batch,
+                             float lr, float beta1, float beta2, float eps, int t0, float* params,
+                             float* adam, float* loss, float* grad, cudaStream_t st) {
+  if (batch < 16 * kTrainWarps || batch > kMlpMaxBatch || batch % (16 * kTrainWarps))
+    return cudaErrorInvalidValue;
+  const size_t smem = train_smem_bytes(batch);
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)train_smem_bytes(kMlpMaxBatch));
+  if (e != cudaSuccess) return e;
+  k_mlp_train<<<1, kTrainThreads, smem, st>>>(x, y, idx, steps, batch, lr, beta1, beta2, eps, t0,
+                                              params, adam, loss, grad);
+  return cudaGetLastError();
+}
+
 #define SLBM_IND_INST(S, R)                                                                  \
   template cudaError_t launch_indicator<S, R>(const Params<R>&, const S*, const S*,          \
                                               const uint8_t*, R*, R*, R*, const IndicatorDev&, \
-                                              float, float*, float*, uint8_t*, cudaStream_t);
+                                              float, float*, float*, uint8_t*, cudaStream_t); \
+  template cudaError_t launch_lattice_loss<S, R>(const Params<R>&, const S*, const S*,       \
+                                                 const uint8_t*, double*, cudaStream_t);
 SLBM_IND_INST(float, float)
 SLBM_IND_INST(double, double)
 SLBM_IND_INST(__half, float)

@@ -122,12 +122,15 @@ __device__ __forceinline__ bool post_tile(const Params<R>& p, S* f0, S* f1,
     int gx = x0 + lx - B, gy = y0 + ly - B;
     uint8_t v = 2;
     bool ok = true;
+    // periodic images by a full modulo: on a grid narrower than the staged
+    // halo one wrap is not enough (those positions are read by no valid cell,
+    // but they must stay inside the flag array)
     if (gx < 0 || gx >= p.nx) {
-      if (p.periodic_x) gx = gx < 0 ? gx + p.nx : gx - p.nx;
+      if (p.periodic_x) gx = ((gx % p.nx) + p.nx) % p.nx;
       else ok = false;
     }
     if (gy < 0 || gy >= p.ny) {
-      if (p.periodic_y) gy = gy < 0 ? gy + p.ny : gy - p.ny;
+      if (p.periodic_y) gy = ((gy % p.ny) + p.ny) % p.ny;
       else ok = false;
     }
     if (ok) v = flag_new[gx + p.nx * gy];

@@ -35,7 +35,7 @@ EXPORTS = [
     "slbm_audit", "slbm_get_pops", "slbm_set_pops", "slbm_get_state", "slbm_set_state",
     "slbm_profile", "slbm_profile_read", "slbm_audit_dense_noalloc", "slbm_last_error",
     "slbm_set_pond", "slbm_get_frame", "slbm_set_frame",
-    "slbm_set_indicator", "slbm_indicator_eval",
+    "slbm_set_indicator", "slbm_indicator_eval", "slbm_lattice_loss", "slbm_mlp_train",
     "slbm_set_twopop", "slbm_get_gpops", "slbm_set_gpops", "slbm_set_rows",
     "slbm_set_viscosity_law", "slbm_tune", "slbm_set_kn_criterion", "slbm_set_channels",
 ]
@@ -117,6 +117,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.slbm_set_frame.argtypes = [p, p, p, p]
     L.slbm_set_indicator.argtypes = [p, p, p, p, p, p, ctypes.c_float, i]
     L.slbm_indicator_eval.argtypes = [p, p, p, p]
+    L.slbm_lattice_loss.argtypes = [p, p]
+    L.slbm_mlp_train.argtypes = [p, p, ctypes.c_longlong, p, i, i, p, i, p, p, p, p, p]
     L.slbm_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name != "slbm_last_error":
@@ -205,6 +207,39 @@ def slbm_indicator_eval(h, n, features=True, logits=False, flags=False):
     fl = np.zeros(n, np.uint8) if flags else None
     _check(load().slbm_indicator_eval(h, *(None if v is None else _ptr(v) for v in (fe, lo, fl))), h)
     return fe, lo, fl
+
+
+def slbm_lattice_loss(h, n):
+    out = np.zeros(n, np.float64)
+    _check(load().slbm_lattice_loss(h, _ptr(out)), h)
+    return out
+
+
+MLP_PARAMS = 16 * 32 + 32 + 32 * 32 + 32 + 32 + 1
+
+
+def slbm_mlp_train(x, y, idx, hyper, t0, params, adam, want_loss=True, want_grad=False,
+                   stream=0):
+    """GPU training steps (see include/slbm.h).  x (n, 16), y (n,), idx
+    (steps, batch) int; params (1633,) and adam (2, 1633) float32 arrays are
+    updated in place.  Returns (per-step losses, last gradient)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32).ravel()
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    if x.ndim != 2 or x.shape[1] != 16 or y.size != x.shape[0] or idx.ndim != 2:
+        raise ValueError("x (n, 16), y (n,), idx (steps, batch)")
+    if params.dtype != np.float32 or params.size != MLP_PARAMS or not params.flags.c_contiguous:
+        raise ValueError("params: contiguous float32, 1633 values")
+    if adam.dtype != np.float32 or adam.size != 2 * MLP_PARAMS or not adam.flags.c_contiguous:
+        raise ValueError("adam: contiguous float32, 2 x 1633 values")
+    steps, batch = idx.shape
+    hp = _f64(hyper, 4)
+    loss = np.zeros(steps, np.float32) if want_loss else None
+    grad = np.zeros(MLP_PARAMS, np.float32) if want_grad else None
+    _check(load().slbm_mlp_train(_ptr(x), _ptr(y), x.shape[0], _ptr(idx), steps, batch, _ptr(hp),
+                                 int(t0), _ptr(params), _ptr(adam), _ptr(loss), _ptr(grad),
+                                 ctypes.c_void_p(stream)))
+    return loss, grad
 
 
 def slbm_set_pond(h, tol, max_iter):
@@ -466,6 +501,11 @@ class Solver:
         """weights: dict w1 (16x32), b1 (32), w2 (32x32), b2 (32), w3 (32), b3."""
         slbm_set_indicator(self.h, weights["w1"], weights["b1"], weights["w2"], weights["b2"],
                            weights["w3"], weights["b3"], interval)
+
+    def lattice_loss(self):
+        """(ny, nx) per-cell lattice loss of one step; the state advances one
+        high-order step (see include/slbm.h)."""
+        return slbm_lattice_loss(self.h, self.n).reshape(self.ny, self.nx)
 
     def indicator_eval(self, features=True, logits=False, flags=False):
         """(features (ny, nx, 16), logits (ny, nx), flags (ny, nx)); unrequested are None."""

@@ -6,7 +6,8 @@ Eight heterogeneous channels: widths 5 .. 33 cells between the walls,
 relaxation times 0.52 .. 3, wall speeds of either sign, D2Q9 or D2Q25
 channels and one channel with D2Q25 next to its walls and D2Q9 in its middle
 (interfaces inside the channel), smooth non-uniform initial fields.  Each
-oracle run is the channel alone: width x 8 cells, periodic along y,
+oracle run is the channel alone: width x NY cells, periodic along y (NY 8,
+and 4 as in the batched Couette workload, a period shorter than 2 G + 1),
 diffuse-reflection walls on its two x sides moving along y.  FP64: every
 channel's rho, u within 1e-11 relative L2 of its oracle after 20 steps (only
 rounding order differs); FP32 within 1e-5.  The gap columns report flag 2 and
@@ -20,7 +21,7 @@ from paper_2102_12559_gb300 import slbm, workloads as WL
 
 pytestmark = pytest.mark.gpu
 
-NY = 8
+NYS = (8, 4)
 WIDTHS = [12, 17, 5, 24, 9, 33, 20, 15]
 TAUS = [0.6, 1.3, 0.75, 0.52, 3.0, 0.9, 0.55, 2.0]
 UW = [(-0.1, 0.1), (0.05, -0.05), (0.0, 0.08), (-0.03, 0.1), (0.1, 0.1), (-0.1, 0.02),
@@ -32,7 +33,7 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
 
 
-def _channel_flags(w, lat):
+def _channel_flags(w, lat, NY):
     if lat == "walls":
         f = np.zeros((NY, w), np.uint8)
         f[:, :4] = 1
@@ -41,7 +42,7 @@ def _channel_flags(w, lat):
     return np.full((NY, w), lat, np.uint8)
 
 
-def _setup():
+def _setup(NY):
     G = 2
     x0, nx = WL.channel_layout(WIDTHS, G)
     rho = np.ones((NY, nx))
@@ -53,15 +54,16 @@ def _setup():
         r, u, v = WL.perturbed(w, NY, seed=30 + c, amp_rho=0.02, amp_u=0.05)
         sl = slice(x0[c], x0[c] + w)
         rho[:, sl], ux[:, sl], uy[:, sl] = r, u, v
-        fl = _channel_flags(w, lat)
+        fl = _channel_flags(w, lat, NY)
         flags[:, sl] = fl
         subs.append((r, u, v, fl))
     return x0, nx, (rho, ux, uy), flags, subs
 
 
-@pytest.fixture(scope="module")
-def oracle_runs():
-    x0, nx, fields, flags, subs = _setup()
+@pytest.fixture(scope="module", params=NYS)
+def oracle_runs(request):
+    NY = request.param
+    x0, nx, fields, flags, subs = _setup(NY)
     out = []
     for c, (w, (r, u, v, fl)) in enumerate(zip(WIDTHS, subs)):
         o = O.Oracle(w, NY, 3, 5, tau=TAUS[c], order=3, periodic=(False, True))
@@ -71,12 +73,13 @@ def oracle_runs():
         o.set_flags(fl)
         o.step(20)
         out.append(o.moments())
-    return out
+    return NY, out
 
 
 @pytest.mark.parametrize("precision,tol", [(slbm.SLBM_FP64, 1e-11), (slbm.SLBM_FP32, 1e-5)])
 def test_channels_match_single_channel_oracle(oracle_runs, precision, tol):
-    x0, nx, fields, flags, subs = _setup()
+    NY, oracle_runs = oracle_runs
+    x0, nx, fields, flags, subs = _setup(NY)
     g = slbm.Solver(nx, NY, 3, 5, tau=0.6, interp_order=3, periodic=(False, True),
                     precision=precision)
     g.init_equilibrium(*fields)
@@ -99,7 +102,7 @@ def test_channels_match_single_channel_oracle(oracle_runs, precision, tol):
 
 
 def test_channels_argument_checks():
-    G = 2
+    G, NY = 2, 8
     x0, nx = WL.channel_layout([8, 8], G)
     g = slbm.Solver(nx, NY, 3, 5, tau=0.6, periodic=(False, True))
     with pytest.raises(slbm.SlbmError):   # channels overlapping their neighbour's wall columns

@@ -298,3 +298,19 @@ def test_full_size_jet_one_step_sampled_fp32():
     speed = np.sqrt(u ** 2 + v ** 2).ravel()
     clear = np.abs(speed - 0.3) > 1e-5
     np.testing.assert_array_equal(new[clear], (speed > 0.3)[clear].astype(np.uint8))
+
+
+@pytest.mark.parametrize("nx,ny", [(10, 4), (3, 12), (40, 2)])
+def test_narrow_periodic_grids_fp64(nx, ny):
+    """Periodic grids narrower than a tile and its band halo (down to the
+    stencil reach G = 2 cells), with random interfaces: 20 steps at 1e-11."""
+    g, o = pair(nx, ny)
+    fields = WL.perturbed(nx, ny, seed=17, amp_rho=0.03, amp_u=0.3)
+    fl = (np.random.default_rng(nx * 100 + ny).uniform(size=(ny, nx)) < 0.4).astype(np.uint8)
+    both(g, o, "init_equilibrium", *fields)
+    both(g, o, "set_flags", fl)
+    both(g, o, "step", 20)
+    mg, mo = g.moments(), o.moments()
+    for q in range(3):
+        assert rel_l2(mg[q], mo[q]) < 1e-11, q
+    np.testing.assert_array_equal(g.get_flags(), o.get_flags())
