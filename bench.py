@@ -358,6 +358,7 @@ def mom_gap(a, b) -> dict:
 
 
 KN_HI = 0.1  # plain rule of the Couette batch: channels above it run D2Q25
+WALL_BAND = 8  # cells of D2Q25 next to each wall in the fixed wall-layer arm
 COUETTE_NY = 4  # streamwise period of the Couette channels, cells
 
 
@@ -365,8 +366,10 @@ def couette_solver(slbm, WL, batch, mode, weights=None, stream=None):
     """The batched Couette channels in one handle: side by side along x
     (wall-normal), streamwise y periodic with COUETTE_NY cells, 2 G gap
     columns, each channel its own tau.  mode: "plain" (D2Q25 in the channels
-    with Kn > KN_HI, fixed), "all" (D2Q25 everywhere, fixed) or "mlp" (the
-    learned indicator sets the flags every 10 steps, from D2Q9 at rest)."""
+    with Kn > KN_HI, fixed), "walls" (D2Q25 within WALL_BAND cells of every
+    wall, D2Q9 inside, the paper's layout), "all" (D2Q25 everywhere) or "mlp" (the
+    learned indicator refines the flags every 10 steps, from D2Q9 at rest:
+    SLBM_CRIT_MLP_REFINE, a cell once high-order stays so)."""
     G, ny = 2, COUETTE_NY
     widths = [ch["H"] for ch in batch]
     x0, nx = WL.channel_layout(widths, G)
@@ -383,10 +386,13 @@ def couette_solver(slbm, WL, batch, mode, weights=None, stream=None):
     for c, ch in enumerate(batch):
         if mode == "all" or (mode == "plain" and ch["kn"] > KN_HI):
             fl[:, x0[c]:x0[c] + widths[c]] = 1
+        if mode == "walls":
+            fl[:, x0[c]:x0[c] + WALL_BAND] = 1
+            fl[:, x0[c] + widths[c] - WALL_BAND:x0[c] + widths[c]] = 1
     g.set_flags(fl)
-    if mode == "mlp":
+    if mode == "mlp":  # refinement only: at tau up to ~170 cells must not switch back
         g.set_indicator(weights, interval=10)
-        g.set_criterion(slbm.SLBM_CRIT_MLP, 0.0)
+        g.set_criterion(slbm.SLBM_CRIT_MLP_REFINE, 0.0)
     return g, x0, widths
 
 
@@ -862,7 +868,7 @@ def run_study(args):
         batch = WL.couette_batch(count=128, seed=3)
         weights, ind_train = train_indicator(slbm, WL, stream)
         arms, states = {}, {}
-        for mode in ("plain", "mlp", "all"):
+        for mode in ("plain", "walls", "mlp", "all"):
             g, x0, widths = couette_solver(slbm, WL, batch, mode, weights, stream=stream)
             ny, nx = COUETTE_NY, g.nx
             g.step(args.warmup)
@@ -902,11 +908,19 @@ def run_study(args):
         plain_fl = plain_couette_flags(batch, x0, widths, (COUETTE_NY, nx))
         ind_fl = states["mlp"][1]
         lab, ind_all = states["all"][2]["lab"], states["all"][2]["ind"]
-        for mode in ("plain", "mlp"):
+        u_all = np.stack(ref[1:3])
+        for mode in ("plain", "walls", "mlp"):
             u = np.stack(states[mode][0][1:3])[:, inside]
             arms[mode]["rel_l2_u_vs_all_d2q25"] = float(np.linalg.norm(u - u_ref) /
                                                         np.linalg.norm(u_ref))
             arms[mode]["high_order_fraction"] = float((states[mode][1][inside] == 1).mean())
+            ua = np.stack(states[mode][0][1:3])
+            per = {}
+            for lo, hi in ((0.01, 0.03), (0.03, 0.1), (0.1, 0.3), (0.3, 1.0)):
+                sel = inside & (kn > lo) & (kn <= hi)
+                per[f"Kn {lo}-{hi}"] = float(np.linalg.norm(ua[:, sel] - u_all[:, sel]) /
+                                             np.linalg.norm(u_all[:, sel]))
+            arms[mode]["rel_l2_u_by_knudsen_band"] = per
         d_ip, d_il, d_pl = decision_gaps(ind_fl, plain_fl, lab, inside)
         bands = {}
         for lo, hi in ((0.01, 0.03), (0.03, 0.1), (0.1, 0.3), (0.3, 1.0)):
@@ -925,8 +939,10 @@ def run_study(args):
             "timing": "CUDA events on the handle's stream",
             "arms": arms,
             "arm_forms": {"plain": f"D2Q25 in the channels with Kn > {KN_HI} (fixed)",
-                          "mlp": "learned indicator every 10 steps (SLBM_CRIT_MLP), from D2Q9 "
-                                 "at rest",
+                          "walls": f"D2Q25 within {WALL_BAND} cells of every wall, D2Q9 "
+                                   "inside (fixed, the paper's Sec. IV.C layout)",
+                          "mlp": "learned indicator every 10 steps, refinement only "
+                                 "(SLBM_CRIT_MLP_REFINE), from D2Q9 at rest",
                           "all": "D2Q25 everywhere (the accuracy reference)"},
             "indicator_decisions_at_end": {
                 "indicator_vs_plain_rule": d_ip, "indicator_vs_lattice_loss_label": d_il,

@@ -125,6 +125,15 @@ typedef struct slbm_s *slbm_t;
 #define SLBM_CRIT_MACH 1     /* after every step: flag = (|u| / c_s > threshold), c_s = 1 */
 #define SLBM_CRIT_MLP  2     /* every `interval` steps: flag = (indicator logit > threshold),
                                 the learned indicator of slbm_set_indicator */
+#define SLBM_CRIT_MLP_REFINE 3  /* as SLBM_CRIT_MLP, refinement only, with a buffer: flag =
+                                old flag OR (a cell within `interval` cells along x or y --
+                                the distance a disturbance travels between evaluations at
+                                CFL = 1 -- has logit > threshold); the buffer stops at bounded
+                                sides and channel gaps.  A cell changes lattice at most once:
+                                at large tau (weak collisions, high Knudsen number) cells
+                                switched back and forth between the lattices every few steps
+                                make the hybrid scheme diverge, while an interface that only
+                                moves one way is stable */
 
 typedef struct {
     int nx, ny;              /* cells (minimum: see slbm_create) */
@@ -193,8 +202,9 @@ SLBM_API int slbm_get_flags(slbm_t h, uint8_t *flags);
 /* Refinement criterion (SLBM_CRIT_*).  SLBM_CRIT_MACH: threshold on the Mach
  * number |u| / c_s, c_s = sqrt(T_L) = 1, applied at once to the current state
  * (flips lifted / projected, asynchronous) and after every step.
- * SLBM_CRIT_MLP: threshold on the learned indicator's logit (0 = probability
- * 1/2), applied at once and every `interval` steps; needs slbm_set_indicator.
+ * SLBM_CRIT_MLP / SLBM_CRIT_MLP_REFINE: threshold on the learned indicator's
+ * logit (0 = probability 1/2), applied at once and every `interval` steps;
+ * needs slbm_set_indicator.
  * Lattice frame only (SLBM_EINVAL otherwise). */
 SLBM_API int slbm_set_criterion(slbm_t h, int kind, double threshold);
 

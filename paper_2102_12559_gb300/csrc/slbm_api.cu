@@ -318,12 +318,12 @@ struct slbm_s {
   int nchan, nwall;
   std::vector<uint8_t> gapcol;
   char* chanbuf;
-  size_t cb_wallu, cb_omega, cb_ghidx, cb_wallcol;
+  size_t cb_wallu, cb_omega, cb_ghidx;
   // learned indicator: weights on the device (owned), evaluation interval
   void* ind_buf;
   IndicatorDev ind;
   int ind_interval;
-  double ind_thr;                // logit threshold of SLBM_CRIT_MLP
+  double ind_thr;                // logit threshold of SLBM_CRIT_MLP(_REFINE)
   int bc_kind[4];
   long long steps;
   long long sc_launches;         // stream-collide launches (scheduler counter parity)
@@ -392,6 +392,18 @@ struct DeviceScope {
   if ((h)->failed) return SLBM_ECUDA;                                   \
   DeviceScope slbm_device_scope_((h)->dev)
 
+bool is_mlp(int kind) { return kind == SLBM_CRIT_MLP || kind == SLBM_CRIT_MLP_REFINE; }
+
+// The stream kernel reads a periodic y axis's rows through their images
+// (Params::wrap_y) on thin grids and with channels (whose walls cover rows
+// 0 .. ny-1 only); the post-step kernel then refreshes no y ghost row.
+int wraps_y(const slbm_s* h) {
+  return h->frame == SLBM_FRAME_LATTICE && h->g.periodic_y &&
+                 (h->g.ny < kWrapRowsMax || h->nchan > 0)
+             ? 1
+             : 0;
+}
+
 BcDev bc_dev(slbm_s* h) {
   BcDev b{};
   for (int s = 0; s < 4; ++s) {
@@ -404,7 +416,6 @@ BcDev bc_dev(slbm_s* h) {
     b.nwall = h->nwall;
     b.wall = reinterpret_cast<const int4*>(h->chanbuf);
     b.wall_u = reinterpret_cast<const double*>(h->chanbuf + h->cb_wallu);
-    b.wallcol = reinterpret_cast<const uint8_t*>(h->chanbuf + h->cb_wallcol);
   }
   return b;
 }
@@ -433,7 +444,7 @@ int build_ghost_tables(slbm_s* h) {
   const int nt = ntiles_of(h);
   int* d_idx = ghost_idx(h);
   SLBM_CK(h, launch_ghost_src(G, nx, ny, h->g.periodic_x ? 1 : 0, h->g.periodic_y ? 1 : 0,
-                              bc_dev(h), d_idx, h->st),
+                              wraps_y(h), bc_dev(h), d_idx, h->st),
           "ghost source launch");
   std::vector<int> src(ring), start(nt + 1, 0), idx, tiles;
   if (ring)
@@ -715,6 +726,7 @@ void fill_params(Params<R>& p, const slbm_s* h, const Lattice1D& a, const Lattic
   p.plane = h->lay.plane;
   p.periodic_x = h->g.periodic_x ? 1 : 0;
   p.periodic_y = h->g.periodic_y ? 1 : 0;
+  p.wrap_y = wraps_y(h);
   p.crit = h->crit;
   p.thr = (R)h->thr;
   p.omega = (R)(1.0 / h->tau);
@@ -990,7 +1002,22 @@ int run_indicator(slbm_s* h, float* feat, float* logit, uint8_t* flags_out) {
 int apply_indicator(slbm_s* h) {
   uint8_t* fold = h->flags(h->fcur);
   uint8_t* fnew = h->flags(h->fcur ^ 1);
-  if (int rc = run_indicator(h, nullptr, nullptr, fnew)) return rc;
+  if (h->crit == SLBM_CRIT_MLP_REFINE) {
+    // the indicator's decisions, widened by the refinement buffer (the cells
+    // a disturbance reaches before the next evaluation: one per step at
+    // CFL = 1), OR-ed with the current flags
+    uint8_t* tmp = h->at<uint8_t>(h->lay.flag_tmp);
+    const int r = h->ind_interval;
+    if (int rc = run_indicator(h, nullptr, nullptr, fnew)) return rc;
+    SLBM_CK(h, launch_dilate(fnew, nullptr, tmp, h->g.nx, h->g.ny, h->g.periodic_x ? 1 : 0, r, 0,
+                             h->st),
+            "refinement buffer launch");
+    SLBM_CK(h, launch_dilate(tmp, fold, fnew, h->g.nx, h->g.ny, h->g.periodic_y ? 1 : 0, r, 1,
+                             h->st),
+            "refinement buffer launch");
+  } else if (int rc = run_indicator(h, nullptr, nullptr, fnew)) {
+    return rc;
+  }
   const size_t nt = (size_t)ntiles_of(h);
   const int half = (int)((h->sc_launches & 1) ^ 1);
   int* work = h->at<int>(h->lay.post_work);
@@ -1232,10 +1259,10 @@ int slbm_get_flags(slbm_t h, uint8_t* flags) {
 
 int slbm_set_criterion(slbm_t h, int kind, double threshold) {
   SLBM_GUARD(h);
-  if ((kind != SLBM_CRIT_NONE && kind != SLBM_CRIT_MACH && kind != SLBM_CRIT_MLP) ||
+  if ((kind != SLBM_CRIT_NONE && kind != SLBM_CRIT_MACH && !is_mlp(kind)) ||
       !std::isfinite(threshold) || (kind == SLBM_CRIT_MACH && !(threshold >= 0.0)))
     return fail(h, SLBM_EINVAL, "criterion kind or threshold invalid");
-  if (kind == SLBM_CRIT_MLP && !h->ind_buf)
+  if (is_mlp(kind) && !h->ind_buf)
     return fail(h, SLBM_EINVAL, "no indicator weights (slbm_set_indicator); use SLBM_CRIT_MACH");
   if (kind == SLBM_CRIT_MACH && h->nchan)
     return fail(h, SLBM_EINVAL, "channels keep fixed flags or the learned indicator");
@@ -1243,7 +1270,7 @@ int slbm_set_criterion(slbm_t h, int kind, double threshold) {
     return fail(h, SLBM_EINVAL, "the Mach criterion belongs to the lattice frame");
   // flags live in buffer fcur either way; the other buffer is scratch
   h->crit = kind;
-  if (kind != SLBM_CRIT_MLP) h->thr = threshold;
+  if (!is_mlp(kind)) h->thr = threshold;
   refresh_params(h);
   if (kind == SLBM_CRIT_MACH) {
     // evaluate the criterion on the current state at once; flips are converted
@@ -1259,7 +1286,7 @@ int slbm_set_criterion(slbm_t h, int kind, double threshold) {
             "flag copy");
     SLBM_CK(h, ghosts(h, h->flags(h->fcur)), "ghost launch");
   }
-  if (kind == SLBM_CRIT_MLP) {
+  if (is_mlp(kind)) {
     h->ind_thr = threshold;
     return apply_indicator(h);
   }
@@ -1531,7 +1558,7 @@ int slbm_step(slbm_t h, int n) {
   while (s < n) {
     // steps up to the next learned-indicator evaluation
     int chunk = n - s;
-    if (h->crit == SLBM_CRIT_MLP) {
+    if (is_mlp(h->crit)) {
       const int to_eval = h->ind_interval - (int)(h->steps % h->ind_interval);
       if (to_eval < chunk) chunk = to_eval;
     }
@@ -1558,7 +1585,7 @@ int slbm_step(slbm_t h, int n) {
       if (rc) return rc;
     }
     s += chunk;
-    if (h->crit == SLBM_CRIT_MLP && h->steps % h->ind_interval == 0) {
+    if (is_mlp(h->crit) && h->steps % h->ind_interval == 0) {
       const int rc = apply_indicator(h);
       if (rc) return rc;
     }
@@ -1774,7 +1801,7 @@ int slbm_set_channels(slbm_t h, int n, const int* x0, const int* width, const do
   }
   // host tables: gap columns, per-column omega, internal wall ghosts (G
   // columns beside each channel side, every row) and their velocities
-  std::vector<uint8_t> gap(nx, 1), wcol(nx, 0);
+  std::vector<uint8_t> gap(nx, 1);
   std::vector<double> om(nx, 1.0 / h->tau);
   std::vector<int> wall;
   std::vector<double> wu;
@@ -1783,15 +1810,12 @@ int slbm_set_channels(slbm_t h, int n, const int* x0, const int* width, const do
       gap[x] = 0;
       om[x] = 1.0 / tau[c];
     }
-    // every row of the wall ghost columns, the y ghost rows included (their
-    // source row wraps), so a channel's corner cells read current wall states
-    for (int y = -G; y < ny + G; ++y)
+    for (int y = 0; y < ny; ++y)
       for (int k = 0; k < G; ++k) {
         wall.insert(wall.end(), {x0[c] - G + k, y, x0[c], SLBM_SIDE_XMIN});
         wu.insert(wu.end(), {0.0, uw_lo[c]});
         wall.insert(wall.end(), {x0[c] + width[c] + k, y, x0[c] + width[c] - 1, SLBM_SIDE_XMAX});
         wu.insert(wu.end(), {0.0, uw_hi[c]});
-        wcol[x0[c] - G + k] = wcol[x0[c] + width[c] + k] = 1;
       }
   }
   const int nwall = (int)(wall.size() / 4);
@@ -1800,8 +1824,7 @@ int slbm_set_channels(slbm_t h, int n, const int* x0, const int* width, const do
   h->cb_wallu = align_up(wall.size() * sizeof(int), 256);
   h->cb_omega = h->cb_wallu + align_up(wu.size() * sizeof(double), 256);
   h->cb_ghidx = h->cb_omega + align_up(nx * es, 256);
-  h->cb_wallcol = h->cb_ghidx + align_up((ring + nwall) * sizeof(int), 256);
-  const size_t bytes = h->cb_wallcol + nx;
+  const size_t bytes = h->cb_ghidx + (ring + nwall) * sizeof(int);
   void* buf = nullptr;
   SLBM_CK(h, cudaMalloc(&buf, bytes), "channel arrays allocation");
   h->chanbuf = (char*)buf;
@@ -1810,8 +1833,7 @@ int slbm_set_channels(slbm_t h, int n, const int* x0, const int* width, const do
   if ((rc = upload(h, h->chanbuf, wall.data(), wall.size() * sizeof(int))) ||
       (rc = upload(h, h->chanbuf + h->cb_wallu, wu.data(), wu.size() * sizeof(double))) ||
       (rc = upload(h, h->chanbuf + h->cb_omega,
-                   es == 8 ? (const void*)om.data() : (const void*)omf.data(), nx * es)) ||
-      (rc = upload(h, h->chanbuf + h->cb_wallcol, wcol.data(), nx)))
+                   es == 8 ? (const void*)om.data() : (const void*)omf.data(), nx * es)))
     return rc;
   h->gapcol = gap;
   h->nchan = n;

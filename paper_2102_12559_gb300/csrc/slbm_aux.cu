@@ -65,7 +65,6 @@ __global__ void k_ghosts(const Params<R> p, S* f0, S* f1, const uint8_t* __restr
   int gx, gy, sx, sy, side = 0, bidx = 0;
   const int kind = ghost_cell(G, p.nx, p.ny, p.periodic_x, p.periodic_y, bc, idx, gx, gy, sx, sy,
                               side, bidx);
-  if (kind == 4) return;  // written by its wall entry
   const int gbase = (gy + G) * p.pitch + (gx + kOX);
   const int sbase = (sy + G) * p.pitch + (sx + kOX);
   if (kind == 1 || kind == 2) {
@@ -317,23 +316,27 @@ k_tile_work(int nx, int ny, int periodic_x, int periodic_y, const uint8_t* __res
   }
 }
 
-// Source tile of every ghost ring cell (set-up of the post-step kernel's
-// per-tile ghost lists): the same ghost rule as every ghost writer.
-__global__ void k_ghost_src(int G, int nx, int ny, int periodic_x, int periodic_y, const BcDev bc,
-                            int* __restrict__ out, int ring) {
+// Source tile of every ghost cell (set-up of the post-step kernel's per-tile
+// ghost lists): the same ghost rule as every ghost writer.  -1 (in no list):
+// DIRICHLET ghosts (constant) and, with skip_y, the y ghost rows, which the
+// stream kernel then never reads (it wraps those rows).
+__global__ void k_ghost_src(int G, int nx, int ny, int periodic_x, int periodic_y, int skip_y,
+                            const BcDev bc, int* __restrict__ out, int ring) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= ring) return;
   int gx, gy, sx, sy, side = 0, idx = 0;
   const int kind = ghost_cell(G, nx, ny, periodic_x, periodic_y, bc, g, gx, gy, sx, sy, side, idx);
   const int ntx = (nx + kTX - 1) / kTX;
-  out[g] = (kind == 2 || kind == 4) ? -1 : (sy / kTY) * ntx + sx / kTX;
+  const bool dead = skip_y && (gy < 0 || gy >= ny);
+  out[g] = (kind == 2 || dead) ? -1 : (sy / kTY) * ntx + sx / kTX;
 }
 
-cudaError_t launch_ghost_src(int G, int nx, int ny, int periodic_x, int periodic_y,
+cudaError_t launch_ghost_src(int G, int nx, int ny, int periodic_x, int periodic_y, int skip_y,
                              const BcDev& bc, int* out, cudaStream_t st) {
   const int ring = 2 * G * (nx + 2 * G) + 2 * G * ny + bc.nwall;
   if (ring == 0) return cudaSuccess;
-  k_ghost_src<<<(ring + 127) / 128, 128, 0, st>>>(G, nx, ny, periodic_x, periodic_y, bc, out, ring);
+  k_ghost_src<<<(ring + 127) / 128, 128, 0, st>>>(G, nx, ny, periodic_x, periodic_y, skip_y, bc,
+                                                  out, ring);
   return cudaGetLastError();
 }
 

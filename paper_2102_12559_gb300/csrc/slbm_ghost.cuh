@@ -71,9 +71,7 @@ __device__ __forceinline__ int ghost_source(int nx, int ny, int px, int py, cons
 
 // Ghost cell g: a ring cell (g < ring, ghost_coords / ghost_source) or an
 // internal wall ghost (g = ring + e, BcDev::wall[e]: always a DIFFUSE wall,
-// idx = -e - 1 selects its velocity in ghost_ux / ghost_uy).  Kind 4: a ring
-// cell in a y ghost row of a wall ghost column, written by its wall entry, so
-// no ring writer touches it.
+// idx = -e - 1 selects its velocity in ghost_ux / ghost_uy).
 __device__ __forceinline__ int ghost_cell(int G, int nx, int ny, int px, int py, const BcDev& bc,
                                           int g, int& gx, int& gy, int& sx, int& sy, int& side,
                                           int& idx) {
@@ -83,17 +81,12 @@ __device__ __forceinline__ int ghost_cell(int G, int nx, int ny, int px, int py,
     gx = w.x;
     gy = w.y;
     sx = w.z;
-    sy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+    sy = w.y;
     side = w.w;
     idx = -(g - ring) - 1;
     return 3;
   }
   ghost_coords(G, nx, ny, g, gx, gy);
-  if (bc.wallcol && (gy < 0 || gy >= ny) && gx >= 0 && gx < nx && bc.wallcol[gx]) {
-    sx = gx;
-    sy = 0;
-    return 4;
-  }
   return ghost_source(nx, ny, px, py, bc, gx, gy, sx, sy, side, idx);
 }
 

@@ -6,8 +6,12 @@
 // plane of lattice k in buffer b holds (ny + 2G) rows of `pitch` elements;
 // cell (x, y), x in [-G, nx+G), y in [-G, ny+G), sits at element
 // (y + G) * pitch + (x + kOX).  The G-wide ring of ghost cells is refreshed
-// after every step (periodic images or boundary states), so the streaming
-// kernel never wraps an index.
+// after every step (periodic images or boundary states) and read by the
+// streaming kernel in place of wrapped indices -- except, on a periodic y
+// axis of fewer than kWrapRowsMax rows or with channels (Params::wrap_y),
+// the y ghost rows: there the streaming kernel reads the rows' images in the
+// grid near its edges, so thin periodic grids (a few rows, where the ghost
+// rows hold as many cells as the grid) rewrite no ghost row per step.
 //
 // Stored values are deviations s_i = f_i - W_i from the rest equilibrium
 // (rho = 1, u = 0, whose lattice populations are the weights W_i).  The
@@ -87,7 +91,11 @@ struct Params {
   int* wcount;                  // 2 counters: entries of each half of wlist
   double cv;                    // C_v of the two-population co-moving model, else 1
   const R* omega_x;             // per-column omega (channels), else null: omega everywhere
+  int wrap_y;                   // 1: periodic y rows are read through their images (no
+                                // y ghost rows; see the layout note above)
 };
+
+constexpr int kWrapRowsMax = 256;  // periodic y axes shorter than this wrap (wrap_y)
 
 // Flag value of a cell that belongs to no lattice: the gap columns between
 // channels (slbm_set_channels), which hold their walls' ghost cells.
@@ -169,10 +177,9 @@ constexpr int kErrFrame = 4;    // non-positive / non-finite frame, or departure
 // Boundary description (device arrays of the prescribed states, may be null).
 // Internal walls (channels, slbm_set_channels): nwall extra ghost cells
 // beyond the ring, ghost index ring + e for e < nwall, each a diffuse wall
-// against an interior source cell: wall[e] = {gx, gy, sx, side}, the source
-// row being gy wrapped into the (periodic) grid, with wall velocity
-// (wall_u[2e], wall_u[2e + 1]).  The walls' ghost columns (wallcol[x] = 1)
-// cover the y ghost rows too, so the ring leaves those cells to them.
+// against an interior source cell in its row: wall[e] = {gx, gy, sx, side},
+// with wall velocity (wall_u[2e], wall_u[2e + 1]).  Rows 0 .. ny-1 only: y
+// is periodic and a channel handle always wraps it (wrap_y).
 struct BcDev {
   int kind[4];                  // per side SLBM_BC_*
   const double* rho[4];
@@ -181,7 +188,6 @@ struct BcDev {
   int nwall;
   const int4* wall;
   const double* wall_u;
-  const uint8_t* wallcol;
 };
 
 // Co-moving frame launchers (slbm_pond.cu).  lam: three frame planes.
@@ -240,6 +246,10 @@ cudaError_t launch_indicator(const Params<R>& p, const S* f0, const S* f1, const
                              float* feat_out, float* logit_out, uint8_t* flag_out,
                              cudaStream_t st);
 
+// Refinement buffer along one axis (0 = x, 1 = y) of radius r: see k_dilate.
+cudaError_t launch_dilate(const uint8_t* in, const uint8_t* keep, uint8_t* out, int nx, int ny,
+                          int periodic, int r, int axis, cudaStream_t st);
+
 // Per-cell lattice loss || a - b ||_2 / rho_a over the high-order planes of
 // two population buffers a, b (same layout as the handle's planes of lattice
 // 1); gap cells get 0.  out: nc doubles.
@@ -269,6 +279,13 @@ cudaError_t launch_stream_collide(const Params<R>& p, int P, const S* fin0, cons
                                   S* fout0, S* fout1, const uint8_t* flag_cur,
                                   uint8_t* flag_nxt, const uint8_t* tile_mask,
                                   uint8_t* mask_next, cudaStream_t st);
+// The same with rows read through their periodic images near the y edges
+// (Params::wrap_y; its own translation units, called by launch_stream_collide).
+template <class S, class R>
+cudaError_t launch_stream_collide_wrap(const Params<R>& p, int P, const S* fin0, const S* fin1,
+                                       S* fout0, S* fout1, const uint8_t* flag_cur,
+                                       uint8_t* flag_nxt, const uint8_t* tile_mask,
+                                       uint8_t* mask_next, cudaStream_t st);
 
 // Post-step: interface conversion for band / flipped cells (flag_old = the
 // lattice each cell was computed in, flag_new = next step's flags) and, if
@@ -310,9 +327,9 @@ struct GhostTables {
 };
 
 // Source tile of every ghost ring cell under the ghost rule (-1: a constant
-// DIRICHLET ghost), ntx tiles per row: out[0 .. ring) with
+// DIRICHLET ghost, or with skip_y a y ghost row), ntx tiles per row: out[0 .. ring) with
 // ring = 2 G (nx + 2 G) + 2 G ny.  The host sorts these into GhostTables.
-cudaError_t launch_ghost_src(int G, int nx, int ny, int periodic_x, int periodic_y,
+cudaError_t launch_ghost_src(int G, int nx, int ny, int periodic_x, int periodic_y, int skip_y,
                              const BcDev& bc, int* out, cudaStream_t st);
 
 // Per-step post-step kernel: interface conversion of the candidate tiles in

@@ -310,6 +310,39 @@ k_indicator(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restri
   }
 }
 
+// Refinement buffer of SLBM_CRIT_MLP_REFINE, one axis per launch (0 = x,
+// 1 = y): out = 1 where `in` is 1 within r cells along the axis, the scan
+// stopping at a gap cell or a bounded side (periodic axes wrap); also where
+// keep = 1 (if given); gap cells stay gaps.
+__global__ void k_dilate(const uint8_t* __restrict__ in, const uint8_t* __restrict__ keep,
+                         uint8_t* __restrict__ out, int nx, int ny, int periodic, int r,
+                         int axis) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= (long long)nx * ny) return;
+  const int x = (int)(c % nx), y = (int)(c / nx);
+  if (in[c] == kFlagGap) {
+    out[c] = kFlagGap;
+    return;
+  }
+  int v = in[c] == 1 || (keep && keep[c] == 1);
+  const int n = axis ? ny : nx, i0 = axis ? y : x;
+  for (int dir = -1; dir <= 1 && !v; dir += 2)
+    for (int d = 1; d <= r; ++d) {
+      int i = i0 + dir * d;
+      if (i < 0 || i >= n) {
+        if (!periodic) break;
+        i = ((i % n) + n) % n;
+      }
+      const uint8_t f = in[axis ? x + (long long)nx * i : i + (long long)nx * y];
+      if (f == kFlagGap) break;
+      if (f == 1) {
+        v = 1;
+        break;
+      }
+    }
+  out[c] = (uint8_t)v;
+}
+
 // Per-cell lattice loss between two buffers of the high-order planes (the
 // stored values are deviations f - W, so the weights cancel in a - b and
 // rho_a = 1 + sum a); FP64 sums.
@@ -685,6 +718,13 @@ cudaError_t launch_lattice_loss(const Params<R>& p, const S* a, const S* b, cons
                                 double* out, cudaStream_t st) {
   const dim3 tg((p.nx + kTX - 1) / kTX, (p.ny + kTY - 1) / kTY);
   k_lattice_loss<S, R><<<tg, dim3(kTX, kTY), 0, st>>>(p, a, b, flag, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dilate(const uint8_t* in, const uint8_t* keep, uint8_t* out, int nx, int ny,
+                          int periodic, int r, int axis, cudaStream_t st) {
+  const long long nc = (long long)nx * ny;
+  k_dilate<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(in, keep, out, nx, ny, periodic, r, axis);
   return cudaGetLastError();
 }
 

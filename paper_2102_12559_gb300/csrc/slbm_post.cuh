@@ -316,7 +316,7 @@ __device__ __forceinline__ void tile_ghosts(const Params<R>& p, S* f0, S* f1,
         if (e >= m * Q) continue;
         const int plane = e / m, j = e - plane * m;
         const int kind = s_kind[j];
-        if (kind == 2 || kind == 4) continue;
+        if (kind == 2) continue;
         const int k = plane < q0 ? 0 : 1;
         const int i = k ? plane - q0 : plane;
         S* f = k ? f1 : f0;

@@ -149,29 +149,48 @@ __device__ __forceinline__ const S* plane_row(const S* col, int plane, int pitch
   return col + (i * plane + r * pitch);
 }
 
-template <int N, bool HI, int P, class S, class R, int I = 0>
+// Input row r of a sweep.  WRAP (strips within the stencil reach of a
+// periodic y edge): the row's periodic image inside the grid, so the y ghost
+// rows of a periodic axis are never read; otherwise r itself (ghost rows of a
+// bounded side hold its boundary states).
+template <bool WRAP>
+__device__ __forceinline__ int in_row(int r, int ny) {
+  if constexpr (WRAP) return r < 0 ? r + ny : (r >= ny ? r - ny : r);
+  else return r;
+}
+
+template <int N, bool HI, int P, class S, class R, bool WRAP, int I = 0>
 __device__ __forceinline__ void prime(const LatTab<R>& L, const S* col, int plane, int pitch,
-                                      int ys, Windows<N, P, R>& W) {
+                                      int ys, int ny, Windows<N, P, R>& W) {
   if constexpr (I < N * N) {
     if constexpr (windowed<N, HI, I>()) {
       const int r0 = ys + L.off[I / N];
-      const S* q = plane_row(col, plane, pitch, I, r0) + x_off<N, HI, I, R>(L);
+      const int xo = x_off<N, HI, I, R>(L);
+      if constexpr (WRAP) {
 #pragma unroll
-      for (int b = 0; b < P - 1; ++b) W.v[I][b] = tap_row<N, HI, P, I, S, R>(L, q + b * pitch);
+        for (int b = 0; b < P - 1; ++b)
+          W.v[I][b] = tap_row<N, HI, P, I, S, R>(
+              L, plane_row(col, plane, pitch, I, in_row<WRAP>(r0 + b, ny)) + xo);
+      } else {
+        const S* q = plane_row(col, plane, pitch, I, r0) + xo;
+#pragma unroll
+        for (int b = 0; b < P - 1; ++b) W.v[I][b] = tap_row<N, HI, P, I, S, R>(L, q + b * pitch);
+      }
     }
-    prime<N, HI, P, S, R, I + 1>(L, col, plane, pitch, ys, W);
+    prime<N, HI, P, S, R, WRAP, I + 1>(L, col, plane, pitch, ys, ny, W);
   }
 }
 
 // Streamed value of every population at output row y (windows advanced).
-template <int N, bool HI, int P, class S, class R, int I = 0>
+template <int N, bool HI, int P, class S, class R, bool WRAP, int I = 0>
 __device__ __forceinline__ void stream_row(const LatTab<R>& L, const S* col, int plane, int pitch,
-                                           int y, Windows<N, P, R>& W, R* f) {
+                                           int y, int ny, Windows<N, P, R>& W, R* f) {
   if constexpr (I < N * N) {
     constexpr int jy = I / N;
     if constexpr (windowed<N, HI, I>()) {
       constexpr int rr = (P - 1) / 2;
-      const S* q = plane_row(col, plane, pitch, I, y + L.off[jy] + P - 1) + x_off<N, HI, I, R>(L);
+      const S* q = plane_row(col, plane, pitch, I, in_row<WRAP>(y + L.off[jy] + P - 1, ny)) +
+                   x_off<N, HI, I, R>(L);
       const R vn = tap_row<N, HI, P, I, S, R>(L, q);
       R v[P];
 #pragma unroll
@@ -186,11 +205,11 @@ __device__ __forceinline__ void stream_row(const LatTab<R>& L, const S* col, int
       for (int b = 0; b < P - 2; ++b) W.v[I][b] = W.v[I][b + 1];
       W.v[I][P - 2] = vn;
     } else {
-      const S* q = plane_row(col, plane, pitch, I, y + snapped_offset(N, jy)) +
+      const S* q = plane_row(col, plane, pitch, I, in_row<WRAP>(y + snapped_offset(N, jy), ny)) +
                    x_off<N, HI, I, R>(L);
       f[I] = tap_row<N, HI, P, I, S, R>(L, q);
     }
-    stream_row<N, HI, P, S, R, I + 1>(L, col, plane, pitch, y, W, f);
+    stream_row<N, HI, P, S, R, WRAP, I + 1>(L, col, plane, pitch, y, ny, W, f);
   }
 }
 
@@ -275,7 +294,7 @@ __host__ __device__ constexpr int side_shift(int sx, int sy) { return 8 + 2 * (s
 // every cell of the lattice streamed, collided and stored; the next flag
 // (criterion) written; per tile q of the strip, the OR of the cells' bits
 // (bit 0/1: next-step lattice, bit 2: flipped) into tb[q].
-template <int N, bool HI, int P, class S, class R>
+template <int N, bool HI, int P, class S, class R, bool WRAP>
 __device__ __forceinline__ void sweep(const Params<R>& p, const LatTab<R>& L, int k,
                                       const S* __restrict__ fin, S* __restrict__ fout,
                                       const uint8_t* __restrict__ flag_cur,
@@ -288,7 +307,7 @@ __device__ __forceinline__ void sweep(const Params<R>& p, const LatTab<R>& L, in
   // relaxation rate of the lane's column (channels carry their own tau)
   const R om = p.omega_x ? p.omega_x[xl] : p.omega;
   Windows<N, P, R> W;
-  prime<N, HI, P, S, R>(L, col, plane, p.pitch, ys, W);
+  prime<N, HI, P, S, R, WRAP>(L, col, plane, p.pitch, ys, p.ny, W);
   int bits = 0, sides = 0;
   const int x0 = x & ~(kTX - 1), lane = threadIdx.x & 31;
   const int rlast = ye + stage_halo(P) - 1;  // last input row the sweep reads
@@ -296,9 +315,10 @@ __device__ __forceinline__ void sweep(const Params<R>& p, const LatTab<R>& L, in
     R f[N * N];
     {
       const int r = y + stage_halo(P) + kPrefetchRows;
-      if (r <= rlast) prefetch_row<N * N, S>(fin, plane, p.pitch, p.G, x0, r, lane);
+      if (r <= rlast)
+        prefetch_row<N * N, S>(fin, plane, p.pitch, p.G, x0, in_row<WRAP>(r, p.ny), lane);
     }
-    stream_row<N, HI, P, S, R>(L, col, plane, p.pitch, y, W, f);
+    stream_row<N, HI, P, S, R, WRAP>(L, col, plane, p.pitch, y, p.ny, W, f);
     const bool act = xin && flag_cur[y * p.nx + x] == k;
     const int ob = (y + p.G) * p.pitch + (x + kOX);
     const uint32_t key = hash32((uint32_t)ob ^ (seed * 0x9e3779b9u));  // FP16 rounding only
@@ -354,7 +374,7 @@ __device__ __forceinline__ void sweep(const Params<R>& p, const LatTab<R>& L, in
 // its 3 x 3 tile neighbourhood (its flip bit into its own), listing the tiles
 // that gain work (add_work, with each returning atomic's result used one tile
 // later so the warp does not wait for it).
-template <int NL, int NH, int P, class S, class R>
+template <int NL, int NH, int P, class S, class R, bool WRAP>
 __global__ void __launch_bounds__(kStripWarps * 32, strip_blocks<S>())
 k_stream_collide(const Params<R> p, const S* __restrict__ fin0, const S* __restrict__ fin1,
                  S* __restrict__ fout0, S* __restrict__ fout1,
@@ -387,18 +407,30 @@ k_stream_collide(const Params<R> p, const S* __restrict__ fin0, const S* __restr
     if (lane < kStripTiles) tb[lane] = 0;
     __syncwarp();
     const int x = sx * kTX + lane, y0 = ty0 * kTY;
-    // each lattice over the rows of its first to its last tile in the strip
+    // each lattice over the rows of its first to its last tile in the strip;
+    // in the WRAP kernel (handles with wrap_y), a sweep whose input rows
+    // (ys - G .. ye - 1 + G) cross the periodic y edge reads their images in
+    // the grid
+    constexpr int H = stage_halo(P);
     if (has_lo) {
       const int ys = y0 + (__ffs(has_lo) - 1) * kTY;
       const int ye = min(y0 + (32 - __clz(has_lo)) * kTY, p.ny);
-      sweep<NL, false, P, S, R>(p, p.lat[0], 0, fin0, fout0, flag_cur, flag_nxt, x, y0, ys, ye,
-                                seed, tb);
+      if (WRAP && (ys < H || ye > p.ny - H))
+        sweep<NL, false, P, S, R, WRAP>(p, p.lat[0], 0, fin0, fout0, flag_cur, flag_nxt, x, y0,
+                                        ys, ye, seed, tb);
+      else
+        sweep<NL, false, P, S, R, false>(p, p.lat[0], 0, fin0, fout0, flag_cur, flag_nxt, x, y0,
+                                         ys, ye, seed, tb);
     }
     if (has_hi) {
       const int ys = y0 + (__ffs(has_hi) - 1) * kTY;
       const int ye = min(y0 + (32 - __clz(has_hi)) * kTY, p.ny);
-      sweep<NH, true, P, S, R>(p, p.lat[1], 1, fin1, fout1, flag_cur, flag_nxt, x, y0, ys, ye,
-                               seed, tb);
+      if (WRAP && (ys < H || ye > p.ny - H))
+        sweep<NH, true, P, S, R, WRAP>(p, p.lat[1], 1, fin1, fout1, flag_cur, flag_nxt, x, y0,
+                                       ys, ye, seed, tb);
+      else
+        sweep<NH, true, P, S, R, false>(p, p.lat[1], 1, fin1, fout1, flag_cur, flag_nxt, x, y0,
+                                        ys, ye, seed, tb);
     }
     __syncwarp();
     for (int q = 0; q < nt; ++q) {
@@ -459,7 +491,7 @@ struct LaunchCache {
   int per_sm[kMaxDevices] = {};
 };
 
-template <class S, class R>
+template <class S, class R, bool WRAP>
 cudaError_t launch_stream_collide_impl(const Params<R>& p, int P, const S* fin0, const S* fin1,
                                        S* fout0, S* fout1, const uint8_t* flag_cur,
                                        uint8_t* flag_nxt, const uint8_t* tile_mask,
@@ -479,7 +511,7 @@ cudaError_t launch_stream_collide_impl(const Params<R>& p, int P, const S* fin0,
     return cudaErrorInvalidDevice;
 #define SLBM_SC_CASE(NL, NH, PP)                                                            \
   if (nl == NL && nh == NH && P == PP) {                                                    \
-    auto kern = k_stream_collide<NL, NH, PP, S, R>;                                         \
+    auto kern = k_stream_collide<NL, NH, PP, S, R, WRAP>;                                   \
     static LaunchCache cache;                                                               \
     int per_sm = 0;                                                                         \
     {                                                                                       \

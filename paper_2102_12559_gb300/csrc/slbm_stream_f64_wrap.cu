@@ -1,0 +1,15 @@
+// Double-precision instantiation of the fused stream-collide kernel for grids whose
+// periodic y rows are read through their images near the edges (wrap_y).
+#include "slbm_stream.cuh"
+
+namespace slbm {
+template <>
+cudaError_t launch_stream_collide_wrap<double, double>(const Params<double>& p, int P, const double* fin0,
+                                             const double* fin1, double* fout0, double* fout1,
+                                             const uint8_t* flag_cur, uint8_t* flag_nxt,
+                                             const uint8_t* tile_mask, uint8_t* mask_next,
+                                             cudaStream_t st) {
+  return launch_stream_collide_impl<double, double, true>(p, P, fin0, fin1, fout0, fout1, flag_cur,
+                                                  flag_nxt, tile_mask, mask_next, st);
+}
+}  // namespace slbm

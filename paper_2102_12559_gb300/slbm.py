@@ -26,7 +26,7 @@ SLBM_POND_REACH = 5
 SLBM_FP32, SLBM_FP64, SLBM_FP16 = 0, 1, 2
 SLBM_BC_OUTFLOW, SLBM_BC_DIRICHLET, SLBM_BC_INLET, SLBM_BC_DIFFUSE = 0, 1, 2, 3
 SLBM_SIDE_XMIN, SLBM_SIDE_XMAX, SLBM_SIDE_YMIN, SLBM_SIDE_YMAX = 0, 1, 2, 3
-SLBM_CRIT_NONE, SLBM_CRIT_MACH, SLBM_CRIT_MLP = 0, 1, 2
+SLBM_CRIT_NONE, SLBM_CRIT_MACH, SLBM_CRIT_MLP, SLBM_CRIT_MLP_REFINE = 0, 1, 2, 3
 
 EXPORTS = [
     "slbm_workspace_bytes", "slbm_create", "slbm_create_in", "slbm_destroy", "slbm_get_info",

@@ -21,6 +21,10 @@ pytestmark = pytest.mark.gpu
 FP32, FP64 = slbm.SLBM_FP32, slbm.SLBM_FP64
 
 
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
 def state_pair(precision, periodic):
     nx, ny = 37, 29
     fields = WL.perturbed(nx, ny, seed=21, amp_rho=0.05, amp_u=0.3)
@@ -122,3 +126,105 @@ def test_mlp_criterion_needs_weights():
     g = slbm.Solver(32, 32, 3, 5, tau=0.6)
     with pytest.raises(slbm.SlbmError):
         g.set_criterion(slbm.SLBM_CRIT_MLP, 0.0)
+
+
+@pytest.mark.parametrize("case,crit", [("periodic", slbm.SLBM_CRIT_MLP),
+                                       ("walled_high_tau", slbm.SLBM_CRIT_MLP),
+                                       ("periodic", slbm.SLBM_CRIT_MLP_REFINE)])
+def test_mlp_flips_match_oracle_replay(case, crit):
+    """Flags set by the learned indicator during a run (every 5 steps, random
+    weights so that cells flip both ways) convert the populations as the
+    oracle does when it is given the same flags at the same steps: FP64
+    moments within 1e-11 after 40 steps.  Refinement only: no flag ever goes
+    back from 1 to 0."""
+    if case == "periodic":
+        nx, ny, tau, periodic = 45, 37, 0.7, (True, True)
+        fields = WL.perturbed(nx, ny, seed=23, amp_rho=0.04, amp_u=0.3)
+    else:
+        nx, ny, tau, periodic = 40, 8, 20.0, (False, True)
+        fields = WL.perturbed(nx, ny, seed=24, amp_rho=0.02, amp_u=0.1)
+    g = slbm.Solver(nx, ny, 3, 5, tau=tau, periodic=periodic, precision=FP64)
+    o = O.Oracle(nx, ny, 3, 5, tau=tau, order=3, periodic=periodic)
+    if not periodic[0]:
+        for side, uw in ((0, -0.1), (1, 0.1)):
+            g.set_boundary(side, slbm.SLBM_BC_DIFFUSE, None, np.zeros(ny), np.full(ny, uw))
+            o.set_bc(side, O.BC_DIFFUSE, None, np.zeros(ny), np.full(ny, uw))
+    g.init_equilibrium(*fields)
+    o.init_equilibrium(*fields)
+    # refinement only: a short interval (buffer) and the threshold at the
+    # initial logits' 90th percentile, so the flagged region starts small
+    every = 5 if crit == slbm.SLBM_CRIT_MLP else 2
+    g.set_indicator(random_weights(9), interval=every)
+    thr = 0.0
+    if crit == slbm.SLBM_CRIT_MLP_REFINE:
+        thr = float(np.quantile(g.indicator_eval(features=False, logits=True)[1], 0.9))
+    g.set_criterion(crit, thr)
+    fl = g.get_flags()
+    o.set_flags(fl)
+    flips = 0
+    for _ in range(40 // every):
+        g.step(every)
+        o.step(every)
+        nf = g.get_flags()
+        flips += int((nf != fl).sum())
+        if crit == slbm.SLBM_CRIT_MLP_REFINE:
+            assert (nf >= fl).all()
+        fl = nf
+        o.set_flags(fl)
+    assert fl.mean() > 0.1 and flips > 5, (fl.mean(), flips)
+    if crit == slbm.SLBM_CRIT_MLP:
+        assert fl.mean() < 0.9
+    mg, mo = g.moments(), o.moments()
+    for q in range(3):
+        assert rel_l2(mg[q], mo[q]) < 1e-11, (q, rel_l2(mg[q], mo[q]))
+    g.close()
+
+
+def density_weights():
+    """logit = 10 relu(relu(10 (rho - 1))) - 2.5: positive iff rho - 1 > 0.025."""
+    w = {"w1": np.zeros((16, 32)), "b1": np.zeros(32), "w2": np.zeros((32, 32)),
+         "b2": np.zeros(32), "w3": np.zeros(32), "b3": -2.5}
+    w["w1"][0, 0] = 1.0
+    w["w2"][0, 0] = 1.0
+    w["w3"][0] = 10.0
+    return w
+
+
+def test_refine_buffer_square_and_channel_gaps():
+    """SLBM_CRIT_MLP_REFINE widens the indicator's decisions by `interval`
+    cells along x and y (a square around an isolated cell on a periodic
+    grid), never across a channel gap, and keeps what was flagged before."""
+    nx, ny, r = 40, 30, 3
+    rho = np.ones((ny, nx))
+    rho[10, 38] = 1.05                           # next to the periodic x edge
+    g = slbm.Solver(nx, ny, 3, 5, tau=0.7, precision=FP64)
+    g.init_equilibrium(rho, np.zeros((ny, nx)), np.zeros((ny, nx)))
+    g.set_indicator(density_weights(), interval=r)
+    g.set_criterion(slbm.SLBM_CRIT_MLP_REFINE, 0.0)
+    want = np.zeros((ny, nx), np.uint8)
+    for dy in range(-r, r + 1):
+        for dx in range(-r, r + 1):
+            want[(10 + dy) % ny, (38 + dx) % nx] = 1
+    np.testing.assert_array_equal(g.get_flags(), want)
+    g.step(2 * r)
+    assert (g.get_flags() >= want).all()
+    g.close()
+
+    widths, G = [20, 24], 2
+    x0, nxc = WL.channel_layout(widths, G)
+    rho = np.ones((8, nxc))
+    rho[:, x0[0] + 17:x0[0] + 20] = 1.05         # against channel 0's right wall
+    c = slbm.Solver(nxc, 8, 3, 5, tau=0.7, periodic=(False, True), precision=FP64)
+    c.init_equilibrium(rho, np.zeros((8, nxc)), np.zeros((8, nxc)))
+    c.set_channels(x0, widths, [0.0, 0.0], [0.0, 0.0], [0.7, 0.9])
+    c.set_indicator(density_weights(), interval=r)
+    c.set_criterion(slbm.SLBM_CRIT_MLP_REFINE, 0.0)
+    fl = c.get_flags()
+    want = np.zeros((8, nxc), np.uint8)
+    gap = np.ones(nxc, bool)
+    for k, w in enumerate(widths):
+        gap[x0[k]:x0[k] + w] = False
+    want[:, gap] = 2
+    want[:, x0[0] + 17 - r:x0[0] + 20] = 1
+    np.testing.assert_array_equal(fl, want)
+    c.close()
