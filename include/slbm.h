@@ -293,6 +293,11 @@ SLBM_API int slbm_set_boundary(slbm_t h, int side, int kind, const double *rho, 
  * results.  A learned indicator or Knudsen criterion splits the steps into
  * chunks between its evaluations. */
 SLBM_API int slbm_step(slbm_t h, int n);
+/* The post-step kernel runs one warp per 32 x 8 tile on grids of 8192 tiles
+ * and more, one thread block per tile below (a small grid's few tiles each
+ * end in one dependent chain, which a block shortens); the environment
+ * variable SLBM_POST_KERNEL = "warp" or "block", read by slbm_create, forces
+ * one of them (results are the same). */
 
 /* Wait for the handle's stream. */
 SLBM_API int slbm_sync(slbm_t h);

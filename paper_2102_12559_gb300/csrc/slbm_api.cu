@@ -182,7 +182,8 @@ struct Layout {
   size_t pops[2][2];         // byte offsets [buffer][lattice]
   size_t flags[2], flag_tmp, tile_mask[2], macro[4], partials, audit_out, err, bc[4][3];
   size_t lam[2];             // co-moving frame planes {u_x, u_y, T} per buffer
-  size_t sched;              // two tile counters of the stream kernel's scheduler
+  size_t sched;              // two tile counters of the stream kernel's scheduler, then the
+                             // post-step kernel's item counter
   size_t seed_ctr;           // FP16 rounding key counter
   size_t gh_start, gh_idx, gh_tiles;  // per-tile ghost lists (GhostTables)
   size_t post_work;          // 2 x ntiles work words (stream kernel -> post-step kernel)
@@ -257,7 +258,7 @@ Layout make_layout(const slbm_grid* g, int lo, int hi, int order, int precision)
   for (int s = 0; s < 4; ++s)
     for (int q = 0; q < 3; ++q) { Lo.bc[s][q] = off; off = align_up(off + side * 8, 256); }
   for (int b = 0; b < 2; ++b) { Lo.lam[b] = off; off = align_up(off + 3 * nc * es, 256); }
-  Lo.sched = off; off = align_up(off + 2 * sizeof(int), 256);
+  Lo.sched = off; off = align_up(off + 4 * sizeof(int), 256);
   Lo.seed_ctr = off; off = align_up(off + sizeof(uint32_t), 256);
   const size_t ring = 2 * (size_t)Lo.G * (g->nx + 2 * Lo.G) + 2 * (size_t)Lo.G * g->ny;
   Lo.gh_start = off; off = align_up(off + (ntiles + 1) * sizeof(int), 256);
@@ -315,6 +316,8 @@ struct slbm_s {
   // device (owned, one allocation) the internal wall ghosts {gx, gy, sx, side},
   // their velocities, the per-column omega and the ghost index list sized for
   // the ring plus the walls
+  int post_kernel;               // per-step post-step kernel: 0 by grid size, 1 warp, 2 block
+                                 // (environment SLBM_POST_KERNEL = warp / block at creation)
   int nchan, nwall;
   std::vector<uint8_t> gapcol;
   char* chanbuf;
@@ -727,6 +730,7 @@ void fill_params(Params<R>& p, const slbm_s* h, const Lattice1D& a, const Lattic
   p.periodic_x = h->g.periodic_x ? 1 : 0;
   p.periodic_y = h->g.periodic_y ? 1 : 0;
   p.wrap_y = wraps_y(h);
+  p.post_warp = h->post_kernel == 1 || (h->post_kernel == 0 && ntiles_of(h) >= kPostWarpTiles);
   p.crit = h->crit;
   p.thr = (R)h->thr;
   p.omega = (R)(1.0 / h->tau);
@@ -1029,6 +1033,10 @@ int apply_indicator(slbm_s* h) {
                               fold, fnew, h->at<uint8_t>(h->lay.tile_mask[h->mcur]), work, list,
                               nlist, half, h->st),
           "tile work launch");
+  // the post-step kernel's item counter (zeroed by every stream launch; none
+  // ran since the last post-step launch)
+  SLBM_CK(h, cudaMemsetAsync(h->at<int>(h->lay.sched) + 2, 0, sizeof(int), h->st),
+          "item counter clear");
   cudaError_t e = with_types(h, [&](auto ty, const auto& prm) {
     SLBM_TYPES(ty);
     return launch_post_step<S, R>(prm, (S*)h->pops(h->cur, 0), (S*)h->pops(h->cur, 1), fold, fnew,
@@ -1080,6 +1088,10 @@ int slbm_create_in(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int i
   h->nsm = 1;
   cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev);
   h->g = *g;
+  {  // the per-step post-step kernel, by grid size unless the environment says
+    const char* pk = std::getenv("SLBM_POST_KERNEL");
+    h->post_kernel = pk && !std::strcmp(pk, "warp") ? 1 : (pk && !std::strcmp(pk, "block") ? 2 : 0);
+  }
   h->nlo = lat_lo;
   h->nhi = lat_hi;
   h->P = interp_order + 1;

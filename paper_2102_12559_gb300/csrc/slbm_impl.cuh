@@ -84,7 +84,8 @@ struct Params {
   ConvTab<R> conv;
   uint32_t* seed_ctr;           // step key of the FP16 stochastic rounding (device counter,
                                 // advanced by every post-step launch)
-  int* sched;                   // two tile counters of the stream kernel's scheduler
+  int* sched;                   // two tile counters of the stream kernel's scheduler; sched[2]:
+                                // the post-step kernel's item counter (zeroed by the stream kernel)
   int sched_parity;             // the counter (and work-bit half) this step uses
   int* work;                    // 2 x ntiles post-step work bits, accumulated by the stream kernel
   int* wlist;                   // 2 x ntiles: candidate work tiles (see add_work)
@@ -93,7 +94,11 @@ struct Params {
   const R* omega_x;             // per-column omega (channels), else null: omega everywhere
   int wrap_y;                   // 1: periodic y rows are read through their images (no
                                 // y ghost rows; see the layout note above)
+  int post_warp;                // 1: the per-step post-step kernel runs one warp per tile
+                                // (grids of kPostWarpTiles tiles and more), else one CTA per tile
 };
+
+constexpr int kPostWarpTiles = 8192;  // tiles from which the warp-per-tile post-step kernel runs
 
 constexpr int kWrapRowsMax = 256;  // periodic y axes shorter than this wrap (wrap_y)
 

@@ -15,6 +15,8 @@
 //     ghosts are constant and written once by the setup ghost kernel.
 #pragma once
 
+#include <mutex>
+
 #include "../../include/slbm.h"
 #include "slbm_ghost.cuh"
 
@@ -342,7 +344,8 @@ __device__ __forceinline__ void tile_ghosts(const Params<R>& p, S* f0, S* f1,
   }
 }
 
-// Per-step post-step kernel.
+// Per-step post-step kernel, one CTA (32 x 8 threads) per tile: the choice
+// for small grids, whose few tiles each end in one chain of the kernel.
 //  1. Interface conversion.  The stream kernel has OR-ed, into one word per
 //     tile, the lattices of the tile's 3 x 3 tile neighbourhood and the tile's
 //     own flip bit, and listed the candidate tiles (add_work).  CTA b takes
@@ -360,7 +363,7 @@ __device__ __forceinline__ void tile_ghosts(const Params<R>& p, S* f0, S* f1,
 //     never used.)
 template <int NL, int NH, class S, class R>
 __global__ void __launch_bounds__(kTX * kTY)
-k_post_step(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ flag_old,
+k_post_step_block(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ flag_old,
             const uint8_t* __restrict__ flag_new, const BcDev bc, const int* __restrict__ work,
             const int* __restrict__ list, const int* __restrict__ nlist, int ntx,
             const int* __restrict__ gh_start, const int* __restrict__ gh_idx,
@@ -409,6 +412,302 @@ k_post_step(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ flag_ol
   }
 }
 
+// ------------------------------------------------------------- per step
+//
+// One warp per tile, no block barrier: the per-step post-step kernel for
+// large grids gives each warp its own chain of tiles, so an SM keeps many
+// independent chains (flag loads, conversions, ghost writes) in flight.
+
+constexpr int kPostWarps = 4;  // warps per CTA of the per-step kernel
+// resident CTAs per SM the per-step kernel is compiled for (80 registers;
+// FP64, the parity build, keeps its registers)
+template <class S>
+constexpr int post_blocks() { return sizeof(S) == 8 ? 3 : 6; }
+
+// Diffuse-wall ghost cell of lattice L (N nodes per axis), all Q populations
+// by one thread: the same sums as diffuse_value, taken once per cell.
+template <int N, class S, class R>
+__device__ __forceinline__ void diffuse_cell(const LatTab<R>& L, S* f, long long plane, int sb,
+                                             int gb, int side, R uwx, R uwy) {
+  const bool axis_y = side >= SLBM_SIDE_YMIN;
+  const R nsign = (side == SLBM_SIDE_XMIN || side == SLBM_SIDE_YMIN) ? R(1) : R(-1);
+  R dx[N], dy[N];
+  dphi<R>(L, N, uwx, dx);
+  dphi<R>(L, N, uwy, dy);
+  R sv[N * N];
+  R s_out = R(0), e_in = R(0), a = R(0);
+#pragma unroll
+  for (int jy = 0; jy < N; ++jy)
+#pragma unroll
+    for (int jx = 0; jx < N; ++jx) {
+      const int j = jx + N * jy;
+      const R cn = (axis_y ? L.c[jy] : L.c[jx]) * nsign;
+      const R w = L.w1[jx] * L.w1[jy];
+      const R e = L.w1[jx] * dy[jy] + dx[jx] * L.w1[jy] + dx[jx] * dy[jy];
+      sv[j] = static_cast<R>(__ldcg(f + (size_t)j * plane + sb));
+      if (cn < R(0)) s_out -= cn * sv[j];
+      if (cn > R(0)) {
+        e_in += cn * e;
+        a += cn * w;
+      }
+    }
+  const R drw = (s_out - e_in) / (a + e_in);
+#pragma unroll
+  for (int jy = 0; jy < N; ++jy)
+#pragma unroll
+    for (int jx = 0; jx < N; ++jx) {
+      const int j = jx + N * jy;
+      const R cn = (axis_y ? L.c[jy] : L.c[jx]) * nsign;
+      const R w = L.w1[jx] * L.w1[jy];
+      const R e = L.w1[jx] * dy[jy] + dx[jx] * L.w1[jy] + dx[jx] * dy[jy];
+      f[(size_t)j * plane + gb] = static_cast<S>(cn > R(0) ? drw * (w + e) + e : sv[j]);
+    }
+}
+
+// Images of ghost cell g (every plane of both lattices) by one thread, under
+// the ghost rule: copies of the source, INLET equilibria (both lattices, in
+// product form) at the source's density (summed over its own lattice) and
+// the side's velocity, DIFFUSE walls; DIRICHLET ghosts are constant.
+// Sources are read through L2 (ld.global.cg): other threads have just
+// written them.
+template <int NL, int NH, class S, class R>
+__device__ __forceinline__ void lane_ghost(const Params<R>& p, S* f0, S* f1,
+                                           const uint8_t* __restrict__ flag, const BcDev& bc,
+                                           int g) {
+  constexpr int q0 = NL * NL, q1 = NH * NH;
+  int gx, gy, sx, sy, side = 0, bi = 0;
+  const int kind = ghost_cell(p.G, p.nx, p.ny, p.periodic_x, p.periodic_y, bc, g, gx, gy, sx, sy,
+                              side, bi);
+  if (kind == 2) return;
+  const int sb = (sy + p.G) * p.pitch + (sx + kOX);
+  const int gb = (gy + p.G) * p.pitch + (gx + kOX);
+  if (kind == 0) {
+    S v[q1];
+#pragma unroll
+    for (int i = 0; i < q0; ++i) v[i] = __ldcg(f0 + (size_t)i * p.plane + sb);
+#pragma unroll
+    for (int i = 0; i < q0; ++i) f0[(size_t)i * p.plane + gb] = v[i];
+#pragma unroll
+    for (int i = 0; i < q1; ++i) v[i] = __ldcg(f1 + (size_t)i * p.plane + sb);
+#pragma unroll
+    for (int i = 0; i < q1; ++i) f1[(size_t)i * p.plane + gb] = v[i];
+  } else if (kind == 3) {
+    const R uwx = (R)ghost_ux(bc, side, bi), uwy = (R)ghost_uy(bc, side, bi);
+    diffuse_cell<NL, S, R>(p.lat[0], f0, p.plane, sb, gb, side, uwx, uwy);
+    diffuse_cell<NH, S, R>(p.lat[1], f1, p.plane, sb, gb, side, uwx, uwy);
+  } else {
+    R dr = R(0);
+    if (__ldcg(flag + sx + p.nx * sy)) {
+#pragma unroll
+      for (int j = 0; j < q1; ++j) dr += static_cast<R>(__ldcg(f1 + (size_t)j * p.plane + sb));
+    } else {
+#pragma unroll
+      for (int j = 0; j < q0; ++j) dr += static_cast<R>(__ldcg(f0 + (size_t)j * p.plane + sb));
+    }
+    write_eq_t<NL, NH, S, R>(p, f0, f1, gb, dr, (R)ghost_ux(bc, side, bi),
+                             (R)ghost_uy(bc, side, bi));
+  }
+}
+
+// A staged column (periodic wrap by a full modulo; -1 beyond a bounded side).
+__device__ __forceinline__ int stage_col(int c, int n, int periodic) {
+  if (c >= 0 && c < n) return c;
+  return periodic ? ((c % n) + n) % n : -1;
+}
+
+// Interface conversion of one tile (origin x0, y0) by one warp.  Flags of
+// the tile's rows and of B rows / columns around it become warp-wide bit
+// masks (ballots of each staged row's 32 columns plus the 2B halo columns
+// loaded by lanes < 2B); "a cell of lattice v within B columns" is the mask
+// OR-ed with itself shifted by 1 .. 2B, and within B rows and columns the OR
+// of 2B + 1 such rows.  A cell converts when its lattice changed or a cell of
+// the other lattice is within the band radius (the rule of post_tile); the
+// cells to convert are compacted over the warp's lanes, lifts first, then
+// projections, 32 at a time.
+template <int NL, int NH, class S, class R>
+__device__ __forceinline__ void warp_convert(const Params<R>& p, S* f0, S* f1,
+                                             const uint8_t* __restrict__ flag_old,
+                                             const uint8_t* __restrict__ flag_new, int x0,
+                                             int y0) {
+  constexpr int kRows = kTY + 2 * kBandMax;
+  const int lane = threadIdx.x & 31, B = p.band;
+  const int cm = stage_col(x0 + lane, p.nx, p.periodic_x);
+  const int ch = lane < 2 * B
+                     ? stage_col(lane < B ? x0 - B + lane : x0 + kTX + lane - B, p.nx, p.periodic_x)
+                     : -1;
+  // per staged row, into the warp's shared words: which lanes' windows
+  // (columns lane - B .. lane + B) hold lattice 0 / 1 (d[0 / 1][row]); per tile
+  // row the new and old lattice masks of the tile's cells (t[0..3][row]:
+  // new 0, new 1, old 0, old 1); then per tile row the cells to lift / project,
+  // the new lattice and the band mask (c[0..3][row]).  Shared, not registers:
+  // the conversions below need the registers.
+  __shared__ unsigned s_d[kPostWarps][2][kRows];
+  __shared__ unsigned s_t[kPostWarps][4][kTY];
+  __shared__ unsigned s_c[kPostWarps][4][kTY];
+  const int wq = threadIdx.x >> 5;
+  unsigned(*sd)[kRows] = s_d[wq];
+  unsigned(*st)[kTY] = s_t[wq];
+  unsigned(*sm)[kTY] = s_c[wq];
+  const bool xin = x0 + lane < p.nx;
+  for (int r = 0; r < kTY + 2 * B; ++r) {
+    const int gy = stage_col(y0 - B + r, p.ny, p.periodic_y);
+    int fm = 2, fh = 2;
+    if (gy >= 0) {
+      if (cm >= 0) fm = flag_new[(long long)gy * p.nx + cm];
+      if (ch >= 0) fh = flag_new[(long long)gy * p.nx + ch];
+    }
+    const unsigned m0 = __ballot_sync(0xffffffffu, fm == 0), m1 = __ballot_sync(0xffffffffu, fm == 1);
+    const unsigned h0 = __ballot_sync(0xffffffffu, fh == 0), h1 = __ballot_sync(0xffffffffu, fh == 1);
+    const unsigned long long lo = (1ull << B) - 1ull;
+    const unsigned long long e0 = ((unsigned long long)h0 & lo) | ((unsigned long long)m0 << B) |
+                                  ((unsigned long long)(h0 >> B) << (kTX + B));
+    const unsigned long long e1 = ((unsigned long long)h1 & lo) | ((unsigned long long)m1 << B) |
+                                  ((unsigned long long)(h1 >> B) << (kTX + B));
+    unsigned long long a0 = e0, a1 = e1;
+    for (int d = 1; d <= 2 * B; ++d) {
+      a0 |= e0 >> d;
+      a1 |= e1 >> d;
+    }
+    if (lane == 0) {
+      sd[0][r] = (unsigned)a0;
+      sd[1][r] = (unsigned)a1;
+    }
+    const int i = r - B;  // tile row
+    if (i >= 0 && i < kTY) {
+      const bool in = xin && y0 + i < p.ny;
+      const int fo = in ? flag_old[(long long)(y0 + i) * p.nx + x0 + lane] : 2;
+      const unsigned t0 = __ballot_sync(0xffffffffu, in && fm == 0);
+      const unsigned t1 = __ballot_sync(0xffffffffu, in && fm == 1);
+      const unsigned t2 = __ballot_sync(0xffffffffu, in && fo == 0);
+      const unsigned t3 = __ballot_sync(0xffffffffu, in && fo == 1);
+      if (lane == 0) {
+        st[0][i] = t0;
+        st[1][i] = t1;
+        st[2][i] = t2;
+        st[3][i] = t3;
+      }
+    }
+  }
+  __syncwarp();
+  int nlift = 0, nproj = 0;
+  for (int i = 0; i < kTY; ++i) {
+    unsigned w0 = 0u, w1 = 0u;  // lattice 0 / 1 within B rows and columns
+    for (int d = 0; d <= 2 * B; ++d) {
+      w0 |= sd[0][i + d];
+      w1 |= sd[1][i + d];
+    }
+    const unsigned n0 = st[0][i], n1 = st[1][i], o0 = st[2][i], o1 = st[3][i];
+    const unsigned band = (n0 & w1) | (n1 & w0);
+    const unsigned flip = (o0 & n1) | (o1 & n0);
+    const unsigned conv = (n0 | n1) & (o0 | o1) & (flip | band);
+    if (lane == 0) {
+      sm[0][i] = conv & o0;
+      sm[1][i] = conv & o1;
+      sm[2][i] = n1;
+      sm[3][i] = band;
+    }
+    nlift += __popc(conv & o0);
+    nproj += __popc(conv & o1);
+  }
+  __syncwarp();
+  using M = PostMath<NL, NH, R>;
+  for (int pass = 0; pass < 2; ++pass) {
+    const int ntot = pass ? nproj : nlift;
+    for (int base = 0; base < ntot; base += 32) {
+      const int k = base + lane;
+      if (k >= ntot) continue;
+      // the k-th cell of the pass: its row by the rows' counts, its column by __fns
+      int i = 0, pre = 0;
+      for (; i < kTY - 1; ++i) {
+        const int c = __popc(sm[pass][i]);
+        if (k < pre + c) break;
+        pre += c;
+      }
+      const int col = (int)__fns(sm[pass][i], 0, k - pre + 1);
+      const int nw = (int)((sm[2][i] >> col) & 1u), band = (int)((sm[3][i] >> col) & 1u);
+      const int base_el = (y0 + i + p.G) * p.pitch + (x0 + col + kOX);
+      R a[kMaxN][kMaxN], b[kMaxN][kMaxN];
+      if (pass == 0) {  // computed in the low-order lattice
+        load_t<NL, S, R>(f0, p.plane, base_el, a);
+        M::lift(p, a, b);
+        store_t<NH, S, R>(f1, p.plane, base_el, b);
+        if (nw == 1 && band) {  // now high-order; low-order readers see its projection
+          M::project(p, b, a);
+          store_t<NL, S, R>(f0, p.plane, base_el, a);
+        }
+      } else {
+        load_t<NH, S, R>(f1, p.plane, base_el, b);
+        M::project(p, b, a);
+        store_t<NL, S, R>(f0, p.plane, base_el, a);
+        if (nw == 0 && band) {  // now low-order; high-order readers see its lifting
+          M::lift(p, a, b);
+          store_t<NH, S, R>(f1, p.plane, base_el, b);
+        }
+      }
+    }
+  }
+  __syncwarp();  // the shared words are rewritten by the warp's next tile
+}
+
+// Per-step post-step kernel, one warp per tile (large grids).
+//  1. Interface conversion.  The stream kernel has OR-ed, into one word per
+//     tile, the lattices of the tile's 3 x 3 tile neighbourhood and the tile's
+//     own flip bit, and listed the candidate tiles (add_work).  Each warp takes
+//     the next item from a counter; list items whose word is work (both
+//     lattices or a flip) are converted by that warp (warp_convert).
+//  2. Ghost images.  Every ghost element depends on one interior cell (its
+//     source), so the warp that converts a tile then writes the ghosts whose
+//     source lies in that tile (per-tile lists gh_start / gh_idx, built at
+//     set-up from the ghost rule), one ghost cell per lane; the other border
+//     tiles (gh_tiles, items after the list) write theirs at once, their
+//     sources being final when the stream kernel ends.  No warp waits for
+//     another.  (A lattice's planes at a cell outside every work tile are read
+//     by no cell of that lattice, so their stale copies are never used.)
+template <int NL, int NH, class S, class R>
+__global__ void __launch_bounds__(kPostWarps * 32, post_blocks<S>())
+k_post_step_warp(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ flag_old,
+            const uint8_t* __restrict__ flag_new, const BcDev bc, const int* __restrict__ work,
+            const int* __restrict__ list, const int* __restrict__ nlist, int ntx,
+            const int* __restrict__ gh_start, const int* __restrict__ gh_idx,
+            const int* __restrict__ gh_tiles, int n_ghtiles) {
+  const int lane = threadIdx.x & 31;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ++*p.seed_ctr;  // the next stream launch rounds with a new key
+  // every index read from the stream kernel's outputs is checked before it
+  // addresses anything: the count against the list's capacity, each entry
+  // against the tile count (a tile is listed at most once per step, so a
+  // valid list never exceeds either)
+  const int ntiles = ntx * ((p.ny + kTY - 1) / kTY);
+  const int nl = min(max(*nlist, 0), ntiles);
+  const int total = nl + n_ghtiles;
+  for (;;) {
+    // the next item, taken by lane 0 from the item counter (zeroed by the
+    // stream kernel): tiles of uneven cost even out over the warps
+    int r = 0;
+    if (lane == 0) r = atomicAdd(p.sched + 2, 1);
+    r = __shfl_sync(0xffffffffu, r, 0);
+    if (r >= total) break;
+    int t;
+    if (r < nl) {
+      t = list[r];
+      if (t < 0 || t >= ntiles || !post_work_word(work[t])) continue;  // warp-uniform
+      warp_convert<NL, NH, S, R>(p, f0, f1, flag_old, flag_new, (t % ntx) * kTX, (t / ntx) * kTY);
+      __syncwarp();  // the tile's conversions are visible to the warp's ghost writes
+    } else {
+      t = gh_tiles[r - nl];
+      if (post_work_word(work[t])) continue;  // written after its conversion
+    }
+    const int g0 = gh_start[t], g1 = gh_start[t + 1];
+    for (int g = g0 + lane; g < g1; g += 32)
+      lane_ghost<NL, NH, S, R>(p, f0, f1, flag_new, bc, gh_idx[g]);
+  }
+}
+
+// Launch cache of the per-step kernel's occupancy, per instantiation and device.
+struct PostLaunchCache {
+  std::mutex mu;
+  int per_sm[64] = {};
+};
+
 template <class S, class R>
 cudaError_t launch_post_step_impl(const Params<R>& p, S* f0, S* f1, const uint8_t* flag_old,
                                   const uint8_t* flag_new, const BcDev& bc, const int* work,
@@ -416,18 +715,50 @@ cudaError_t launch_post_step_impl(const Params<R>& p, S* f0, S* f1, const uint8_
                                   cudaStream_t st) {
   const int ntx = (p.nx + kTX - 1) / kTX;
   const int nl = p.lat[0].n, nh = p.lat[1].n;
-  const dim3 blk(kTX, kTY);
-  // items are taken by stride; four CTAs fit per SM, and a small grid needs no
-  // more CTAs than it can have items (list entries + border tiles), which
-  // leaves the GPU to concurrent launches of other handles
   const int nty = (p.ny + kTY - 1) / kTY;
-  const int items = ntx * nty + gt.ntiles;
-  const int grid = items < 4 * p.nsm ? items : 4 * p.nsm;
+  const long long items = (long long)ntx * nty + gt.ntiles;
+  if (!p.post_warp) {
+    // one CTA per item; four CTAs fit per SM, and a small grid needs no more
+    // CTAs than it can have items (list entries + border tiles), which leaves
+    // the GPU to concurrent launches of other handles
+    const int grid = (int)(items < 4LL * p.nsm ? items : 4LL * p.nsm);
 #define SLBM_POSTSTEP_CASE(NL, NH)                                                          \
   if (nl == NL && nh == NH) {                                                               \
-    k_post_step<NL, NH, S, R><<<grid, blk, 0, st>>>(p, f0, f1, flag_old, flag_new, bc, work, \
-                                                     list, nlist, ntx, gt.start, gt.idx,     \
-                                                     gt.tiles, gt.ntiles);                   \
+    k_post_step_block<NL, NH, S, R><<<grid > 0 ? grid : 1, dim3(kTX, kTY), 0, st>>>(        \
+        p, f0, f1, flag_old, flag_new, bc, work, list, nlist, ntx, gt.start, gt.idx,         \
+        gt.tiles, gt.ntiles);                                                               \
+    return cudaGetLastError();                                                              \
+  }
+    SLBM_POSTSTEP_CASE(3, 4)
+    SLBM_POSTSTEP_CASE(3, 5)
+    SLBM_POSTSTEP_CASE(4, 5)
+#undef SLBM_POSTSTEP_CASE
+    return cudaErrorInvalidValue;
+  }
+  // one warp per item: as many warps as fit the GPU at once, and no more than
+  // there can be items
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+#define SLBM_POSTSTEP_CASE(NL, NH)                                                          \
+  if (nl == NL && nh == NH) {                                                               \
+    auto kern = k_post_step_warp<NL, NH, S, R>;                                             \
+    static PostLaunchCache cache;                                                           \
+    int per_sm = 0;                                                                         \
+    {                                                                                       \
+      std::lock_guard<std::mutex> lock(cache.mu);                                           \
+      if (cache.per_sm[dev] < 1) {                                                          \
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(                \
+            &cache.per_sm[dev], kern, kPostWarps * 32, 0);                                  \
+        if (e != cudaSuccess) return e;                                                     \
+      }                                                                                     \
+      per_sm = cache.per_sm[dev];                                                           \
+    }                                                                                       \
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;                                   \
+    const long long want = (items + kPostWarps - 1) / kPostWarps;                           \
+    const int grid = (int)(want < (long long)per_sm * p.nsm ? want : (long long)per_sm * p.nsm); \
+    kern<<<grid > 0 ? grid : 1, kPostWarps * 32, 0, st>>>(p, f0, f1, flag_old, flag_new, bc,  \
+                                                          work, list, nlist, ntx, gt.start,  \
+                                                          gt.idx, gt.tiles, gt.ntiles);      \
     return cudaGetLastError();                                                              \
   }
   SLBM_POSTSTEP_CASE(3, 4)

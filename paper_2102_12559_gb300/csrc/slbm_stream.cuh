@@ -386,6 +386,7 @@ k_stream_collide(const Params<R> p, const S* __restrict__ fin0, const S* __restr
   const int ntiles = ntx * nty;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     p.sched[p.sched_parity ^ 1] = 0;
+    p.sched[2] = 0;                    // the post-step kernel's item counter, used after this launch
     p.wcount[p.sched_parity ^ 1] = 0;  // the other work list, likewise
   }
   const uint32_t seed = *p.seed_ctr;  // FP16 rounding key of this step

@@ -60,9 +60,8 @@ def _setup(NY):
     return x0, nx, (rho, ux, uy), flags, subs
 
 
-@pytest.fixture(scope="module", params=NYS)
-def oracle_runs(request):
-    NY = request.param
+def single_channel_runs(NY):
+    """Moments of every channel run alone by the oracle (20 steps)."""
     x0, nx, fields, flags, subs = _setup(NY)
     out = []
     for c, (w, (r, u, v, fl)) in enumerate(zip(WIDTHS, subs)):
@@ -74,6 +73,11 @@ def oracle_runs(request):
         o.step(20)
         out.append(o.moments())
     return NY, out
+
+
+@pytest.fixture(scope="module", params=NYS)
+def oracle_runs(request):
+    return single_channel_runs(request.param)
 
 
 @pytest.mark.parametrize("precision,tol", [(slbm.SLBM_FP64, 1e-11), (slbm.SLBM_FP32, 1e-5)])
