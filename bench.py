@@ -606,6 +606,14 @@ def headline(args):
         moms[name] = (r.moments(), fl)
         r.close()
     ref, ref_fl = moms["fp64"]
+    # the refinement-independent reference: D2Q25 everywhere, FP64
+    r = slbm.Solver(VN, VN, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=VTAU, interp_order=3,
+                    precision=slbm.SLBM_FP64, stream=stream)
+    r.init_equilibrium(*fields)
+    r.set_flags(np.ones((VN, VN), np.uint8))
+    r.step(PARITY_STEPS)
+    ref_hi = r.moments()
+    r.close()
 
     def arm_line(name, ms, kern):
         m, fl = moms[name]
@@ -614,6 +622,7 @@ def headline(args):
                 "kernels_ms_per_step": dict(zip(slbm.KERNEL_NAMES, kern)),
                 "rel_l2_vs_fp64_at_200_steps": mom_gap(m[:3], ref[:3]),
                 "rel_l2_vs_fp32_at_200_steps": mom_gap(m[:3], moms["fp32"][0][:3]),
+                "rel_l2_vs_all_d2q25_fp64_at_200_steps": mom_gap(m[:3], ref_hi[:3]),
                 "flags_agree_with_fp64_run": float(np.mean(fl == ref_fl)),
                 "high_order_fraction_at_200_steps": float(fl.mean())}
 
@@ -651,6 +660,9 @@ def headline(args):
                                  form="FP16 storage of f_i - W_i, Mach criterion every step"),
         "indicator": {"training": ind_train, "on_this_field": ind_vortex},
         "fp32_parity": {"rel_l2_vs_fp64_at_200_steps": mom_gap(moms["fp32"][0][:3], ref[:3]),
+                        "rel_l2_vs_all_d2q25_fp64_at_200_steps": mom_gap(moms["fp32"][0][:3],
+                                                                          ref_hi[:3]),
+                        "fp64_mach_run_vs_all_d2q25_fp64": mom_gap(ref[:3], ref_hi[:3]),
                         "flags_agree_with_fp64_run": float(np.mean(moms["fp32"][1] == ref_fl)),
                         "reference": "FP64 build of the library (at 1e-11 parity with the FP64 "
                                      "oracle), Mach criterion every step, 200 steps"},
@@ -724,6 +736,35 @@ def run_study(args):
                                     for i, k in enumerate(slbm.KERNEL_NAMES)},
             "stream_collide_gbs": bytes_sc / (sc_ms * 1e-3) / 1e9}), flush=True)
         g.close()
+        return
+    if args.workload == "indicator":
+        # the learned indicator on the headline's field (FP16 storage): its
+        # GPU training, then steps with the indicator re-flagging every 10
+        # steps against the same steps with the flags held fixed; the
+        # difference is the evaluations' cost (features, network, conversions)
+        n = args.size
+        count = max(1, VCOUNT * n * n // (VN * VN))
+        fields = WL.random_vortex_field(n, count, seed=VSEED, rmin=VRMIN, rmax=VRMAX, umax=VUMAX)
+        t0 = time.time()
+        weights, rep = train_indicator(slbm, WL, stream)
+        train_s = time.time() - t0
+        out = {}
+        for mode in ("indicator", "fixed"):
+            g = slbm.Solver(n, n, slbm.SLBM_D2Q9, slbm.SLBM_D2Q25, tau=VTAU, interp_order=3,
+                            precision=slbm.SLBM_FP16, stream=stream)
+            g.init_equilibrium(*fields)
+            g.set_indicator(weights, interval=10)
+            g.set_criterion(slbm.SLBM_CRIT_MLP, 0.0)
+            if mode == "fixed":
+                g.set_criterion(slbm.SLBM_CRIT_NONE, 0.0)
+            out[mode] = time_steps(g, stream, args.steps, args.warmup)
+            g.close()
+        print(json.dumps({
+            "study": "learned indicator on the random-vortex field (FP16 storage)", "n": n,
+            "steps": args.steps, "ms_per_step_with_indicator": out["indicator"],
+            "ms_per_step_fixed_flags": out["fixed"],
+            "ms_per_evaluation": (out["indicator"] - out["fixed"]) * 10,
+            "training_wall_s": train_s, "training": rep}), flush=True)
         return
     if args.workload == "jet":
         # the free jet 1024 x 512 (FP32, Mach criterion every step): per-step
@@ -988,7 +1029,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=E2E_STEPS,
                     help="steps of the end-to-end measurement (default: the field's horizon)")
     ap.add_argument("--workload", default="vortex4096",
-                    choices=["vortex4096", "vortex-fp32", "jet", "strip", "pond", "shock",
+                    choices=["vortex4096", "vortex-fp32", "indicator", "jet", "strip", "pond", "shock",
                              "couette"],
                     help="vortex4096: the headline line; the others: secondary studies")
     args = ap.parse_args()
