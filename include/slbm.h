@@ -435,8 +435,11 @@ SLBM_API int slbm_set_viscosity_law(slbm_t h, const double *mu1, const double *T
  * states' density beyond the ends) and the local hard-sphere mean free path
  * lambda = 16 / (5 sqrt(2 pi gamma)) mu a / p (mu from the row's law,
  * a = sqrt(gamma T), p = rho T, gamma = (C_v + 1) / C_v).  Applied at once and
- * after every `interval` steps of slbm_step; flipped cells are lifted or
- * projected as by slbm_set_flags. */
+ * after every `interval` steps of slbm_step, refinement only (a cell once
+ * high-order stays so: Sec. IV.C initialises the shock on the low-order lattice
+ * and refines it; cells switched back and forth at the shock's edges make the
+ * nearly collisionless hybrid lose positivity); refined cells are lifted as
+ * by slbm_set_flags. */
 SLBM_API int slbm_set_kn_criterion(slbm_t h, double thr, int interval);
 
 /* Per-kernel timing (tracing).  slbm_profile(h, 1) clears previous records

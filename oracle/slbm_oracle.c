@@ -1069,7 +1069,7 @@ static void apply_kn(orc_t *s)
             double mu = s->mu1 * pow(T[c] / s->T1, s->s_exp);
             double lam = 16.0 / (5.0 * sqrt(2.0 * 3.14159265358979323846 * gam)) * mu * sqrt(gam * T[c]) / (rho[c] * T[c]);
             double kn = lam * fabs(drdx) / rho[c];
-            fl[c] = kn > s->kn_thr ? 1 : 0;
+            fl[c] = (kn > s->kn_thr || s->flag[c]) ? 1 : 0;   /* refinement only */
         }
     orc_set_flags(s, fl);
     free(rho); free(T); free(fl);
@@ -1316,7 +1316,12 @@ int orc_set_viscosity_law(orc_t *s, double mu1, double T1, double s_exp, double 
 }
 
 /* Knudsen refinement criterion (apply_kn) every `interval` steps, and at once;
- * needs the viscosity law and fixed end states. */
+ * needs the viscosity law and fixed end states.  Refinement only (Sec. IV.C:
+ * the shock is initialised on the low-order lattice and refined): a cell with
+ * Kn > thr becomes high-order and stays so.  A criterion that also coarsens
+ * switches cells at the shock's edges back and forth, and in this nearly
+ * collisionless regime (tau ~ 110 upstream) the hybrid then loses positivity
+ * within 20 steps at Mach 1.6. */
 int orc_set_kn_criterion(orc_t *s, double thr, int interval)
 {
     if (!s->hs || !s->ends_set || interval < 1 || !(thr > 0.0)) return -1;

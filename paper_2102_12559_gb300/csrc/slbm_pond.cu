@@ -748,7 +748,8 @@ __device__ __forceinline__ void cell_rho_T(const PondParams<R>& p, const PondLat
 // L = |rho / (d rho / dx)| by central differences (the end states' density
 // beyond the ends), lambda = 16 / (5 sqrt(2 pi gamma)) mu a / p of hard
 // spheres with the row's viscosity law, a = sqrt(gamma T), p = rho T; the new
-// flag is Kn > thr (cells beyond the instance keep theirs).
+// flag is Kn > thr or the old flag (refinement only: a cell once high-order
+// stays so; cells beyond the instance keep theirs).
 template <int NL, int NH, class S, class R>
 __global__ void __launch_bounds__(kThreads)
 k_pond_kn(const PondParams<R> p, const S* __restrict__ f0, const S* __restrict__ f1,
@@ -780,7 +781,7 @@ k_pond_kn(const PondParams<R> p, const S* __restrict__ f0, const S* __restrict__
   const R lmf = R(16) / (R(5) * sqrt(R(2) * R(3.14159265358979323846) * gam)) * mu *
                 sqrt(gam * T) / (rho * T);
   const R kn = lmf * fabs(R(0.5) * (rr - rl)) / rho;
-  out[c] = kn > thr ? 1 : 0;
+  out[c] = (kn > thr || flag[c]) ? 1 : 0;
 }
 
 // Plane i of lattice k's g planes to / from absolute g (cell-major doubles).

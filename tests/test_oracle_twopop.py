@@ -291,3 +291,65 @@ def test_knudsen_criterion_against_the_mean_free_path(L, refined):
     u.set_kn_criterion(0.02, 1)
     u.step(2)
     assert u.get_flags().sum() == 0
+
+
+def test_knudsen_refined_shock_stays_positive():
+    """The paper's shock case (Sec. IV.C: Mach 1.6, lambda_1 = 50 cells,
+    initialised on D2Q16 and refined to D2Q25 where Kn > 0.02): with the
+    criterion refining only, the cells once high-order stay so and rho, T stay
+    positive and within 10 % of the Rankine-Hugoniot range for 100 steps.  The
+    same run coarsening cells again where Kn drops below the threshold (flags
+    recomputed from scratch every step) loses positivity within 40 steps: in
+    this nearly collisionless regime (tau ~ 110 upstream) cells switched back
+    and forth at the shock's edges are what breaks it.  1024 cells, so that
+    the initial ramp (two mean free paths wide) meets the fixed end states
+    without a jump that the criterion would refine; at 640 cells the upstream
+    end is refined at once and the run loses positivity next to it after 56
+    steps."""
+    nx, gamma, thr = 1024, 5.0 / 3.0, 0.02
+    inst = WL.shock_batch(1, seed=1, mach_range=(1.6, 1.6), len_range=(nx, nx))[0]
+    rho, ux, T = (a[None, :] for a in WL.shock_profile(inst, nx, width=100.0))
+    (r1, u1, t1), (r2, u2, t2) = inst["left"], inst["right"]
+
+    def make():
+        o = O.Oracle(nx, 1, 4, 5, tau=0.7, frame=O.FRAME_POND, periodic=(False, True))
+        o.set_twopop(1.5, 0.8)
+        o.set_pond_ends((r1, u1, 0.0, t1), (r2, u2, 0.0, t2))
+        o.set_viscosity_law(inst["mu1"], inst["T1"], 0.5, 2 / 3)
+        o.init_equilibrium(rho, ux, 0 * rho, T)
+        return o
+
+    def positive(o):
+        r, _, _, TT = o.moments()
+        return np.isfinite(r).all() and (r > 0).all() and np.isfinite(TT).all() and (TT > 0).all()
+
+    o = make()
+    o.set_kn_criterion(thr, 1)
+    prev = o.get_flags()
+    assert prev.sum() > 0
+    for _ in range(100):
+        o.step(1)
+        fl = o.get_flags()
+        assert (fl >= prev).all()
+        prev = fl
+        assert positive(o)
+    r = o.moments()[0]
+    assert r.min() > 0.9 * r1 and r.max() < 1.1 * r2
+
+    def kn_flags(o):
+        r, _, _, TT = o.moments()
+        r, TT = r[0], TT[0]
+        mu = inst["mu1"] * (TT / inst["T1"]) ** 0.5
+        lam = 16 / (5 * np.sqrt(2 * np.pi * gamma)) * mu * np.sqrt(gamma * TT) / (r * TT)
+        rp = np.concatenate([[r1], r, [r2]])
+        return (lam * np.abs(0.5 * (rp[2:] - rp[:-2])) / r > thr).astype(np.uint8)[None, :]
+
+    o = make()
+    broke = None
+    for s in range(40):
+        o.set_flags(kn_flags(o))
+        o.step(1)
+        if not positive(o):
+            broke = s + 1
+            break
+    assert broke is not None
