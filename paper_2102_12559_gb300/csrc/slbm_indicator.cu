@@ -38,14 +38,14 @@ __device__ void cell_features_n(const Params<R>& p, const LatTab<R>& L, const S*
                                 const uint8_t* flag, const R* mrho, const R* mux, const R* muy,
                                 float* out) {
   const size_t base = (size_t)(y + p.G) * p.pitch + (x + kOX);
-  R s[N * N];
+  // two passes over the populations (moments, then the non-equilibrium sums;
+  // the second reads them again from L1) instead of N^2 registers
   R dr = R(0), jx = R(0), jy = R(0), e2 = R(0);
 #pragma unroll
   for (int iy = 0; iy < N; ++iy)
 #pragma unroll
     for (int ix = 0; ix < N; ++ix) {
       const R v = static_cast<R>(f[(size_t)(ix + N * iy) * p.plane + base]);
-      s[ix + N * iy] = v;
       dr += v;
       jx += L.c[ix] * v;
       jy += L.c[iy] * v;
@@ -65,7 +65,7 @@ __device__ void cell_features_n(const Params<R>& p, const LatTab<R>& L, const S*
     for (int ix = 0; ix < N; ++ix) {
       const R px = L.w1[ix] + dx[ix];
       const R e = dr * px * py + L.w1[ix] * dy[iy] + dx[ix] * py;
-      const R ne = s[ix + N * iy] - e;
+      const R ne = static_cast<R>(f[(size_t)(ix + N * iy) * p.plane + base]) - e;
       const R cx = L.c[ix], cy = L.c[iy], c2 = cx * cx + cy * cy;
       pxx += cx * cx * ne;
       pxy += cx * cy * ne;
@@ -105,17 +105,12 @@ __device__ void cell_features_n(const Params<R>& p, const LatTab<R>& L, const S*
   for (int q = 0; q < kFeat; ++q) out[q] *= c_scale[q];
 }
 
-template <class S, class R>
+template <int NL, int NH, class S, class R>
 __device__ void cell_features(const Params<R>& p, const S* f0, const S* f1, int k, int x, int y,
                               const uint8_t* flag, const R* mrho, const R* mux, const R* muy,
                               float* out) {
-  const LatTab<R>& L = p.lat[k];
-  const S* f = k ? f1 : f0;
-  switch (L.n) {
-    case 3: cell_features_n<3, S, R>(p, L, f, x, y, flag, mrho, mux, muy, out); break;
-    case 4: cell_features_n<4, S, R>(p, L, f, x, y, flag, mrho, mux, muy, out); break;
-    default: cell_features_n<5, S, R>(p, L, f, x, y, flag, mrho, mux, muy, out); break;
-  }
+  if (k) cell_features_n<NH, S, R>(p, p.lat[1], f1, x, y, flag, mrho, mux, muy, out);
+  else cell_features_n<NL, S, R>(p, p.lat[0], f0, x, y, flag, mrho, mux, muy, out);
 }
 
 // rho, u_x, u_y of one cell from its own lattice, in the arithmetic type
@@ -200,7 +195,7 @@ __device__ __forceinline__ void bfrag(const __half* W, int ncols, int k0, int nt
 // then runs the MLP with the C fragments of one layer reused in registers as
 // the A fragments of the next.  Outputs (any may be null): FP32 features
 // (nc x 16, cell-major), logits, flags (logit > thr).
-template <class S, class R>
+template <int NL, int NH, class S, class R>
 __global__ void __launch_bounds__(kIndThreads)
 k_indicator(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restrict__ flag,
             const R* __restrict__ mrho, const R* __restrict__ mux,
@@ -208,7 +203,7 @@ k_indicator(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restri
             const float* __restrict__ b1, const __half* __restrict__ w2,
             const float* __restrict__ b2, const float* __restrict__ w3, float b3, float thr,
             float* feat_out, float* logit_out, uint8_t* flag_out) {
-  __shared__ __half sfeat[kIndThreads / 32][32][kFeat + 2];
+  __shared__ __align__(16) __half sfeat[kIndThreads / 32][32][kFeat + 2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
   const long long nc = (long long)p.nx * p.ny;
@@ -232,7 +227,7 @@ k_indicator(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restri
     const int fc = c < nc ? flag[c] : (int)kFlagGap;
     if (fc != kFlagGap) {
       const int x = (int)(c % p.nx), y = (int)(c / p.nx);
-      cell_features<S, R>(p, f0, f1, fc, x, y, flag, mrho, mux, muy, fe);
+      cell_features<NL, NH, S, R>(p, f0, f1, fc, x, y, flag, mrho, mux, muy, fe);
     }
     if (c < nc) {
       if (feat_out)
@@ -240,17 +235,19 @@ k_indicator(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restri
         for (int q = 0; q < kFeat; ++q) feat_out[c * kFeat + q] = fe[q];
     }
 #pragma unroll
-    for (int q = 0; q < kFeat; ++q) sfeat[warp][lane][q] = __float2half_rn(fe[q]);
+    for (int q = 0; q < kFeat; q += 2)  // in pairs: 4-byte shared stores
+      *reinterpret_cast<__half2*>(&sfeat[warp][lane][q]) = __floats2half2_rn(fe[q], fe[q + 1]);
     __syncwarp();
     if (have_w) {
 #pragma unroll
       for (int mt = 0; mt < 2; ++mt) {
         const int r0 = 16 * mt + g, r1 = r0 + 8;
         uint32_t A[4];
-        A[0] = pack2(sfeat[warp][r0][2 * t], sfeat[warp][r0][2 * t + 1]);
-        A[1] = pack2(sfeat[warp][r1][2 * t], sfeat[warp][r1][2 * t + 1]);
-        A[2] = pack2(sfeat[warp][r0][2 * t + 8], sfeat[warp][r0][2 * t + 9]);
-        A[3] = pack2(sfeat[warp][r1][2 * t + 8], sfeat[warp][r1][2 * t + 9]);
+        // pairs of features as 4-byte loads (rows of 18 halves keep them aligned)
+        A[0] = *reinterpret_cast<const uint32_t*>(&sfeat[warp][r0][2 * t]);
+        A[1] = *reinterpret_cast<const uint32_t*>(&sfeat[warp][r1][2 * t]);
+        A[2] = *reinterpret_cast<const uint32_t*>(&sfeat[warp][r0][2 * t + 8]);
+        A[3] = *reinterpret_cast<const uint32_t*>(&sfeat[warp][r1][2 * t + 8]);
         // layer 1: 16 -> 32, ReLU
         float H1[4][4];
 #pragma unroll
@@ -707,10 +704,19 @@ cudaError_t launch_indicator(const Params<R>& p, const S* f0, const S* f1, const
   long long blocks = (nc + kIndThreads - 1) / kIndThreads;
   const long long cap = (long long)p.nsm * 16;
   if (blocks > cap) blocks = cap;
-  k_indicator<S, R><<<(unsigned)blocks, kIndThreads, 0, st>>>(
-      p, f0, f1, flag, mrho, mux, muy, w.w1, w.b1, w.w2, w.b2, w.w3, w.b3, thr, feat_out,
-      logit_out, flag_out);
-  return cudaGetLastError();
+  const int nl = p.lat[0].n, nh = p.lat[1].n;
+#define SLBM_IND_CASE(NL, NH)                                                                 \
+  if (nl == NL && nh == NH) {                                                                 \
+    k_indicator<NL, NH, S, R><<<(unsigned)blocks, kIndThreads, 0, st>>>(                      \
+        p, f0, f1, flag, mrho, mux, muy, w.w1, w.b1, w.w2, w.b2, w.w3, w.b3, thr, feat_out,    \
+        logit_out, flag_out);                                                                 \
+    return cudaGetLastError();                                                                \
+  }
+  SLBM_IND_CASE(3, 4)
+  SLBM_IND_CASE(3, 5)
+  SLBM_IND_CASE(4, 5)
+#undef SLBM_IND_CASE
+  return cudaErrorInvalidValue;
 }
 
 template <class S, class R>
