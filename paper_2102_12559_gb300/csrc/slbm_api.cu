@@ -980,17 +980,14 @@ bool create_args_ok(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int 
   return true;
 }
 
-// Evaluate the learned indicator on the current state: moment planes into
-// the macro slots, then features + MLP; features / logits / flags to the given
-// device buffers (any may be null).
+// Evaluate the learned indicator on the current state (features + MLP);
+// features / logits / flags to the given device buffers (any may be null).
 int run_indicator(slbm_s* h, float* feat, float* logit, uint8_t* flags_out) {
-  double* d[3];  // scratch for the moment planes (nc values of the arithmetic type each)
-  for (int m = 0; m < 3; ++m) d[m] = h->at<double>(h->lay.macro[m]);
   cudaError_t e = with_types(h, [&](auto ty, const auto& prm) {
     SLBM_TYPES(ty);
     return launch_indicator<S, R>(prm, (const S*)h->pops(h->cur, 0), (const S*)h->pops(h->cur, 1),
-                                  h->flags(h->fcur), (R*)d[0], (R*)d[1], (R*)d[2], h->ind,
-                                  (float)h->ind_thr, feat, logit, flags_out, h->st);
+                                  h->flags(h->fcur), h->ind, (float)h->ind_thr, feat, logit,
+                                  flags_out, h->st);
   });
   SLBM_CK(h, e, "indicator launch");
   return SLBM_OK;

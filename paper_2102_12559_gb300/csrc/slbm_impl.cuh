@@ -241,15 +241,13 @@ struct IndicatorDev {
   float b3;
 };
 
-// Learned indicator on the current buffer: the moment planes rho, u_x, u_y
-// in the arithmetic type (mrho, mux, muy: nc values each, overwritten), then
-// features and the MLP; features (nc x 16 FP32), logits and flags (logit >
-// thr) to any of the non-null outputs.
+// Learned indicator on the current buffer: features and the MLP in one
+// launch; features (nc x 16 FP32), logits and flags (logit > thr) to any of
+// the non-null outputs.
 template <class S, class R>
 cudaError_t launch_indicator(const Params<R>& p, const S* f0, const S* f1, const uint8_t* flag,
-                             R* mrho, R* mux, R* muy, const IndicatorDev& w, float thr,
-                             float* feat_out, float* logit_out, uint8_t* flag_out,
-                             cudaStream_t st);
+                             const IndicatorDev& w, float thr, float* feat_out, float* logit_out,
+                             uint8_t* flag_out, cudaStream_t st);
 
 // Refinement buffer along one axis (0 = x, 1 = y) of radius r: see k_dilate.
 cudaError_t launch_dilate(const uint8_t* in, const uint8_t* keep, uint8_t* out, int nx, int ny,

@@ -21,7 +21,10 @@ namespace {
 
 constexpr int kFeat = 16;
 constexpr int kHid = 32;
-constexpr int kIndThreads = 128;  // 4 warps, 32 cells per warp per pass
+// one tile of 32 x 16 cells per block pass; 8 warps, each two rows of 32
+constexpr int kIndTX = 32, kIndTY = 16;
+constexpr int kIndWarps = 8, kIndThreads = 32 * kIndWarps;
+constexpr int kHaloX = kIndTX + 2, kHaloY = kIndTY + 2;
 
 __constant__ float c_scale[kFeat] = {10.f,  3.f,   3.f,   10.f,  100.f, 100.f, 100.f, 100.f,
                                      100.f, 100.f, 100.f, 100.f, 100.f, 100.f, 100.f, 3.f};
@@ -32,59 +35,69 @@ __device__ __forceinline__ int clampwrap(int v, int n, int periodic) {
   return v;
 }
 
-// Features of cell (x, y) from its own lattice (N nodes per axis).
-template <int N, class S, class R>
-__device__ void cell_features_n(const Params<R>& p, const LatTab<R>& L, const S* f, int x, int y,
-                                const uint8_t* flag, const R* mrho, const R* mux, const R* muy,
-                                float* out) {
-  const size_t base = (size_t)(y + p.G) * p.pitch + (x + kOX);
-  // two passes over the populations (moments, then the non-equilibrium sums;
-  // the second reads them again from L1) instead of N^2 registers
-  R dr = R(0), jx = R(0), jy = R(0), e2 = R(0);
+// Raw moments of one cell's stored deviations v_i = f_i - W_i on its own
+// lattice (N nodes per axis), M_ab = sum_i c_ix^a c_iy^b v_i, in one pass over
+// the populations by row sums r_a(iy) = sum_ix c_ix^a v_i:
+//   M[0..2] = M_00, M_10, M_01;  with FULL also
+//   M[3..9] = M_20, M_11, M_02, M_30, M_21, M_12, M_03.
+template <int N, bool FULL, class S, class R>
+__device__ __forceinline__ void raw_moments(const Params<R>& p, const LatTab<R>& L, const S* f,
+                                            size_t base, R* M) {
 #pragma unroll
-  for (int iy = 0; iy < N; ++iy)
+  for (int k = 0; k < (FULL ? 10 : 3); ++k) M[k] = R(0);
+#pragma unroll
+  for (int iy = 0; iy < N; ++iy) {
+    R r0 = R(0), r1 = R(0), r2 = R(0), r3 = R(0);
 #pragma unroll
     for (int ix = 0; ix < N; ++ix) {
       const R v = static_cast<R>(f[(size_t)(ix + N * iy) * p.plane + base]);
-      dr += v;
-      jx += L.c[ix] * v;
-      jy += L.c[iy] * v;
-      e2 += (L.c[ix] * L.c[ix] + L.c[iy] * L.c[iy]) * v;
+      const R cx = L.c[ix];
+      r0 += v;
+      r1 += cx * v;
+      if (FULL) {
+        r2 += cx * cx * v;
+        r3 += cx * cx * cx * v;
+      }
     }
-  const R rho = R(1) + dr;
-  const R ux = jx / rho, uy = jy / rho;
-  const R T = ((R(2) + e2) / rho - ux * ux - uy * uy) / R(2);
-  R dx[N], dy[N];
-  dphi<R>(L, N, ux, dx);
-  dphi<R>(L, N, uy, dy);
-  R pxx = R(0), pxy = R(0), pyy = R(0), qx = R(0), qy = R(0);
-#pragma unroll
-  for (int iy = 0; iy < N; ++iy) {
-    const R py = L.w1[iy] + dy[iy];
-#pragma unroll
-    for (int ix = 0; ix < N; ++ix) {
-      const R px = L.w1[ix] + dx[ix];
-      const R e = dr * px * py + L.w1[ix] * dy[iy] + dx[ix] * py;
-      const R ne = static_cast<R>(f[(size_t)(ix + N * iy) * p.plane + base]) - e;
-      const R cx = L.c[ix], cy = L.c[iy], c2 = cx * cx + cy * cy;
-      pxx += cx * cx * ne;
-      pxy += cx * cy * ne;
-      pyy += cy * cy * ne;
-      qx += R(0.5) * cx * c2 * ne;
-      qy += R(0.5) * cy * c2 * ne;
+    const R cy = L.c[iy];
+    M[0] += r0;
+    M[1] += r1;
+    M[2] += cy * r0;
+    if (FULL) {
+      M[3] += r2;
+      M[4] += cy * r1;
+      M[5] += cy * cy * r0;
+      M[6] += r3;
+      M[7] += cy * r2;
+      M[8] += cy * cy * r1;
+      M[9] += cy * cy * cy * r0;
     }
   }
-  const int xm = clampwrap(x - 1, p.nx, p.periodic_x), xp = clampwrap(x + 1, p.nx, p.periodic_x);
-  const int ym = clampwrap(y - 1, p.ny, p.periodic_y), yp = clampwrap(y + 1, p.ny, p.periodic_y);
-  const long long c = x + (long long)p.nx * y;
-  // a gap neighbour (the wall side of a channel) counts as the edge: the cell
-  // itself is repeated, as at a non-periodic side
-  long long cxm = xm + (long long)p.nx * y, cxp = xp + (long long)p.nx * y;
-  long long cym = x + (long long)p.nx * ym, cyp = x + (long long)p.nx * yp;
-  if (flag[cxm] == kFlagGap) cxm = c;
-  if (flag[cxp] == kFlagGap) cxp = c;
-  if (flag[cym] == kFlagGap) cym = c;
-  if (flag[cyp] == kFlagGap) cyp = c;
+}
+
+// Features 0-8 and 15 from the raw moments (FULL set) of a cell on a lattice
+// of N nodes per axis.  The moments of f^L - W follow from the product form
+// f^L = rho phi_x phi_y: with H_a(u) = sum_j c_j^a phi_j(u) = mu_a + d_a(u),
+// mu = (1, 0, 1, 0) the moments of the weights (T_L = 1),
+//   sum_i c_ix^a c_iy^b (f^L - W)_i = dr mu_a mu_b
+//                                   + rho (mu_a d_b(u_y) + d_a(u_x) mu_b + d_a(u_x) d_b(u_y)),
+// where d_1 = u, d_2 = u^2 (moment conditions, a < N) and d_3 = u^3 + 3 u for
+// N >= 4; on three nodes {0, +-a} c^3 = a^2 c, so d_3 = a^2 u.  The
+// non-equilibrium stress and energy flux are M_ab minus these.
+template <int N, class R>
+__device__ __forceinline__ void moment_features(const LatTab<R>& L, const R* M, float* out) {
+  const R dr = M[0], rho = R(1) + dr;
+  const R ux = M[1] / rho, uy = M[2] / rho;
+  const R ux2 = ux * ux, uy2 = uy * uy;
+  const R a2 = L.c[N - 1] * L.c[N - 1];
+  const R d3x = N >= 4 ? ux * (ux2 + R(3)) : a2 * ux;
+  const R d3y = N >= 4 ? uy * (uy2 + R(3)) : a2 * uy;
+  const R pxx = M[3] - (dr + rho * ux2);
+  const R pxy = M[4] - rho * ux * uy;
+  const R pyy = M[5] - (dr + rho * uy2);
+  const R qx = R(0.5) * ((M[6] - rho * d3x) + (M[8] - rho * ux * (R(1) + uy2)));
+  const R qy = R(0.5) * ((M[7] - rho * uy * (R(1) + ux2)) + (M[9] - rho * d3y));
+  const R T = ((R(2) + M[3] + M[5]) / rho - ux2 - uy2) / R(2);
   out[0] = (float)dr;
   out[1] = (float)ux;
   out[2] = (float)uy;
@@ -94,73 +107,25 @@ __device__ void cell_features_n(const Params<R>& p, const LatTab<R>& L, const S*
   out[6] = (float)pyy;
   out[7] = (float)qx;
   out[8] = (float)qy;
-  out[9] = (float)(R(0.5) * (mrho[cxp] - mrho[cxm]));
-  out[10] = (float)(R(0.5) * (mrho[cyp] - mrho[cym]));
-  out[11] = (float)(R(0.5) * (mux[cxp] - mux[cxm]));
-  out[12] = (float)(R(0.5) * (mux[cyp] - mux[cym]));
-  out[13] = (float)(R(0.5) * (muy[cxp] - muy[cxm]));
-  out[14] = (float)(R(0.5) * (muy[cyp] - muy[cym]));
-  out[15] = (float)sqrt(ux * ux + uy * uy);
-#pragma unroll
-  for (int q = 0; q < kFeat; ++q) out[q] *= c_scale[q];
+  out[15] = (float)sqrt(ux2 + uy2);
 }
 
-template <int NL, int NH, class S, class R>
-__device__ void cell_features(const Params<R>& p, const S* f0, const S* f1, int k, int x, int y,
-                              const uint8_t* flag, const R* mrho, const R* mux, const R* muy,
-                              float* out) {
-  if (k) cell_features_n<NH, S, R>(p, p.lat[1], f1, x, y, flag, mrho, mux, muy, out);
-  else cell_features_n<NL, S, R>(p, p.lat[0], f0, x, y, flag, mrho, mux, muy, out);
-}
-
-// rho, u_x, u_y of one cell from its own lattice, in the arithmetic type
-// (the values the gradient features difference).
-template <int N, class S, class R>
-__device__ __forceinline__ void cell_ru(const Params<R>& p, const LatTab<R>& L, const S* f,
-                                        size_t base, R* out) {
-  R dr = R(0), jx = R(0), jy = R(0);
-#pragma unroll
-  for (int iy = 0; iy < N; ++iy)
-#pragma unroll
-    for (int ix = 0; ix < N; ++ix) {
-      const R v = static_cast<R>(f[(size_t)(ix + N * iy) * p.plane + base]);
-      dr += v;
-      jx += L.c[ix] * v;
-      jy += L.c[iy] * v;
-    }
-  const R rho = R(1) + dr;
-  out[0] = rho;
-  out[1] = jx / rho;
-  out[2] = jy / rho;
-}
-
-// Moment planes of the gradient features, one thread per cell.
-template <class S, class R>
-__global__ void __launch_bounds__(kTX * kTY)
-k_ind_moments(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restrict__ flag,
-              R* __restrict__ mrho, R* __restrict__ mux, R* __restrict__ muy) {
-  const int x = blockIdx.x * kTX + threadIdx.x, y = blockIdx.y * kTY + threadIdx.y;
-  if (x >= p.nx || y >= p.ny) return;
-  const long long c = x + (long long)p.nx * y;
-  const int k = flag[c];
-  if (k == kFlagGap) {  // no fluid between channels: zero gradients at their walls
-    mrho[c] = R(1);
-    mux[c] = R(0);
-    muy[c] = R(0);
-    return;
-  }
-  const LatTab<R>& L = p.lat[k];
-  const S* f = k ? f1 : f0;
+// Moments of cell (x, y) (FULL or the first three) from its own lattice; a
+// gap cell (no fluid) gets zeros: rho 1, at rest.
+template <int NL, int NH, bool FULL, class S, class R>
+__device__ __forceinline__ int cell_moments(const Params<R>& p, const S* f0, const S* f1,
+                                            const uint8_t* flag, int x, int y, R* M) {
+  const int k = flag[x + (long long)p.nx * y];
   const size_t base = (size_t)(y + p.G) * p.pitch + (x + kOX);
-  R m[3];
-  switch (L.n) {
-    case 3: cell_ru<3, S, R>(p, L, f, base, m); break;
-    case 4: cell_ru<4, S, R>(p, L, f, base, m); break;
-    default: cell_ru<5, S, R>(p, L, f, base, m); break;
+  if (k == kFlagGap) {
+#pragma unroll
+    for (int q = 0; q < (FULL ? 10 : 3); ++q) M[q] = R(0);
+  } else if (k) {
+    raw_moments<NH, FULL, S, R>(p, p.lat[1], f1, base, M);
+  } else {
+    raw_moments<NL, FULL, S, R>(p, p.lat[0], f0, base, M);
   }
-  mrho[c] = m[0];
-  mux[c] = m[1];
-  muy[c] = m[2];
+  return k;
 }
 
 __device__ __forceinline__ uint32_t pack2(__half lo, __half hi) {
@@ -168,8 +133,12 @@ __device__ __forceinline__ uint32_t pack2(__half lo, __half hi) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-__device__ __forceinline__ uint32_t pack2f(float lo, float hi) {
-  return pack2(__float2half_rn(lo), __float2half_rn(hi));
+// {relu(lo), relu(hi)} rounded to FP16 and packed (lo in the low half) by one
+// conversion; the same bits as rounding max(v, 0).
+__device__ __forceinline__ uint32_t pack2_relu(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
 }
 
 // D += A (16 x 16, row-major, FP16) * B (16 x 8, column-major, FP16), FP32.
@@ -190,23 +159,30 @@ __device__ __forceinline__ void bfrag(const __half* W, int ncols, int k0, int nt
   b1 = pack2(W[(k0 + 2 * t + 8) * ncols + n], W[(k0 + 2 * t + 9) * ncols + n]);
 }
 
-// One pass: each warp takes 32 consecutive cells (two m16 tiles).  Lane l
-// computes the features of cell base + l into shared memory (FP16); the warp
-// then runs the MLP with the C fragments of one layer reused in registers as
-// the A fragments of the next.  Outputs (any may be null): FP32 features
-// (nc x 16, cell-major), logits, flags (logit > thr).
+// One tile per block pass.  First the moments of the tile's cells (the full
+// set, kept in registers: each warp owns two rows of 32) and of the one-cell
+// ring around it (periodic wrap, else the edge cell repeated; the ring's slots
+// spread over the warps), with {dr, u_x, u_y} of every slot in shared memory;
+// then per row lane l computes the features of cell x0 + l (gradients from the
+// shared moments, a gap neighbour replaced by the cell itself) into shared
+// memory (FP16), and the warp runs the MLP with the C fragments of one layer
+// reused in registers as the A fragments of the next.  Outputs (any may be
+// null): FP32 features (nc x 16, cell-major), logits, flags (logit > thr).
 template <int NL, int NH, class S, class R>
 __global__ void __launch_bounds__(kIndThreads)
 k_indicator(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restrict__ flag,
-            const R* __restrict__ mrho, const R* __restrict__ mux,
-            const R* __restrict__ muy, const __half* __restrict__ w1,
-            const float* __restrict__ b1, const __half* __restrict__ w2,
-            const float* __restrict__ b2, const float* __restrict__ w3, float b3, float thr,
-            float* feat_out, float* logit_out, uint8_t* flag_out) {
-  __shared__ __align__(16) __half sfeat[kIndThreads / 32][32][kFeat + 2];
+            const __half* __restrict__ w1, const float* __restrict__ b1,
+            const __half* __restrict__ w2, const float* __restrict__ b2,
+            const float* __restrict__ w3, float b3, float thr, float* feat_out,
+            float* logit_out, uint8_t* flag_out) {
+  constexpr int kRing = 2 * kHaloX + 2 * kIndTY;  // 100 slots
+  constexpr int kRows = kIndTY / kIndWarps;        // rows per warp
+  __shared__ R sm[kHaloY][kHaloX][3];
+  __shared__ uint8_t sfl[kHaloY][kHaloX];
+  __shared__ __align__(16) __half sfeat[kIndWarps][32][kFeat + 2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
-  const long long nc = (long long)p.nx * p.ny;
+  const int ntx = (p.nx + kIndTX - 1) / kIndTX, nty = (p.ny + kIndTY - 1) / kIndTY;
   // weights in B-fragment form, held for the whole kernel
   uint32_t B1[4][2], B2[2][4][2];
   const bool have_w = w1 != nullptr;
@@ -218,92 +194,154 @@ k_indicator(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restri
 #pragma unroll
       for (int nt = 0; nt < 4; ++nt) bfrag(w2, kHid, 16 * kk, nt, g, t, B2[kk][nt][0], B2[kk][nt][1]);
   }
-  for (long long base = ((long long)blockIdx.x * (kIndThreads / 32) + warp) * 32; base < nc;
-       base += (long long)gridDim.x * kIndThreads) {
-    const long long c = base + lane;
-    float fe[kFeat];
-#pragma unroll
-    for (int q = 0; q < kFeat; ++q) fe[q] = 0.f;
-    const int fc = c < nc ? flag[c] : (int)kFlagGap;
-    if (fc != kFlagGap) {
-      const int x = (int)(c % p.nx), y = (int)(c / p.nx);
-      cell_features<NL, NH, S, R>(p, f0, f1, fc, x, y, flag, mrho, mux, muy, fe);
+  for (int tile = blockIdx.x; tile < ntx * nty; tile += gridDim.x) {
+    const int x0 = (tile % ntx) * kIndTX, y0 = (tile / ntx) * kIndTY;
+    // the ring: slot j on lane j / 8 of warp j % 8; top and bottom rows, then
+    // the left and right columns.  A slot beyond the grid's last row or
+    // column plus one is read by no cell and is skipped.
+    for (int j = lane * kIndWarps + warp; j < kRing; j += 32 * kIndWarps) {
+      int hx, hy;
+      if (j < 2 * kHaloX) {
+        hx = j % kHaloX;
+        hy = j < kHaloX ? 0 : kHaloY - 1;
+      } else {
+        const int i = j - 2 * kHaloX;
+        hx = i < kIndTY ? 0 : kHaloX - 1;
+        hy = 1 + i % kIndTY;
+      }
+      const int rx = x0 - 1 + hx, ry = y0 - 1 + hy;
+      if (rx > p.nx || ry > p.ny) continue;
+      R m[3];
+      const int k = cell_moments<NL, NH, false, S, R>(p, f0, f1, flag,
+                                                      clampwrap(rx, p.nx, p.periodic_x),
+                                                      clampwrap(ry, p.ny, p.periodic_y), m);
+      sm[hy][hx][0] = m[0];
+      sm[hy][hx][1] = m[1] / (R(1) + m[0]);
+      sm[hy][hx][2] = m[2] / (R(1) + m[0]);
+      sfl[hy][hx] = (uint8_t)k;
     }
-    if (c < nc) {
-      if (feat_out)
+    // the tile's own slots: the full moments stay in registers (a slot one
+    // past the grid's last column or row holds the wrapped or repeated cell)
+    R Mi[kRows][10];
+#pragma unroll
+    for (int rr = 0; rr < kRows; ++rr) {
+      const int ly = warp + rr * kIndWarps;
+      const int rx = x0 + lane, ry = y0 + ly;
+#pragma unroll
+      for (int q = 0; q < 10; ++q) Mi[rr][q] = R(0);
+      if (rx > p.nx || ry > p.ny) continue;
+      const int k = cell_moments<NL, NH, true, S, R>(p, f0, f1, flag,
+                                                     clampwrap(rx, p.nx, p.periodic_x),
+                                                     clampwrap(ry, p.ny, p.periodic_y), Mi[rr]);
+      sm[ly + 1][lane + 1][0] = Mi[rr][0];
+      sm[ly + 1][lane + 1][1] = Mi[rr][1] / (R(1) + Mi[rr][0]);
+      sm[ly + 1][lane + 1][2] = Mi[rr][2] / (R(1) + Mi[rr][0]);
+      sfl[ly + 1][lane + 1] = (uint8_t)k;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rr = 0; rr < kRows; ++rr) {
+      const int ly = warp + rr * kIndWarps;
+      const int x = x0 + lane, y = y0 + ly;
+      const bool in = x < p.nx && y < p.ny;
+      const long long c = x + (long long)p.nx * y;
+      const int hx = lane + 1, hy = ly + 1;
+      const int fc = in ? sfl[hy][hx] : (int)kFlagGap;
+      float fe[kFeat];
+#pragma unroll
+      for (int q = 0; q < kFeat; ++q) fe[q] = 0.f;
+      if (fc != kFlagGap) {
+        if (fc) moment_features<NH, R>(p.lat[1], Mi[rr], fe);
+        else moment_features<NL, R>(p.lat[0], Mi[rr], fe);
+        // central differences; a gap neighbour (the wall side of a channel)
+        // counts as the edge: the cell itself is repeated
+        const R* own = sm[hy][hx];
+        const R* xm = sfl[hy][hx - 1] == kFlagGap ? own : sm[hy][hx - 1];
+        const R* xp = sfl[hy][hx + 1] == kFlagGap ? own : sm[hy][hx + 1];
+        const R* ym = sfl[hy - 1][hx] == kFlagGap ? own : sm[hy - 1][hx];
+        const R* yp = sfl[hy + 1][hx] == kFlagGap ? own : sm[hy + 1][hx];
+        fe[9] = (float)(R(0.5) * (xp[0] - xm[0]));
+        fe[10] = (float)(R(0.5) * (yp[0] - ym[0]));
+        fe[11] = (float)(R(0.5) * (xp[1] - xm[1]));
+        fe[12] = (float)(R(0.5) * (yp[1] - ym[1]));
+        fe[13] = (float)(R(0.5) * (xp[2] - xm[2]));
+        fe[14] = (float)(R(0.5) * (yp[2] - ym[2]));
+#pragma unroll
+        for (int q = 0; q < kFeat; ++q) fe[q] *= c_scale[q];
+      }
+      if (in && feat_out)
 #pragma unroll
         for (int q = 0; q < kFeat; ++q) feat_out[c * kFeat + q] = fe[q];
-    }
 #pragma unroll
-    for (int q = 0; q < kFeat; q += 2)  // in pairs: 4-byte shared stores
-      *reinterpret_cast<__half2*>(&sfeat[warp][lane][q]) = __floats2half2_rn(fe[q], fe[q + 1]);
-    __syncwarp();
-    if (have_w) {
+      for (int q = 0; q < kFeat; q += 2)  // in pairs: 4-byte shared stores
+        *reinterpret_cast<__half2*>(&sfeat[warp][lane][q]) = __floats2half2_rn(fe[q], fe[q + 1]);
+      __syncwarp();
+      if (have_w) {
 #pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        const int r0 = 16 * mt + g, r1 = r0 + 8;
-        uint32_t A[4];
-        // pairs of features as 4-byte loads (rows of 18 halves keep them aligned)
-        A[0] = *reinterpret_cast<const uint32_t*>(&sfeat[warp][r0][2 * t]);
-        A[1] = *reinterpret_cast<const uint32_t*>(&sfeat[warp][r1][2 * t]);
-        A[2] = *reinterpret_cast<const uint32_t*>(&sfeat[warp][r0][2 * t + 8]);
-        A[3] = *reinterpret_cast<const uint32_t*>(&sfeat[warp][r1][2 * t + 8]);
-        // layer 1: 16 -> 32, ReLU
-        float H1[4][4];
+        for (int mt = 0; mt < 2; ++mt) {
+          const int r0 = 16 * mt + g, r1 = r0 + 8;
+          uint32_t A[4];
+          // pairs of features as 4-byte loads (rows of 18 halves keep them aligned)
+          A[0] = *reinterpret_cast<const uint32_t*>(&sfeat[warp][r0][2 * t]);
+          A[1] = *reinterpret_cast<const uint32_t*>(&sfeat[warp][r1][2 * t]);
+          A[2] = *reinterpret_cast<const uint32_t*>(&sfeat[warp][r0][2 * t + 8]);
+          A[3] = *reinterpret_cast<const uint32_t*>(&sfeat[warp][r1][2 * t + 8]);
+          // layer 1: 16 -> 32, ReLU
+          float H1[4][4];
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-          const float ba = b1[8 * nt + 2 * t], bb = b1[8 * nt + 2 * t + 1];
-          H1[nt][0] = ba; H1[nt][1] = bb; H1[nt][2] = ba; H1[nt][3] = bb;
-          mma16816(H1[nt], A, B1[nt][0], B1[nt][1]);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) H1[nt][q] = fmaxf(H1[nt][q], 0.f);
-        }
-        // layer 2: 32 -> 32, ReLU; the C fragments of layer 1 are A fragments
-        float H2[4][4];
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-          const float ba = b2[8 * nt + 2 * t], bb = b2[8 * nt + 2 * t + 1];
-          H2[nt][0] = ba; H2[nt][1] = bb; H2[nt][2] = ba; H2[nt][3] = bb;
-        }
-#pragma unroll
-        for (int kk = 0; kk < 2; ++kk) {
-          uint32_t A2[4];
-          A2[0] = pack2f(H1[2 * kk][0], H1[2 * kk][1]);
-          A2[1] = pack2f(H1[2 * kk][2], H1[2 * kk][3]);
-          A2[2] = pack2f(H1[2 * kk + 1][0], H1[2 * kk + 1][1]);
-          A2[3] = pack2f(H1[2 * kk + 1][2], H1[2 * kk + 1][3]);
-#pragma unroll
-          for (int nt = 0; nt < 4; ++nt) mma16816(H2[nt], A2, B2[kk][nt][0], B2[kk][nt][1]);
-        }
-        // output: 32 -> 1, reduced over the four lanes of a row group
-        float o0 = 0.f, o1 = 0.f;
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-          const float wa = w3[8 * nt + 2 * t], wb = w3[8 * nt + 2 * t + 1];
-          o0 += fmaxf(H2[nt][0], 0.f) * wa + fmaxf(H2[nt][1], 0.f) * wb;
-          o1 += fmaxf(H2[nt][2], 0.f) * wa + fmaxf(H2[nt][3], 0.f) * wb;
-        }
-        o0 += __shfl_xor_sync(0xffffffffu, o0, 1);
-        o0 += __shfl_xor_sync(0xffffffffu, o0, 2);
-        o1 += __shfl_xor_sync(0xffffffffu, o1, 1);
-        o1 += __shfl_xor_sync(0xffffffffu, o1, 2);
-        if (t == 0) {
-          const long long ca = base + r0, cb = base + r1;
-          // gap cells keep their flag and get logit 0
-          if (ca < nc) {
-            const bool gap = flag[ca] == kFlagGap;
-            if (logit_out) logit_out[ca] = gap ? 0.f : o0 + b3;
-            if (flag_out) flag_out[ca] = gap ? kFlagGap : ((o0 + b3) > thr ? 1 : 0);
+          for (int nt = 0; nt < 4; ++nt) {
+            const float ba = b1[8 * nt + 2 * t], bb = b1[8 * nt + 2 * t + 1];
+            H1[nt][0] = ba; H1[nt][1] = bb; H1[nt][2] = ba; H1[nt][3] = bb;
+            mma16816(H1[nt], A, B1[nt][0], B1[nt][1]);
           }
-          if (cb < nc) {
-            const bool gap = flag[cb] == kFlagGap;
-            if (logit_out) logit_out[cb] = gap ? 0.f : o1 + b3;
-            if (flag_out) flag_out[cb] = gap ? kFlagGap : ((o1 + b3) > thr ? 1 : 0);
+          // layer 2: 32 -> 32, ReLU; the C fragments of layer 1, through the
+          // ReLU and rounded to FP16, are its A fragments
+          float H2[4][4];
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) {
+            const float ba = b2[8 * nt + 2 * t], bb = b2[8 * nt + 2 * t + 1];
+            H2[nt][0] = ba; H2[nt][1] = bb; H2[nt][2] = ba; H2[nt][3] = bb;
+          }
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+            uint32_t A2[4];
+            A2[0] = pack2_relu(H1[2 * kk][0], H1[2 * kk][1]);
+            A2[1] = pack2_relu(H1[2 * kk][2], H1[2 * kk][3]);
+            A2[2] = pack2_relu(H1[2 * kk + 1][0], H1[2 * kk + 1][1]);
+            A2[3] = pack2_relu(H1[2 * kk + 1][2], H1[2 * kk + 1][3]);
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) mma16816(H2[nt], A2, B2[kk][nt][0], B2[kk][nt][1]);
+          }
+          // output: 32 -> 1, reduced over the four lanes of a row group
+          float o0 = 0.f, o1 = 0.f;
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) {
+            const float wa = w3[8 * nt + 2 * t], wb = w3[8 * nt + 2 * t + 1];
+            o0 += fmaxf(H2[nt][0], 0.f) * wa + fmaxf(H2[nt][1], 0.f) * wb;
+            o1 += fmaxf(H2[nt][2], 0.f) * wa + fmaxf(H2[nt][3], 0.f) * wb;
+          }
+          o0 += __shfl_xor_sync(0xffffffffu, o0, 1);
+          o0 += __shfl_xor_sync(0xffffffffu, o0, 2);
+          o1 += __shfl_xor_sync(0xffffffffu, o1, 1);
+          o1 += __shfl_xor_sync(0xffffffffu, o1, 2);
+          if (t == 0 && y < p.ny) {
+            // gap cells keep their flag and get logit 0
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int r = h ? r1 : r0;
+              if (x0 + r >= p.nx) continue;
+              const long long cr = x0 + r + (long long)p.nx * y;
+              const bool gap = sfl[hy][r + 1] == kFlagGap;
+              const float o = (h ? o1 : o0) + b3;
+              if (logit_out) logit_out[cr] = gap ? 0.f : o;
+              if (flag_out) flag_out[cr] = gap ? kFlagGap : (o > thr ? 1 : 0);
+            }
           }
         }
       }
+      __syncwarp();  // sfeat is rewritten by the warp's next row
     }
-    __syncwarp();  // sfeat is rewritten next pass
+    __syncthreads();  // the shared moments are rewritten for the next tile
   }
 }
 
@@ -693,23 +731,18 @@ k_mlp_train(const float* __restrict__ x, const float* __restrict__ y,
 
 template <class S, class R>
 cudaError_t launch_indicator(const Params<R>& p, const S* f0, const S* f1, const uint8_t* flag,
-                             R* mrho, R* mux, R* muy, const IndicatorDev& w, float thr,
-                             float* feat_out, float* logit_out, uint8_t* flag_out,
-                             cudaStream_t st) {
-  const dim3 tg((p.nx + kTX - 1) / kTX, (p.ny + kTY - 1) / kTY);
-  k_ind_moments<S, R><<<tg, dim3(kTX, kTY), 0, st>>>(p, f0, f1, flag, mrho, mux, muy);
-  const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const long long nc = (long long)p.nx * p.ny;
-  long long blocks = (nc + kIndThreads - 1) / kIndThreads;
-  const long long cap = (long long)p.nsm * 16;
+                             const IndicatorDev& w, float thr, float* feat_out, float* logit_out,
+                             uint8_t* flag_out, cudaStream_t st) {
+  const long long ntiles = (long long)((p.nx + kIndTX - 1) / kIndTX) * ((p.ny + kIndTY - 1) / kIndTY);
+  long long blocks = ntiles;
+  const long long cap = (long long)p.nsm * 8;
   if (blocks > cap) blocks = cap;
   const int nl = p.lat[0].n, nh = p.lat[1].n;
 #define SLBM_IND_CASE(NL, NH)                                                                 \
   if (nl == NL && nh == NH) {                                                                 \
     k_indicator<NL, NH, S, R><<<(unsigned)blocks, kIndThreads, 0, st>>>(                      \
-        p, f0, f1, flag, mrho, mux, muy, w.w1, w.b1, w.w2, w.b2, w.w3, w.b3, thr, feat_out,    \
-        logit_out, flag_out);                                                                 \
+        p, f0, f1, flag, w.w1, w.b1, w.w2, w.b2, w.w3, w.b3, thr, feat_out, logit_out,         \
+        flag_out);                                                                            \
     return cudaGetLastError();                                                                \
   }
   SLBM_IND_CASE(3, 4)
@@ -750,8 +783,8 @@ cudaError_t launch_mlp_train(const float* x, const float* y, const int* idx, int
 
 #define SLBM_IND_INST(S, R)                                                                  \
   template cudaError_t launch_indicator<S, R>(const Params<R>&, const S*, const S*,          \
-                                              const uint8_t*, R*, R*, R*, const IndicatorDev&, \
-                                              float, float*, float*, uint8_t*, cudaStream_t); \
+                                              const uint8_t*, const IndicatorDev&, float,     \
+                                              float*, float*, uint8_t*, cudaStream_t);        \
   template cudaError_t launch_lattice_loss<S, R>(const Params<R>&, const S*, const S*,       \
                                                  const uint8_t*, double*, cudaStream_t);
 SLBM_IND_INST(float, float)

@@ -549,16 +549,30 @@ __device__ __forceinline__ void warp_convert(const Params<R>& p, S* f0, S* f1,
   unsigned(*st)[kTY] = s_t[wq];
   unsigned(*sm)[kTY] = s_c[wq];
   const bool xin = x0 + lane < p.nx;
-  for (int r = 0; r < kTY + 2 * B; ++r) {
-    const int gy = stage_col(y0 - B + r, p.ny, p.periodic_y);
-    int fm = 2, fh = 2;
+  // every flag this lane stages, loaded before any is used (one memory
+  // latency per tile, not one per row): staged row r is grid row
+  // y0 - kBandMax + r, whatever the band radius
+  int fm[kRows], fh[kRows], fo[kTY];
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) {
+    const int gy = stage_col(y0 - kBandMax + r, p.ny, p.periodic_y);
+    fm[r] = 2;
+    fh[r] = 2;
     if (gy >= 0) {
-      if (cm >= 0) fm = flag_new[(long long)gy * p.nx + cm];
-      if (ch >= 0) fh = flag_new[(long long)gy * p.nx + ch];
+      if (cm >= 0) fm[r] = flag_new[(long long)gy * p.nx + cm];
+      if (ch >= 0) fh[r] = flag_new[(long long)gy * p.nx + ch];
     }
-    const unsigned m0 = __ballot_sync(0xffffffffu, fm == 0), m1 = __ballot_sync(0xffffffffu, fm == 1);
-    const unsigned h0 = __ballot_sync(0xffffffffu, fh == 0), h1 = __ballot_sync(0xffffffffu, fh == 1);
-    const unsigned long long lo = (1ull << B) - 1ull;
+  }
+#pragma unroll
+  for (int i = 0; i < kTY; ++i) {
+    const bool in = xin && y0 + i < p.ny;
+    fo[i] = in ? flag_old[(long long)(y0 + i) * p.nx + x0 + lane] : 2;
+  }
+  const unsigned long long lo = (1ull << B) - 1ull;
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) {
+    const unsigned m0 = __ballot_sync(0xffffffffu, fm[r] == 0), m1 = __ballot_sync(0xffffffffu, fm[r] == 1);
+    const unsigned h0 = __ballot_sync(0xffffffffu, fh[r] == 0), h1 = __ballot_sync(0xffffffffu, fh[r] == 1);
     const unsigned long long e0 = ((unsigned long long)h0 & lo) | ((unsigned long long)m0 << B) |
                                   ((unsigned long long)(h0 >> B) << (kTX + B));
     const unsigned long long e1 = ((unsigned long long)h1 & lo) | ((unsigned long long)m1 << B) |
@@ -572,14 +586,13 @@ __device__ __forceinline__ void warp_convert(const Params<R>& p, S* f0, S* f1,
       sd[0][r] = (unsigned)a0;
       sd[1][r] = (unsigned)a1;
     }
-    const int i = r - B;  // tile row
+    const int i = r - kBandMax;  // tile row
     if (i >= 0 && i < kTY) {
       const bool in = xin && y0 + i < p.ny;
-      const int fo = in ? flag_old[(long long)(y0 + i) * p.nx + x0 + lane] : 2;
-      const unsigned t0 = __ballot_sync(0xffffffffu, in && fm == 0);
-      const unsigned t1 = __ballot_sync(0xffffffffu, in && fm == 1);
-      const unsigned t2 = __ballot_sync(0xffffffffu, in && fo == 0);
-      const unsigned t3 = __ballot_sync(0xffffffffu, in && fo == 1);
+      const unsigned t0 = __ballot_sync(0xffffffffu, in && fm[r] == 0);
+      const unsigned t1 = __ballot_sync(0xffffffffu, in && fm[r] == 1);
+      const unsigned t2 = __ballot_sync(0xffffffffu, in && fo[i] == 0);
+      const unsigned t3 = __ballot_sync(0xffffffffu, in && fo[i] == 1);
       if (lane == 0) {
         st[0][i] = t0;
         st[1][i] = t1;
@@ -592,7 +605,7 @@ __device__ __forceinline__ void warp_convert(const Params<R>& p, S* f0, S* f1,
   int nlift = 0, nproj = 0;
   for (int i = 0; i < kTY; ++i) {
     unsigned w0 = 0u, w1 = 0u;  // lattice 0 / 1 within B rows and columns
-    for (int d = 0; d <= 2 * B; ++d) {
+    for (int d = kBandMax - B; d <= kBandMax + B; ++d) {
       w0 |= sd[0][i + d];
       w1 |= sd[1][i + d];
     }
@@ -679,21 +692,24 @@ k_post_step_warp(const Params<R> p, S* f0, S* f1, const uint8_t* __restrict__ fl
   const int ntiles = ntx * ((p.ny + kTY - 1) / kTY);
   const int nl = min(max(*nlist, 0), ntiles);
   const int total = nl + n_ghtiles;
-  for (;;) {
-    // the next item, taken by lane 0 from the item counter (zeroed by the
-    // stream kernel): tiles of uneven cost even out over the warps
-    int r = 0;
+  // items are taken by lane 0 from the item counter (zeroed by the stream
+  // kernel), so tiles of uneven cost even out over the warps; the warp asks
+  // for its next item when it starts one, and the counter's answer arrives
+  // while the current item is processed
+  int r = 0;
+  if (lane == 0) r = atomicAdd(p.sched + 2, 1);
+  r = __shfl_sync(0xffffffffu, r, 0);
+  for (; r < total; r = __shfl_sync(0xffffffffu, r, 0)) {
+    const int cur = r;
     if (lane == 0) r = atomicAdd(p.sched + 2, 1);
-    r = __shfl_sync(0xffffffffu, r, 0);
-    if (r >= total) break;
     int t;
-    if (r < nl) {
-      t = list[r];
+    if (cur < nl) {
+      t = list[cur];
       if (t < 0 || t >= ntiles || !post_work_word(work[t])) continue;  // warp-uniform
       warp_convert<NL, NH, S, R>(p, f0, f1, flag_old, flag_new, (t % ntx) * kTX, (t / ntx) * kTY);
       __syncwarp();  // the tile's conversions are visible to the warp's ghost writes
     } else {
-      t = gh_tiles[r - nl];
+      t = gh_tiles[cur - nl];
       if (post_work_word(work[t])) continue;  // written after its conversion
     }
     const int g0 = gh_start[t], g1 = gh_start[t + 1];
