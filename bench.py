@@ -861,7 +861,7 @@ def run_study(args):
         # grid (one launch per step for all), upstream Mach 1.2-4.0,
         # two-population co-moving model, initial ramp 2 mean free paths wide;
         # the paper's scheme: D2Q16 refined to D2Q25 where Kn > 0.02
-        # (refinement only, every step), against D2Q25 everywhere
+        # (refinement only, every --kn-interval steps), against D2Q25 everywhere
         b = WL.shock_batch(256, seed=2, mach_range=(1.2, 4.0))
         nx, ny = max(i["len"] for i in b), len(b)
         active = sum(i["len"] for i in b)
@@ -881,7 +881,7 @@ def run_study(args):
             g.set_rows([i["len"] for i in b], ends)
             g.set_viscosity_law([i["mu1"] for i in b], [i["T1"] for i in b], 0.5, 2.0 / 3.0)
             if kn:
-                g.set_kn_criterion(0.02, 1)
+                g.set_kn_criterion(0.02, args.kn_interval)
             else:
                 g.set_flags(np.ones((ny, nx), np.uint8))
             g.set_pond(1e-5, 30)          # FP32 predictor-corrector tolerance at T up to ~6
@@ -920,6 +920,7 @@ def run_study(args):
                 "workload": f"{ny} instances, lengths {min(i['len'] for i in b)}-{nx}, "
                             f"Mach 1.2-4.0, lambda_1 = 50 cells, two-population PonD "
                             f"(C_v = 3/2, Pr = 2/3, hard-sphere viscosity), FP32",
+                "kn_interval": args.kn_interval if kn else None,
                 "active_cells": active, "block_shape": shape, "steps": steps, "ms_per_step": ms,
                 "mlups": active / (ms * 1e-3) / 1e6,
                 "kernels_ms_per_step": {n: kern[i] / max(ksteps, 1)
@@ -1092,6 +1093,8 @@ def main():
     ap.add_argument("--impl", default="slbm", choices=["slbm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--size", type=int, default=VN, help="grid side of the vortex-fp32 study")
+    ap.add_argument("--kn-interval", type=int, default=1,
+                    help="steps between Knudsen criterion evaluations in the shock study")
     ap.add_argument("--e2e-steps", type=int, default=E2E_STEPS,
                     help="steps of the end-to-end measurement (default: the field's horizon)")
     ap.add_argument("--workload", default="vortex4096",

@@ -581,11 +581,11 @@ int pond_convert_band(slbm_s* h, int buf) {
                                                 (double*)h->pops(buf, 1), (double*)h->gp(buf, 0),
                                                 (double*)h->gp(buf, 1),
                                                 (const double*)h->lam(buf), h->flags(h->fcur),
-                                                mask, h->st)
+                                                mask, nullptr, h->st)
           : launch_pond_convert<float, float>(h->qf, (float*)h->pops(buf, 0),
                                               (float*)h->pops(buf, 1), (float*)h->gp(buf, 0),
                                               (float*)h->gp(buf, 1), (const float*)h->lam(buf),
-                                              h->flags(h->fcur), mask, h->st);
+                                              h->flags(h->fcur), mask, nullptr, h->st);
   SLBM_CK(h, e, "co-moving conversion launch");
   return SLBM_OK;
 }
@@ -1227,12 +1227,12 @@ int slbm_set_flags(slbm_t h, const uint8_t* flags) {
                                                   (double*)h->gp(h->cur, 0),
                                                   (double*)h->gp(h->cur, 1),
                                                   (const double*)h->lam(h->cur),
-                                                  h->flags(h->fcur), nullptr, h->st)
+                                                  h->flags(h->fcur), nullptr, nullptr, h->st)
             : launch_pond_convert<float, float>(h->qf, (float*)h->pops(h->cur, 0),
                                                 (float*)h->pops(h->cur, 1),
                                                 (float*)h->gp(h->cur, 0), (float*)h->gp(h->cur, 1),
                                                 (const float*)h->lam(h->cur), h->flags(h->fcur),
-                                                nullptr, h->st);
+                                                nullptr, nullptr, h->st);
     SLBM_CK(h, e, "co-moving conversion launch");
     SLBM_CK(h, cudaMemcpyAsync(h->flags(h->fcur), tmp, norm.size(), cudaMemcpyDeviceToDevice,
                                h->st),
@@ -1504,44 +1504,33 @@ int slbm_set_boundary(slbm_t h, int side, int kind, const double* rho, const dou
 
 namespace {
 // Knudsen criterion on the current buffer: new flags into the temporary
-// plane, every cell's other lattice from its current one (flipped cells take
-// it as their new native vector), then the new flags, masks and band.
+// plane, the refined cells' other lattice from their current one (their new
+// native vector), then the new flags, masks and band.
 int apply_kn(slbm_s* h) {
   uint8_t* tmp = h->at<uint8_t>(h->lay.flag_tmp);
-  cudaError_t e =
-      h->precision == SLBM_FP64
-          ? launch_pond_kn<double, double>(h->qd, (const double*)h->pops(h->cur, 0),
-                                           (const double*)h->pops(h->cur, 1),
-                                           (const double*)h->gp(h->cur, 0),
-                                           (const double*)h->gp(h->cur, 1),
-                                           (const double*)h->lam(h->cur), h->flags(h->fcur),
-                                           h->kn_thr, tmp, h->st)
-          : launch_pond_kn<float, float>(h->qf, (const float*)h->pops(h->cur, 0),
-                                         (const float*)h->pops(h->cur, 1),
-                                         (const float*)h->gp(h->cur, 0),
-                                         (const float*)h->gp(h->cur, 1),
-                                         (const float*)h->lam(h->cur), h->flags(h->fcur),
-                                         h->kn_thr, tmp, h->st);
-  SLBM_CK(h, e, "Knudsen criterion launch");
-  e = h->precision == SLBM_FP64
-          ? launch_pond_convert<double, double>(h->qd, (double*)h->pops(h->cur, 0),
-                                                (double*)h->pops(h->cur, 1),
-                                                (double*)h->gp(h->cur, 0),
-                                                (double*)h->gp(h->cur, 1),
-                                                (const double*)h->lam(h->cur), h->flags(h->fcur),
-                                                nullptr, h->st)
-          : launch_pond_convert<float, float>(h->qf, (float*)h->pops(h->cur, 0),
-                                              (float*)h->pops(h->cur, 1), (float*)h->gp(h->cur, 0),
-                                              (float*)h->gp(h->cur, 1),
-                                              (const float*)h->lam(h->cur), h->flags(h->fcur),
-                                              nullptr, h->st);
+  uint8_t* fl = h->flags(h->fcur);
+  const int c = h->cur;
+  cudaError_t e;
+  if (h->precision == SLBM_FP64) {
+    double *f0 = (double*)h->pops(c, 0), *f1 = (double*)h->pops(c, 1);
+    double *e0 = (double*)h->gp(c, 0), *e1 = (double*)h->gp(c, 1);
+    const double* lam = (const double*)h->lam(c);
+    e = launch_pond_kn<double, double>(h->qd, f0, f1, e0, e1, lam, fl, h->kn_thr, tmp, h->st);
+    SLBM_CK(h, e, "Knudsen criterion launch");
+    e = launch_pond_convert<double, double>(h->qd, f0, f1, e0, e1, lam, fl, nullptr, tmp, h->st);
+  } else {
+    float *f0 = (float*)h->pops(c, 0), *f1 = (float*)h->pops(c, 1);
+    float *e0 = (float*)h->gp(c, 0), *e1 = (float*)h->gp(c, 1);
+    const float* lam = (const float*)h->lam(c);
+    e = launch_pond_kn<float, float>(h->qf, f0, f1, e0, e1, lam, fl, h->kn_thr, tmp, h->st);
+    SLBM_CK(h, e, "Knudsen criterion launch");
+    e = launch_pond_convert<float, float>(h->qf, f0, f1, e0, e1, lam, fl, nullptr, tmp, h->st);
+  }
   SLBM_CK(h, e, "co-moving conversion launch");
-  SLBM_CK(h, cudaMemcpyAsync(h->flags(h->fcur), tmp, h->ncell(), cudaMemcpyDeviceToDevice, h->st),
-          "flag copy");
-  SLBM_CK(h, launch_pond_masks(h->g.nx, h->g.ny, h->flags(h->fcur),
-                               h->at<uint8_t>(h->lay.tile_mask[0]), h->st),
+  SLBM_CK(h, cudaMemcpyAsync(fl, tmp, h->ncell(), cudaMemcpyDeviceToDevice, h->st), "flag copy");
+  SLBM_CK(h, launch_pond_masks(h->g.nx, h->g.ny, fl, h->at<uint8_t>(h->lay.tile_mask[0]), h->st),
           "mask launch");
-  return pond_convert_band(h, h->cur);
+  return pond_convert_band(h, c);
 }
 }  // namespace
 

@@ -210,11 +210,15 @@ cudaError_t launch_pond_step(const PondParams<R>& p, const S* f0, const S* f1, c
                              S* lam_out, const uint8_t* flag, int* err, cudaStream_t st);
 cudaError_t launch_pond_masks(int nx, int ny, const uint8_t* flag, uint8_t* mask,
                               cudaStream_t st);
-// mask null: convert every cell; else the cells of tiles whose 3 x 3 tile
-// neighbourhood holds both lattices.
+// Each converted cell's other lattice from its current one (flag).  flag_to
+// given: only the cells whose lattice flag_to changes (they take the result as
+// their new native vector); else mask null: every cell; else the cells of
+// tiles whose 3 x 3 tile neighbourhood holds both lattices (batched rows: the
+// cells that read the other lattice).
 template <class S, class R>
 cudaError_t launch_pond_convert(const PondParams<R>& p, S* f0, S* f1, S* e0, S* e1, const S* lam,
-                                const uint8_t* flag, const uint8_t* mask, cudaStream_t st);
+                                const uint8_t* flag, const uint8_t* mask, const uint8_t* flag_to,
+                                cudaStream_t st);
 template <class S, class R>
 cudaError_t launch_pond_frame_io(const PondParams<R>& p, S* lam, double* ux, double* uy,
                                  double* T, int unpack, cudaStream_t st);

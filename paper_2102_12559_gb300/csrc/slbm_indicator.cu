@@ -150,6 +150,16 @@ __device__ __forceinline__ void mma16816(float* d, const uint32_t* a, uint32_t b
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// D = A * B + C with C = {c0, c1, c0, c1}: a bias per output column pair.
+__device__ __forceinline__ void mma16816_bias(float* d, const uint32_t* a, uint32_t b0,
+                                              uint32_t b1, float c0, float c1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
+      "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%10, %11, %10, %11};"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c0), "f"(c1));
+}
+
 // B fragment of n-tile nt, k-rows k0 .. k0 + 15, of a row-major K x N weight
 // matrix W: lane (g, t) holds W[k0 + 2t .. + 1][8 nt + g] and W[k0 + 2t + 8 .. + 9][8 nt + g].
 __device__ __forceinline__ void bfrag(const __half* W, int ncols, int k0, int nt, int g, int t,
@@ -287,21 +297,16 @@ k_indicator(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restri
           A[2] = *reinterpret_cast<const uint32_t*>(&sfeat[warp][r0][2 * t + 8]);
           A[3] = *reinterpret_cast<const uint32_t*>(&sfeat[warp][r1][2 * t + 8]);
           // layer 1: 16 -> 32, ReLU
+          // (bias pairs as 8-byte loads: the pair index 8 nt + 2 t is even)
           float H1[4][4];
 #pragma unroll
           for (int nt = 0; nt < 4; ++nt) {
-            const float ba = b1[8 * nt + 2 * t], bb = b1[8 * nt + 2 * t + 1];
-            H1[nt][0] = ba; H1[nt][1] = bb; H1[nt][2] = ba; H1[nt][3] = bb;
-            mma16816(H1[nt], A, B1[nt][0], B1[nt][1]);
+            const float2 bv = *reinterpret_cast<const float2*>(b1 + 8 * nt + 2 * t);
+            mma16816_bias(H1[nt], A, B1[nt][0], B1[nt][1], bv.x, bv.y);
           }
           // layer 2: 32 -> 32, ReLU; the C fragments of layer 1, through the
           // ReLU and rounded to FP16, are its A fragments
           float H2[4][4];
-#pragma unroll
-          for (int nt = 0; nt < 4; ++nt) {
-            const float ba = b2[8 * nt + 2 * t], bb = b2[8 * nt + 2 * t + 1];
-            H2[nt][0] = ba; H2[nt][1] = bb; H2[nt][2] = ba; H2[nt][3] = bb;
-          }
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk) {
             uint32_t A2[4];
@@ -310,15 +315,22 @@ k_indicator(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restri
             A2[2] = pack2_relu(H1[2 * kk + 1][0], H1[2 * kk + 1][1]);
             A2[3] = pack2_relu(H1[2 * kk + 1][2], H1[2 * kk + 1][3]);
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt) mma16816(H2[nt], A2, B2[kk][nt][0], B2[kk][nt][1]);
+            for (int nt = 0; nt < 4; ++nt) {
+              if (kk == 0) {
+                const float2 bv = *reinterpret_cast<const float2*>(b2 + 8 * nt + 2 * t);
+                mma16816_bias(H2[nt], A2, B2[0][nt][0], B2[0][nt][1], bv.x, bv.y);
+              } else {
+                mma16816(H2[nt], A2, B2[1][nt][0], B2[1][nt][1]);
+              }
+            }
           }
           // output: 32 -> 1, reduced over the four lanes of a row group
           float o0 = 0.f, o1 = 0.f;
 #pragma unroll
           for (int nt = 0; nt < 4; ++nt) {
-            const float wa = w3[8 * nt + 2 * t], wb = w3[8 * nt + 2 * t + 1];
-            o0 += fmaxf(H2[nt][0], 0.f) * wa + fmaxf(H2[nt][1], 0.f) * wb;
-            o1 += fmaxf(H2[nt][2], 0.f) * wa + fmaxf(H2[nt][3], 0.f) * wb;
+            const float2 wv = *reinterpret_cast<const float2*>(w3 + 8 * nt + 2 * t);
+            o0 += fmaxf(H2[nt][0], 0.f) * wv.x + fmaxf(H2[nt][1], 0.f) * wv.y;
+            o1 += fmaxf(H2[nt][2], 0.f) * wv.x + fmaxf(H2[nt][3], 0.f) * wv.y;
           }
           o0 += __shfl_xor_sync(0xffffffffu, o0, 1);
           o0 += __shfl_xor_sync(0xffffffffu, o0, 2);

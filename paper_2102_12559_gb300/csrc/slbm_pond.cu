@@ -675,9 +675,20 @@ __device__ void pond_convert_cell(const PondParams<R>& p, S* f0, S* f1, S* e0, S
 template <int NQ, int NQQ, class S, class R>
 __global__ void __launch_bounds__(kThreads)
 k_pond_convert(const PondParams<R> p, S* f0, S* f1, S* e0, S* e1, const S* __restrict__ lam,
-               const uint8_t* __restrict__ flag, const uint8_t* __restrict__ mask) {
+               const uint8_t* __restrict__ flag, const uint8_t* __restrict__ mask,
+               const uint8_t* __restrict__ flag_to) {
   const int x = blockIdx.x * kTX + threadIdx.x;
   const int y = blockIdx.y * kTY + threadIdx.y;
+  if (flag_to) {  // only the cells whose lattice changes
+    if (x >= p.nx || y >= p.ny) return;
+    if (p.rows && x >= p.row_len[y]) return;
+    const long long c = (long long)x + (long long)p.nx * y;
+    const int k = flag[c] ? 1 : 0;
+    if ((flag_to[c] ? 1 : 0) == k) return;
+    pond_convert_cell<NQ, NQQ, S, R>(p, f0, f1, e0, e1, k, (size_t)(y + p.G) * p.pitch + (x + kOX),
+                                     lam, c);
+    return;
+  }
   if (mask) {
     // 3 x 3 tile neighbourhood (periodic) must hold both lattices
     const int tx = blockIdx.x, ty = blockIdx.y, ntx = gridDim.x, nty = gridDim.y;
@@ -825,9 +836,10 @@ cudaError_t step_pair(const PondParams<R>& p, const S* f0, const S* f1, const S*
 
 template <int NL, int NH, class S, class R>
 cudaError_t convert_pair(const PondParams<R>& p, S* f0, S* f1, S* e0, S* e1, const S* lam,
-                         const uint8_t* flag, const uint8_t* mask, cudaStream_t st) {
+                         const uint8_t* flag, const uint8_t* mask, const uint8_t* flag_to,
+                         cudaStream_t st) {
   k_pond_convert<NL, NH, S, R><<<tile_grid(p.nx, p.ny), dim3(kTX, kTY), 0, st>>>(
-      p, f0, f1, e0, e1, lam, flag, mask);
+      p, f0, f1, e0, e1, lam, flag, mask, flag_to);
   return cudaGetLastError();
 }
 
@@ -864,11 +876,15 @@ cudaError_t launch_pond_masks(int nx, int ny, const uint8_t* flag, uint8_t* mask
 
 template <class S, class R>
 cudaError_t launch_pond_convert(const PondParams<R>& p, S* f0, S* f1, S* e0, S* e1, const S* lam,
-                                const uint8_t* flag, const uint8_t* mask, cudaStream_t st) {
+                                const uint8_t* flag, const uint8_t* mask, const uint8_t* flag_to,
+                                cudaStream_t st) {
   const int lo = p.lat[0].n, hi = p.lat[1].n;
-  if (lo == 3 && hi == 4) return convert_pair<3, 4, S, R>(p, f0, f1, e0, e1, lam, flag, mask, st);
-  if (lo == 3 && hi == 5) return convert_pair<3, 5, S, R>(p, f0, f1, e0, e1, lam, flag, mask, st);
-  if (lo == 4 && hi == 5) return convert_pair<4, 5, S, R>(p, f0, f1, e0, e1, lam, flag, mask, st);
+  if (lo == 3 && hi == 4)
+    return convert_pair<3, 4, S, R>(p, f0, f1, e0, e1, lam, flag, mask, flag_to, st);
+  if (lo == 3 && hi == 5)
+    return convert_pair<3, 5, S, R>(p, f0, f1, e0, e1, lam, flag, mask, flag_to, st);
+  if (lo == 4 && hi == 5)
+    return convert_pair<4, 5, S, R>(p, f0, f1, e0, e1, lam, flag, mask, flag_to, st);
   return cudaErrorInvalidValue;
 }
 
@@ -910,7 +926,7 @@ cudaError_t launch_pond_frame_io(const PondParams<R>& p, S* lam, double* ux, dou
                                               S*, const uint8_t*, int*, cudaStream_t);         \
   template cudaError_t launch_pond_convert<S, R>(const PondParams<R>&, S*, S*, S*, S*,         \
                                                  const S*, const uint8_t*, const uint8_t*,     \
-                                                 cudaStream_t);                                \
+                                                 const uint8_t*, cudaStream_t);                \
   template cudaError_t launch_pond_frame_io<S, R>(const PondParams<R>&, S*, double*, double*,  \
                                                   double*, int, cudaStream_t);                 \
   template cudaError_t launch_pond_gio<S, R>(const PondParams<R>&, int, int, S*, const S*,     \
