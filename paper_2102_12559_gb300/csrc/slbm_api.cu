@@ -189,6 +189,8 @@ struct Layout {
   size_t post_work;          // 2 x ntiles work words (stream kernel -> post-step kernel)
   size_t post_nlist;         // 2 counters: work tiles listed in each half of post_list
   size_t post_list;          // 2 x ntiles: candidate work tiles (stream kernel -> post-step kernel)
+  size_t conv_count;         // 2 counters of the co-moving conversion lists (their cell lists
+                             // use the macro[2] / macro[3] staging slots, see conv_lists)
   size_t total;
 };
 
@@ -267,6 +269,7 @@ Layout make_layout(const slbm_grid* g, int lo, int hi, int order, int precision)
   Lo.post_work = off; off = align_up(off + 2 * ntiles * sizeof(int), 256);
   Lo.post_nlist = off; off = align_up(off + 2 * sizeof(int), 256);
   Lo.post_list = off; off = align_up(off + 2 * ntiles * sizeof(int), 256);
+  Lo.conv_count = off; off = align_up(off + 2 * sizeof(int), 256);
   Lo.total = off;
   return Lo;
 }
@@ -572,6 +575,15 @@ cudaError_t mark(slbm_s* h) {
 
 // One time step: stream-collide (old flags) -> interface conversion (new
 // flags) -> ghost-ring refresh.
+// Cell lists of the co-moving conversions: the macro[2] and macro[3] slots
+// (nc doubles each, room for nc ints), which otherwise only stage host data
+// within one call, every read of it stream-ordered before any conversion the
+// call launches.
+ConvLists conv_lists(slbm_s* h) {
+  return ConvLists{h->at<int>(h->lay.conv_count), h->at<int>(h->lay.macro[2]),
+                   h->at<int>(h->lay.macro[3])};
+}
+
 int pond_convert_band(slbm_s* h, int buf) {
   if (!h->pond_mixed) return SLBM_OK;
   const uint8_t* mask = h->at<uint8_t>(h->lay.tile_mask[0]);
@@ -581,11 +593,11 @@ int pond_convert_band(slbm_s* h, int buf) {
                                                 (double*)h->pops(buf, 1), (double*)h->gp(buf, 0),
                                                 (double*)h->gp(buf, 1),
                                                 (const double*)h->lam(buf), h->flags(h->fcur),
-                                                mask, nullptr, h->st)
+                                                mask, nullptr, 0, conv_lists(h), h->st)
           : launch_pond_convert<float, float>(h->qf, (float*)h->pops(buf, 0),
                                               (float*)h->pops(buf, 1), (float*)h->gp(buf, 0),
                                               (float*)h->gp(buf, 1), (const float*)h->lam(buf),
-                                              h->flags(h->fcur), mask, nullptr, h->st);
+                                              h->flags(h->fcur), mask, nullptr, 0, conv_lists(h), h->st);
   SLBM_CK(h, e, "co-moving conversion launch");
   return SLBM_OK;
 }
@@ -798,6 +810,7 @@ void fill_pond(PondParams<R>& q, const slbm_s* h, const Params<R>& p, const Latt
   q.bx = h->pond_bx;
   q.by = h->pond_by;
   q.P = h->P;
+  q.nsm = h->nsm;
   q.reach = (R)kPondReach;
   for (int k = 0; k < 2; ++k) {
     const Lattice1D& L = k ? b : a;
@@ -1227,17 +1240,17 @@ int slbm_set_flags(slbm_t h, const uint8_t* flags) {
                                                   (double*)h->gp(h->cur, 0),
                                                   (double*)h->gp(h->cur, 1),
                                                   (const double*)h->lam(h->cur),
-                                                  h->flags(h->fcur), nullptr, nullptr, h->st)
+                                                  h->flags(h->fcur), nullptr, nullptr, 0, conv_lists(h), h->st)
             : launch_pond_convert<float, float>(h->qf, (float*)h->pops(h->cur, 0),
                                                 (float*)h->pops(h->cur, 1),
                                                 (float*)h->gp(h->cur, 0), (float*)h->gp(h->cur, 1),
                                                 (const float*)h->lam(h->cur), h->flags(h->fcur),
-                                                nullptr, nullptr, h->st);
+                                                nullptr, nullptr, 0, conv_lists(h), h->st);
     SLBM_CK(h, e, "co-moving conversion launch");
     SLBM_CK(h, cudaMemcpyAsync(h->flags(h->fcur), tmp, norm.size(), cudaMemcpyDeviceToDevice,
                                h->st),
             "flag copy");
-    SLBM_CK(h, launch_pond_masks(h->g.nx, h->g.ny, h->flags(h->fcur),
+    SLBM_CK(h, launch_pond_masks(h->g.nx, h->g.ny, h->flags(h->fcur), nullptr,
                                  h->at<uint8_t>(h->lay.tile_mask[0]), h->st),
             "mask launch");
     bool any0 = false, any1 = false;
@@ -1505,11 +1518,16 @@ int slbm_set_boundary(slbm_t h, int side, int kind, const double* rho, const dou
 namespace {
 // Knudsen criterion on the current buffer: new flags into the temporary
 // plane, the refined cells' other lattice from their current one (their new
-// native vector), then the new flags, masks and band.
-int apply_kn(slbm_s* h) {
+// native vector), masks of the new flags (with the tiles whose cells changed
+// lattice), then the band conversion (full_band: every cell that reads the
+// other lattice; else only those in the 3 x 3 tile neighbourhood of a changed
+// cell, the others having been converted after the step, from the same
+// native vectors) and the new flags.
+int apply_kn(slbm_s* h, bool full_band) {
   uint8_t* tmp = h->at<uint8_t>(h->lay.flag_tmp);
+  uint8_t* mask = h->at<uint8_t>(h->lay.tile_mask[0]);
   uint8_t* fl = h->flags(h->fcur);
-  const int c = h->cur;
+  const int c = h->cur, near = full_band ? 0 : 1;
   cudaError_t e;
   if (h->precision == SLBM_FP64) {
     double *f0 = (double*)h->pops(c, 0), *f1 = (double*)h->pops(c, 1);
@@ -1517,20 +1535,26 @@ int apply_kn(slbm_s* h) {
     const double* lam = (const double*)h->lam(c);
     e = launch_pond_kn<double, double>(h->qd, f0, f1, e0, e1, lam, fl, h->kn_thr, tmp, h->st);
     SLBM_CK(h, e, "Knudsen criterion launch");
-    e = launch_pond_convert<double, double>(h->qd, f0, f1, e0, e1, lam, fl, nullptr, tmp, h->st);
+    e = launch_pond_convert<double, double>(h->qd, f0, f1, e0, e1, lam, fl, nullptr, tmp, 0, conv_lists(h), h->st);
+    SLBM_CK(h, e, "co-moving conversion launch");
+    SLBM_CK(h, launch_pond_masks(h->g.nx, h->g.ny, tmp, fl, mask, h->st), "mask launch");
+    e = launch_pond_convert<double, double>(h->qd, f0, f1, e0, e1, lam, tmp, mask, nullptr, near,
+                                            conv_lists(h), h->st);
   } else {
     float *f0 = (float*)h->pops(c, 0), *f1 = (float*)h->pops(c, 1);
     float *e0 = (float*)h->gp(c, 0), *e1 = (float*)h->gp(c, 1);
     const float* lam = (const float*)h->lam(c);
     e = launch_pond_kn<float, float>(h->qf, f0, f1, e0, e1, lam, fl, h->kn_thr, tmp, h->st);
     SLBM_CK(h, e, "Knudsen criterion launch");
-    e = launch_pond_convert<float, float>(h->qf, f0, f1, e0, e1, lam, fl, nullptr, tmp, h->st);
+    e = launch_pond_convert<float, float>(h->qf, f0, f1, e0, e1, lam, fl, nullptr, tmp, 0, conv_lists(h), h->st);
+    SLBM_CK(h, e, "co-moving conversion launch");
+    SLBM_CK(h, launch_pond_masks(h->g.nx, h->g.ny, tmp, fl, mask, h->st), "mask launch");
+    e = launch_pond_convert<float, float>(h->qf, f0, f1, e0, e1, lam, tmp, mask, nullptr, near,
+                                          conv_lists(h), h->st);
   }
   SLBM_CK(h, e, "co-moving conversion launch");
   SLBM_CK(h, cudaMemcpyAsync(fl, tmp, h->ncell(), cudaMemcpyDeviceToDevice, h->st), "flag copy");
-  SLBM_CK(h, launch_pond_masks(h->g.nx, h->g.ny, fl, h->at<uint8_t>(h->lay.tile_mask[0]), h->st),
-          "mask launch");
-  return pond_convert_band(h, c);
+  return SLBM_OK;
 }
 }  // namespace
 
@@ -1544,7 +1568,7 @@ int slbm_set_kn_criterion(slbm_t h, double thr, int interval) {
   h->kn_interval = interval;
   h->pond_mixed = 1;  // flags may change every interval: keep the band conversion on
   drop_graphs(h);
-  if (int rc = apply_kn(h)) return rc;
+  if (int rc = apply_kn(h, true)) return rc;
   SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
   return check_device_error(h);
 }
@@ -1588,7 +1612,7 @@ int slbm_step(slbm_t h, int n) {
       if (rc) return rc;
     }
     if (h->kn_on && h->steps % h->kn_interval == 0) {
-      const int rc = apply_kn(h);
+      const int rc = apply_kn(h, false);
       if (rc) return rc;
     }
   }
@@ -1724,7 +1748,7 @@ int slbm_set_state(slbm_t h, const void* buf, size_t bytes) {
     // flags (with their masks), frames, then populations and band conversions
     std::vector<uint8_t> fl((const uint8_t*)(p + sizeof(hd)), (const uint8_t*)(p + sizeof(hd)) + nc);
     if ((rc = upload(h, h->flags(h->fcur), fl.data(), nc))) return rc;
-    SLBM_CK(h, launch_pond_masks(h->g.nx, h->g.ny, h->flags(h->fcur),
+    SLBM_CK(h, launch_pond_masks(h->g.nx, h->g.ny, h->flags(h->fcur), nullptr,
                                  h->at<uint8_t>(h->lay.tile_mask[0]), h->st),
             "mask launch");
     bool any0 = false, any1 = false;

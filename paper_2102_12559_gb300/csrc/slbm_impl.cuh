@@ -162,6 +162,7 @@ struct PondParams {
   const double* row_visc;
   R s_exp, inv_pr;
   int bx, by;                   // thread-block shape of the step kernel (bx * by = 256)
+  int nsm;                      // multiprocessors of the device
   int P;                        // collocation points per axis
   R reach;                      // largest departure distance allowed, cells
   PondLat<R> lat[2];
@@ -208,17 +209,31 @@ template <class S, class R>
 cudaError_t launch_pond_step(const PondParams<R>& p, const S* f0, const S* f1, const S* e0,
                              const S* e1, const S* lam, S* g0, S* g1, S* eo0, S* eo1,
                              S* lam_out, const uint8_t* flag, int* err, cudaStream_t st);
-cudaError_t launch_pond_masks(int nx, int ny, const uint8_t* flag, uint8_t* mask,
-                              cudaStream_t st);
-// Each converted cell's other lattice from its current one (flag).  flag_to
+// Per 32 x 8 tile: bit 1 / 2 if it holds a cell of lattice 0 / 1 (flag), bit
+// 4 if a cell's lattice differs from flag_old (when given).
+cudaError_t launch_pond_masks(int nx, int ny, const uint8_t* flag, const uint8_t* flag_old,
+                              uint8_t* mask, cudaStream_t st);
+// Cell lists of one interface conversion (device): count[0] cells to lift
+// (computed in the low-order lattice) in lift[], count[1] to project in proj[],
+// each with room for every cell of the grid.
+struct ConvLists {
+  int* count;
+  int* lift;
+  int* proj;
+};
+
+// Each converted cell's other lattice from its current one (flag): a light
+// screening launch lists the cells, then one thread per listed cell converts
+// (lifts first, so a warp mostly runs one of the two).  flag_to
 // given: only the cells whose lattice flag_to changes (they take the result as
 // their new native vector); else mask null: every cell; else the cells of
 // tiles whose 3 x 3 tile neighbourhood holds both lattices (batched rows: the
-// cells that read the other lattice).
+// cells that read the other lattice) and, with near_change, a cell whose
+// lattice changed (mask bit 4, see launch_pond_masks).
 template <class S, class R>
 cudaError_t launch_pond_convert(const PondParams<R>& p, S* f0, S* f1, S* e0, S* e1, const S* lam,
                                 const uint8_t* flag, const uint8_t* mask, const uint8_t* flag_to,
-                                cudaStream_t st);
+                                int near_change, const ConvLists& lists, cudaStream_t st);
 template <class S, class R>
 cudaError_t launch_pond_frame_io(const PondParams<R>& p, S* lam, double* ux, double* uy,
                                  double* T, int unpack, cudaStream_t st);

@@ -492,11 +492,14 @@ k_pond_init(const PondParams<R> p, S* f0, S* f1, S* e0, S* e1, S* lam,
 
 // Per 32 x 8 tile: bit 0 = a low-order cell, bit 1 = a high-order cell.
 __global__ void __launch_bounds__(kThreads)
-k_pond_masks(int nx, int ny, const uint8_t* __restrict__ flag, uint8_t* __restrict__ mask) {
+k_pond_masks(int nx, int ny, const uint8_t* __restrict__ flag, const uint8_t* __restrict__ flag_old,
+             uint8_t* __restrict__ mask) {
   const int x = blockIdx.x * kTX + threadIdx.x;
   const int y = blockIdx.y * kTY + threadIdx.y;
   const bool in = x < nx && y < ny;
-  const int bit = in ? (flag[(long long)x + (long long)nx * y] ? 2 : 1) : 0;
+  const long long c = (long long)x + (long long)nx * y;
+  int bit = in ? (flag[c] ? 2 : 1) : 0;
+  if (in && flag_old && (flag_old[c] ? 1 : 0) != (flag[c] ? 1 : 0)) bit |= 4;
   __shared__ int acc;
   if (threadIdx.x == 0 && threadIdx.y == 0) acc = 0;
   __syncthreads();
@@ -672,48 +675,76 @@ __device__ void pond_convert_cell(const PondParams<R>& p, S* f0, S* f1, S* e0, S
   }
 }
 
-template <int NQ, int NQQ, class S, class R>
+// Screening for a conversion, one thread per cell of a 32 x 8 tile (few
+// registers, so many tiles are resident): flag_to given, the cells whose
+// lattice changes; else mask null, every cell; else the cells of tiles whose
+// 3 x 3 tile neighbourhood holds both lattices (and, with near_change, a
+// changed cell), on batched rows only those that read the other lattice.
+// Selected cells are appended per warp to the lift or the projection list.
+template <class R>
 __global__ void __launch_bounds__(kThreads)
-k_pond_convert(const PondParams<R> p, S* f0, S* f1, S* e0, S* e1, const S* __restrict__ lam,
-               const uint8_t* __restrict__ flag, const uint8_t* __restrict__ mask,
-               const uint8_t* __restrict__ flag_to) {
+k_pond_screen(const PondParams<R> p, const uint8_t* __restrict__ flag,
+              const uint8_t* __restrict__ mask, const uint8_t* __restrict__ flag_to,
+              int near_change, ConvLists L) {
   const int x = blockIdx.x * kTX + threadIdx.x;
   const int y = blockIdx.y * kTY + threadIdx.y;
-  if (flag_to) {  // only the cells whose lattice changes
-    if (x >= p.nx || y >= p.ny) return;
-    if (p.rows && x >= p.row_len[y]) return;
-    const long long c = (long long)x + (long long)p.nx * y;
-    const int k = flag[c] ? 1 : 0;
-    if ((flag_to[c] ? 1 : 0) == k) return;
-    pond_convert_cell<NQ, NQQ, S, R>(p, f0, f1, e0, e1, k, (size_t)(y + p.G) * p.pitch + (x + kOX),
-                                     lam, c);
-    return;
-  }
-  if (mask) {
-    // 3 x 3 tile neighbourhood (periodic) must hold both lattices
+  bool sel = x < p.nx && y < p.ny && !(p.rows && x >= p.row_len[y]);
+  const long long c = (long long)x + (long long)p.nx * y;
+  const int k = sel ? (flag[c] ? 1 : 0) : 0;
+  if (flag_to) {
+    if (sel) sel = (flag_to[c] ? 1 : 0) != k;
+  } else if (mask) {
+    // 3 x 3 tile neighbourhood (periodic) must hold both lattices (the same
+    // answer for the whole block)
     const int tx = blockIdx.x, ty = blockIdx.y, ntx = gridDim.x, nty = gridDim.y;
     int bits = 0;
     for (int j = -1; j <= 1; ++j)
       for (int i = -1; i <= 1; ++i)
         bits |= mask[wrapm(tx + i, ntx) + ntx * wrapm(ty + j, nty)];
-    if (bits != 3) return;
+    if ((bits & 3) != 3 || (near_change && !(bits & 4))) sel = false;
+    if (sel && p.rows) {
+      // a row reads only itself: only cells that a cell of the other lattice
+      // within the largest departure plus the stencil half-width reads
+      const int B = (int)p.reach + (p.P + 1) / 2;
+      const int lo = max(0, x - B), hi = min(p.row_len[y] - 1, x + B);
+      bool other = false;
+      for (int xi = lo; xi <= hi && !other; ++xi)
+        other = (flag[(long long)xi + (long long)p.nx * y] ? 1 : 0) != k;
+      sel = other;
+    }
   }
-  if (x >= p.nx || y >= p.ny) return;
-  if (p.rows && x >= p.row_len[y]) return;
-  const long long c = (long long)x + (long long)p.nx * y;
-  const int k = flag[c] ? 1 : 0;
-  if (mask && p.rows) {
-    // a row reads only itself: convert only cells that a cell of the other
-    // lattice within the largest departure plus the stencil half-width reads
-    const int B = (int)p.reach + (p.P + 1) / 2;
-    const int lo = max(0, x - B), hi = min(p.row_len[y] - 1, x + B);
-    bool other = false;
-    for (int xi = lo; xi <= hi && !other; ++xi)
-      other = (flag[(long long)xi + (long long)p.nx * y] ? 1 : 0) != k;
-    if (!other) return;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) {
+    const bool mine = sel && k == kk;
+    const unsigned b = __ballot_sync(0xffffffffu, mine);
+    if (!b) continue;
+    const int leader = __ffs(b) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(L.count + kk, __popc(b));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (mine) (kk ? L.proj : L.lift)[base + __popc(b & ((1u << lane) - 1u))] = (int)c;
   }
-  pond_convert_cell<NQ, NQQ, S, R>(p, f0, f1, e0, e1, k, (size_t)(y + p.G) * p.pitch + (x + kOX),
-                                   lam, c);
+}
+
+constexpr int kConvThreads = 128;
+
+// The listed conversions, one thread per cell.
+template <int NQ, int NQQ, class S, class R>
+__global__ void __launch_bounds__(kConvThreads)
+k_pond_convert_list(const PondParams<R> p, S* f0, S* f1, S* e0, S* e1, const S* __restrict__ lam,
+                    ConvLists L) {
+  const int nc = (int)p.nc;
+  const int n0 = min(max(L.count[0], 0), nc), n1 = min(max(L.count[1], 0), nc);
+  for (int i = blockIdx.x * kConvThreads + threadIdx.x; i < n0 + n1;
+       i += gridDim.x * kConvThreads) {
+    const int k = i < n0 ? 0 : 1;
+    const int c = k ? L.proj[i - n0] : L.lift[i];
+    if (c < 0 || c >= nc) continue;
+    const int x = c % p.nx, y = c / p.nx;
+    pond_convert_cell<NQ, NQQ, S, R>(p, f0, f1, e0, e1, k, (size_t)(y + p.G) * p.pitch + (x + kOX),
+                                     lam, c);
+  }
 }
 
 template <class S, class R>
@@ -836,10 +867,9 @@ cudaError_t step_pair(const PondParams<R>& p, const S* f0, const S* f1, const S*
 
 template <int NL, int NH, class S, class R>
 cudaError_t convert_pair(const PondParams<R>& p, S* f0, S* f1, S* e0, S* e1, const S* lam,
-                         const uint8_t* flag, const uint8_t* mask, const uint8_t* flag_to,
-                         cudaStream_t st) {
-  k_pond_convert<NL, NH, S, R><<<tile_grid(p.nx, p.ny), dim3(kTX, kTY), 0, st>>>(
-      p, f0, f1, e0, e1, lam, flag, mask, flag_to);
+                         const ConvLists& L, cudaStream_t st) {
+  k_pond_convert_list<NL, NH, S, R><<<2 * (p.nsm > 0 ? p.nsm : 1), kConvThreads, 0, st>>>(
+      p, f0, f1, e0, e1, lam, L);
   return cudaGetLastError();
 }
 
@@ -868,24 +898,28 @@ cudaError_t launch_pond_step(const PondParams<R>& p, const S* f0, const S* f1, c
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_pond_masks(int nx, int ny, const uint8_t* flag, uint8_t* mask,
-                              cudaStream_t st) {
-  k_pond_masks<<<tile_grid(nx, ny), dim3(kTX, kTY), 0, st>>>(nx, ny, flag, mask);
+cudaError_t launch_pond_masks(int nx, int ny, const uint8_t* flag, const uint8_t* flag_old,
+                              uint8_t* mask, cudaStream_t st) {
+  k_pond_masks<<<tile_grid(nx, ny), dim3(kTX, kTY), 0, st>>>(nx, ny, flag, flag_old, mask);
   return cudaGetLastError();
 }
 
 template <class S, class R>
 cudaError_t launch_pond_convert(const PondParams<R>& p, S* f0, S* f1, S* e0, S* e1, const S* lam,
                                 const uint8_t* flag, const uint8_t* mask, const uint8_t* flag_to,
-                                cudaStream_t st) {
+                                int near_change, const ConvLists& lists, cudaStream_t st) {
   const int lo = p.lat[0].n, hi = p.lat[1].n;
-  if (lo == 3 && hi == 4)
-    return convert_pair<3, 4, S, R>(p, f0, f1, e0, e1, lam, flag, mask, flag_to, st);
-  if (lo == 3 && hi == 5)
-    return convert_pair<3, 5, S, R>(p, f0, f1, e0, e1, lam, flag, mask, flag_to, st);
-  if (lo == 4 && hi == 5)
-    return convert_pair<4, 5, S, R>(p, f0, f1, e0, e1, lam, flag, mask, flag_to, st);
-  return cudaErrorInvalidValue;
+  if (!((lo == 3 && hi == 4) || (lo == 3 && hi == 5) || (lo == 4 && hi == 5)))
+    return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(lists.count, 0, 2 * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_pond_screen<R><<<tile_grid(p.nx, p.ny), dim3(kTX, kTY), 0, st>>>(p, flag, mask, flag_to,
+                                                                     near_change, lists);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (lo == 3 && hi == 4) return convert_pair<3, 4, S, R>(p, f0, f1, e0, e1, lam, lists, st);
+  if (lo == 3 && hi == 5) return convert_pair<3, 5, S, R>(p, f0, f1, e0, e1, lam, lists, st);
+  return convert_pair<4, 5, S, R>(p, f0, f1, e0, e1, lam, lists, st);
 }
 
 template <class S, class R>
@@ -926,7 +960,8 @@ cudaError_t launch_pond_frame_io(const PondParams<R>& p, S* lam, double* ux, dou
                                               S*, const uint8_t*, int*, cudaStream_t);         \
   template cudaError_t launch_pond_convert<S, R>(const PondParams<R>&, S*, S*, S*, S*,         \
                                                  const S*, const uint8_t*, const uint8_t*,     \
-                                                 const uint8_t*, cudaStream_t);                \
+                                                 const uint8_t*, int, const ConvLists&,        \
+                                                 cudaStream_t);                                \
   template cudaError_t launch_pond_frame_io<S, R>(const PondParams<R>&, S*, double*, double*,  \
                                                   double*, int, cudaStream_t);                 \
   template cudaError_t launch_pond_gio<S, R>(const PondParams<R>&, int, int, S*, const S*,     \
