@@ -1191,8 +1191,10 @@ int slbm_get_info(slbm_t h, slbm_info_t* info) {
   info->pitch = h->lay.pitch;
   info->rows = h->lay.rows;
   info->precision = h->precision;
+  // lattice frame: stream-collide and post-step; co-moving: the step, plus
+  // the conversion's screening and list launches when both lattices are used
   info->kernels_per_step =
-      h->frame == SLBM_FRAME_LATTICE ? 2 : (h->pond_mixed ? 2 : 1);
+      h->frame == SLBM_FRAME_LATTICE ? 2 : (h->pond_mixed ? 3 : 1);
   info->workspace_bytes = h->lay.total;
   info->steps = h->steps;
   return SLBM_OK;
