@@ -17,8 +17,8 @@ LIB = os.path.join(HERE, "libslbm.so")
 
 SOURCES = ["slbm_api.cu", "slbm_aux.cu", "slbm_post.cu", "slbm_stream_f32.cu",
            "slbm_stream_f64.cu", "slbm_stream_f16.cu", "slbm_stream_f32_wrap.cu",
-           "slbm_stream_f64_wrap.cu", "slbm_stream_f16_wrap.cu", "slbm_noalloc.cu", "slbm_pond.cu",
-           "slbm_indicator.cu"]
+           "slbm_stream_f64_wrap.cu", "slbm_stream_f16_wrap.cu", "slbm_stream_fx16.cu",
+           "slbm_stream_fx16_wrap.cu", "slbm_noalloc.cu", "slbm_pond.cu", "slbm_indicator.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", INCLUDE]

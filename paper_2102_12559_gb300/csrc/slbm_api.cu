@@ -173,7 +173,7 @@ void fill_lat(LatTab<R>& T, const Lattice1D& L, double dt, int P) {
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 int elem_size(int precision) {
-  return precision == SLBM_FP64 ? 8 : (precision == SLBM_FP16 ? 2 : 4);
+  return precision == SLBM_FP64 ? 8 : (precision == SLBM_FP16 || precision == SLBM_FX16 ? 2 : 4);
 }
 
 struct Layout {
@@ -201,8 +201,9 @@ bool config_ok(const slbm_grid* g, int lo, int hi, int order, int precision, cha
     return false;
   }
   if (order < 1 || order > 5) { snprintf(err, 256, "interp_order must be in 1..5"); return false; }
-  if (precision != SLBM_FP32 && precision != SLBM_FP64 && precision != SLBM_FP16) {
-    snprintf(err, 256, "precision must be SLBM_FP32, SLBM_FP64 or SLBM_FP16");
+  if (precision != SLBM_FP32 && precision != SLBM_FP64 && precision != SLBM_FP16 &&
+      precision != SLBM_FX16) {
+    snprintf(err, 256, "precision must be SLBM_FP32, SLBM_FP64, SLBM_FP16 or SLBM_FX16");
     return false;
   }
   if (g->nx < 1 || g->ny < 1 || (long long)g->nx * g->ny > (1LL << 30)) {
@@ -348,6 +349,7 @@ struct slbm_s {
   std::vector<GraphEntry> graphs;
   cudaStream_t cap_st;           // private stream the graphs are captured on
   int graphs_off;                // a capture failed: step with direct launches
+  float fx_sc[2][kMaxN * kMaxN];  // SLBM_FX16 plane scales (see include/slbm.h), by lattice
 
   template <class T> T* at(size_t off) { return reinterpret_cast<T*>(ws + off); }
   void* pops(int buf, int k) { return ws + lay.pops[buf][k]; }
@@ -499,6 +501,7 @@ auto with_types(slbm_s* h, F&& f) -> decltype(f(Ty<float, float>{}, h->pf)) {
   switch (h->precision) {
     case SLBM_FP64: return f(Ty<double, double>{}, h->pd);
     case SLBM_FP16: return f(Ty<__half, float>{}, h->pf);
+    case SLBM_FX16: return f(Ty<fx16, float>{}, h->pf);
     default: return f(Ty<float, float>{}, h->pf);
   }
 }
@@ -760,6 +763,13 @@ void fill_params(Params<R>& p, const slbm_s* h, const Lattice1D& a, const Lattic
                   : nullptr;
   fill_lat(p.lat[0], a, dt, h->P);
   fill_lat(p.lat[1], b, dt, h->P);
+  // fixed-point plane scales (1 for the other storage types, unused there)
+  for (int k = 0; k < 2; ++k)
+    for (int i = 0; i < kMaxN * kMaxN; ++i) {
+      const double sc = h->precision == SLBM_FX16 ? (double)h->fx_sc[k][i] : 1.0;
+      p.lat[k].sc[i] = (R)sc;
+      p.lat[k].isc[i] = (R)(1.0 / sc);
+    }
   ConvTab<R>& t = p.conv;
   for (int j = 0; j < kMaxN; ++j)
     for (int m = 0; m < kMaxN; ++m) {
@@ -898,6 +908,31 @@ int pack_any(slbm_s* h, int k, double* host, int unpack, const double* in) {
   });
 }
 
+// SLBM_FX16 plane scales from the equilibria staged in macro[0..2] (rho,
+// u_x, u_y): sc_i = max(2 max|s_i|, W_i / 4) / 32767 per plane of each
+// lattice.  Synchronous.
+int set_fx_scales(slbm_s* h) {
+  constexpr int Q = kMaxN * kMaxN;
+  unsigned* d = h->at<unsigned>(h->lay.partials);  // scratch: 2 Q words
+  SLBM_CK(h, cudaMemsetAsync(d, 0, 2 * Q * sizeof(unsigned), h->st), "memset");
+  SLBM_CK(h, launch_fx_range(h->pf, h->at<double>(h->lay.macro[0]), h->at<double>(h->lay.macro[1]),
+                             h->at<double>(h->lay.macro[2]), d, h->st),
+          "fixed-point range launch");
+  unsigned bits[2 * Q];
+  SLBM_CK(h, cudaMemcpyAsync(bits, d, sizeof(bits), cudaMemcpyDeviceToHost, h->st), "D2H copy");
+  SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
+  const Lattice1D L[2] = {make_1d(h->nlo), make_1d(h->nhi)};
+  for (int k = 0; k < 2; ++k)
+    for (int i = 0; i < L[k].n * L[k].n; ++i) {
+      float m;
+      std::memcpy(&m, &bits[k * Q + i], sizeof(m));
+      const double W = L[k].w[i % L[k].n] * L[k].w[i / L[k].n];
+      h->fx_sc[k][i] = (float)(std::max(2.0 * (double)m, 0.25 * W) / 32767.0);
+    }
+  refresh_params(h);
+  return SLBM_OK;
+}
+
 int init_eq_dev(slbm_s* h, bool with_T = false) {
   cudaError_t e;
   double* r = h->at<double>(h->lay.macro[0]);
@@ -941,7 +976,7 @@ bool create_args_ok(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int 
     snprintf(g_create_err, sizeof(g_create_err), "unknown frame");
     return false;
   }
-  if (frame != SLBM_FRAME_LATTICE && precision == SLBM_FP16) {
+  if (frame != SLBM_FRAME_LATTICE && (precision == SLBM_FP16 || precision == SLBM_FX16)) {
     snprintf(g_create_err, sizeof(g_create_err), "the co-moving frame runs in FP32 or FP64");
     return false;
   }
@@ -1118,6 +1153,14 @@ int slbm_create_in(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int i
   h->ind_interval = 1;
   h->ind_thr = 0.0;
   for (int s = 0; s < 4; ++s) h->bc_kind[s] = SLBM_BC_OUTFLOW;
+  {  // fixed-point scales before the first slbm_init_equilibrium: range +-W_i / 4
+    const Lattice1D L[2] = {make_1d(lat_lo), make_1d(lat_hi)};
+    for (int k = 0; k < 2; ++k)
+      for (int i = 0; i < kMaxN * kMaxN; ++i)
+        h->fx_sc[k][i] = i < L[k].n * L[k].n
+                             ? (float)(0.25 * L[k].w[i % L[k].n] * L[k].w[i / L[k].n] / 32767.0)
+                             : 1.0f;
+  }
   refresh_params(h);
   // zero everything (finite stale values), flags 0, then rest state rho = 1, u = 0
   if (cudaMemsetAsync(h->ws, 0, lay.total, h->st) != cudaSuccess) {
@@ -1215,6 +1258,7 @@ int slbm_init_equilibrium(slbm_t h, const double* rho, const double* ux, const d
   if ((rc = upload(h, h->at<double>(h->lay.macro[1]), ux, b))) return rc;
   if ((rc = upload(h, h->at<double>(h->lay.macro[2]), uy, b))) return rc;
   if (T && (rc = upload(h, h->at<double>(h->lay.macro[3]), T, b))) return rc;
+  if (h->precision == SLBM_FX16 && (rc = set_fx_scales(h))) return rc;
   if ((rc = init_eq_dev(h, T != nullptr))) return rc;
   // the caller may reuse its arrays on return
   SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
@@ -1398,7 +1442,7 @@ int slbm_lattice_loss(slbm_t h, double* loss) {
   for (uint8_t v : fl)
     if (v != 1 && v != kFlagGap)
       return fail(h, SLBM_EINVAL, "the lattice loss starts from an all-high-order state");
-  const size_t es = h->precision == SLBM_FP64 ? 8 : (h->precision == SLBM_FP16 ? 2 : 4);
+  const size_t es = (size_t)elem_size(h->precision);
   const size_t bytes = (size_t)(h->nhi * h->nhi) * h->lay.plane * es;
   char* tmp = nullptr;
   if (cudaMalloc(&tmp, 2 * bytes + nc * sizeof(double)) != cudaSuccess) {

@@ -18,7 +18,7 @@ __device__ __forceinline__ void load_dev(const LatTab<R>& L, const S* f, long lo
                                          R (*s)[kMaxN]) {
   for (int iy = 0; iy < L.n; ++iy)
     for (int ix = 0; ix < L.n; ++ix)
-      s[iy][ix] = static_cast<R>(f[(size_t)(ix + L.n * iy) * plane + base]);
+      s[iy][ix] = from_s<R>(f[(size_t)(ix + L.n * iy) * plane + base], L.sc[ix + L.n * iy]);
 }
 
 template <class S, class R>
@@ -26,7 +26,7 @@ __device__ __forceinline__ void store_dev(const LatTab<R>& L, S* f, long long pl
                                           const R (*s)[kMaxN]) {
   for (int iy = 0; iy < L.n; ++iy)
     for (int ix = 0; ix < L.n; ++ix)
-      f[(size_t)(ix + L.n * iy) * plane + base] = static_cast<S>(s[iy][ix]);
+      f[(size_t)(ix + L.n * iy) * plane + base] = to_s<S, R>(s[iy][ix], L.isc[ix + L.n * iy]);
 }
 
 // rho of an interior cell from its own lattice (FP64 sum of 1 + deviations).
@@ -38,7 +38,7 @@ __device__ double cell_rho(const Params<R>& p, const S* f0, const S* f1, const u
   const S* f = k ? f1 : f0;
   const int base = (y + p.G) * p.pitch + (x + kOX);
   double r = 1.0;
-  for (int i = 0; i < n * n; ++i) r += (double)f[(size_t)i * p.plane + base];
+  for (int i = 0; i < n * n; ++i) r += (double)from_s<R>(f[(size_t)i * p.plane + base], p.lat[k].sc[i]);
   return r;
 }
 
@@ -81,7 +81,7 @@ __global__ void k_ghosts(const Params<R> p, S* f0, S* f1, const uint8_t* __restr
         if (n == 3) v = diffuse_value<3, S, R>(p.lat[k], f, p.plane, sbase, side, uwx, uwy, i);
         else if (n == 4) v = diffuse_value<4, S, R>(p.lat[k], f, p.plane, sbase, side, uwx, uwy, i);
         else v = diffuse_value<5, S, R>(p.lat[k], f, p.plane, sbase, side, uwx, uwy, i);
-        f[(size_t)i * p.plane + gbase] = static_cast<S>(v);
+        f[(size_t)i * p.plane + gbase] = to_s<S, R>(v, p.lat[k].isc[i]);
       }
     }
   } else {
@@ -126,13 +126,15 @@ __device__ void cell_moments(const Params<R>& p, const S* f0, const S* f1, int k
   e = 1.0;  // sum W_i |c_i|^2 / 2 = D T_L / 2 = 1
   for (int iy = 0; iy < L.n; ++iy)
     for (int ix = 0; ix < L.n; ++ix) {
-      const double v = (double)f[(size_t)(ix + L.n * iy) * p.plane + base];
+      const double v =
+          (double)from_s<R>(f[(size_t)(ix + L.n * iy) * p.plane + base], L.sc[ix + L.n * iy]);
       const double cx = (double)L.c[ix], cy = (double)L.c[iy];
       r += v;
       jx += cx * v;
       jy += cy * v;
       e += 0.5 * (cx * cx + cy * cy) * v;
     }
+  if constexpr (!is_fx16<S>())  // co-moving frames (lam) never store fixed point
   if (lam) {
     const long long nc = (long long)p.nx * p.ny;
     const double ux = (double)lam[c], uy = (double)lam[nc + c], T = (double)lam[2 * nc + c];
@@ -144,7 +146,7 @@ __device__ void cell_moments(const Params<R>& p, const S* f0, const S* f1, int k
     const S* g = k ? e1 : e0;
     if (g) {  // sum g = T (sum e + C_v - 1)
       double sg = p.cv - 1.0;
-      for (int i = 0; i < L.n * L.n; ++i) sg += (double)g[(size_t)i * p.plane + base];
+      for (int i = 0; i < L.n * L.n; ++i) sg += (double)from_s<R>(g[(size_t)i * p.plane + base], R(1));
       e += T * sg;
     }
   }
@@ -256,9 +258,9 @@ __global__ void k_pack(const Params<R> p, int k, int i0, int cnt, const S* f, do
     const int x = (int)(c % p.nx), y = (int)(c / p.nx);
     const size_t e = (size_t)i * p.plane + (y + p.G) * p.pitch + (x + kOX);
     if (unpack)
-      fw[e] = static_cast<S>(in[t] - Wi);
+      fw[e] = to_s<S, R>((R)(in[t] - Wi), L.isc[i]);
     else
-      out[t] = static_cast<double>(f[e]) + Wi;
+      out[t] = (double)from_s<R>(f[e], L.sc[i]) + Wi;
   }
 }
 
@@ -399,6 +401,50 @@ cudaError_t launch_pack(const Params<R>& p, int k, int i0, int cnt, const S* f, 
   return cudaGetLastError();
 }
 
+// Largest |f^L_i(rho, u) - W_i| of every plane i of both lattices over the
+// cells' equilibria, into out[k * 25 + i] as float bits (nonnegative floats
+// order like their bit patterns; out zeroed by the caller).
+__global__ void __launch_bounds__(kThreads)
+k_fx_range(const Params<float> p, const double* __restrict__ rho, const double* __restrict__ ux,
+           const double* __restrict__ uy, unsigned* __restrict__ out) {
+  constexpr int Q = kMaxN * kMaxN;
+  float m[2][Q];
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) m[k][i] = 0.f;
+  const long long nc = (long long)p.nx * p.ny;
+  for (long long c = (long long)blockIdx.x * kThreads + threadIdx.x; c < nc;
+       c += (long long)gridDim.x * kThreads) {
+    for (int k = 0; k < 2; ++k) {
+      float e[kMaxN][kMaxN];
+      const int n = p.lat[k].n;
+      eq_dev<float>(p.lat[k], n, (float)(rho[c] - 1.0), (float)ux[c], (float)uy[c], e);
+#pragma unroll
+      for (int iy = 0; iy < kMaxN; ++iy)
+#pragma unroll
+        for (int ix = 0; ix < kMaxN; ++ix)
+          if (iy < n && ix < n) m[k][ix + n * iy] = fmaxf(m[k][ix + n * iy], fabsf(e[iy][ix]));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const unsigned b = __reduce_max_sync(0xffffffffu, __float_as_uint(m[k][i]));
+      if ((threadIdx.x & 31) == 0 && b) atomicMax(out + k * Q + i, b);
+    }
+}
+
+cudaError_t launch_fx_range(const Params<float>& p, const double* rho, const double* ux,
+                            const double* uy, unsigned* out, cudaStream_t st) {
+  const long long nc = (long long)p.nx * p.ny;
+  long long blocks = (nc + kThreads - 1) / kThreads;
+  if (blocks > 8LL * p.nsm) blocks = 8LL * p.nsm;
+  k_fx_range<<<(unsigned)(blocks > 0 ? blocks : 1), kThreads, 0, st>>>(p, rho, ux, uy, out);
+  return cudaGetLastError();
+}
+
 #define SLBM_AUX_INST(S, R)                                                                  \
   template cudaError_t launch_ghosts<S, R>(const Params<R>&, S*, S*, const uint8_t*,         \
                                            const BcDev&, cudaStream_t);                      \
@@ -418,6 +464,7 @@ cudaError_t launch_pack(const Params<R>& p, int k, int i0, int cnt, const S* f, 
 SLBM_AUX_INST(float, float)
 SLBM_AUX_INST(double, double)
 SLBM_AUX_INST(__half, float)
+SLBM_AUX_INST(fx16, float)
 #undef SLBM_AUX_INST
 
 }  // namespace slbm

@@ -124,7 +124,7 @@ __device__ __forceinline__ R diffuse_value(const LatTab<R>& L, const S* f, long 
       const R cn = (axis_y ? L.c[jy] : L.c[jx]) * nsign;
       const R w = L.w1[jx] * L.w1[jy];
       const R e = L.w1[jx] * dy[jy] + dx[jx] * L.w1[jy] + dx[jx] * dy[jy];
-      const R sj = static_cast<R>(__ldcg(f + (size_t)j * plane + sbase));
+      const R sj = from_s<R>(ldcg_s(f + (size_t)j * plane + sbase), L.sc[j]);
       if (cn < R(0)) s_out -= cn * sj;
       if (cn > R(0)) {
         e_in += cn * e;
@@ -164,20 +164,26 @@ __device__ __forceinline__ R inlet_value(const Params<R>& p, int k, int i, R dr,
   return dr * px * py + L.w1[ix] * dyi + dxi * L.w1[iy] + dxi * dyi;
 }
 
+// The N x N populations of lattice L at element `base` of its planes f, in
+// the arithmetic type (load_t), and back to storage (store_t).
 template <int N, class S, class R>
-__device__ __forceinline__ void load_t(const S* f, long long plane, int base, R (*s)[kMaxN]) {
+__device__ __forceinline__ void load_t(const LatTab<R>& L, const S* f, long long plane, int base,
+                                       R (*s)[kMaxN]) {
 #pragma unroll
   for (int iy = 0; iy < N; ++iy)
 #pragma unroll
-    for (int ix = 0; ix < N; ++ix) s[iy][ix] = static_cast<R>(f[(size_t)(ix + N * iy) * plane + base]);
+    for (int ix = 0; ix < N; ++ix)
+      s[iy][ix] = from_s<R>(f[(size_t)(ix + N * iy) * plane + base], L.sc[ix + N * iy]);
 }
 
 template <int N, class S, class R>
-__device__ __forceinline__ void store_t(S* f, long long plane, int base, const R (*s)[kMaxN]) {
+__device__ __forceinline__ void store_t(const LatTab<R>& L, S* f, long long plane, int base,
+                                        const R (*s)[kMaxN]) {
 #pragma unroll
   for (int iy = 0; iy < N; ++iy)
 #pragma unroll
-    for (int ix = 0; ix < N; ++ix) f[(size_t)(ix + N * iy) * plane + base] = static_cast<S>(s[iy][ix]);
+    for (int ix = 0; ix < N; ++ix)
+      f[(size_t)(ix + N * iy) * plane + base] = to_s<S, R>(s[iy][ix], L.isc[ix + N * iy]);
 }
 
 // Ghost coordinates along one axis that are copies of interior coordinate v
@@ -202,9 +208,9 @@ template <int NL, int NH, class S, class R>
 __device__ void write_eq_t(const Params<R>& p, S* f0, S* f1, int base, R dr, R ux, R uy) {
   R e[kMaxN][kMaxN];
   eq_dev<R>(p.lat[0], NL, dr, ux, uy, e);
-  store_t<NL, S, R>(f0, p.plane, base, e);
+  store_t<NL, S, R>(p.lat[0], f0, p.plane, base, e);
   eq_dev<R>(p.lat[1], NH, dr, ux, uy, e);
-  store_t<NH, S, R>(f1, p.plane, base, e);
+  store_t<NH, S, R>(p.lat[1], f1, p.plane, base, e);
 }
 
 // INLET ghosts fed by interior cell (x, y) (density deviation dr): the

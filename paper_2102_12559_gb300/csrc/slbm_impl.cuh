@@ -24,6 +24,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace slbm {
 
 constexpr int kMaxN = 5;        // largest 1-D node count (D1Q5)
@@ -60,7 +62,62 @@ struct LatTab {
   // constants through exactly even with rounded weights.
   R w[kMaxN][kMaxP];
   R vinv[kMaxN][kMaxN];         // inverse Vandermonde: phi_j(u) = sum_m vinv[j][m] h_m(u)
+  // 16-bit fixed-point storage (SLBM_FX16): plane i holds round(s_i / sc[i]),
+  // s_i = f_i - W_i; isc = 1 / sc.  Unused by the other storage types.
+  R sc[kMaxN * kMaxN];
+  R isc[kMaxN * kMaxN];
 };
+
+// 16-bit fixed-point storage of a deviation: value = v * (its plane's scale).
+struct fx16 {
+  int16_t v;
+};
+template <class S>
+__host__ __device__ constexpr bool is_fx16() {
+  return std::is_same<S, fx16>::value;
+}
+
+// A stored population value in the arithmetic type: plain conversion, or for
+// fixed point v times the plane's scale sc.
+template <class R, class S>
+__device__ __forceinline__ R from_s(S v, R) {
+  return static_cast<R>(v);
+}
+template <class R>
+__device__ __forceinline__ R from_s(fx16 v, R sc) {
+  return sc * static_cast<R>(v.v);
+}
+
+// A value to storage, rounded to nearest: plain conversion, or for fixed
+// point round(v * isc), saturating at +-32767.
+template <class S, class R>
+__device__ __forceinline__ S to_s(R v, R) {
+  return static_cast<S>(v);
+}
+template <>
+__device__ __forceinline__ fx16 to_s<fx16, float>(float v, float isc) {
+  const float q = fminf(fmaxf(rintf(v * isc), -32767.f), 32767.f);
+  return fx16{(int16_t)__float2int_rn(q)};
+}
+
+// Loads through the read-only path (ld.global.nc) and through L2
+// (ld.global.cg) of a stored element; fixed point as its raw 16 bits.
+template <class S>
+__device__ __forceinline__ S ldg_s(const S* a) {
+  return __ldg(a);
+}
+template <>
+__device__ __forceinline__ fx16 ldg_s<fx16>(const fx16* a) {
+  return fx16{__ldg(reinterpret_cast<const short*>(a))};
+}
+template <class S>
+__device__ __forceinline__ S ldcg_s(const S* a) {
+  return __ldcg(a);
+}
+template <>
+__device__ __forceinline__ fx16 ldcg_s<fx16>(const fx16* a) {
+  return fx16{__ldcg(reinterpret_cast<const short*>(a))};
+}
 
 // Interface conversion tables.
 template <class R>
@@ -364,6 +421,12 @@ cudaError_t launch_post_step(const Params<R>& p, S* f0, S* f1, const uint8_t* fl
                              const uint8_t* flag_new, const BcDev& bc, const int* work,
                              const int* list, const int* nlist, const GhostTables& gt,
                              cudaStream_t st);
+
+// Largest |f^L_i - W_i| per plane of both lattices over the equilibria at
+// (rho, u) of every cell, as float bits into out[k * 25 + i] (zeroed by the
+// caller): the range of the SLBM_FX16 plane scales.
+cudaError_t launch_fx_range(const Params<float>& p, const double* rho, const double* ux,
+                            const double* uy, unsigned* out, cudaStream_t st);
 
 template <class S, class R>
 cudaError_t launch_init_eq(const Params<R>& p, S* f0, S* f1, const double* rho,

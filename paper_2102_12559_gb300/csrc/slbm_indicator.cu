@@ -50,7 +50,7 @@ __device__ __forceinline__ void raw_moments(const Params<R>& p, const LatTab<R>&
     R r0 = R(0), r1 = R(0), r2 = R(0), r3 = R(0);
 #pragma unroll
     for (int ix = 0; ix < N; ++ix) {
-      const R v = static_cast<R>(f[(size_t)(ix + N * iy) * p.plane + base]);
+      const R v = from_s<R>(f[(size_t)(ix + N * iy) * p.plane + base], L.sc[ix + N * iy]);
       const R cx = L.c[ix];
       r0 += v;
       r1 += cx * v;
@@ -408,8 +408,8 @@ k_lattice_loss(const Params<R> p, const S* __restrict__ a, const S* __restrict__
   const int q = p.lat[1].n * p.lat[1].n;
   double sa = 0.0, d2 = 0.0;
   for (int i = 0; i < q; ++i) {
-    const double va = (double)static_cast<R>(a[(size_t)i * p.plane + base]);
-    const double vb = (double)static_cast<R>(b[(size_t)i * p.plane + base]);
+    const double va = (double)from_s<R>(a[(size_t)i * p.plane + base], p.lat[1].sc[i]);
+    const double vb = (double)from_s<R>(b[(size_t)i * p.plane + base], p.lat[1].sc[i]);
     sa += va;
     d2 += (va - vb) * (va - vb);
   }
@@ -802,6 +802,7 @@ cudaError_t launch_mlp_train(const float* x, const float* y, const int* idx, int
 SLBM_IND_INST(float, float)
 SLBM_IND_INST(double, double)
 SLBM_IND_INST(__half, float)
+SLBM_IND_INST(fx16, float)
 #undef SLBM_IND_INST
 
 }  // namespace slbm

@@ -29,6 +29,15 @@ cudaError_t launch_post<__half, float>(const Params<float>& p, __half* f0, __hal
                                          tile_mask, st);
 }
 
+template <>
+cudaError_t launch_post<fx16, float>(const Params<float>& p, fx16* f0, fx16* f1,
+                                     const uint8_t* flag_old, const uint8_t* flag_new,
+                                     const BcDev& bc, int images, const uint8_t* mask_in,
+                                     uint8_t* tile_mask, cudaStream_t st) {
+  return launch_post_impl<fx16, float>(p, f0, f1, flag_old, flag_new, bc, images, mask_in,
+                                       tile_mask, st);
+}
+
 #define SLBM_POSTSTEP_INST(S, R)                                                             \
   template <>                                                                                \
   cudaError_t launch_post_step<S, R>(const Params<R>& p, S* f0, S* f1,                       \
@@ -42,5 +51,6 @@ cudaError_t launch_post<__half, float>(const Params<float>& p, __half* f0, __hal
 SLBM_POSTSTEP_INST(float, float)
 SLBM_POSTSTEP_INST(double, double)
 SLBM_POSTSTEP_INST(__half, float)
+SLBM_POSTSTEP_INST(fx16, float)
 #undef SLBM_POSTSTEP_INST
 }  // namespace slbm

@@ -196,20 +196,20 @@ __device__ __forceinline__ bool post_tile(const Params<R>& p, S* f0, S* f1,
     R a[kMaxN][kMaxN], b[kMaxN][kMaxN];
     using M = PostMath<NL, NH, R>;
     if (o == 0) {
-      load_t<NL, S, R>(f0, p.plane, base, a);
+      load_t<NL, S, R>(p.lat[0], f0, p.plane, base, a);
       M::lift(p, a, b);
-      store_t<NH, S, R>(f1, p.plane, base, b);
+      store_t<NH, S, R>(p.lat[1], f1, p.plane, base, b);
       if (o != nn && bd) {  // now high-order; low-order readers see its projection
         M::project(p, b, a);
-        store_t<NL, S, R>(f0, p.plane, base, a);
+        store_t<NL, S, R>(p.lat[0], f0, p.plane, base, a);
       }
     } else {
-      load_t<NH, S, R>(f1, p.plane, base, b);
+      load_t<NH, S, R>(p.lat[1], f1, p.plane, base, b);
       M::project(p, b, a);
-      store_t<NL, S, R>(f0, p.plane, base, a);
+      store_t<NL, S, R>(p.lat[0], f0, p.plane, base, a);
       if (o != nn && bd) {  // now low-order; high-order readers see its lifting
         M::lift(p, a, b);
-        store_t<NH, S, R>(f1, p.plane, base, b);
+        store_t<NH, S, R>(p.lat[1], f1, p.plane, base, b);
       }
     }
   }
@@ -299,10 +299,12 @@ __device__ __forceinline__ void tile_ghosts(const Params<R>& p, S* f0, S* f1,
         R dr = R(0);
         if (__ldcg(flag + sx + p.nx * sy)) {
 #pragma unroll
-          for (int j = 0; j < q1; ++j) dr += static_cast<R>(__ldcg(f1 + (size_t)j * p.plane + sb));
+          for (int j = 0; j < q1; ++j)
+            dr += from_s<R>(ldcg_s(f1 + (size_t)j * p.plane + sb), p.lat[1].sc[j]);
         } else {
 #pragma unroll
-          for (int j = 0; j < q0; ++j) dr += static_cast<R>(__ldcg(f0 + (size_t)j * p.plane + sb));
+          for (int j = 0; j < q0; ++j)
+            dr += from_s<R>(ldcg_s(f0 + (size_t)j * p.plane + sb), p.lat[0].sc[j]);
         }
         s_dr[tid] = dr;
       }
@@ -325,15 +327,17 @@ __device__ __forceinline__ void tile_ghosts(const Params<R>& p, S* f0, S* f1,
         const size_t off = (size_t)i * p.plane;
         dst[u] = f + off + s_gb[j];
         if (kind == 0) {
-          val[u] = __ldcg(f + off + s_sb[j]);
+          val[u] = ldcg_s(f + off + s_sb[j]);
         } else if (kind == 3) {
-          val[u] = static_cast<S>(
+          val[u] = to_s<S, R>(
               k ? diffuse_value<NH, S, R>(p.lat[1], f1, p.plane, s_sb[j], s_side[j], s_ux[j],
                                           s_uy[j], i)
                 : diffuse_value<NL, S, R>(p.lat[0], f0, p.plane, s_sb[j], s_side[j], s_ux[j],
-                                          s_uy[j], i));
+                                          s_uy[j], i),
+              p.lat[k].isc[i]);
         } else {
-          val[u] = static_cast<S>(inlet_value<NL, NH, R>(p, k, i, s_dr[j], s_ux[j], s_uy[j]));
+          val[u] = to_s<S, R>(inlet_value<NL, NH, R>(p, k, i, s_dr[j], s_ux[j], s_uy[j]),
+                              p.lat[k].isc[i]);
         }
       }
 #pragma unroll
@@ -444,7 +448,7 @@ __device__ __forceinline__ void diffuse_cell(const LatTab<R>& L, S* f, long long
       const R cn = (axis_y ? L.c[jy] : L.c[jx]) * nsign;
       const R w = L.w1[jx] * L.w1[jy];
       const R e = L.w1[jx] * dy[jy] + dx[jx] * L.w1[jy] + dx[jx] * dy[jy];
-      sv[j] = static_cast<R>(__ldcg(f + (size_t)j * plane + sb));
+      sv[j] = from_s<R>(ldcg_s(f + (size_t)j * plane + sb), L.sc[j]);
       if (cn < R(0)) s_out -= cn * sv[j];
       if (cn > R(0)) {
         e_in += cn * e;
@@ -460,7 +464,7 @@ __device__ __forceinline__ void diffuse_cell(const LatTab<R>& L, S* f, long long
       const R cn = (axis_y ? L.c[jy] : L.c[jx]) * nsign;
       const R w = L.w1[jx] * L.w1[jy];
       const R e = L.w1[jx] * dy[jy] + dx[jx] * L.w1[jy] + dx[jx] * dy[jy];
-      f[(size_t)j * plane + gb] = static_cast<S>(cn > R(0) ? drw * (w + e) + e : sv[j]);
+      f[(size_t)j * plane + gb] = to_s<S, R>(cn > R(0) ? drw * (w + e) + e : sv[j], L.isc[j]);
     }
 }
 
@@ -484,11 +488,11 @@ __device__ __forceinline__ void lane_ghost(const Params<R>& p, S* f0, S* f1,
   if (kind == 0) {
     S v[q1];
 #pragma unroll
-    for (int i = 0; i < q0; ++i) v[i] = __ldcg(f0 + (size_t)i * p.plane + sb);
+    for (int i = 0; i < q0; ++i) v[i] = ldcg_s(f0 + (size_t)i * p.plane + sb);
 #pragma unroll
     for (int i = 0; i < q0; ++i) f0[(size_t)i * p.plane + gb] = v[i];
 #pragma unroll
-    for (int i = 0; i < q1; ++i) v[i] = __ldcg(f1 + (size_t)i * p.plane + sb);
+    for (int i = 0; i < q1; ++i) v[i] = ldcg_s(f1 + (size_t)i * p.plane + sb);
 #pragma unroll
     for (int i = 0; i < q1; ++i) f1[(size_t)i * p.plane + gb] = v[i];
   } else if (kind == 3) {
@@ -499,10 +503,12 @@ __device__ __forceinline__ void lane_ghost(const Params<R>& p, S* f0, S* f1,
     R dr = R(0);
     if (__ldcg(flag + sx + p.nx * sy)) {
 #pragma unroll
-      for (int j = 0; j < q1; ++j) dr += static_cast<R>(__ldcg(f1 + (size_t)j * p.plane + sb));
+      for (int j = 0; j < q1; ++j)
+        dr += from_s<R>(ldcg_s(f1 + (size_t)j * p.plane + sb), p.lat[1].sc[j]);
     } else {
 #pragma unroll
-      for (int j = 0; j < q0; ++j) dr += static_cast<R>(__ldcg(f0 + (size_t)j * p.plane + sb));
+      for (int j = 0; j < q0; ++j)
+        dr += from_s<R>(ldcg_s(f0 + (size_t)j * p.plane + sb), p.lat[0].sc[j]);
     }
     write_eq_t<NL, NH, S, R>(p, f0, f1, gb, dr, (R)ghost_ux(bc, side, bi),
                              (R)ghost_uy(bc, side, bi));
@@ -641,20 +647,20 @@ __device__ __forceinline__ void warp_convert(const Params<R>& p, S* f0, S* f1,
       const int base_el = (y0 + i + p.G) * p.pitch + (x0 + col + kOX);
       R a[kMaxN][kMaxN], b[kMaxN][kMaxN];
       if (pass == 0) {  // computed in the low-order lattice
-        load_t<NL, S, R>(f0, p.plane, base_el, a);
+        load_t<NL, S, R>(p.lat[0], f0, p.plane, base_el, a);
         M::lift(p, a, b);
-        store_t<NH, S, R>(f1, p.plane, base_el, b);
+        store_t<NH, S, R>(p.lat[1], f1, p.plane, base_el, b);
         if (nw == 1 && band) {  // now high-order; low-order readers see its projection
           M::project(p, b, a);
-          store_t<NL, S, R>(f0, p.plane, base_el, a);
+          store_t<NL, S, R>(p.lat[0], f0, p.plane, base_el, a);
         }
       } else {
-        load_t<NH, S, R>(f1, p.plane, base_el, b);
+        load_t<NH, S, R>(p.lat[1], f1, p.plane, base_el, b);
         M::project(p, b, a);
-        store_t<NL, S, R>(f0, p.plane, base_el, a);
+        store_t<NL, S, R>(p.lat[0], f0, p.plane, base_el, a);
         if (nw == 0 && band) {  // now low-order; high-order readers see its lifting
           M::lift(p, a, b);
-          store_t<NH, S, R>(f1, p.plane, base_el, b);
+          store_t<NH, S, R>(p.lat[1], f1, p.plane, base_el, b);
         }
       }
     }

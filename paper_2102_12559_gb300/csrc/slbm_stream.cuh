@@ -86,15 +86,23 @@ __device__ __forceinline__ uint32_t pop_random(uint32_t key, int i) {
 }
 
 template <class S, class R>
-__device__ __forceinline__ S to_storage(R v, uint32_t) {
+__device__ __forceinline__ S to_storage(R v, uint32_t, R) {
   return static_cast<S>(v);
 }
 
 template <>
-__device__ __forceinline__ __half to_storage<__half, float>(float v, uint32_t r) {
+__device__ __forceinline__ __half to_storage<__half, float>(float v, uint32_t r, float) {
   if (!(fabsf(v) >= 6.103515625e-05f) || fabsf(v) >= 65504.0f) return __float2half_rn(v);
   const uint32_t b = __float_as_uint(v);
   return __float2half_rz(__uint_as_float((b + r) & ~0x1fffu));
+}
+
+// Fixed point: floor(v * isc + r / 2^13), saturating at +-32767 -- rounded up
+// with probability equal to the distance from the value below, as above.
+template <>
+__device__ __forceinline__ fx16 to_storage<fx16, float>(float v, uint32_t r, float isc) {
+  const float q = floorf(fmaf(v, isc, (float)r * (1.0f / 8192.0f)));
+  return fx16{(int16_t)__float2int_rz(fminf(fmaxf(q, -32767.f), 32767.f))};
 }
 
 // One row of node jx's stencil at plane row pointer `row` (elements a = 0 ..
@@ -103,23 +111,27 @@ __device__ __forceinline__ __half to_storage<__half, float>(float v, uint32_t r)
 template <int P, class S, class R>
 __device__ __forceinline__ R row_interp(const S* __restrict__ row, const R* w) {
   constexpr int r = (P - 1) / 2;
-  const R vr = static_cast<R>(__ldg(row + r));
+  const R vr = from_s<R>(ldg_s(row + r), R(1));
   R t = vr;
 #pragma unroll
   for (int a = 0; a < P; ++a)
-    if (a != r) t += w[a] * (static_cast<R>(__ldg(row + a)) - vr);
+    if (a != r) t += w[a] * (from_s<R>(ldg_s(row + a), R(1)) - vr);
   return t;
 }
 
 // Value of population I's stencil row at plane row pointer `row`: a single
-// tap (integer x shift) or the x-interpolation.
+// tap (integer x shift) or the x-interpolation.  Fixed point: the taps stay
+// integers and the plane's scale multiplies the row's result once.
 template <int N, bool HI, int P, int I, class S, class R>
 __device__ __forceinline__ R tap_row(const LatTab<R>& L, const S* __restrict__ row) {
   constexpr int jx = I % N;
+  R v;
   if constexpr (node_snapped(N, HI, jx))
-    return static_cast<R>(__ldg(row));
+    v = from_s<R>(ldg_s(row), R(1));
   else
-    return row_interp<P, S, R>(row, L.w[jx]);
+    v = row_interp<P, S, R>(row, L.w[jx]);
+  if constexpr (is_fx16<S>()) v *= L.sc[I];
+  return v;
 }
 
 // x offset (first column relative to the cell) of population I's stencil
@@ -261,7 +273,8 @@ __device__ __forceinline__ void collide(const Params<R>& p, const LatTab<R>& L, 
   if (store) {
     const int pl = (int)p.plane;
 #pragma unroll
-    for (int i = 0; i < N * N; ++i) o[i * pl] = to_storage<S, R>(f[i], pop_random(key, i));
+    for (int i = 0; i < N * N; ++i)
+      o[i * pl] = to_storage<S, R>(f[i], pop_random(key, i), L.isc[i]);
   }
 }
 

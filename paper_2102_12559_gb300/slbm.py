@@ -23,7 +23,7 @@ SLBM_ENONFINITE, SLBM_ENOCONV, SLBM_ETIMEOUT, SLBM_ESTATE = -4, -5, -6, -7
 SLBM_D2Q9, SLBM_D2Q16, SLBM_D2Q25 = 3, 4, 5
 SLBM_FRAME_LATTICE, SLBM_FRAME_POND, SLBM_FRAME_POND_ISOTHERMAL = 0, 1, 2
 SLBM_POND_REACH = 5
-SLBM_FP32, SLBM_FP64, SLBM_FP16 = 0, 1, 2
+SLBM_FP32, SLBM_FP64, SLBM_FP16, SLBM_FX16 = 0, 1, 2, 3
 SLBM_BC_OUTFLOW, SLBM_BC_DIRICHLET, SLBM_BC_INLET, SLBM_BC_DIFFUSE = 0, 1, 2, 3
 SLBM_SIDE_XMIN, SLBM_SIDE_XMAX, SLBM_SIDE_YMIN, SLBM_SIDE_YMAX = 0, 1, 2, 3
 SLBM_CRIT_NONE, SLBM_CRIT_MACH, SLBM_CRIT_MLP, SLBM_CRIT_MLP_REFINE = 0, 1, 2, 3

@@ -1,0 +1,140 @@
+"""16-bit fixed-point storage of the deviations s_i = f_i - W_i (SLBM_FX16,
+FP32 arithmetic) against the FP64 oracle and against the FP32 path.
+
+Tolerances.  Plane i of a lattice stores round(s_i / sc_i) in 16 bits with
+sc_i = max(2 max|s_i|, W_i / 4) / 32767 over the initial equilibria, so a
+stored value is off by at most one step sc_i (stochastic rounding in the
+stream-collide kernel, round to nearest elsewhere): 6.1e-5 of twice the
+plane's largest initial deviation, against FP16's 2^-11 of every value.  An
+emulation of this format on the FP64 oracle (rounding the stored deviations
+after every step of the 200-step convected vortex) gives 4.3e-6 on rho and
+6.4e-5 on u; FP16 gives 4e-5 and 6.1e-4 there.  The vortex test therefore
+asserts the 1e-4 relative L2 on u aimed at for the reduced-precision form
+(the test that FP16 fails, `test_gpu_fp16.py`), and 2e-5 on rho.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2102_12559_gb300 import workloads as WL
+from paper_2102_12559_gb300 import slbm
+
+pytestmark = pytest.mark.gpu
+
+FX16, FP16, FP32 = slbm.SLBM_FX16, slbm.SLBM_FP16, slbm.SLBM_FP32
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def test_info_and_workspace():
+    g = slbm.Solver(64, 48, 3, 5, tau=0.6, precision=FX16)
+    assert g.info.precision == FX16
+    n16 = slbm.slbm_workspace_bytes(64, 48, 1, 1, 3, 5, 3, FX16)
+    assert n16 == slbm.slbm_workspace_bytes(64, 48, 1, 1, 3, 5, 3, FP16)
+    assert n16 < slbm.slbm_workspace_bytes(64, 48, 1, 1, 3, 5, 3, FP32)
+
+
+def test_uniform_flow_fx16():
+    N = 48
+    g = slbm.Solver(N, N, 3, 5, tau=0.55, precision=FX16)
+    g.init_equilibrium(*WL.uniform(N, N, 1.2, 0.25, -0.15))
+    g.set_flags(WL.random_flags(N, N, seed=3))
+    g.step(20)
+    r, u, v, _ = g.moments()
+    assert abs(r - 1.2).max() < 5e-5 and abs(u - 0.25).max() < 5e-5 and abs(v + 0.15).max() < 5e-5
+
+
+def test_init_within_one_step_of_the_oracle():
+    """The initial equilibria of a Mach 0.9 vortex field, both lattices, are
+    stored within one scale step of the FP64 values: the scales cover the
+    field (no saturation)."""
+    n = 96
+    fields = WL.random_vortex_field(n, 6, seed=7, rmin=6.0, rmax=20.0, umax=0.9)[:3]
+    g = slbm.Solver(n, n, 3, 5, tau=0.6, precision=FX16)
+    o = O.Oracle(n, n, 3, 5, tau=0.6)
+    for s in (g, o):
+        s.init_equilibrium(*fields)
+    for k in (0, 1):
+        a, b = g.get_pops(k), o.get_pops(k)
+        W = O.lattice(o.n[k])[2]
+        smax = np.abs(b - W).max(axis=(0, 1))
+        step = np.maximum(2.0 * smax, 0.25 * W) / 32767.0
+        assert (np.abs(a - b) <= 0.5 * step + 1e-7).all()
+
+
+@pytest.fixture(scope="module")
+def vortex_oracle():
+    L = 64
+    rho, ux, uy, disc = WL.convected_vortex(L)
+    dt = O.Oracle(8, 8, 3, 5, tau=0.6).dt
+    tau = 1e-3 / dt + 0.5
+    o = O.Oracle(L, L, 3, 5, tau=tau, order=3)
+    o.init_equilibrium(rho, ux, uy)
+    o.set_flags(disc)
+    o.step(200)
+    return dict(fields=(rho, ux, uy), disc=disc, tau=tau, mom=o.moments())
+
+
+def test_convected_vortex_fx16_meets_1e4_on_u(vortex_oracle):
+    L = 64
+    g = slbm.Solver(L, L, 3, 5, tau=vortex_oracle["tau"], interp_order=3, precision=FX16)
+    g.init_equilibrium(*vortex_oracle["fields"])
+    g.set_flags(vortex_oracle["disc"])
+    g.step(200)
+    mom, ref = g.moments(), vortex_oracle["mom"]
+    er = rel_l2(mom[0], ref[0])
+    eu = rel_l2(np.stack(mom[1:3]), np.stack(ref[1:3]))
+    ey = rel_l2(mom[2], ref[2])
+    ex = rel_l2(mom[1] - 0.1, ref[1] - 0.1)
+    print(f"FX16 vortex: rel L2 rho {er:.2e}, u {eu:.2e}, u_y {ey:.2e}, u_x - U0 {ex:.2e}")
+    assert er < 2e-5 and eu < 1e-4
+
+
+@pytest.mark.parametrize("n_lo,n_hi", [(3, 4), (3, 5), (4, 5)])
+def test_one_step_fx16_close_to_oracle(n_lo, n_hi):
+    nx, ny = 37, 29
+    fields = WL.perturbed(nx, ny, seed=4, amp_rho=0.05, amp_u=0.2)
+    fl = WL.random_flags(nx, ny, seed=2, blobs=3, rmin=3, rmax=7)
+    g = slbm.Solver(nx, ny, n_lo, n_hi, tau=0.57, precision=FX16)
+    o = O.Oracle(nx, ny, n_lo, n_hi, tau=0.57)
+    for s in (g, o):
+        s.init_equilibrium(*fields)
+        s.set_flags(fl)
+        s.step(1)
+    for k in (0, 1):
+        m = fl == k
+        # |f - W| <= ~0.2 here: a few scale steps of about 1.2e-5
+        np.testing.assert_allclose(g.get_pops(k)[m], o.get_pops(k)[m], rtol=0, atol=5e-5)
+
+
+def test_jet_fx16_tracks_fp32():
+    """The free jet (inlet / outflow / free-stream boundaries, Mach criterion),
+    100 steps: fixed-point storage against the FP32 path.  Measured 1.3e-5 on
+    rho and 1.1e-4 on u (FP16: 5e-5 and 4e-4); the jet's Mach 0.5 core sets
+    the scales of the planes, so the co-flow's smaller deviations keep fewer
+    significant bits than in the vortex."""
+    nx, ny = 256, 128
+    J = WL.free_jet(nx, ny, slot=16, ma_jet=0.5, ma_co=0.05)
+    out = []
+    for prec in (FP32, FX16):
+        g = slbm.Solver(nx, ny, 3, 5, tau=0.55, periodic=(False, False), precision=prec)
+        g.init_equilibrium(J["rho"], J["ux"], J["uy"])
+        g.set_boundary(slbm.SLBM_SIDE_XMIN, slbm.SLBM_BC_INLET, None, J["in_ux"], J["in_uy"])
+        g.set_boundary(slbm.SLBM_SIDE_XMAX, slbm.SLBM_BC_OUTFLOW)
+        for side in (slbm.SLBM_SIDE_YMIN, slbm.SLBM_SIDE_YMAX):
+            g.set_boundary(side, slbm.SLBM_BC_DIRICHLET, np.full(nx, J["fs_rho"]),
+                           np.full(nx, J["fs_ux"]), np.full(nx, J["fs_uy"]))
+        g.set_criterion(slbm.SLBM_CRIT_MACH, 0.3)
+        g.step(100)
+        out.append(g.moments())
+    er = rel_l2(out[1][0], out[0][0])
+    eu = rel_l2(np.stack(out[1][1:3]), np.stack(out[0][1:3]))
+    print(f"FX16 jet vs FP32: rel L2 rho {er:.2e}, u {eu:.2e}")
+    assert er < 3e-5 and eu < 2e-4
+
+
+def test_co_moving_frame_rejects_fx16():
+    with pytest.raises(slbm.SlbmError):
+        slbm.Solver(32, 32, 3, 5, tau=0.6, precision=FX16, frame=slbm.SLBM_FRAME_POND)
