@@ -581,13 +581,15 @@ def headline(args):
         dist.destroy_process_group()
         return
 
-    # ---- reduced-precision arms (rank 0): FP16 storage alone, and FP16 with
-    # the learned indicator every 10 steps and the FP64 audit every 1000
+    # ---- reduced-precision arms (rank 0): FP16 and fixed-point storage
+    # alone, and FP16 with the learned indicator every 10 steps and the FP64
+    # audit every 1000
     weights, ind_train = train_indicator(slbm, WL, stream)
     ind_vortex = indicator_check_vortex(slbm, fields, weights, stream)
     arms = {}
-    for name, learned in (("fp16", False), ("fp16+indicator+audit", True)):
-        r = vortex_arm(slbm, stream, fields, slbm.SLBM_FP16, weights if learned else None)
+    for name, prec, learned in (("fp16", slbm.SLBM_FP16, False), ("fx16", slbm.SLBM_FX16, False),
+                                ("fp16+indicator+audit", slbm.SLBM_FP16, True)):
+        r = vortex_arm(slbm, stream, fields, prec, weights if learned else None)
         r.step(args.warmup)
         if learned:
             ms = time_steps(r, stream, AUDIT_EVERY, 0, audit_every=AUDIT_EVERY)
@@ -601,7 +603,7 @@ def headline(args):
     # the FP64 build of the library
     moms = {}
     for name, prec, learned in (("fp64", slbm.SLBM_FP64, False), ("fp32", slbm.SLBM_FP32, False),
-                                ("fp16", slbm.SLBM_FP16, False),
+                                ("fp16", slbm.SLBM_FP16, False), ("fx16", slbm.SLBM_FX16, False),
                                 ("fp16+indicator+audit", slbm.SLBM_FP16, True)):
         r = vortex_arm(slbm, stream, fields, prec, weights if learned else None)
         if learned:
@@ -668,6 +670,9 @@ def headline(args):
                   "the timed region"),
         "fp16_storage_arm": dict(arm_line("fp16", arms["fp16"]["ms"], arms["fp16"]["kern"]),
                                  form="FP16 storage of f_i - W_i, Mach criterion every step"),
+        "fx16_storage_arm": dict(arm_line("fx16", arms["fx16"]["ms"], arms["fx16"]["kern"]),
+                                 form="16-bit fixed-point storage of f_i - W_i (one scale per "
+                                      "plane), Mach criterion every step"),
         "indicator": {"training": ind_train, "on_this_field": ind_vortex},
         "fp32_parity": {"rel_l2_vs_fp64_at_200_steps": mom_gap(moms["fp32"][0][:3], ref[:3]),
                         "rel_l2_vs_all_d2q25_fp64_at_200_steps": mom_gap(moms["fp32"][0][:3],
