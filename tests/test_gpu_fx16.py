@@ -138,3 +138,54 @@ def test_jet_fx16_tracks_fp32():
 def test_co_moving_frame_rejects_fx16():
     with pytest.raises(slbm.SlbmError):
         slbm.Solver(32, 32, 3, 5, tau=0.6, precision=FX16, frame=slbm.SLBM_FRAME_POND)
+
+
+def test_couette_walls_fx16_tracks_oracle():
+    """Diffuse walls (the wall ghosts' scaled conversions): the shear-driven
+    Couette channel with the high-order lattice in the wall layers, 300 steps,
+    against the FP64 oracle.  The channel starts at rest, so every plane keeps
+    the floor scale W_i / 4 / 32767 and the wall-driven deviations (about
+    0.05 W_i) keep 1 part in 1.5e4.  Measured 2.8e-6 on rho and 1.2e-4 on u;
+    bound 3e-4."""
+    nx, ny = 8, 32
+    fl = np.zeros((ny, nx), np.uint8)
+    fl[:4] = 1
+    fl[-4:] = 1
+    g = slbm.Solver(nx, ny, 3, 4, tau=0.9, periodic=(True, False), precision=FX16)
+    o = O.Oracle(nx, ny, 3, 4, tau=0.9, periodic=(True, False))
+    for obj, gpu in ((g, True), (o, False)):
+        obj.init_equilibrium(*WL.uniform(nx, ny))
+        obj.set_flags(fl)
+        kind = slbm.SLBM_BC_DIFFUSE if gpu else O.BC_DIFFUSE
+        lo, hi = (slbm.SLBM_SIDE_YMIN, slbm.SLBM_SIDE_YMAX) if gpu else (2, 3)
+        fn = obj.set_boundary if gpu else obj.set_bc
+        fn(lo, kind, None, np.full(nx, -0.05), np.zeros(nx))
+        fn(hi, kind, None, np.full(nx, 0.05), np.zeros(nx))
+    g.step(300)
+    o.step(300)
+    mg, mo = g.moments(), o.moments()
+    er = rel_l2(mg[0], mo[0])
+    eu = rel_l2(np.stack(mg[1:3]), np.stack(mo[1:3]))
+    print(f"FX16 Couette: rel L2 rho {er:.2e}, u {eu:.2e}")
+    assert er < 3e-5 and eu < 3e-4
+
+
+def test_indicator_features_fx16():
+    """The learned indicator's features (moments, non-equilibrium stress and
+    flux, gradients) read from fixed-point storage, against the oracle's: the
+    stress and flux features carry a scale of 100, so a stored step of about
+    1.2e-5 per population moves them by up to about 1e-3 (measured 1.6e-3 at
+    most; FP32 storage: 1e-4)."""
+    from oracle import indicator as OI
+    nx, ny = 37, 29
+    fields = WL.perturbed(nx, ny, seed=21, amp_rho=0.05, amp_u=0.3)
+    fl = WL.random_flags(nx, ny, seed=4, blobs=2, rmin=3, rmax=6)
+    g = slbm.Solver(nx, ny, 3, 5, tau=0.62, precision=FX16)
+    o = O.Oracle(nx, ny, 3, 5, tau=0.62)
+    for s in (g, o):
+        s.init_equilibrium(*fields)
+        s.set_flags(fl)
+        s.step(2)
+    d = np.abs(g.indicator_eval()[0] - OI.features(o)).max()
+    print(f"FX16 indicator features: max abs difference {d:.2e}")
+    assert d < 3e-3
