@@ -96,14 +96,16 @@ typedef struct slbm_s *slbm_t;
 #define SLBM_FP64 1          /* double storage and arithmetic */
 #define SLBM_FP16 2          /* half-precision storage of the deviations (half the bytes
                                 per cell update), float arithmetic; lattice frame only */
-#define SLBM_FX16 3          /* 16-bit fixed-point storage of the deviations, one scale per
-                                population plane (plane i of a lattice holds
-                                round(s_i / sc_i), saturating at +-32767), float
+#define SLBM_FX16 3          /* 16-bit companded fixed-point storage of the deviations,
+                                one range A_i per population plane: plane i of a lattice
+                                holds q = round(32767 sign(s_i) sqrt(|s_i| / A_i)),
+                                saturating at +-32767, read back as A_i (q / 32767)^2
+                                sign(q), so the step grows like sqrt|s_i|; float
                                 arithmetic; lattice frame only.  slbm_init_equilibrium
-                                sets sc_i = max(2 max|s_i|, W_i / 4) / 32767 over the
-                                initial equilibria (until then W_i / 32767); values
-                                written later (steps, slbm_set_pops, slbm_set_state)
-                                use the scales in force */
+                                sets A_i = max(2 max|s_i|, W_i / 4) over the initial
+                                equilibria (until then W_i / 4); values written later
+                                (steps, slbm_set_pops, slbm_set_state) use the ranges in
+                                force */
 
 /* Boundary kinds for a non-periodic side (ghost layer contents):
  *  OUTFLOW   zero-order extrapolation: copy of the nearest interior cell;

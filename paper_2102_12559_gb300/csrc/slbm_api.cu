@@ -909,8 +909,9 @@ int pack_any(slbm_s* h, int k, double* host, int unpack, const double* in) {
 }
 
 // SLBM_FX16 plane scales from the equilibria staged in macro[0..2] (rho,
-// u_x, u_y): sc_i = max(2 max|s_i|, W_i / 4) / 32767 per plane of each
-// lattice.  Synchronous.
+// u_x, u_y): per plane of each lattice the range A_i = max(2 max|s_i|, W_i / 4)
+// and sc_i = A_i / 32767^2 (the companded integers reach +-32767 at +-A_i).
+// Synchronous.
 int set_fx_scales(slbm_s* h) {
   constexpr int Q = kMaxN * kMaxN;
   unsigned* d = h->at<unsigned>(h->lay.partials);  // scratch: 2 Q words
@@ -927,7 +928,7 @@ int set_fx_scales(slbm_s* h) {
       float m;
       std::memcpy(&m, &bits[k * Q + i], sizeof(m));
       const double W = L[k].w[i % L[k].n] * L[k].w[i / L[k].n];
-      h->fx_sc[k][i] = (float)(std::max(2.0 * (double)m, 0.25 * W) / 32767.0);
+      h->fx_sc[k][i] = (float)(std::max(2.0 * (double)m, 0.25 * W) / (32767.0 * 32767.0));
     }
   refresh_params(h);
   return SLBM_OK;
@@ -1158,7 +1159,8 @@ int slbm_create_in(const slbm_grid* g, int lat_lo, int lat_hi, double tau, int i
     for (int k = 0; k < 2; ++k)
       for (int i = 0; i < kMaxN * kMaxN; ++i)
         h->fx_sc[k][i] = i < L[k].n * L[k].n
-                             ? (float)(0.25 * L[k].w[i % L[k].n] * L[k].w[i / L[k].n] / 32767.0)
+                             ? (float)(0.25 * L[k].w[i % L[k].n] * L[k].w[i / L[k].n] /
+                                       (32767.0 * 32767.0))
                              : 1.0f;
   }
   refresh_params(h);

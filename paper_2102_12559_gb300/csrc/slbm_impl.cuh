@@ -62,13 +62,16 @@ struct LatTab {
   // constants through exactly even with rounded weights.
   R w[kMaxN][kMaxP];
   R vinv[kMaxN][kMaxN];         // inverse Vandermonde: phi_j(u) = sum_m vinv[j][m] h_m(u)
-  // 16-bit fixed-point storage (SLBM_FX16): plane i holds round(s_i / sc[i]),
-  // s_i = f_i - W_i; isc = 1 / sc.  Unused by the other storage types.
+  // 16-bit companded fixed-point storage (SLBM_FX16): plane i holds
+  // q = round(sign(s) sqrt(|s| isc[i])), s = f_i - W_i, read back as
+  // sc[i] q |q|; isc = 1 / sc.  Unused by the other storage types.
   R sc[kMaxN * kMaxN];
   R isc[kMaxN * kMaxN];
 };
 
-// 16-bit fixed-point storage of a deviation: value = v * (its plane's scale).
+// 16-bit companded fixed-point storage of a deviation s: q with s = sc q |q|
+// (sc its plane's scale), so the step between neighbouring values grows like
+// sqrt|s| -- fine steps for small deviations, a bounded range for large ones.
 struct fx16 {
   int16_t v;
 };
@@ -78,25 +81,36 @@ __host__ __device__ constexpr bool is_fx16() {
 }
 
 // A stored population value in the arithmetic type: plain conversion, or for
-// fixed point v times the plane's scale sc.
+// fixed point sc q |q| (q the stored integer, sc the plane's scale).
 template <class R, class S>
 __device__ __forceinline__ R from_s(S v, R) {
   return static_cast<R>(v);
 }
 template <class R>
 __device__ __forceinline__ R from_s(fx16 v, R sc) {
-  return sc * static_cast<R>(v.v);
+  const R q = static_cast<R>(v.v);
+  return sc * (q * fabs(q));
+}
+
+// The companded value sign(v) sqrt(|v| isc) of fixed-point storage, before
+// rounding.  The hardware's approximate square root (sqrt.approx.f32, a few
+// units in the last of 24 bits) is far finer than the 16-bit rounding that
+// follows.
+__device__ __forceinline__ float fx_compand(float v, float isc) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(fabsf(v) * isc));
+  return copysignf(r, v);
 }
 
 // A value to storage, rounded to nearest: plain conversion, or for fixed
-// point round(v * isc), saturating at +-32767.
+// point the companded value rounded, saturating at +-32767.
 template <class S, class R>
 __device__ __forceinline__ S to_s(R v, R) {
   return static_cast<S>(v);
 }
 template <>
 __device__ __forceinline__ fx16 to_s<fx16, float>(float v, float isc) {
-  const float q = fminf(fmaxf(rintf(v * isc), -32767.f), 32767.f);
+  const float q = fminf(fmaxf(rintf(fx_compand(v, isc)), -32767.f), 32767.f);
   return fx16{(int16_t)__float2int_rn(q)};
 }
 

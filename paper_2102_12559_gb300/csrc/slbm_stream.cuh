@@ -97,11 +97,12 @@ __device__ __forceinline__ __half to_storage<__half, float>(float v, uint32_t r,
   return __float2half_rz(__uint_as_float((b + r) & ~0x1fffu));
 }
 
-// Fixed point: floor(v * isc + r / 2^13), saturating at +-32767 -- rounded up
-// with probability equal to the distance from the value below, as above.
+// Fixed point: floor(c + r / 2^13) of the companded value c, saturating at
+// +-32767 -- rounded up with probability equal to c's distance from the
+// integer below, as above.
 template <>
 __device__ __forceinline__ fx16 to_storage<fx16, float>(float v, uint32_t r, float isc) {
-  const float q = floorf(fmaf(v, isc, (float)r * (1.0f / 8192.0f)));
+  const float q = floorf(fx_compand(v, isc) + (float)r * (1.0f / 8192.0f));
   return fx16{(int16_t)__float2int_rz(fminf(fmaxf(q, -32767.f), 32767.f))};
 }
 
@@ -120,8 +121,9 @@ __device__ __forceinline__ R row_interp(const S* __restrict__ row, const R* w) {
 }
 
 // Value of population I's stencil row at plane row pointer `row`: a single
-// tap (integer x shift) or the x-interpolation.  Fixed point: the taps stay
-// integers and the plane's scale multiplies the row's result once.
+// tap (integer x shift) or the x-interpolation.  Fixed point: the taps are
+// decoded without the plane's scale (q |q|), which multiplies the row's result
+// once.
 template <int N, bool HI, int P, int I, class S, class R>
 __device__ __forceinline__ R tap_row(const LatTab<R>& L, const S* __restrict__ row) {
   constexpr int jx = I % N;

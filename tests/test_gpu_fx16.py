@@ -1,14 +1,17 @@
-"""16-bit fixed-point storage of the deviations s_i = f_i - W_i (SLBM_FX16,
-FP32 arithmetic) against the FP64 oracle and against the FP32 path.
+"""16-bit companded fixed-point storage of the deviations s_i = f_i - W_i
+(SLBM_FX16, FP32 arithmetic) against the FP64 oracle and against the FP32
+path.
 
-Tolerances.  Plane i of a lattice stores round(s_i / sc_i) in 16 bits with
-sc_i = max(2 max|s_i|, W_i / 4) / 32767 over the initial equilibria, so a
-stored value is off by at most one step sc_i (stochastic rounding in the
-stream-collide kernel, round to nearest elsewhere): 6.1e-5 of twice the
-plane's largest initial deviation, against FP16's 2^-11 of every value.  An
-emulation of this format on the FP64 oracle (rounding the stored deviations
-after every step of the 200-step convected vortex) gives 4.3e-6 on rho and
-6.4e-5 on u; FP16 gives 4e-5 and 6.1e-4 there.  The vortex test therefore
+Tolerances.  Plane i of a lattice stores q = round(32767 sign(s) sqrt(|s| /
+A_i)) in 16 bits, with the range A_i = max(2 max|s_i|, W_i / 4) over the
+initial equilibria, and reads back A_i (q / 32767)^2 sign(q): a rounding of q
+by at most one (stochastic in the stream-collide kernel, half a step to
+nearest elsewhere) moves s by at most 2 sqrt(|s| A_i) / 32767 -- 6.1e-5 A_i
+at the top of the range, 10x finer at |s| = A_i / 100.  Emulations on the
+FP64 oracle (the stored deviations rounded after every step) give 7.6e-5 on
+u for the 200-step convected vortex and 8.9e-5 for a Mach 0.9 random-vortex
+field over 100 steps, against 6.1e-4 and 4.2e-4 for FP16 and 6.4e-5 and
+1.7e-4 for uncompanded fixed point with the same ranges.  The vortex test
 asserts the 1e-4 relative L2 on u aimed at for the reduced-precision form
 (the test that FP16 fails, `test_gpu_fp16.py`), and 2e-5 on rho.
 """
@@ -48,8 +51,8 @@ def test_uniform_flow_fx16():
 
 def test_init_within_one_step_of_the_oracle():
     """The initial equilibria of a Mach 0.9 vortex field, both lattices, are
-    stored within one scale step of the FP64 values: the scales cover the
-    field (no saturation)."""
+    stored within half a step of the FP64 values (at most A_i / 32767): the
+    ranges cover the field (no saturation)."""
     n = 96
     fields = WL.random_vortex_field(n, 6, seed=7, rmin=6.0, rmax=20.0, umax=0.9)[:3]
     g = slbm.Solver(n, n, 3, 5, tau=0.6, precision=FX16)
@@ -60,8 +63,8 @@ def test_init_within_one_step_of_the_oracle():
         a, b = g.get_pops(k), o.get_pops(k)
         W = O.lattice(o.n[k])[2]
         smax = np.abs(b - W).max(axis=(0, 1))
-        step = np.maximum(2.0 * smax, 0.25 * W) / 32767.0
-        assert (np.abs(a - b) <= 0.5 * step + 1e-7).all()
+        A = np.maximum(2.0 * smax, 0.25 * W)
+        assert (np.abs(a - b) <= A / 32767.0 + 1e-7).all()
 
 
 @pytest.fixture(scope="module")
@@ -111,10 +114,8 @@ def test_one_step_fx16_close_to_oracle(n_lo, n_hi):
 
 def test_jet_fx16_tracks_fp32():
     """The free jet (inlet / outflow / free-stream boundaries, Mach criterion),
-    100 steps: fixed-point storage against the FP32 path.  Measured 1.3e-5 on
-    rho and 1.1e-4 on u (FP16: 5e-5 and 4e-4); the jet's Mach 0.5 core sets
-    the scales of the planes, so the co-flow's smaller deviations keep fewer
-    significant bits than in the vortex."""
+    100 steps: fixed-point storage against the FP32 path.  Measured 9e-6 on
+    rho and 8e-5 on u (FP16: 5e-5 and 4e-4)."""
     nx, ny = 256, 128
     J = WL.free_jet(nx, ny, slot=16, ma_jet=0.5, ma_co=0.05)
     out = []
@@ -144,9 +145,9 @@ def test_couette_walls_fx16_tracks_oracle():
     """Diffuse walls (the wall ghosts' scaled conversions): the shear-driven
     Couette channel with the high-order lattice in the wall layers, 300 steps,
     against the FP64 oracle.  The channel starts at rest, so every plane keeps
-    the floor scale W_i / 4 / 32767 and the wall-driven deviations (about
-    0.05 W_i) keep 1 part in 1.5e4.  Measured 2.8e-6 on rho and 1.2e-4 on u;
-    bound 3e-4."""
+    the floor range W_i / 4 and the wall-driven deviations (about
+    0.05 W_i) are stored to 1 part in 7e4.  Measured 1.5e-6 on rho and 5e-5
+    on u; bound 2e-4."""
     nx, ny = 8, 32
     fl = np.zeros((ny, nx), np.uint8)
     fl[:4] = 1
@@ -167,15 +168,15 @@ def test_couette_walls_fx16_tracks_oracle():
     er = rel_l2(mg[0], mo[0])
     eu = rel_l2(np.stack(mg[1:3]), np.stack(mo[1:3]))
     print(f"FX16 Couette: rel L2 rho {er:.2e}, u {eu:.2e}")
-    assert er < 3e-5 and eu < 3e-4
+    assert er < 2e-5 and eu < 2e-4
 
 
 def test_indicator_features_fx16():
     """The learned indicator's features (moments, non-equilibrium stress and
     flux, gradients) read from fixed-point storage, against the oracle's: the
-    stress and flux features carry a scale of 100, so a stored step of about
-    1.2e-5 per population moves them by up to about 1e-3 (measured 1.6e-3 at
-    most; FP32 storage: 1e-4)."""
+    stress and flux features carry a scale of 100, so stored steps of up to
+    about 2e-5 per population move them by up to about 1e-3 (measured 1.7e-3
+    at most; FP32 storage: 1e-4)."""
     from oracle import indicator as OI
     nx, ny = 37, 29
     fields = WL.perturbed(nx, ny, seed=21, amp_rho=0.05, amp_u=0.3)
