@@ -276,10 +276,13 @@ cudaError_t launch_pond_init(const PondParams<R>& p, S* f0, S* f1, S* e0, S* e1,
 // e0 / e1) with frames lam -> g0 / g1 (eo0 / eo1) with frames lam_out.  The g
 // planes hold g / T_frame - (C_v - 1) W_i (deviation of the g populations in
 // units of the frame temperature); null when the model has one population.
+// split: one launch per lattice (when both are in use), each carrying only
+// its lattice's code.
 template <class S, class R>
 cudaError_t launch_pond_step(const PondParams<R>& p, const S* f0, const S* f1, const S* e0,
                              const S* e1, const S* lam, S* g0, S* g1, S* eo0, S* eo1,
-                             S* lam_out, const uint8_t* flag, int* err, cudaStream_t st);
+                             S* lam_out, const uint8_t* flag, int* err, int split,
+                             cudaStream_t st);
 // Per 32 x 8 tile: bit 1 / 2 if it holds a cell of lattice 0 / 1 (flag), bit
 // 4 if a cell's lattice differs from flag_old (when given).
 cudaError_t launch_pond_masks(int nx, int ny, const uint8_t* flag, const uint8_t* flag_old,
