@@ -862,8 +862,8 @@ def run_study(args):
                 "l2": "not flushed (back-to-back steps)"}), flush=True)
         return
     if args.workload == "shock":
-        # batched shock structures (configs[2]): 256 quasi-1-D instances in one
-        # grid (one launch per step for all), upstream Mach 1.2-4.0,
+        # batched shock structures (Sec. IV.C): 256 quasi-1-D instances in one
+        # grid (every step advances all of them at once), upstream Mach 1.2-4.0,
         # two-population co-moving model, initial ramp 2 mean free paths wide;
         # the paper's scheme: D2Q16 refined to D2Q25 where Kn > 0.02
         # (refinement only, every --kn-interval steps), against D2Q25 everywhere
