@@ -1,5 +1,6 @@
 """Host logic of the seeded workload generators and the benchmark's unit
-mappings (no GPU): the Couette channel batch and its relaxation times."""
+mappings (no GPU): the Couette channel batch and its relaxation times, and the
+roofline traffic's lookup in the committed ncu summary."""
 import math
 
 import numpy as np
@@ -34,3 +35,21 @@ def test_couette_tau_matches_the_mean_free_path():
         lam = nu * math.sqrt(math.pi / 2.0)
         assert abs(lam - kn * h) < 1e-9 * kn * h
     assert bench.couette_tau(0.02, 100, dt) > bench.couette_tau(0.01, 100, dt) > 0.5
+
+
+def test_profile_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
+    """The roofline's DRAM traffic is read from the committed ncu summary only
+    while the stream kernel's source hash matches the one recorded there."""
+    h = bench.kernel_hash()
+    assert len(h) == 16 and int(h, 16) >= 0
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / bench.PROFILE_SUMMARY).write_text(
+        f"- kernel_source_hash: `{h}`\n- dram_bytes_per_launch: `123456`\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_hash", lambda: h)
+    assert bench.read_traffic(h) == 123456.0
+    assert bench.read_traffic("0" * 16) is None
+    (prof / bench.PROFILE_SUMMARY).write_text("- kernel_source_hash: `x`\n")
+    assert bench.read_traffic(h) is None
+
