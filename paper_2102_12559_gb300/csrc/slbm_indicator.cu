@@ -86,8 +86,8 @@ __device__ __forceinline__ void raw_moments(const Params<R>& p, const LatTab<R>&
 // non-equilibrium stress and energy flux are M_ab minus these.
 template <int N, class R>
 __device__ __forceinline__ void moment_features(const LatTab<R>& L, const R* M, float* out) {
-  const R dr = M[0], rho = R(1) + dr;
-  const R ux = M[1] / rho, uy = M[2] / rho;
+  const R dr = M[0], rho = R(1) + dr, inv = R(1) / rho;
+  const R ux = M[1] * inv, uy = M[2] * inv;
   const R ux2 = ux * ux, uy2 = uy * uy;
   const R a2 = L.c[N - 1] * L.c[N - 1];
   const R d3x = N >= 4 ? ux * (ux2 + R(3)) : a2 * ux;
@@ -97,7 +97,7 @@ __device__ __forceinline__ void moment_features(const LatTab<R>& L, const R* M, 
   const R pyy = M[5] - (dr + rho * uy2);
   const R qx = R(0.5) * ((M[6] - rho * d3x) + (M[8] - rho * ux * (R(1) + uy2)));
   const R qy = R(0.5) * ((M[7] - rho * uy * (R(1) + ux2)) + (M[9] - rho * d3y));
-  const R T = ((R(2) + M[3] + M[5]) / rho - ux2 - uy2) / R(2);
+  const R T = ((R(2) + M[3] + M[5]) * inv - ux2 - uy2) * R(0.5);
   out[0] = (float)dr;
   out[1] = (float)ux;
   out[2] = (float)uy;
@@ -225,9 +225,10 @@ k_indicator(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restri
       const int k = cell_moments<NL, NH, false, S, R>(p, f0, f1, flag,
                                                       clampwrap(rx, p.nx, p.periodic_x),
                                                       clampwrap(ry, p.ny, p.periodic_y), m);
+      const R inv = R(1) / (R(1) + m[0]);
       sm[hy][hx][0] = m[0];
-      sm[hy][hx][1] = m[1] / (R(1) + m[0]);
-      sm[hy][hx][2] = m[2] / (R(1) + m[0]);
+      sm[hy][hx][1] = m[1] * inv;
+      sm[hy][hx][2] = m[2] * inv;
       sfl[hy][hx] = (uint8_t)k;
     }
     // the tile's own slots: the full moments stay in registers (a slot one
@@ -243,9 +244,10 @@ k_indicator(const Params<R> p, const S* f0, const S* f1, const uint8_t* __restri
       const int k = cell_moments<NL, NH, true, S, R>(p, f0, f1, flag,
                                                      clampwrap(rx, p.nx, p.periodic_x),
                                                      clampwrap(ry, p.ny, p.periodic_y), Mi[rr]);
+      const R inv = R(1) / (R(1) + Mi[rr][0]);
       sm[ly + 1][lane + 1][0] = Mi[rr][0];
-      sm[ly + 1][lane + 1][1] = Mi[rr][1] / (R(1) + Mi[rr][0]);
-      sm[ly + 1][lane + 1][2] = Mi[rr][2] / (R(1) + Mi[rr][0]);
+      sm[ly + 1][lane + 1][1] = Mi[rr][1] * inv;
+      sm[ly + 1][lane + 1][2] = Mi[rr][2] * inv;
       sfl[ly + 1][lane + 1] = (uint8_t)k;
     }
     __syncthreads();
