@@ -549,7 +549,7 @@ int check_device_error(slbm_s* h) {
   SLBM_CK(h, cudaStreamSynchronize(h->st), "sync");
   if (v & kErrTimeout) {
     h->failed = 1;
-    return fail(h, SLBM_ETIMEOUT, "a bounded device wait ran out (TMA copy did not complete)");
+    return fail(h, SLBM_ETIMEOUT, "a bounded device wait ran out");
   }
   if (v) {
     SLBM_CK(h, cudaMemsetAsync(h->at<int>(h->lay.err), 0, sizeof(int), h->st), "memset");
