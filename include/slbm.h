@@ -300,8 +300,9 @@ SLBM_API int slbm_set_boundary(slbm_t h, int side, int kind, const double *rho, 
  * the ghost ring).  Once the kernels have run directly, runs of 16 (then 2)
  * steps are replayed as CUDA graphs captured on a private stream; n = 1,
  * traced steps and a refused capture launch directly, with bit-identical
- * results.  A learned indicator or Knudsen criterion splits the steps into
- * chunks between its evaluations. */
+ * results.  A learned indicator, or a Knudsen criterion evaluated less often
+ * than every step, splits the steps into chunks between its evaluations; a
+ * Knudsen criterion every step is recorded in the replays with its step. */
 SLBM_API int slbm_step(slbm_t h, int n);
 /* The post-step kernel runs one warp per 32 x 8 tile on grids of 8192 tiles
  * and more, one thread block per tile below (a small grid's few tiles each

@@ -685,14 +685,63 @@ int step_once(slbm_s* h) {
 
 constexpr int kGraphPairs = 8;  // pairs of steps in a long graph
 
+// Knudsen criterion on the current buffer: new flags into the temporary
+// plane, the refined cells' other lattice from their current one (their new
+// native vector), masks of the new flags (with the tiles whose cells changed
+// lattice), then the band conversion (full_band: every cell that reads the
+// other lattice; else only those in the 3 x 3 tile neighbourhood of a changed
+// cell, the others having been converted after the step, from the same
+// native vectors) and the new flags.
+int apply_kn(slbm_s* h, bool full_band) {
+  uint8_t* tmp = h->at<uint8_t>(h->lay.flag_tmp);
+  uint8_t* mask = h->at<uint8_t>(h->lay.tile_mask[0]);
+  uint8_t* fl = h->flags(h->fcur);
+  const int c = h->cur, near = full_band ? 0 : 1;
+  cudaError_t e;
+  if (h->precision == SLBM_FP64) {
+    double *f0 = (double*)h->pops(c, 0), *f1 = (double*)h->pops(c, 1);
+    double *e0 = (double*)h->gp(c, 0), *e1 = (double*)h->gp(c, 1);
+    const double* lam = (const double*)h->lam(c);
+    e = launch_pond_kn<double, double>(h->qd, f0, f1, e0, e1, lam, fl, h->kn_thr, tmp, h->st);
+    SLBM_CK(h, e, "Knudsen criterion launch");
+    e = launch_pond_convert<double, double>(h->qd, f0, f1, e0, e1, lam, fl, nullptr, tmp, 0,
+                                            conv_lists(h), h->st);
+    SLBM_CK(h, e, "co-moving conversion launch");
+    SLBM_CK(h, launch_pond_masks(h->g.nx, h->g.ny, tmp, fl, mask, h->st), "mask launch");
+    e = launch_pond_convert<double, double>(h->qd, f0, f1, e0, e1, lam, tmp, mask, nullptr, near,
+                                            conv_lists(h), h->st);
+  } else {
+    float *f0 = (float*)h->pops(c, 0), *f1 = (float*)h->pops(c, 1);
+    float *e0 = (float*)h->gp(c, 0), *e1 = (float*)h->gp(c, 1);
+    const float* lam = (const float*)h->lam(c);
+    e = launch_pond_kn<float, float>(h->qf, f0, f1, e0, e1, lam, fl, h->kn_thr, tmp, h->st);
+    SLBM_CK(h, e, "Knudsen criterion launch");
+    e = launch_pond_convert<float, float>(h->qf, f0, f1, e0, e1, lam, fl, nullptr, tmp, 0,
+                                          conv_lists(h), h->st);
+    SLBM_CK(h, e, "co-moving conversion launch");
+    SLBM_CK(h, launch_pond_masks(h->g.nx, h->g.ny, tmp, fl, mask, h->st), "mask launch");
+    e = launch_pond_convert<float, float>(h->qf, f0, f1, e0, e1, lam, tmp, mask, nullptr, near,
+                                          conv_lists(h), h->st);
+  }
+  SLBM_CK(h, e, "co-moving conversion launch");
+  SLBM_CK(h, cudaMemcpyAsync(fl, tmp, h->ncell(), cudaMemcpyDeviceToDevice, h->st), "flag copy");
+  return SLBM_OK;
+}
+
+// The Knudsen criterion after every step (interval 1) is part of the step:
+// direct steps apply it after each step_once, and graph replays record it.
+bool kn_every_step(const slbm_s* h) { return h->kn_on && h->kn_interval == 1; }
+
 // m pairs of steps as one CUDA graph launch: the kernel launches of 2 m
 // step_once calls, captured once per parity state (buffer, flag and mask
 // halves, scheduler counter and work-list halves) and length on a private
 // stream and replayed on the handle's stream.  (Co-moving steps alternate the
 // buffer only.)  After two steps every parity is back where it was, so the
 // replay only advances the counters.  Longer graphs cut the host's launches
-// for small grids, where one step takes a few microseconds.  Returns 1 (and
-// stops trying) if the capture is refused, so the caller steps directly.
+// for small grids, where one step takes a few microseconds.  With the
+// Knudsen criterion every step, each recorded step is followed by the
+// criterion's launches.  Returns 1 (and stops trying) if the capture is
+// refused, so the caller steps directly.
 int step_pair(slbm_s* h, int m) {
   const int key =
       h->cur | h->mcur << 1 | h->fcur << 2 | (int)(h->sc_launches & 1) << 3 | m << 4;
@@ -714,7 +763,10 @@ int step_pair(slbm_s* h, int m) {
     int rc = SLBM_OK;
     cudaError_t e = cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      for (int i = 0; i < 2 * m && rc == SLBM_OK; ++i) rc = step_once(h);
+      for (int i = 0; i < 2 * m && rc == SLBM_OK; ++i) {
+        rc = step_once(h);
+        if (rc == SLBM_OK && kn_every_step(h)) rc = apply_kn(h, false);
+      }
       e = cudaStreamEndCapture(h->cap_st, &g);
     }
     h->st = st;
@@ -1572,48 +1624,6 @@ int slbm_set_boundary(slbm_t h, int side, int kind, const double* rho, const dou
   return build_ghost_tables(h);
 }
 
-namespace {
-// Knudsen criterion on the current buffer: new flags into the temporary
-// plane, the refined cells' other lattice from their current one (their new
-// native vector), masks of the new flags (with the tiles whose cells changed
-// lattice), then the band conversion (full_band: every cell that reads the
-// other lattice; else only those in the 3 x 3 tile neighbourhood of a changed
-// cell, the others having been converted after the step, from the same
-// native vectors) and the new flags.
-int apply_kn(slbm_s* h, bool full_band) {
-  uint8_t* tmp = h->at<uint8_t>(h->lay.flag_tmp);
-  uint8_t* mask = h->at<uint8_t>(h->lay.tile_mask[0]);
-  uint8_t* fl = h->flags(h->fcur);
-  const int c = h->cur, near = full_band ? 0 : 1;
-  cudaError_t e;
-  if (h->precision == SLBM_FP64) {
-    double *f0 = (double*)h->pops(c, 0), *f1 = (double*)h->pops(c, 1);
-    double *e0 = (double*)h->gp(c, 0), *e1 = (double*)h->gp(c, 1);
-    const double* lam = (const double*)h->lam(c);
-    e = launch_pond_kn<double, double>(h->qd, f0, f1, e0, e1, lam, fl, h->kn_thr, tmp, h->st);
-    SLBM_CK(h, e, "Knudsen criterion launch");
-    e = launch_pond_convert<double, double>(h->qd, f0, f1, e0, e1, lam, fl, nullptr, tmp, 0, conv_lists(h), h->st);
-    SLBM_CK(h, e, "co-moving conversion launch");
-    SLBM_CK(h, launch_pond_masks(h->g.nx, h->g.ny, tmp, fl, mask, h->st), "mask launch");
-    e = launch_pond_convert<double, double>(h->qd, f0, f1, e0, e1, lam, tmp, mask, nullptr, near,
-                                            conv_lists(h), h->st);
-  } else {
-    float *f0 = (float*)h->pops(c, 0), *f1 = (float*)h->pops(c, 1);
-    float *e0 = (float*)h->gp(c, 0), *e1 = (float*)h->gp(c, 1);
-    const float* lam = (const float*)h->lam(c);
-    e = launch_pond_kn<float, float>(h->qf, f0, f1, e0, e1, lam, fl, h->kn_thr, tmp, h->st);
-    SLBM_CK(h, e, "Knudsen criterion launch");
-    e = launch_pond_convert<float, float>(h->qf, f0, f1, e0, e1, lam, fl, nullptr, tmp, 0, conv_lists(h), h->st);
-    SLBM_CK(h, e, "co-moving conversion launch");
-    SLBM_CK(h, launch_pond_masks(h->g.nx, h->g.ny, tmp, fl, mask, h->st), "mask launch");
-    e = launch_pond_convert<float, float>(h->qf, f0, f1, e0, e1, lam, tmp, mask, nullptr, near,
-                                          conv_lists(h), h->st);
-  }
-  SLBM_CK(h, e, "co-moving conversion launch");
-  SLBM_CK(h, cudaMemcpyAsync(fl, tmp, h->ncell(), cudaMemcpyDeviceToDevice, h->st), "flag copy");
-  return SLBM_OK;
-}
-}  // namespace
 
 int slbm_set_kn_criterion(slbm_t h, double thr, int interval) {
   SLBM_GUARD(h);
@@ -1641,7 +1651,7 @@ int slbm_step(slbm_t h, int n) {
       const int to_eval = h->ind_interval - (int)(h->steps % h->ind_interval);
       if (to_eval < chunk) chunk = to_eval;
     }
-    if (h->kn_on) {
+    if (h->kn_on && !kn_every_step(h)) {
       const int to_eval = h->kn_interval - (int)(h->steps % h->kn_interval);
       if (to_eval < chunk) chunk = to_eval;
     }
@@ -1660,7 +1670,8 @@ int slbm_step(slbm_t h, int n) {
       done += 2 * m;
     }
     for (; done < chunk; ++done) {
-      const int rc = step_once(h);
+      int rc = step_once(h);
+      if (!rc && kn_every_step(h)) rc = apply_kn(h, false);
       if (rc) return rc;
     }
     s += chunk;
@@ -1668,7 +1679,7 @@ int slbm_step(slbm_t h, int n) {
       const int rc = apply_indicator(h);
       if (rc) return rc;
     }
-    if (h->kn_on && h->steps % h->kn_interval == 0) {
+    if (h->kn_on && !kn_every_step(h) && h->steps % h->kn_interval == 0) {
       const int rc = apply_kn(h, false);
       if (rc) return rc;
     }

@@ -119,16 +119,19 @@ def test_tuner_keeps_the_state_and_the_results():
 
 
 @pytest.mark.parametrize("precision,tol", [(slbm.SLBM_FP64, 1e-11), (slbm.SLBM_FP32, 1e-5)])
-def test_knudsen_refinement_matches_oracle(precision, tol):
-    """Knudsen criterion (Kn > 0.02, every 2 steps) on the batch against the
-    oracle's criterion on each instance: identical flags, moments within the
-    tolerance after 6 steps."""
+@pytest.mark.parametrize("interval", [2, 1])
+def test_knudsen_refinement_matches_oracle(precision, tol, interval):
+    """Knudsen criterion (Kn > 0.02, every 2 steps, or every step -- then
+    recorded in the graph replays of the second call) on the batch against
+    the oracle's criterion on each instance: identical flags, moments within
+    the tolerance after 6 steps."""
     b = instances()
     nx, steps = 64, 6
     g = batch_solver(b, nx, precision)
     g.set_flags(np.zeros((len(b), nx), np.uint8))
-    g.set_kn_criterion(0.02, 2)
-    g.step(steps)
+    g.set_kn_criterion(0.02, interval)
+    g.step(1)
+    g.step(steps - 1)
     gm, gf = g.moments(), g.get_flags()
     assert gf.sum() > 0
     for r, inst in enumerate(b):
@@ -140,9 +143,30 @@ def test_knudsen_refinement_matches_oracle(precision, tol):
                         (inst["right"][0], inst["right"][1], 0.0, inst["right"][2]))
         o.set_viscosity_law(inst["mu1"], inst["T1"], 0.5, PR)
         o.init_equilibrium(rho[None, :L], ux[None, :L], np.zeros((1, L)), T[None, :L])
-        o.set_kn_criterion(0.02, 2)
+        o.set_kn_criterion(0.02, interval)
         o.step(steps)
         np.testing.assert_array_equal(gf[r, :L], o.get_flags()[0])
         om = o.moments()
         for q in (0, 1, 3):
             assert rel_l2(gm[q][r, :L], om[q][0]) < tol
+
+
+def test_knudsen_every_step_graph_replays_equal_direct_steps():
+    """With the criterion every step, slbm_step records it in its graph
+    replays: a batch stepped one step per call (direct launches) and one
+    stepped in one call (replays of step + criterion) agree bit for bit."""
+    b = instances()
+    nx = 64
+    a = batch_solver(b, nx, slbm.SLBM_FP32)
+    c = batch_solver(b, nx, slbm.SLBM_FP32)
+    for g in (a, c):
+        g.set_flags(np.zeros((len(b), nx), np.uint8))
+        g.set_kn_criterion(0.02, 1)
+    for _ in range(9):
+        a.step(1)
+    c.step(1)
+    c.step(8)
+    for k in (0, 1):
+        np.testing.assert_array_equal(a.get_pops(k), c.get_pops(k))
+    np.testing.assert_array_equal(a.get_flags(), c.get_flags())
+    assert c.get_flags().sum() > 0
